@@ -1,0 +1,262 @@
+"""Python entry to the FP64 CPU oracle (``kp_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY.  The product path never imports this module; only
+``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` do.  It shares no code with the CUDA library.
+
+Arrays are numpy ``float64`` vectors of length N = H*W in the paper's
+y-fastest order (index ``i*H + j``, i = x column, j = y row; Sec. 2.3,
+Eq. 14-15).  A channel held as a numpy array of shape ``(W, H)`` in C order
+has exactly this layout.
+
+Parity notes: every function states which passage of arXiv 2511.17634 it
+follows.  The stencil, right-hand side and CSR assembly are pinned by the
+consistency test against the continuous PDE (Eq. 5, linearised as in Sec. 2.3)
+on quadratic fields, where the central differences are exact; GMRES and the
+projection are pinned by dense LU, the discrete-sine closed form, the Arnoldi
+identities and the FOM residual formula (tests/test_oracle_pins.py).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "kp_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libkp_oracle.so")
+
+_d = ctypes.c_double
+_i = ctypes.c_int
+_pd = ctypes.POINTER(ctypes.c_double)
+_pi = ctypes.POINTER(ctypes.c_int)
+
+NOT_CONVERGED = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile kp_oracle.c into a shared library with gcc (OpenMP if available)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    try:
+        subprocess.run(base[:2] + ["-fopenmp"] + base[2:], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        L.orc_coeffs.argtypes = [_i, _i, _d, _d, _d, _pd, _pd, _pd, _pd]
+        L.orc_rhs.argtypes = [_i, _i, _d, _d, _pd, _pd, _pd, _pd]
+        L.orc_apply.argtypes = [_i, _i, _pd, _pd, _pd]
+        L.orc_csr.argtypes = [_i, _i, _pd, _pi, _pi, _pd]
+        L.orc_csr.restype = _i
+        L.orc_csr_matvec.argtypes = [_i, _pi, _pi, _pd, _pd, _pd]
+        L.orc_gmres.argtypes = [_i, _i, _pd, _pd, _pd, _d, _i, _i, _pi, _pd, _pd, _i,
+                                _pd, _pd, _pi, _pi]
+        L.orc_gmres.restype = _i
+        L.orc_project.argtypes = [_i, _i, _i, _i, _pd, _pd, _pd, _pd, _pd]
+        L.orc_project.restype = _i
+        L.orc_dense_lu_solve.argtypes = [_i, _pd, _pd, _pd]
+        L.orc_dense_lu_solve.restype = _i
+        L.orc_march_step.argtypes = [_i, _i, _d, _d, _d, _i, _pd, _i, _pd, _pi, _i, _d, _i,
+                                     _i, _d, _i, _i, _pi, _pi, _pd, _pi, _pd]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    assert a.flags["C_CONTIGUOUS"]
+    if a.dtype == np.float64:
+        return a.ctypes.data_as(_pd)
+    assert a.dtype == np.int32
+    return a.ctypes.data_as(_pi)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+
+
+def coeffs(H, W, g2, dt, h, mt, fx=None, fy=None):
+    """Stencil coefficients (Sec. 2.3, listing after Eq. 11): array (N, 5) of
+    [diag, east, west, north, south] per grid point."""
+    mt, fx, fy = _f64(mt), _f64(fx), _f64(fy)
+    C = np.zeros(5 * H * W)
+    lib().orc_coeffs(H, W, g2, dt, h, _p(mt), _p(fx), _p(fy), _p(C))
+    return C.reshape(H * W, 5)
+
+
+def rhs(H, W, dt, h, mprev, fx=None, fy=None):
+    """b = m^{n-1}/dt - Div_h f (Sec. 2.3, last line of the listing)."""
+    mprev, fx, fy = _f64(mprev), _f64(fx), _f64(fy)
+    b = np.zeros(H * W)
+    lib().orc_rhs(H, W, dt, h, _p(mprev), _p(fx), _p(fy), _p(b))
+    return b
+
+
+def apply(H, W, C, x):
+    """y = A x from the stencil coefficients (Eq. 11)."""
+    C = np.ascontiguousarray(C, dtype=np.float64).reshape(-1)
+    x = _f64(x)
+    y = np.zeros(H * W)
+    lib().orc_apply(H, W, _p(C), _p(x), _p(y))
+    return y
+
+
+def csr(H, W, C):
+    """Explicit CSR matrix assembled from the block form (Eq. 12-15):
+    returns (rowptr, col, val)."""
+    N = H * W
+    C = np.ascontiguousarray(C, dtype=np.float64).reshape(-1)
+    rowptr = np.zeros(N + 1, dtype=np.int32)
+    col = np.zeros(5 * N, dtype=np.int32)
+    val = np.zeros(5 * N)
+    nnz = lib().orc_csr(H, W, _p(C), _p(rowptr), _p(col), _p(val))
+    return rowptr, col[:nnz].copy(), val[:nnz].copy()
+
+
+def csr_dense(H, W, C):
+    """Dense N x N copy of the CSR matrix (tiny grids only)."""
+    rowptr, col, val = csr(H, W, C)
+    N = H * W
+    A = np.zeros((N, N))
+    for r in range(N):
+        for k in range(rowptr[r], rowptr[r + 1]):
+            A[r, col[k]] = val[k]
+    return A
+
+
+def csr_matvec(rowptr, col, val, x):
+    x = _f64(x)
+    y = np.zeros(len(rowptr) - 1)
+    lib().orc_csr_matvec(len(rowptr) - 1, _p(rowptr), _p(col), _p(val), _p(x), _p(y))
+    return y
+
+
+@dataclass
+class GmresResult:
+    x: np.ndarray
+    status: int
+    iters: int
+    rel_res: float
+    hist: np.ndarray
+    V: np.ndarray | None = None      # (a'+has_next, N): rows are v_1, v_2, ...
+    Hbar: np.ndarray | None = None   # (a'+1, a') unrotated Hessenberg
+    a: int = 0
+    has_next: int = 0
+
+
+def gmres(H, W, C, b, x0=None, tol=1e-10, m=30, maxit=1000, capture=0):
+    """Restarted GMRES(m), MGS Arnoldi run twice + Givens (Saad 2003, Alg. 6.9); with
+    ``capture=a`` keeps the first cycle's basis and Hessenberg (Sec. 3,
+    Phase 1)."""
+    N = H * W
+    C = np.ascontiguousarray(C, dtype=np.float64).reshape(-1)
+    b = _f64(b)
+    x = np.zeros(N) if x0 is None else _f64(x0).copy()
+    it = np.zeros(1, dtype=np.int32)
+    rr = np.zeros(1)
+    hist = np.full(maxit + 1, np.nan)
+    capV = capH = None
+    used = np.zeros(1, dtype=np.int32)
+    nxt = np.zeros(1, dtype=np.int32)
+    if capture > 0:
+        capV = np.zeros((capture + 1) * N)
+        capH = np.zeros((capture + 1) * capture)
+    st = lib().orc_gmres(H, W, _p(C), _p(b), _p(x), tol, m, maxit, _p(it), _p(rr), _p(hist),
+                         capture, _p(capV), _p(capH), _p(used), _p(nxt))
+    res = GmresResult(x=x, status=st, iters=int(it[0]), rel_res=float(rr[0]),
+                      hist=hist[~np.isnan(hist)])
+    if capture > 0:
+        a = int(used[0])
+        res.a, res.has_next = a, int(nxt[0])
+        res.V = capV.reshape(capture + 1, N)[: a + res.has_next].copy()
+        res.Hbar = capH.reshape(capture, capture + 1).T[: a + 1, :a].copy()
+    return res
+
+
+def project(V, Hbar, a, has_next, r, xinit=None):
+    """Sec. 3, Phase 2: x0 = xinit + V_a H_a^{-1} V_a^T r (least squares on
+    Hbar if H_a is numerically singular).  Returns (x0, used_lsq)."""
+    N = V.shape[1]
+    lda = a + 1
+    Vc = np.zeros((a + 1) * N)
+    Vc[: V.shape[0] * N] = V.reshape(-1)
+    Hc = np.zeros((a + 1) * max(a, 1))
+    Hc.reshape(max(a, 1), a + 1)[:a, : Hbar.shape[0]] = Hbar.T
+    r = _f64(r)
+    xi = _f64(xinit)
+    x0 = np.zeros(N)
+    lsq = lib().orc_project(N, a, lda, has_next, _p(Vc), _p(Hc), _p(r), _p(xi), _p(x0))
+    return x0, bool(lsq)
+
+
+def dense_lu_solve(A, b):
+    """Dense LU with partial pivoting (tiny systems)."""
+    n = A.shape[0]
+    A = np.ascontiguousarray(A, dtype=np.float64).copy()
+    b = _f64(b).copy()
+    x = np.zeros(n)
+    rc = lib().orc_dense_lu_solve(n, _p(A.reshape(-1)), _p(b), _p(x))
+    if rc != 0:
+        raise ArithmeticError("singular matrix")
+    return x
+
+
+MODE_PROJECTED, MODE_PLAIN, MODE_WARM = 0, 1, 2
+
+
+@dataclass
+class StepStats:
+    seed_iters: np.ndarray
+    tgt_iters: np.ndarray
+    tgt_res: np.ndarray
+    tgt_status: np.ndarray
+    tgt_x0res: np.ndarray
+
+
+def march_step(H, W, dt, h, g2, mseed, mtgt, target_seed, mode=MODE_PROJECTED,
+               tol_seed=1e-10, m_seed=40, a=40, tol_ref=1e-8, m_ref=40, maxit=1000):
+    """One timestep of Sec. 2.3 + Sec. 3 for seeds and targets of one grid
+    size (f = 0).  ``mseed`` (nseed, N) and ``mtgt`` (ntgt, N) are updated in
+    place from m^{n-1} to m^n."""
+    assert mseed.dtype == np.float64 and mseed.flags["C_CONTIGUOUS"]
+    assert mtgt.dtype == np.float64 and mtgt.flags["C_CONTIGUOUS"]
+    ns, nt = mseed.shape[0], mtgt.shape[0]
+    ts = np.ascontiguousarray(target_seed, dtype=np.int32)
+    st = StepStats(np.zeros(ns, np.int32), np.zeros(nt, np.int32), np.zeros(nt),
+                   np.zeros(nt, np.int32), np.zeros(nt))
+    lib().orc_march_step(H, W, dt, h, g2, ns, _p(mseed), nt, _p(mtgt), _p(ts), mode,
+                         tol_seed, m_seed, a, tol_ref, m_ref, maxit, _p(st.seed_iters),
+                         _p(st.tgt_iters), _p(st.tgt_res), _p(st.tgt_status), _p(st.tgt_x0res))
+    return st
+
+
+def march(H, W, T, g2, seeds, targets, target_seed, steps=None, **kw):
+    """Time march n = 1..steps (default T) with dt = 1/T, h = 1/H (Sec. 2.3),
+    from m^0 = the images.  Returns (m_seed^n, m_target^n, list of StepStats)."""
+    dt, h = 1.0 / T, 1.0 / H
+    ms = np.array(seeds, dtype=np.float64).reshape(len(seeds), -1).copy()
+    mt = np.array(targets, dtype=np.float64).reshape(len(targets), -1).copy()
+    stats = []
+    for n in range(steps if steps is not None else T):
+        stats.append(march_step(H, W, dt, h, float(g2[n]), ms, mt, target_seed, **kw))
+    return ms, mt, stats
