@@ -1,0 +1,180 @@
+/*
+ * kp.h -- C ABI of the GB300 (sm_103a) cross-matrix Krylov projection solver
+ * for the implicit log-density Fokker-Planck systems of
+ * "Efficient Score Pre-computation for Diffusion Models via Cross-Matrix
+ * Krylov Projection" (arXiv 2511.17634).
+ *
+ * One linear system per (image channel, timestep n):  A^n m^n = b^n  (Eq. 12),
+ * the five-point discretisation of Sec. 2.3 (Eq. 11 and its coefficient
+ * listing), with the lagged field m~ = m^{n-1} in the first-order term.
+ *
+ * Vectors.  A channel of H rows and W columns is N = H*W doubles in the
+ * paper's y-fastest order (Eq. 14): element p = i*H + j with i in [0,W) the x
+ * index (east = i+1) and j in [0,H) the y index (north = j+1).  Out-of-grid
+ * neighbours are zero (zero padding, Sec. 2.3).
+ *
+ * Memory and ownership.  Every vector argument is a DEVICE pointer owned by
+ * the caller (8-byte aligned, N contiguous doubles); arrays of such pointers
+ * (`const double* const* b`) and arrays of kp_op descriptors are HOST arrays
+ * that the library copies before the call returns.  The library owns its
+ * seed-basis store and workspaces; they live until kp_destroy.
+ *
+ * Streams.  All work is enqueued on the context's CUDA stream and the calls
+ * return before it finishes; read outputs after synchronising that stream.
+ * One context serves one stream from one host thread at a time.
+ *
+ * Errors.  Every call returns a kp_status: KP_OK, or a negative code for an
+ * API-level failure (then nothing was enqueued and kp_last_error() explains
+ * it).  Per-system convergence is reported through kp_info (device array),
+ * never as a return code.  No C++ exception crosses this interface.
+ */
+#ifndef KP_H
+#define KP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  KP_OK = 0,
+  KP_NOT_CONVERGED = 1,   /* kp_info.status: maxit reached, best iterate returned */
+  KP_BREAKDOWN = 2,       /* kp_info.status: non-finite residual (NaN/Inf input)  */
+  KP_ERR_ARG = -1,        /* invalid argument (size, pointer, option)               */
+  KP_ERR_CUDA = -2,       /* a CUDA runtime call failed                             */
+  KP_ERR_OOM = -3,        /* device allocation failed                               */
+  KP_ERR_NO_BASIS = -4,   /* project_targets: no basis stored for (seed, timestep)  */
+  KP_ERR_TIMEOUT = -5,    /* reserved: a bounded device wait gave up                */
+  KP_ERR_UNSUPPORTED = -6 /* valid request this build does not implement            */
+} kp_status;
+
+typedef enum {
+  KP_PREC_FP64 = 0,  /* everything in FP64 */
+  KP_PREC_MIXED = 1  /* FP32 Krylov vectors and stencil inside FP64 iterative
+                        refinement; FP64 reductions, Hessenberg and Givens;
+                        BF16 tensor-core projection with FP32 accumulation */
+} kp_precision;
+
+typedef struct kp_ctx kp_ctx;
+
+/* Context options.  Fill with kp_options_default() and change what you need. */
+typedef struct {
+  int max_seeds;     /* seed-basis slots in the store (>= 1)                     */
+  int max_a;         /* basis vectors kept per slot: a of Sec. 3 (1..64)          */
+  int max_n;         /* largest N = H*W any call will pass (<= 16384)             */
+  int precision;     /* kp_precision                                              */
+  int smem_vectors;  /* Krylov vectors held in shared memory per system; the rest
+                        live in a device workspace (0 = choose automatically)      */
+  int reorth;        /* 0: CGS2, two classical Gram-Schmidt passes every step;
+                        1: second pass only when the first removed more than
+                        half of the vector's norm (Daniel-Gragg-Kaufman-Stewart)  */
+} kp_options;
+
+/* Operator of one system (Sec. 2.3): A(m~; g^2, dt, h, f).  `mtilde` is the
+ * lagged field m~ (device, N doubles).  fx, fy are the drift components on
+ * the grid (device, N doubles each) or NULL for f = 0, the paper's setting
+ * (Sec. 5).  g2 = (g^n)^2. */
+typedef struct {
+  int H, W;
+  double dt, g2, h;
+  const double* mtilde;
+  const double* fx;
+  const double* fy;
+} kp_op;
+
+/* Per-system result, written to a device array by the solver calls. */
+typedef struct {
+  int iters;       /* Arnoldi steps (operator applications, residuals excluded) */
+  int status;      /* 0 converged, KP_NOT_CONVERGED, KP_BREAKDOWN               */
+  double rel_res;  /* ||b - A x||_2 / ||b||_2 of the returned x, in FP64        */
+} kp_info;
+
+void kp_options_default(kp_options* opt);
+
+/* Create a context bound to `cuda_stream` (a cudaStream_t; NULL = legacy
+ * default stream) on the current device.  Allocates the basis store. */
+kp_status kp_create(kp_ctx** ctx, const kp_options* opt, void* cuda_stream);
+kp_status kp_destroy(kp_ctx* ctx);
+kp_status kp_set_stream(kp_ctx* ctx, void* cuda_stream);
+/* Last error message of this context (static string storage of the context). */
+const char* kp_last_error(kp_ctx* ctx);
+/* Library version string, e.g. "kp 0.1 sm_103a". */
+const char* kp_version(void);
+
+/*
+ * y_k = A_k x_k for k < nsys (Sec. 2.3, Eq. 11; matrix form Eq. 12-13).
+ * ops[k] describes A_k; x[k], y[k] device vectors of N_k doubles.
+ */
+kp_status kp_apply(kp_ctx* ctx, int nsys, const kp_op* ops, const double* const* x,
+                   double* const* y);
+
+/*
+ * b_k = m^{n-1}_k / dt - Div_h f  (Sec. 2.3, right-hand side of Eq. 11).
+ * mprev[k] device vector; f taken from ops[k].fx/fy (NULL = 0).
+ */
+kp_status kp_rhs(kp_ctx* ctx, int nsys, const kp_op* ops, const double* const* mprev,
+                 double* const* b);
+
+/*
+ * Phase 1 of Sec. 3: solve the seed systems A_k x_k = b_k with restarted
+ * GMRES(m) (CGS2 Arnoldi, FP64 Givens least squares, true FP64 residual at
+ * every restart) to ||b - A x|| <= tol ||b|| or maxit Arnoldi steps.
+ * x[k] holds the initial guess on entry (zero for the paper's seed solve) and
+ * the solution on return.  The first restart cycle's orthonormal basis
+ * v_1..v_{a'+1} (v_1 = r0/||r0||) and Hessenberg matrix of every system are
+ * kept in the context until the next kp_seed_solve, for kp_store_basis.
+ * info: device array of nsys kp_info, or NULL.  1 <= m <= 64; the number of
+ * kept vectors a' = min(max_a, steps of the first cycle).
+ */
+kp_status kp_seed_solve(kp_ctx* ctx, int nsys, const kp_op* ops, const double* const* b,
+                        double* const* x, double tol, int m, int maxit, kp_info* info);
+
+/*
+ * Keep the basis of system `sys` of the last kp_seed_solve as the basis
+ * V_a^n of seed slot `seed_id` for timestep `timestep` (Sec. 3: one basis per
+ * timestep), replacing what the slot held.  Also factors H_a (Givens QR)
+ * once, so that each projection needs only a rotation and a triangular solve.
+ */
+kp_status kp_store_basis(kp_ctx* ctx, int seed_id, int timestep, int sys);
+
+/*
+ * Phase 2 of Sec. 3 for nt targets that share seed slot `seed_id`:
+ *   c = V_a^T r_k,   alpha = H_a^{-1} c,   x_k <- x_k + V_a alpha
+ * with H_a = V_a^T A_seed V_a from the seed's Arnoldi process.  r_k is the
+ * target's right-hand side b_k (paper: x_k = 0 on entry, so x_k becomes the
+ * initial guess V_a alpha) or the residual b_k - A_k x_k of a guess x_k.  If
+ * H_a is numerically singular (Givens pivot < 1e-14 max|H_a|) and v_{a+1} was
+ * kept, alpha minimises ||Hbar_a alpha - V_{a+1}^T r_k|| instead.
+ * Returns KP_ERR_NO_BASIS if the slot holds no basis for `timestep`.
+ * ops[k] only supplies H, W (checked against the stored basis).
+ */
+kp_status kp_project_targets(kp_ctx* ctx, int seed_id, int timestep, int nt,
+                             const kp_op* ops, const double* const* r_or_b, double* const* x);
+
+/* As kp_project_targets, with a seed slot per target (one launch). */
+kp_status kp_project_targets_multi(kp_ctx* ctx, int timestep, int nt, const int* seed_ids,
+                                   const kp_op* ops, const double* const* r_or_b,
+                                   double* const* x);
+
+/*
+ * The refine step of Sec. 3 (end of Phase 2): GMRES(m) on the target's own
+ * A_k from the initial guess in x[k] to ||b - A x|| <= tol ||b|| (FP64 true
+ * residual), or maxit Arnoldi steps.  Same algorithm as kp_seed_solve
+ * without keeping a basis.  info: device array of nsys kp_info, or NULL.
+ */
+kp_status kp_refine(kp_ctx* ctx, int nsys, const kp_op* ops, const double* const* b,
+                    double* const* x, double tol, int m, int maxit, kp_info* info);
+
+/* Inspect a stored basis (tests, diagnostics).  a_out, has_next_out, host.
+ * V (device, N*(a+1) doubles, column k = v_{k+1}) and Hbar (host, (a+1)*a
+ * doubles column-major, unrotated) may be NULL. */
+kp_status kp_basis_get(kp_ctx* ctx, int seed_id, int timestep, int* a_out, int* has_next_out,
+                       double* V, double* Hbar);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KP_H */

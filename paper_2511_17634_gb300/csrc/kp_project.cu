@@ -1,0 +1,165 @@
+// kp_project.cu -- the seed-basis store and the Galerkin projection of
+// Sec. 3, Phase 2, in FP64:
+//   store:    V_a^n and the Givens QR factors of H_a = V_a^T A_seed V_a
+//             (taken from the seed's Arnoldi process), once per seed;
+//   project:  c = V_a^T r,  alpha = H_a^{-1} c,  x <- x + V_a alpha,
+//             one thread block per target, the seed's V read through L2 by
+//             all targets that share it.
+#include "kp_internal.cuh"
+
+namespace kp {
+namespace {
+
+__device__ __forceinline__ void givens2(double a, double b, double& c, double& s) {
+  if (b == 0.0) { c = 1.0; s = 0.0; return; }
+  const double r = hypot(a, b);
+  const double ir = 1.0 / r;
+  c = a * ir;
+  s = b * ir;
+}
+
+// Copies the captured basis of system p.sys into slot p.seed_id and factors
+// its Hessenberg matrix.  One block; thread 0 does the (tiny) factorisation.
+__global__ void factor_kernel(const FactorParams p) {
+  const CapMeta cm = p.capMeta[p.sys];
+  const int a = cm.valid ? cm.a : 0;
+  const int hn = cm.valid ? cm.has_next : 0;
+  const int N = cm.N;
+  const double* cv = p.capV + (size_t)p.sys * (p.cap_a + 1) * p.cap_ld;
+  double* sv = p.slotV + (size_t)p.seed_id * (p.max_a + 1) * p.ld;
+  const int nvec = a + hn;
+  for (int idx = threadIdx.x; idx < nvec * N; idx += blockDim.x) {
+    const int k = idx / N, q = idx - k * N;
+    sv[(size_t)k * p.ld + q] = cv[(size_t)k * p.cap_ld + q];
+  }
+  if (threadIdx.x != 0) return;
+  const int cld = p.cap_a + 1;
+  const int sld = p.max_a + 1;
+  const double* ch = p.capH + (size_t)p.sys * cld * p.cap_a;
+  double* sh = p.slotH + (size_t)p.seed_id * sld * p.max_a;
+  double* R = p.slotR + (size_t)p.seed_id * sld * p.max_a;   // (a+1) x a, ld max_a+1
+  double* rot = p.slotRot + (size_t)p.seed_id * 2 * p.max_a;
+  double hmax = 0.0;
+  for (int j = 0; j < a; ++j)
+    for (int i = 0; i <= a; ++i) {
+      const double v = (i <= j + 1) ? ch[i + j * cld] : 0.0;
+      sh[i + j * sld] = v;
+      if (i < a) hmax = fmax(hmax, fabs(v));
+    }
+  int lsq = 0, nrot = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    lsq = pass;
+    const int nr = lsq ? a + 1 : a;
+    for (int j = 0; j < a; ++j)
+      for (int i = 0; i <= a; ++i) R[i + j * sld] = (i < nr) ? sh[i + j * sld] : 0.0;
+    nrot = 0;
+    for (int j = 0; j < a && j + 1 < nr; ++j) {
+      double c, s;
+      givens2(R[j + j * sld], R[(j + 1) + j * sld], c, s);
+      for (int l = j; l < a; ++l) {
+        const double t1 = R[j + l * sld], t2 = R[(j + 1) + l * sld];
+        R[j + l * sld] = c * t1 + s * t2;
+        R[(j + 1) + l * sld] = -s * t1 + c * t2;
+      }
+      rot[2 * j] = c;
+      rot[2 * j + 1] = s;
+      ++nrot;
+    }
+    int singular = 0;
+    for (int j = 0; j < a; ++j)
+      if (!(fabs(R[j + j * sld]) > 1e-14 * hmax)) singular = 1;
+    if (singular && !lsq && hn) continue;
+    break;
+  }
+  SlotMeta mt;
+  mt.a = a;
+  mt.has_next = hn;
+  mt.timestep = p.timestep;
+  mt.N = N;
+  mt.lsq = lsq;
+  mt.nrot = nrot;
+  mt.pad_[0] = mt.pad_[1] = 0;
+  p.meta[p.seed_id] = mt;
+}
+
+template <int EPT, int NT>
+__global__ void __launch_bounds__(NT) project_fp64_kernel(const ProjParams p) {
+  constexpr int NWARPS = NT / 32;
+  __shared__ double red[NWARPS * kMaxV];
+  __shared__ double cvec[kMaxV];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int t = blockIdx.x; t < p.nt; t += gridDim.x) {
+    const SysDesc d = p.sys[t];
+    const int N = d.H * d.W;
+    const SlotMeta mt = p.meta[d.slot];
+    if (mt.timestep != p.timestep || mt.N != N || mt.a == 0) continue;   // uniform per block
+    const int a = mt.a;
+    const int nv = mt.lsq ? a + 1 : a;
+    const double* V = p.slotV + (size_t)d.slot * (p.max_a + 1) * p.ld;
+    double r[EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int pp = tid + k * NT;
+      r[k] = (pp < N) ? d.b[pp] : 0.0;
+    }
+    // c = V^T r (c_i over the first nv basis vectors)
+    block_partials<NT>(nv, [&](int i) {
+      const double* vi = V + (size_t)i * p.ld;
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int pp = tid + k * NT;
+        if (pp < N) s += vi[pp] * r[k];
+      }
+      return s;
+    }, red);
+    if (warp == 0) {
+      for (int i = lane; i < nv; i += 32) cvec[i] = cross_warp<NT>(red, i);
+      __syncwarp();
+      if (lane == 0) {
+        const int sld = p.max_a + 1;
+        const double* R = p.slotR + (size_t)d.slot * sld * p.max_a;
+        const double* rot = p.slotRot + (size_t)d.slot * 2 * p.max_a;
+        for (int j = 0; j < mt.nrot; ++j) {
+          const double c = rot[2 * j], s = rot[2 * j + 1];
+          const double t1 = cvec[j], t2 = cvec[j + 1];
+          cvec[j] = c * t1 + s * t2;
+          cvec[j + 1] = -s * t1 + c * t2;
+        }
+        for (int i = a - 1; i >= 0; --i) {          // alpha overwrites cvec[0..a)
+          double s = cvec[i];
+          for (int l = i + 1; l < a; ++l) s -= R[i + l * sld] * cvec[l];
+          const double rii = R[i + i * sld];
+          cvec[i] = (rii != 0.0) ? s / rii : 0.0;
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int pp = tid + k * NT;
+      if (pp < N) {
+        double xv = d.x[pp];
+        for (int i = 0; i < a; ++i) xv = fma(cvec[i], V[(size_t)i * p.ld + pp], xv);
+        d.x[pp] = xv;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_factor(const FactorParams& p, cudaStream_t st) {
+  factor_kernel<<<1, 256, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project_fp64(const ProjParams& p, int ept, int nt, cudaStream_t st) {
+  if (ept == 4 && nt == 256) project_fp64_kernel<4, 256><<<p.nt, 256, 0, st>>>(p);
+  else if (ept == 8 && nt == 512) project_fp64_kernel<8, 512><<<p.nt, 512, 0, st>>>(p);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+}  // namespace kp

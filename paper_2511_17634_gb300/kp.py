@@ -1,0 +1,225 @@
+"""Thin Python binding of the C ABI in ``include/kp.h`` (argument marshalling
+only; every step of the solver runs in the CUDA library ``libkp.so``).
+
+Vectors are CUDA ``torch.float64`` tensors.  A batch of systems of one grid
+size is a 2-D tensor ``(nsys, N)``; a list of 1-D tensors also works.  The
+library must have been built (``paper_2511_17634_gb300.build``); importing
+this module without it raises ``ImportError`` -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libkp.so")
+
+OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
+ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NO_BASIS, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+PREC_FP64, PREC_MIXED = 0, 1
+
+
+class KPError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"kp status {status}: {msg}")
+        self.status = status
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("max_seeds", ctypes.c_int), ("max_a", ctypes.c_int), ("max_n", ctypes.c_int),
+                ("precision", ctypes.c_int), ("smem_vectors", ctypes.c_int),
+                ("reorth", ctypes.c_int)]
+
+
+# kp_op: int H, W; double dt, g2, h; const double *mtilde, *fx, *fy
+OP_DTYPE = np.dtype({"names": ["H", "W", "dt", "g2", "h", "mt", "fx", "fy"],
+                     "formats": [np.int32, np.int32, np.float64, np.float64, np.float64,
+                                 np.uint64, np.uint64, np.uint64],
+                     "offsets": [0, 4, 8, 16, 24, 32, 40, 48], "itemsize": 56})
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA library not built: {LIB_PATH} (run paper_2511_17634_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.kp_options_default.argtypes = [ctypes.POINTER(_Options)]
+        L.kp_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_Options), vp]
+        L.kp_destroy.argtypes = [vp]
+        L.kp_set_stream.argtypes = [vp, vp]
+        L.kp_last_error.argtypes = [vp]
+        L.kp_last_error.restype = ctypes.c_char_p
+        L.kp_version.restype = ctypes.c_char_p
+        L.kp_apply.argtypes = [vp, i, vp, vp, vp]
+        L.kp_rhs.argtypes = [vp, i, vp, vp, vp]
+        L.kp_seed_solve.argtypes = [vp, i, vp, vp, vp, d, i, i, vp]
+        L.kp_refine.argtypes = [vp, i, vp, vp, vp, d, i, i, vp]
+        L.kp_store_basis.argtypes = [vp, i, i, i]
+        L.kp_project_targets.argtypes = [vp, i, i, i, vp, vp, vp]
+        L.kp_project_targets_multi.argtypes = [vp, i, i, vp, vp, vp, vp]
+        L.kp_basis_get.argtypes = [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i), vp, vp]
+        for f in ("kp_create", "kp_destroy", "kp_set_stream", "kp_apply", "kp_rhs", "kp_seed_solve",
+                  "kp_refine", "kp_store_basis", "kp_project_targets", "kp_project_targets_multi",
+                  "kp_basis_get"):
+            getattr(L, f).restype = i
+        _lib = L
+    return _lib
+
+
+def version() -> str:
+    return lib().kp_version().decode()
+
+
+def _ptrs(vs):
+    """Host array of device pointers for a 2-D tensor (rows) or a list of tensors."""
+    import torch
+    if isinstance(vs, torch.Tensor):
+        assert vs.is_cuda and vs.dtype == torch.float64 and vs.dim() == 2 and vs.stride(1) == 1
+        base = vs.data_ptr()
+        arr = (np.arange(vs.shape[0], dtype=np.uint64) * np.uint64(vs.stride(0) * 8)
+               + np.uint64(base))
+    else:
+        for v in vs:
+            assert v.is_cuda and v.dtype == torch.float64 and v.is_contiguous()
+        arr = np.array([v.data_ptr() for v in vs], dtype=np.uint64)
+    return np.ascontiguousarray(arr)
+
+
+class Ops:
+    """Host array of kp_op descriptors plus references to the tensors they
+    point to (so that those stay alive while the descriptors are in use)."""
+
+    def __init__(self, arr, refs):
+        self.arr = arr
+        self.refs = refs
+
+    def __len__(self):
+        return len(self.arr)
+
+    @staticmethod
+    def concat(parts):
+        return Ops(np.concatenate([p.arr for p in parts]), tuple(r for p in parts for r in p.refs))
+
+
+def make_ops(H, W, dt, g2, h, mtilde, fx=None, fy=None):
+    """kp_op descriptors for systems of one grid size; dt, g2, h may be
+    per-system arrays."""
+    mt = _ptrs(mtilde)
+    n = len(mt)
+    ops = np.zeros(n, dtype=OP_DTYPE)
+    ops["H"], ops["W"] = H, W
+    ops["dt"], ops["g2"], ops["h"] = dt, g2, h
+    ops["mt"] = mt
+    ops["fx"] = _ptrs(fx) if fx is not None else 0
+    ops["fy"] = _ptrs(fy) if fy is not None else 0
+    return Ops(ops, (mtilde, fx, fy))
+
+
+def info_tensor(nsys, device="cuda"):
+    import torch
+    return torch.zeros((nsys, 2), dtype=torch.float64, device=device)
+
+
+def decode_info(info):
+    """(iters, status, rel_res) numpy arrays from an info tensor."""
+    a = info.detach().cpu().numpy()
+    i32 = a.view(np.int32).reshape(a.shape[0], 4)
+    return i32[:, 0].copy(), i32[:, 1].copy(), a[:, 1].copy()
+
+
+class Context:
+    """A kp_ctx bound to a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, max_seeds=64, max_a=40, max_n=4096, precision=PREC_FP64, smem_vectors=0,
+                 reorth=0, stream=None):
+        import torch
+        L = lib()
+        o = _Options()
+        L.kp_options_default(ctypes.byref(o))
+        o.max_seeds, o.max_a, o.max_n = max_seeds, max_a, max_n
+        o.precision, o.smem_vectors, o.reorth = precision, smem_vectors, reorth
+        self._h = ctypes.c_void_p()
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        st = L.kp_create(ctypes.byref(self._h), ctypes.byref(o), ctypes.c_void_p(s.cuda_stream))
+        if st != OK:
+            raise KPError(st, "kp_create failed")
+
+    def close(self):
+        if self._h:
+            lib().kp_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != OK:
+            raise KPError(st, lib().kp_last_error(self._h).decode())
+
+    @staticmethod
+    def _arr(a):
+        if isinstance(a, Ops):
+            a = a.arr
+        return a.ctypes.data_as(ctypes.c_void_p)
+
+    def apply(self, ops, x, y):
+        self._check(lib().kp_apply(self._h, len(ops), self._arr(ops), self._arr(_ptrs(x)),
+                                   self._arr(_ptrs(y))))
+
+    def rhs(self, ops, mprev, b):
+        self._check(lib().kp_rhs(self._h, len(ops), self._arr(ops), self._arr(_ptrs(mprev)),
+                                 self._arr(_ptrs(b))))
+
+    def seed_solve(self, ops, b, x, tol=1e-10, m=40, maxit=1000, info=None):
+        if info is None:
+            info = info_tensor(len(ops))
+        self._check(lib().kp_seed_solve(self._h, len(ops), self._arr(ops), self._arr(_ptrs(b)),
+                                        self._arr(_ptrs(x)), tol, m, maxit,
+                                        ctypes.c_void_p(info.data_ptr())))
+        return info
+
+    def refine(self, ops, b, x, tol=1e-8, m=40, maxit=1000, info=None):
+        if info is None:
+            info = info_tensor(len(ops))
+        self._check(lib().kp_refine(self._h, len(ops), self._arr(ops), self._arr(_ptrs(b)),
+                                    self._arr(_ptrs(x)), tol, m, maxit,
+                                    ctypes.c_void_p(info.data_ptr())))
+        return info
+
+    def store_basis(self, seed_id, timestep, sys):
+        self._check(lib().kp_store_basis(self._h, seed_id, timestep, sys))
+
+    def project_targets(self, seed_id, timestep, ops, r, x):
+        self._check(lib().kp_project_targets(self._h, seed_id, timestep, len(ops), self._arr(ops),
+                                             self._arr(_ptrs(r)), self._arr(_ptrs(x))))
+
+    def project_targets_multi(self, timestep, seed_ids, ops, r, x):
+        ids = np.ascontiguousarray(seed_ids, dtype=np.int32)
+        self._check(lib().kp_project_targets_multi(self._h, timestep, len(ops), self._arr(ids),
+                                                   self._arr(ops), self._arr(_ptrs(r)),
+                                                   self._arr(_ptrs(x))))
+
+    def basis_get(self, seed_id, timestep, N):
+        """(a, has_next, V (a+has_next, N) tensor, Hbar (a+1, a) numpy)."""
+        import torch
+        a = ctypes.c_int()
+        hn = ctypes.c_int()
+        self._check(lib().kp_basis_get(self._h, seed_id, timestep, ctypes.byref(a),
+                                       ctypes.byref(hn), None, None))
+        V = torch.zeros((a.value + hn.value, N), dtype=torch.float64, device="cuda")
+        Hb = np.zeros((a.value + 1) * max(a.value, 1))
+        self._check(lib().kp_basis_get(self._h, seed_id, timestep, None, None,
+                                       ctypes.c_void_p(V.data_ptr()) if V.numel() else None,
+                                       self._arr(Hb)))
+        Hbar = Hb[: (a.value + 1) * a.value].reshape(a.value, a.value + 1).T.copy()
+        return a.value, hn.value, V, Hbar
