@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark: target systems solved per second to relative residual 1e-8,
+projected + refine vs plain GMRES, on one GB300 (or N replicas under torchrun).
+
+Workload (default): 32x32x3 blob images, 10 templates with one seed image
+each and 256 target images, T = 1000 implicit timesteps, GMRES restart 40,
+FP64 throughout -- 768 target systems and 30 seed systems per timestep.
+Synthetic images of the paper's CIFAR-10 shape stand in for the dataset.
+
+One step = one whole march n = 1..T over the batch (every row of the hot
+path: right-hand sides, seed GMRES with basis capture, basis store,
+projection, refine), from the initial images already resident in HBM.  The
+per-timestep working set fits in L2, so L2 is flushed (a 512 MiB write)
+between timed steps, outside the timed events.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (a
+bounded sample of the same workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2511_17634_gb300 import synth  # noqa: E402
+
+FP64_PEAK_TFLOPS = 152 * 2070e6 * 4 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+METRIC = "target systems solved/s to rel. residual 1e-8, projected vs plain GMRES, 1 GB300"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", type=int, default=2)
+    ap.add_argument("--T", type=int, default=None, help="fewer timesteps (testing only)")
+    ap.add_argument("--ntargets", type=int, default=None, help="fewer targets (testing only)")
+    ap.add_argument("--no-baselines", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=12)
+    return ap.parse_args()
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if "Active" in f[5 + k] and "Not" not in f[5 + k]:
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(wl, steps, threads):
+    """Oracle march over the first `steps` timesteps of the workload (all seeds
+    and targets); returns (target systems, wall seconds)."""
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    from oracle import oracle as O
+    O.build()
+    nsys, wall = 0, 0.0
+    for g in wl.groups:
+        t0 = time.perf_counter()
+        O.march(g.H, g.W, wl.T, wl.g2, g.seeds, g.targets, g.target_seed, steps=steps,
+                tol_seed=wl.tol_seed, m_seed=wl.m_seed, a=wl.a, tol_ref=wl.tol, m_ref=wl.m)
+        wall += time.perf_counter() - t0
+        nsys += g.targets.shape[0] * steps
+    return nsys, wall
+
+
+def workload(args, rank=0):
+    wl = synth.config(args.config, T=args.T, ntargets=args.ntargets)
+    if rank:
+        # each replica solves its own targets (weak scaling, no exchange)
+        nt = args.ntargets
+        base = synth.config(args.config, T=args.T, ntargets=nt)
+        for gi, g in enumerate(base.groups):
+            ntg = g.targets.shape[0] // g.channels
+            tag = gi + 1 if args.config == 3 else 0
+            ng = synth.make_group(1234 + args.config, g.H, g.W, g.channels,
+                                  g.seeds.shape[0] // g.channels, ntg, tag=tag,
+                                  target_offset=rank * ntg)
+            wl.groups[gi] = ng
+    return wl
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workload(args)
+    cores = cpu_cores()
+    k = args.cpu_sample_steps
+    for _ in range(args.warmup):
+        oracle_sample(wl, 1, cores)
+    tot_sys, tot_wall = 0, 0.0
+    for _ in range(args.steps):
+        n, w = oracle_sample(wl, k, cores)
+        tot_sys += n
+        tot_wall += w
+    value = tot_sys / tot_wall
+    sample = (f"first {k} of {wl.T} timesteps of the full workload per step "
+              f"({tot_sys // args.steps} target systems + seeds), OpenMP over systems")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "systems/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * tot_wall / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "T": wl.T, "targets": wl.n_target_planes,
+                   "seeds": wl.n_seed_planes, "tol": wl.tol},
+        "cpu_baseline": {"value": value, "unit": "systems/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "systems/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2511_17634_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    from paper_2511_17634_gb300 import kp
+
+    wl = workload(args, rank)
+    T = wl.T
+    nmax = max(g.N for g in wl.groups)
+    ctx = kp.Context(max_seeds=max(wl.n_seed_planes, 1), max_a=wl.a, max_n=nmax)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    img_s = [torch.as_tensor(g.seeds.reshape(len(g.seeds), -1), device=dev) for g in wl.groups]
+    img_t = [torch.as_tensor(g.targets.reshape(len(g.targets), -1), device=dev) for g in wl.groups]
+    st_s = [x.clone() for x in img_s]
+    st_t = [x.clone() for x in img_t]
+    groups = [(st_s[k], st_t[k], g.target_seed, g.H, g.W) for k, g in enumerate(wl.groups)]
+    nt_planes = wl.n_target_planes
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def reset():
+        for a, b in zip(st_s, img_s):
+            a.copy_(b)
+        for a, b in zip(st_t, img_t):
+            a.copy_(b)
+
+    def timed(plan, k_steps, warm):
+        for _ in range(warm):
+            reset()
+            plan.run(0, T)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        total = 0.0
+        for _ in range(k_steps):
+            reset()
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.run(0, T)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1) / 1000.0
+        if dist:
+            t = torch.tensor([total], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        return total
+
+    common = dict(T=T, g2=wl.g2, tol_seed=wl.tol_seed, tol=wl.tol, m_seed=wl.m_seed, m=wl.m,
+                  maxit=1000)
+    proj = kp.March(ctx, groups, mode=kp.MARCH_PROJECTED, **common)
+    with Clocks(local) as clk:
+        t_proj = timed(proj, args.steps, args.warmup)
+    value = world * nt_planes * T * args.steps / t_proj
+
+    # per-timestep statistics and per-kernel CUDA-event times of one full march
+    reset()
+    stats, tm = proj.run(0, T, stats=True, timing=True)
+    tgt_iters = sum(s.tgt_iters for s in stats)
+    refine_flops = sum(s.refine_flops for s in stats)
+    not_conv = sum(s.not_converged for s in stats)
+    max_res = max(s.max_rel_res for s in stats)
+    achieved = refine_flops / (tm.refine_ms / 1000.0) / 1e12
+    launches_per_step = tm.launches
+
+    out = {}
+    if not args.no_baselines:
+        for name, mode in (("plain_x0_zero", kp.MARCH_PLAIN), ("plain_warm_start", kp.MARCH_WARM)):
+            pl = kp.March(ctx, groups, mode=mode, **common)
+            t = timed(pl, max(1, args.steps // 2), 1)
+            reset()
+            st2, _ = pl.run(0, T, stats=True)
+            out[name] = {"value": world * nt_planes * T * max(1, args.steps // 2) / t,
+                         "unit": "systems/s",
+                         "iters_per_solve": sum(s.tgt_iters for s in st2) / (nt_planes * T)}
+            pl.close()
+
+    # end to end through the public API: host images in, final states out
+    h_s = [torch.as_tensor(g.seeds.reshape(len(g.seeds), -1)).pin_memory() for g in wl.groups]
+    h_t = [torch.as_tensor(g.targets.reshape(len(g.targets), -1)).pin_memory() for g in wl.groups]
+    o_t = [torch.empty_like(x).pin_memory() for x in h_t]
+    h2d = sum(x.numel() * 8 for x in h_s + h_t)
+    d2h = sum(x.numel() * 8 for x in o_t)
+    e2e_total = 0.0
+    e2e_steps = max(1, args.steps // 2)
+    for k in range(e2e_steps + 1):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for a, b in zip(st_s, h_s):
+            a.copy_(b, non_blocking=True)
+        for a, b in zip(st_t, h_t):
+            a.copy_(b, non_blocking=True)
+        proj.run(0, T)
+        for a, b in zip(o_t, st_t):
+            a.copy_(b, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k > 0:
+            e2e_total += e0.elapsed_time(e1) / 1000.0
+    if dist:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * nt_planes * T * e2e_steps / e2e_total
+
+    cpu = None
+    if rank == 0 and world == 1:
+        cores = cpu_cores()
+        n, w = oracle_sample(wl, args.cpu_sample_steps, cores)
+        cpu = {"value": n / w, "unit": "systems/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {args.cpu_sample_steps} of {T} timesteps, all {nt_planes} "
+                         f"target and {wl.n_seed_planes} seed channels, OpenMP over systems"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "systems/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * t_proj / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded blob images shaped like the paper's 32x32 CIFAR-10 set)",
+            "config": {"workload": wl.name, "T": T, "targets": nt_planes,
+                       "seeds": wl.n_seed_planes, "grid": [g.H for g in wl.groups],
+                       "tol": wl.tol, "m": wl.m, "parallelism": f"replicas x{world}",
+                       "l2": "flushed between timed steps (512 MiB write)"},
+            "e2e": {"value": e2e_value, "unit": "systems/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "traffic": None, "kernel": "gmres_fp64_kernel (refine)",
+                         "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz"},
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+            "iters_per_solve": tgt_iters / (nt_planes * T),
+            "max_rel_res": max_res, "not_converged": not_conv,
+            "kernel_ms_per_march": {"seed": tm.seed_ms, "store": tm.store_ms,
+                                    "project": tm.proj_ms, "refine": tm.refine_ms,
+                                    "timestep_total": tm.step_ms},
+            **out,
+        }
+        if "plain_x0_zero" in out:
+            line["speedup_vs_plain_x0_zero"] = value / out["plain_x0_zero"]["value"]
+            line["speedup_vs_plain_warm_start"] = value / out["plain_warm_start"]["value"]
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -173,6 +173,67 @@ kp_status kp_refine(kp_ctx* ctx, int nsys, const kp_op* ops, const double* const
 kp_status kp_basis_get(kp_ctx* ctx, int seed_id, int timestep, int* a_out, int* has_next_out,
                        double* V, double* Hbar);
 
+/* ------------------------------------------------------------------------
+ * Time march (Sec. 2.3 with Sec. 3 applied at every timestep n = 1..T).
+ *
+ * For each timestep, in one stream and (by default) one CUDA graph per
+ * parity of n:
+ *   seeds:   b = m^{n-1}/dt, GMRES(m_seed) from x0 = 0 to tol_seed with the
+ *            first-cycle basis kept (Phase 1), basis stored per seed;
+ *   targets: b = m^{n-1}/dt, initial guess per `mode` -- PROJECTED: the
+ *            Galerkin projection onto the basis of the target's seed (Phase 2);
+ *            PLAIN: x0 = 0; WARM: x0 = m^{n-1} -- then GMRES(m) to tol;
+ *   m^{n-1} <- m^n.
+ * f = 0 (the paper's setting, Sec. 5), dt = 1/T, h = 1/H per group, and
+ * g2[n-1] = (g^n)^2.  Groups may have different grid sizes; all seeds run in
+ * one launch and all targets in one launch.  Seed slots 0..nseed_total-1 of
+ * the context are used (max_seeds must be at least the total seed count).
+ * ------------------------------------------------------------------------ */
+typedef enum { KP_MARCH_PROJECTED = 0, KP_MARCH_PLAIN = 1, KP_MARCH_WARM = 2 } kp_march_mode;
+
+typedef struct {
+  int H, W;
+  int nseed, ntgt;
+  double* m_seed;        /* device [nseed][H*W]: m^{n0} in, m^{n0+steps} out   */
+  double* m_tgt;         /* device [ntgt][H*W]                                   */
+  const int* tgt_seed;   /* host [ntgt]: seed (index within this group) per target */
+} kp_group;
+
+typedef struct {
+  int T;                 /* timesteps of the full march; dt = 1/T              */
+  const double* g2;      /* host [T]: (g^n)^2                                   */
+  int mode;              /* kp_march_mode                                        */
+  double tol_seed, tol;  /* relative residuals for seeds and targets             */
+  int m_seed, m, maxit;  /* restart lengths, Arnoldi-step cap per solve          */
+  int use_graph;         /* capture each timestep in a CUDA graph (1) or not (0) */
+} kp_march_opts;
+
+/* Per-timestep totals, filled on the host by kp_march_run. */
+typedef struct {
+  double seed_iters, tgt_iters, tgt_iters_max, not_converged, max_rel_res;
+  double refine_flops, seed_flops, proj_flops;   /* FP64 flops of the algorithm */
+} kp_step_stats;
+
+/* Summed device time per kernel class (event-timed mode). */
+typedef struct {
+  float seed_ms, store_ms, proj_ms, refine_ms, step_ms;
+  int launches;          /* kernel launches of this library in the run         */
+} kp_march_timing;
+
+typedef struct kp_march_plan kp_march_plan;
+
+/* Builds the plan: device state, descriptors and (if use_graph) the graphs.
+ * The group arrays are read now; their device buffers are used by every run. */
+kp_status kp_march_create(kp_ctx* ctx, int ngroups, const kp_group* groups,
+                          const kp_march_opts* opt, kp_march_plan** plan);
+/* Runs timesteps n0+1 .. n0+steps (0 <= n0, n0+steps <= T) from the states in
+ * the groups' buffers and leaves the result there.  stats (host, [steps]) and
+ * timing may be NULL; when either is given the call waits for the GPU.  With
+ * timing != NULL each kernel is bracketed by CUDA events (no graph). */
+kp_status kp_march_run(kp_march_plan* plan, int n0, int steps, kp_step_stats* stats,
+                       kp_march_timing* timing);
+kp_status kp_march_destroy(kp_march_plan* plan);
+
 #ifdef __cplusplus
 }
 #endif

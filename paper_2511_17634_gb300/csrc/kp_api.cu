@@ -11,63 +11,16 @@
 #include <vector>
 
 #include "kp.h"
+#include "kp_ctx.h"
 #include "kp_internal.cuh"
 
 using kp::CapMeta;
 using kp::SlotMeta;
 using kp::SysDesc;
 
-namespace {
+namespace kp {
 
-constexpr int kRing = 8;
-
-struct Staging {
-  SysDesc* host = nullptr;   // pinned
-  size_t cap = 0;
-  cudaEvent_t done = nullptr;
-  bool pending = false;
-};
-
-}  // namespace
-
-struct kp_ctx {
-  kp_options opt{};
-  cudaStream_t stream = nullptr;
-  int device = 0;
-  int sms = 0;
-  size_t smem_optin = 0;
-  char err[512] = {0};
-
-  // per-call descriptor upload: pinned host ring -> device buffer
-  Staging ring[kRing];
-  int ring_next = 0;
-  SysDesc* d_desc = nullptr;
-  size_t d_desc_cap = 0;
-
-  // first-cycle capture of the last seed solve
-  double* capV = nullptr;
-  double* capH = nullptr;
-  CapMeta* capMeta = nullptr;
-  int cap_nsys = 0;       // capacity in systems
-  int cap_last = 0;       // systems in the last seed solve
-
-  // seed-basis store
-  double* slotV = nullptr;
-  SlotMeta* slotMeta = nullptr;
-  double* slotR = nullptr;
-  double* slotRot = nullptr;
-  double* slotH = nullptr;
-  std::vector<int> slot_timestep;
-  std::vector<int> slot_n;
-
-  // Krylov-vector workspace for vectors that do not fit in shared memory
-  double* spill = nullptr;
-  size_t spill_bytes = 0;
-};
-
-namespace {
-
-kp_status fail(kp_ctx* c, kp_status s, const char* fmt, ...) {
+kp_status set_error(kp_ctx* c, kp_status s, const char* fmt, ...) {
   if (c) {
     va_list ap;
     va_start(ap, fmt);
@@ -77,10 +30,37 @@ kp_status fail(kp_ctx* c, kp_status s, const char* fmt, ...) {
   return s;
 }
 
-kp_status cuda_fail(kp_ctx* c, cudaError_t e, const char* what) {
-  return fail(c, e == cudaErrorMemoryAllocation ? KP_ERR_OOM : KP_ERR_CUDA, "%s: %s", what,
-              cudaGetErrorString(e));
+kp_status cuda_error(kp_ctx* c, cudaError_t e, const char* what) {
+  return set_error(c, e == cudaErrorMemoryAllocation ? KP_ERR_OOM : KP_ERR_CUDA, "%s: %s", what,
+                   cudaGetErrorString(e));
 }
+
+kp_status gmres_shape(kp_ctx* c, int nmax, int m, Shape* out) {
+  Shape sh;
+  if (nmax <= 1024) { sh.ept = 4; sh.nt = 256; }
+  else if (nmax <= 4096) { sh.ept = 8; sh.nt = 512; }
+  else return set_error(c, KP_ERR_UNSUPPORTED, "N=%d: grids above 4096 unknowns are not supported by this kernel", nmax);
+  const int npad = sh.ept * sh.nt;
+  const size_t fixed = gmres_fp64_smem_bytes(sh.ept, sh.nt, 0, m);
+  const size_t per = (size_t)npad * sizeof(double);
+  int S = c->opt.smem_vectors;
+  if (S <= 0) {
+    // small systems: leave room for two resident blocks per SM
+    const size_t budget = (npad <= 1024) ? c->smem_optin / 2 : c->smem_optin;
+    S = budget > fixed ? (int)((budget - fixed) / per) : 0;
+  }
+  S = std::min(S, m + 1);
+  while (S > 1 && fixed + S * per > c->smem_optin) --S;
+  if (S < 1) return set_error(c, KP_ERR_UNSUPPORTED, "shared memory too small");
+  sh.S = S;
+  sh.smem = fixed + S * per;
+  *out = sh;
+  return KP_OK;
+}
+
+}  // namespace kp
+
+namespace {
 
 template <typename T>
 cudaError_t grow(T** p, size_t* cap_bytes, size_t need_bytes) {
@@ -98,16 +78,16 @@ cudaError_t grow(T** p, size_t* cap_bytes, size_t need_bytes) {
 
 // Validate the operator descriptors of a call; returns the largest N.
 kp_status check_ops(kp_ctx* c, int nsys, const kp_op* ops, int* nmax) {
-  if (nsys < 0) return fail(c, KP_ERR_ARG, "nsys < 0");
-  if (nsys > 0 && !ops) return fail(c, KP_ERR_ARG, "ops is NULL");
+  if (nsys < 0) return kp::set_error(c, KP_ERR_ARG, "nsys < 0");
+  if (nsys > 0 && !ops) return kp::set_error(c, KP_ERR_ARG, "ops is NULL");
   int mx = 0;
   for (int k = 0; k < nsys; ++k) {
     const kp_op& o = ops[k];
-    if (o.H < 1 || o.W < 1) return fail(c, KP_ERR_ARG, "system %d: H, W must be >= 1", k);
+    if (o.H < 1 || o.W < 1) return kp::set_error(c, KP_ERR_ARG, "system %d: H, W must be >= 1", k);
     const long long n = (long long)o.H * o.W;
-    if (n > c->opt.max_n) return fail(c, KP_ERR_ARG, "system %d: N=%lld exceeds max_n=%d", k, n, c->opt.max_n);
+    if (n > c->opt.max_n) return kp::set_error(c, KP_ERR_ARG, "system %d: N=%lld exceeds max_n=%d", k, n, c->opt.max_n);
     if (!(o.dt > 0.0) || !(o.h > 0.0) || !(o.g2 >= 0.0))
-      return fail(c, KP_ERR_ARG, "system %d: need dt > 0, h > 0, g2 >= 0", k);
+      return kp::set_error(c, KP_ERR_ARG, "system %d: need dt > 0, h > 0, g2 >= 0", k);
     mx = std::max(mx, (int)n);
   }
   *nmax = mx;
@@ -118,12 +98,12 @@ kp_status check_ops(kp_ctx* c, int nsys, const kp_op* ops, int* nmax) {
 kp_status upload(kp_ctx* c, const std::vector<SysDesc>& h, SysDesc** out) {
   const size_t n = h.size();
   if (n == 0) { *out = c->d_desc; return KP_OK; }
-  Staging& s = c->ring[c->ring_next];
-  c->ring_next = (c->ring_next + 1) % kRing;
+  kp::Staging& s = c->ring[c->ring_next];
+  c->ring_next = (c->ring_next + 1) % kp::kRing;
   cudaError_t e;
   if (s.pending) {
     e = cudaEventSynchronize(s.done);       // the copy that last read this slot is done
-    if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventSynchronize");
+    if (e != cudaSuccess) return kp::cuda_error(c, e, "cudaEventSynchronize");
     s.pending = false;
   }
   if (s.cap < n) {
@@ -131,16 +111,16 @@ kp_status upload(kp_ctx* c, const std::vector<SysDesc>& h, SysDesc** out) {
     s.host = nullptr;
     s.cap = 0;
     e = cudaMallocHost((void**)&s.host, n * sizeof(SysDesc));
-    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMallocHost");
+    if (e != cudaSuccess) return kp::cuda_error(c, e, "cudaMallocHost");
     s.cap = n;
   }
   std::memcpy(s.host, h.data(), n * sizeof(SysDesc));
   e = grow(&c->d_desc, &c->d_desc_cap, n * sizeof(SysDesc));
-  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(descriptors)");
+  if (e != cudaSuccess) return kp::cuda_error(c, e, "cudaMalloc(descriptors)");
   e = cudaMemcpyAsync(c->d_desc, s.host, n * sizeof(SysDesc), cudaMemcpyHostToDevice, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync(descriptors)");
+  if (e != cudaSuccess) return kp::cuda_error(c, e, "cudaMemcpyAsync(descriptors)");
   e = cudaEventRecord(s.done, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
+  if (e != cudaSuccess) return kp::cuda_error(c, e, "cudaEventRecord");
   s.pending = true;
   *out = c->d_desc;
   return KP_OK;
@@ -163,50 +143,32 @@ SysDesc make_desc(const kp_op& o, const double* b, double* x, int slot) {
   return d;
 }
 
-// Thread-block shape for systems of up to nmax unknowns.
-bool pick_shape(int nmax, int* ept, int* nt) {
-  if (nmax <= 1024) { *ept = 4; *nt = 256; return true; }
-  if (nmax <= 4096) { *ept = 8; *nt = 512; return true; }
-  return false;
-}
-
 kp_status run_gmres(kp_ctx* c, int nsys, const kp_op* ops, const double* const* b,
                     double* const* x, double tol, int m, int maxit, kp_info* info,
                     bool capture) {
   int nmax = 0;
   kp_status st = check_ops(c, nsys, ops, &nmax);
   if (st != KP_OK) return st;
-  if (m < 1 || m > kp::kMaxM) return fail(c, KP_ERR_ARG, "restart length m=%d not in [1, %d]", m, kp::kMaxM);
-  if (maxit < 0) return fail(c, KP_ERR_ARG, "maxit < 0");
-  if (!(tol >= 0.0)) return fail(c, KP_ERR_ARG, "tol must be >= 0");
+  if (m < 1 || m > kp::kMaxM) return kp::set_error(c, KP_ERR_ARG, "restart length m=%d not in [1, %d]", m, kp::kMaxM);
+  if (maxit < 0) return kp::set_error(c, KP_ERR_ARG, "maxit < 0");
+  if (!(tol >= 0.0)) return kp::set_error(c, KP_ERR_ARG, "tol must be >= 0");
   if (nsys == 0) return KP_OK;
-  if (!b || !x) return fail(c, KP_ERR_ARG, "b or x is NULL");
+  if (!b || !x) return kp::set_error(c, KP_ERR_ARG, "b or x is NULL");
   if (c->opt.precision != KP_PREC_FP64)
-    return fail(c, KP_ERR_UNSUPPORTED, "precision mode %d not built in this path", c->opt.precision);
+    return kp::set_error(c, KP_ERR_UNSUPPORTED, "precision mode %d not built in this path", c->opt.precision);
   for (int k = 0; k < nsys; ++k) {
-    if (!ops[k].mtilde || !b[k] || !x[k]) return fail(c, KP_ERR_ARG, "system %d: NULL vector", k);
+    if (!ops[k].mtilde || !b[k] || !x[k]) return kp::set_error(c, KP_ERR_ARG, "system %d: NULL vector", k);
   }
-  int ept, nt;
-  if (!pick_shape(nmax, &ept, &nt))
-    return fail(c, KP_ERR_UNSUPPORTED, "N=%d: grids above 4096 unknowns are not supported by this kernel", nmax);
-  const int npad = ept * nt;
-  // shared-memory Krylov window
-  int S = c->opt.smem_vectors;
-  const size_t fixed = kp::gmres_fp64_smem_bytes(ept, nt, 0, m);
-  const size_t per = (size_t)npad * sizeof(double);
-  if (S <= 0) {
-    const size_t budget = (npad <= 1024) ? c->smem_optin / 2 : c->smem_optin;
-    S = budget > fixed ? (int)((budget - fixed) / per) : 0;
-  }
-  S = std::min(S, m + 1);
-  while (S > 1 && fixed + S * per > c->smem_optin) --S;
-  if (S < 1) return fail(c, KP_ERR_UNSUPPORTED, "shared memory too small");
-  const size_t smem = fixed + S * per;
+  kp::Shape sh;
+  st = kp::gmres_shape(c, nmax, m, &sh);
+  if (st != KP_OK) return st;
+  const int ept = sh.ept, nt = sh.nt, S = sh.S, npad = ept * nt;
+  const size_t smem = sh.smem;
   cudaError_t e;
   if (S < m + 1) {
     const size_t need = (size_t)nsys * (m + 1 - S) * npad * sizeof(double);
     e = grow(&c->spill, &c->spill_bytes, need);
-    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(Krylov workspace)");
+    if (e != cudaSuccess) return kp::cuda_error(c, e, "cudaMalloc(Krylov workspace)");
   }
   if (capture) {
     const int a = c->opt.max_a;
@@ -216,11 +178,11 @@ kp_status run_gmres(kp_ctx* c, int nsys, const kp_op* ops, const double* const* 
       e = cudaMalloc((void**)&c->capV, (size_t)nsys * (a + 1) * c->opt.max_n * sizeof(double));
       if (e == cudaSuccess) e = cudaMalloc((void**)&c->capH, (size_t)nsys * (a + 1) * a * sizeof(double));
       if (e == cudaSuccess) e = cudaMalloc((void**)&c->capMeta, (size_t)nsys * sizeof(CapMeta));
-      if (e != cudaSuccess) return cuda_fail(c, e, "cudaMalloc(capture)");
+      if (e != cudaSuccess) return kp::cuda_error(c, e, "cudaMalloc(capture)");
       c->cap_nsys = nsys;
     }
     e = cudaMemsetAsync(c->capMeta, 0, (size_t)nsys * sizeof(CapMeta), c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "cudaMemsetAsync");
+    if (e != cudaSuccess) return kp::cuda_error(c, e, "cudaMemsetAsync");
     c->cap_last = nsys;
   }
   std::vector<SysDesc> h(nsys);
@@ -247,7 +209,7 @@ kp_status run_gmres(kp_ctx* c, int nsys, const kp_op* ops, const double* const* 
     p.cap_ld = c->opt.max_n;
   }
   e = kp::launch_gmres_fp64(p, ept, nt, smem, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "GMRES launch");
+  if (e != cudaSuccess) return kp::cuda_error(c, e, "GMRES launch");
   return KP_OK;
 }
 
@@ -286,7 +248,7 @@ kp_status kp_create(kp_ctx** out, const kp_options* opt, void* stream) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device);
   c->smem_optin = (size_t)v;
-  for (int i = 0; i < kRing && e == cudaSuccess; ++i)
+  for (int i = 0; i < kp::kRing && e == cudaSuccess; ++i)
     e = cudaEventCreateWithFlags(&c->ring[i].done, cudaEventDisableTiming);
   const size_t a = o.max_a;
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->slotV, (size_t)o.max_seeds * (a + 1) * o.max_n * sizeof(double));
@@ -345,17 +307,17 @@ kp_status kp_apply(kp_ctx* c, int nsys, const kp_op* ops, const double* const* x
   kp_status st = check_ops(c, nsys, ops, &nmax);
   if (st != KP_OK) return st;
   if (nsys == 0) return KP_OK;
-  if (!x || !y) return fail(c, KP_ERR_ARG, "x or y is NULL");
+  if (!x || !y) return kp::set_error(c, KP_ERR_ARG, "x or y is NULL");
   std::vector<SysDesc> h(nsys);
   for (int k = 0; k < nsys; ++k) {
-    if (!ops[k].mtilde || !x[k] || !y[k]) return fail(c, KP_ERR_ARG, "system %d: NULL vector", k);
+    if (!ops[k].mtilde || !x[k] || !y[k]) return kp::set_error(c, KP_ERR_ARG, "system %d: NULL vector", k);
     h[k] = make_desc(ops[k], x[k], y[k], 0);
   }
   SysDesc* dd;
   st = upload(c, h, &dd);
   if (st != KP_OK) return st;
   cudaError_t e = kp::launch_apply(dd, nsys, 0, c->stream);
-  return e == cudaSuccess ? KP_OK : cuda_fail(c, e, "apply launch");
+  return e == cudaSuccess ? KP_OK : kp::cuda_error(c, e, "apply launch");
 }
 
 kp_status kp_rhs(kp_ctx* c, int nsys, const kp_op* ops, const double* const* mprev, double* const* b) {
@@ -364,17 +326,17 @@ kp_status kp_rhs(kp_ctx* c, int nsys, const kp_op* ops, const double* const* mpr
   kp_status st = check_ops(c, nsys, ops, &nmax);
   if (st != KP_OK) return st;
   if (nsys == 0) return KP_OK;
-  if (!mprev || !b) return fail(c, KP_ERR_ARG, "mprev or b is NULL");
+  if (!mprev || !b) return kp::set_error(c, KP_ERR_ARG, "mprev or b is NULL");
   std::vector<SysDesc> h(nsys);
   for (int k = 0; k < nsys; ++k) {
-    if (!mprev[k] || !b[k]) return fail(c, KP_ERR_ARG, "system %d: NULL vector", k);
+    if (!mprev[k] || !b[k]) return kp::set_error(c, KP_ERR_ARG, "system %d: NULL vector", k);
     h[k] = make_desc(ops[k], mprev[k], b[k], 0);
   }
   SysDesc* dd;
   st = upload(c, h, &dd);
   if (st != KP_OK) return st;
   cudaError_t e = kp::launch_apply(dd, nsys, 1, c->stream);
-  return e == cudaSuccess ? KP_OK : cuda_fail(c, e, "rhs launch");
+  return e == cudaSuccess ? KP_OK : kp::cuda_error(c, e, "rhs launch");
 }
 
 kp_status kp_seed_solve(kp_ctx* c, int nsys, const kp_op* ops, const double* const* b,
@@ -392,10 +354,10 @@ kp_status kp_refine(kp_ctx* c, int nsys, const kp_op* ops, const double* const* 
 kp_status kp_store_basis(kp_ctx* c, int seed_id, int timestep, int sys) {
   if (!c) return KP_ERR_ARG;
   if (seed_id < 0 || seed_id >= c->opt.max_seeds)
-    return fail(c, KP_ERR_ARG, "seed_id %d not in [0, %d)", seed_id, c->opt.max_seeds);
-  if (timestep < 0) return fail(c, KP_ERR_ARG, "timestep < 0");
+    return kp::set_error(c, KP_ERR_ARG, "seed_id %d not in [0, %d)", seed_id, c->opt.max_seeds);
+  if (timestep < 0) return kp::set_error(c, KP_ERR_ARG, "timestep < 0");
   if (sys < 0 || sys >= c->cap_last)
-    return fail(c, KP_ERR_NO_BASIS, "system %d not in the last seed solve (%d systems)", sys, c->cap_last);
+    return kp::set_error(c, KP_ERR_NO_BASIS, "system %d not in the last seed solve (%d systems)", sys, c->cap_last);
   kp::FactorParams p{};
   p.capV = c->capV;
   p.capH = c->capH;
@@ -412,8 +374,10 @@ kp_status kp_store_basis(kp_ctx* c, int seed_id, int timestep, int sys) {
   p.timestep = timestep;
   p.max_a = c->opt.max_a;
   p.ld = c->opt.max_n;
+  p.count = 1;
+  p.step = nullptr;
   cudaError_t e = kp::launch_factor(p, c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "store_basis launch");
+  if (e != cudaSuccess) return kp::cuda_error(c, e, "store_basis launch");
   c->slot_timestep[seed_id] = timestep;
   return KP_OK;
 }
@@ -425,21 +389,22 @@ kp_status kp_project_targets_multi(kp_ctx* c, int timestep, int nt, const int* s
   kp_status st = check_ops(c, nt, ops, &nmax);
   if (st != KP_OK) return st;
   if (nt == 0) return KP_OK;
-  if (!seed_ids || !r || !x) return fail(c, KP_ERR_ARG, "seed_ids, r or x is NULL");
+  if (!seed_ids || !r || !x) return kp::set_error(c, KP_ERR_ARG, "seed_ids, r or x is NULL");
   if (c->opt.precision != KP_PREC_FP64)
-    return fail(c, KP_ERR_UNSUPPORTED, "precision mode %d not built in this path", c->opt.precision);
+    return kp::set_error(c, KP_ERR_UNSUPPORTED, "precision mode %d not built in this path", c->opt.precision);
   std::vector<SysDesc> h(nt);
   for (int k = 0; k < nt; ++k) {
     const int s = seed_ids[k];
-    if (s < 0 || s >= c->opt.max_seeds) return fail(c, KP_ERR_ARG, "target %d: seed_id %d out of range", k, s);
+    if (s < 0 || s >= c->opt.max_seeds) return kp::set_error(c, KP_ERR_ARG, "target %d: seed_id %d out of range", k, s);
     if (c->slot_timestep[s] != timestep)
-      return fail(c, KP_ERR_NO_BASIS, "target %d: seed %d holds no basis for timestep %d", k, s, timestep);
-    if (!r[k] || !x[k]) return fail(c, KP_ERR_ARG, "target %d: NULL vector", k);
+      return kp::set_error(c, KP_ERR_NO_BASIS, "target %d: seed %d holds no basis for timestep %d", k, s, timestep);
+    if (!r[k] || !x[k]) return kp::set_error(c, KP_ERR_ARG, "target %d: NULL vector", k);
     h[k] = make_desc(ops[k], r[k], x[k], s);
   }
-  int ept, nt_;
-  if (!pick_shape(nmax, &ept, &nt_))
-    return fail(c, KP_ERR_UNSUPPORTED, "N=%d: grids above 4096 unknowns are not supported", nmax);
+  kp::Shape sh;
+  st = kp::gmres_shape(c, nmax, 1, &sh);
+  if (st != KP_OK) return st;
+  const int ept = sh.ept, nt_ = sh.nt;
   SysDesc* dd;
   st = upload(c, h, &dd);
   if (st != KP_OK) return st;
@@ -454,13 +419,13 @@ kp_status kp_project_targets_multi(kp_ctx* c, int timestep, int nt, const int* s
   p.max_a = c->opt.max_a;
   p.ld = c->opt.max_n;
   cudaError_t e = kp::launch_project_fp64(p, ept, nt_, c->stream);
-  return e == cudaSuccess ? KP_OK : cuda_fail(c, e, "projection launch");
+  return e == cudaSuccess ? KP_OK : kp::cuda_error(c, e, "projection launch");
 }
 
 kp_status kp_project_targets(kp_ctx* c, int seed_id, int timestep, int nt, const kp_op* ops,
                              const double* const* r, double* const* x) {
   if (!c) return KP_ERR_ARG;
-  if (nt < 0) return fail(c, KP_ERR_ARG, "nt < 0");
+  if (nt < 0) return kp::set_error(c, KP_ERR_ARG, "nt < 0");
   std::vector<int> ids(nt, seed_id);
   return kp_project_targets_multi(c, timestep, nt, ids.data(), ops, r, x);
 }
@@ -468,13 +433,13 @@ kp_status kp_project_targets(kp_ctx* c, int seed_id, int timestep, int nt, const
 kp_status kp_basis_get(kp_ctx* c, int seed_id, int timestep, int* a_out, int* has_next_out,
                        double* V, double* Hbar) {
   if (!c) return KP_ERR_ARG;
-  if (seed_id < 0 || seed_id >= c->opt.max_seeds) return fail(c, KP_ERR_ARG, "seed_id out of range");
+  if (seed_id < 0 || seed_id >= c->opt.max_seeds) return kp::set_error(c, KP_ERR_ARG, "seed_id out of range");
   if (c->slot_timestep[seed_id] != timestep)
-    return fail(c, KP_ERR_NO_BASIS, "seed %d holds no basis for timestep %d", seed_id, timestep);
+    return kp::set_error(c, KP_ERR_NO_BASIS, "seed %d holds no basis for timestep %d", seed_id, timestep);
   SlotMeta mt;
   cudaError_t e = cudaMemcpyAsync(&mt, c->slotMeta + seed_id, sizeof(mt), cudaMemcpyDeviceToHost, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-  if (e != cudaSuccess) return cuda_fail(c, e, "basis metadata");
+  if (e != cudaSuccess) return kp::cuda_error(c, e, "basis metadata");
   if (a_out) *a_out = mt.a;
   if (has_next_out) *has_next_out = mt.has_next;
   const int a = c->opt.max_a;
@@ -484,20 +449,20 @@ kp_status kp_basis_get(kp_ctx* c, int seed_id, int timestep, int* a_out, int* ha
                           c->slotV + (size_t)seed_id * (a + 1) * c->opt.max_n,
                           (size_t)c->opt.max_n * sizeof(double), (size_t)mt.N * sizeof(double), nv,
                           cudaMemcpyDeviceToDevice, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "basis copy");
+    if (e != cudaSuccess) return kp::cuda_error(c, e, "basis copy");
   }
   if (Hbar) {
     std::vector<double> tmp((size_t)(a + 1) * a);
     e = cudaMemcpyAsync(tmp.data(), c->slotH + (size_t)seed_id * (a + 1) * a, tmp.size() * sizeof(double),
                         cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "Hessenberg copy");
+    if (e != cudaSuccess) return kp::cuda_error(c, e, "Hessenberg copy");
     for (int j = 0; j < mt.a; ++j)
       for (int i = 0; i <= mt.a; ++i) Hbar[i + (size_t)j * (mt.a + 1)] = tmp[i + (size_t)j * (a + 1)];
   }
   if (V) {
     e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "basis copy");
+    if (e != cudaSuccess) return kp::cuda_error(c, e, "basis copy");
   }
   return KP_OK;
 }

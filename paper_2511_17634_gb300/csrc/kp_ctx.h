@@ -1,0 +1,73 @@
+// kp_ctx.h -- host-side context shared by the C-ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "kp.h"
+#include "kp_internal.cuh"
+
+namespace kp {
+
+constexpr int kRing = 8;
+
+struct Staging {
+  SysDesc* host = nullptr;   // pinned
+  size_t cap = 0;
+  cudaEvent_t done = nullptr;
+  bool pending = false;
+};
+
+}  // namespace kp
+
+struct kp_ctx {
+  kp_options opt{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sms = 0;
+  size_t smem_optin = 0;
+  char err[512] = {0};
+
+  // per-call descriptor upload: pinned host ring -> device buffer
+  kp::Staging ring[kp::kRing];
+  int ring_next = 0;
+  kp::SysDesc* d_desc = nullptr;
+  size_t d_desc_cap = 0;
+
+  // first-cycle capture of the last seed solve
+  double* capV = nullptr;
+  double* capH = nullptr;
+  kp::CapMeta* capMeta = nullptr;
+  int cap_nsys = 0;       // capacity in systems
+  int cap_last = 0;       // systems in the last seed solve
+
+  // seed-basis store
+  double* slotV = nullptr;
+  kp::SlotMeta* slotMeta = nullptr;
+  double* slotR = nullptr;
+  double* slotRot = nullptr;
+  double* slotH = nullptr;
+  std::vector<int> slot_timestep;
+  std::vector<int> slot_n;
+
+  // Krylov-vector workspace for vectors that do not fit in shared memory
+  double* spill = nullptr;
+  size_t spill_bytes = 0;
+};
+
+
+namespace kp {
+
+// Launch shape of the GMRES kernel family for systems of up to nmax unknowns.
+struct Shape {
+  int ept = 0, nt = 0, S = 0;
+  size_t smem = 0;
+};
+
+kp_status set_error(kp_ctx* c, kp_status s, const char* fmt, ...);
+kp_status cuda_error(kp_ctx* c, cudaError_t e, const char* what);
+// Chooses threads, elements per thread and the shared-memory Krylov window.
+kp_status gmres_shape(kp_ctx* c, int nmax, int m, Shape* out);
+
+}  // namespace kp

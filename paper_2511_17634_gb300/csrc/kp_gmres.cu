@@ -80,9 +80,10 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
     const SysDesc d = p.sys[sysi];
     const int H = d.H, W = d.W, N = H * W;
     const double hh = d.h;
-    const double cc = d.g2 / (2.0 * hh * hh);
-    const double ee = d.g2 / (8.0 * hh * hh);
-    const double cd = 1.0 / d.dt + 2.0 * d.g2 / (hh * hh);
+    const double g2 = p.step ? p.g2_sched[*p.step] : d.g2;
+    const double cc = g2 / (2.0 * hh * hh);
+    const double ee = g2 / (8.0 * hh * hh);
+    const double cd = 1.0 / d.dt + 2.0 * g2 / (hh * hh);
     const double i2h = 1.0 / (2.0 * hh);
     const bool capture = p.capV != nullptr;
     double* capV = capture ? p.capV + (size_t)sysi * (p.cap_a + 1) * p.cap_ld : nullptr;

@@ -62,6 +62,9 @@ struct GmresParams {
   CapMeta* capMeta; // [nsys]
   int cap_a;
   int cap_ld;
+  // time march: timestep index and g^2 schedule in device memory (graph replay)
+  const int* step;          // null = not marching
+  const double* g2_sched;   // if step: g2 = g2_sched[*step] for every system
 };
 
 struct ProjParams {
@@ -70,10 +73,11 @@ struct ProjParams {
   int timestep;
   const double* slotV;     // [max_seeds][max_a + 1][ld]
   const SlotMeta* meta;    // [max_seeds]
-  const double* slotR;     // [max_seeds][max_a * max_a] col-major R factor
+  const double* slotR;     // [max_seeds][(max_a + 1) * max_a] col-major R factor, ld max_a + 1
   const double* slotRot;   // [max_seeds][2 * max_a] (c, s) pairs
   int max_a;
   int ld;
+  const int* step;         // if non-null, the timestep is *step
 };
 
 struct FactorParams {
@@ -88,10 +92,12 @@ struct FactorParams {
   double* slotR;
   double* slotRot;
   double* slotH;           // [max_seeds][(max_a + 1) * max_a] unrotated Hbar copy
-  int seed_id;
+  int seed_id;             // block b stores capture sys + b into slot seed_id + b
   int timestep;
   int max_a;
   int ld;
+  int count;               // number of (sys, slot) pairs, one block each
+  const int* step;         // if non-null, the timestep is *step
 };
 
 // ---- block reductions shared by the kernels ----

@@ -20,7 +20,10 @@ __device__ __forceinline__ void givens2(double a, double b, double& c, double& s
 
 // Copies the captured basis of system p.sys into slot p.seed_id and factors
 // its Hessenberg matrix.  One block; thread 0 does the (tiny) factorisation.
-__global__ void factor_kernel(const FactorParams p) {
+__global__ void factor_kernel(FactorParams p) {
+  p.sys += blockIdx.x;
+  p.seed_id += blockIdx.x;
+  if (p.step) p.timestep = *p.step;
   const CapMeta cm = p.capMeta[p.sys];
   const int a = cm.valid ? cm.a : 0;
   const int hn = cm.valid ? cm.has_next : 0;
@@ -88,11 +91,12 @@ __global__ void __launch_bounds__(NT) project_fp64_kernel(const ProjParams p) {
   __shared__ double red[NWARPS * kMaxV];
   __shared__ double cvec[kMaxV];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int timestep = p.step ? *p.step : p.timestep;
   for (int t = blockIdx.x; t < p.nt; t += gridDim.x) {
     const SysDesc d = p.sys[t];
     const int N = d.H * d.W;
     const SlotMeta mt = p.meta[d.slot];
-    if (mt.timestep != p.timestep || mt.N != N || mt.a == 0) continue;   // uniform per block
+    if (mt.timestep != timestep || mt.N != N || mt.a == 0) continue;   // uniform per block
     const int a = mt.a;
     const int nv = mt.lsq ? a + 1 : a;
     const double* V = p.slotV + (size_t)d.slot * (p.max_a + 1) * p.ld;
@@ -151,7 +155,7 @@ __global__ void __launch_bounds__(NT) project_fp64_kernel(const ProjParams p) {
 }  // namespace
 
 cudaError_t launch_factor(const FactorParams& p, cudaStream_t st) {
-  factor_kernel<<<1, 256, 0, st>>>(p);
+  factor_kernel<<<p.count > 0 ? p.count : 1, 256, 0, st>>>(p);
   return cudaGetLastError();
 }
 

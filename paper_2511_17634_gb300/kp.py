@@ -223,3 +223,94 @@ class Context:
                                        self._arr(Hb)))
         Hbar = Hb[: (a.value + 1) * a.value].reshape(a.value, a.value + 1).T.copy()
         return a.value, hn.value, V, Hbar
+
+
+# ---------------------------------------------------------------- time march
+MARCH_PROJECTED, MARCH_PLAIN, MARCH_WARM = 0, 1, 2
+
+
+class _Group(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("nseed", ctypes.c_int),
+                ("ntgt", ctypes.c_int), ("m_seed", ctypes.c_void_p), ("m_tgt", ctypes.c_void_p),
+                ("tgt_seed", ctypes.c_void_p)]
+
+
+class _MarchOpts(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int), ("g2", ctypes.c_void_p), ("mode", ctypes.c_int),
+                ("tol_seed", ctypes.c_double), ("tol", ctypes.c_double), ("m_seed", ctypes.c_int),
+                ("m", ctypes.c_int), ("maxit", ctypes.c_int), ("use_graph", ctypes.c_int)]
+
+
+class StepStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("seed_iters", "tgt_iters", "tgt_iters_max",
+                                                "not_converged", "max_rel_res", "refine_flops",
+                                                "seed_flops", "proj_flops")]
+
+
+class MarchTiming(ctypes.Structure):
+    _fields_ = [("seed_ms", ctypes.c_float), ("store_ms", ctypes.c_float),
+                ("proj_ms", ctypes.c_float), ("refine_ms", ctypes.c_float),
+                ("step_ms", ctypes.c_float), ("launches", ctypes.c_int)]
+
+
+def _march_lib():
+    L = lib()
+    if not hasattr(L, "_march_ready"):
+        vp = ctypes.c_void_p
+        L.kp_march_create.argtypes = [vp, ctypes.c_int, vp, ctypes.POINTER(_MarchOpts),
+                                      ctypes.POINTER(vp)]
+        L.kp_march_run.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, vp]
+        L.kp_march_destroy.argtypes = [vp]
+        for f in ("kp_march_create", "kp_march_run", "kp_march_destroy"):
+            getattr(L, f).restype = ctypes.c_int
+        L._march_ready = True
+    return L
+
+
+class March:
+    """Time march over groups of (seed, target) channel planes of one grid size
+    each.  groups: list of (seeds (ns, N) tensor, targets (nt, N) tensor,
+    target_seed int array, H, W).  The tensors are updated in place by run()."""
+
+    def __init__(self, ctx, groups, T, g2, mode=MARCH_PROJECTED, tol_seed=1e-10, tol=1e-8,
+                 m_seed=40, m=40, maxit=1000, use_graph=True):
+        L = _march_lib()
+        self.ctx = ctx
+        self._keep = []
+        arr = (_Group * len(groups))()
+        for k, (s, t, ts, H, W) in enumerate(groups):
+            ts = np.ascontiguousarray(ts, dtype=np.int32)
+            self._keep += [s, t, ts]
+            arr[k].H, arr[k].W = H, W
+            arr[k].nseed, arr[k].ntgt = s.shape[0], t.shape[0]
+            arr[k].m_seed = s.data_ptr() if s.numel() else None
+            arr[k].m_tgt = t.data_ptr() if t.numel() else None
+            arr[k].tgt_seed = ts.ctypes.data if len(ts) else None
+        g2 = np.ascontiguousarray(g2, dtype=np.float64)
+        self._keep.append(g2)
+        o = _MarchOpts(T, g2.ctypes.data, mode, tol_seed, tol, m_seed, m, maxit, int(use_graph))
+        self.T = T
+        self._h = ctypes.c_void_p()
+        ctx._check(L.kp_march_create(ctx._h, len(groups), ctypes.cast(arr, ctypes.c_void_p),
+                                     ctypes.byref(o), ctypes.byref(self._h)))
+
+    def run(self, n0, steps, stats=False, timing=False):
+        """Timesteps n0+1..n0+steps.  Returns (stats list or None, timing or None)."""
+        L = _march_lib()
+        st = (StepStats * steps)() if stats else None
+        tm = MarchTiming() if timing else None
+        self.ctx._check(L.kp_march_run(self._h, n0, steps,
+                                       ctypes.cast(st, ctypes.c_void_p) if st is not None else None,
+                                       ctypes.byref(tm) if tm is not None else None))
+        return st, tm
+
+    def close(self):
+        if self._h:
+            _march_lib().kp_march_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,95 @@
+"""The native time march (graph-replayed timesteps) against the oracle's
+march, for the three initial-guess modes, one and several grid sizes."""
+import numpy as np
+import pytest
+
+from paper_2511_17634_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_17634_gb300 import build
+    build.build()
+    from paper_2511_17634_gb300 import kp as K
+    return K
+
+
+def _groups(wl):
+    out = []
+    for g in wl.groups:
+        s = torch.as_tensor(g.seeds.reshape(len(g.seeds), -1).copy(), device="cuda")
+        t = torch.as_tensor(g.targets.reshape(len(g.targets), -1).copy(), device="cuda")
+        out.append((s, t, g.target_seed, g.H, g.W))
+    return out
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_march_matches_oracle_tiny(kp, orc, mode, use_graph):
+    wl = synth.config(1)
+    g = wl.groups[0]
+    ctx = kp.Context(max_seeds=4, max_a=wl.a, max_n=g.N)
+    grp = _groups(wl)
+    mr = kp.March(ctx, grp, wl.T, wl.g2, mode=mode, tol_seed=1e-10, tol=1e-12, m_seed=wl.m_seed,
+                  m=wl.m, maxit=1000, use_graph=use_graph)
+    stats, _ = mr.run(0, 20, stats=True)
+    stats2, _ = mr.run(20, wl.T - 20, stats=True)      # resume from the returned state
+    torch.cuda.synchronize()
+    oms, omt, ost = orc.march(g.H, g.W, wl.T, wl.g2, g.seeds, g.targets, g.target_seed,
+                              mode=mode, tol_seed=1e-10, m_seed=wl.m_seed, a=wl.a, tol_ref=1e-12,
+                              m_ref=wl.m)
+    gt = grp[0][1].cpu().numpy()
+    assert np.abs(gt - omt).max() <= 1e-9 * np.abs(omt).max()
+    assert np.abs(grp[0][0].cpu().numpy() - oms).max() <= 1e-8 * np.abs(oms).max()
+    allst = list(stats) + list(stats2)
+    assert len(allst) == wl.T
+    assert all(s.not_converged == 0 for s in allst)
+    assert max(s.max_rel_res for s in allst) <= 1e-12
+    gpu_it = np.array([s.tgt_iters for s in allst])
+    orc_it = np.array([st.tgt_iters.sum() for st in ost])
+    assert np.abs(gpu_it - orc_it).max() <= len(g.targets)       # at most +-1 per solve
+
+
+def test_march_mixed_sizes_one_launch(kp, orc):
+    # two grid sizes in one plan: all seeds in one launch, all targets in one
+    gA = synth.make_group(77, 9, 11, 2, 2, 3, tag=1)
+    gB = synth.make_group(78, 20, 16, 1, 1, 2, tag=2)
+    T = 12
+    g2 = synth.beta_schedule(T)
+    wl = synth.Workload("mixed", T, g2, [gA, gB])
+    ctx = kp.Context(max_seeds=8, max_a=30, max_n=400)
+    grp = _groups(wl)
+    mr = kp.March(ctx, grp, T, g2, mode=0, tol_seed=1e-10, tol=1e-12, m_seed=30, m=30)
+    mr.run(0, T)
+    torch.cuda.synchronize()
+    for k, g in enumerate(wl.groups):
+        oms, omt, _ = orc.march(g.H, g.W, T, g2, g.seeds, g.targets, g.target_seed,
+                                tol_seed=1e-10, m_seed=30, a=30, tol_ref=1e-12, m_ref=30)
+        assert np.abs(grp[k][1].cpu().numpy() - omt).max() <= 1e-9 * np.abs(omt).max()
+
+
+def test_march_workload_32x32_sampled(kp, orc):
+    # the benchmark's grid and launch configuration (32x32x3, 10 templates,
+    # restart 40, tol 1e-8), over the first timesteps, all targets compared
+    wl = synth.config(2, T=1000, ntargets=40)
+    g = wl.groups[0]
+    steps = 3
+    ctx = kp.Context(max_seeds=wl.n_seed_planes, max_a=wl.a, max_n=g.N)
+    grp = _groups(wl)
+    mr = kp.March(ctx, grp, wl.T, wl.g2, mode=0, tol_seed=wl.tol_seed, tol=wl.tol,
+                  m_seed=wl.m_seed, m=wl.m)
+    stats, tm = mr.run(0, steps, stats=True, timing=True)
+    torch.cuda.synchronize()
+    oms, omt, _ = orc.march(g.H, g.W, wl.T, wl.g2, g.seeds, g.targets, g.target_seed, steps=steps,
+                            tol_seed=wl.tol_seed, m_seed=wl.m_seed, a=wl.a, tol_ref=wl.tol,
+                            m_ref=wl.m)
+    # both sides stop at 1e-8 relative residual; cond <= 1.1 here
+    err = np.abs(grp[0][1].cpu().numpy() - omt).max() / np.abs(omt).max()
+    assert err <= 1e-6
+    assert all(s.max_rel_res <= 1e-8 for s in stats)
+    assert tm.refine_ms > 0 and tm.launches == 7 * steps
