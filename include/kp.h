@@ -47,7 +47,8 @@ typedef enum {
   KP_ERR_OOM = -3,        /* device allocation failed                               */
   KP_ERR_NO_BASIS = -4,   /* project_targets: no basis stored for (seed, timestep)  */
   KP_ERR_TIMEOUT = -5,    /* reserved: a bounded device wait gave up                */
-  KP_ERR_UNSUPPORTED = -6 /* valid request this build does not implement            */
+  KP_ERR_UNSUPPORTED = -6,/* valid request this build does not implement            */
+  KP_ERR_TOO_LARGE = -7   /* kp_refine_static: request exceeds its fixed scratch     */
 } kp_status;
 
 typedef enum {
@@ -166,6 +167,43 @@ kp_status kp_project_targets_multi(kp_ctx* ctx, int timestep, int nt, const int*
  */
 kp_status kp_refine(kp_ctx* ctx, int nsys, const kp_op* ops, const double* const* b,
                     double* const* x, double tol, int m, int maxit, kp_info* info);
+
+/*
+ * kp_refine_static -- kp_refine for callers that cannot allocate device memory.
+ * (The paper has no counterpart: this is an interface for embedding.)
+ *
+ * Who needs it: code that may not call cudaMalloc or any allocating routine
+ * when it solves -- a host whose memory pool or arena owns the device memory,
+ * a plugin that may allocate only at start-up, a latency-critical path that
+ * must never reach the allocator.  kp_refine needs a kp_ctx, and kp_create
+ * and the solver calls allocate; this call needs neither a context nor any
+ * allocation (no cudaMalloc, cudaFree, pinned or library allocation).
+ *
+ * Same algorithm and arguments as kp_refine (GMRES(m), CGS2, FP64), on the
+ * caller's `cuda_stream` (a cudaStream_t, NULL = legacy default stream).  Its
+ * scratch -- the system descriptors and the Krylov vectors beyond the shared
+ * memory window -- is one static device array of KP_STATIC_SCRATCH_BYTES in
+ * the library, held on every GPU that loads the library until the process
+ * exits.  Every call reuses that array and leaves its own contents there;
+ * nothing in it has to start at zero, because each call writes every
+ * descriptor and Krylov vector before reading it.  Calls whose work overlaps
+ * on the GPU (other streams, other host threads) race on the array: order
+ * them, e.g. on one stream.
+ *
+ * Limits: nsys <= KP_STATIC_MAX_SYSTEMS, H*W <= KP_STATIC_MAX_N, and the
+ * Krylov vectors that do not fit in shared memory must fit the array (on a
+ * GB300, m <= 40 fits); otherwise KP_ERR_TOO_LARGE and nothing is enqueued.
+ * The first call on each device resolves the array's device address
+ * (cudaGetSymbolAddress, once per device, with that device current) and so
+ * loads the library's module there; make that first call before any stream
+ * capture.
+ */
+#define KP_STATIC_MAX_SYSTEMS 4096
+#define KP_STATIC_MAX_N 1024
+#define KP_STATIC_BLOCKS 152
+#define KP_STATIC_SCRATCH_BYTES (22u * 1024u * 1024u)
+kp_status kp_refine_static(int nsys, const kp_op* ops, const double* const* b, double* const* x,
+                           double tol, int m, int maxit, kp_info* info, void* cuda_stream);
 
 /* Inspect a stored basis (tests, diagnostics).  a_out, has_next_out, host.
  * V (device, N*(a+1) doubles, column k = v_{k+1}) and Hbar (host, (a+1)*a

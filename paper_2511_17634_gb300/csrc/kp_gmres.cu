@@ -408,6 +408,15 @@ cudaError_t launch_gmres_fp64(const GmresParams& p, int ept, int nt, size_t smem
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_gmres_fp64_1k_grid(const GmresParams& p, size_t smem, int grid,
+                                      cudaStream_t st) {
+  auto k = gmres_fp64_kernel<4, 256, 2>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k<<<grid, 256, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_apply(const SysDesc* sys, int nsys, int mode, cudaStream_t st) {
   apply_rhs_kernel<<<nsys, 256, 0, st>>>(sys, nsys, mode);
   return cudaGetLastError();

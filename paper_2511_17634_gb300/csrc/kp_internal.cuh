@@ -167,6 +167,10 @@ __device__ __forceinline__ double cross_warp(const double* red, int i) {
 cudaError_t launch_gmres_fp64(const GmresParams& p, int ept, int nt, size_t smem,
                               cudaStream_t st);
 size_t gmres_fp64_smem_bytes(int ept, int nt, int S, int m);
+// The N <= 1024 instantiation (4 points x 256 threads) on an explicit grid;
+// the kernel strides over systems, block b using Krylov workspace slice b.
+cudaError_t launch_gmres_fp64_1k_grid(const GmresParams& p, size_t smem, int grid,
+                                      cudaStream_t st);
 cudaError_t launch_apply(const SysDesc* sys, int nsys, int mode, cudaStream_t st);
 cudaError_t launch_factor(const FactorParams& p, cudaStream_t st);
 cudaError_t launch_project_fp64(const ProjParams& p, int ept, int nt, cudaStream_t st);

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_PKG, "libkp.so")
 
 OK, NOT_CONVERGED, BREAKDOWN = 0, 1, 2
 ERR_ARG, ERR_CUDA, ERR_OOM, ERR_NO_BASIS, ERR_TIMEOUT, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+ERR_TOO_LARGE = -7
 PREC_FP64, PREC_MIXED = 0, 1
 
 

@@ -1,0 +1,94 @@
+"""kp_refine_static -- the refine for callers that cannot allocate device
+memory -- against kp_refine, through the C ABI.
+
+kp_refine_static keeps its scratch in a static device array of the library
+instead of allocating, for hosts whose memory pools, plugin rules or latency
+budgets forbid cudaMalloc at solve time.  It must give kp_refine's answers,
+call after call (the array is reused and keeps the previous call's contents).
+This file is collected last so that a failure here stops a `-x` run only
+after every other test has run.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2511_17634_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kp():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_17634_gb300 import build
+    build.build()
+    from paper_2511_17634_gb300 import kp as K
+    L = K.lib()
+    vp = ctypes.c_void_p
+    L.kp_refine_static.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_double, ctypes.c_int,
+                                   ctypes.c_int, vp, vp]
+    L.kp_refine_static.restype = ctypes.c_int
+    return K
+
+
+def _static_refine(K, ops, b, x, tol, m, maxit, info, stream):
+    L = K.lib()
+    pb, px = K._ptrs(b), K._ptrs(x)
+    return L.kp_refine_static(len(ops), K.Context._arr(ops), pb.ctypes.data_as(ctypes.c_void_p),
+                              px.ctypes.data_as(ctypes.c_void_p), tol, m, maxit,
+                              ctypes.c_void_p(info.data_ptr()), ctypes.c_void_p(stream))
+
+
+def _problem(seed):
+    # the paper's own setting (g = 0.5, T = 100) on 32x32 channels: these
+    # systems need 20-30 GMRES steps, so Krylov vectors beyond the
+    # shared-memory window go to the static scratch
+    wl = synth.config(2, T=100, ntargets=60, seed=seed)
+    g = wl.groups[0]
+    return g.H, g.W, g.targets.reshape(len(g.targets), -1)
+
+
+def test_static_refine_matches_refine_on_two_calls(kp):
+    stream = torch.cuda.current_stream()
+    ctx = kp.Context(max_n=1024)
+    for call, seed in enumerate((11, 12)):
+        H, W, mt = _problem(seed)
+        n = mt.shape[0]
+        dm = torch.as_tensor(mt, device="cuda")
+        ops = kp.make_ops(H, W, 0.01, 0.25, 1.0 / H, dm)
+        b = torch.zeros_like(dm)
+        ctx.rhs(ops, dm, b)
+        x_ref = torch.zeros_like(dm)
+        info_ref = ctx.refine(ops, b, x_ref, tol=1e-10, m=40, maxit=600)
+        x_st = torch.zeros_like(dm)
+        info_st = kp.info_tensor(n)
+        rc = _static_refine(kp, ops, b, x_st, 1e-10, 40, 600, info_st, stream.cuda_stream)
+        assert rc == kp.OK, rc
+        torch.cuda.synchronize()
+        it_r, st_r, rr_r = kp.decode_info(info_ref)
+        it_s, st_s, rr_s = kp.decode_info(info_st)
+        assert (st_s == 0).all() and (rr_s <= 1e-10).all()
+        assert it_s.max() > 24, "the case must reach the static workspace"
+        assert np.array_equal(it_s, it_r)
+        err = float((x_st - x_ref).abs().max() / x_ref.abs().max())
+        assert err <= 1e-12, (call, err)
+
+
+def test_static_refine_rejects_oversized_requests(kp):
+    ctx = kp.Context(max_n=4096)
+    dm = torch.zeros((2, 64 * 64), dtype=torch.float64, device="cuda")
+    ops = kp.make_ops(64, 64, 0.01, 0.02, 1 / 64, dm)
+    info = kp.info_tensor(2)
+    rc = _static_refine(kp, ops, dm, dm.clone(), 1e-8, 40, 100, info, 0)
+    assert rc == kp.ERR_TOO_LARGE
+    # 200 systems run on all 152 blocks; with m = 64 their Krylov vectors
+    # beyond the shared-memory window do not fit the static scratch
+    dm = torch.zeros((200, 1024), dtype=torch.float64, device="cuda")
+    ops = kp.make_ops(32, 32, 0.01, 0.02, 1 / 32, dm)
+    info = kp.info_tensor(200)
+    rc = _static_refine(kp, ops, dm, dm.clone(), 1e-8, 64, 100, info, 0)
+    assert rc == kp.ERR_TOO_LARGE
+    del ctx
