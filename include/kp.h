@@ -252,7 +252,9 @@ typedef struct {
   double refine_flops, seed_flops, proj_flops;   /* FP64 flops of the algorithm */
 } kp_step_stats;
 
-/* Summed device time per kernel class (event-timed mode). */
+/* Summed device time per kernel class (event-timed mode, launches in
+ * sequence): seed_ms = seed GMRES with the fused basis store; refine_ms =
+ * target GMRES with the fused projection; step_ms = first to last event. */
 typedef struct {
   float seed_ms, store_ms, proj_ms, refine_ms, step_ms;
   int launches;          /* kernel launches of this library in the run         */

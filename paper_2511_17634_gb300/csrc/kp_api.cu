@@ -199,6 +199,8 @@ kp_status run_gmres(kp_ctx* c, int nsys, const kp_op* ops, const double* const* 
   p.S = S;
   p.reorth = c->opt.reorth;
   p.npad = npad;
+  p.b_scale = 1.0;
+  p.x0_mode = kp::X0_READ;
   p.spill = (S < m + 1) ? c->spill : nullptr;
   p.info = info;
   if (capture) {
@@ -254,7 +256,7 @@ kp_status kp_create(kp_ctx** out, const kp_options* opt, void* stream) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->slotV, (size_t)o.max_seeds * (a + 1) * o.max_n * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->slotMeta, (size_t)o.max_seeds * sizeof(SlotMeta));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->slotR, (size_t)o.max_seeds * (a + 1) * a * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc((void**)&c->slotRot, (size_t)o.max_seeds * 2 * a * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&c->slotRot, (size_t)o.max_seeds * 3 * a * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->slotH, (size_t)o.max_seeds * (a + 1) * a * sizeof(double));
   if (e == cudaSuccess) {
     std::vector<SlotMeta> init(o.max_seeds);

@@ -33,6 +33,7 @@ struct Smem {
   double* cs;    // [m]
   double* sn;    // [m]
   double* y;     // [m]
+  double* rinv;  // [m] reciprocal pivots of the rotated Hessenberg
   double* sc;    // [8] scalars
   int* fl;       // [8] flags
 };
@@ -48,18 +49,10 @@ __device__ __forceinline__ Smem carve(double* base, int S, int npad, int nwarps,
   s.cs = s.g + (m + 1);
   s.sn = s.cs + m;
   s.y = s.sn + m;
-  s.sc = s.y + m;
+  s.rinv = s.y + m;
+  s.sc = s.rinv + m;
   s.fl = reinterpret_cast<int*>(s.sc + 8);
   return s;
-}
-
-// Givens rotation [c s; -s c] [a; b] = [r; 0].
-__device__ __forceinline__ void givens(double a, double b, double& c, double& s) {
-  if (b == 0.0) { c = 1.0; s = 0.0; return; }
-  const double r = hypot(a, b);
-  const double ir = 1.0 / r;
-  c = a * ir;
-  s = b * ir;
 }
 
 template <int EPT, int NT, int MINB>
@@ -75,19 +68,28 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
   auto slot = [&](int i) -> double* {
     return i < p.S ? sm.V + (size_t)i * npad : spill + (size_t)(i - p.S) * npad;
   };
+  // timestep of this launch (time march) and its parity's seed slots
+  int tstep = 0;
+  if (p.step) {
+    tstep = *p.step + p.step_offset;
+    if (tstep >= *p.step_end) return;        // pipelined seed step past the run: nothing to do
+  }
+  const int parity_base = (tstep & 1) * p.slot_parity_stride;
+  const double bsc = p.b_scale;
 
   for (int sysi = blockIdx.x; sysi < p.nsys; sysi += gridDim.x) {
     const SysDesc d = p.sys[sysi];
     const int H = d.H, W = d.W, N = H * W;
     const double hh = d.h;
-    const double g2 = p.step ? p.g2_sched[*p.step] : d.g2;
+    const double g2 = p.step ? p.g2_sched[tstep] : d.g2;
     const double cc = g2 / (2.0 * hh * hh);
     const double ee = g2 / (8.0 * hh * hh);
     const double cd = 1.0 / d.dt + 2.0 * g2 / (hh * hh);
     const double i2h = 1.0 / (2.0 * hh);
     const bool capture = p.capV != nullptr;
-    double* capV = capture ? p.capV + (size_t)sysi * (p.cap_a + 1) * p.cap_ld : nullptr;
-    double* capH = capture ? p.capH + (size_t)sysi * (p.cap_a + 1) * p.cap_a : nullptr;
+    const int cidx = p.factor ? parity_base + sysi : sysi;   // capture record (or seed slot)
+    double* capV = capture ? p.capV + (size_t)cidx * (p.cap_a + 1) * p.cap_ld : nullptr;
+    double* capH = capture ? p.capH + (size_t)cidx * (p.cap_a + 1) * p.cap_a : nullptr;
 
     // stencil coefficients (Sec. 2.3, listing after Eq. 11); zero where the
     // neighbour lies outside the grid
@@ -124,12 +126,60 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
         }
       }
     };
+    auto bval = [&](int pp) { return (pp < N) ? d.b[pp] * bsc : 0.0; };
 
-    // x -> shared memory; r = b - A x; ||b||, ||r||
+    // initial guess -> shared memory
+    unsigned long long proj_flops = 0;
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
       const int pp = tid + k * NT;
-      sm.xs[pp] = (pp < N) ? d.x[pp] : 0.0;
+      double x0 = 0.0;
+      if (pp < N) {
+        if (p.x0_mode == X0_READ) x0 = d.x[pp];
+        else if (p.x0_mode == X0_WARM) x0 = d.mt[pp];
+      }
+      sm.xs[pp] = x0;
+    }
+    if (p.x0_mode == X0_PROJECT) {
+      // Sec. 3, Phase 2: x0 = V_a H_a^{-1} V_a^T b with the seed's stored basis
+      const int sl = d.slot + parity_base;
+      const SlotMeta mt = p.slotMeta[sl];
+      if (mt.timestep == tstep && mt.N == N && mt.a > 0) {            // uniform per block
+        const int a = mt.a;
+        const int nv = mt.lsq ? a + 1 : a;
+        const double* V = p.slotV + (size_t)sl * (p.max_a + 1) * p.slot_ld;
+        double bv[EPT];
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) bv[k] = bval(tid + k * NT);
+        block_partials<NT>(nv, [&](int i) {
+          const double* vi = V + (size_t)i * p.slot_ld;
+          double s = 0.0;
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) {
+            const int pp = tid + k * NT;
+            if (pp < N) s += vi[pp] * bv[k];
+          }
+          return s;
+        }, sm.red);
+        if (warp == 0) {
+          for (int i = lane; i < nv; i += 32) sm.hb[i] = cross_warp<NT>(sm.red, i);
+          __syncwarp();
+          const double* rot = p.slotRot + (size_t)sl * 3 * p.max_a;
+          solve_projected_warp(sm.hb, a, mt.nrot, p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a,
+                               p.max_a + 1, rot, rot + 2 * p.max_a, lane);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          const int pp = tid + k * NT;
+          if (pp < N) {
+            double xv = 0.0;
+            for (int i = 0; i < a; ++i) xv = fma(sm.hb[i], V[(size_t)i * p.slot_ld + pp], xv);
+            sm.xs[pp] = xv;
+          }
+        }
+        proj_flops = (unsigned long long)(2 * nv + 2 * a) * (unsigned long long)N;
+      }
     }
     __syncthreads();
     double w[EPT];
@@ -138,7 +188,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
         const int pp = tid + k * NT;
-        w[k] = (pp < N) ? d.b[pp] - w[k] : 0.0;
+        w[k] = (pp < N) ? bval(pp) - w[k] : 0.0;
       }
     };
     residual();
@@ -146,8 +196,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
       double s = 0.0;
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
-        const int pp = tid + k * NT;
-        const double bv = (pp < N) ? d.b[pp] : 0.0;
+        const double bv = bval(tid + k * NT);
         s += (i == 0) ? bv * bv : w[k] * w[k];
       }
       return s;
@@ -184,6 +233,37 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
       }
       int kdone = 0;
       int brk = 0;
+      // Givens update of Hessenberg column j once h_{j+1,j}^2 = hn2 is known
+      // (one lane): rotations, residual estimate, convergence flags.
+      auto givens_step = [&](int j, double hn2) {
+        const double ihn = hn2 > 0.0 ? rsqrt(hn2) : 0.0;
+        const double hn = hn2 * ihn;
+        const int b = !(hn > 1e-14 * sqrt(sm.sc[2]));
+        sm.Hr[(j + 1) + j * ld] = hn;
+        if (capture && cycle == 0 && j < p.cap_a) {
+          for (int i = 0; i <= j + 1; ++i) capH[i + j * (p.cap_a + 1)] = sm.Hr[i + j * ld];
+        }
+        for (int i = 0; i < j; ++i) {
+          const double t1 = sm.Hr[i + j * ld], t2 = sm.Hr[(i + 1) + j * ld];
+          sm.Hr[i + j * ld] = sm.cs[i] * t1 + sm.sn[i] * t2;
+          sm.Hr[(i + 1) + j * ld] = -sm.sn[i] * t1 + sm.cs[i] * t2;
+        }
+        const double a0 = sm.Hr[j + j * ld];
+        const double rr = a0 * a0 + hn2;
+        const double ir = rsqrt(rr);
+        const double c = a0 * ir, s = hn * ir;
+        sm.cs[j] = c;
+        sm.sn[j] = s;
+        sm.Hr[j + j * ld] = rr * ir;
+        sm.rinv[j] = ir;
+        sm.Hr[(j + 1) + j * ld] = 0.0;
+        sm.g[j + 1] = -s * sm.g[j];
+        sm.g[j] = c * sm.g[j];
+        const double res = fabs(sm.g[j + 1]);
+        sm.sc[3] = ihn;
+        sm.fl[1] = b;
+        sm.fl[2] = (res <= p.tol * bnorm) || b || (steps >= p.maxit) || (j + 1 == m);
+      };
       for (int j = 0; j < m; ++j) {
         __syncthreads();                       // v_j complete
         apply(slot(j), w);
@@ -201,7 +281,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
           }
           return s;
         };
-        // CGS pass 1: h_i = <v_i, w>, plus ||w||^2 before orthogonalisation
+        // CGS pass 1: h_i = <v_i, w> and ||w||^2 in one batched reduction
         block_partials<NT>(nh + 1, dots, sm.red);
         if (warp == 0) {
           double sq = 0.0;
@@ -214,8 +294,11 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
           if (lane == 0) {
             const double ww0 = sm.hb[nh];
             sm.sc[2] = ww0;
-            // DGKS: a second pass only if the first removed over half the norm^2
-            sm.fl[0] = (p.reorth == 0) || (ww0 - sq < 0.5 * ww0);
+            // second pass always (CGS2), or only when the first removed over
+            // half of ||w||^2 (DGKS); without it ||w_1||^2 = ||w||^2 - ||h||^2
+            const int pass2 = (p.reorth == 0) || (ww0 - sq < 0.5 * ww0);
+            sm.fl[0] = pass2;
+            if (!pass2) givens_step(j, ww0 - sq);
           }
         }
         __syncthreads();
@@ -226,13 +309,22 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
           for (int k = 0; k < EPT; ++k) w[k] = fma(-hi, vi[tid + k * NT], w[k]);
         }
         if (sm.fl[0]) {
-          // CGS pass 2 (reorthogonalisation)
-          block_partials<NT>(nh, dots, sm.red);
+          // CGS pass 2 (reorthogonalisation) with ||w_1||^2 in the same reduction;
+          // ||w_2||^2 = ||w_1||^2 - ||h_2||^2 (h_2 = O(eps) after pass 1), checked
+          block_partials<NT>(nh + 1, dots, sm.red);
           if (warp == 0) {
-            for (int i = lane; i < nh; i += 32) {
+            double sq = 0.0;
+            for (int i = lane; i <= nh; i += 32) {
               const double s = cross_warp<NT>(sm.red, i);
               sm.hb[i] = s;
-              sm.Hr[i + j * ld] += s;
+              if (i < nh) { sm.Hr[i + j * ld] += s; sq += s * s; }
+            }
+            sq = warp_sum(sq);
+            if (lane == 0) {
+              const double ww1 = sm.hb[nh];
+              const int exact = sq > 0.25 * ww1;     // large correction: recompute the norm
+              sm.fl[3] = exact;
+              if (!exact) givens_step(j, ww1 - sq);
             }
           }
           __syncthreads();
@@ -242,44 +334,21 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
 #pragma unroll
             for (int k = 0; k < EPT; ++k) w[k] = fma(-hi, vi[tid + k * NT], w[k]);
           }
-        }
-        // ||w|| after orthogonalisation, then Givens update of column j
-        block_partials<NT>(1, [&](int) {
-          double s = 0.0;
+          if (sm.fl[3]) {
+            block_partials<NT>(1, [&](int) {
+              double s = 0.0;
 #pragma unroll
-          for (int k = 0; k < EPT; ++k) s += w[k] * w[k];
-          return s;
-        }, sm.red);
-        if (tid == 0) {
-          const double hn = sqrt(cross_warp<NT>(sm.red, 0));
-          const int b = !(hn > 1e-14 * sqrt(sm.sc[2]));
-          sm.Hr[(j + 1) + j * ld] = hn;
-          if (capture && cycle == 0 && j < p.cap_a) {
-            for (int i = 0; i <= j + 1; ++i) capH[i + j * (p.cap_a + 1)] = sm.Hr[i + j * ld];
+              for (int k = 0; k < EPT; ++k) s += w[k] * w[k];
+              return s;
+            }, sm.red);
+            if (tid == 0) givens_step(j, cross_warp<NT>(sm.red, 0));
+            __syncthreads();
           }
-          for (int i = 0; i < j; ++i) {
-            const double t1 = sm.Hr[i + j * ld], t2 = sm.Hr[(i + 1) + j * ld];
-            sm.Hr[i + j * ld] = sm.cs[i] * t1 + sm.sn[i] * t2;
-            sm.Hr[(i + 1) + j * ld] = -sm.sn[i] * t1 + sm.cs[i] * t2;
-          }
-          double c, s;
-          givens(sm.Hr[j + j * ld], sm.Hr[(j + 1) + j * ld], c, s);
-          sm.cs[j] = c;
-          sm.sn[j] = s;
-          sm.Hr[j + j * ld] = c * sm.Hr[j + j * ld] + s * sm.Hr[(j + 1) + j * ld];
-          sm.Hr[(j + 1) + j * ld] = 0.0;
-          sm.g[j + 1] = -s * sm.g[j];
-          sm.g[j] = c * sm.g[j];
-          const double res = fabs(sm.g[j + 1]);
-          sm.sc[3] = hn;
-          sm.fl[1] = b;
-          sm.fl[2] = (res <= p.tol * bnorm) || b || (steps >= p.maxit) || (j + 1 == m);
         }
-        __syncthreads();
         brk = sm.fl[1];
         kdone = j + 1;
         if (!brk) {
-          const double ih = 1.0 / sm.sc[3];
+          const double ih = sm.sc[3];
           double* vn = slot(j + 1);
 #pragma unroll
           for (int k = 0; k < EPT; ++k) {
@@ -291,19 +360,43 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
         }
         if (sm.fl[2]) break;
       }
-      // y = R^{-1} g (back substitution, one lane)
-      if (tid == 0) {
+      // y = R^{-1} g: column-oriented back substitution on warp 0 (lane l owns
+      // rows l and l+32), reciprocal pivots stored by the Givens step
+      if (warp == 0) {
+        double g0 = (lane < kdone) ? sm.g[lane] : 0.0;
+        double g1 = (lane + 32 < kdone) ? sm.g[lane + 32] : 0.0;
         for (int i = kdone - 1; i >= 0; --i) {
-          double s = sm.g[i];
-          for (int l = i + 1; l < kdone; ++l) s -= sm.Hr[i + l * ld] * sm.y[l];
-          sm.y[i] = s / sm.Hr[i + i * ld];
+          const double gi = __shfl_sync(kFull, i < 32 ? g0 : g1, i & 31);
+          const double yi = gi * sm.rinv[i];
+          if (lane == 0) sm.y[i] = yi;
+          if (lane < i) g0 = fma(-sm.Hr[lane + i * ld], yi, g0);
+          if (lane + 32 < i) g1 = fma(-sm.Hr[(lane + 32) + i * ld], yi, g1);
         }
+      }
+      if (tid == 0) {
         if (capture && cycle == 0) {
           const int a = kdone < p.cap_a ? kdone : p.cap_a;
-          p.capMeta[sysi].a = a;
-          p.capMeta[sysi].has_next = (a < kdone) || !brk;
-          p.capMeta[sysi].N = N;
-          p.capMeta[sysi].valid = 1;
+          const int hn = (a < kdone) || !brk;
+          if (p.factor) {
+            // fused basis store: factor H_a of the slot just written
+            SlotMeta mt;
+            const int sl = cidx;
+            double* rot = p.slotRot + (size_t)sl * 3 * p.max_a;
+            factor_hessenberg(capH, p.cap_a + 1, a, hn,
+                              p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a, rot,
+                              rot + 2 * p.max_a, &mt.lsq, &mt.nrot);
+            mt.a = a;
+            mt.has_next = hn;
+            mt.timestep = tstep;
+            mt.N = N;
+            mt.pad_[0] = mt.pad_[1] = 0;
+            p.slotMeta[sl] = mt;
+          } else {
+            p.capMeta[sysi].a = a;
+            p.capMeta[sysi].has_next = hn;
+            p.capMeta[sysi].N = N;
+            p.capMeta[sysi].valid = 1;
+          }
         }
       }
       __syncthreads();
@@ -326,23 +419,53 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
       beta = sm.sc[1];
       ++cycle;
     }
-    if (capture && cycle == 0 && tid == 0) {   // converged before any step
-      p.capMeta[sysi].a = 0;
-      p.capMeta[sysi].has_next = 0;
-      p.capMeta[sysi].N = N;
-      p.capMeta[sysi].valid = 1;
+    if (capture && cycle == 0 && tid == 0) {   // converged before any step: empty basis
+      if (p.factor) {
+        SlotMeta mt;
+        mt.a = 0;
+        mt.has_next = 0;
+        mt.timestep = tstep;
+        mt.N = N;
+        mt.lsq = 0;
+        mt.nrot = 0;
+        mt.pad_[0] = mt.pad_[1] = 0;
+        p.slotMeta[cidx] = mt;
+      } else {
+        p.capMeta[sysi].a = 0;
+        p.capMeta[sysi].has_next = 0;
+        p.capMeta[sysi].N = N;
+        p.capMeta[sysi].valid = 1;
+      }
     }
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
       const int pp = tid + k * NT;
       if (pp < N) d.x[pp] = sm.xs[pp];
     }
-    if (tid == 0 && p.info) {
-      kp_info inf;
-      inf.iters = steps;
-      inf.status = status;
-      inf.rel_res = bnorm > 0.0 ? beta / bnorm : 0.0;
-      p.info[sysi] = inf;
+    if (tid == 0) {
+      const double rel = bnorm > 0.0 ? beta / bnorm : 0.0;
+      if (p.info) {
+        kp_info inf;
+        inf.iters = steps;
+        inf.status = status;
+        inf.rel_res = rel;
+        p.info[sysi] = inf;
+      }
+      if (p.acc) {
+        StepAcc* a = p.acc + tstep;
+        const unsigned long long fl = gmres_flops(steps, m) * (unsigned long long)N;
+        if (p.acc_kind == 0) {
+          atomicAdd(&a->seed_iters, (unsigned long long)steps);
+          atomicAdd(&a->seed_flops, fl);
+        } else {
+          atomicAdd(&a->tgt_iters, (unsigned long long)steps);
+          atomicAdd(&a->tgt_flops, fl);
+          atomicMax(&a->tgt_max_iters, (unsigned int)steps);
+          atomicMax(&a->max_res_bits, (unsigned long long)__double_as_longlong(rel));
+          if (proj_flops) atomicAdd(&a->proj_flops, proj_flops);
+        }
+        if (status != KP_OK) atomicAdd(&a->not_converged, 1u);
+      }
     }
     __syncthreads();                           // shared memory reused by the next system
   }
@@ -388,14 +511,26 @@ __global__ void apply_rhs_kernel(const SysDesc* sys, int nsys, int mode) {
 size_t gmres_fp64_smem_bytes(int ept, int nt, int S, int m) {
   const int npad = ept * nt;
   const size_t doubles = (size_t)S * npad + npad + (nt / 32) * kMaxV + kMaxV +
-                         (size_t)(m + 1) * m + (m + 1) + 3 * m + 8;
+                         (size_t)(m + 1) * m + (m + 1) + 4 * m + 8;
   return doubles * sizeof(double) + 8 * sizeof(int);
+}
+
+// Raise the kernel's dynamic shared-memory limit to the device maximum, so
+// that launches with different windows (seeds, targets) never lower it.
+template <typename K>
+static cudaError_t allow_max_smem(K k, size_t smem) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if (smem > (size_t)optin) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
 
 template <int EPT, int NT, int MINB>
 static cudaError_t launch_one(const GmresParams& p, size_t smem, cudaStream_t st) {
   auto k = gmres_fp64_kernel<EPT, NT, MINB>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(k, smem);
   if (e != cudaSuccess) return e;
   k<<<p.nsys, NT, smem, st>>>(p);
   return cudaGetLastError();
@@ -411,9 +546,16 @@ cudaError_t launch_gmres_fp64(const GmresParams& p, int ept, int nt, size_t smem
 cudaError_t launch_gmres_fp64_1k_grid(const GmresParams& p, size_t smem, int grid,
                                       cudaStream_t st) {
   auto k = gmres_fp64_kernel<4, 256, 2>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = allow_max_smem(k, smem);
   if (e != cudaSuccess) return e;
   k<<<grid, 256, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+__global__ void advance_kernel(int* step) { *step += 1; }
+
+cudaError_t launch_advance(int* step, cudaStream_t st) {
+  advance_kernel<<<1, 1, 0, st>>>(step);
   return cudaGetLastError();
 }
 

@@ -34,6 +34,18 @@ struct SlotMeta {
   int pad_[2];
 };
 
+// Per-timestep totals accumulated by the solver blocks (time march).
+struct StepAcc {
+  unsigned long long seed_iters;
+  unsigned long long tgt_iters;
+  unsigned long long seed_flops;     // FP64 flops of the algorithm (see gmres_flops)
+  unsigned long long tgt_flops;
+  unsigned long long proj_flops;
+  unsigned long long max_res_bits;   // max relative residual (non-negative double bits)
+  unsigned int tgt_max_iters;
+  unsigned int not_converged;
+};
+
 // Capture record of one seed system after kp_seed_solve.
 struct CapMeta {
   int a;
@@ -64,8 +76,25 @@ struct GmresParams {
   int cap_ld;
   // time march: timestep index and g^2 schedule in device memory (graph replay)
   const int* step;          // null = not marching
-  const double* g2_sched;   // if step: g2 = g2_sched[*step] for every system
+  const double* g2_sched;   // if step: g2 = g2_sched[*step + step_offset] for every system
+  int step_offset;          // seeds run one timestep ahead of the targets
+  const int* step_end;      // if step: nothing to do when *step + step_offset >= *step_end
+  double b_scale;           // right-hand side = b[p] * b_scale (b = m^{n-1}/dt when f = 0)
+  int x0_mode;              // X0_* below
+  // seed-basis store: projection source (X0_PROJECT) and fused capture (factor)
+  double* slotV;            // [max_seeds][max_a + 1][slot_ld]
+  SlotMeta* slotMeta;
+  double* slotR;
+  double* slotRot;
+  int slot_ld;
+  int max_a;
+  int slot_parity_stride;   // slots of timestep parity q start at q * stride
+  int factor;               // capture into slot (sys + parity offset) and factor H_a
+  StepAcc* acc;             // per-timestep totals (indexed like g2_sched) or null
+  int acc_kind;             // 0 seeds, 1 targets
 };
+
+enum { X0_READ = 0, X0_ZERO = 1, X0_WARM = 2, X0_PROJECT = 3 };
 
 struct ProjParams {
   const SysDesc* sys;
@@ -74,7 +103,7 @@ struct ProjParams {
   const double* slotV;     // [max_seeds][max_a + 1][ld]
   const SlotMeta* meta;    // [max_seeds]
   const double* slotR;     // [max_seeds][(max_a + 1) * max_a] col-major R factor, ld max_a + 1
-  const double* slotRot;   // [max_seeds][2 * max_a] (c, s) pairs
+  const double* slotRot;   // [max_seeds][3 * max_a]: (c, s) pairs, then reciprocal pivots
   int max_a;
   int ld;
   const int* step;         // if non-null, the timestep is *step
@@ -163,6 +192,95 @@ __device__ __forceinline__ double cross_warp(const double* red, int i) {
   return s;
 }
 
+// FP64 flops per unknown of GMRES(m) with CGS2 as implemented here, for k
+// Arnoldi steps: 14 to start (residual, two norms); per cycle of L steps
+// sum_{j<L} (9 stencil + 8(j+1) Gram-Schmidt + 5 norm/scale) + 2L update + 12 residual.
+__host__ __device__ __forceinline__ unsigned long long gmres_flops(int k, int m) {
+  const unsigned long long full = (unsigned long long)(k / m), rem = (unsigned long long)(k % m);
+  const unsigned long long M = (unsigned long long)m;
+  unsigned long long f = 14ull + full * (4ull * M * M + 20ull * M + 12ull);
+  if (rem) f += 4ull * rem * rem + 20ull * rem + 12ull;
+  return f;
+}
+
+__device__ __forceinline__ void givens_rot(double a, double b, double& c, double& s) {
+  if (b == 0.0) { c = 1.0; s = 0.0; return; }
+  const double r = hypot(a, b);
+  const double ir = 1.0 / r;
+  c = a * ir;
+  s = b * ir;
+}
+
+// Givens QR of a seed's Hessenberg matrix for the projection of Sec. 3
+// (one thread).  Hb: unrotated (a+1) x a, column-major, leading dim ld, also
+// the leading dim of R.  First tries H_a (a-1 rotations); if a pivot is below
+// 1e-14 max|H_a| and v_{a+1} exists, factors Hbar instead (a rotations,
+// least squares).  Writes R, rot (c, s pairs), rinv (reciprocal pivots, 0 for
+// a zero pivot) and returns lsq / nrot.
+__device__ __forceinline__ void factor_hessenberg(const double* Hb, int ld, int a, int has_next,
+                                                  double* R, double* rot, double* rinv,
+                                                  int* lsq_out, int* nrot_out) {
+  double hmax = 0.0;
+  for (int j = 0; j < a; ++j)
+    for (int i = 0; i < a && i <= j + 1; ++i) hmax = fmax(hmax, fabs(Hb[i + j * ld]));
+  int lsq = 0, nrot = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    lsq = pass;
+    const int nr = lsq ? a + 1 : a;
+    for (int j = 0; j < a; ++j)
+      for (int i = 0; i <= a; ++i) R[i + j * ld] = (i < nr && i <= j + 1) ? Hb[i + j * ld] : 0.0;
+    nrot = 0;
+    for (int j = 0; j < a && j + 1 < nr; ++j) {
+      double c, s;
+      givens_rot(R[j + j * ld], R[(j + 1) + j * ld], c, s);
+      for (int l = j; l < a; ++l) {
+        const double t1 = R[j + l * ld], t2 = R[(j + 1) + l * ld];
+        R[j + l * ld] = c * t1 + s * t2;
+        R[(j + 1) + l * ld] = -s * t1 + c * t2;
+      }
+      rot[2 * j] = c;
+      rot[2 * j + 1] = s;
+      ++nrot;
+    }
+    int singular = 0;
+    for (int j = 0; j < a; ++j)
+      if (!(fabs(R[j + j * ld]) > 1e-14 * hmax)) singular = 1;
+    if (singular && !lsq && has_next) continue;
+    break;
+  }
+  for (int j = 0; j < a; ++j) rinv[j] = (R[j + j * ld] != 0.0) ? 1.0 / R[j + j * ld] : 0.0;
+  *lsq_out = lsq;
+  *nrot_out = nrot;
+}
+
+// alpha from c in place, c <- R^{-1} (G c), by one warp: the rotations on lane
+// 0, then a column-oriented back substitution (lane l owns rows l, l+32).
+// c lives in shared memory; a <= 64.  Ends with __syncwarp.
+__device__ __forceinline__ void solve_projected_warp(double* c, int a, int nrot, const double* R,
+                                                     int ld, const double* rot,
+                                                     const double* rinv, int lane) {
+  if (lane == 0) {
+    for (int j = 0; j < nrot; ++j) {
+      const double cc = rot[2 * j], s = rot[2 * j + 1];
+      const double t1 = c[j], t2 = c[j + 1];
+      c[j] = cc * t1 + s * t2;
+      c[j + 1] = -s * t1 + cc * t2;
+    }
+  }
+  __syncwarp();
+  double g0 = (lane < a) ? c[lane] : 0.0;
+  double g1 = (lane + 32 < a) ? c[lane + 32] : 0.0;
+  __syncwarp();
+  for (int i = a - 1; i >= 0; --i) {
+    const double gi = __shfl_sync(0xffffffffu, i < 32 ? g0 : g1, i & 31);
+    const double ai = gi * rinv[i];
+    if (lane == 0) c[i] = ai;
+    if (lane < i) g0 = fma(-R[lane + i * ld], ai, g0);
+    if (lane + 32 < i) g1 = fma(-R[(lane + 32) + i * ld], ai, g1);
+  }
+  __syncwarp();
+}
+
 // Launchers (defined in the .cu files; return a cudaError_t of the launch).
 cudaError_t launch_gmres_fp64(const GmresParams& p, int ept, int nt, size_t smem,
                               cudaStream_t st);
@@ -174,5 +292,6 @@ cudaError_t launch_gmres_fp64_1k_grid(const GmresParams& p, size_t smem, int gri
 cudaError_t launch_apply(const SysDesc* sys, int nsys, int mode, cudaStream_t st);
 cudaError_t launch_factor(const FactorParams& p, cudaStream_t st);
 cudaError_t launch_project_fp64(const ProjParams& p, int ept, int nt, cudaStream_t st);
+cudaError_t launch_advance(int* step, cudaStream_t st);
 
 }  // namespace kp

@@ -1,11 +1,17 @@
 // kp_march.cu -- the time march of Sec. 2.3 with the two phases of Sec. 3 at
 // every timestep, replayed from one CUDA graph per parity of n.
 //
-// The plan owns two copies of every state plane (ping-pong: the solution of
-// step n is written into the buffer that held m^{n-2}), the right-hand sides,
-// the per-system results and the device-side timestep counter, so that one
-// captured graph serves every even and one every odd timestep; the g^2
-// schedule is read on the device at the counter's index.
+// Per timestep n the graph holds two solver launches on parallel branches:
+//   targets of step n: b = m^{n-1}/dt formed on the fly, initial guess by
+//     projection onto the seed basis of step n (or 0, or m^{n-1}), GMRES(m);
+//   seeds of step n+1: GMRES(m_seed) from 0 with the first-cycle basis
+//     written straight into the seed slots of parity n+1 and H_a factored.
+// Seeds never depend on targets, so running them one step ahead lets their
+// (latency-bound, few-block) solves fill the SMs the target wave leaves idle.
+// A one-thread kernel then advances the device-side timestep counter, from
+// which both launches read g^2 and their slot parity; two copies of every
+// state plane alternate by parity, so one graph serves all even and one all
+// odd timesteps.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,75 +26,6 @@ using kp::SysDesc;
 
 namespace {
 
-enum Stat { kSeedIters = 0, kTgtIters, kTgtMax, kNotConv, kMaxRes, kRefFlops, kSeedFlops, kProjFlops, kNStat };
-
-// FP64 flops of GMRES(m) with CGS2 as implemented, per unknown, for k Arnoldi
-// steps: start (residual + norms) 14; per cycle of L steps
-// sum_j (9 stencil + 8(j+1) Gram-Schmidt + 5 norm/scale) + 2L update + 12 residual.
-__device__ __forceinline__ double gmres_flops_per_unknown(int k, int m) {
-  double f = 14.0;
-  const int full = k / m, rem = k - full * m;
-  const double Lm = m;
-  f += full * (4.0 * Lm * Lm + 20.0 * Lm + 12.0);
-  if (rem > 0) f += 4.0 * rem * rem + 20.0 * rem + 12.0;
-  return f;
-}
-
-struct StatsParams {
-  const kp_info* infoS;
-  const int* nS;           // unknowns per seed system
-  int ns;
-  const kp_info* infoT;
-  const int* nT;
-  const int* slotT;        // seed slot per target
-  int nt;
-  const kp::SlotMeta* meta;
-  int m_seed, m;
-  int project;
-  int* step;
-  int n0;
-  double* stats;           // [steps][kNStat]
-};
-
-__global__ void march_stats_kernel(const StatsParams p) {
-  __shared__ double red[kNStat][256];
-  double v[kNStat];
-  for (int k = 0; k < kNStat; ++k) v[k] = 0.0;
-  for (int i = threadIdx.x; i < p.ns; i += blockDim.x) {
-    const kp_info in = p.infoS[i];
-    v[kSeedIters] += in.iters;
-    v[kNotConv] += (in.status != 0);
-    v[kSeedFlops] += gmres_flops_per_unknown(in.iters, p.m_seed) * p.nS[i];
-  }
-  for (int i = threadIdx.x; i < p.nt; i += blockDim.x) {
-    const kp_info in = p.infoT[i];
-    v[kTgtIters] += in.iters;
-    v[kTgtMax] = fmax(v[kTgtMax], (double)in.iters);
-    v[kNotConv] += (in.status != 0);
-    v[kMaxRes] = fmax(v[kMaxRes], in.rel_res);
-    v[kRefFlops] += gmres_flops_per_unknown(in.iters, p.m) * p.nT[i];
-    if (p.project) {
-      const kp::SlotMeta mt = p.meta[p.slotT[i]];
-      v[kProjFlops] += (2.0 * (mt.lsq ? mt.a + 1 : mt.a) + 2.0 * mt.a) * p.nT[i];
-    }
-  }
-  for (int k = 0; k < kNStat; ++k) red[k][threadIdx.x] = v[k];
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s)
-      for (int k = 0; k < kNStat; ++k) {
-        const double a = red[k][threadIdx.x], b = red[k][threadIdx.x + s];
-        red[k][threadIdx.x] = (k == kTgtMax || k == kMaxRes) ? fmax(a, b) : a + b;
-      }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    const int st = *p.step;
-    for (int k = 0; k < kNStat; ++k) p.stats[(size_t)(st - p.n0) * kNStat + k] = red[k][0];
-    *p.step = st + 1;
-  }
-}
-
 template <typename T>
 cudaError_t dmalloc(T** p, size_t count) {
   return cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
@@ -99,178 +36,108 @@ cudaError_t dmalloc(T** p, size_t count) {
 struct kp_march_plan {
   kp_ctx* ctx = nullptr;
   kp_march_opts opt{};
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr;         // main branch (targets) and graph launches
+  cudaStream_t st2 = nullptr;        // seed branch inside the captured graph
+  cudaEvent_t fork = nullptr, join = nullptr;
   int ns = 0, nt = 0;
   size_t seed_elems = 0, tgt_elems = 0;
   std::vector<kp_group> groups;
   std::vector<size_t> seed_off, tgt_off;     // element offsets of each group's planes
   // device state
-  double* S[2] = {nullptr, nullptr};
-  double* Tt[2] = {nullptr, nullptr};
-  double* bS = nullptr;
-  double* bT = nullptr;
-  kp_info* infoS = nullptr;
-  kp_info* infoT = nullptr;
-  int* nS = nullptr;
-  int* nT = nullptr;
-  int* slotT = nullptr;
+  double* S[2] = {nullptr, nullptr};        // seed states, m_s^k in S[k & 1]
+  double* Tt[2] = {nullptr, nullptr};       // target states, m_t^k in Tt[k & 1]
   double* g2 = nullptr;
-  int* step = nullptr;
-  double* stats = nullptr;
-  double* capV = nullptr;
-  double* capH = nullptr;
-  kp::CapMeta* capMeta = nullptr;
+  int* step = nullptr;                      // [0] current target timestep, [1] end of run
+  kp::StepAcc* acc = nullptr;               // [T]
   double* spill = nullptr;
-  SysDesc* desc[2] = {nullptr, nullptr};     // per parity: seedRhs, seedSolve, tgtRhs, tgtProj, tgtSolve
+  SysDesc* desc[2] = {nullptr, nullptr};     // per parity p: seeds (step n+1), targets (step n)
   kp::Shape shS, shT;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int launches_per_step = 0;
-  int n0_host = 0;           // source of the counter reset (outlives the async copy)
+  int host_step[2] = {0, 0};                 // source of the counter reset (outlives the copy)
 };
 
 namespace {
 
-// Offsets of the descriptor sub-arrays inside desc[parity].
-struct DescLayout {
-  size_t seedRhs, seedSolve, tgtRhs, tgtProj, tgtSolve, total;
-};
-
-DescLayout layout(int ns, int nt) {
-  DescLayout L;
-  L.seedRhs = 0;
-  L.seedSolve = ns;
-  L.tgtRhs = 2 * (size_t)ns;
-  L.tgtProj = L.tgtRhs + nt;
-  L.tgtSolve = L.tgtProj + nt;
-  L.total = L.tgtSolve + nt;
-  return L;
-}
-
-// Enqueue timestep work for parity `par` (state read from buffer par, written
-// to buffer 1-par).  ev != null: bracket the kernels with events
-// (ev[0..7] = seed start/end, store start/end, proj start/end, refine start/end).
-kp_status enqueue_step(kp_march_plan* P, int par, cudaEvent_t* ev, int* launches) {
+kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset) {
   kp_ctx* c = P->ctx;
-  const DescLayout L = layout(P->ns, P->nt);
-  SysDesc* D = P->desc[par];
-  double* nxtS = P->S[1 - par];
-  double* curT = P->Tt[par];
-  double* nxtT = P->Tt[1 - par];
-  cudaError_t e = cudaSuccess;
-  int nl = 0;
-  auto rec = [&](int k) { if (ev && e == cudaSuccess) e = cudaEventRecord(ev[k], P->st); };
-  // ---- Phase 1: seeds
-  if (P->ns > 0) {
-    e = kp::launch_apply(D + L.seedRhs, P->ns, 1, P->st); ++nl;
-    if (e == cudaSuccess) e = cudaMemsetAsync(nxtS, 0, P->seed_elems * sizeof(double), P->st);
-    rec(0);
-    kp::GmresParams g{};
-    g.sys = D + L.seedSolve;
-    g.nsys = P->ns;
-    g.tol = P->opt.tol_seed;
-    g.m = P->opt.m_seed;
-    g.maxit = P->opt.maxit;
-    g.S = P->shS.S;
-    g.reorth = c->opt.reorth;
-    g.npad = P->shS.ept * P->shS.nt;
-    g.spill = (P->shS.S < g.m + 1) ? P->spill : nullptr;
-    g.info = P->infoS;
-    g.capV = P->capV;
-    g.capH = P->capH;
-    g.capMeta = P->capMeta;
+  kp::GmresParams g{};
+  const kp::Shape& sh = seeds ? P->shS : P->shT;
+  g.sys = P->desc[par] + (seeds ? 0 : P->ns);
+  g.nsys = seeds ? P->ns : P->nt;
+  g.tol = seeds ? P->opt.tol_seed : P->opt.tol;
+  g.m = seeds ? P->opt.m_seed : P->opt.m;
+  g.maxit = P->opt.maxit;
+  g.S = sh.S;
+  g.reorth = c->opt.reorth;
+  g.npad = sh.ept * sh.nt;
+  size_t spS = 0;
+  if (P->ns && P->shS.S < P->opt.m_seed + 1)
+    spS = (size_t)P->ns * (P->opt.m_seed + 1 - P->shS.S) * P->shS.ept * P->shS.nt;
+  g.spill = (sh.S < g.m + 1) ? P->spill + (seeds ? 0 : spS) : nullptr;
+  g.info = nullptr;
+  g.step = P->step;
+  g.g2_sched = P->g2;
+  g.step_offset = offset;
+  g.step_end = P->step + 1;
+  g.b_scale = (double)P->opt.T;               // b = m^{n-1} / dt with dt = 1/T
+  g.slotV = c->slotV;
+  g.slotMeta = c->slotMeta;
+  g.slotR = c->slotR;
+  g.slotRot = c->slotRot;
+  g.slot_ld = c->opt.max_n;
+  g.max_a = c->opt.max_a;
+  g.slot_parity_stride = P->ns;
+  g.acc = P->acc;
+  if (seeds) {
+    g.x0_mode = kp::X0_ZERO;
+    g.capV = c->slotV;                       // capture straight into the seed slots
+    g.capH = c->slotH;
     g.cap_a = c->opt.max_a;
     g.cap_ld = c->opt.max_n;
-    g.step = P->step;
-    g.g2_sched = P->g2;
-    if (e == cudaSuccess) { e = kp::launch_gmres_fp64(g, P->shS.ept, P->shS.nt, P->shS.smem, P->st); ++nl; }
-    rec(1);
-    rec(2);
-    kp::FactorParams f{};
-    f.capV = P->capV;
-    f.capH = P->capH;
-    f.capMeta = P->capMeta;
-    f.sys = 0;
-    f.cap_a = c->opt.max_a;
-    f.cap_ld = c->opt.max_n;
-    f.slotV = c->slotV;
-    f.meta = c->slotMeta;
-    f.slotR = c->slotR;
-    f.slotRot = c->slotRot;
-    f.slotH = c->slotH;
-    f.seed_id = 0;
-    f.timestep = 0;
-    f.max_a = c->opt.max_a;
-    f.ld = c->opt.max_n;
-    f.count = P->ns;
-    f.step = P->step;
-    if (e == cudaSuccess) { e = kp::launch_factor(f, P->st); ++nl; }
-    rec(3);
+    g.factor = 1;
+    g.acc_kind = 0;
+  } else {
+    g.x0_mode = P->opt.mode == KP_MARCH_PROJECTED ? (P->ns ? kp::X0_PROJECT : kp::X0_ZERO)
+              : P->opt.mode == KP_MARCH_WARM ? kp::X0_WARM : kp::X0_ZERO;
+    g.acc_kind = 1;
   }
-  // ---- Phase 2: targets
-  if (P->nt > 0) {
-    if (e == cudaSuccess) { e = kp::launch_apply(D + L.tgtRhs, P->nt, 1, P->st); ++nl; }
-    rec(4);
-    if (e == cudaSuccess) {
-      if (P->opt.mode == KP_MARCH_WARM)
-        e = cudaMemcpyAsync(nxtT, curT, P->tgt_elems * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
-      else
-        e = cudaMemsetAsync(nxtT, 0, P->tgt_elems * sizeof(double), P->st);
-    }
-    if (P->opt.mode == KP_MARCH_PROJECTED && P->ns > 0 && e == cudaSuccess) {
-      kp::ProjParams pp{};
-      pp.sys = D + L.tgtProj;
-      pp.nt = P->nt;
-      pp.timestep = 0;
-      pp.slotV = c->slotV;
-      pp.meta = c->slotMeta;
-      pp.slotR = c->slotR;
-      pp.slotRot = c->slotRot;
-      pp.max_a = c->opt.max_a;
-      pp.ld = c->opt.max_n;
-      pp.step = P->step;
-      e = kp::launch_project_fp64(pp, P->shT.ept, P->shT.nt, P->st);
-      ++nl;
-    }
-    rec(5);
-    rec(6);
-    kp::GmresParams g{};
-    g.sys = D + L.tgtSolve;
-    g.nsys = P->nt;
-    g.tol = P->opt.tol;
-    g.m = P->opt.m;
-    g.maxit = P->opt.maxit;
-    g.S = P->shT.S;
-    g.reorth = c->opt.reorth;
-    g.npad = P->shT.ept * P->shT.nt;
-    g.spill = (P->shT.S < g.m + 1) ? P->spill : nullptr;
-    g.info = P->infoT;
-    g.step = P->step;
-    g.g2_sched = P->g2;
-    if (e == cudaSuccess) { e = kp::launch_gmres_fp64(g, P->shT.ept, P->shT.nt, P->shT.smem, P->st); ++nl; }
-    rec(7);
+  return g;
+}
+
+// Target step n and seed step n+1 for parity p = n & 1.  With ev (timing
+// mode) the two launches run one after the other between events
+// ev[0..1] (seeds) and ev[2..3] (targets); otherwise on two branches.
+kp_status enqueue_step(kp_march_plan* P, int par, cudaEvent_t* ev, int* launches) {
+  cudaError_t e = cudaSuccess;
+  int nl = 0;
+  const bool branch = (ev == nullptr) && P->ns > 0 && P->nt > 0;
+  cudaStream_t sst = branch ? P->st2 : P->st;
+  if (branch) {
+    e = cudaEventRecord(P->fork, P->st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P->st2, P->fork, 0);
   }
-  StatsParams sp{};
-  sp.infoS = P->infoS;
-  sp.nS = P->nS;
-  sp.ns = P->ns;
-  sp.infoT = P->infoT;
-  sp.nT = P->nT;
-  sp.slotT = P->slotT;
-  sp.nt = P->nt;
-  sp.meta = c->slotMeta;
-  sp.m_seed = P->opt.m_seed;
-  sp.m = P->opt.m;
-  sp.project = (P->opt.mode == KP_MARCH_PROJECTED && P->ns > 0);
-  sp.step = P->step;
-  sp.n0 = 0;
-  sp.stats = P->stats;
-  if (e == cudaSuccess) {
-    march_stats_kernel<<<1, 256, 0, P->st>>>(sp);
-    e = cudaGetLastError();
+  if (P->ns > 0 && e == cudaSuccess) {
+    if (ev) e = cudaEventRecord(ev[0], sst);
+    kp::GmresParams g = solver_params(P, true, par, 1);
+    if (e == cudaSuccess) e = kp::launch_gmres_fp64(g, P->shS.ept, P->shS.nt, P->shS.smem, sst);
     ++nl;
+    if (ev && e == cudaSuccess) e = cudaEventRecord(ev[1], sst);
   }
+  if (P->nt > 0 && e == cudaSuccess) {
+    if (ev) e = cudaEventRecord(ev[2], P->st);
+    kp::GmresParams g = solver_params(P, false, par, 0);
+    if (e == cudaSuccess) e = kp::launch_gmres_fp64(g, P->shT.ept, P->shT.nt, P->shT.smem, P->st);
+    ++nl;
+    if (ev && e == cudaSuccess) e = cudaEventRecord(ev[3], P->st);
+  }
+  if (branch && e == cudaSuccess) {
+    e = cudaEventRecord(P->join, P->st2);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(P->st, P->join, 0);
+  }
+  if (e == cudaSuccess) { e = kp::launch_advance(P->step, P->st); ++nl; }
   if (launches) *launches = nl;
-  return e == cudaSuccess ? KP_OK : kp::cuda_error(c, e, "march step enqueue");
+  return e == cudaSuccess ? KP_OK : kp::cuda_error(P->ctx, e, "march step enqueue");
 }
 
 }  // namespace
@@ -287,9 +154,13 @@ kp_status kp_march_destroy(kp_march_plan* P) {
     cudaFree(P->Tt[k]);
     cudaFree(P->desc[k]);
   }
-  cudaFree(P->bS); cudaFree(P->bT); cudaFree(P->infoS); cudaFree(P->infoT);
-  cudaFree(P->nS); cudaFree(P->nT); cudaFree(P->slotT); cudaFree(P->g2); cudaFree(P->step);
-  cudaFree(P->stats); cudaFree(P->capV); cudaFree(P->capH); cudaFree(P->capMeta); cudaFree(P->spill);
+  cudaFree(P->g2);
+  cudaFree(P->step);
+  cudaFree(P->acc);
+  cudaFree(P->spill);
+  if (P->fork) cudaEventDestroy(P->fork);
+  if (P->join) cudaEventDestroy(P->join);
+  if (P->st2) cudaStreamDestroy(P->st2);
   if (P->st) cudaStreamDestroy(P->st);
   delete P;
   return KP_OK;
@@ -297,7 +168,8 @@ kp_status kp_march_destroy(kp_march_plan* P) {
 
 kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const kp_march_opts* opt,
                           kp_march_plan** out) {
-  if (!c || !out || !opt || ngroups < 1 || !groups) return c ? kp::set_error(c, KP_ERR_ARG, "bad march arguments") : KP_ERR_ARG;
+  if (!c) return KP_ERR_ARG;
+  if (!out || !opt || ngroups < 1 || !groups) return kp::set_error(c, KP_ERR_ARG, "bad march arguments");
   *out = nullptr;
   if (c->opt.precision != KP_PREC_FP64)
     return kp::set_error(c, KP_ERR_UNSUPPORTED, "precision mode %d not built in the march", c->opt.precision);
@@ -318,13 +190,12 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
       kp_march_destroy(P);
       return kp::set_error(c, KP_ERR_ARG, "group %d: bad sizes or pointers", gi);
     }
-    for (int t = 0; t < g.ntgt; ++t)
-      if (g.tgt_seed[t] < 0 || g.tgt_seed[t] >= g.nseed) {
-        if (o.mode == KP_MARCH_PROJECTED) {
+    if (o.mode == KP_MARCH_PROJECTED)
+      for (int t = 0; t < g.ntgt; ++t)
+        if (g.tgt_seed[t] < 0 || g.tgt_seed[t] >= g.nseed) {
           kp_march_destroy(P);
           return kp::set_error(c, KP_ERR_ARG, "group %d target %d: seed index out of range", gi, t);
         }
-      }
     P->seed_off.push_back(P->seed_elems);
     P->tgt_off.push_back(P->tgt_elems);
     P->seed_elems += (size_t)g.nseed * N;
@@ -334,58 +205,43 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
     if (g.nseed) nmaxS = std::max(nmaxS, N);
     if (g.ntgt) nmaxT = std::max(nmaxT, N);
   }
-  if (P->ns > c->opt.max_seeds) {
+  if (2 * P->ns > c->opt.max_seeds) {
     kp_march_destroy(P);
-    return kp::set_error(c, KP_ERR_ARG, "%d seeds exceed max_seeds=%d", P->ns, c->opt.max_seeds);
+    return kp::set_error(c, KP_ERR_ARG, "%d seeds need 2x%d basis slots (one set per timestep parity); max_seeds=%d",
+                         P->ns, P->ns, c->opt.max_seeds);
   }
   kp_status s = KP_OK;
   if (P->ns) s = kp::gmres_shape(c, nmaxS, o.m_seed, &P->shS);
   if (s == KP_OK && P->nt) s = kp::gmres_shape(c, nmaxT, o.m, &P->shT);
   if (s != KP_OK) { kp_march_destroy(P); return s; }
   cudaError_t e = cudaStreamCreateWithFlags(&P->st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->st2, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->join, cudaEventDisableTiming);
   const int ns = P->ns, nt = P->nt;
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
     e = dmalloc(&P->S[k], P->seed_elems);
     if (e == cudaSuccess) e = dmalloc(&P->Tt[k], P->tgt_elems);
   }
-  if (e == cudaSuccess) e = dmalloc(&P->bS, P->seed_elems);
-  if (e == cudaSuccess) e = dmalloc(&P->bT, P->tgt_elems);
-  if (e == cudaSuccess) e = dmalloc(&P->infoS, ns);
-  if (e == cudaSuccess) e = dmalloc(&P->infoT, nt);
-  if (e == cudaSuccess) e = dmalloc(&P->nS, ns);
-  if (e == cudaSuccess) e = dmalloc(&P->nT, nt);
-  if (e == cudaSuccess) e = dmalloc(&P->slotT, nt);
   if (e == cudaSuccess) e = dmalloc(&P->g2, o.T);
-  if (e == cudaSuccess) e = dmalloc(&P->step, 1);
-  if (e == cudaSuccess) e = dmalloc(&P->stats, (size_t)o.T * kNStat);
-  if (e == cudaSuccess && ns) {
-    e = dmalloc(&P->capV, (size_t)ns * (c->opt.max_a + 1) * c->opt.max_n);
-    if (e == cudaSuccess) e = dmalloc(&P->capH, (size_t)ns * (c->opt.max_a + 1) * c->opt.max_a);
-    if (e == cudaSuccess) e = dmalloc(&P->capMeta, ns);
-  }
-  size_t spill = 0;
-  if (ns && P->shS.S < o.m_seed + 1)
-    spill = std::max(spill, (size_t)ns * (o.m_seed + 1 - P->shS.S) * P->shS.ept * P->shS.nt);
-  if (nt && P->shT.S < o.m + 1)
-    spill = std::max(spill, (size_t)nt * (o.m + 1 - P->shT.S) * P->shT.ept * P->shT.nt);
-  if (e == cudaSuccess && spill) e = dmalloc(&P->spill, spill);
-  const DescLayout L = layout(ns, nt);
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = dmalloc(&P->desc[k], L.total);
+  if (e == cudaSuccess) e = dmalloc(&P->step, 2);
+  if (e == cudaSuccess) e = dmalloc(&P->acc, o.T);
+  // one Krylov workspace per branch: seed blocks first, then target blocks
+  size_t spS = 0, spT = 0;
+  if (ns && P->shS.S < o.m_seed + 1) spS = (size_t)ns * (o.m_seed + 1 - P->shS.S) * P->shS.ept * P->shS.nt;
+  if (nt && P->shT.S < o.m + 1) spT = (size_t)nt * (o.m + 1 - P->shT.S) * P->shT.ept * P->shT.nt;
+  if (e == cudaSuccess && spS + spT) e = dmalloc(&P->spill, spS + spT);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = dmalloc(&P->desc[k], (size_t)ns + nt);
   if (e != cudaSuccess) {
     kp_status r = kp::cuda_error(c, e, "march allocation");
     kp_march_destroy(P);
     return r;
   }
-  // host-side tables
+  // descriptors for parity p: seeds of step n+1 (m_s^{n+1} in S[1-p] -> S[p]),
+  // targets of step n (m_t^n in T[p] -> T[1-p]); b is the state itself, scaled by 1/dt
   const double dt = 1.0 / o.T;
-  std::vector<int> hnS(std::max(ns, 1)), hnT(std::max(nt, 1)), hslot(std::max(nt, 1));
-  std::vector<SysDesc> hd[2];
-  for (int par = 0; par < 2; ++par) {
-    hd[par].resize(L.total);
-    double* cS = P->S[par];
-    double* xS = P->S[1 - par];
-    double* cT = P->Tt[par];
-    double* xT = P->Tt[1 - par];
+  for (int par = 0; par < 2 && e == cudaSuccess; ++par) {
+    std::vector<SysDesc> hd((size_t)ns + nt);
     int si = 0, ti = 0, seed_base = 0;
     for (int gi = 0; gi < ngroups; ++gi) {
       const kp_group& g = groups[gi];
@@ -394,44 +250,33 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
         const size_t off = P->seed_off[gi] + (size_t)k * N;
         SysDesc d{};
         d.H = g.H; d.W = g.W; d.dt = dt; d.g2 = 0.0; d.h = 1.0 / g.H;
-        d.mt = cS + off; d.fx = d.fy = nullptr;
-        d.b = cS + off; d.x = P->bS + off;            // rhs: b <- m^{n-1}/dt
-        hd[par][L.seedRhs + si] = d;
-        d.b = P->bS + off; d.x = xS + off;            // solve into the other buffer
-        hd[par][L.seedSolve + si] = d;
-        hnS[si] = N;
+        d.mt = P->S[1 - par] + off;
+        d.b = d.mt;
+        d.x = P->S[par] + off;
+        d.slot = 0;
+        hd[si] = d;
       }
       for (int k = 0; k < g.ntgt; ++k, ++ti) {
         const size_t off = P->tgt_off[gi] + (size_t)k * N;
         SysDesc d{};
         d.H = g.H; d.W = g.W; d.dt = dt; d.g2 = 0.0; d.h = 1.0 / g.H;
-        d.mt = cT + off; d.fx = d.fy = nullptr;
-        d.b = cT + off; d.x = P->bT + off;
-        hd[par][L.tgtRhs + ti] = d;
-        d.b = P->bT + off; d.x = xT + off;
-        const int sd = (g.tgt_seed[k] >= 0 && g.tgt_seed[k] < g.nseed) ? g.tgt_seed[k] : 0;
-        d.slot = seed_base + sd;
-        hd[par][L.tgtProj + ti] = d;
-        d.slot = 0;
-        hd[par][L.tgtSolve + ti] = d;
-        hnT[ti] = N;
-        hslot[ti] = seed_base + sd;
+        d.mt = P->Tt[par] + off;
+        d.b = d.mt;
+        d.x = P->Tt[1 - par] + off;
+        const int sd = (g.tgt_seed && g.tgt_seed[k] >= 0 && g.tgt_seed[k] < g.nseed) ? g.tgt_seed[k] : 0;
+        d.slot = seed_base + sd;               // parity offset added on the device
+        hd[(size_t)ns + ti] = d;
       }
       seed_base += g.nseed;
     }
+    e = cudaMemcpy(P->desc[par], hd.data(), hd.size() * sizeof(SysDesc), cudaMemcpyHostToDevice);
   }
-  for (int k = 0; k < 2 && e == cudaSuccess; ++k)
-    e = cudaMemcpy(P->desc[k], hd[k].data(), L.total * sizeof(SysDesc), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(P->nS, hnS.data(), ns * sizeof(int), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(P->nT, hnT.data(), nt * sizeof(int), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(P->slotT, hslot.data(), nt * sizeof(int), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(P->g2, o.g2, o.T * sizeof(double), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     kp_status r = kp::cuda_error(c, e, "march tables");
     kp_march_destroy(P);
     return r;
   }
-  // graphs: one per parity
   if (o.use_graph) {
     for (int par = 0; par < 2; ++par) {
       cudaGraph_t gr = nullptr;
@@ -462,33 +307,44 @@ kp_status kp_march_run(kp_march_plan* P, int n0, int steps, kp_step_stats* stats
   if (n0 < 0 || steps < 0 || n0 + steps > P->opt.T)
     return kp::set_error(c, KP_ERR_ARG, "timesteps %d..%d outside 1..%d", n0 + 1, n0 + steps, P->opt.T);
   if (steps == 0) return KP_OK;
+  const int q0 = n0 & 1;
   cudaError_t e = cudaSuccess;
-  // order after the caller's stream, then copy the caller's states in
-  cudaEvent_t join = nullptr;
-  e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventRecord(join, c->stream);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(P->st, join, 0);
+  // after the caller's stream: states in, counters and totals reset
+  cudaEvent_t sync_ev = nullptr;
+  e = cudaEventCreateWithFlags(&sync_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(sync_ev, c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(P->st, sync_ev, 0);
   for (size_t gi = 0; gi < P->groups.size() && e == cudaSuccess; ++gi) {
     const kp_group& g = P->groups[gi];
     const size_t N = (size_t)g.H * g.W;
-    if (g.nseed) e = cudaMemcpyAsync(P->S[0] + P->seed_off[gi], g.m_seed, g.nseed * N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
-    if (e == cudaSuccess && g.ntgt) e = cudaMemcpyAsync(P->Tt[0] + P->tgt_off[gi], g.m_tgt, g.ntgt * N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
+    if (g.nseed) e = cudaMemcpyAsync(P->S[q0] + P->seed_off[gi], g.m_seed, g.nseed * N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
+    if (e == cudaSuccess && g.ntgt) e = cudaMemcpyAsync(P->Tt[q0] + P->tgt_off[gi], g.m_tgt, g.ntgt * N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
   }
-  P->n0_host = n0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(P->step, &P->n0_host, sizeof(int), cudaMemcpyHostToDevice, P->st);
+  P->host_step[0] = n0;
+  P->host_step[1] = n0 + steps;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(P->step, P->host_step, 2 * sizeof(int), cudaMemcpyHostToDevice, P->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P->acc + n0, 0, (size_t)steps * sizeof(kp::StepAcc), P->st);
   std::vector<cudaEvent_t> ev;
   int launches = 0;
   if (e == cudaSuccess && timing) {
-    ev.resize((size_t)steps * 8, nullptr);
+    ev.resize((size_t)steps * 4 + 2, nullptr);
     for (auto& x : ev)
       if (e == cudaSuccess) e = cudaEventCreate(&x);
   }
   kp_status r = KP_OK;
+  // prologue: seeds of step n0 (their basis serves the targets of step n0)
+  if (e == cudaSuccess && P->ns) {
+    kp::GmresParams g = solver_params(P, true, 1 - q0, 0);
+    if (timing) e = cudaEventRecord(ev[(size_t)steps * 4], P->st);
+    if (e == cudaSuccess) e = kp::launch_gmres_fp64(g, P->shS.ept, P->shS.nt, P->shS.smem, P->st);
+    if (timing && e == cudaSuccess) e = cudaEventRecord(ev[(size_t)steps * 4 + 1], P->st);
+    ++launches;
+  }
   for (int k = 0; k < steps && e == cudaSuccess && r == KP_OK; ++k) {
-    const int par = k & 1;
+    const int par = (n0 + k) & 1;
     if (timing) {
       int nl = 0;
-      r = enqueue_step(P, par, ev.data() + (size_t)k * 8, &nl);
+      r = enqueue_step(P, par, ev.data() + (size_t)k * 4, &nl);
       launches += nl;
     } else if (P->graph[par]) {
       e = cudaGraphLaunch(P->graph[par], P->st);
@@ -499,57 +355,58 @@ kp_status kp_march_run(kp_march_plan* P, int n0, int steps, kp_step_stats* stats
       launches += nl;
     }
   }
-  // states back to the caller's buffers
-  const int fin = steps & 1;
+  const int fin = (n0 + steps) & 1;
   for (size_t gi = 0; gi < P->groups.size() && e == cudaSuccess && r == KP_OK; ++gi) {
     const kp_group& g = P->groups[gi];
     const size_t N = (size_t)g.H * g.W;
     if (g.nseed) e = cudaMemcpyAsync(g.m_seed, P->S[fin] + P->seed_off[gi], g.nseed * N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
     if (e == cudaSuccess && g.ntgt) e = cudaMemcpyAsync(g.m_tgt, P->Tt[fin] + P->tgt_off[gi], g.ntgt * N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
   }
-  if (e == cudaSuccess) e = cudaEventRecord(join, P->st);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, join, 0);
+  if (e == cudaSuccess) e = cudaEventRecord(sync_ev, P->st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, sync_ev, 0);
   if (e == cudaSuccess && (stats || timing)) e = cudaStreamSynchronize(P->st);
   if (e == cudaSuccess && stats) {
-    std::vector<double> h((size_t)steps * kNStat);
-    e = cudaMemcpy(h.data(), P->stats + (size_t)n0 * kNStat, h.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    std::vector<kp::StepAcc> h(steps);
+    e = cudaMemcpy(h.data(), P->acc + n0, steps * sizeof(kp::StepAcc), cudaMemcpyDeviceToHost);
     for (int k = 0; k < steps && e == cudaSuccess; ++k) {
-      const double* v = h.data() + (size_t)k * kNStat;
-      stats[k].seed_iters = v[kSeedIters];
-      stats[k].tgt_iters = v[kTgtIters];
-      stats[k].tgt_iters_max = v[kTgtMax];
-      stats[k].not_converged = v[kNotConv];
-      stats[k].max_rel_res = v[kMaxRes];
-      stats[k].refine_flops = v[kRefFlops];
-      stats[k].seed_flops = v[kSeedFlops];
-      stats[k].proj_flops = v[kProjFlops];
+      const kp::StepAcc& a = h[k];
+      double mr;
+      std::memcpy(&mr, &a.max_res_bits, sizeof(mr));
+      stats[k].seed_iters = (double)a.seed_iters;
+      stats[k].tgt_iters = (double)a.tgt_iters;
+      stats[k].tgt_iters_max = (double)a.tgt_max_iters;
+      stats[k].not_converged = (double)a.not_converged;
+      stats[k].max_rel_res = mr;
+      stats[k].refine_flops = (double)a.tgt_flops;
+      stats[k].seed_flops = (double)a.seed_flops;
+      stats[k].proj_flops = (double)a.proj_flops;
     }
   }
   if (e == cudaSuccess && timing) {
     std::memset(timing, 0, sizeof(*timing));
+    float t = 0.f;
+    if (P->ns) {
+      e = cudaEventElapsedTime(&t, ev[(size_t)steps * 4], ev[(size_t)steps * 4 + 1]);
+      timing->seed_ms += t;
+    }
     for (int k = 0; k < steps && e == cudaSuccess; ++k) {
-      cudaEvent_t* x = ev.data() + (size_t)k * 8;
-      float a = 0, b = 0, cc = 0, d = 0, s = 0;
+      cudaEvent_t* x = ev.data() + (size_t)k * 4;
       if (P->ns) {
-        e = cudaEventElapsedTime(&a, x[0], x[1]);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&b, x[2], x[3]);
+        e = cudaEventElapsedTime(&t, x[0], x[1]);
+        timing->seed_ms += t;
       }
       if (e == cudaSuccess && P->nt) {
-        e = cudaEventElapsedTime(&cc, x[4], x[5]);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&d, x[6], x[7]);
+        e = cudaEventElapsedTime(&t, x[2], x[3]);
+        timing->refine_ms += t;
       }
-      if (e == cudaSuccess && P->ns && P->nt) e = cudaEventElapsedTime(&s, x[0], x[7]);
-      timing->seed_ms += a;
-      timing->store_ms += b;
-      timing->proj_ms += cc;
-      timing->refine_ms += d;
-      timing->step_ms += s;
     }
+    if (e == cudaSuccess && P->ns && P->nt)
+      e = cudaEventElapsedTime(&timing->step_ms, ev[(size_t)steps * 4], ev[(size_t)(steps - 1) * 4 + 3]);
   }
   if (timing) timing->launches = launches;
   for (auto& x : ev)
     if (x) cudaEventDestroy(x);
-  if (join) cudaEventDestroy(join);
+  if (sync_ev) cudaEventDestroy(sync_ev);
   if (r != KP_OK) return r;
   return e == cudaSuccess ? KP_OK : kp::cuda_error(c, e, "march run");
 }

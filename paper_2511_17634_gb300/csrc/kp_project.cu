@@ -10,14 +10,6 @@
 namespace kp {
 namespace {
 
-__device__ __forceinline__ void givens2(double a, double b, double& c, double& s) {
-  if (b == 0.0) { c = 1.0; s = 0.0; return; }
-  const double r = hypot(a, b);
-  const double ir = 1.0 / r;
-  c = a * ir;
-  s = b * ir;
-}
-
 // Copies the captured basis of system p.sys into slot p.seed_id and factors
 // its Hessenberg matrix.  One block; thread 0 does the (tiny) factorisation.
 __global__ void factor_kernel(FactorParams p) {
@@ -41,39 +33,11 @@ __global__ void factor_kernel(FactorParams p) {
   const double* ch = p.capH + (size_t)p.sys * cld * p.cap_a;
   double* sh = p.slotH + (size_t)p.seed_id * sld * p.max_a;
   double* R = p.slotR + (size_t)p.seed_id * sld * p.max_a;   // (a+1) x a, ld max_a+1
-  double* rot = p.slotRot + (size_t)p.seed_id * 2 * p.max_a;
-  double hmax = 0.0;
+  double* rot = p.slotRot + (size_t)p.seed_id * 3 * p.max_a;
   for (int j = 0; j < a; ++j)
-    for (int i = 0; i <= a; ++i) {
-      const double v = (i <= j + 1) ? ch[i + j * cld] : 0.0;
-      sh[i + j * sld] = v;
-      if (i < a) hmax = fmax(hmax, fabs(v));
-    }
+    for (int i = 0; i <= a; ++i) sh[i + j * sld] = (i <= j + 1) ? ch[i + j * cld] : 0.0;
   int lsq = 0, nrot = 0;
-  for (int pass = 0; pass < 2; ++pass) {
-    lsq = pass;
-    const int nr = lsq ? a + 1 : a;
-    for (int j = 0; j < a; ++j)
-      for (int i = 0; i <= a; ++i) R[i + j * sld] = (i < nr) ? sh[i + j * sld] : 0.0;
-    nrot = 0;
-    for (int j = 0; j < a && j + 1 < nr; ++j) {
-      double c, s;
-      givens2(R[j + j * sld], R[(j + 1) + j * sld], c, s);
-      for (int l = j; l < a; ++l) {
-        const double t1 = R[j + l * sld], t2 = R[(j + 1) + l * sld];
-        R[j + l * sld] = c * t1 + s * t2;
-        R[(j + 1) + l * sld] = -s * t1 + c * t2;
-      }
-      rot[2 * j] = c;
-      rot[2 * j + 1] = s;
-      ++nrot;
-    }
-    int singular = 0;
-    for (int j = 0; j < a; ++j)
-      if (!(fabs(R[j + j * sld]) > 1e-14 * hmax)) singular = 1;
-    if (singular && !lsq && hn) continue;
-    break;
-  }
+  factor_hessenberg(sh, sld, a, hn, R, rot, rot + 2 * p.max_a, &lsq, &nrot);
   SlotMeta mt;
   mt.a = a;
   mt.has_next = hn;
@@ -120,23 +84,10 @@ __global__ void __launch_bounds__(NT) project_fp64_kernel(const ProjParams p) {
     if (warp == 0) {
       for (int i = lane; i < nv; i += 32) cvec[i] = cross_warp<NT>(red, i);
       __syncwarp();
-      if (lane == 0) {
-        const int sld = p.max_a + 1;
-        const double* R = p.slotR + (size_t)d.slot * sld * p.max_a;
-        const double* rot = p.slotRot + (size_t)d.slot * 2 * p.max_a;
-        for (int j = 0; j < mt.nrot; ++j) {
-          const double c = rot[2 * j], s = rot[2 * j + 1];
-          const double t1 = cvec[j], t2 = cvec[j + 1];
-          cvec[j] = c * t1 + s * t2;
-          cvec[j + 1] = -s * t1 + c * t2;
-        }
-        for (int i = a - 1; i >= 0; --i) {          // alpha overwrites cvec[0..a)
-          double s = cvec[i];
-          for (int l = i + 1; l < a; ++l) s -= R[i + l * sld] * cvec[l];
-          const double rii = R[i + i * sld];
-          cvec[i] = (rii != 0.0) ? s / rii : 0.0;
-        }
-      }
+      const int sld = p.max_a + 1;
+      const double* rot = p.slotRot + (size_t)d.slot * 3 * p.max_a;
+      solve_projected_warp(cvec, a, mt.nrot, p.slotR + (size_t)d.slot * sld * p.max_a, sld, rot,
+                           rot + 2 * p.max_a, lane);
     }
     __syncthreads();
 #pragma unroll

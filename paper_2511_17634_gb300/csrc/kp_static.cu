@@ -123,6 +123,8 @@ extern "C" kp_status kp_refine_static(int nsys, const kp_op* ops, const double* 
   p.S = S;
   p.reorth = 0;
   p.npad = kNpad;
+  p.b_scale = 1.0;
+  p.x0_mode = kp::X0_READ;
   p.spill = (S < m + 1) ? reinterpret_cast<double*>(ds->scratch + kDescRegion) : nullptr;
   p.info = info;
   const size_t smem = fixed + (size_t)S * per;
