@@ -191,7 +191,12 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
         w[k] = (pp < N) ? bval(pp) - w[k] : 0.0;
       }
     };
-    residual();
+    if (p.x0_mode == X0_ZERO) {                // r = b, no operator application needed
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) w[k] = bval(tid + k * NT);
+    } else {
+      residual();
+    }
     block_partials<NT>(2, [&](int i) {
       double s = 0.0;
 #pragma unroll

@@ -167,18 +167,54 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Warp reduce-scatter of 4 values per lane: lanes with (lane & 7) == 0 end
+// with the warp sum of value 2*bit4 + bit3 (6 adds instead of 4 x 5).
+__device__ __forceinline__ double warp_reduce4(double (&a)[8], int lane) {
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const bool up = lane & 16;
+    const double send = up ? a[k] : a[k + 2];
+    const double keep = up ? a[k + 2] : a[k];
+    a[k] = keep + __shfl_xor_sync(kFull, send, 16);
+  }
+  {
+    const bool up = lane & 8;
+    const double send = up ? a[0] : a[1];
+    const double keep = up ? a[1] : a[0];
+    a[0] = keep + __shfl_xor_sync(kFull, send, 8);
+  }
+  a[0] += __shfl_xor_sync(kFull, a[0], 4);
+  a[0] += __shfl_xor_sync(kFull, a[0], 2);
+  a[0] += __shfl_xor_sync(kFull, a[0], 1);
+  return a[0];
+}
+
 // Per-warp partial sums of nv values partial(i) into red[warp][i]; ends with
-// a block barrier.  Every thread must call it with the same nv.
+// a block barrier.  Every thread must call it with the same nv.  Chunks of 8
+// values use an 8-wide reduce-scatter, a last chunk of up to 4 a 4-wide one,
+// a single value a plain butterfly.
 template <int NT, typename F>
 __device__ __forceinline__ void block_partials(int nv, F&& partial, double* red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i0 = 0; i0 < nv; i0 += 8) {
+  int i0 = 0;
+  for (; i0 + 4 < nv; i0 += 8) {
     double a[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) a[k] = (i0 + k < nv) ? partial(i0 + k) : 0.0;
     const double s = warp_reduce8(a, lane);
     const int v = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
     if ((lane & 3) == 0 && i0 + v < nv) red[warp * kMaxV + i0 + v] = s;
+  }
+  if (i0 + 1 < nv) {
+    double a[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] = (i0 + k < nv) ? partial(i0 + k) : 0.0;
+    const double s = warp_reduce4(a, lane);
+    const int v = ((lane >> 4) & 1) * 2 + ((lane >> 3) & 1);
+    if ((lane & 7) == 0 && i0 + v < nv) red[warp * kMaxV + i0 + v] = s;
+  } else if (i0 < nv) {
+    const double s = warp_sum(partial(i0));
+    if (lane == 0) red[warp * kMaxV + i0] = s;
   }
   __syncthreads();
 }
