@@ -205,6 +205,18 @@ kp_status kp_refine(kp_ctx* ctx, int nsys, const kp_op* ops, const double* const
 kp_status kp_refine_static(int nsys, const kp_op* ops, const double* const* b, double* const* x,
                            double tol, int m, int maxit, kp_info* info, void* cuda_stream);
 
+/*
+ * The contraction of Sec. 3, Phase 2 on the tensor cores:
+ *   C[t][i] = sum_{k<K} B[t][k] V[i][k]   for t < nt, i < nv,
+ * i.e. c_t = V_a^T b_t for every target, with tcgen05 MMAs (BF16 inputs, FP32
+ * accumulation in tensor memory).  V: device BF16 [nv][ldv] (nv <= 48),
+ * B: device BF16 [nt][ldb], C: device FP32 [nt][ldc]; ldv, ldb multiples of
+ * 8 elements and V, B 16-byte aligned (TMA); K <= ldv, ldb.  Asynchronous on
+ * the context's stream.
+ */
+kp_status kp_project_gemm_bf16(kp_ctx* ctx, int nt, int nv, int K, const void* B, int ldb,
+                               const void* V, int ldv, float* C, int ldc);
+
 /* Inspect a stored basis (tests, diagnostics).  a_out, has_next_out, host.
  * V (device, N*(a+1) doubles, column k = v_{k+1}) and Hbar (host, (a+1)*a
  * doubles column-major, unrotated) may be NULL. */
@@ -249,7 +261,8 @@ typedef struct {
 /* Per-timestep totals, filled on the host by kp_march_run. */
 typedef struct {
   double seed_iters, tgt_iters, tgt_iters_max, not_converged, max_rel_res;
-  double refine_flops, seed_flops, proj_flops;   /* FP64 flops of the algorithm */
+  double refine_flops, seed_flops, proj_flops;   /* flops of the algorithm: FP64, except */
+  double refine_flops32;                         /* FP32 Krylov flops (mixed precision)  */
 } kp_step_stats;
 
 /* Summed device time per kernel class (event-timed mode, launches in

@@ -35,14 +35,15 @@ kp_status cuda_error(kp_ctx* c, cudaError_t e, const char* what) {
                    cudaGetErrorString(e));
 }
 
-kp_status gmres_shape(kp_ctx* c, int nmax, int m, Shape* out) {
+kp_status gmres_shape(kp_ctx* c, int nmax, int m, Shape* out, bool mixed) {
   Shape sh;
   if (nmax <= 1024) { sh.ept = 4; sh.nt = 256; }
   else if (nmax <= 4096) { sh.ept = 8; sh.nt = 512; }
   else return set_error(c, KP_ERR_UNSUPPORTED, "N=%d: grids above 4096 unknowns are not supported by this kernel", nmax);
   const int npad = sh.ept * sh.nt;
-  const size_t fixed = gmres_fp64_smem_bytes(sh.ept, sh.nt, 0, m);
-  const size_t per = (size_t)npad * sizeof(double);
+  const size_t fixed = mixed ? gmres_mixed_smem_bytes(sh.ept, sh.nt, 0, m)
+                             : gmres_fp64_smem_bytes(sh.ept, sh.nt, 0, m);
+  const size_t per = (size_t)npad * (mixed ? sizeof(float) : sizeof(double));
   int S = c->opt.smem_vectors;
   if (S <= 0) {
     // small systems: leave room for two resident blocks per SM
@@ -154,28 +155,30 @@ kp_status run_gmres(kp_ctx* c, int nsys, const kp_op* ops, const double* const* 
   if (!(tol >= 0.0)) return kp::set_error(c, KP_ERR_ARG, "tol must be >= 0");
   if (nsys == 0) return KP_OK;
   if (!b || !x) return kp::set_error(c, KP_ERR_ARG, "b or x is NULL");
-  if (c->opt.precision != KP_PREC_FP64)
-    return kp::set_error(c, KP_ERR_UNSUPPORTED, "precision mode %d not built in this path", c->opt.precision);
+  const bool mixed = c->opt.precision == KP_PREC_MIXED;
   for (int k = 0; k < nsys; ++k) {
     if (!ops[k].mtilde || !b[k] || !x[k]) return kp::set_error(c, KP_ERR_ARG, "system %d: NULL vector", k);
   }
   kp::Shape sh;
-  st = kp::gmres_shape(c, nmax, m, &sh);
+  st = kp::gmres_shape(c, nmax, m, &sh, mixed);
   if (st != KP_OK) return st;
   const int ept = sh.ept, nt = sh.nt, S = sh.S, npad = ept * nt;
   const size_t smem = sh.smem;
   cudaError_t e;
   if (S < m + 1) {
-    const size_t need = (size_t)nsys * (m + 1 - S) * npad * sizeof(double);
-    e = grow(&c->spill, &c->spill_bytes, need);
+    const size_t need = (size_t)nsys * (m + 1 - S) * npad * (mixed ? sizeof(float) : sizeof(double));
+    e = mixed ? grow(&c->spill32, &c->spill32_bytes, need) : grow(&c->spill, &c->spill_bytes, need);
     if (e != cudaSuccess) return kp::cuda_error(c, e, "cudaMalloc(Krylov workspace)");
   }
   if (capture) {
     const int a = c->opt.max_a;
     if (nsys > c->cap_nsys) {
-      cudaFree(c->capV); cudaFree(c->capH); cudaFree(c->capMeta);
-      c->capV = nullptr; c->capH = nullptr; c->capMeta = nullptr; c->cap_nsys = 0;
-      e = cudaMalloc((void**)&c->capV, (size_t)nsys * (a + 1) * c->opt.max_n * sizeof(double));
+      cudaFree(c->capV); cudaFree(c->capV32); cudaFree(c->capH); cudaFree(c->capMeta);
+      c->capV = nullptr; c->capV32 = nullptr; c->capH = nullptr; c->capMeta = nullptr; c->cap_nsys = 0;
+      if (mixed)
+        e = cudaMalloc((void**)&c->capV32, (size_t)nsys * (a + 1) * c->opt.max_n * sizeof(float));
+      else
+        e = cudaMalloc((void**)&c->capV, (size_t)nsys * (a + 1) * c->opt.max_n * sizeof(double));
       if (e == cudaSuccess) e = cudaMalloc((void**)&c->capH, (size_t)nsys * (a + 1) * a * sizeof(double));
       if (e == cudaSuccess) e = cudaMalloc((void**)&c->capMeta, (size_t)nsys * sizeof(CapMeta));
       if (e != cudaSuccess) return kp::cuda_error(c, e, "cudaMalloc(capture)");
@@ -201,16 +204,19 @@ kp_status run_gmres(kp_ctx* c, int nsys, const kp_op* ops, const double* const* 
   p.npad = npad;
   p.b_scale = 1.0;
   p.x0_mode = kp::X0_READ;
-  p.spill = (S < m + 1) ? c->spill : nullptr;
+  p.spill = (!mixed && S < m + 1) ? c->spill : nullptr;
+  p.spill32 = (mixed && S < m + 1) ? c->spill32 : nullptr;
   p.info = info;
   if (capture) {
     p.capV = c->capV;
+    p.capV32 = c->capV32;
     p.capH = c->capH;
     p.capMeta = c->capMeta;
     p.cap_a = c->opt.max_a;
     p.cap_ld = c->opt.max_n;
   }
-  e = kp::launch_gmres_fp64(p, ept, nt, smem, c->stream);
+  e = mixed ? kp::launch_gmres_mixed(p, ept, nt, smem, c->stream)
+            : kp::launch_gmres_fp64(p, ept, nt, smem, c->stream);
   if (e != cudaSuccess) return kp::cuda_error(c, e, "GMRES launch");
   return KP_OK;
 }
@@ -254,6 +260,8 @@ kp_status kp_create(kp_ctx** out, const kp_options* opt, void* stream) {
     e = cudaEventCreateWithFlags(&c->ring[i].done, cudaEventDisableTiming);
   const size_t a = o.max_a;
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->slotV, (size_t)o.max_seeds * (a + 1) * o.max_n * sizeof(double));
+  if (e == cudaSuccess && o.precision == KP_PREC_MIXED)
+    e = cudaMalloc((void**)&c->slotV32, (size_t)o.max_seeds * (a + 1) * o.max_n * sizeof(float));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->slotMeta, (size_t)o.max_seeds * sizeof(SlotMeta));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->slotR, (size_t)o.max_seeds * (a + 1) * a * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->slotRot, (size_t)o.max_seeds * 3 * a * sizeof(double));
@@ -286,11 +294,16 @@ kp_status kp_destroy(kp_ctx* c) {
   cudaFree(c->capH);
   cudaFree(c->capMeta);
   cudaFree(c->slotV);
+  cudaFree(c->slotV32);
+  cudaFree(c->capV32);
+  cudaFree(c->spill32);
   cudaFree(c->slotMeta);
   cudaFree(c->slotR);
   cudaFree(c->slotRot);
   cudaFree(c->slotH);
   cudaFree(c->spill);
+  cudaFree(c->d_tiles);
+  cudaFree(c->d_err);
   delete c;
   return KP_OK;
 }
@@ -378,6 +391,8 @@ kp_status kp_store_basis(kp_ctx* c, int seed_id, int timestep, int sys) {
   p.ld = c->opt.max_n;
   p.count = 1;
   p.step = nullptr;
+  p.capV32 = c->capV32;
+  p.slotV32 = c->slotV32;
   cudaError_t e = kp::launch_factor(p, c->stream);
   if (e != cudaSuccess) return kp::cuda_error(c, e, "store_basis launch");
   c->slot_timestep[seed_id] = timestep;
@@ -392,8 +407,6 @@ kp_status kp_project_targets_multi(kp_ctx* c, int timestep, int nt, const int* s
   if (st != KP_OK) return st;
   if (nt == 0) return KP_OK;
   if (!seed_ids || !r || !x) return kp::set_error(c, KP_ERR_ARG, "seed_ids, r or x is NULL");
-  if (c->opt.precision != KP_PREC_FP64)
-    return kp::set_error(c, KP_ERR_UNSUPPORTED, "precision mode %d not built in this path", c->opt.precision);
   std::vector<SysDesc> h(nt);
   for (int k = 0; k < nt; ++k) {
     const int s = seed_ids[k];
@@ -420,6 +433,7 @@ kp_status kp_project_targets_multi(kp_ctx* c, int timestep, int nt, const int* s
   p.slotRot = c->slotRot;
   p.max_a = c->opt.max_a;
   p.ld = c->opt.max_n;
+  p.slotV32 = c->slotV32;
   cudaError_t e = kp::launch_project_fp64(p, ept, nt_, c->stream);
   return e == cudaSuccess ? KP_OK : kp::cuda_error(c, e, "projection launch");
 }
@@ -430,6 +444,39 @@ kp_status kp_project_targets(kp_ctx* c, int seed_id, int timestep, int nt, const
   if (nt < 0) return kp::set_error(c, KP_ERR_ARG, "nt < 0");
   std::vector<int> ids(nt, seed_id);
   return kp_project_targets_multi(c, timestep, nt, ids.data(), ops, r, x);
+}
+
+kp_status kp_project_gemm_bf16(kp_ctx* c, int nt, int nv, int K, const void* B, int ldb,
+                               const void* V, int ldv, float* C, int ldc) {
+  if (!c) return KP_ERR_ARG;
+  if (nt < 0 || nv < 1 || nv > 48 || K < 1 || ldb < K || ldv < K || ldc < nv || (ldb % 8) ||
+      (ldv % 8) || ((uintptr_t)B % 16) || ((uintptr_t)V % 16) || !C)
+    return kp::set_error(c, KP_ERR_ARG, "projection GEMM: bad sizes, strides or alignment");
+  if (nt == 0) return KP_OK;
+  const int ntiles = (nt + 127) / 128;
+  std::vector<kp::ProjTile> tiles(ntiles);
+  for (int t = 0; t < ntiles; ++t) {
+    tiles[t].row0 = 128 * t;
+    tiles[t].vrow0 = 0;
+    tiles[t].crow0 = 128 * t;
+    tiles[t].count = std::min(128, nt - 128 * t);
+    tiles[t].nv = nv;
+  }
+  cudaError_t e = grow(&c->d_tiles, &c->d_tiles_bytes, tiles.size() * sizeof(kp::ProjTile));
+  if (e == cudaSuccess && !c->d_err) {
+    e = cudaMalloc((void**)&c->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(int));
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_tiles, tiles.data(), tiles.size() * sizeof(kp::ProjTile),
+                        cudaMemcpyHostToDevice, c->stream);
+  alignas(64) CUtensorMap mb, mv;
+  if (e == cudaSuccess) e = kp::make_bf16_map(&mb, B, nt, K, ldb, 128);
+  if (e == cudaSuccess) e = kp::make_bf16_map(&mv, V, nv, K, ldv, 48);
+  if (e == cudaSuccess)
+    e = kp::launch_proj_gemm_bf16(mb, mv, c->d_tiles, ntiles, K, C, ldc, c->d_err,
+                                  std::min(ntiles, c->sms), c->stream);
+  return e == cudaSuccess ? KP_OK : kp::cuda_error(c, e, "projection GEMM");
 }
 
 kp_status kp_basis_get(kp_ctx* c, int seed_id, int timestep, int* a_out, int* has_next_out,
@@ -445,7 +492,11 @@ kp_status kp_basis_get(kp_ctx* c, int seed_id, int timestep, int* a_out, int* ha
   if (a_out) *a_out = mt.a;
   if (has_next_out) *has_next_out = mt.has_next;
   const int a = c->opt.max_a;
-  if (V) {
+  if (V && c->slotV32) {
+    e = kp::launch_widen(c->slotV32 + (size_t)seed_id * (a + 1) * c->opt.max_n, c->opt.max_n, V,
+                         mt.N, mt.N, mt.a + mt.has_next, c->stream);
+    if (e != cudaSuccess) return kp::cuda_error(c, e, "basis copy");
+  } else if (V) {
     const int nv = mt.a + mt.has_next;
     e = cudaMemcpy2DAsync(V, (size_t)mt.N * sizeof(double),
                           c->slotV + (size_t)seed_id * (a + 1) * c->opt.max_n,

@@ -44,6 +44,8 @@ struct kp_ctx {
 
   // seed-basis store
   double* slotV = nullptr;
+  float* slotV32 = nullptr;   // mixed precision: FP32 seed bases
+  float* capV32 = nullptr;    // mixed precision: FP32 capture
   kp::SlotMeta* slotMeta = nullptr;
   double* slotR = nullptr;
   double* slotRot = nullptr;
@@ -53,6 +55,11 @@ struct kp_ctx {
 
   // Krylov-vector workspace for vectors that do not fit in shared memory
   double* spill = nullptr;
+  kp::ProjTile* d_tiles = nullptr;   // tile list of the projection GEMM
+  size_t d_tiles_bytes = 0;
+  int* d_err = nullptr;               // device error flag of bounded waits
+  float* spill32 = nullptr;
+  size_t spill32_bytes = 0;
   size_t spill_bytes = 0;
 };
 
@@ -67,7 +74,8 @@ struct Shape {
 
 kp_status set_error(kp_ctx* c, kp_status s, const char* fmt, ...);
 kp_status cuda_error(kp_ctx* c, cudaError_t e, const char* what);
-// Chooses threads, elements per thread and the shared-memory Krylov window.
-kp_status gmres_shape(kp_ctx* c, int nmax, int m, Shape* out);
+// Chooses threads, elements per thread and the shared-memory Krylov window
+// (FP64 vectors, or FP32 ones for the mixed-precision solver).
+kp_status gmres_shape(kp_ctx* c, int nmax, int m, Shape* out, bool mixed = false);
 
 }  // namespace kp

@@ -1,0 +1,543 @@
+// kp_gmres_mixed.cu -- mixed-precision solver for the five-point systems of
+// Sec. 2.3: FP64 iterative refinement around an FP32 restarted GMRES.
+//
+// On GB300 an SM retires about 2 FP64 FMAs per clock against 128 FP32 FMAs,
+// so the Krylov work (stencil, Gram-Schmidt updates, normalisation) runs in
+// FP32 on FP32 vectors held in shared memory, and FP64 is kept where the
+// answer's accuracy is decided:
+//   * the true residual r = b - A x and the solution x are FP64;
+//   * inner products of FP32 vectors are summed in FP32 within a warp (its
+//     few hundred products) and in FP64 across warps; the Gram-Schmidt
+//     coefficients of both CGS passes, all norms and the residual norms are
+//     FP64 numbers;
+//   * the Hessenberg matrix, Givens rotations and least-squares solve are FP64.
+// Outer loop: r = b - A x (FP64); inner GMRES(m) on A d = r in FP32 until the
+// residual estimate drops by eta = 1e-5 (FP32 cannot resolve much more) or to
+// a tenth of the outer target; x += d.  The outer loop stops on the FP64 true
+// residual, so every returned solve meets ||b - A x|| <= tol ||b|| in FP64.
+//
+// The operator is applied from q_x = f_x/(2h) - e (m~_E - m~_W) and q_y per
+// point (two numbers instead of four coefficients, which keeps the 4096-point
+// instance within its registers):
+//   A x = cd x_p - c (x_E + x_W + x_N + x_S) + q_x (x_E - x_W) + q_y (x_N - x_S)
+// with out-of-grid neighbours zero -- algebraically the coefficients of the
+// listing after Eq. 11.
+#include "kp_internal.cuh"
+
+namespace kp {
+namespace {
+
+struct SmemM {
+  float* V;      // [S][npad] FP32 Krylov vectors
+  double* xs;    // [npad] FP64 solution
+  double* red;   // [NWARPS][kMaxV]
+  double* hb;    // [kMaxV]
+  double* Hr;    // [(m+1) * m]
+  double* g;     // [m+1]
+  double* cs;    // [m]
+  double* sn;    // [m]
+  double* y;     // [m]
+  double* rinv;  // [m]
+  double* sc;    // [8]
+  int* fl;       // [8]
+};
+
+__device__ __forceinline__ SmemM carve_m(double* base, int npad, int nwarps, int m, int S) {
+  SmemM s;
+  s.xs = base;
+  s.red = s.xs + npad;
+  s.hb = s.red + nwarps * kMaxV;
+  s.Hr = s.hb + kMaxV;
+  s.g = s.Hr + (m + 1) * m;
+  s.cs = s.g + (m + 1);
+  s.sn = s.cs + m;
+  s.y = s.sn + m;
+  s.rinv = s.y + m;
+  s.sc = s.rinv + m;
+  s.fl = reinterpret_cast<int*>(s.sc + 8);
+  s.V = reinterpret_cast<float*>(s.fl + 8);
+  (void)S;
+  return s;
+}
+
+template <int EPT, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams p) {
+  constexpr int NWARPS = NT / 32;
+  extern __shared__ __align__(16) double smem_raw[];
+  const int npad = EPT * NT;
+  const int m = p.m;
+  const int ld = m + 1;
+  SmemM sm = carve_m(smem_raw, npad, NWARPS, m, p.S);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* spill = p.spill32 ? p.spill32 + (size_t)blockIdx.x * (m + 1 - p.S) * npad : nullptr;
+  auto slot = [&](int i) -> float* {
+    return i < p.S ? sm.V + (size_t)i * npad : spill + (size_t)(i - p.S) * npad;
+  };
+  int tstep = 0;
+  if (p.step) {
+    tstep = *p.step + p.step_offset;
+    if (tstep >= *p.step_end) return;
+  }
+  const int parity_base = (tstep & 1) * p.slot_parity_stride;
+  const double bsc = p.b_scale;
+  constexpr double kEta = 1e-5;                // inner residual reduction per outer step
+
+  for (int sysi = blockIdx.x; sysi < p.nsys; sysi += gridDim.x) {
+    const SysDesc d = p.sys[sysi];
+    const int H = d.H, W = d.W, N = H * W;
+    const double hh = d.h;
+    const double g2 = p.step ? p.g2_sched[tstep] : d.g2;
+    const double cc = g2 / (2.0 * hh * hh);
+    const double ee = g2 / (8.0 * hh * hh);
+    const double cd = 1.0 / d.dt + 2.0 * g2 / (hh * hh);
+    const double i2h = 1.0 / (2.0 * hh);
+    const float ccf = (float)cc, cdf = (float)cd;
+    const bool capture = p.capV32 != nullptr;
+    const int cidx = p.factor ? parity_base + sysi : sysi;
+    float* capV = capture ? p.capV32 + (size_t)cidx * (p.cap_a + 1) * p.cap_ld : nullptr;
+    double* capH = capture ? p.capH + (size_t)cidx * (p.cap_a + 1) * p.cap_a : nullptr;
+
+    // q_x, q_y per point (FP64 and FP32 copies) and neighbour masks
+    double qx[EPT], qy[EPT];
+    float qxf[EPT], qyf[EPT];
+    unsigned msk[EPT];                          // bit0 E, bit1 W, bit2 N, bit3 S present
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int pp = tid + k * NT;
+      qx[k] = qy[k] = 0.0;
+      msk[k] = 0;
+      if (pp < N) {
+        const int i = pp / H, j = pp - i * H;
+        const double mE = (i + 1 < W) ? d.mt[pp + H] : 0.0;
+        const double mW = (i > 0) ? d.mt[pp - H] : 0.0;
+        const double mN = (j + 1 < H) ? d.mt[pp + 1] : 0.0;
+        const double mS = (j > 0) ? d.mt[pp - 1] : 0.0;
+        const double fxp = d.fx ? d.fx[pp] : 0.0;
+        const double fyp = d.fy ? d.fy[pp] : 0.0;
+        qx[k] = fxp * i2h - ee * (mE - mW);
+        qy[k] = fyp * i2h - ee * (mN - mS);
+        msk[k] = (i + 1 < W ? 1u : 0u) | (i > 0 ? 2u : 0u) | (j + 1 < H ? 4u : 0u) | (j > 0 ? 8u : 0u);
+      }
+      qxf[k] = (float)qx[k];
+      qyf[k] = (float)qy[k];
+    }
+    auto apply64 = [&](const double* v, double (&out)[EPT]) {
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int pp = tid + k * NT;
+        out[k] = 0.0;
+        if (pp < N) {
+          const double xE = (msk[k] & 1u) ? v[pp + H] : 0.0;
+          const double xW = (msk[k] & 2u) ? v[pp - H] : 0.0;
+          const double xN = (msk[k] & 4u) ? v[pp + 1] : 0.0;
+          const double xS = (msk[k] & 8u) ? v[pp - 1] : 0.0;
+          out[k] = cd * v[pp] - cc * (xE + xW + xN + xS) + qx[k] * (xE - xW) + qy[k] * (xN - xS);
+        }
+      }
+    };
+    auto apply32 = [&](const float* v, float (&out)[EPT]) {
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int pp = tid + k * NT;
+        out[k] = 0.f;
+        if (pp < N) {
+          const float xE = (msk[k] & 1u) ? v[pp + H] : 0.f;
+          const float xW = (msk[k] & 2u) ? v[pp - H] : 0.f;
+          const float xN = (msk[k] & 4u) ? v[pp + 1] : 0.f;
+          const float xS = (msk[k] & 8u) ? v[pp - 1] : 0.f;
+          out[k] = cdf * v[pp] - ccf * (xE + xW + xN + xS) + qxf[k] * (xE - xW) + qyf[k] * (xN - xS);
+        }
+      }
+    };
+    auto bval = [&](int pp) { return (pp < N) ? d.b[pp] * bsc : 0.0; };
+
+    // initial guess (FP64)
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int pp = tid + k * NT;
+      double x0 = 0.0;
+      if (pp < N) {
+        if (p.x0_mode == X0_READ) x0 = d.x[pp];
+        else if (p.x0_mode == X0_WARM) x0 = d.mt[pp];
+      }
+      sm.xs[pp] = x0;
+    }
+    unsigned long long proj_flops = 0;
+    if (p.x0_mode == X0_PROJECT) {
+      // Sec. 3, Phase 2 with the seed's FP32 basis: c = V^T b (FP64 sums),
+      // alpha = H_a^{-1} c (FP64), x0 = V alpha
+      const int sl = d.slot + parity_base;
+      const SlotMeta mt = p.slotMeta[sl];
+      if (mt.timestep == tstep && mt.N == N && mt.a > 0) {
+        const int a = mt.a;
+        const int nv = mt.lsq ? a + 1 : a;
+        const float* V = p.slotV32 + (size_t)sl * (p.max_a + 1) * p.slot_ld;
+        if (p.cproj) {
+          // c computed beforehand (tensor-core projection GEMM)
+          if (tid < nv) sm.hb[tid] = (double)p.cproj[(size_t)sysi * p.cproj_ld + tid];
+          __syncthreads();
+        } else {
+          float bv[EPT];
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) bv[k] = (float)bval(tid + k * NT);
+          block_partials_f32<NT>(nv, [&](int i) {
+            const float* vi = V + (size_t)i * p.slot_ld;
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) {
+              const int pp = tid + k * NT;
+              if (pp < N) s = fmaf(vi[pp], bv[k], s);
+            }
+            return s;
+          }, sm.red);
+          if (warp == 0)
+            for (int i = lane; i < nv; i += 32) sm.hb[i] = cross_warp<NT>(sm.red, i);
+        }
+        if (warp == 0) {
+          __syncwarp();
+          const double* rot = p.slotRot + (size_t)sl * 3 * p.max_a;
+          solve_projected_warp(sm.hb, a, mt.nrot, p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a,
+                               p.max_a + 1, rot, rot + 2 * p.max_a, lane);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          const int pp = tid + k * NT;
+          if (pp < N) {
+            float xv = 0.f;
+            for (int i = 0; i < a; ++i) xv = fmaf((float)sm.hb[i], V[(size_t)i * p.slot_ld + pp], xv);
+            sm.xs[pp] = (double)xv;
+          }
+        }
+        proj_flops = (unsigned long long)(2 * nv + 2 * a) * (unsigned long long)N;
+      }
+    }
+    __syncthreads();
+    double r[EPT];
+    auto residual = [&]() {
+      apply64(sm.xs, r);
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int pp = tid + k * NT;
+        r[k] = (pp < N) ? bval(pp) - r[k] : 0.0;
+      }
+    };
+    if (p.x0_mode == X0_ZERO) {
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) r[k] = bval(tid + k * NT);
+    } else {
+      residual();
+    }
+    block_partials<NT>(2, [&](int i) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const double bv = bval(tid + k * NT);
+        s += (i == 0) ? bv * bv : r[k] * r[k];
+      }
+      return s;
+    }, sm.red);
+    if (tid == 0) {
+      sm.sc[0] = sqrt(cross_warp<NT>(sm.red, 0));
+      sm.sc[1] = sqrt(cross_warp<NT>(sm.red, 1));
+    }
+    __syncthreads();
+    const double bnorm = sm.sc[0];
+    double beta = sm.sc[1];
+    int steps = 0, status = KP_NOT_CONVERGED, outer = 0, restarts = 0;
+    if (bnorm == 0.0) {
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) sm.xs[tid + k * NT] = 0.0;
+      beta = 0.0;
+      status = KP_OK;
+    }
+    float w[EPT];
+    while (status == KP_NOT_CONVERGED) {
+      if (beta <= p.tol * bnorm) { status = KP_OK; break; }
+      if (!isfinite(beta)) { status = KP_BREAKDOWN; break; }
+      if (steps >= p.maxit || outer >= 64) break;
+      const bool first = (outer == 0);
+      // the seed's captured cycle runs to the seed tolerance, so its basis has
+      // the dimension the FP64 method would keep (Sec. 3, Phase 1)
+      const double target = (capture && first) ? p.tol * bnorm : fmax(kEta * beta, 0.1 * p.tol * bnorm);
+      // ---- inner FP32 GMRES(m) on A d = r, from d = 0
+      {
+        const double ib = 1.0 / beta;
+        float* v0 = slot(0);
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          const int pp = tid + k * NT;
+          const float v = (float)(r[k] * ib);
+          v0[pp] = v;
+          if (capture && first && pp < N) capV[pp] = v;
+        }
+        if (tid == 0) sm.g[0] = beta;
+      }
+      int kdone = 0, brk = 0;
+      auto givens_step = [&](int j, double hn2) {
+        const double ihn = hn2 > 0.0 ? rsqrt(hn2) : 0.0;
+        const double hn = hn2 * ihn;
+        const int b = !(hn > 1e-7 * sqrt(sm.sc[2]));      // FP32 vectors: breakdown at FP32 level
+        sm.Hr[(j + 1) + j * ld] = hn;
+        if (capture && first && j < p.cap_a) {
+          for (int i = 0; i <= j + 1; ++i) capH[i + j * (p.cap_a + 1)] = sm.Hr[i + j * ld];
+        }
+        for (int i = 0; i < j; ++i) {
+          const double t1 = sm.Hr[i + j * ld], t2 = sm.Hr[(i + 1) + j * ld];
+          sm.Hr[i + j * ld] = sm.cs[i] * t1 + sm.sn[i] * t2;
+          sm.Hr[(i + 1) + j * ld] = -sm.sn[i] * t1 + sm.cs[i] * t2;
+        }
+        const double a0 = sm.Hr[j + j * ld];
+        const double rr = a0 * a0 + hn2;
+        const double ir = rsqrt(rr);
+        const double c = a0 * ir, s = hn * ir;
+        sm.cs[j] = c;
+        sm.sn[j] = s;
+        sm.Hr[j + j * ld] = rr * ir;
+        sm.rinv[j] = ir;
+        sm.Hr[(j + 1) + j * ld] = 0.0;
+        sm.g[j + 1] = -s * sm.g[j];
+        sm.g[j] = c * sm.g[j];
+        const double res = fabs(sm.g[j + 1]);
+        sm.sc[3] = ihn;
+        sm.fl[1] = b;
+        sm.fl[2] = (res <= target) || b || (steps >= p.maxit) || (j + 1 == m);
+      };
+      for (int j = 0; j < m; ++j) {
+        __syncthreads();
+        apply32(slot(j), w);
+        ++steps;
+        const int nh = j + 1;
+        auto dots = [&](int i) {
+          float s = 0.f;
+          if (i < nh) {
+            const float* vi = slot(i);
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) s = fmaf(vi[tid + k * NT], w[k], s);
+          } else {
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) s = fmaf(w[k], w[k], s);
+          }
+          return s;
+        };
+        block_partials_f32<NT>(nh + 1, dots, sm.red);
+        if (warp == 0) {
+          double sq = 0.0;
+          for (int i = lane; i <= nh; i += 32) {
+            const double s = cross_warp<NT>(sm.red, i);
+            sm.hb[i] = s;
+            if (i < nh) { sm.Hr[i + j * ld] = s; sq += s * s; }
+          }
+          sq = warp_sum(sq);
+          if (lane == 0) {
+            const double ww0 = sm.hb[nh];
+            sm.sc[2] = ww0;
+            const int pass2 = (p.reorth == 0) || (ww0 - sq < 0.5 * ww0);
+            sm.fl[0] = pass2;
+            if (!pass2) givens_step(j, ww0 - sq);
+          }
+        }
+        __syncthreads();
+        for (int i = 0; i < nh; ++i) {
+          const float hi = (float)sm.hb[i];
+          const float* vi = slot(i);
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) w[k] = fmaf(-hi, vi[tid + k * NT], w[k]);
+        }
+        if (sm.fl[0]) {
+          block_partials_f32<NT>(nh + 1, dots, sm.red);
+          if (warp == 0) {
+            double sq = 0.0;
+            for (int i = lane; i <= nh; i += 32) {
+              const double s = cross_warp<NT>(sm.red, i);
+              sm.hb[i] = s;
+              if (i < nh) { sm.Hr[i + j * ld] += s; sq += s * s; }
+            }
+            sq = warp_sum(sq);
+            if (lane == 0) {
+              const double ww1 = sm.hb[nh];
+              const int exact = sq > 0.25 * ww1;
+              sm.fl[3] = exact;
+              if (!exact) givens_step(j, ww1 - sq);
+            }
+          }
+          __syncthreads();
+          for (int i = 0; i < nh; ++i) {
+            const float hi = (float)sm.hb[i];
+            const float* vi = slot(i);
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) w[k] = fmaf(-hi, vi[tid + k * NT], w[k]);
+          }
+          if (sm.fl[3]) {
+            block_partials_f32<NT>(1, [&](int) {
+              float s = 0.f;
+#pragma unroll
+              for (int k = 0; k < EPT; ++k) s = fmaf(w[k], w[k], s);
+              return s;
+            }, sm.red);
+            if (tid == 0) givens_step(j, cross_warp<NT>(sm.red, 0));
+            __syncthreads();
+          }
+        }
+        brk = sm.fl[1];
+        kdone = j + 1;
+        if (!brk) {
+          const float ih = (float)sm.sc[3];
+          float* vn = slot(j + 1);
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) {
+            const int pp = tid + k * NT;
+            vn[pp] = w[k] * ih;
+            if (capture && first && j + 1 <= p.cap_a && pp < N)
+              capV[(size_t)(j + 1) * p.cap_ld + pp] = w[k] * ih;
+          }
+        }
+        if (sm.fl[2]) break;
+      }
+      if (warp == 0) {
+        double g0 = (lane < kdone) ? sm.g[lane] : 0.0;
+        double g1 = (lane + 32 < kdone) ? sm.g[lane + 32] : 0.0;
+        for (int i = kdone - 1; i >= 0; --i) {
+          const double gi = __shfl_sync(kFull, i < 32 ? g0 : g1, i & 31);
+          const double yi = gi * sm.rinv[i];
+          if (lane == 0) sm.y[i] = yi;
+          if (lane < i) g0 = fma(-sm.Hr[lane + i * ld], yi, g0);
+          if (lane + 32 < i) g1 = fma(-sm.Hr[(lane + 32) + i * ld], yi, g1);
+        }
+      }
+      if (tid == 0 && capture && first) {
+        const int a = kdone < p.cap_a ? kdone : p.cap_a;
+        const int hn = (a < kdone) || !brk;
+        if (p.factor) {
+          SlotMeta mt;
+          const int sl = cidx;
+          double* rot = p.slotRot + (size_t)sl * 3 * p.max_a;
+          factor_hessenberg(capH, p.cap_a + 1, a, hn,
+                            p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a, rot,
+                            rot + 2 * p.max_a, &mt.lsq, &mt.nrot);
+          mt.a = a;
+          mt.has_next = hn;
+          mt.timestep = tstep;
+          mt.N = N;
+          mt.pad_[0] = mt.pad_[1] = 0;
+          p.slotMeta[sl] = mt;
+        } else {
+          p.capMeta[sysi].a = a;
+          p.capMeta[sysi].has_next = hn;
+          p.capMeta[sysi].N = N;
+          p.capMeta[sysi].valid = 1;
+        }
+      }
+      __syncthreads();
+      // d = V y in FP32, x += d in FP64
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int pp = tid + k * NT;
+        float dv = 0.f;
+        for (int i = 0; i < kdone; ++i) dv = fmaf((float)sm.y[i], slot(i)[pp], dv);
+        sm.xs[pp] += (double)dv;
+      }
+      __syncthreads();
+      residual();                                 // FP64 true residual
+      block_partials<NT>(1, [&](int) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) s += r[k] * r[k];
+        return s;
+      }, sm.red);
+      if (tid == 0) sm.sc[1] = sqrt(cross_warp<NT>(sm.red, 0));
+      __syncthreads();
+      beta = sm.sc[1];
+      ++outer;
+      ++restarts;
+    }
+    if (capture && outer == 0 && tid == 0) {
+      if (p.factor) {
+        SlotMeta mt;
+        mt.a = 0; mt.has_next = 0; mt.timestep = tstep; mt.N = N; mt.lsq = 0; mt.nrot = 0;
+        mt.pad_[0] = mt.pad_[1] = 0;
+        p.slotMeta[cidx] = mt;
+      } else {
+        p.capMeta[sysi].a = 0;
+        p.capMeta[sysi].has_next = 0;
+        p.capMeta[sysi].N = N;
+        p.capMeta[sysi].valid = 1;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int pp = tid + k * NT;
+      if (pp < N) {
+        d.x[pp] = sm.xs[pp];
+        if (p.bnext) p.bnext[(size_t)sysi * p.bnext_ld + pp] = __float2bfloat16_rn((float)(sm.xs[pp] * bsc));
+      }
+    }
+    if (tid == 0) {
+      const double rel = bnorm > 0.0 ? beta / bnorm : 0.0;
+      if (p.info) {
+        kp_info inf;
+        inf.iters = steps;
+        inf.status = status;
+        inf.rel_res = rel;
+        p.info[sysi] = inf;
+      }
+      if (p.acc) {
+        StepAcc* a = p.acc + tstep;
+        // FP64 flops of the refinement (residuals, x update); FP32 Krylov work
+        // is counted separately
+        const unsigned long long fl = (unsigned long long)(14 + restarts * 13) * (unsigned long long)N;
+        const unsigned long long fl32 = (gmres_flops(steps, m) - 14ull) * (unsigned long long)N;
+        if (p.acc_kind == 0) {
+          atomicAdd(&a->seed_iters, (unsigned long long)steps);
+          atomicAdd(&a->seed_flops, fl + fl32);
+        } else {
+          atomicAdd(&a->tgt_iters, (unsigned long long)steps);
+          atomicAdd(&a->tgt_flops, fl);
+          atomicAdd(&a->tgt_flops32, fl32);
+          atomicMax(&a->tgt_max_iters, (unsigned int)steps);
+          atomicMax(&a->max_res_bits, (unsigned long long)__double_as_longlong(rel));
+          if (proj_flops) atomicAdd(&a->proj_flops, proj_flops);
+        }
+        if (status != KP_OK) atomicAdd(&a->not_converged, 1u);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename K>
+cudaError_t allow_max_smem_m(K k, size_t smem) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if (smem > (size_t)optin) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
+template <int EPT, int NT, int MINB>
+cudaError_t launch_m(const GmresParams& p, size_t smem, cudaStream_t st) {
+  auto k = gmres_mixed_kernel<EPT, NT, MINB>;
+  cudaError_t e = allow_max_smem_m(k, smem);
+  if (e != cudaSuccess) return e;
+  k<<<p.nsys, NT, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t gmres_mixed_smem_bytes(int ept, int nt, int S, int m) {
+  const int npad = ept * nt;
+  const size_t doubles = (size_t)npad + (nt / 32) * kMaxV + kMaxV + (size_t)(m + 1) * m +
+                         (m + 1) + 4 * m + 8;
+  return doubles * sizeof(double) + 8 * sizeof(int) + (size_t)S * npad * sizeof(float);
+}
+
+cudaError_t launch_gmres_mixed(const GmresParams& p, int ept, int nt, size_t smem,
+                               cudaStream_t st) {
+  if (ept == 4 && nt == 256) return launch_m<4, 256, 2>(p, smem, st);
+  if (ept == 8 && nt == 512) return launch_m<8, 512, 1>(p, smem, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace kp

@@ -1,6 +1,8 @@
 // kp_internal.cuh -- device-side types and helpers shared by the solver kernels.
 #pragma once
 
+#include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -41,6 +43,7 @@ struct StepAcc {
   unsigned long long seed_flops;     // FP64 flops of the algorithm (see gmres_flops)
   unsigned long long tgt_flops;
   unsigned long long proj_flops;
+  unsigned long long tgt_flops32;    // FP32 Krylov flops of mixed-precision target solves
   unsigned long long max_res_bits;   // max relative residual (non-negative double bits)
   unsigned int tgt_max_iters;
   unsigned int not_converged;
@@ -92,6 +95,14 @@ struct GmresParams {
   int factor;               // capture into slot (sys + parity offset) and factor H_a
   StepAcc* acc;             // per-timestep totals (indexed like g2_sched) or null
   int acc_kind;             // 0 seeds, 1 targets
+  // mixed precision (FP32 Krylov vectors)
+  float* spill32;           // [gridDim.x][m + 1 - S][npad] workspace
+  float* capV32;            // capture target for FP32 bases (slot layout when factor)
+  const float* slotV32;     // [max_seeds][max_a + 1][slot_ld] FP32 seed bases
+  const float* cproj;       // if set: c = V^T b per target, [nsys][cproj_ld] (tensor-core GEMM)
+  int cproj_ld;
+  __nv_bfloat16* bnext;     // if set: write BF16 (x * b_scale) per system, [nsys][bnext_ld]
+  int bnext_ld;
 };
 
 enum { X0_READ = 0, X0_ZERO = 1, X0_WARM = 2, X0_PROJECT = 3 };
@@ -107,6 +118,7 @@ struct ProjParams {
   int max_a;
   int ld;
   const int* step;         // if non-null, the timestep is *step
+  const float* slotV32;    // mixed precision: FP32 bases instead of slotV
 };
 
 struct FactorParams {
@@ -127,6 +139,8 @@ struct FactorParams {
   int ld;
   int count;               // number of (sys, slot) pairs, one block each
   const int* step;         // if non-null, the timestep is *step
+  const float* capV32;     // mixed precision: FP32 capture and slot bases (else null)
+  float* slotV32;
 };
 
 // ---- block reductions shared by the kernels ----
@@ -215,6 +229,48 @@ __device__ __forceinline__ void block_partials(int nv, F&& partial, double* red)
   } else if (i0 < nv) {
     const double s = warp_sum(partial(i0));
     if (lane == 0) red[warp * kMaxV + i0] = s;
+  }
+  __syncthreads();
+}
+
+// FP32 variants for the mixed-precision solver: FP32 partials and warp
+// reduce-scatter, FP64 cross-warp sum (cross_warp) afterwards.
+__device__ __forceinline__ float warp_reduce8f(float (&a)[8], int lane) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const bool up = lane & 16;
+    const float send = up ? a[k] : a[k + 4];
+    const float keep = up ? a[k + 4] : a[k];
+    a[k] = keep + __shfl_xor_sync(kFull, send, 16);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const bool up = lane & 8;
+    const float send = up ? a[k] : a[k + 2];
+    const float keep = up ? a[k + 2] : a[k];
+    a[k] = keep + __shfl_xor_sync(kFull, send, 8);
+  }
+  {
+    const bool up = lane & 4;
+    const float send = up ? a[0] : a[1];
+    const float keep = up ? a[1] : a[0];
+    a[0] = keep + __shfl_xor_sync(kFull, send, 4);
+  }
+  a[0] += __shfl_xor_sync(kFull, a[0], 2);
+  a[0] += __shfl_xor_sync(kFull, a[0], 1);
+  return a[0];
+}
+
+template <int NT, typename F>
+__device__ __forceinline__ void block_partials_f32(int nv, F&& partial, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i0 = 0; i0 < nv; i0 += 8) {
+    float a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = (i0 + k < nv) ? partial(i0 + k) : 0.f;
+    const float s = warp_reduce8f(a, lane);
+    const int v = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    if ((lane & 3) == 0 && i0 + v < nv) red[warp * kMaxV + i0 + v] = (double)s;
   }
   __syncthreads();
 }
@@ -317,10 +373,20 @@ __device__ __forceinline__ void solve_projected_warp(double* c, int a, int nrot,
   __syncwarp();
 }
 
+// One tile of the tensor-core projection GEMM: targets row0..row0+127 of the
+// BF16 right-hand-side matrix against basis rows vrow0..vrow0+47; C rows
+// crow0 + (0..count), columns 0..nv.
+struct ProjTile {
+  int row0, vrow0, crow0, count, nv;
+};
+
 // Launchers (defined in the .cu files; return a cudaError_t of the launch).
 cudaError_t launch_gmres_fp64(const GmresParams& p, int ept, int nt, size_t smem,
                               cudaStream_t st);
 size_t gmres_fp64_smem_bytes(int ept, int nt, int S, int m);
+size_t gmres_mixed_smem_bytes(int ept, int nt, int S, int m);
+cudaError_t launch_gmres_mixed(const GmresParams& p, int ept, int nt, size_t smem,
+                               cudaStream_t st);
 // The N <= 1024 instantiation (4 points x 256 threads) on an explicit grid;
 // the kernel strides over systems, block b using Krylov workspace slice b.
 cudaError_t launch_gmres_fp64_1k_grid(const GmresParams& p, size_t smem, int grid,
@@ -329,5 +395,14 @@ cudaError_t launch_apply(const SysDesc* sys, int nsys, int mode, cudaStream_t st
 cudaError_t launch_factor(const FactorParams& p, cudaStream_t st);
 cudaError_t launch_project_fp64(const ProjParams& p, int ept, int nt, cudaStream_t st);
 cudaError_t launch_advance(int* step, cudaStream_t st);
+size_t proj_gemm_smem_bytes();
+// Tensor map of a row-major BF16 matrix (rows x cols, row stride ld elements)
+// read in boxes of box_rows x 64 with 128-byte swizzle.
+cudaError_t make_bf16_map(void* map, const void* base, int rows, int cols, int ld, int box_rows);
+cudaError_t launch_proj_gemm_bf16(const CUtensorMap& mapB, const CUtensorMap& mapV,
+                                  const ProjTile* tiles, int ntiles, int K, float* C, int ldc,
+                                  int* err, int grid, cudaStream_t st);
+cudaError_t launch_widen(const float* src, size_t src_ld, double* dst, size_t dst_ld, int n, int rows,
+                         cudaStream_t st);
 
 }  // namespace kp

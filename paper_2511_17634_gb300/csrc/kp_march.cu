@@ -50,6 +50,8 @@ struct kp_march_plan {
   int* step = nullptr;                      // [0] current target timestep, [1] end of run
   kp::StepAcc* acc = nullptr;               // [T]
   double* spill = nullptr;
+  float* spill32 = nullptr;
+  bool mixed = false;
   SysDesc* desc[2] = {nullptr, nullptr};     // per parity p: seeds (step n+1), targets (step n)
   kp::Shape shS, shT;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -74,7 +76,11 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset)
   size_t spS = 0;
   if (P->ns && P->shS.S < P->opt.m_seed + 1)
     spS = (size_t)P->ns * (P->opt.m_seed + 1 - P->shS.S) * P->shS.ept * P->shS.nt;
-  g.spill = (sh.S < g.m + 1) ? P->spill + (seeds ? 0 : spS) : nullptr;
+  if (P->mixed)
+    g.spill32 = (sh.S < g.m + 1) ? P->spill32 + (seeds ? 0 : spS) : nullptr;
+  else
+    g.spill = (sh.S < g.m + 1) ? P->spill + (seeds ? 0 : spS) : nullptr;
+  g.slotV32 = c->slotV32;
   g.info = nullptr;
   g.step = P->step;
   g.g2_sched = P->g2;
@@ -91,7 +97,8 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset)
   g.acc = P->acc;
   if (seeds) {
     g.x0_mode = kp::X0_ZERO;
-    g.capV = c->slotV;                       // capture straight into the seed slots
+    if (P->mixed) g.capV32 = c->slotV32;     // capture straight into the seed slots
+    else g.capV = c->slotV;
     g.capH = c->slotH;
     g.cap_a = c->opt.max_a;
     g.cap_ld = c->opt.max_n;
@@ -103,6 +110,12 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset)
     g.acc_kind = 1;
   }
   return g;
+}
+
+cudaError_t launch_solver(kp_march_plan* P, const kp::GmresParams& g, const kp::Shape& sh,
+                          cudaStream_t st) {
+  return P->mixed ? kp::launch_gmres_mixed(g, sh.ept, sh.nt, sh.smem, st)
+                  : kp::launch_gmres_fp64(g, sh.ept, sh.nt, sh.smem, st);
 }
 
 // Target step n and seed step n+1 for parity p = n & 1.  With ev (timing
@@ -120,14 +133,14 @@ kp_status enqueue_step(kp_march_plan* P, int par, cudaEvent_t* ev, int* launches
   if (P->ns > 0 && e == cudaSuccess) {
     if (ev) e = cudaEventRecord(ev[0], sst);
     kp::GmresParams g = solver_params(P, true, par, 1);
-    if (e == cudaSuccess) e = kp::launch_gmres_fp64(g, P->shS.ept, P->shS.nt, P->shS.smem, sst);
+    if (e == cudaSuccess) e = launch_solver(P, g, P->shS, sst);
     ++nl;
     if (ev && e == cudaSuccess) e = cudaEventRecord(ev[1], sst);
   }
   if (P->nt > 0 && e == cudaSuccess) {
     if (ev) e = cudaEventRecord(ev[2], P->st);
     kp::GmresParams g = solver_params(P, false, par, 0);
-    if (e == cudaSuccess) e = kp::launch_gmres_fp64(g, P->shT.ept, P->shT.nt, P->shT.smem, P->st);
+    if (e == cudaSuccess) e = launch_solver(P, g, P->shT, P->st);
     ++nl;
     if (ev && e == cudaSuccess) e = cudaEventRecord(ev[3], P->st);
   }
@@ -158,6 +171,7 @@ kp_status kp_march_destroy(kp_march_plan* P) {
   cudaFree(P->step);
   cudaFree(P->acc);
   cudaFree(P->spill);
+  cudaFree(P->spill32);
   if (P->fork) cudaEventDestroy(P->fork);
   if (P->join) cudaEventDestroy(P->join);
   if (P->st2) cudaStreamDestroy(P->st2);
@@ -171,8 +185,6 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
   if (!c) return KP_ERR_ARG;
   if (!out || !opt || ngroups < 1 || !groups) return kp::set_error(c, KP_ERR_ARG, "bad march arguments");
   *out = nullptr;
-  if (c->opt.precision != KP_PREC_FP64)
-    return kp::set_error(c, KP_ERR_UNSUPPORTED, "precision mode %d not built in the march", c->opt.precision);
   const kp_march_opts& o = *opt;
   if (o.T < 1 || !o.g2 || o.mode < 0 || o.mode > 2 || o.m_seed < 1 || o.m_seed > kp::kMaxM ||
       o.m < 1 || o.m > kp::kMaxM || o.maxit < 0 || !(o.tol >= 0) || !(o.tol_seed >= 0))
@@ -210,9 +222,10 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
     return kp::set_error(c, KP_ERR_ARG, "%d seeds need 2x%d basis slots (one set per timestep parity); max_seeds=%d",
                          P->ns, P->ns, c->opt.max_seeds);
   }
+  P->mixed = c->opt.precision == KP_PREC_MIXED;
   kp_status s = KP_OK;
-  if (P->ns) s = kp::gmres_shape(c, nmaxS, o.m_seed, &P->shS);
-  if (s == KP_OK && P->nt) s = kp::gmres_shape(c, nmaxT, o.m, &P->shT);
+  if (P->ns) s = kp::gmres_shape(c, nmaxS, o.m_seed, &P->shS, P->mixed);
+  if (s == KP_OK && P->nt) s = kp::gmres_shape(c, nmaxT, o.m, &P->shT, P->mixed);
   if (s != KP_OK) { kp_march_destroy(P); return s; }
   cudaError_t e = cudaStreamCreateWithFlags(&P->st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->st2, cudaStreamNonBlocking);
@@ -230,7 +243,10 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
   size_t spS = 0, spT = 0;
   if (ns && P->shS.S < o.m_seed + 1) spS = (size_t)ns * (o.m_seed + 1 - P->shS.S) * P->shS.ept * P->shS.nt;
   if (nt && P->shT.S < o.m + 1) spT = (size_t)nt * (o.m + 1 - P->shT.S) * P->shT.ept * P->shT.nt;
-  if (e == cudaSuccess && spS + spT) e = dmalloc(&P->spill, spS + spT);
+  if (e == cudaSuccess && spS + spT) {
+    if (P->mixed) e = dmalloc(&P->spill32, spS + spT);
+    else e = dmalloc(&P->spill, spS + spT);
+  }
   for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = dmalloc(&P->desc[k], (size_t)ns + nt);
   if (e != cudaSuccess) {
     kp_status r = kp::cuda_error(c, e, "march allocation");
@@ -336,7 +352,7 @@ kp_status kp_march_run(kp_march_plan* P, int n0, int steps, kp_step_stats* stats
   if (e == cudaSuccess && P->ns) {
     kp::GmresParams g = solver_params(P, true, 1 - q0, 0);
     if (timing) e = cudaEventRecord(ev[(size_t)steps * 4], P->st);
-    if (e == cudaSuccess) e = kp::launch_gmres_fp64(g, P->shS.ept, P->shS.nt, P->shS.smem, P->st);
+    if (e == cudaSuccess) e = launch_solver(P, g, P->shS, P->st);
     if (timing && e == cudaSuccess) e = cudaEventRecord(ev[(size_t)steps * 4 + 1], P->st);
     ++launches;
   }
@@ -380,6 +396,7 @@ kp_status kp_march_run(kp_march_plan* P, int n0, int steps, kp_step_stats* stats
       stats[k].refine_flops = (double)a.tgt_flops;
       stats[k].seed_flops = (double)a.seed_flops;
       stats[k].proj_flops = (double)a.proj_flops;
+      stats[k].refine_flops32 = (double)a.tgt_flops32;
     }
   }
   if (e == cudaSuccess && timing) {

@@ -23,9 +23,18 @@ __global__ void factor_kernel(FactorParams p) {
   const double* cv = p.capV + (size_t)p.sys * (p.cap_a + 1) * p.cap_ld;
   double* sv = p.slotV + (size_t)p.seed_id * (p.max_a + 1) * p.ld;
   const int nvec = a + hn;
-  for (int idx = threadIdx.x; idx < nvec * N; idx += blockDim.x) {
-    const int k = idx / N, q = idx - k * N;
-    sv[(size_t)k * p.ld + q] = cv[(size_t)k * p.cap_ld + q];
+  if (p.capV32) {
+    const float* cv32 = p.capV32 + (size_t)p.sys * (p.cap_a + 1) * p.cap_ld;
+    float* sv32 = p.slotV32 + (size_t)p.seed_id * (p.max_a + 1) * p.ld;
+    for (int idx = threadIdx.x; idx < nvec * N; idx += blockDim.x) {
+      const int k = idx / N, q = idx - k * N;
+      sv32[(size_t)k * p.ld + q] = cv32[(size_t)k * p.cap_ld + q];
+    }
+  } else {
+    for (int idx = threadIdx.x; idx < nvec * N; idx += blockDim.x) {
+      const int k = idx / N, q = idx - k * N;
+      sv[(size_t)k * p.ld + q] = cv[(size_t)k * p.cap_ld + q];
+    }
   }
   if (threadIdx.x != 0) return;
   const int cld = p.cap_a + 1;
@@ -71,13 +80,16 @@ __global__ void __launch_bounds__(NT) project_fp64_kernel(const ProjParams p) {
       r[k] = (pp < N) ? d.b[pp] : 0.0;
     }
     // c = V^T r (c_i over the first nv basis vectors)
+    const float* V32 = p.slotV32 ? p.slotV32 + (size_t)d.slot * (p.max_a + 1) * p.ld : nullptr;
+    auto vget = [&](int i, int pp) -> double {
+      return V32 ? (double)V32[(size_t)i * p.ld + pp] : V[(size_t)i * p.ld + pp];
+    };
     block_partials<NT>(nv, [&](int i) {
-      const double* vi = V + (size_t)i * p.ld;
       double s = 0.0;
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
         const int pp = tid + k * NT;
-        if (pp < N) s += vi[pp] * r[k];
+        if (pp < N) s += vget(i, pp) * r[k];
       }
       return s;
     }, red);
@@ -95,7 +107,7 @@ __global__ void __launch_bounds__(NT) project_fp64_kernel(const ProjParams p) {
       const int pp = tid + k * NT;
       if (pp < N) {
         double xv = d.x[pp];
-        for (int i = 0; i < a; ++i) xv = fma(cvec[i], V[(size_t)i * p.ld + pp], xv);
+        for (int i = 0; i < a; ++i) xv = fma(cvec[i], vget(i, pp), xv);
         d.x[pp] = xv;
       }
     }
@@ -104,6 +116,18 @@ __global__ void __launch_bounds__(NT) project_fp64_kernel(const ProjParams p) {
 }
 
 }  // namespace
+
+__global__ void widen_kernel(const float* src, size_t src_ld, double* dst, size_t dst_ld, int n) {
+  const int r = blockIdx.x;
+  for (int q = threadIdx.x; q < n; q += blockDim.x) dst[(size_t)r * dst_ld + q] = (double)src[(size_t)r * src_ld + q];
+}
+
+cudaError_t launch_widen(const float* src, size_t src_ld, double* dst, size_t dst_ld, int n, int rows,
+                         cudaStream_t st) {
+  if (rows <= 0) return cudaSuccess;
+  widen_kernel<<<rows, 256, 0, st>>>(src, src_ld, dst, dst_ld, n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_factor(const FactorParams& p, cudaStream_t st) {
   factor_kernel<<<p.count > 0 ? p.count : 1, 256, 0, st>>>(p);

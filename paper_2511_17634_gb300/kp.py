@@ -65,9 +65,10 @@ def lib():
         L.kp_project_targets.argtypes = [vp, i, i, i, vp, vp, vp]
         L.kp_project_targets_multi.argtypes = [vp, i, i, vp, vp, vp, vp]
         L.kp_basis_get.argtypes = [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i), vp, vp]
+        L.kp_project_gemm_bf16.argtypes = [vp, i, i, i, vp, i, vp, i, vp, i]
         for f in ("kp_create", "kp_destroy", "kp_set_stream", "kp_apply", "kp_rhs", "kp_seed_solve",
                   "kp_refine", "kp_store_basis", "kp_project_targets", "kp_project_targets_multi",
-                  "kp_basis_get"):
+                  "kp_basis_get", "kp_project_gemm_bf16"):
             getattr(L, f).restype = i
         _lib = L
     return _lib
@@ -210,6 +211,16 @@ class Context:
                                                    self._arr(ops), self._arr(_ptrs(r)),
                                                    self._arr(_ptrs(x))))
 
+    def project_gemm_bf16(self, B, V, C, K=None):
+        """C[t][i] = sum_k B[t][k] V[i][k] on the tensor cores (BF16 in, FP32 out)."""
+        import torch
+        assert B.dtype == torch.bfloat16 and V.dtype == torch.bfloat16 and C.dtype == torch.float32
+        K = B.shape[1] if K is None else K
+        self._check(lib().kp_project_gemm_bf16(self._h, B.shape[0], V.shape[0], K,
+                                               ctypes.c_void_p(B.data_ptr()), B.stride(0),
+                                               ctypes.c_void_p(V.data_ptr()), V.stride(0),
+                                               ctypes.c_void_p(C.data_ptr()), C.stride(0)))
+
     def basis_get(self, seed_id, timestep, N):
         """(a, has_next, V (a+has_next, N) tensor, Hbar (a+1, a) numpy)."""
         import torch
@@ -245,7 +256,7 @@ class _MarchOpts(ctypes.Structure):
 class StepStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("seed_iters", "tgt_iters", "tgt_iters_max",
                                                 "not_converged", "max_rel_res", "refine_flops",
-                                                "seed_flops", "proj_flops")]
+                                                "seed_flops", "proj_flops", "refine_flops32")]
 
 
 class MarchTiming(ctypes.Structure):
