@@ -262,6 +262,12 @@ kp_status kp_create(kp_ctx** out, const kp_options* opt, void* stream) {
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->slotV, (size_t)o.max_seeds * (a + 1) * o.max_n * sizeof(double));
   if (e == cudaSuccess && o.precision == KP_PREC_MIXED)
     e = cudaMalloc((void**)&c->slotV32, (size_t)o.max_seeds * (a + 1) * o.max_n * sizeof(float));
+  if (e == cudaSuccess && o.precision == KP_PREC_MIXED) {
+    c->vb_ld = (o.max_n + 7) / 8 * 8;
+    e = cudaMalloc((void**)&c->slotVb, (size_t)o.max_seeds * kp::kVbRows * c->vb_ld * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess)   // rows past a basis are read by the GEMM: keep them finite
+      e = cudaMemset(c->slotVb, 0, (size_t)o.max_seeds * kp::kVbRows * c->vb_ld * sizeof(__nv_bfloat16));
+  }
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->slotMeta, (size_t)o.max_seeds * sizeof(SlotMeta));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->slotR, (size_t)o.max_seeds * (a + 1) * a * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc((void**)&c->slotRot, (size_t)o.max_seeds * 3 * a * sizeof(double));
@@ -295,6 +301,7 @@ kp_status kp_destroy(kp_ctx* c) {
   cudaFree(c->capMeta);
   cudaFree(c->slotV);
   cudaFree(c->slotV32);
+  cudaFree(c->slotVb);
   cudaFree(c->capV32);
   cudaFree(c->spill32);
   cudaFree(c->slotMeta);

@@ -45,6 +45,8 @@ struct kp_ctx {
   // seed-basis store
   double* slotV = nullptr;
   float* slotV32 = nullptr;   // mixed precision: FP32 seed bases
+  __nv_bfloat16* slotVb = nullptr;   // mixed precision: BF16 seed bases [slot][48][vb_ld]
+  int vb_ld = 0;
   float* capV32 = nullptr;    // mixed precision: FP32 capture
   kp::SlotMeta* slotMeta = nullptr;
   double* slotR = nullptr;

@@ -269,7 +269,10 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
           const int pp = tid + k * NT;
           const float v = (float)(r[k] * ib);
           v0[pp] = v;
-          if (capture && first && pp < N) capV[pp] = v;
+          if (capture && first && pp < N) {
+            capV[pp] = v;
+            if (p.capVb) p.capVb[(size_t)cidx * kVbRows * p.capVb_ld + pp] = __float2bfloat16_rn(v);
+          }
         }
         if (tid == 0) sm.g[0] = beta;
       }
@@ -388,8 +391,11 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
           for (int k = 0; k < EPT; ++k) {
             const int pp = tid + k * NT;
             vn[pp] = w[k] * ih;
-            if (capture && first && j + 1 <= p.cap_a && pp < N)
+            if (capture && first && j + 1 <= p.cap_a && pp < N) {
               capV[(size_t)(j + 1) * p.cap_ld + pp] = w[k] * ih;
+              if (p.capVb && j + 1 < kVbRows)
+                p.capVb[((size_t)cidx * kVbRows + j + 1) * p.capVb_ld + pp] = __float2bfloat16_rn(w[k] * ih);
+            }
           }
         }
         if (sm.fl[2]) break;

@@ -103,7 +103,11 @@ struct GmresParams {
   int cproj_ld;
   __nv_bfloat16* bnext;     // if set: write BF16 (x * b_scale) per system, [nsys][bnext_ld]
   int bnext_ld;
+  __nv_bfloat16* capVb;     // if set: BF16 copy of the captured basis, [slot][kVbRows][capVb_ld]
+  int capVb_ld;
 };
+
+constexpr int kVbRows = 48;   // rows per seed slot of the BF16 basis (tensor-core N tile)
 
 enum { X0_READ = 0, X0_ZERO = 1, X0_WARM = 2, X0_PROJECT = 3 };
 
@@ -395,6 +399,12 @@ cudaError_t launch_apply(const SysDesc* sys, int nsys, int mode, cudaStream_t st
 cudaError_t launch_factor(const FactorParams& p, cudaStream_t st);
 cudaError_t launch_project_fp64(const ProjParams& p, int ept, int nt, cudaStream_t st);
 cudaError_t launch_advance(int* step, cudaStream_t st);
+// dst[q] = src[perm[q]] (gather) or dst[perm[q]] = src[q] (scatter), planes of n doubles
+cudaError_t launch_permute(double* dst, const double* src, const int* perm, int count, int n,
+                           int gather, cudaStream_t st);
+// b16[q] = bf16(src[q] * scale), planes of n doubles into rows of ld BF16
+cudaError_t launch_to_bf16(__nv_bfloat16* dst, int ld, const double* src, int count, int n,
+                           double scale, cudaStream_t st);
 size_t proj_gemm_smem_bytes();
 // Tensor map of a row-major BF16 matrix (rows x cols, row stride ld elements)
 // read in boxes of box_rows x 64 with 128-byte swizzle.

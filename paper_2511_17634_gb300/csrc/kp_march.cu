@@ -52,6 +52,18 @@ struct kp_march_plan {
   double* spill = nullptr;
   float* spill32 = nullptr;
   bool mixed = false;
+  // targets are stored sorted by seed so that a seed's targets form whole
+  // tensor-core tiles: internal plane q of group g holds user plane perm[q]
+  int* perm = nullptr;                       // device, group-local indices
+  std::vector<int> tgt_base;                 // first internal target of each group
+  // tensor-core projection (mixed precision)
+  __nv_bfloat16* Bb = nullptr;               // [nt][vb_ld] BF16 right-hand sides
+  float* Cp = nullptr;                       // [nt][kVbRows] projections c = V^T b
+  kp::ProjTile* tiles[2] = {nullptr, nullptr};
+  std::vector<int> tile_off, tile_cnt;       // per group, within each parity's list
+  std::vector<CUtensorMap> mapB, mapV;       // per group
+  int* err = nullptr;
+  int gemm_grid = 0;
   SysDesc* desc[2] = {nullptr, nullptr};     // per parity p: seeds (step n+1), targets (step n)
   kp::Shape shS, shT;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -97,8 +109,13 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset)
   g.acc = P->acc;
   if (seeds) {
     g.x0_mode = kp::X0_ZERO;
-    if (P->mixed) g.capV32 = c->slotV32;     // capture straight into the seed slots
-    else g.capV = c->slotV;
+    if (P->mixed) {
+      g.capV32 = c->slotV32;                 // capture straight into the seed slots
+      g.capVb = c->slotVb;                   // and its BF16 copy for the tensor cores
+      g.capVb_ld = c->vb_ld;
+    } else {
+      g.capV = c->slotV;
+    }
     g.capH = c->slotH;
     g.cap_a = c->opt.max_a;
     g.cap_ld = c->opt.max_n;
@@ -108,6 +125,12 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset)
     g.x0_mode = P->opt.mode == KP_MARCH_PROJECTED ? (P->ns ? kp::X0_PROJECT : kp::X0_ZERO)
               : P->opt.mode == KP_MARCH_WARM ? kp::X0_WARM : kp::X0_ZERO;
     g.acc_kind = 1;
+    if (P->Cp) {
+      g.cproj = P->Cp;                       // c = V^T b from the tensor-core GEMM
+      g.cproj_ld = kp::kVbRows;
+      g.bnext = P->Bb;                       // BF16 b of the next timestep
+      g.bnext_ld = c->vb_ld;
+    }
   }
   return g;
 }
@@ -139,6 +162,16 @@ kp_status enqueue_step(kp_march_plan* P, int par, cudaEvent_t* ev, int* launches
   }
   if (P->nt > 0 && e == cudaSuccess) {
     if (ev) e = cudaEventRecord(ev[2], P->st);
+    if (P->Cp) {
+      for (size_t gi = 0; gi < P->groups.size() && e == cudaSuccess; ++gi) {
+        if (!P->tile_cnt[gi]) continue;
+        e = kp::launch_proj_gemm_bf16(P->mapB[gi], P->mapV[gi], P->tiles[par] + P->tile_off[gi],
+                                      P->tile_cnt[gi], P->groups[gi].H * P->groups[gi].W, P->Cp,
+                                      kp::kVbRows, P->err, std::min(P->tile_cnt[gi], P->gemm_grid),
+                                      P->st);
+        ++nl;
+      }
+    }
     kp::GmresParams g = solver_params(P, false, par, 0);
     if (e == cudaSuccess) e = launch_solver(P, g, P->shT, P->st);
     ++nl;
@@ -172,6 +205,12 @@ kp_status kp_march_destroy(kp_march_plan* P) {
   cudaFree(P->acc);
   cudaFree(P->spill);
   cudaFree(P->spill32);
+  cudaFree(P->perm);
+  cudaFree(P->Bb);
+  cudaFree(P->Cp);
+  cudaFree(P->tiles[0]);
+  cudaFree(P->tiles[1]);
+  cudaFree(P->err);
   if (P->fork) cudaEventDestroy(P->fork);
   if (P->join) cudaEventDestroy(P->join);
   if (P->st2) cudaStreamDestroy(P->st2);
@@ -256,6 +295,23 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
   // descriptors for parity p: seeds of step n+1 (m_s^{n+1} in S[1-p] -> S[p]),
   // targets of step n (m_t^n in T[p] -> T[1-p]); b is the state itself, scaled by 1/dt
   const double dt = 1.0 / o.T;
+  // internal target order: by seed within each group (stable)
+  std::vector<int> hperm(std::max(nt, 1));
+  {
+    int base = 0;
+    for (int gi = 0; gi < ngroups; ++gi) {
+      const kp_group& g = groups[gi];
+      P->tgt_base.push_back(base);
+      std::vector<int> ord(g.ntgt);
+      for (int k = 0; k < g.ntgt; ++k) ord[k] = k;
+      if (o.mode == KP_MARCH_PROJECTED)
+        std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return g.tgt_seed[x] < g.tgt_seed[y]; });
+      for (int k = 0; k < g.ntgt; ++k) hperm[base + k] = ord[k];
+      base += g.ntgt;
+    }
+  }
+  if (e == cudaSuccess) e = dmalloc(&P->perm, nt);
+  if (e == cudaSuccess) e = cudaMemcpy(P->perm, hperm.data(), nt * sizeof(int), cudaMemcpyHostToDevice);
   for (int par = 0; par < 2 && e == cudaSuccess; ++par) {
     std::vector<SysDesc> hd((size_t)ns + nt);
     int si = 0, ti = 0, seed_base = 0;
@@ -279,7 +335,8 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
         d.mt = P->Tt[par] + off;
         d.b = d.mt;
         d.x = P->Tt[1 - par] + off;
-        const int sd = (g.tgt_seed && g.tgt_seed[k] >= 0 && g.tgt_seed[k] < g.nseed) ? g.tgt_seed[k] : 0;
+        const int u = hperm[P->tgt_base[gi] + k];   // user index of internal target k
+        const int sd = (g.tgt_seed && g.tgt_seed[u] >= 0 && g.tgt_seed[u] < g.nseed) ? g.tgt_seed[u] : 0;
         d.slot = seed_base + sd;               // parity offset added on the device
         hd[(size_t)ns + ti] = d;
       }
@@ -288,6 +345,56 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
     e = cudaMemcpy(P->desc[par], hd.data(), hd.size() * sizeof(SysDesc), cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) e = cudaMemcpy(P->g2, o.g2, o.T * sizeof(double), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && P->mixed && o.mode == KP_MARCH_PROJECTED && ns > 0 && nt > 0 &&
+      c->opt.max_a + 1 <= kp::kVbRows) {
+    // tensor-core projection: BF16 right-hand sides, c = V^T b, tile lists
+    const int vb_ld = c->vb_ld;
+    e = dmalloc(&P->Bb, (size_t)nt * vb_ld);
+    if (e == cudaSuccess) e = cudaMemset(P->Bb, 0, (size_t)nt * vb_ld * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = dmalloc(&P->Cp, (size_t)nt * kp::kVbRows);
+    if (e == cudaSuccess) e = dmalloc(&P->err, 1);
+    if (e == cudaSuccess) e = cudaMemset(P->err, 0, sizeof(int));
+    std::vector<kp::ProjTile> tl[2];
+    int seed_base = 0;
+    P->mapB.resize(ngroups);
+    P->mapV.resize(ngroups);
+    for (int gi = 0; gi < ngroups && e == cudaSuccess; ++gi) {
+      const kp_group& g = groups[gi];
+      const int N = g.H * g.W;
+      P->tile_off.push_back((int)tl[0].size());
+      int k = 0;
+      while (k < g.ntgt) {                      // runs of targets sharing a seed
+        const int sd = g.tgt_seed[hperm[P->tgt_base[gi] + k]];
+        int end = k;
+        while (end < g.ntgt && g.tgt_seed[hperm[P->tgt_base[gi] + end]] == sd) ++end;
+        for (int q = k; q < end; q += 128)
+          for (int par = 0; par < 2; ++par) {
+            kp::ProjTile t;
+            t.row0 = q;
+            t.vrow0 = (par * ns + seed_base + sd) * kp::kVbRows;
+            t.crow0 = P->tgt_base[gi] + q;
+            t.count = std::min(128, end - q);
+            t.nv = kp::kVbRows;
+            tl[par].push_back(t);
+          }
+        k = end;
+      }
+      P->tile_cnt.push_back((int)tl[0].size() - P->tile_off.back());
+      if (g.ntgt) e = kp::make_bf16_map(&P->mapB[gi], P->Bb + (size_t)P->tgt_base[gi] * vb_ld,
+                                        g.ntgt, N, vb_ld, 128);
+      if (e == cudaSuccess)
+        e = kp::make_bf16_map(&P->mapV[gi], c->slotVb, c->opt.max_seeds * kp::kVbRows, N, vb_ld,
+                              kp::kVbRows);
+      seed_base += g.nseed;
+    }
+    for (int par = 0; par < 2 && e == cudaSuccess; ++par) {
+      e = dmalloc(&P->tiles[par], tl[par].size());
+      if (e == cudaSuccess)
+        e = cudaMemcpy(P->tiles[par], tl[par].data(), tl[par].size() * sizeof(kp::ProjTile),
+                       cudaMemcpyHostToDevice);
+    }
+    P->gemm_grid = c->sms;
+  }
   if (e != cudaSuccess) {
     kp_status r = kp::cuda_error(c, e, "march tables");
     kp_march_destroy(P);
@@ -334,7 +441,12 @@ kp_status kp_march_run(kp_march_plan* P, int n0, int steps, kp_step_stats* stats
     const kp_group& g = P->groups[gi];
     const size_t N = (size_t)g.H * g.W;
     if (g.nseed) e = cudaMemcpyAsync(P->S[q0] + P->seed_off[gi], g.m_seed, g.nseed * N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
-    if (e == cudaSuccess && g.ntgt) e = cudaMemcpyAsync(P->Tt[q0] + P->tgt_off[gi], g.m_tgt, g.ntgt * N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
+    if (e == cudaSuccess && g.ntgt)
+      e = kp::launch_permute(P->Tt[q0] + P->tgt_off[gi], g.m_tgt, P->perm + P->tgt_base[gi], g.ntgt,
+                             (int)N, 1, P->st);
+    if (e == cudaSuccess && g.ntgt && P->Bb)
+      e = kp::launch_to_bf16(P->Bb + (size_t)P->tgt_base[gi] * c->vb_ld, c->vb_ld,
+                             P->Tt[q0] + P->tgt_off[gi], g.ntgt, (int)N, (double)P->opt.T, P->st);
   }
   P->host_step[0] = n0;
   P->host_step[1] = n0 + steps;
@@ -376,7 +488,9 @@ kp_status kp_march_run(kp_march_plan* P, int n0, int steps, kp_step_stats* stats
     const kp_group& g = P->groups[gi];
     const size_t N = (size_t)g.H * g.W;
     if (g.nseed) e = cudaMemcpyAsync(g.m_seed, P->S[fin] + P->seed_off[gi], g.nseed * N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
-    if (e == cudaSuccess && g.ntgt) e = cudaMemcpyAsync(g.m_tgt, P->Tt[fin] + P->tgt_off[gi], g.ntgt * N * sizeof(double), cudaMemcpyDeviceToDevice, P->st);
+    if (e == cudaSuccess && g.ntgt)
+      e = kp::launch_permute(g.m_tgt, P->Tt[fin] + P->tgt_off[gi], P->perm + P->tgt_base[gi], g.ntgt,
+                             (int)N, 0, P->st);
   }
   if (e == cudaSuccess) e = cudaEventRecord(sync_ev, P->st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(c->stream, sync_ev, 0);

@@ -122,6 +122,33 @@ __global__ void widen_kernel(const float* src, size_t src_ld, double* dst, size_
   for (int q = threadIdx.x; q < n; q += blockDim.x) dst[(size_t)r * dst_ld + q] = (double)src[(size_t)r * src_ld + q];
 }
 
+__global__ void permute_kernel(double* dst, const double* src, const int* perm, int n, int gather) {
+  const int q = blockIdx.x;
+  const size_t from = gather ? (size_t)perm[q] : (size_t)q;
+  const size_t to = gather ? (size_t)q : (size_t)perm[q];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[to * n + i] = src[from * n + i];
+}
+
+cudaError_t launch_permute(double* dst, const double* src, const int* perm, int count, int n,
+                           int gather, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  permute_kernel<<<count, 256, 0, st>>>(dst, src, perm, n, gather);
+  return cudaGetLastError();
+}
+
+__global__ void to_bf16_kernel(__nv_bfloat16* dst, int ld, const double* src, int n, double scale) {
+  const int q = blockIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    dst[(size_t)q * ld + i] = __float2bfloat16_rn((float)(src[(size_t)q * n + i] * scale));
+}
+
+cudaError_t launch_to_bf16(__nv_bfloat16* dst, int ld, const double* src, int count, int n,
+                           double scale, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  to_bf16_kernel<<<count, 256, 0, st>>>(dst, ld, src, n, scale);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_widen(const float* src, size_t src_ld, double* dst, size_t dst_ld, int n, int rows,
                          cudaStream_t st) {
   if (rows <= 0) return cudaSuccess;
