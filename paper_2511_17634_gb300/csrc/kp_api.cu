@@ -35,19 +35,34 @@ kp_status cuda_error(kp_ctx* c, cudaError_t e, const char* what) {
                    cudaGetErrorString(e));
 }
 
-kp_status gmres_shape(kp_ctx* c, int nmax, int m, Shape* out, bool mixed) {
+cudaError_t launch_solver(const GmresParams& p, const Shape& sh, bool mixed, cudaStream_t st) {
+  if (sh.cs > 0) return launch_gmres_cluster(p, sh.ept, sh.nt, sh.cs, sh.smem, st);
+  return mixed ? launch_gmres_mixed(p, sh.ept, sh.nt, sh.smem, st)
+               : launch_gmres_fp64(p, sh.ept, sh.nt, sh.smem, st);
+}
+
+kp_status gmres_shape(kp_ctx* c, int nmax, int m, Shape* out, bool mixed, int wmin) {
   Shape sh;
   if (nmax <= 1024) { sh.ept = 4; sh.nt = 256; }
   else if (nmax <= 4096) { sh.ept = 8; sh.nt = 512; }
-  else return set_error(c, KP_ERR_UNSUPPORTED, "N=%d: grids above 4096 unknowns are not supported by this kernel", nmax);
+  else if (mixed) {
+    // a cluster of cs CTAs, each holding W/cs whole columns (<= 2048 points)
+    sh.ept = 8; sh.nt = 256;
+    for (int cs : {2, 4, 8})
+      if ((nmax + cs - 1) / cs <= 2048) { sh.cs = cs; break; }
+    if (!sh.cs || wmin <= 0 || wmin % sh.cs)
+      return set_error(c, KP_ERR_UNSUPPORTED, "N=%d: needs W divisible by the cluster size and N <= 16384", nmax);
+  }
+  else return set_error(c, KP_ERR_UNSUPPORTED, "N=%d: FP64 grids above 4096 unknowns are not supported (use the mixed-precision mode)", nmax);
   const int npad = sh.ept * sh.nt;
-  const size_t fixed = mixed ? gmres_mixed_smem_bytes(sh.ept, sh.nt, 0, m)
+  const size_t fixed = sh.cs ? gmres_cluster_smem_bytes(sh.ept, sh.nt, 0, m)
+                     : mixed ? gmres_mixed_smem_bytes(sh.ept, sh.nt, 0, m)
                              : gmres_fp64_smem_bytes(sh.ept, sh.nt, 0, m);
   const size_t per = (size_t)npad * (mixed ? sizeof(float) : sizeof(double));
   int S = c->opt.smem_vectors;
   if (S <= 0) {
     // small systems: leave room for two resident blocks per SM
-    const size_t budget = (npad <= 1024) ? c->smem_optin / 2 : c->smem_optin;
+    const size_t budget = (npad <= 1024 && !sh.cs) ? c->smem_optin / 2 : c->smem_optin;
     S = budget > fixed ? (int)((budget - fixed) / per) : 0;
   }
   S = std::min(S, m + 1);
@@ -159,14 +174,20 @@ kp_status run_gmres(kp_ctx* c, int nsys, const kp_op* ops, const double* const* 
   for (int k = 0; k < nsys; ++k) {
     if (!ops[k].mtilde || !b[k] || !x[k]) return kp::set_error(c, KP_ERR_ARG, "system %d: NULL vector", k);
   }
+  int wmin = 1 << 30;
+  for (int k = 0; k < nsys; ++k) wmin = std::min(wmin, ops[k].W);
+  for (int k = 0; k < nsys && nmax > 4096; ++k)
+    if ((long long)ops[k].H * ops[k].W != nmax)
+      return kp::set_error(c, KP_ERR_UNSUPPORTED, "grids above 4096 unknowns must share one size per call");
   kp::Shape sh;
-  st = kp::gmres_shape(c, nmax, m, &sh, mixed);
+  st = kp::gmres_shape(c, nmax, m, &sh, mixed, wmin);
   if (st != KP_OK) return st;
   const int ept = sh.ept, nt = sh.nt, S = sh.S, npad = ept * nt;
   const size_t smem = sh.smem;
   cudaError_t e;
   if (S < m + 1) {
-    const size_t need = (size_t)nsys * (m + 1 - S) * npad * (mixed ? sizeof(float) : sizeof(double));
+    const size_t need = (size_t)nsys * (sh.cs ? sh.cs : 1) * (m + 1 - S) * npad *
+                        (mixed ? sizeof(float) : sizeof(double));
     e = mixed ? grow(&c->spill32, &c->spill32_bytes, need) : grow(&c->spill, &c->spill_bytes, need);
     if (e != cudaSuccess) return kp::cuda_error(c, e, "cudaMalloc(Krylov workspace)");
   }
@@ -215,8 +236,8 @@ kp_status run_gmres(kp_ctx* c, int nsys, const kp_op* ops, const double* const* 
     p.cap_a = c->opt.max_a;
     p.cap_ld = c->opt.max_n;
   }
-  e = mixed ? kp::launch_gmres_mixed(p, ept, nt, smem, c->stream)
-            : kp::launch_gmres_fp64(p, ept, nt, smem, c->stream);
+  (void)ept; (void)nt; (void)smem;
+  e = kp::launch_solver(p, sh, mixed, c->stream);
   if (e != cudaSuccess) return kp::cuda_error(c, e, "GMRES launch");
   return KP_OK;
 }
@@ -423,10 +444,9 @@ kp_status kp_project_targets_multi(kp_ctx* c, int timestep, int nt, const int* s
     if (!r[k] || !x[k]) return kp::set_error(c, KP_ERR_ARG, "target %d: NULL vector", k);
     h[k] = make_desc(ops[k], r[k], x[k], s);
   }
-  kp::Shape sh;
-  st = kp::gmres_shape(c, nmax, 1, &sh);
-  if (st != KP_OK) return st;
-  const int ept = sh.ept, nt_ = sh.nt;
+  int ept = 16, nt_ = 1024;                       // N <= 16384
+  if (nmax <= 1024) { ept = 4; nt_ = 256; }
+  else if (nmax <= 4096) { ept = 8; nt_ = 512; }
   SysDesc* dd;
   st = upload(c, h, &dd);
   if (st != KP_OK) return st;

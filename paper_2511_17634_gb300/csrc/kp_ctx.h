@@ -72,12 +72,16 @@ namespace kp {
 struct Shape {
   int ept = 0, nt = 0, S = 0;
   size_t smem = 0;
+  int cs = 0;   // > 0: thread-block cluster of cs CTAs per system (slices of W/cs columns)
 };
 
 kp_status set_error(kp_ctx* c, kp_status s, const char* fmt, ...);
 kp_status cuda_error(kp_ctx* c, cudaError_t e, const char* what);
 // Chooses threads, elements per thread and the shared-memory Krylov window
 // (FP64 vectors, or FP32 ones for the mixed-precision solver).
-kp_status gmres_shape(kp_ctx* c, int nmax, int m, Shape* out, bool mixed = false);
+kp_status gmres_shape(kp_ctx* c, int nmax, int m, Shape* out, bool mixed = false,
+                      int wmin = 0);
+// Launch the solver kernel family that `sh` selects.
+cudaError_t launch_solver(const GmresParams& p, const Shape& sh, bool mixed, cudaStream_t st);
 
 }  // namespace kp

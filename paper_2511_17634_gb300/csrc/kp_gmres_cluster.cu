@@ -1,0 +1,542 @@
+// kp_gmres_cluster.cu -- the mixed-precision solver of kp_gmres_mixed.cu for
+// grids too large for one SM (128x128 = 16384 unknowns): a thread-block
+// cluster of CS CTAs per system, CTA r holding columns [r*W/CS, (r+1)*W/CS)
+// of every vector (whole columns, so north/south neighbours stay local).
+//
+//  * East/west neighbours across a slice edge are read from the adjacent
+//    CTA's shared memory (distributed shared memory), or from its slice of
+//    the device workspace for Krylov vectors beyond the shared-memory window.
+//  * Inner products: FP32 per thread and warp, FP64 across warps, then the CS
+//    per-CTA partials are summed in rank order by every CTA (one cluster
+//    barrier, double-buffered partials), so all CTAs hold bit-identical
+//    coefficients and run the FP64 Hessenberg / Givens updates redundantly
+//    instead of broadcasting them.
+//  * Same arithmetic and stopping rules as the one-block mixed kernel: FP32
+//    Krylov inside FP64 iterative refinement on the FP64 true residual.
+#include <cooperative_groups.h>
+
+#include "kp_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace kp {
+namespace {
+
+template <int EPT, int NT, int CS>
+__global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams p) {
+  constexpr int NWARPS = NT / 32;
+  extern __shared__ __align__(16) double smem_raw[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int npad = EPT * NT;
+  const int m = p.m;
+  const int ld = m + 1;
+  // shared-memory carve (identical offsets in every CTA of the cluster)
+  double* xs = smem_raw;                          // [npad] FP64 slice of x
+  double* red = xs + npad;                        // [NWARPS][kMaxV]
+  double* hb = red + NWARPS * kMaxV;              // [kMaxV] cluster sums
+  double* cpart = hb + kMaxV;                     // [2][kMaxV] per-CTA partials
+  double* Hr = cpart + 2 * kMaxV;                 // [(m+1) m]
+  double* gv = Hr + (m + 1) * m;
+  double* cs = gv + (m + 1);
+  double* sn = cs + m;
+  double* yv = sn + m;
+  double* rinv = yv + m;
+  double* sc = rinv + m;                          // [8]
+  int* fl = reinterpret_cast<int*>(sc + 8);       // [8]
+  float* V = reinterpret_cast<float*>(fl + 8);    // [S][npad]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int sysi = blockIdx.x / CS;
+  const int cta0 = blockIdx.x - rank;             // first CTA of this cluster
+  const size_t spill_per = (size_t)(m + 1 - p.S) * npad;
+  auto vloc = [&](int i) -> float* {
+    return i < p.S ? V + (size_t)i * npad : p.spill32 + (size_t)blockIdx.x * spill_per + (size_t)(i - p.S) * npad;
+  };
+  auto vrem = [&](int i, int r) -> const float* {
+    return i < p.S ? cluster.map_shared_rank(V + (size_t)i * npad, r)
+                   : p.spill32 + (size_t)(cta0 + r) * spill_per + (size_t)(i - p.S) * npad;
+  };
+  int tstep = 0;
+  if (p.step) {
+    tstep = *p.step + p.step_offset;
+    if (tstep >= *p.step_end) return;            // uniform over the whole grid
+  }
+  if (sysi >= p.nsys) return;                     // uniform over the cluster
+  const int parity_base = (tstep & 1) * p.slot_parity_stride;
+  const double bsc = p.b_scale;
+  constexpr double kEta = 1e-5;
+
+  const SysDesc d = p.sys[sysi];
+  const int H = d.H, W = d.W, N = H * W;
+  const int SL = N / CS;                          // slice length (whole columns)
+  const int base = rank * SL;
+  const double hh = d.h;
+  const double g2 = p.step ? p.g2_sched[tstep] : d.g2;
+  const double cc = g2 / (2.0 * hh * hh);
+  const double ee = g2 / (8.0 * hh * hh);
+  const double cd = 1.0 / d.dt + 2.0 * g2 / (hh * hh);
+  const double i2h = 1.0 / (2.0 * hh);
+  const float ccf = (float)cc, cdf = (float)cd;
+  const bool capture = p.capV32 != nullptr;
+  const int cidx = p.factor ? parity_base + sysi : sysi;
+  float* capV = capture ? p.capV32 + (size_t)cidx * (p.cap_a + 1) * p.cap_ld : nullptr;
+  double* capH = capture ? p.capH + (size_t)cidx * (p.cap_a + 1) * p.cap_a : nullptr;
+
+  double qx[EPT], qy[EPT];
+  float qxf[EPT], qyf[EPT];
+  unsigned msk[EPT];
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int l = tid + k * NT, pp = base + l;
+    qx[k] = qy[k] = 0.0;
+    msk[k] = 0;
+    if (l < SL) {
+      const int i = pp / H, j = pp - i * H;
+      const double mE = (i + 1 < W) ? d.mt[pp + H] : 0.0;
+      const double mW = (i > 0) ? d.mt[pp - H] : 0.0;
+      const double mN = (j + 1 < H) ? d.mt[pp + 1] : 0.0;
+      const double mS = (j > 0) ? d.mt[pp - 1] : 0.0;
+      const double fxp = d.fx ? d.fx[pp] : 0.0;
+      const double fyp = d.fy ? d.fy[pp] : 0.0;
+      qx[k] = fxp * i2h - ee * (mE - mW);
+      qy[k] = fyp * i2h - ee * (mN - mS);
+      msk[k] = (i + 1 < W ? 1u : 0u) | (i > 0 ? 2u : 0u) | (j + 1 < H ? 4u : 0u) | (j > 0 ? 8u : 0u);
+    }
+    qxf[k] = (float)qx[k];
+    qyf[k] = (float)qy[k];
+  }
+  const double* xs_next = rank + 1 < CS ? cluster.map_shared_rank(xs, rank + 1) : nullptr;
+  const double* xs_prev = rank > 0 ? cluster.map_shared_rank(xs, rank - 1) : nullptr;
+  auto apply64 = [&](double (&out)[EPT]) {
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int l = tid + k * NT;
+      out[k] = 0.0;
+      if (l < SL) {
+        const double xE = (msk[k] & 1u) ? (l + H < SL ? xs[l + H] : xs_next[l + H - SL]) : 0.0;
+        const double xW = (msk[k] & 2u) ? (l - H >= 0 ? xs[l - H] : xs_prev[l - H + SL]) : 0.0;
+        const double xN = (msk[k] & 4u) ? xs[l + 1] : 0.0;
+        const double xS = (msk[k] & 8u) ? xs[l - 1] : 0.0;
+        out[k] = cd * xs[l] - cc * (xE + xW + xN + xS) + qx[k] * (xE - xW) + qy[k] * (xN - xS);
+      }
+    }
+  };
+  auto apply32 = [&](int vi, float (&out)[EPT]) {
+    const float* v = vloc(vi);
+    const float* vn = rank + 1 < CS ? vrem(vi, rank + 1) : nullptr;
+    const float* vp = rank > 0 ? vrem(vi, rank - 1) : nullptr;
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int l = tid + k * NT;
+      out[k] = 0.f;
+      if (l < SL) {
+        const float xE = (msk[k] & 1u) ? (l + H < SL ? v[l + H] : vn[l + H - SL]) : 0.f;
+        const float xW = (msk[k] & 2u) ? (l - H >= 0 ? v[l - H] : vp[l - H + SL]) : 0.f;
+        const float xN = (msk[k] & 4u) ? v[l + 1] : 0.f;
+        const float xS = (msk[k] & 8u) ? v[l - 1] : 0.f;
+        out[k] = cdf * v[l] - ccf * (xE + xW + xN + xS) + qxf[k] * (xE - xW) + qyf[k] * (xN - xS);
+      }
+    }
+  };
+  auto bval = [&](int l) { return (l < SL) ? d.b[base + l] * bsc : 0.0; };
+  int buf = 0;
+  // cluster-wide sums of nv values whose per-warp partials are in red;
+  // result in hb[0..nv) of every CTA (identical, rank order)
+  auto cluster_sum = [&](int nv) {
+    if (warp == 0)
+      for (int i = lane; i < nv; i += 32) cpart[buf * kMaxV + i] = cross_warp<NT>(red, i);
+    cluster.sync();
+    if (warp == 0) {
+      for (int i = lane; i < nv; i += 32) {
+        double s = 0.0;
+#pragma unroll
+        for (int r = 0; r < CS; ++r) s += cluster.map_shared_rank(cpart + buf * kMaxV, r)[i];
+        hb[i] = s;
+      }
+    }
+    __syncthreads();
+    buf ^= 1;
+  };
+
+  // initial guess
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int l = tid + k * NT;
+    double x0 = 0.0;
+    if (l < SL) {
+      if (p.x0_mode == X0_READ) x0 = d.x[base + l];
+      else if (p.x0_mode == X0_WARM) x0 = d.mt[base + l];
+    }
+    xs[l] = x0;
+  }
+  unsigned long long proj_flops = 0;
+  if (p.x0_mode == X0_PROJECT) {
+    const int sl = d.slot + parity_base;
+    const SlotMeta mt = p.slotMeta[sl];
+    if (mt.timestep == tstep && mt.N == N && mt.a > 0) {
+      const int a = mt.a;
+      const int nv = mt.lsq ? a + 1 : a;
+      const float* Vs = p.slotV32 + (size_t)sl * (p.max_a + 1) * p.slot_ld + base;
+      if (p.cproj) {
+        if (tid < nv) hb[tid] = (double)p.cproj[(size_t)sysi * p.cproj_ld + tid];
+        __syncthreads();
+      } else {
+        float bv[EPT];
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) bv[k] = (float)bval(tid + k * NT);
+        block_partials_f32<NT>(nv, [&](int i) {
+          const float* vi = Vs + (size_t)i * p.slot_ld;
+          float s = 0.f;
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) {
+            const int l = tid + k * NT;
+            if (l < SL) s = fmaf(vi[l], bv[k], s);
+          }
+          return s;
+        }, red);
+        cluster_sum(nv);
+      }
+      if (warp == 0) {
+        __syncwarp();
+        const double* rot = p.slotRot + (size_t)sl * 3 * p.max_a;
+        solve_projected_warp(hb, a, mt.nrot, p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a,
+                             p.max_a + 1, rot, rot + 2 * p.max_a, lane);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int l = tid + k * NT;
+        if (l < SL) {
+          float xv = 0.f;
+          for (int i = 0; i < a; ++i) xv = fmaf((float)hb[i], Vs[(size_t)i * p.slot_ld + l], xv);
+          xs[l] = (double)xv;
+        }
+      }
+      proj_flops = (unsigned long long)(2 * nv + 2 * a) * (unsigned long long)N;
+    }
+  }
+  cluster.sync();                                 // x slices visible cluster-wide
+  double r[EPT];
+  auto residual = [&]() {
+    apply64(r);
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int l = tid + k * NT;
+      r[k] = (l < SL) ? bval(l) - r[k] : 0.0;
+    }
+  };
+  if (p.x0_mode == X0_ZERO) {
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) r[k] = bval(tid + k * NT);
+  } else {
+    residual();
+  }
+  block_partials<NT>(2, [&](int i) {
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const double bv = bval(tid + k * NT);
+      s += (i == 0) ? bv * bv : r[k] * r[k];
+    }
+    return s;
+  }, red);
+  cluster_sum(2);
+  const double bnorm = sqrt(hb[0]);
+  double beta = sqrt(hb[1]);
+  int steps = 0, status = KP_NOT_CONVERGED, outer = 0;
+  if (bnorm == 0.0) {
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) xs[tid + k * NT] = 0.0;
+    beta = 0.0;
+    status = KP_OK;
+  }
+  float w[EPT];
+  while (status == KP_NOT_CONVERGED) {
+    if (beta <= p.tol * bnorm) { status = KP_OK; break; }
+    if (!isfinite(beta)) { status = KP_BREAKDOWN; break; }
+    if (steps >= p.maxit || outer >= 64) break;
+    const bool first = (outer == 0);
+    const double target = (capture && first) ? p.tol * bnorm : fmax(kEta * beta, 0.1 * p.tol * bnorm);
+    {
+      const double ib = 1.0 / beta;
+      float* v0 = vloc(0);
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int l = tid + k * NT;
+        const float v = (float)(r[k] * ib);
+        v0[l] = v;
+        if (capture && first && l < SL) {
+          capV[base + l] = v;
+          if (p.capVb) p.capVb[(size_t)cidx * kVbRows * p.capVb_ld + base + l] = __float2bfloat16_rn(v);
+        }
+      }
+      if (tid == 0) gv[0] = beta;
+    }
+    int kdone = 0, brk = 0;
+    auto givens_step = [&](int j, double hn2) {
+      const double ihn = hn2 > 0.0 ? rsqrt(hn2) : 0.0;
+      const double hn = hn2 * ihn;
+      const int b = !(hn > 1e-7 * sqrt(sc[2]));
+      Hr[(j + 1) + j * ld] = hn;
+      if (capture && first && j < p.cap_a && rank == 0) {
+        for (int i = 0; i <= j + 1; ++i) capH[i + j * (p.cap_a + 1)] = Hr[i + j * ld];
+      }
+      for (int i = 0; i < j; ++i) {
+        const double t1 = Hr[i + j * ld], t2 = Hr[(i + 1) + j * ld];
+        Hr[i + j * ld] = cs[i] * t1 + sn[i] * t2;
+        Hr[(i + 1) + j * ld] = -sn[i] * t1 + cs[i] * t2;
+      }
+      const double a0 = Hr[j + j * ld];
+      const double rr = a0 * a0 + hn2;
+      const double ir = rsqrt(rr);
+      const double c = a0 * ir, s = hn * ir;
+      cs[j] = c;
+      sn[j] = s;
+      Hr[j + j * ld] = rr * ir;
+      rinv[j] = ir;
+      Hr[(j + 1) + j * ld] = 0.0;
+      gv[j + 1] = -s * gv[j];
+      gv[j] = c * gv[j];
+      const double res = fabs(gv[j + 1]);
+      sc[3] = ihn;
+      fl[1] = b;
+      fl[2] = (res <= target) || b || (steps >= p.maxit) || (j + 1 == m);
+    };
+    for (int j = 0; j < m; ++j) {
+      cluster.sync();                             // v_j slices visible cluster-wide
+      apply32(j, w);
+      ++steps;
+      const int nh = j + 1;
+      auto dots = [&](int i) {
+        float s = 0.f;
+        if (i < nh) {
+          const float* vi = vloc(i);
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) s = fmaf(vi[tid + k * NT], w[k], s);
+        } else {
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) s = fmaf(w[k], w[k], s);
+        }
+        return s;
+      };
+      block_partials_f32<NT>(nh + 1, dots, red);
+      cluster_sum(nh + 1);
+      if (warp == 0) {
+        double sq = 0.0;
+        for (int i = lane; i < nh; i += 32) { Hr[i + j * ld] = hb[i]; sq += hb[i] * hb[i]; }
+        sq = warp_sum(sq);
+        if (lane == 0) {
+          const double ww0 = hb[nh];
+          sc[2] = ww0;
+          const int pass2 = (p.reorth == 0) || (ww0 - sq < 0.5 * ww0);
+          fl[0] = pass2;
+          if (!pass2) givens_step(j, ww0 - sq);
+        }
+      }
+      __syncthreads();
+      for (int i = 0; i < nh; ++i) {
+        const float hi = (float)hb[i];
+        const float* vi = vloc(i);
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) w[k] = fmaf(-hi, vi[tid + k * NT], w[k]);
+      }
+      if (fl[0]) {
+        block_partials_f32<NT>(nh + 1, dots, red);
+        cluster_sum(nh + 1);
+        if (warp == 0) {
+          double sq = 0.0;
+          for (int i = lane; i < nh; i += 32) { Hr[i + j * ld] += hb[i]; sq += hb[i] * hb[i]; }
+          sq = warp_sum(sq);
+          if (lane == 0) {
+            const double ww1 = hb[nh];
+            const int exact = sq > 0.25 * ww1;
+            fl[3] = exact;
+            if (!exact) givens_step(j, ww1 - sq);
+          }
+        }
+        __syncthreads();
+        for (int i = 0; i < nh; ++i) {
+          const float hi = (float)hb[i];
+          const float* vi = vloc(i);
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) w[k] = fmaf(-hi, vi[tid + k * NT], w[k]);
+        }
+        if (fl[3]) {
+          block_partials_f32<NT>(1, [&](int) {
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) s = fmaf(w[k], w[k], s);
+            return s;
+          }, red);
+          cluster_sum(1);
+          if (tid == 0) givens_step(j, hb[0]);
+          __syncthreads();
+        }
+      }
+      brk = fl[1];
+      kdone = j + 1;
+      if (!brk) {
+        const float ih = (float)sc[3];
+        float* vn = vloc(j + 1);
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          const int l = tid + k * NT;
+          vn[l] = w[k] * ih;
+          if (capture && first && j + 1 <= p.cap_a && l < SL) {
+            capV[(size_t)(j + 1) * p.cap_ld + base + l] = w[k] * ih;
+            if (p.capVb && j + 1 < kVbRows)
+              p.capVb[((size_t)cidx * kVbRows + j + 1) * p.capVb_ld + base + l] = __float2bfloat16_rn(w[k] * ih);
+          }
+        }
+      }
+      if (fl[2]) break;
+    }
+    if (warp == 0) {
+      double g0 = (lane < kdone) ? gv[lane] : 0.0;
+      double g1 = (lane + 32 < kdone) ? gv[lane + 32] : 0.0;
+      for (int i = kdone - 1; i >= 0; --i) {
+        const double gi = __shfl_sync(kFull, i < 32 ? g0 : g1, i & 31);
+        const double yi = gi * rinv[i];
+        if (lane == 0) yv[i] = yi;
+        if (lane < i) g0 = fma(-Hr[lane + i * ld], yi, g0);
+        if (lane + 32 < i) g1 = fma(-Hr[(lane + 32) + i * ld], yi, g1);
+      }
+    }
+    if (tid == 0 && rank == 0 && capture && first) {
+      const int a = kdone < p.cap_a ? kdone : p.cap_a;
+      const int hn = (a < kdone) || !brk;
+      if (p.factor) {
+        SlotMeta mt;
+        double* rot = p.slotRot + (size_t)cidx * 3 * p.max_a;
+        factor_hessenberg(capH, p.cap_a + 1, a, hn, p.slotR + (size_t)cidx * (p.max_a + 1) * p.max_a,
+                          rot, rot + 2 * p.max_a, &mt.lsq, &mt.nrot);
+        mt.a = a;
+        mt.has_next = hn;
+        mt.timestep = tstep;
+        mt.N = N;
+        mt.pad_[0] = mt.pad_[1] = 0;
+        p.slotMeta[cidx] = mt;
+      } else {
+        p.capMeta[sysi].a = a;
+        p.capMeta[sysi].has_next = hn;
+        p.capMeta[sysi].N = N;
+        p.capMeta[sysi].valid = 1;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int l = tid + k * NT;
+      float dv = 0.f;
+      for (int i = 0; i < kdone; ++i) dv = fmaf((float)yv[i], vloc(i)[l], dv);
+      xs[l] += (double)dv;
+    }
+    cluster.sync();                               // x slices visible cluster-wide
+    residual();
+    block_partials<NT>(1, [&](int) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) s += r[k] * r[k];
+      return s;
+    }, red);
+    cluster_sum(1);
+    beta = sqrt(hb[0]);
+    ++outer;
+  }
+  if (capture && outer == 0 && tid == 0 && rank == 0) {
+    if (p.factor) {
+      SlotMeta mt;
+      mt.a = 0; mt.has_next = 0; mt.timestep = tstep; mt.N = N; mt.lsq = 0; mt.nrot = 0;
+      mt.pad_[0] = mt.pad_[1] = 0;
+      p.slotMeta[cidx] = mt;
+    } else {
+      p.capMeta[sysi].a = 0;
+      p.capMeta[sysi].has_next = 0;
+      p.capMeta[sysi].N = N;
+      p.capMeta[sysi].valid = 1;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int l = tid + k * NT;
+    if (l < SL) {
+      d.x[base + l] = xs[l];
+      if (p.bnext)
+        p.bnext[(size_t)sysi * p.bnext_ld + base + l] = __float2bfloat16_rn((float)(xs[l] * bsc));
+    }
+  }
+  if (tid == 0 && rank == 0) {
+    const double rel = bnorm > 0.0 ? beta / bnorm : 0.0;
+    if (p.info) {
+      kp_info inf;
+      inf.iters = steps;
+      inf.status = status;
+      inf.rel_res = rel;
+      p.info[sysi] = inf;
+    }
+    if (p.acc) {
+      StepAcc* a = p.acc + tstep;
+      const unsigned long long fl64 = (unsigned long long)(14 + outer * 13) * (unsigned long long)N;
+      const unsigned long long fl32 = (gmres_flops(steps, m) - 14ull) * (unsigned long long)N;
+      if (p.acc_kind == 0) {
+        atomicAdd(&a->seed_iters, (unsigned long long)steps);
+        atomicAdd(&a->seed_flops, fl64 + fl32);
+      } else {
+        atomicAdd(&a->tgt_iters, (unsigned long long)steps);
+        atomicAdd(&a->tgt_flops, fl64);
+        atomicAdd(&a->tgt_flops32, fl32);
+        atomicMax(&a->tgt_max_iters, (unsigned int)steps);
+        atomicMax(&a->max_res_bits, (unsigned long long)__double_as_longlong(rel));
+        if (proj_flops) atomicAdd(&a->proj_flops, proj_flops);
+      }
+      if (status != KP_OK) atomicAdd(&a->not_converged, 1u);
+    }
+  }
+  cluster.sync();                                 // no CTA leaves while others read its memory
+}
+
+template <int EPT, int NT, int CS>
+cudaError_t launch_c(const GmresParams& p, size_t smem, cudaStream_t st) {
+  auto k = gmres_cluster_kernel<EPT, NT, CS>;
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if (smem > (size_t)optin) return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(p.nsys * CS));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CS;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, k, p);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t gmres_cluster_smem_bytes(int ept, int nt, int S, int m) {
+  const int npad = ept * nt;
+  const size_t doubles = (size_t)npad + (nt / 32) * kMaxV + kMaxV + 2 * kMaxV +
+                         (size_t)(m + 1) * m + (m + 1) + 4 * m + 8;
+  return doubles * sizeof(double) + 8 * sizeof(int) + (size_t)S * npad * sizeof(float);
+}
+
+cudaError_t launch_gmres_cluster(const GmresParams& p, int ept, int nt, int cs, size_t smem,
+                                 cudaStream_t st) {
+  if (ept == 8 && nt == 256 && cs == 8) return launch_c<8, 256, 8>(p, smem, st);
+  if (ept == 8 && nt == 256 && cs == 2) return launch_c<8, 256, 2>(p, smem, st);
+  if (ept == 8 && nt == 256 && cs == 4) return launch_c<8, 256, 4>(p, smem, st);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace kp

@@ -391,6 +391,10 @@ size_t gmres_fp64_smem_bytes(int ept, int nt, int S, int m);
 size_t gmres_mixed_smem_bytes(int ept, int nt, int S, int m);
 cudaError_t launch_gmres_mixed(const GmresParams& p, int ept, int nt, size_t smem,
                                cudaStream_t st);
+size_t gmres_cluster_smem_bytes(int ept, int nt, int S, int m);
+// Cluster of cs CTAs per system (grids above 4096 unknowns, mixed precision).
+cudaError_t launch_gmres_cluster(const GmresParams& p, int ept, int nt, int cs, size_t smem,
+                                 cudaStream_t st);
 // The N <= 1024 instantiation (4 points x 256 threads) on an explicit grid;
 // the kernel strides over systems, block b using Krylov workspace slice b.
 cudaError_t launch_gmres_fp64_1k_grid(const GmresParams& p, size_t smem, int grid,

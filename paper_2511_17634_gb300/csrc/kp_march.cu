@@ -87,7 +87,8 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset)
   g.npad = sh.ept * sh.nt;
   size_t spS = 0;
   if (P->ns && P->shS.S < P->opt.m_seed + 1)
-    spS = (size_t)P->ns * (P->opt.m_seed + 1 - P->shS.S) * P->shS.ept * P->shS.nt;
+    spS = (size_t)P->ns * (P->shS.cs ? P->shS.cs : 1) * (P->opt.m_seed + 1 - P->shS.S) * P->shS.ept *
+          P->shS.nt;
   if (P->mixed)
     g.spill32 = (sh.S < g.m + 1) ? P->spill32 + (seeds ? 0 : spS) : nullptr;
   else
@@ -137,8 +138,7 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset)
 
 cudaError_t launch_solver(kp_march_plan* P, const kp::GmresParams& g, const kp::Shape& sh,
                           cudaStream_t st) {
-  return P->mixed ? kp::launch_gmres_mixed(g, sh.ept, sh.nt, sh.smem, st)
-                  : kp::launch_gmres_fp64(g, sh.ept, sh.nt, sh.smem, st);
+  return kp::launch_solver(g, sh, P->mixed, st);
 }
 
 // Target step n and seed step n+1 for parity p = n & 1.  With ev (timing
@@ -232,7 +232,7 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
   P->ctx = c;
   P->opt = o;
   P->groups.assign(groups, groups + ngroups);
-  int nmaxS = 0, nmaxT = 0;
+  int nmaxS = 0, nmaxT = 0, wminS = 1 << 30, wminT = 1 << 30;
   for (int gi = 0; gi < ngroups; ++gi) {
     const kp_group& g = groups[gi];
     const int N = g.H * g.W;
@@ -253,8 +253,8 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
     P->tgt_elems += (size_t)g.ntgt * N;
     P->ns += g.nseed;
     P->nt += g.ntgt;
-    if (g.nseed) nmaxS = std::max(nmaxS, N);
-    if (g.ntgt) nmaxT = std::max(nmaxT, N);
+    if (g.nseed) { nmaxS = std::max(nmaxS, N); wminS = std::min(wminS, g.W); }
+    if (g.ntgt) { nmaxT = std::max(nmaxT, N); wminT = std::min(wminT, g.W); }
   }
   if (2 * P->ns > c->opt.max_seeds) {
     kp_march_destroy(P);
@@ -263,8 +263,12 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
   }
   P->mixed = c->opt.precision == KP_PREC_MIXED;
   kp_status s = KP_OK;
-  if (P->ns) s = kp::gmres_shape(c, nmaxS, o.m_seed, &P->shS, P->mixed);
-  if (s == KP_OK && P->nt) s = kp::gmres_shape(c, nmaxT, o.m, &P->shT, P->mixed);
+  if (P->ns) s = kp::gmres_shape(c, nmaxS, o.m_seed, &P->shS, P->mixed, wminS);
+  if (s == KP_OK && P->nt) s = kp::gmres_shape(c, nmaxT, o.m, &P->shT, P->mixed, wminT);
+  if (s == KP_OK && ((P->shS.cs && ngroups > 1) || (P->shT.cs && ngroups > 1))) {
+    kp_march_destroy(P);
+    return kp::set_error(c, KP_ERR_UNSUPPORTED, "grids above 4096 unknowns: one grid size per plan");
+  }
   if (s != KP_OK) { kp_march_destroy(P); return s; }
   cudaError_t e = cudaStreamCreateWithFlags(&P->st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->st2, cudaStreamNonBlocking);
@@ -280,8 +284,9 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
   if (e == cudaSuccess) e = dmalloc(&P->acc, o.T);
   // one Krylov workspace per branch: seed blocks first, then target blocks
   size_t spS = 0, spT = 0;
-  if (ns && P->shS.S < o.m_seed + 1) spS = (size_t)ns * (o.m_seed + 1 - P->shS.S) * P->shS.ept * P->shS.nt;
-  if (nt && P->shT.S < o.m + 1) spT = (size_t)nt * (o.m + 1 - P->shT.S) * P->shT.ept * P->shT.nt;
+  const int csS = P->shS.cs ? P->shS.cs : 1, csT = P->shT.cs ? P->shT.cs : 1;
+  if (ns && P->shS.S < o.m_seed + 1) spS = (size_t)ns * csS * (o.m_seed + 1 - P->shS.S) * P->shS.ept * P->shS.nt;
+  if (nt && P->shT.S < o.m + 1) spT = (size_t)nt * csT * (o.m + 1 - P->shT.S) * P->shT.ept * P->shT.nt;
   if (e == cudaSuccess && spS + spT) {
     if (P->mixed) e = dmalloc(&P->spill32, spS + spT);
     else e = dmalloc(&P->spill, spS + spT);
