@@ -21,3 +21,19 @@ def test_tune_times_every_candidate_and_caches(tmp_path):
     assert len(calls) == len(autotune.M_CANDIDATES) * len(autotune.WINDOW_CANDIDATES)
     r2 = autotune.tune(wl, cache_path=path, time_fn=lambda m, S: 1 / 0)   # served from the cache
     assert r2["m"] == 40
+
+
+def test_tune_on_gpu_picks_a_candidate(tmp_path):
+    import pytest
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2511_17634_gb300 import build
+    build.build()
+    wl = synth.config(2, T=1000, ntargets=16)
+    r = autotune.tune(wl, steps=2, cache_path=str(tmp_path / "t.json"))
+    assert r["m"] in autotune.M_CANDIDATES and r["smem_vectors"] in autotune.WINDOW_CANDIDATES
+    assert len(r["timings"]) == len(autotune.M_CANDIDATES) * len(autotune.WINDOW_CANDIDATES)
+
+
+test_tune_on_gpu_picks_a_candidate = __import__("pytest").mark.gpu(test_tune_on_gpu_picks_a_candidate)
