@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--ntargets", type=int, default=None, help="fewer targets (testing only)")
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=12)
+    ap.add_argument("--block-threads", type=int, default=0,
+                    help="threads per system for grids <= 1024 points (0 = library default)")
+    ap.add_argument("--reorth", type=int, default=0, help="0 CGS2 (default), 1 DGKS-conditional")
     return ap.parse_args()
 
 
@@ -207,7 +210,8 @@ def main():
     nmax = max(g.N for g in wl.groups)
     mixed = wl.precision == "mixed"
     ctx = kp.Context(max_seeds=max(2 * wl.n_seed_planes, 1), max_a=wl.a, max_n=nmax,
-                     precision=kp.PREC_MIXED if mixed else kp.PREC_FP64)
+                     precision=kp.PREC_MIXED if mixed else kp.PREC_FP64,
+                     block_threads=args.block_threads, reorth=args.reorth)
     dev = torch.device("cuda", torch.cuda.current_device())
     img_s = [torch.as_tensor(g.seeds.reshape(len(g.seeds), -1), device=dev) for g in wl.groups]
     img_t = [torch.as_tensor(g.targets.reshape(len(g.targets), -1), device=dev) for g in wl.groups]
@@ -329,6 +333,8 @@ def main():
             "config": {"workload": wl.name, "T": T, "targets": nt_planes,
                        "seeds": wl.n_seed_planes, "grid": [g.H for g in wl.groups],
                        "tol": wl.tol, "m": wl.m, "parallelism": f"replicas x{world}",
+                       "block_threads": args.block_threads or 256,
+                       "orthogonalisation": "CGS2" if args.reorth == 0 else "CGS+DGKS",
                        "l2": "flushed between timed steps (512 MiB write)"},
             "e2e": {"value": e2e_value, "unit": "systems/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

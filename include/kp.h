@@ -71,6 +71,8 @@ typedef struct {
   int reorth;        /* 0: CGS2, two classical Gram-Schmidt passes every step;
                         1: second pass only when the first removed more than
                         half of the vector's norm (Daniel-Gragg-Kaufman-Stewart)  */
+  int block_threads; /* threads per system for grids of <= 1024 points: 256 (4
+                        points per thread), 128 (8 points per thread), 0 = 256   */
 } kp_options;
 
 /* Operator of one system (Sec. 2.3): A(m~; g^2, dt, h, f).  `mtilde` is the

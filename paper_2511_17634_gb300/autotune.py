@@ -3,7 +3,8 @@ shared-memory Krylov window (which sets how many blocks share an SM) for a
 workload by timing a few calibration timesteps of the real march, and caches
 the choice in a JSON file keyed by (device, grid sizes, batch, precision).
 
-Candidates: m in {20, 30, 40, 60} x shared-memory window in {auto, small}.
+Candidates: m in {20, 30, 40, 60} x shared-memory window in {auto, small} x
+threads per system in {256, 128} (grids of up to 1024 points).
 The timing runs through the C ABI (kp_march_*) on the GPU; only the choice of
 the fastest candidate and the cache are host logic.
 """
@@ -14,6 +15,7 @@ import os
 
 M_CANDIDATES = (20, 30, 40, 60)
 WINDOW_CANDIDATES = (0, 6)      # 0 = automatic (two blocks per SM when N <= 1024)
+THREAD_CANDIDATES = (256, 128)  # threads per system for grids of <= 1024 points
 
 
 def cache_key(device: str, grids, nseed: int, ntgt: int, precision: str, mode: int) -> str:
@@ -39,13 +41,13 @@ def save_cache(path: str, cache: dict) -> None:
 
 
 def choose(timings: dict):
-    """Fastest candidate of {(m, window): seconds}; ties go to the smaller m."""
-    return min(timings.items(), key=lambda kv: (kv[1], kv[0][0], kv[0][1]))[0]
+    """Fastest candidate of {(m, window, threads): seconds}; ties go to the smaller m."""
+    return min(timings.items(), key=lambda kv: (kv[1],) + tuple(kv[0]))[0]
 
 
 def tune(wl, mode=0, steps=4, cache_path=None, time_fn=None):
-    """Returns {'m': m, 'smem_vectors': S, 'timings': {...}} for workload `wl`
-    (synth.Workload).  time_fn(m, S) -> seconds overrides the GPU timing (tests)."""
+    """Returns {'m', 'smem_vectors', 'block_threads', 'timings'} for workload `wl`
+    (synth.Workload).  time_fn(m, S, threads) -> seconds overrides the GPU timing."""
     precision = wl.precision
     if time_fn is None:
         import torch
@@ -59,13 +61,15 @@ def tune(wl, mode=0, steps=4, cache_path=None, time_fn=None):
         return cache[key]
     if time_fn is None:
         time_fn = _gpu_timer(wl, mode, steps)
+    threads = THREAD_CANDIDATES if max(g.N for g in wl.groups) <= 1024 else (0,)
     timings = {}
     for m in M_CANDIDATES:
         for S in WINDOW_CANDIDATES:
-            timings[(m, S)] = time_fn(m, S)
-    m, S = choose(timings)
-    res = {"m": m, "smem_vectors": S,
-           "timings": {f"m{a}_S{b}": t for (a, b), t in timings.items()}}
+            for nt in threads:
+                timings[(m, S, nt)] = time_fn(m, S, nt)
+    m, S, nt = choose(timings)
+    res = {"m": m, "smem_vectors": S, "block_threads": nt,
+           "timings": {f"m{a}_S{b}_t{c}": t for (a, b, c), t in timings.items()}}
     if cache_path:
         cache[key] = res
         save_cache(cache_path, cache)
@@ -83,9 +87,9 @@ def _gpu_timer(wl, mode, steps):
     nmax = max(g.N for g in wl.groups)
     prec = kp.PREC_MIXED if wl.precision == "mixed" else kp.PREC_FP64
 
-    def run(m, S):
+    def run(m, S, nt):
         ctx = kp.Context(max_seeds=max(2 * wl.n_seed_planes, 1), max_a=min(m, 47), max_n=nmax,
-                         precision=prec, smem_vectors=S)
+                         precision=prec, smem_vectors=S, block_threads=nt)
         ss = [x.clone() for x in seeds]
         tt = [x.clone() for x in tgts]
         groups = [(ss[k], tt[k], g.target_seed, g.H, g.W) for k, g in enumerate(wl.groups)]

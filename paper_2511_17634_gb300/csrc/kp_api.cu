@@ -43,7 +43,8 @@ cudaError_t launch_solver(const GmresParams& p, const Shape& sh, bool mixed, cud
 
 kp_status gmres_shape(kp_ctx* c, int nmax, int m, Shape* out, bool mixed, int wmin) {
   Shape sh;
-  if (nmax <= 1024) { sh.ept = 4; sh.nt = 256; }
+  if (nmax <= 1024 && c->opt.block_threads == 128) { sh.ept = 8; sh.nt = 128; }
+  else if (nmax <= 1024) { sh.ept = 4; sh.nt = 256; }
   else if (nmax <= 4096) { sh.ept = 8; sh.nt = 512; }
   else if (mixed) {
     // a cluster of cs CTAs, each holding W/cs whole columns (<= 2048 points)
@@ -62,7 +63,7 @@ kp_status gmres_shape(kp_ctx* c, int nmax, int m, Shape* out, bool mixed, int wm
   int S = c->opt.smem_vectors;
   if (S <= 0) {
     // small systems: leave room for two resident blocks per SM
-    const size_t budget = (npad <= 1024 && !sh.cs) ? c->smem_optin / 2 : c->smem_optin;
+    const size_t budget = (npad <= 1024 && !sh.cs) ? c->smem_optin / 2 : c->smem_optin;   // 2 blocks/SM
     S = budget > fixed ? (int)((budget - fixed) / per) : 0;
   }
   S = std::min(S, m + 1);
@@ -256,6 +257,7 @@ void kp_options_default(kp_options* o) {
   o->precision = KP_PREC_FP64;
   o->smem_vectors = 0;
   o->reorth = 0;
+  o->block_threads = 0;
 }
 
 kp_status kp_create(kp_ctx** out, const kp_options* opt, void* stream) {
@@ -266,7 +268,8 @@ kp_status kp_create(kp_ctx** out, const kp_options* opt, void* stream) {
   if (opt) o = *opt;
   if (o.max_seeds < 1 || o.max_a < 1 || o.max_a > kp::kMaxM || o.max_n < 1 || o.max_n > 16384 ||
       (o.precision != KP_PREC_FP64 && o.precision != KP_PREC_MIXED) ||
-      o.smem_vectors < 0 || (o.reorth != 0 && o.reorth != 1))
+      o.smem_vectors < 0 || (o.reorth != 0 && o.reorth != 1) ||
+      (o.block_threads != 0 && o.block_threads != 128 && o.block_threads != 256))
     return KP_ERR_ARG;
   kp_ctx* c = new (std::nothrow) kp_ctx();
   if (!c) return KP_ERR_OOM;

@@ -126,6 +126,23 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
         }
       }
     };
+    // Arnoldi runs on the shifted operator A - cd I (the constant diagonal
+    // removed): the same Krylov space, with H_A = H + cd I restored in the
+    // Hessenberg column.  A ~ (1/dt) I + small, so A v_j is nearly parallel to
+    // v_j and the unshifted Gram-Schmidt would cancel most of it.
+    auto apply_off = [&](const double* v, double (&out)[EPT]) {
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int pp = tid + k * NT;
+        if (pp < N) {
+          const int pe = min(pp + H, N - 1), pw = max(pp - H, 0);
+          const int pn = min(pp + 1, N - 1), ps = max(pp - 1, 0);
+          out[k] = cE[k] * v[pe] + cW[k] * v[pw] + cN[k] * v[pn] + cS[k] * v[ps];
+        } else {
+          out[k] = 0.0;
+        }
+      }
+    };
     auto bval = [&](int pp) { return (pp < N) ? d.b[pp] * bsc : 0.0; };
 
     // initial guess -> shared memory
@@ -244,6 +261,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
         const double ihn = hn2 > 0.0 ? rsqrt(hn2) : 0.0;
         const double hn = hn2 * ihn;
         const int b = !(hn > 1e-14 * sqrt(sm.sc[2]));
+        sm.Hr[j + j * ld] += cd;                 // H_A = H_{A - cd I} + cd I
         sm.Hr[(j + 1) + j * ld] = hn;
         if (capture && cycle == 0 && j < p.cap_a) {
           for (int i = 0; i <= j + 1; ++i) capH[i + j * (p.cap_a + 1)] = sm.Hr[i + j * ld];
@@ -271,7 +289,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
       };
       for (int j = 0; j < m; ++j) {
         __syncthreads();                       // v_j complete
-        apply(slot(j), w);
+        apply_off(slot(j), w);
         ++steps;
         const int nh = j + 1;
         auto dots = [&](int i) {
@@ -544,6 +562,7 @@ static cudaError_t launch_one(const GmresParams& p, size_t smem, cudaStream_t st
 cudaError_t launch_gmres_fp64(const GmresParams& p, int ept, int nt, size_t smem,
                               cudaStream_t st) {
   if (ept == 4 && nt == 256) return launch_one<4, 256, 2>(p, smem, st);
+  if (ept == 8 && nt == 128) return launch_one<8, 128, 2>(p, smem, st);
   if (ept == 8 && nt == 512) return launch_one<8, 512, 1>(p, smem, st);
   return cudaErrorInvalidValue;
 }

@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
   const double ee = g2 / (8.0 * hh * hh);
   const double cd = 1.0 / d.dt + 2.0 * g2 / (hh * hh);
   const double i2h = 1.0 / (2.0 * hh);
-  const float ccf = (float)cc, cdf = (float)cd;
+  const float ccf = (float)cc;
   const bool capture = p.capV32 != nullptr;
   const int cidx = p.factor ? parity_base + sysi : sysi;
   float* capV = capture ? p.capV32 + (size_t)cidx * (p.cap_a + 1) * p.cap_ld : nullptr;
@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
         const float xW = (msk[k] & 2u) ? (l - H >= 0 ? v[l - H] : vp[l - H + SL]) : 0.f;
         const float xN = (msk[k] & 4u) ? v[l + 1] : 0.f;
         const float xS = (msk[k] & 8u) ? v[l - 1] : 0.f;
-        out[k] = cdf * v[l] - ccf * (xE + xW + xN + xS) + qxf[k] * (xE - xW) + qyf[k] * (xN - xS);
+        out[k] = -ccf * (xE + xW + xN + xS) + qxf[k] * (xE - xW) + qyf[k] * (xN - xS);
       }
     }
   };
@@ -277,6 +277,7 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
       const double ihn = hn2 > 0.0 ? rsqrt(hn2) : 0.0;
       const double hn = hn2 * ihn;
       const int b = !(hn > 1e-7 * sqrt(sc[2]));
+      Hr[j + j * ld] += cd;                       // H_A = H_(A - cd I) + cd I
       Hr[(j + 1) + j * ld] = hn;
       if (capture && first && j < p.cap_a && rank == 0) {
         for (int i = 0; i <= j + 1; ++i) capH[i + j * (p.cap_a + 1)] = Hr[i + j * ld];

@@ -290,12 +290,13 @@ __device__ __forceinline__ double cross_warp(const double* red, int i) {
 
 // FP64 flops per unknown of GMRES(m) with CGS2 as implemented here, for k
 // Arnoldi steps: 14 to start (residual, two norms); per cycle of L steps
-// sum_{j<L} (9 stencil + 8(j+1) Gram-Schmidt + 5 norm/scale) + 2L update + 12 residual.
+// sum_{j<L} (7 shifted stencil + 8(j+1) Gram-Schmidt + 5 norm/scale)
+// + 2L update + 12 residual.
 __host__ __device__ __forceinline__ unsigned long long gmres_flops(int k, int m) {
   const unsigned long long full = (unsigned long long)(k / m), rem = (unsigned long long)(k % m);
   const unsigned long long M = (unsigned long long)m;
-  unsigned long long f = 14ull + full * (4ull * M * M + 20ull * M + 12ull);
-  if (rem) f += 4ull * rem * rem + 20ull * rem + 12ull;
+  unsigned long long f = 14ull + full * (4ull * M * M + 18ull * M + 12ull);
+  if (rem) f += 4ull * rem * rem + 18ull * rem + 12ull;
   return f;
 }
 

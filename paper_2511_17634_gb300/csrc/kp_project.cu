@@ -163,6 +163,7 @@ cudaError_t launch_factor(const FactorParams& p, cudaStream_t st) {
 
 cudaError_t launch_project_fp64(const ProjParams& p, int ept, int nt, cudaStream_t st) {
   if (ept == 4 && nt == 256) project_fp64_kernel<4, 256><<<p.nt, 256, 0, st>>>(p);
+  else if (ept == 8 && nt == 128) project_fp64_kernel<8, 128><<<p.nt, 128, 0, st>>>(p);
   else if (ept == 8 && nt == 512) project_fp64_kernel<8, 512><<<p.nt, 512, 0, st>>>(p);
   else if (ept == 16 && nt == 1024) project_fp64_kernel<16, 1024><<<p.nt, 1024, 0, st>>>(p);
   else return cudaErrorInvalidValue;

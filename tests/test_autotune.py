@@ -3,23 +3,24 @@ from paper_2511_17634_gb300 import autotune, synth
 
 
 def test_choose_prefers_fastest_then_smaller_m():
-    t = {(20, 0): 2.0, (30, 0): 1.0, (40, 0): 1.0, (60, 6): 3.0}
-    assert autotune.choose(t) == (30, 0)
+    t = {(20, 0, 256): 2.0, (30, 0, 256): 1.0, (40, 0, 128): 1.0, (60, 6, 256): 3.0}
+    assert autotune.choose(t) == (30, 0, 256)
 
 
 def test_tune_times_every_candidate_and_caches(tmp_path):
     wl = synth.config(1, T=4)
     calls = []
 
-    def fake(m, S):
-        calls.append((m, S))
-        return abs(m - 40) + 0.1 * S
+    def fake(m, S, nt):
+        calls.append((m, S, nt))
+        return abs(m - 40) + 0.1 * S + (0.01 if nt == 256 else 0.0)
 
     path = str(tmp_path / "tune.json")
     r = autotune.tune(wl, cache_path=path, time_fn=fake)
-    assert r["m"] == 40 and r["smem_vectors"] == 0
-    assert len(calls) == len(autotune.M_CANDIDATES) * len(autotune.WINDOW_CANDIDATES)
-    r2 = autotune.tune(wl, cache_path=path, time_fn=lambda m, S: 1 / 0)   # served from the cache
+    assert r["m"] == 40 and r["smem_vectors"] == 0 and r["block_threads"] == 128
+    assert len(calls) == (len(autotune.M_CANDIDATES) * len(autotune.WINDOW_CANDIDATES)
+                          * len(autotune.THREAD_CANDIDATES))
+    r2 = autotune.tune(wl, cache_path=path, time_fn=lambda m, S, nt: 1 / 0)   # from the cache
     assert r2["m"] == 40
 
 
@@ -33,7 +34,8 @@ def test_tune_on_gpu_picks_a_candidate(tmp_path):
     wl = synth.config(2, T=1000, ntargets=16)
     r = autotune.tune(wl, steps=2, cache_path=str(tmp_path / "t.json"))
     assert r["m"] in autotune.M_CANDIDATES and r["smem_vectors"] in autotune.WINDOW_CANDIDATES
-    assert len(r["timings"]) == len(autotune.M_CANDIDATES) * len(autotune.WINDOW_CANDIDATES)
+    assert len(r["timings"]) == (len(autotune.M_CANDIDATES) * len(autotune.WINDOW_CANDIDATES)
+                                 * len(autotune.THREAD_CANDIDATES))
 
 
 test_tune_on_gpu_picks_a_candidate = __import__("pytest").mark.gpu(test_tune_on_gpu_picks_a_candidate)
