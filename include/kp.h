@@ -219,6 +219,41 @@ kp_status kp_refine_static(int nsys, const kp_op* ops, const double* const* b, d
 kp_status kp_project_gemm_bf16(kp_ctx* ctx, int nt, int nv, int K, const void* B, int ldb,
                                const void* V, int ldv, float* C, int ldc);
 
+/* r_k = b_k - A_k x_k (FP64), e.g. the residual of an initial guess before
+ * projecting it (Sec. 3, Phase 2 in residual form). */
+kp_status kp_residual(kp_ctx* ctx, int nsys, const kp_op* ops, const double* const* b,
+                      const double* const* x, double* const* r);
+
+/* ------------------------------------------------------------------------
+ * Learned initial guess (not in the paper): a 3x3 convolutional network with
+ * zero padding and ReLU between layers, trained on the GPU with this
+ * library's kernels -- every convolution, its input gradient and its weight
+ * gradient is a tcgen05 GEMM over im2col operands (BF16 inputs, FP32
+ * accumulation); biases, ReLU, MSE loss and Adam (FP32 master weights, BF16
+ * copies) are elementwise kernels.  Activations are FP32 planes
+ * [batch][channels][H*W] in the solver's vector order.
+ * Parameters (flat FP32): for each layer l, W_l [c_{l+1}][c_l][3][3] (tap
+ * (di,dj) at index (di+1)*3 + (dj+1), di along x/columns, dj along y/rows),
+ * then b_l [c_{l+1}].
+ * ------------------------------------------------------------------------ */
+typedef struct kp_cnn kp_cnn;
+/* channels[0..nlayers]: c_0 (inputs) ... c_L (outputs), each 1..32. */
+kp_status kp_cnn_create(kp_ctx* ctx, int H, int W, int max_batch, int nlayers,
+                        const int* channels, kp_cnn** cnn);
+kp_status kp_cnn_destroy(kp_cnn* cnn);
+int kp_cnn_num_params(const kp_cnn* cnn);
+kp_status kp_cnn_set_params(kp_cnn* cnn, const float* host_params);   /* resets Adam state */
+kp_status kp_cnn_get_params(kp_cnn* cnn, float* host_params);
+/* out (device [B][c_L][H*W]) = network(in (device [B][c_0][H*W])). */
+kp_status kp_cnn_forward(kp_cnn* cnn, int B, const float* in, float* out);
+/* Loss = mean over B*H*W of (out - target)^2 (c_L = 1); gradients of the loss
+ * (device [num_params], may be NULL) and the loss (host, may be NULL). */
+kp_status kp_cnn_gradients(kp_cnn* cnn, int B, const float* in, const float* target,
+                           float* grads, double* loss);
+/* One Adam step (Kingma & Ba 2015) on that loss; t = 1, 2, ... */
+kp_status kp_cnn_train_step(kp_cnn* cnn, int B, const float* in, const float* target, float lr,
+                            float beta1, float beta2, float eps, int t, double* loss);
+
 /* Inspect a stored basis (tests, diagnostics).  a_out, has_next_out, host.
  * V (device, N*(a+1) doubles, column k = v_{k+1}) and Hbar (host, (a+1)*a
  * doubles column-major, unrotated) may be NULL. */

@@ -385,6 +385,24 @@ kp_status kp_rhs(kp_ctx* c, int nsys, const kp_op* ops, const double* const* mpr
   return e == cudaSuccess ? KP_OK : kp::cuda_error(c, e, "rhs launch");
 }
 
+kp_status kp_residual(kp_ctx* c, int nsys, const kp_op* ops, const double* const* b,
+                      const double* const* x, double* const* r) {
+  if (!c) return KP_ERR_ARG;
+  if (!b || !x || !r) return nsys ? kp::set_error(c, KP_ERR_ARG, "b, x or r is NULL") : KP_OK;
+  kp_status st = kp_apply(c, nsys, ops, x, r);             // r = A x
+  if (st != KP_OK || nsys == 0) return st;
+  std::vector<SysDesc> h(nsys);
+  for (int k = 0; k < nsys; ++k) {
+    if (!b[k]) return kp::set_error(c, KP_ERR_ARG, "system %d: NULL vector", k);
+    h[k] = make_desc(ops[k], b[k], r[k], 0);
+  }
+  SysDesc* dd;
+  st = upload(c, h, &dd);
+  if (st != KP_OK) return st;
+  cudaError_t e = kp::launch_apply(dd, nsys, 2, c->stream);    // r = b - r
+  return e == cudaSuccess ? KP_OK : kp::cuda_error(c, e, "residual launch");
+}
+
 kp_status kp_seed_solve(kp_ctx* c, int nsys, const kp_op* ops, const double* const* b,
                         double* const* x, double tol, int m, int maxit, kp_info* info) {
   if (!c) return KP_ERR_ARG;
@@ -491,6 +509,9 @@ kp_status kp_project_gemm_bf16(kp_ctx* c, int nt, int nv, int K, const void* B, 
     tiles[t].crow0 = 128 * t;
     tiles[t].count = std::min(128, nt - 128 * t);
     tiles[t].nv = nv;
+    tiles[t].ccol0 = 0;
+    tiles[t].kc0 = tiles[t].kc1 = 0;
+    tiles[t].atomic = 0;
   }
   cudaError_t e = grow(&c->d_tiles, &c->d_tiles_bytes, tiles.size() * sizeof(kp::ProjTile));
   if (e == cudaSuccess && !c->d_err) {

@@ -1,0 +1,444 @@
+// kp_cnn.cu -- the learned initial guess: a small 3x3 convolutional network
+// trained on the GPU by this library's own forward and backward kernels.
+//
+// Every convolution is an implicit GEMM on the tcgen05 tensor cores (the
+// projection GEMM of kp_proj_tc.cu, BF16 operands, FP32 accumulation):
+//   forward      Z[p][co]   = sum_k Xcol[p][k]  W[co][k]        k = c*9 + tap
+//   input grad   dX[p][c]   = sum_k dZcol[p][k] W2[c][k]        k = co*9 + tap
+//   weight grad  dW[co][k]  = sum_p dZt[co][p]  XcolT[k][p]     (split over p)
+// with im2col gathers (zero padding at the grid border) writing the BF16
+// operands.  Biases, ReLU, the MSE loss and Adam (FP32 master weights, BF16
+// copies for the tensor cores) are elementwise kernels.  Activations are FP32
+// planes [B][C][H*W] in the solver's y-fastest order.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "kp.h"
+#include "kp_ctx.h"
+#include "kp_internal.cuh"
+
+namespace {
+
+constexpr int kMaxLayers = 8;
+
+__device__ __forceinline__ int tap_offset(int tap, int H) {   // (di, dj) in {-1,0,1}^2
+  const int di = tap / 3 - 1, dj = tap % 3 - 1;
+  return di * H + dj;
+}
+
+__device__ __forceinline__ bool tap_inside(int pp, int tap, int H, int W, int sign) {
+  const int i = pp / H, j = pp - i * H;
+  const int di = sign * (tap / 3 - 1), dj = sign * (tap % 3 - 1);
+  return (unsigned)(i + di) < (unsigned)W && (unsigned)(j + dj) < (unsigned)H;
+}
+
+// Xcol[b*P + p][c*9 + tap] = X[b][c][p + sign*off(tap)] (0 outside the grid)
+__global__ void im2col_kernel(const float* X, __nv_bfloat16* Xcol, int ld, int C, int H, int W, int sign) {
+  const int P = H * W;
+  const size_t row = blockIdx.x;                 // b*P + p
+  const int b = (int)(row / P), p = (int)(row - (size_t)b * P);
+  for (int k = threadIdx.x; k < ld; k += blockDim.x) {
+    float v = 0.f;
+    if (k < 9 * C) {
+      const int c = k / 9, tap = k - c * 9;
+      if (tap_inside(p, tap, H, W, sign)) v = X[((size_t)b * C + c) * P + p + sign * tap_offset(tap, H)];
+    }
+    Xcol[row * ld + k] = __float2bfloat16_rn(v);
+  }
+}
+
+// XcolT[c*9 + tap][b*P + p] = X[b][c][p + off(tap)]
+__global__ void im2colT_kernel(const float* X, __nv_bfloat16* XcolT, size_t ld, int C, int H, int W, int B) {
+  const int P = H * W;
+  const int k = blockIdx.y;                      // c*9 + tap
+  const int c = k / 9, tap = k - c * 9;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < (size_t)B * P;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(q / P), p = (int)(q - (size_t)b * P);
+    float v = 0.f;
+    if (tap_inside(p, tap, H, W, 1)) v = X[((size_t)b * C + c) * P + p + tap_offset(tap, H)];
+    XcolT[(size_t)k * ld + q] = __float2bfloat16_rn(v);
+  }
+}
+
+// dZt[co][b*P + p] = dZ[b][co][p]
+__global__ void planes_to_rows_kernel(const float* dZ, __nv_bfloat16* dZt, size_t ld, int C, int P, int B) {
+  const int co = blockIdx.y;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < (size_t)B * P;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(q / P), p = (int)(q - (size_t)b * P);
+    dZt[(size_t)co * ld + q] = __float2bfloat16_rn(dZ[((size_t)b * C + co) * P + p]);
+  }
+}
+
+// Y[b][co][p] = act(Cm[b*P + p][co] + bias[co])
+__global__ void fwd_epilogue_kernel(const float* Cm, int ldc, const float* bias, float* Y, int Cout, int P,
+                                    int B, int relu) {
+  const size_t n = (size_t)B * Cout * P;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(q % P);
+    const size_t bc = q / P;
+    const int co = (int)(bc % Cout), b = (int)(bc / Cout);
+    float v = Cm[((size_t)b * P + p) * ldc + co] + bias[co];
+    Y[q] = relu ? fmaxf(v, 0.f) : v;
+  }
+}
+
+// dZprev[b][c][p] = (Yprev > 0) * Cm[b*P + p][c]  (input gradient through ReLU)
+__global__ void dgrad_epilogue_kernel(const float* Cm, int ldc, const float* Yprev, float* dZprev, int Cin,
+                                      int P, int B) {
+  const size_t n = (size_t)B * Cin * P;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(q % P);
+    const size_t bc = q / P;
+    const int c = (int)(bc % Cin), b = (int)(bc / Cin);
+    dZprev[q] = Yprev[q] > 0.f ? Cm[((size_t)b * P + p) * ldc + c] : 0.f;
+  }
+}
+
+// MSE loss over B*P values and its gradient 2 (y - t) / (B P)
+__global__ void mse_kernel(const float* y, const float* t, float* dz, size_t n, double* loss) {
+  __shared__ double red[256];
+  double s = 0.0;
+  const float sc = 2.f / (float)n;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+    const float d = y[q] - t[q];
+    dz[q] = sc * d;
+    s += (double)d * d;
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(loss, red[0] / (double)n);
+}
+
+// db[co] += sum over b, p of dZ[b][co][p]
+__global__ void bias_grad_kernel(const float* dZ, float* db, int Cout, int P, int B) {
+  __shared__ float red[256];
+  const int co = blockIdx.y;
+  float s = 0.f;
+  for (size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x; q < (size_t)B * P;
+       q += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(q / P), p = (int)(q - (size_t)b * P);
+    s += dZ[((size_t)b * Cout + co) * P + p];
+  }
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) atomicAdd(db + co, red[0]);
+}
+
+// Adam on the FP32 master parameters (Kingma & Ba 2015)
+__global__ void adam_kernel(float* w, const float* g, float* m, float* v, int n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+    const float gq = g[q];
+    const float mq = b1 * m[q] + (1.f - b1) * gq;
+    const float vq = b2 * v[q] + (1.f - b2) * gq * gq;
+    m[q] = mq;
+    v[q] = vq;
+    w[q] -= lr * (mq / c1) / (sqrtf(vq / c2) + eps);
+  }
+}
+
+// BF16 tensor-core copies of layer weights: Wb[co][k] (k = c*9+tap) and the
+// transposed W2b[c][k'] (k' = co*9+tap) used by the input gradient
+__global__ void weights_bf16_kernel(const float* Wl, __nv_bfloat16* Wb, int ldw, __nv_bfloat16* W2b, int ldw2,
+                                    int Cin, int Cout) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < Cout * Cin * 9; q += gridDim.x * blockDim.x) {
+    const int co = q / (Cin * 9), k = q - co * Cin * 9;
+    const int c = k / 9, tap = k - c * 9;
+    const __nv_bfloat16 v = __float2bfloat16_rn(Wl[q]);
+    Wb[(size_t)co * ldw + k] = v;
+    W2b[(size_t)c * ldw2 + co * 9 + tap] = v;
+  }
+}
+
+size_t up8(size_t x) { return (x + 7) / 8 * 8; }
+
+}  // namespace
+
+struct kp_cnn {
+  kp_ctx* ctx = nullptr;
+  int H = 0, W = 0, P = 0, maxB = 0, L = 0;
+  int ch[kMaxLayers + 1] = {0};
+  std::vector<size_t> woff, boff;      // offsets of W[l] and b[l] in the flat parameter array
+  int nparams = 0;
+  float* params = nullptr;             // FP32 master [nparams]
+  float* grads = nullptr;
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  __nv_bfloat16* wb = nullptr;         // per layer Wb then W2b, packed
+  std::vector<size_t> wb_off, w2b_off;
+  float* act = nullptr;                // Y[l] for l = 1..L, packed
+  std::vector<size_t> act_off;
+  float* dz = nullptr;                 // [maxB][Cmax][P]
+  float* dz2 = nullptr;
+  __nv_bfloat16* col = nullptr;        // im2col rows [maxB*P][ldmax]
+  __nv_bfloat16* colT = nullptr;       // [9*Cmax][maxB*P]
+  __nv_bfloat16* rows = nullptr;       // [Cmax][maxB*P]
+  float* cm = nullptr;                 // GEMM output [maxB*P][48]
+  kp::ProjTile* tiles = nullptr;
+  size_t tiles_cap = 0;
+  double* d_loss = nullptr;
+  int* d_err = nullptr;
+  int Cmax = 0;
+};
+
+namespace {
+
+kp_status gemm(kp_cnn* n, const __nv_bfloat16* Bop, int brows, int K, size_t ldb,
+               const __nv_bfloat16* Vop, int vrows, size_t ldv, float* C, int ldc,
+               const std::vector<kp::ProjTile>& tiles) {
+  kp_ctx* c = n->ctx;
+  alignas(64) CUtensorMap mb, mv;
+  cudaError_t e = kp::make_bf16_map(&mb, Bop, brows, K, (int)ldb, 128);
+  if (e == cudaSuccess) e = kp::make_bf16_map(&mv, Vop, vrows, K, (int)ldv, 48);
+  if (e == cudaSuccess && tiles.size() > n->tiles_cap) {
+    cudaFree(n->tiles);
+    n->tiles = nullptr;
+    e = cudaMalloc((void**)&n->tiles, tiles.size() * sizeof(kp::ProjTile));
+    n->tiles_cap = e == cudaSuccess ? tiles.size() : 0;
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(n->tiles, tiles.data(), tiles.size() * sizeof(kp::ProjTile), cudaMemcpyHostToDevice,
+                        c->stream);
+  if (e == cudaSuccess)
+    e = kp::launch_proj_gemm_bf16(mb, mv, n->tiles, (int)tiles.size(), K, C, ldc, n->d_err,
+                                  std::min((int)tiles.size(), c->sms), c->stream);
+  return e == cudaSuccess ? KP_OK : kp::cuda_error(c, e, "CNN GEMM");
+}
+
+// Tiles of 128 rows of the B operand against one 48-row tile of V.
+std::vector<kp::ProjTile> row_tiles(int rows, int nv) {
+  std::vector<kp::ProjTile> t;
+  for (int r = 0; r < rows; r += 128) {
+    kp::ProjTile x{};
+    x.row0 = r; x.vrow0 = 0; x.crow0 = r; x.count = std::min(128, rows - r); x.nv = nv;
+    t.push_back(x);
+  }
+  return t;
+}
+
+int grid_for(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 4096); }
+
+kp_status forward_impl(kp_cnn* n, int B, const float* in) {
+  cudaStream_t st = n->ctx->stream;
+  const int P = n->P;
+  const float* X = in;
+  for (int l = 0; l < n->L; ++l) {
+    const int cin = n->ch[l], cout = n->ch[l + 1];
+    const size_t ld = up8(9 * cin);
+    im2col_kernel<<<B * P, 64, 0, st>>>(X, n->col, (int)ld, cin, n->H, n->W, 1);
+    kp_status s = gemm(n, n->col, B * P, 9 * cin, ld, n->wb + n->wb_off[l], cout, ld, n->cm, 48,
+                       row_tiles(B * P, cout));
+    if (s != KP_OK) return s;
+    float* Y = n->act + n->act_off[l];
+    fwd_epilogue_kernel<<<grid_for((size_t)B * cout * P), 256, 0, st>>>(
+        n->cm, 48, n->params + n->boff[l], Y, cout, P, B, l + 1 < n->L);
+    X = Y;
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN forward");
+}
+
+kp_status refresh_bf16(kp_cnn* n) {
+  cudaStream_t st = n->ctx->stream;
+  for (int l = 0; l < n->L; ++l) {
+    const int cin = n->ch[l], cout = n->ch[l + 1];
+    weights_bf16_kernel<<<grid_for((size_t)cout * cin * 9), 256, 0, st>>>(
+        n->params + n->woff[l], n->wb + n->wb_off[l], (int)up8(9 * cin), n->wb + n->w2b_off[l],
+        (int)up8(9 * cout), cin, cout);
+  }
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN weights");
+}
+
+// forward + MSE + backward into n->grads; loss on the host if wanted
+kp_status backward_impl(kp_cnn* n, int B, const float* in, const float* target, double* loss) {
+  cudaStream_t st = n->ctx->stream;
+  const int P = n->P;
+  kp_status s = forward_impl(n, B, in);
+  if (s != KP_OK) return s;
+  cudaError_t e = cudaMemsetAsync(n->grads, 0, (size_t)n->nparams * sizeof(float), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->d_loss, 0, sizeof(double), st);
+  if (e != cudaSuccess) return kp::cuda_error(n->ctx, e, "CNN backward");
+  const size_t nout = (size_t)B * P;
+  mse_kernel<<<grid_for(nout), 256, 0, st>>>(n->act + n->act_off[n->L - 1], target, n->dz, nout, n->d_loss);
+  float* dZ = n->dz;
+  float* dZo = n->dz2;
+  const size_t ldp = up8((size_t)B * P);
+  for (int l = n->L - 1; l >= 0; --l) {
+    const int cin = n->ch[l], cout = n->ch[l + 1];
+    const float* X = l == 0 ? in : n->act + n->act_off[l - 1];
+    // bias gradient
+    bias_grad_kernel<<<dim3(64, cout), 256, 0, st>>>(dZ, n->grads + n->boff[l], cout, P, B);
+    // weight gradient: dW[co][k] = sum_p dZt[co][p] XcolT[k][p], split over p
+    im2colT_kernel<<<dim3(grid_for((size_t)B * P), 9 * cin), 256, 0, st>>>(X, n->colT, ldp, cin, n->H, n->W, B);
+    planes_to_rows_kernel<<<dim3(grid_for((size_t)B * P), cout), 256, 0, st>>>(dZ, n->rows, ldp, cout, P, B);
+    {
+      std::vector<kp::ProjTile> tl;
+      const int nk = (int)((B * (size_t)P + 63) / 64);
+      const int ntn = (9 * cin + 47) / 48;
+      const int splits = std::max(1, std::min(nk, (2 * n->ctx->sms) / std::max(ntn, 1)));
+      for (int tn = 0; tn < ntn; ++tn)
+        for (int sp = 0; sp < splits; ++sp) {
+          kp::ProjTile t{};
+          t.row0 = 0; t.vrow0 = 48 * tn; t.crow0 = 0; t.count = cout;
+          t.nv = std::min(48, 9 * cin - 48 * tn); t.ccol0 = 48 * tn;
+          t.kc0 = (int)((long long)nk * sp / splits); t.kc1 = (int)((long long)nk * (sp + 1) / splits);
+          t.atomic = 1;
+          if (t.kc1 > t.kc0) tl.push_back(t);
+        }
+      s = gemm(n, n->rows, cout, B * P, ldp, n->colT, 9 * cin, ldp, n->grads + n->woff[l], 9 * cin, tl);
+      if (s != KP_OK) return s;
+    }
+    if (l == 0) break;
+    // input gradient through the previous layer's ReLU
+    const size_t ld2 = up8(9 * cout);
+    im2col_kernel<<<B * P, 64, 0, st>>>(dZ, n->col, (int)ld2, cout, n->H, n->W, -1);
+    s = gemm(n, n->col, B * P, 9 * cout, ld2, n->wb + n->w2b_off[l], cin, ld2, n->cm, 48, row_tiles(B * P, cin));
+    if (s != KP_OK) return s;
+    dgrad_epilogue_kernel<<<grid_for((size_t)B * cin * P), 256, 0, st>>>(n->cm, 48, n->act + n->act_off[l - 1],
+                                                                          dZo, cin, P, B);
+    std::swap(dZ, dZo);
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess && loss) {
+    e = cudaMemcpyAsync(loss, n->d_loss, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  }
+  return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN backward");
+}
+
+}  // namespace
+
+extern "C" {
+
+kp_status kp_cnn_destroy(kp_cnn* n) {
+  if (!n) return KP_OK;
+  if (n->ctx) cudaStreamSynchronize(n->ctx->stream);
+  cudaFree(n->params); cudaFree(n->grads); cudaFree(n->adam_m); cudaFree(n->adam_v); cudaFree(n->wb);
+  cudaFree(n->act); cudaFree(n->dz); cudaFree(n->dz2); cudaFree(n->col); cudaFree(n->colT); cudaFree(n->rows);
+  cudaFree(n->cm); cudaFree(n->tiles); cudaFree(n->d_loss); cudaFree(n->d_err);
+  delete n;
+  return KP_OK;
+}
+
+kp_status kp_cnn_create(kp_ctx* c, int H, int W, int max_batch, int nlayers, const int* channels,
+                        kp_cnn** out) {
+  if (!c) return KP_ERR_ARG;
+  if (!out || H < 1 || W < 1 || max_batch < 1 || nlayers < 1 || nlayers > kMaxLayers || !channels)
+    return kp::set_error(c, KP_ERR_ARG, "CNN: bad sizes");
+  for (int l = 0; l <= nlayers; ++l)
+    if (channels[l] < 1 || channels[l] > 32) return kp::set_error(c, KP_ERR_ARG, "CNN: 1..32 channels per layer");
+  if ((size_t)max_batch * H * W > (1u << 30)) return kp::set_error(c, KP_ERR_ARG, "CNN: batch too large");
+  kp_cnn* n = new kp_cnn();
+  n->ctx = c; n->H = H; n->W = W; n->P = H * W; n->maxB = max_batch; n->L = nlayers;
+  for (int l = 0; l <= nlayers; ++l) { n->ch[l] = channels[l]; n->Cmax = std::max(n->Cmax, channels[l]); }
+  size_t np = 0, nwb = 0, nact = 0;
+  for (int l = 0; l < nlayers; ++l) {
+    const int cin = n->ch[l], cout = n->ch[l + 1];
+    n->woff.push_back(np); np += (size_t)cout * cin * 9;
+    n->boff.push_back(np); np += cout;
+    n->wb_off.push_back(nwb); nwb += (size_t)cout * up8(9 * cin);
+    nwb = up8(nwb);
+    n->w2b_off.push_back(nwb); nwb += (size_t)cin * up8(9 * cout);
+    nwb = up8(nwb);
+    n->act_off.push_back(nact); nact += (size_t)max_batch * cout * n->P;
+  }
+  n->nparams = (int)np;
+  const size_t BP = (size_t)max_batch * n->P;
+  const size_t ldmax = up8(9 * n->Cmax);
+  cudaError_t e = cudaMalloc((void**)&n->params, np * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->grads, np * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->adam_m, np * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->adam_v, np * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->wb, nwb * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMemset(n->wb, 0, nwb * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->act, nact * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->dz, BP * n->Cmax * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->dz2, BP * n->Cmax * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->col, BP * ldmax * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->colT, 9 * (size_t)n->Cmax * up8(BP) * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->rows, (size_t)n->Cmax * up8(BP) * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->cm, BP * 48 * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->d_loss, sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->d_err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(n->d_err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(n->params, 0, np * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(n->adam_m, 0, np * sizeof(float));
+  if (e == cudaSuccess) e = cudaMemset(n->adam_v, 0, np * sizeof(float));
+  if (e != cudaSuccess) {
+    kp_status r = kp::cuda_error(c, e, "CNN allocation");
+    kp_cnn_destroy(n);
+    return r;
+  }
+  *out = n;
+  return KP_OK;
+}
+
+int kp_cnn_num_params(const kp_cnn* n) { return n ? n->nparams : 0; }
+
+kp_status kp_cnn_set_params(kp_cnn* n, const float* host) {
+  if (!n || !host) return KP_ERR_ARG;
+  cudaError_t e = cudaMemcpyAsync(n->params, host, (size_t)n->nparams * sizeof(float), cudaMemcpyHostToDevice,
+                                  n->ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->adam_m, 0, (size_t)n->nparams * sizeof(float), n->ctx->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(n->adam_v, 0, (size_t)n->nparams * sizeof(float), n->ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(n->ctx->stream);
+  if (e != cudaSuccess) return kp::cuda_error(n->ctx, e, "CNN parameters");
+  return refresh_bf16(n);
+}
+
+kp_status kp_cnn_get_params(kp_cnn* n, float* host) {
+  if (!n || !host) return KP_ERR_ARG;
+  cudaError_t e = cudaMemcpyAsync(host, n->params, (size_t)n->nparams * sizeof(float), cudaMemcpyDeviceToHost,
+                                  n->ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(n->ctx->stream);
+  return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN parameters");
+}
+
+kp_status kp_cnn_forward(kp_cnn* n, int B, const float* in, float* out) {
+  if (!n || B < 1 || B > n->maxB || !in || !out) return n ? kp::set_error(n->ctx, KP_ERR_ARG, "CNN forward: bad batch") : KP_ERR_ARG;
+  kp_status s = forward_impl(n, B, in);
+  if (s != KP_OK) return s;
+  cudaError_t e = cudaMemcpyAsync(out, n->act + n->act_off[n->L - 1], (size_t)B * n->P * n->ch[n->L] * sizeof(float),
+                                  cudaMemcpyDeviceToDevice, n->ctx->stream);
+  return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN forward");
+}
+
+kp_status kp_cnn_gradients(kp_cnn* n, int B, const float* in, const float* target, float* grads, double* loss) {
+  if (!n || B < 1 || B > n->maxB || !in || !target) return n ? kp::set_error(n->ctx, KP_ERR_ARG, "CNN: bad batch") : KP_ERR_ARG;
+  if (n->ch[n->L] != 1) return kp::set_error(n->ctx, KP_ERR_UNSUPPORTED, "CNN: loss needs one output channel");
+  kp_status s = backward_impl(n, B, in, target, loss);
+  if (s != KP_OK || !grads) return s;
+  cudaError_t e = cudaMemcpyAsync(grads, n->grads, (size_t)n->nparams * sizeof(float), cudaMemcpyDeviceToDevice,
+                                  n->ctx->stream);
+  return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN gradients");
+}
+
+kp_status kp_cnn_train_step(kp_cnn* n, int B, const float* in, const float* target, float lr, float beta1,
+                            float beta2, float eps, int t, double* loss) {
+  if (!n || t < 1) return n ? kp::set_error(n->ctx, KP_ERR_ARG, "CNN: Adam step t >= 1") : KP_ERR_ARG;
+  kp_status s = kp_cnn_gradients(n, B, in, target, nullptr, loss);
+  if (s != KP_OK) return s;
+  const float c1 = 1.f - powf(beta1, (float)t), c2 = 1.f - powf(beta2, (float)t);
+  adam_kernel<<<grid_for(n->nparams), 256, 0, n->ctx->stream>>>(n->params, n->grads, n->adam_m, n->adam_v,
+                                                                 n->nparams, lr, beta1, beta2, eps, c1, c2);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return kp::cuda_error(n->ctx, e, "CNN Adam");
+  return refresh_bf16(n);
+}
+
+}  // extern "C"

@@ -505,6 +505,10 @@ __global__ void apply_rhs_kernel(const SysDesc* sys, int nsys, int mode) {
   const double i2h = 1.0 / (2.0 * hh);
   for (int pp = threadIdx.x; pp < N; pp += blockDim.x) {
     const int i = pp / H, j = pp - i * H;
+    if (mode == 2) {                      // x <- b - x
+      d.x[pp] = d.b[pp] - d.x[pp];
+      continue;
+    }
     if (mode == 1) {
       const double fE = (d.fx && i + 1 < W) ? d.fx[pp + H] : 0.0;
       const double fW = (d.fx && i > 0) ? d.fx[pp - H] : 0.0;

@@ -383,6 +383,9 @@ __device__ __forceinline__ void solve_projected_warp(double* c, int a, int nrot,
 // crow0 + (0..count), columns 0..nv.
 struct ProjTile {
   int row0, vrow0, crow0, count, nv;
+  int ccol0;        // first C column of this tile
+  int kc0, kc1;     // K range in 64-element chunks; kc1 == 0: the whole K
+  int atomic;       // accumulate into C with atomicAdd (split K) instead of storing
 };
 
 // Launchers (defined in the .cu files; return a cudaError_t of the launch).

@@ -380,6 +380,9 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
             t.crow0 = P->tgt_base[gi] + q;
             t.count = std::min(128, end - q);
             t.nv = kp::kVbRows;
+            t.ccol0 = 0;
+            t.kc0 = t.kc1 = 0;
+            t.atomic = 0;
             tl[par].push_back(t);
           }
         k = end;

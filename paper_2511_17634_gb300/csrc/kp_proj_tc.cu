@@ -160,26 +160,28 @@ proj_gemm_bf16_kernel(const __grid_constant__ CUtensorMap mapB, const __grid_con
   const uint32_t tmem = sm.tmem_base;
   constexpr uint32_t idesc = idesc_bf16_f32(kTileM, kTileN);
   uint32_t issued = 0;                            // TMA stage loads issued (producer thread)
+  uint32_t base_phase = 0;                        // K chunks of earlier tiles of this CTA
 
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const ProjTile tile = tiles[t];
     const int round = (t - (int)blockIdx.x) / (int)gridDim.x;   // tiles already done by this CTA
-    const uint32_t base_phase = (uint32_t)(round * nk);
+    const int kc0 = tile.kc1 > 0 ? tile.kc0 : 0;
+    const int nkt = tile.kc1 > 0 ? tile.kc1 - tile.kc0 : nk;
     if (warp == 0 && lane == 0) {
       // TMA producer
-      for (int kc = 0; kc < nk; ++kc) {
+      for (int kc = 0; kc < nkt; ++kc) {
         const uint32_t it = base_phase + kc;
         const int s = it % kStages;
         const uint32_t use = it / kStages;
         if (use > 0 && !mbar_wait(&sm.empty[s], (use - 1) & 1)) { sm.abort = 1; break; }
         mbar_expect_tx(&sm.full[s], kBytesA + kBytesB);
-        tma_load_2d(sm.A[s], &mapB, kc * kTileK, tile.row0, &sm.full[s]);
-        tma_load_2d(sm.B[s], &mapV, kc * kTileK, tile.vrow0, &sm.full[s]);
+        tma_load_2d(sm.A[s], &mapB, (kc0 + kc) * kTileK, tile.row0, &sm.full[s]);
+        tma_load_2d(sm.B[s], &mapV, (kc0 + kc) * kTileK, tile.vrow0, &sm.full[s]);
         issued = it + 1;
       }
     } else if (warp == 1 && lane == 0) {
       // MMA issuer
-      for (int kc = 0; kc < nk; ++kc) {
+      for (int kc = 0; kc < nkt; ++kc) {
         const uint32_t it = base_phase + kc;
         const int s = it % kStages;
         const uint32_t use = it / kStages;
@@ -210,13 +212,18 @@ proj_gemm_bf16_kernel(const __grid_constant__ CUtensorMap mapB, const __grid_con
       float v[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
       if (r < tile.count) {
+        float* crow = C + (size_t)(tile.crow0 + r) * ldc + tile.ccol0 + c0;
 #pragma unroll
         for (int i = 0; i < 16; ++i)
-          if (c0 + i < tile.nv) C[(size_t)(tile.crow0 + r) * ldc + c0 + i] = v[i];
+          if (c0 + i < tile.nv) {
+            if (tile.atomic) atomicAdd(crow + i, v[i]);
+            else crow[i] = v[i];
+          }
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    base_phase += (uint32_t)nkt;
   }
   __syncthreads();
   if (sm.abort && warp == 0 && lane == 0) {

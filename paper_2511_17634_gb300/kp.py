@@ -66,9 +66,21 @@ def lib():
         L.kp_project_targets_multi.argtypes = [vp, i, i, vp, vp, vp, vp]
         L.kp_basis_get.argtypes = [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i), vp, vp]
         L.kp_project_gemm_bf16.argtypes = [vp, i, i, i, vp, i, vp, i, vp, i]
+        L.kp_residual.argtypes = [vp, i, vp, vp, vp, vp]
+        f32 = ctypes.c_float
+        L.kp_cnn_create.argtypes = [vp, i, i, i, i, vp, ctypes.POINTER(vp)]
+        L.kp_cnn_destroy.argtypes = [vp]
+        L.kp_cnn_num_params.argtypes = [vp]
+        L.kp_cnn_set_params.argtypes = [vp, vp]
+        L.kp_cnn_get_params.argtypes = [vp, vp]
+        L.kp_cnn_forward.argtypes = [vp, i, vp, vp]
+        L.kp_cnn_gradients.argtypes = [vp, i, vp, vp, vp, vp]
+        L.kp_cnn_train_step.argtypes = [vp, i, vp, vp, f32, f32, f32, f32, i, vp]
         for f in ("kp_create", "kp_destroy", "kp_set_stream", "kp_apply", "kp_rhs", "kp_seed_solve",
                   "kp_refine", "kp_store_basis", "kp_project_targets", "kp_project_targets_multi",
-                  "kp_basis_get", "kp_project_gemm_bf16"):
+                  "kp_basis_get", "kp_project_gemm_bf16", "kp_residual", "kp_cnn_create",
+                  "kp_cnn_destroy", "kp_cnn_num_params", "kp_cnn_set_params", "kp_cnn_get_params",
+                  "kp_cnn_forward", "kp_cnn_gradients", "kp_cnn_train_step"):
             getattr(L, f).restype = i
         _lib = L
     return _lib
@@ -212,6 +224,11 @@ class Context:
                                                    self._arr(ops), self._arr(_ptrs(r)),
                                                    self._arr(_ptrs(x))))
 
+    def residual(self, ops, b, x, r):
+        """r = b - A x (FP64)."""
+        self._check(lib().kp_residual(self._h, len(ops), self._arr(ops), self._arr(_ptrs(b)),
+                                      self._arr(_ptrs(x)), self._arr(_ptrs(r))))
+
     def project_gemm_bf16(self, B, V, C, K=None):
         """C[t][i] = sum_k B[t][k] V[i][k] on the tensor cores (BF16 in, FP32 out)."""
         import torch
@@ -327,3 +344,57 @@ class March:
             self.close()
         except Exception:
             pass
+
+
+class CNN:
+    """The learned-initial-guess network on the GPU (kp_cnn_*)."""
+
+    def __init__(self, ctx, H, W, channels=(6, 32, 32, 32, 1), max_batch=16):
+        L = lib()
+        self.ctx = ctx
+        ch = (ctypes.c_int * len(channels))(*channels)
+        self._h = ctypes.c_void_p()
+        ctx._check(L.kp_cnn_create(ctx._h, H, W, max_batch, len(channels) - 1,
+                                   ctypes.cast(ch, ctypes.c_void_p), ctypes.byref(self._h)))
+        self.H, self.W, self.channels, self.max_batch = H, W, tuple(channels), max_batch
+        self.nparams = L.kp_cnn_num_params(self._h)
+
+    def close(self):
+        if self._h:
+            lib().kp_cnn_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.nparams
+        self.ctx._check(lib().kp_cnn_set_params(self._h, p.ctypes.data_as(ctypes.c_void_p)))
+
+    def get_params(self):
+        p = np.zeros(self.nparams, dtype=np.float32)
+        self.ctx._check(lib().kp_cnn_get_params(self._h, p.ctypes.data_as(ctypes.c_void_p)))
+        return p
+
+    def forward(self, x, out):
+        """x: CUDA float32 [B][c0][H*W]; out: CUDA float32 [B][cL][H*W]."""
+        self.ctx._check(lib().kp_cnn_forward(self._h, x.shape[0], ctypes.c_void_p(x.data_ptr()),
+                                             ctypes.c_void_p(out.data_ptr())))
+
+    def gradients(self, x, target, grads=None):
+        loss = ctypes.c_double()
+        self.ctx._check(lib().kp_cnn_gradients(
+            self._h, x.shape[0], ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+            ctypes.c_void_p(grads.data_ptr()) if grads is not None else None, ctypes.byref(loss)))
+        return loss.value
+
+    def train_step(self, x, target, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
+        loss = ctypes.c_double()
+        self.ctx._check(lib().kp_cnn_train_step(
+            self._h, x.shape[0], ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(target.data_ptr()),
+            lr, beta1, beta2, eps, t, ctypes.byref(loss)))
+        return loss.value
