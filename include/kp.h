@@ -250,6 +250,19 @@ kp_status kp_cnn_forward(kp_cnn* cnn, int B, const float* in, float* out);
  * (device [num_params], may be NULL) and the loss (host, may be NULL). */
 kp_status kp_cnn_gradients(kp_cnn* cnn, int B, const float* in, const float* target,
                            float* grads, double* loss);
+/* Network input of the learned guess for B targets at time tau = n/T: planes
+ * [target image, seed state m_seed^n, sin 2 pi tau, cos 2 pi tau, sin 4 pi tau,
+ * cos 4 pi tau] into in (device [B][6][H*W] FP32); img, seed: host arrays of
+ * B device pointers to FP64 planes. */
+kp_status kp_cnn_pack_inputs(kp_cnn* cnn, int B, const double* const* img, const double* const* seed,
+                             double tau, float* in);
+/* Training target of the learned guess: out_b = a_b - b_b (m_i^n - m_seed^n)
+ * into out (device [B][H*W] FP32); a, b: host arrays of device FP64 planes. */
+kp_status kp_cnn_pack_target(kp_cnn* cnn, int B, const double* const* a, const double* const* b,
+                             float* out);
+/* x_b = base_b + delta_b: the FP64 initial guess m_seed^n + network output. */
+kp_status kp_cnn_add_guess(kp_cnn* cnn, int B, const float* delta, const double* const* base,
+                           double* const* x);
 /* One Adam step (Kingma & Ba 2015) on that loss; t = 1, 2, ... */
 kp_status kp_cnn_train_step(kp_cnn* cnn, int B, const float* in, const float* target, float lr,
                             float beta1, float beta2, float eps, int t, double* loss);

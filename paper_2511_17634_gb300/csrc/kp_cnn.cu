@@ -166,6 +166,35 @@ __global__ void weights_bf16_kernel(const float* Wl, __nv_bfloat16* Wb, int ldw,
 
 size_t up8(size_t x) { return (x + 7) / 8 * 8; }
 
+// Network input planes of sample b: target image, seed state, then the time
+// embedding sin(2 pi tau), cos(2 pi tau), sin(4 pi tau), cos(4 pi tau).
+__global__ void pack_inputs_kernel(const double* const* img, const double* const* seed, float tau, float* in,
+                                   int P) {
+  const int b = blockIdx.y;
+  const float e[4] = {sinpif(2.f * tau), cospif(2.f * tau), sinpif(4.f * tau), cospif(4.f * tau)};
+  float* o = in + (size_t)b * 6 * P;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    o[p] = (float)img[b][p];
+    o[P + p] = (float)seed[b][p];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o[(2 + k) * P + p] = e[k];
+  }
+}
+
+// out_b = a_b - b_b in FP32 (training targets m_i^n - m_seed^n)
+__global__ void diff_kernel(const double* const* a, const double* const* bb, float* out, int P) {
+  const int b = blockIdx.y;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
+    out[(size_t)b * P + p] = (float)(a[b][p] - bb[b][p]);
+}
+
+// x_b = base_b + delta_b (FP64 initial guess from the network's correction)
+__global__ void add_guess_kernel(const float* delta, const double* const* base, double* const* x, int P) {
+  const int b = blockIdx.y;
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
+    x[b][p] = base[b][p] + (double)delta[(size_t)b * P + p];
+}
+
 }  // namespace
 
 struct kp_cnn {
@@ -426,6 +455,53 @@ kp_status kp_cnn_gradients(kp_cnn* n, int B, const float* in, const float* targe
   cudaError_t e = cudaMemcpyAsync(grads, n->grads, (size_t)n->nparams * sizeof(float), cudaMemcpyDeviceToDevice,
                                   n->ctx->stream);
   return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN gradients");
+}
+
+kp_status kp_cnn_pack_inputs(kp_cnn* n, int B, const double* const* img, const double* const* seed,
+                             double tau, float* in) {
+  if (!n || B < 1 || !img || !seed || !in) return n ? kp::set_error(n->ctx, KP_ERR_ARG, "CNN pack: bad arguments") : KP_ERR_ARG;
+  if (n->ch[0] != 6) return kp::set_error(n->ctx, KP_ERR_UNSUPPORTED, "CNN pack: the network needs 6 input planes");
+  std::vector<const double*> h(2 * (size_t)B);
+  for (int b = 0; b < B; ++b) { h[b] = img[b]; h[B + b] = seed[b]; }
+  const double** d = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&d, h.size() * sizeof(double*), n->ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double*), cudaMemcpyHostToDevice, n->ctx->stream);
+  if (e == cudaSuccess) {
+    pack_inputs_kernel<<<dim3(grid_for(n->P), B), 256, 0, n->ctx->stream>>>(d, d + B, (float)tau, in, n->P);
+    e = cudaGetLastError();
+  }
+  if (d) cudaFreeAsync(d, n->ctx->stream);
+  return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN pack");
+}
+
+kp_status kp_cnn_add_guess(kp_cnn* n, int B, const float* delta, const double* const* base, double* const* x) {
+  if (!n || B < 1 || !delta || !base || !x) return n ? kp::set_error(n->ctx, KP_ERR_ARG, "CNN guess: bad arguments") : KP_ERR_ARG;
+  std::vector<const double*> h(2 * (size_t)B);
+  for (int b = 0; b < B; ++b) { h[b] = base[b]; h[B + b] = x[b]; }
+  const double** d = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&d, h.size() * sizeof(double*), n->ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double*), cudaMemcpyHostToDevice, n->ctx->stream);
+  if (e == cudaSuccess) {
+    add_guess_kernel<<<dim3(grid_for(n->P), B), 256, 0, n->ctx->stream>>>(delta, d, const_cast<double* const*>(d + B), n->P);
+    e = cudaGetLastError();
+  }
+  if (d) cudaFreeAsync(d, n->ctx->stream);
+  return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN guess");
+}
+
+kp_status kp_cnn_pack_target(kp_cnn* n, int B, const double* const* a, const double* const* b, float* out) {
+  if (!n || B < 1 || !a || !b || !out) return n ? kp::set_error(n->ctx, KP_ERR_ARG, "CNN target: bad arguments") : KP_ERR_ARG;
+  std::vector<const double*> h(2 * (size_t)B);
+  for (int k = 0; k < B; ++k) { h[k] = a[k]; h[B + k] = b[k]; }
+  const double** d = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&d, h.size() * sizeof(double*), n->ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double*), cudaMemcpyHostToDevice, n->ctx->stream);
+  if (e == cudaSuccess) {
+    diff_kernel<<<dim3(grid_for(n->P), B), 256, 0, n->ctx->stream>>>(d, d + B, out, n->P);
+    e = cudaGetLastError();
+  }
+  if (d) cudaFreeAsync(d, n->ctx->stream);
+  return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN target");
 }
 
 kp_status kp_cnn_train_step(kp_cnn* n, int B, const float* in, const float* target, float lr, float beta1,

@@ -76,11 +76,15 @@ def lib():
         L.kp_cnn_forward.argtypes = [vp, i, vp, vp]
         L.kp_cnn_gradients.argtypes = [vp, i, vp, vp, vp, vp]
         L.kp_cnn_train_step.argtypes = [vp, i, vp, vp, f32, f32, f32, f32, i, vp]
+        L.kp_cnn_pack_inputs.argtypes = [vp, i, vp, vp, d, vp]
+        L.kp_cnn_add_guess.argtypes = [vp, i, vp, vp, vp]
+        L.kp_cnn_pack_target.argtypes = [vp, i, vp, vp, vp]
         for f in ("kp_create", "kp_destroy", "kp_set_stream", "kp_apply", "kp_rhs", "kp_seed_solve",
                   "kp_refine", "kp_store_basis", "kp_project_targets", "kp_project_targets_multi",
                   "kp_basis_get", "kp_project_gemm_bf16", "kp_residual", "kp_cnn_create",
                   "kp_cnn_destroy", "kp_cnn_num_params", "kp_cnn_set_params", "kp_cnn_get_params",
-                  "kp_cnn_forward", "kp_cnn_gradients", "kp_cnn_train_step"):
+                  "kp_cnn_forward", "kp_cnn_gradients", "kp_cnn_train_step", "kp_cnn_pack_inputs",
+                  "kp_cnn_add_guess", "kp_cnn_pack_target"):
             getattr(L, f).restype = i
         _lib = L
     return _lib
@@ -391,6 +395,27 @@ class CNN:
             self._h, x.shape[0], ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(target.data_ptr()),
             ctypes.c_void_p(grads.data_ptr()) if grads is not None else None, ctypes.byref(loss)))
         return loss.value
+
+    def pack_inputs(self, img, seed, tau, out):
+        """out [B][6][H*W] float32 from FP64 image and seed-state planes (rows or lists)."""
+        pi, ps = _ptrs(img), _ptrs(seed)
+        self.ctx._check(lib().kp_cnn_pack_inputs(self._h, len(pi), pi.ctypes.data_as(ctypes.c_void_p),
+                                                 ps.ctypes.data_as(ctypes.c_void_p), float(tau),
+                                                 ctypes.c_void_p(out.data_ptr())))
+
+    def pack_target(self, a, b, out):
+        """out [B][1][H*W] float32 = a - b (FP64 planes)."""
+        pa, pb = _ptrs(a), _ptrs(b)
+        self.ctx._check(lib().kp_cnn_pack_target(self._h, len(pa), pa.ctypes.data_as(ctypes.c_void_p),
+                                                 pb.ctypes.data_as(ctypes.c_void_p),
+                                                 ctypes.c_void_p(out.data_ptr())))
+
+    def add_guess(self, delta, base, x):
+        """x = base + delta (FP64 planes; delta float32 [B][1][H*W])."""
+        pb, px = _ptrs(base), _ptrs(x)
+        self.ctx._check(lib().kp_cnn_add_guess(self._h, len(pb), ctypes.c_void_p(delta.data_ptr()),
+                                               pb.ctypes.data_as(ctypes.c_void_p),
+                                               px.ctypes.data_as(ctypes.c_void_p)))
 
     def train_step(self, x, target, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         loss = ctypes.c_double()
