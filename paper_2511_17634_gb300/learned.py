@@ -27,7 +27,6 @@ def init_params(seed=0, channels=CHANNELS):
         parts.append(rng.normal(scale=np.sqrt(2.0 / (9 * ci)), size=co * ci * 9))
         parts.append(np.zeros(co))
     p = np.concatenate(parts)
-    p[-1 - 0] = 0.0
     # start the last layer near zero so that X_init starts at m_seed^n
     nlast = channels[-2] * 9 * channels[-1]
     p[-(nlast + channels[-1]):-channels[-1]] *= 0.01
@@ -90,7 +89,8 @@ def step_compare(ctx, net, group, T, g2, n, seeds_prev, tgt_prev, tol_seed=1e-10
                  slot_base=0):
     """Timestep n (1-based) for targets whose m^{n-1} is tgt_prev and seeds
     whose m^{n-1} is seeds_prev (CUDA [k][P] FP64).  Solves it three ways and
-    returns {mode: (initial relative residuals, Arnoldi steps, solutions)} for
+    returns ({mode: (initial relative residuals, Arnoldi steps, solutions),
+    'times': {mode: seconds of the target-side work}}, seed solutions) for
     'projected' (paper), 'learned' and 'plain' (x0 = 0)."""
     import torch
     H, W = group.H, group.W
@@ -110,32 +110,51 @@ def step_compare(ctx, net, group, T, g2, n, seeds_prev, tgt_prev, tol_seed=1e-10
     ctx.rhs(tops, tgt_prev, tb)
     slots = np.asarray(group.target_seed, dtype=np.int32) + slot_base
     out = {}
+    times = {}
     bn = tb.norm(dim=1)
     r = torch.empty_like(tb)
+    stream = torch.cuda.current_stream()
 
-    def finish(name, x0):
-        ctx.residual(tops, tb, x0, r)
-        res0 = (r.norm(dim=1) / bn).cpu().numpy()
-        x = x0.clone()
-        it, st, rr = kp.decode_info(ctx.refine(tops, tb, x, tol=tol, m=m, maxit=1000))
+    def timed(name, fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x0, x, info = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times[name] = e0.elapsed_time(e1) / 1000.0
+        it, st, rr = kp.decode_info(info)
         assert (st == 0).all()
-        out[name] = (res0, it, x)
+        ctx.residual(tops, tb, x0, r)
+        out[name] = ((r.norm(dim=1) / bn).cpu().numpy(), it, x)
 
-    # paper: x0 = V H^{-1} V^T b
-    x0 = torch.zeros_like(tgt_prev)
-    ctx.project_targets_multi(n, slots, tops, tb, x0)
-    finish("projected", x0)
-    # learned: X_init = m_seed^n + Delta, then the residual projected
+    def projected():
+        x0 = torch.zeros_like(tgt_prev)
+        ctx.project_targets_multi(n, slots, tops, tb, x0)       # paper: x0 = V H^-1 V^T b
+        x = x0.clone()
+        return x0, x, ctx.refine(tops, tb, x, tol=tol, m=m, maxit=1000)
+
     seed_rows = [sx[int(k)] for k in group.target_seed]
     xin = torch.empty((nt, 6, H * W), dtype=torch.float32, device=tgt_prev.device)
-    net.pack_inputs([img[k] for k in range(nt)], seed_rows, n / T, xin)
     delta = torch.empty((nt, 1, H * W), dtype=torch.float32, device=tgt_prev.device)
-    for k in range(0, nt, net.max_batch):
-        net.forward(xin[k:k + net.max_batch], delta[k:k + net.max_batch])
-    xl = torch.empty_like(tgt_prev)
-    net.add_guess(delta, seed_rows, xl)
-    ctx.residual(tops, tb, xl, r)
-    ctx.project_targets_multi(n, slots, tops, r, xl)
-    finish("learned", xl)
-    finish("plain", torch.zeros_like(tgt_prev))
+
+    def learned_():
+        net.pack_inputs([img[k] for k in range(nt)], seed_rows, n / T, xin)
+        for k in range(0, nt, net.max_batch):
+            net.forward(xin[k:k + net.max_batch], delta[k:k + net.max_batch])
+        x0 = torch.empty_like(tgt_prev)
+        net.add_guess(delta, seed_rows, x0)                     # X_init = m_seed^n + Delta
+        ctx.residual(tops, tb, x0, r)
+        ctx.project_targets_multi(n, slots, tops, r, x0)        # + V H^-1 V^T (b - A X_init)
+        x = x0.clone()
+        return x0, x, ctx.refine(tops, tb, x, tol=tol, m=m, maxit=1000)
+
+    def plain():
+        x0 = torch.zeros_like(tgt_prev)
+        x = x0.clone()
+        return x0, x, ctx.refine(tops, tb, x, tol=tol, m=m, maxit=1000)
+
+    timed("projected", projected)
+    timed("learned", learned_)
+    timed("plain", plain)
+    out["times"] = times
     return out, sx
