@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--block-threads", type=int, default=0,
                     help="threads per system for grids <= 1024 points (0 = library default)")
     ap.add_argument("--reorth", type=int, default=0, help="0 CGS2 (default), 1 DGKS-conditional")
+    ap.add_argument("--window", type=int, default=0,
+                    help="FP64 march: timesteps per target launch (0 = 8; 1 = per-timestep launches)")
+    ap.add_argument("--target-blocks", type=int, default=0,
+                    help="FP64 march windows: persistent target blocks (0 = all resident slots)")
     ap.add_argument("--learned", action="store_true",
                     help="128x128x3 learned-guess measurement (bounded sample)")
     return ap.parse_args()
@@ -269,7 +273,9 @@ def main():
     T = wl.T
     nmax = max(g.N for g in wl.groups)
     mixed = wl.precision == "mixed"
-    ctx = kp.Context(max_seeds=max(2 * wl.n_seed_planes, 1), max_a=wl.a, max_n=nmax,
+    window = args.window if args.window > 0 else 8
+    ctx = kp.Context(max_seeds=max(2 * (1 if mixed else window) * wl.n_seed_planes, 1), max_a=wl.a,
+                     max_n=nmax,
                      precision=kp.PREC_MIXED if mixed else kp.PREC_FP64,
                      block_threads=args.block_threads, reorth=args.reorth)
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -314,7 +320,7 @@ def main():
         return total
 
     common = dict(T=T, g2=wl.g2, tol_seed=wl.tol_seed, tol=wl.tol, m_seed=wl.m_seed, m=wl.m,
-                  maxit=1000)
+                  maxit=1000, window=window, target_blocks=args.target_blocks)
     proj = kp.March(ctx, groups, mode=kp.MARCH_PROJECTED, **common)
     with Clocks(local) as clk:
         t_proj = timed(proj, args.steps, args.warmup)
@@ -395,6 +401,7 @@ def main():
                        "tol": wl.tol, "m": wl.m, "parallelism": f"replicas x{world}",
                        "block_threads": args.block_threads or 256,
                        "orthogonalisation": "CGS2" if args.reorth == 0 else "CGS+DGKS",
+                       "window": 1 if mixed else window,
                        "l2": "flushed between timed steps (512 MiB write)"},
             "e2e": {"value": e2e_value, "unit": "systems/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -286,8 +286,10 @@ kp_status kp_basis_get(kp_ctx* ctx, int seed_id, int timestep, int* a_out, int* 
  *   m^{n-1} <- m^n.
  * f = 0 (the paper's setting, Sec. 5), dt = 1/T, h = 1/H per group, and
  * g2[n-1] = (g^n)^2.  Groups may have different grid sizes; all seeds run in
- * one launch and all targets in one launch.  Seed slots 0..nseed_total-1 of
- * the context are used (max_seeds must be at least the total seed count).
+ * one launch and all targets in one launch.  The seed bases of a timestep
+ * live in one set of nseed_total context slots; a plan rotates 2 sets (one
+ * timestep per launch) or 2K sets (windows of K timesteps), so max_seeds must
+ * be at least 2 x nseed_total, and 2K x nseed_total for a window of K.
  * ------------------------------------------------------------------------ */
 typedef enum { KP_MARCH_PROJECTED = 0, KP_MARCH_PLAIN = 1, KP_MARCH_WARM = 2 } kp_march_mode;
 
@@ -306,6 +308,13 @@ typedef struct {
   double tol_seed, tol;  /* relative residuals for seeds and targets             */
   int m_seed, m, maxit;  /* restart lengths, Arnoldi-step cap per solve          */
   int use_graph;         /* capture each timestep in a CUDA graph (1) or not (0) */
+  int window;            /* FP64 plans: timesteps per target launch K (work items
+                            claimed dynamically across the window); 0 = automatic
+                            (8, capped by max_seeds / (2 x seeds): a window needs
+                            2K basis slot sets), 1 = one timestep per launch.
+                            Mixed precision and cluster shapes always use 1.     */
+  int target_blocks;     /* window mode: persistent target blocks; 0 = every
+                            resident slot of the GPU                              */
 } kp_march_opts;
 
 /* Per-timestep totals, filled on the host by kp_march_run. */

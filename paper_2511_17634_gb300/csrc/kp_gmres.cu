@@ -68,17 +68,51 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
   auto slot = [&](int i) -> double* {
     return i < p.S ? sm.V + (size_t)i * npad : spill + (size_t)(i - p.S) * npad;
   };
-  // timestep of this launch (time march) and its parity's seed slots
-  int tstep = 0;
+  if (p.pdl == 1) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  // timesteps of this launch (time march): t0 .. t0 + nstep - 1
+  int t0 = 0, nstep = 1;
   if (p.step) {
-    tstep = *p.step + p.step_offset;
-    if (tstep >= *p.step_end) return;        // pipelined seed step past the run: nothing to do
+    t0 = *p.step + p.step_offset;
+    nstep = min(p.win > 0 ? p.win : 1, *p.step_end - t0);
+    if (nstep <= 0) {                        // pipelined seed step past the run: nothing to do
+      if (p.pdl == 2) asm volatile("griddepcontrol.wait;" ::: "memory");
+      return;
+    }
   }
-  const int parity_base = (tstep & 1) * p.slot_parity_stride;
   const double bsc = p.b_scale;
-
-  for (int sysi = blockIdx.x; sysi < p.nsys; sysi += gridDim.x) {
-    const SysDesc d = p.sys[sysi];
+  const int nitems = p.nsys * nstep;
+  int sysi = blockIdx.x, kstep = 0;          // static schedule: a block marches its systems
+  for (;;) {
+    if (p.queue) {
+      // dynamic schedule over (timestep, system) items, timestep-major: a
+      // block that finishes early takes the next item instead of idling
+      // until the slowest system of its wave is done
+      if (tid == 0) sm.fl[6] = atomicAdd(p.queue, 1);
+      __syncthreads();
+      const int item = sm.fl[6];
+      if (item >= nitems) break;
+      kstep = item / p.nsys;
+      sysi = item - kstep * p.nsys;
+    } else if (sysi >= p.nsys) {
+      break;
+    }
+    const int tstep = t0 + kstep;
+    if (p.done) {
+      // m^{n-1} of this system comes from its previous item, claimed earlier
+      // by a block that is therefore running: wait for its release
+      const int need = tstep - *p.run_start;
+      if (tid == 0) {
+        int it = 0;
+        while (ld_acquire_gpu(p.done + sysi) < need) {
+          if (++it > kWaitLimit) { atomicOr(p.err, 2); break; }
+          __nanosleep(256);
+        }
+      }
+      __syncthreads();
+      (void)ld_acquire_gpu(p.done + sysi);    // orders this thread's loads of m^{n-1}
+    }
+    const int parity_base = slot_set_base(p, tstep);
+    const SysDesc d = p.sys_par[0] ? p.sys_par[(tstep + p.sys_shift) & 1][sysi] : p.sys[sysi];
     const int H = d.H, W = d.W, N = H * W;
     const double hh = d.h;
     const double g2 = p.step ? p.g2_sched[tstep] : d.g2;
@@ -490,8 +524,15 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
         if (status != KP_OK) atomicAdd(&a->not_converged, 1u);
       }
     }
-    __syncthreads();                           // shared memory reused by the next system
+    if (p.done) {                              // release m^n of this system
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) st_release_gpu(p.done + sysi, tstep + 1 - *p.run_start);
+    }
+    __syncthreads();                           // shared memory reused by the next item
+    if (!p.queue && ++kstep == nstep) { kstep = 0; sysi += gridDim.x; }
   }
+  if (p.pdl == 2) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // y = A x (mode 0) or b = m^{n-1}/dt - Div_h f (mode 1), one block per system.
@@ -559,7 +600,23 @@ static cudaError_t launch_one(const GmresParams& p, size_t smem, cudaStream_t st
   auto k = gmres_fp64_kernel<EPT, NT, MINB>;
   cudaError_t e = allow_max_smem(k, smem);
   if (e != cudaSuccess) return e;
-  k<<<p.nsys, NT, smem, st>>>(p);
+  const int grid = p.grid > 0 ? p.grid : p.nsys;
+  if (p.pdl == 2) {
+    // programmatic dependent launch: the blocks may start while the previous
+    // kernel of the stream still runs (it signals at entry)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, p);
+  }
+  k<<<grid, NT, smem, st>>>(p);
   return cudaGetLastError();
 }
 
@@ -580,11 +637,27 @@ cudaError_t launch_gmres_fp64_1k_grid(const GmresParams& p, size_t smem, int gri
   return cudaGetLastError();
 }
 
-__global__ void advance_kernel(int* step) { *step += 1; }
+__global__ void advance_kernel(int* step, int by, int* zero) {
+  *step += by;
+  if (zero) *zero = 0;
+}
 
-cudaError_t launch_advance(int* step, cudaStream_t st) {
-  advance_kernel<<<1, 1, 0, st>>>(step);
+cudaError_t launch_advance(int* step, cudaStream_t st, int by, int* zero) {
+  advance_kernel<<<1, 1, 0, st>>>(step, by, zero);
   return cudaGetLastError();
+}
+
+int gmres_fp64_blocks_per_sm(int ept, int nt, size_t smem) {
+  int n = 0;
+  cudaError_t e = cudaErrorInvalidValue;
+  auto occ = [&](auto k, int threads) {
+    e = allow_max_smem(k, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem);
+  };
+  if (ept == 4 && nt == 256) occ(gmres_fp64_kernel<4, 256, 2>, 256);
+  else if (ept == 8 && nt == 128) occ(gmres_fp64_kernel<8, 128, 2>, 128);
+  else if (ept == 8 && nt == 512) occ(gmres_fp64_kernel<8, 512, 1>, 512);
+  return e == cudaSuccess ? n : 0;
 }
 
 cudaError_t launch_apply(const SysDesc* sys, int nsys, int mode, cudaStream_t st) {

@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
     if (tstep >= *p.step_end) return;            // uniform over the whole grid
   }
   if (sysi >= p.nsys) return;                     // uniform over the cluster
-  const int parity_base = (tstep & 1) * p.slot_parity_stride;
+  const int parity_base = slot_set_base(p, tstep);
   const double bsc = p.b_scale;
   constexpr double kEta = 1e-5;
 

@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
     tstep = *p.step + p.step_offset;
     if (tstep >= *p.step_end) return;
   }
-  const int parity_base = (tstep & 1) * p.slot_parity_stride;
+  const int parity_base = slot_set_base(p, tstep);
   const double bsc = p.b_scale;
   constexpr double kEta = 1e-5;                // inner residual reduction per outer step
 

@@ -105,7 +105,40 @@ struct GmresParams {
   int bnext_ld;
   __nv_bfloat16* capVb;     // if set: BF16 copy of the captured basis, [slot][kVbRows][capVb_ld]
   int capVb_ld;
+  // march windows (FP64 solver): one launch covers timesteps
+  // *step + step_offset .. + win - 1 (clipped at *step_end)
+  int win;                  // 0 = one timestep per launch
+  int slot_sets;            // seed-slot sets: timestep t uses set t % slot_sets (0 = 2)
+  const SysDesc* sys_par[2];// if set: timestep t uses sys_par[(t + sys_shift) & 1] (else sys)
+  int sys_shift;
+  int* queue;               // dynamic schedule: item counter (zeroed before the launch);
+                            // null = static (each block marches its systems through the window)
+  int* done;                // [nsys] timesteps completed since *run_start (dynamic schedule)
+  const int* run_start;
+  int* err;                 // bit 1: a dependency wait gave up
+  int grid;                 // blocks of the launch (0 = one per system)
+  int pdl;                  // programmatic launch: 1 = let the stream's next launch start
+                            // at once; 2 = launched that way: wait for the prior grid
+                            // (its completion and memory) before exiting
 };
+
+constexpr int kWaitLimit = 1 << 22;   // polls (>= 256 ns apart) before a wait gives up
+
+// First seed slot of timestep t (slot sets rotate with the timestep).
+__host__ __device__ inline int slot_set_base(const GmresParams& p, int t) {
+  const int sets = p.slot_sets > 2 ? p.slot_sets : 2;
+  return (t % sets) * p.slot_parity_stride;
+}
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* a) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(a) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(int* a, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(a), "r"(v) : "memory");
+}
 
 constexpr int kVbRows = 48;   // rows per seed slot of the BF16 basis (tensor-core N tile)
 
@@ -406,7 +439,9 @@ cudaError_t launch_gmres_fp64_1k_grid(const GmresParams& p, size_t smem, int gri
 cudaError_t launch_apply(const SysDesc* sys, int nsys, int mode, cudaStream_t st);
 cudaError_t launch_factor(const FactorParams& p, cudaStream_t st);
 cudaError_t launch_project_fp64(const ProjParams& p, int ept, int nt, cudaStream_t st);
-cudaError_t launch_advance(int* step, cudaStream_t st);
+cudaError_t launch_advance(int* step, cudaStream_t st, int by = 1, int* zero = nullptr);
+// Resident blocks per SM of the FP64 solver shape (0 if unknown).
+int gmres_fp64_blocks_per_sm(int ept, int nt, size_t smem);
 // dst[q] = src[perm[q]] (gather) or dst[perm[q]] = src[q] (scatter), planes of n doubles
 cudaError_t launch_permute(double* dst, const double* src, const int* perm, int count, int n,
                            int gather, cudaStream_t st);

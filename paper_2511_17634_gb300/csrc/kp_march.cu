@@ -12,6 +12,14 @@
 // which both launches read g^2 and their slot parity; two copies of every
 // state plane alternate by parity, so one graph serves all even and one all
 // odd timesteps.
+//
+// FP64 plans march in windows of K timesteps instead: one graph replay runs
+// the seeds of window w+1 (each seed block marches its system through the K
+// steps, writing slot set t mod 2K) and, started programmatically beside
+// them, one persistent target launch over the K x (targets) items of window w.  Target blocks claim items from a
+// counter in timestep-major order, so the launch has no per-timestep wave
+// tail; an item waits (bounded) only for its own system's previous timestep,
+// which an earlier claim -- a running block -- is solving.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -68,7 +76,12 @@ struct kp_march_plan {
   kp::Shape shS, shT;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int launches_per_step = 0;
-  int host_step[2] = {0, 0};                 // source of the counter reset (outlives the copy)
+  int host_step[3] = {0, 0, 0};              // source of the counter reset (outlives the copy)
+  // windows of K timesteps (FP64): K = 1 is the per-timestep scheme above
+  int K = 1;
+  int* queue = nullptr;                      // item counter of the target launch
+  int* done = nullptr;                       // [nt] steps completed in this run
+  int tgt_grid = 0;                          // persistent target blocks
 };
 
 namespace {
@@ -108,6 +121,22 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset)
   g.max_a = c->opt.max_a;
   g.slot_parity_stride = P->ns;
   g.acc = P->acc;
+  g.err = P->err;
+  if (P->K > 1) {
+    // window: descriptors and slot sets chosen per timestep on the device
+    g.win = P->K;
+    g.slot_sets = 2 * P->K;
+    g.sys_par[0] = P->desc[0] + (seeds ? 0 : P->ns);
+    g.sys_par[1] = P->desc[1] + (seeds ? 0 : P->ns);
+    g.sys_shift = seeds ? 1 : 0;
+    g.step_offset = seeds ? offset : 0;
+    if (!seeds) {
+      g.queue = P->queue;
+      g.done = P->done;
+      g.run_start = P->step + 2;
+      g.grid = P->tgt_grid;
+    }
+  }
   if (seeds) {
     g.x0_mode = kp::X0_ZERO;
     if (P->mixed) {
@@ -186,6 +215,38 @@ kp_status enqueue_step(kp_march_plan* P, int par, cudaEvent_t* ev, int* launches
   return e == cudaSuccess ? KP_OK : kp::cuda_error(P->ctx, e, "march step enqueue");
 }
 
+// Window of K timesteps from the device counter t0, on one stream: the seeds
+// of t0+K..t0+2K-1, then the targets of t0..t0+K-1 as a programmatic
+// dependent launch (the seed blocks signal at entry, so the persistent target
+// blocks fill every slot the few seed blocks leave and take theirs when the
+// seed chains end; targets never read this window's seeds), then t0 += K and
+// the item counter reset.  With ev (timing mode) the launches are plain and
+// bracketed by ev[0..1] (seeds) and ev[2..3] (targets).
+kp_status enqueue_window(kp_march_plan* P, cudaEvent_t* ev, int* launches) {
+  cudaError_t e = cudaSuccess;
+  int nl = 0;
+  const bool pdl = (ev == nullptr) && P->ns > 0 && P->nt > 0;
+  if (P->ns > 0) {
+    if (ev) e = cudaEventRecord(ev[0], P->st);
+    kp::GmresParams g = solver_params(P, true, 0, P->K);
+    g.pdl = pdl ? 1 : 0;
+    if (e == cudaSuccess) e = launch_solver(P, g, P->shS, P->st);
+    ++nl;
+    if (ev && e == cudaSuccess) e = cudaEventRecord(ev[1], P->st);
+  }
+  if (P->nt > 0 && e == cudaSuccess) {
+    if (ev) e = cudaEventRecord(ev[2], P->st);
+    kp::GmresParams g = solver_params(P, false, 0, 0);
+    g.pdl = pdl ? 2 : 0;
+    if (e == cudaSuccess) e = launch_solver(P, g, P->shT, P->st);
+    ++nl;
+    if (ev && e == cudaSuccess) e = cudaEventRecord(ev[3], P->st);
+  }
+  if (e == cudaSuccess) { e = kp::launch_advance(P->step, P->st, P->K, P->queue); ++nl; }
+  if (launches) *launches = nl;
+  return e == cudaSuccess ? KP_OK : kp::cuda_error(P->ctx, e, "march window enqueue");
+}
+
 }  // namespace
 
 extern "C" {
@@ -211,6 +272,8 @@ kp_status kp_march_destroy(kp_march_plan* P) {
   cudaFree(P->tiles[0]);
   cudaFree(P->tiles[1]);
   cudaFree(P->err);
+  cudaFree(P->queue);
+  cudaFree(P->done);
   if (P->fork) cudaEventDestroy(P->fork);
   if (P->join) cudaEventDestroy(P->join);
   if (P->st2) cudaStreamDestroy(P->st2);
@@ -270,8 +333,19 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
     return kp::set_error(c, KP_ERR_UNSUPPORTED, "grids above 4096 unknowns: one grid size per plan");
   }
   if (s != KP_OK) { kp_march_destroy(P); return s; }
+  // window length: FP64 one-block solvers only; 2K slot sets must fit
+  if (!P->mixed && !P->shS.cs && !P->shT.cs && o.window != 1 && P->nt > 0) {
+    int K = o.window > 0 ? o.window : 8;
+    if (P->ns) K = std::min(K, c->opt.max_seeds / (2 * P->ns));
+    P->K = std::max(1, std::min(K, o.T));
+  }
   cudaError_t e = cudaStreamCreateWithFlags(&P->st, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&P->st2, cudaStreamNonBlocking);
+  // the seed branch gets the higher priority: when both branches are ready
+  // the block scheduler places the few seed blocks first and the persistent
+  // target blocks take the remaining slots (and the seeds' once they finish)
+  int prio_lo = 0, prio_hi = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&P->st2, cudaStreamNonBlocking, prio_hi);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P->join, cudaEventDisableTiming);
   const int ns = P->ns, nt = P->nt;
@@ -280,7 +354,16 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
     if (e == cudaSuccess) e = dmalloc(&P->Tt[k], P->tgt_elems);
   }
   if (e == cudaSuccess) e = dmalloc(&P->g2, o.T);
-  if (e == cudaSuccess) e = dmalloc(&P->step, 2);
+  if (e == cudaSuccess) e = dmalloc(&P->step, 3);
+  if (e == cudaSuccess) e = dmalloc(&P->err, 1);
+  if (e == cudaSuccess) e = cudaMemset(P->err, 0, sizeof(int));
+  if (e == cudaSuccess && P->K > 1) {
+    e = dmalloc(&P->queue, 1);
+    if (e == cudaSuccess) e = dmalloc(&P->done, nt);
+    const int per_sm = kp::gmres_fp64_blocks_per_sm(P->shT.ept, P->shT.nt, P->shT.smem);
+    const int slots = (per_sm > 0 ? per_sm : 1) * c->sms;
+    P->tgt_grid = std::max(1, std::min(nt, o.target_blocks > 0 ? o.target_blocks : slots));
+  }
   if (e == cudaSuccess) e = dmalloc(&P->acc, o.T);
   // one Krylov workspace per branch: seed blocks first, then target blocks
   size_t spS = 0, spT = 0;
@@ -357,8 +440,6 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
     e = dmalloc(&P->Bb, (size_t)nt * vb_ld);
     if (e == cudaSuccess) e = cudaMemset(P->Bb, 0, (size_t)nt * vb_ld * sizeof(__nv_bfloat16));
     if (e == cudaSuccess) e = dmalloc(&P->Cp, (size_t)nt * kp::kVbRows);
-    if (e == cudaSuccess) e = dmalloc(&P->err, 1);
-    if (e == cudaSuccess) e = cudaMemset(P->err, 0, sizeof(int));
     std::vector<kp::ProjTile> tl[2];
     int seed_base = 0;
     P->mapB.resize(ngroups);
@@ -408,7 +489,23 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
     kp_march_destroy(P);
     return r;
   }
-  if (o.use_graph) {
+  if (o.use_graph && P->K > 1) {
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamBeginCapture(P->st, cudaStreamCaptureModeThreadLocal);
+    kp_status r = KP_OK;
+    if (e == cudaSuccess) {
+      r = enqueue_window(P, nullptr, &P->launches_per_step);
+      cudaError_t e2 = cudaStreamEndCapture(P->st, &gr);
+      if (r == KP_OK) e = e2;
+    }
+    if (r == KP_OK && e == cudaSuccess) e = cudaGraphInstantiate(&P->graph[0], gr, 0);
+    if (gr) cudaGraphDestroy(gr);
+    if (r != KP_OK || e != cudaSuccess) {
+      if (r == KP_OK) r = kp::cuda_error(c, e, "march graph capture");
+      kp_march_destroy(P);
+      return r;
+    }
+  } else if (o.use_graph) {
     for (int par = 0; par < 2; ++par) {
       cudaGraph_t gr = nullptr;
       e = cudaStreamBeginCapture(P->st, cudaStreamCaptureModeThreadLocal);
@@ -458,36 +555,43 @@ kp_status kp_march_run(kp_march_plan* P, int n0, int steps, kp_step_stats* stats
   }
   P->host_step[0] = n0;
   P->host_step[1] = n0 + steps;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(P->step, P->host_step, 2 * sizeof(int), cudaMemcpyHostToDevice, P->st);
+  P->host_step[2] = n0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(P->step, P->host_step, 3 * sizeof(int), cudaMemcpyHostToDevice, P->st);
+  if (e == cudaSuccess && P->done) e = cudaMemsetAsync(P->done, 0, (size_t)P->nt * sizeof(int), P->st);
+  if (e == cudaSuccess && P->queue) e = cudaMemsetAsync(P->queue, 0, sizeof(int), P->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(P->acc + n0, 0, (size_t)steps * sizeof(kp::StepAcc), P->st);
   std::vector<cudaEvent_t> ev;
   int launches = 0;
+  const int K = P->K;
+  const int nwin = (steps + K - 1) / K;       // launches of the step (K = 1) or window graph
   if (e == cudaSuccess && timing) {
-    ev.resize((size_t)steps * 4 + 2, nullptr);
+    ev.resize((size_t)nwin * 4 + 2, nullptr);
     for (auto& x : ev)
       if (e == cudaSuccess) e = cudaEventCreate(&x);
   }
   kp_status r = KP_OK;
-  // prologue: seeds of step n0 (their basis serves the targets of step n0)
+  // prologue: seeds of step n0 (or of the first window), whose bases serve
+  // the first targets
   if (e == cudaSuccess && P->ns) {
     kp::GmresParams g = solver_params(P, true, 1 - q0, 0);
-    if (timing) e = cudaEventRecord(ev[(size_t)steps * 4], P->st);
+    if (timing) e = cudaEventRecord(ev[(size_t)nwin * 4], P->st);
     if (e == cudaSuccess) e = launch_solver(P, g, P->shS, P->st);
-    if (timing && e == cudaSuccess) e = cudaEventRecord(ev[(size_t)steps * 4 + 1], P->st);
+    if (timing && e == cudaSuccess) e = cudaEventRecord(ev[(size_t)nwin * 4 + 1], P->st);
     ++launches;
   }
-  for (int k = 0; k < steps && e == cudaSuccess && r == KP_OK; ++k) {
-    const int par = (n0 + k) & 1;
+  for (int k = 0; k < nwin && e == cudaSuccess && r == KP_OK; ++k) {
+    const int par = K > 1 ? 0 : (n0 + k) & 1;
     if (timing) {
       int nl = 0;
-      r = enqueue_step(P, par, ev.data() + (size_t)k * 4, &nl);
+      r = K > 1 ? enqueue_window(P, ev.data() + (size_t)k * 4, &nl)
+                : enqueue_step(P, par, ev.data() + (size_t)k * 4, &nl);
       launches += nl;
     } else if (P->graph[par]) {
       e = cudaGraphLaunch(P->graph[par], P->st);
       launches += P->launches_per_step;
     } else {
       int nl = 0;
-      r = enqueue_step(P, par, nullptr, &nl);
+      r = K > 1 ? enqueue_window(P, nullptr, &nl) : enqueue_step(P, par, nullptr, &nl);
       launches += nl;
     }
   }
@@ -521,14 +625,22 @@ kp_status kp_march_run(kp_march_plan* P, int n0, int steps, kp_step_stats* stats
       stats[k].refine_flops32 = (double)a.tgt_flops32;
     }
   }
+  if (e == cudaSuccess && (stats || timing)) {
+    int herr = 0;
+    e = cudaMemcpy(&herr, P->err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && herr) {
+      cudaMemset(P->err, 0, sizeof(int));
+      r = kp::set_error(c, KP_ERR_TIMEOUT, "march: a device wait gave up (flags 0x%x)", herr);
+    }
+  }
   if (e == cudaSuccess && timing) {
     std::memset(timing, 0, sizeof(*timing));
     float t = 0.f;
     if (P->ns) {
-      e = cudaEventElapsedTime(&t, ev[(size_t)steps * 4], ev[(size_t)steps * 4 + 1]);
+      e = cudaEventElapsedTime(&t, ev[(size_t)nwin * 4], ev[(size_t)nwin * 4 + 1]);
       timing->seed_ms += t;
     }
-    for (int k = 0; k < steps && e == cudaSuccess; ++k) {
+    for (int k = 0; k < nwin && e == cudaSuccess; ++k) {
       cudaEvent_t* x = ev.data() + (size_t)k * 4;
       if (P->ns) {
         e = cudaEventElapsedTime(&t, x[0], x[1]);
@@ -540,7 +652,7 @@ kp_status kp_march_run(kp_march_plan* P, int n0, int steps, kp_step_stats* stats
       }
     }
     if (e == cudaSuccess && P->ns && P->nt)
-      e = cudaEventElapsedTime(&timing->step_ms, ev[(size_t)steps * 4], ev[(size_t)(steps - 1) * 4 + 3]);
+      e = cudaEventElapsedTime(&timing->step_ms, ev[(size_t)nwin * 4], ev[(size_t)(nwin - 1) * 4 + 3]);
   }
   if (timing) timing->launches = launches;
   for (auto& x : ev)

@@ -272,7 +272,8 @@ class _Group(ctypes.Structure):
 class _MarchOpts(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int), ("g2", ctypes.c_void_p), ("mode", ctypes.c_int),
                 ("tol_seed", ctypes.c_double), ("tol", ctypes.c_double), ("m_seed", ctypes.c_int),
-                ("m", ctypes.c_int), ("maxit", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("m", ctypes.c_int), ("maxit", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("window", ctypes.c_int), ("target_blocks", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
@@ -307,7 +308,7 @@ class March:
     target_seed int array, H, W).  The tensors are updated in place by run()."""
 
     def __init__(self, ctx, groups, T, g2, mode=MARCH_PROJECTED, tol_seed=1e-10, tol=1e-8,
-                 m_seed=40, m=40, maxit=1000, use_graph=True):
+                 m_seed=40, m=40, maxit=1000, use_graph=True, window=0, target_blocks=0):
         L = _march_lib()
         self.ctx = ctx
         self._keep = []
@@ -322,7 +323,8 @@ class March:
             arr[k].tgt_seed = ts.ctypes.data if len(ts) else None
         g2 = np.ascontiguousarray(g2, dtype=np.float64)
         self._keep.append(g2)
-        o = _MarchOpts(T, g2.ctypes.data, mode, tol_seed, tol, m_seed, m, maxit, int(use_graph))
+        o = _MarchOpts(T, g2.ctypes.data, mode, tol_seed, tol, m_seed, m, maxit, int(use_graph),
+                       int(window), int(target_blocks))
         self.T = T
         self._h = ctypes.c_void_p()
         ctx._check(L.kp_march_create(ctx._h, len(groups), ctypes.cast(arr, ctypes.c_void_p),

@@ -93,3 +93,37 @@ def test_march_workload_32x32_sampled(kp, orc):
     assert err <= 1e-6
     assert all(s.max_rel_res <= 1e-8 for s in stats)
     assert tm.refine_ms > 0 and tm.launches == 3 * steps + 1
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_march_windows_bit_identical(kp, orc, mode):
+    # windows of K timesteps with dynamically claimed (timestep, system) items
+    # compute every solve exactly as one launch per timestep does: the states,
+    # iteration counts and residuals agree bit for bit, including ragged
+    # windows and a run resumed in the middle of one
+    wl = synth.config(2, T=1000, ntargets=48)
+    g = wl.groups[0]
+    steps = 21
+    res = {}
+    for K in (1, 8, 3):
+        ctx = kp.Context(max_seeds=2 * K * wl.n_seed_planes, max_a=wl.a, max_n=g.N)
+        grp = _groups(wl)
+        mr = kp.March(ctx, grp, wl.T, wl.g2, mode=mode, tol_seed=wl.tol_seed, tol=wl.tol,
+                      m_seed=wl.m_seed, m=wl.m, window=K)
+        st1, tm = mr.run(0, 5, stats=True, timing=True)
+        st2, _ = mr.run(5, steps - 5, stats=True)
+        torch.cuda.synchronize()
+        nwin = -(-5 // K)
+        assert tm.launches == 3 * nwin + 1
+        res[K] = (grp[0][0].cpu().numpy(), grp[0][1].cpu().numpy(),
+                  [(s.tgt_iters, s.seed_iters, s.max_rel_res) for s in list(st1) + list(st2)])
+        mr.close()
+        ctx.close()
+    for K in (8, 3):
+        assert np.array_equal(res[K][0], res[1][0])
+        assert np.array_equal(res[K][1], res[1][1])
+        assert res[K][2] == res[1][2]
+    oms, omt, _ = orc.march(g.H, g.W, wl.T, wl.g2, g.seeds, g.targets, g.target_seed, steps=steps,
+                            mode=mode, tol_seed=wl.tol_seed, m_seed=wl.m_seed, a=wl.a,
+                            tol_ref=wl.tol, m_ref=wl.m)
+    assert np.abs(res[8][1] - omt).max() / np.abs(omt).max() <= 1e-6
