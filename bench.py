@@ -52,7 +52,7 @@ def parse():
                     help="threads per system for grids <= 1024 points (0 = library default)")
     ap.add_argument("--reorth", type=int, default=0, help="0 CGS2 (default), 1 DGKS-conditional")
     ap.add_argument("--window", type=int, default=0,
-                    help="FP64 march: timesteps per target launch (0 = 8; 1 = per-timestep launches)")
+                    help="FP64 march: timesteps per target launch (0 = 16; 1 = per-timestep launches)")
     ap.add_argument("--target-blocks", type=int, default=0,
                     help="FP64 march windows: persistent target blocks (0 = all resident slots)")
     ap.add_argument("--learned", action="store_true",
@@ -273,7 +273,7 @@ def main():
     T = wl.T
     nmax = max(g.N for g in wl.groups)
     mixed = wl.precision == "mixed"
-    window = args.window if args.window > 0 else 8
+    window = args.window if args.window > 0 else 16
     ctx = kp.Context(max_seeds=max(2 * (1 if mixed else window) * wl.n_seed_planes, 1), max_a=wl.a,
                      max_n=nmax,
                      precision=kp.PREC_MIXED if mixed else kp.PREC_FP64,
