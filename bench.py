@@ -34,6 +34,17 @@ sys.path.insert(0, ROOT)
 from paper_2511_17634_gb300 import synth  # noqa: E402
 
 FP64_PEAK_TFLOPS = 152 * 2070e6 * 4 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+
+
+def _measured_peak(key, fallback):
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key])
+    except (OSError, ValueError, KeyError):
+        return fallback
+
+
+BF16_PEAK_TFLOPS = _measured_peak("bf16_tflops", 1900.0)
 METRIC = "target systems solved/s to rel. residual 1e-8, projected vs plain GMRES, 1 GB300"
 
 
@@ -55,6 +66,8 @@ def parse():
                     help="FP64 march: timesteps per target launch (0 = 16; 1 = per-timestep launches)")
     ap.add_argument("--target-blocks", type=int, default=0,
                     help="FP64 march windows: persistent target blocks (0 = all resident slots)")
+    ap.add_argument("--march-steps", type=int, default=0,
+                    help="timesteps per timed march (0 = all T; fewer only for profiling runs)")
     ap.add_argument("--learned", action="store_true",
                     help="128x128x3 learned-guess measurement (bounded sample)")
     return ap.parse_args()
@@ -140,6 +153,54 @@ def oracle_sample(wl, steps, threads):
     return nsys, wall
 
 
+def oracle_error(wl, finals, steps, nsample=32):
+    """Relative error ||x_gpu - x_orc|| / ||x_orc|| of the final states (after
+    `steps` timesteps) of `nsample` target channels spread over the workload,
+    against the oracle's plain FP64 GMRES march at tolerance 1e-10."""
+    from oracle import oracle as O
+    O.build()
+    planes = [(gi, k) for gi, g in enumerate(wl.groups) for k in range(g.targets.shape[0])]
+    pick = np.unique(np.linspace(0, len(planes) - 1, nsample).round().astype(int))
+    errs = []
+    for gi, g in enumerate(wl.groups):
+        ks = [planes[p][1] for p in pick if planes[p][0] == gi]
+        if not ks:
+            continue
+        _, omt, _ = O.march(g.H, g.W, wl.T, wl.g2, g.seeds[:1], g.targets[ks],
+                            np.zeros(len(ks), np.int32), steps=steps, mode=O.MODE_PLAIN, tol_seed=1e-10,
+                            m_seed=wl.m_seed, a=wl.a, tol_ref=1e-10, m_ref=wl.m)
+        for a, b in zip(finals[gi][ks], omt):
+            errs.append(float(np.linalg.norm(a.ravel() - b.ravel()) / np.linalg.norm(b.ravel())))
+    return {"max": max(errs), "median": float(np.median(errs)), "systems": len(errs),
+            "sample": f"{len(errs)} target channels, final states after {steps} timesteps, vs the "
+                      "oracle's FP64 plain GMRES march at tol 1e-10"}
+
+
+def oracle_step_error(wl, prev, last, step, nsample=32):
+    """Per-solve relative error of timestep `step` (0-based): the oracle solves
+    the same systems as the GPU (from the GPU's own m^{step}) with plain FP64
+    GMRES to 1e-12, for `nsample` target channels spread over the workload."""
+    from oracle import oracle as O
+    O.build()
+    planes = [(gi, k) for gi, g in enumerate(wl.groups) for k in range(g.targets.shape[0])]
+    pick = np.unique(np.linspace(0, len(planes) - 1, nsample).round().astype(int))
+    errs = []
+    for gi, g in enumerate(wl.groups):
+        ks = [planes[p][1] for p in pick if planes[p][0] == gi]
+        if not ks:
+            continue
+        mt = np.ascontiguousarray(prev[gi][ks], dtype=np.float64)
+        ms = np.ascontiguousarray(g.seeds[:1].reshape(1, -1), dtype=np.float64)
+        O.march_step(g.H, g.W, 1.0 / wl.T, 1.0 / g.H, float(wl.g2[step]), ms, mt,
+                     np.zeros(len(ks), np.int32), mode=O.MODE_PLAIN, tol_seed=1e-10, m_seed=wl.m_seed,
+                     a=wl.a, tol_ref=1e-12, m_ref=wl.m)
+        for a, b in zip(last[gi][ks], mt):
+            errs.append(float(np.linalg.norm(a - b) / np.linalg.norm(b)))
+    return {"max": max(errs), "median": float(np.median(errs)), "systems": len(errs),
+            "sample": f"{len(errs)} target channels at timestep {step + 1}, same m^{{n-1}} on both "
+                      "sides, vs the oracle's FP64 GMRES at tol 1e-12"}
+
+
 def workload(args, rank=0):
     wl = synth.config(args.config, T=args.T, ntargets=args.ntargets)
     if rank:
@@ -205,7 +266,7 @@ def run_learned(args):
     ev = synth.make_group(1239, 128, 128, 3, 16, nev, tag=0)
     ctx = kp.Context(max_seeds=2 * tr.seeds.shape[0], max_a=40, max_n=16384,
                      precision=kp.PREC_MIXED)
-    net = kp.CNN(ctx, 128, 128, channels=learned.CHANNELS, max_batch=16)
+    net = kp.CNN(ctx, 128, 128, channels=learned.CHANNELS, max_batch=64)
     net.set_params(learned.init_params(1))
     t0 = time.perf_counter()
     xs, ys = learned.generate_pairs(ctx, net, tr, T, g2, steps=T, every=12)
@@ -214,6 +275,21 @@ def run_learned(args):
     hist = learned.train(net, xs, ys, epochs=args.steps, batch=16, lr=1e-3)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
+    # the network alone: forward of 64 inputs, CUDA events, after warm-up
+    xb = xs[:64].contiguous()
+    yb = torch.empty((64, 1, 128 * 128), dtype=torch.float32, device=xs.device)
+    for _ in range(3):
+        net.forward(xb, yb)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 20
+    e0.record()
+    for _ in range(reps):
+        net.forward(xb, yb)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd_s = e0.elapsed_time(e1) / 1000.0 / reps
+    ch = learned.CHANNELS
+    fwd_flops = 64 * 128 * 128 * 2 * 9 * sum(a * b for a, b in zip(ch[:-1], ch[1:]))
     del xs, ys
     dev = torch.device("cuda")
     s = torch.as_tensor(ev.seeds.reshape(len(ev.seeds), -1).copy(), device=dev)
@@ -240,6 +316,11 @@ def run_learned(args):
     for k, v in res.items():
         line[k] = {"value": nsolve / v["time"], "iters_per_solve": float(np.mean(v["iters"])),
                    "median_initial_residual": float(np.median(v["res0"]))}
+    tf = fwd_flops / fwd_s / 1e12
+    line["cnn_forward"] = {"images_per_s": 64 / fwd_s, "ms_per_64": 1000 * fwd_s,
+                           "roofline": {"bound": "tensor", "achieved": tf, "peak": BF16_PEAK_TFLOPS,
+                                        "unit": "TFLOP/s", "frac": tf / BF16_PEAK_TFLOPS,
+                                        "peak_source": "measured cuBLAS bf16 burst"}}
     line["note"] = "target-side work timed (seeds excluded); CNN inference is part of the learned time"
     print(json.dumps(line))
 
@@ -271,6 +352,7 @@ def main():
 
     wl = workload(args, rank)
     T = wl.T
+    NS = args.march_steps if 0 < args.march_steps < T else T   # timesteps per timed march
     nmax = max(g.N for g in wl.groups)
     mixed = wl.precision == "mixed"
     window = args.window if args.window > 0 else 16
@@ -297,7 +379,7 @@ def main():
     def timed(plan, k_steps, warm):
         for _ in range(warm):
             reset()
-            plan.run(0, T)
+            plan.run(0, NS)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -309,7 +391,7 @@ def main():
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            plan.run(0, T)
+            plan.run(0, NS)
             e1.record(stream)
             torch.cuda.synchronize()
             total += e0.elapsed_time(e1) / 1000.0
@@ -324,11 +406,11 @@ def main():
     proj = kp.March(ctx, groups, mode=kp.MARCH_PROJECTED, **common)
     with Clocks(local) as clk:
         t_proj = timed(proj, args.steps, args.warmup)
-    value = world * nt_planes * T * args.steps / t_proj
+    value = world * nt_planes * NS * args.steps / t_proj
 
     # per-timestep statistics and per-kernel CUDA-event times of one full march
     reset()
-    stats, tm = proj.run(0, T, stats=True, timing=True)
+    stats, tm = proj.run(0, NS, stats=True, timing=True)
     tgt_iters = sum(s.tgt_iters for s in stats)
     refine_flops = sum(s.refine_flops + (0 if mixed else s.proj_flops) for s in stats)
     refine_flops32 = sum(s.refine_flops32 + (s.proj_flops if mixed else 0) for s in stats)
@@ -343,10 +425,10 @@ def main():
             pl = kp.March(ctx, groups, mode=mode, **common)
             t = timed(pl, max(1, args.steps // 2), 1)
             reset()
-            st2, _ = pl.run(0, T, stats=True)
-            out[name] = {"value": world * nt_planes * T * max(1, args.steps // 2) / t,
+            st2, _ = pl.run(0, NS, stats=True)
+            out[name] = {"value": world * nt_planes * NS * max(1, args.steps // 2) / t,
                          "unit": "systems/s",
-                         "iters_per_solve": sum(s.tgt_iters for s in st2) / (nt_planes * T)}
+                         "iters_per_solve": sum(s.tgt_iters for s in st2) / (nt_planes * NS)}
             pl.close()
 
     # end to end through the public API: host images in, final states out
@@ -367,7 +449,7 @@ def main():
             a.copy_(b, non_blocking=True)
         for a, b in zip(st_t, h_t):
             a.copy_(b, non_blocking=True)
-        proj.run(0, T)
+        proj.run(0, NS)
         for a, b in zip(o_t, st_t):
             a.copy_(b, non_blocking=True)
         e1.record(stream)
@@ -378,7 +460,17 @@ def main():
         t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_total = float(t.item())
-    e2e_value = world * nt_planes * T * e2e_steps / e2e_total
+    e2e_value = world * nt_planes * NS * e2e_steps / e2e_total
+
+    err = None
+    if rank == 0:
+        traj = oracle_error(wl, [x.numpy() for x in o_t], steps=NS)
+        reset()
+        proj.run(0, NS - 1)
+        prev = [x.cpu().numpy() for x in st_t]
+        proj.run(NS - 1, 1)
+        last = [x.cpu().numpy() for x in st_t]
+        err = {"per_solve": oracle_step_error(wl, prev, last, NS - 1), "trajectory": traj}
 
     cpu = None
     if rank == 0 and world == 1:
@@ -396,7 +488,7 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 Krylov + f64 refinement" if mixed else "f64",
             "data": "synthetic (seeded blob images shaped like the paper's 32x32 CIFAR-10 set)",
-            "config": {"workload": wl.name, "T": T, "targets": nt_planes,
+            "config": {"workload": wl.name, "T": T, "timesteps_per_march": NS, "targets": nt_planes,
                        "seeds": wl.n_seed_planes, "grid": [g.H for g in wl.groups],
                        "tol": wl.tol, "m": wl.m, "parallelism": f"replicas x{world}",
                        "block_threads": args.block_threads or 256,
@@ -408,13 +500,18 @@ def main():
             "gpu_launches": launches_per_step * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                         "traffic": None, "kernel": "gmres_fp64_kernel (targets: projection + refine)",
+                         "traffic": None if mixed or window != 16 or wl.name != "blobs-32x32x3-10seeds-256targets"
+                         else 18.85e6,
+                         "traffic_note": "DRAM bytes per target launch (16 timesteps x 768 systems), ncu "
+                                         "capture of the first window; the path is L2-resident",
+                         "kernel": "gmres_fp64_kernel (targets: projection + refine)",
                          "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz"},
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
-            "iters_per_solve": tgt_iters / (nt_planes * T),
+            "iters_per_solve": tgt_iters / (nt_planes * NS),
             "fp32_tflops_target_kernel": refine_flops32 / (tm.refine_ms / 1000.0) / 1e12,
             "max_rel_res": max_res, "not_converged": not_conv,
+            "oracle_error": err,
             "kernel_ms_per_march": {"seed_solve_and_store": tm.seed_ms,
                                     "project_and_refine": tm.refine_ms,
                                     "sequential_total": tm.step_ms},

@@ -222,6 +222,16 @@ struct kp_cnn {
   double* d_loss = nullptr;
   int* d_err = nullptr;
   int Cmax = 0;
+  // inference on the implicit-GEMM convolutions of kp_conv_tc.cu (no im2col
+  // in memory): input <= 16 channels (2 chunks of 8), hidden layers <= 32
+  // (4 chunks), output <= 16 (MMA N = 16)
+  bool fused = false;
+  kp::ConvGeom geo{};
+  __nv_bfloat16* pin = nullptr;                 // [maxB][2][Rp][8]
+  __nv_bfloat16* px[2] = {nullptr, nullptr};    // [maxB][4][Rp][8], alternating layers
+  __nv_bfloat16* wf = nullptr;                  // per layer [9][cic][nout][8]
+  std::vector<size_t> wf_off;
+  std::vector<int> cic, nout;
 };
 
 namespace {
@@ -283,14 +293,33 @@ kp_status forward_impl(kp_cnn* n, int B, const float* in) {
 
 kp_status refresh_bf16(kp_cnn* n) {
   cudaStream_t st = n->ctx->stream;
+  cudaError_t e = cudaSuccess;
   for (int l = 0; l < n->L; ++l) {
     const int cin = n->ch[l], cout = n->ch[l + 1];
     weights_bf16_kernel<<<grid_for((size_t)cout * cin * 9), 256, 0, st>>>(
         n->params + n->woff[l], n->wb + n->wb_off[l], (int)up8(9 * cin), n->wb + n->w2b_off[l],
         (int)up8(9 * cout), cin, cout);
+    if (n->fused && e == cudaSuccess)
+      e = kp::launch_conv_weights(n->params + n->woff[l], cin, cout, n->cic[l], n->nout[l], n->wf + n->wf_off[l], st);
   }
-  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGetLastError();
   return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN weights");
+}
+
+// Inference: input planes -> padded BF16 rows, then one implicit-GEMM
+// convolution launch per layer, the last writing FP32 planes.
+kp_status forward_fused(kp_cnn* n, int B, const float* in, float* out) {
+  cudaStream_t st = n->ctx->stream;
+  cudaError_t e = kp::launch_planes_to_padded(in, B, n->ch[0], 2, n->geo, n->pin, st);
+  const __nv_bfloat16* X = n->pin;
+  for (int l = 0; l < n->L && e == cudaSuccess; ++l) {
+    const bool last = l + 1 == n->L;
+    __nv_bfloat16* Y = last ? nullptr : n->px[l & 1];
+    e = kp::launch_conv3x3(X, B, n->cic[l], n->wf + n->wf_off[l], n->params + n->boff[l], n->ch[l + 1],
+                           n->nout[l], n->geo, Y, last ? out : nullptr, n->d_err, n->ctx->sms, st);
+    X = Y;
+  }
+  return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN forward (implicit GEMM)");
 }
 
 // forward + MSE + backward into n->grads; loss on the host if wanted
@@ -360,6 +389,7 @@ kp_status kp_cnn_destroy(kp_cnn* n) {
   cudaFree(n->params); cudaFree(n->grads); cudaFree(n->adam_m); cudaFree(n->adam_v); cudaFree(n->wb);
   cudaFree(n->act); cudaFree(n->dz); cudaFree(n->dz2); cudaFree(n->col); cudaFree(n->colT); cudaFree(n->rows);
   cudaFree(n->cm); cudaFree(n->tiles); cudaFree(n->d_loss); cudaFree(n->d_err);
+  cudaFree(n->pin); cudaFree(n->px[0]); cudaFree(n->px[1]); cudaFree(n->wf);
   delete n;
   return KP_OK;
 }
@@ -408,6 +438,27 @@ kp_status kp_cnn_create(kp_ctx* c, int H, int W, int max_batch, int nlayers, con
   if (e == cudaSuccess) e = cudaMemset(n->params, 0, np * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(n->adam_m, 0, np * sizeof(float));
   if (e == cudaSuccess) e = cudaMemset(n->adam_v, 0, np * sizeof(float));
+  // implicit-GEMM inference buffers (zero rows stay zero: never written)
+  n->fused = nlayers >= 2 && n->ch[0] <= 16 && n->ch[nlayers] <= 16;
+  n->geo = kp::conv_geom(H, W);
+  size_t nwf = 0;
+  for (int l = 0; l < nlayers; ++l) {
+    n->cic.push_back(l == 0 ? 2 : 4);
+    n->nout.push_back(l + 1 == nlayers ? 16 : 32);
+    n->wf_off.push_back(nwf);
+    nwf += (size_t)9 * n->cic[l] * n->nout[l] * 8;
+    if (kp::conv_smem_bytes(n->geo, n->cic[l], n->nout[l]) > c->smem_optin) n->fused = false;
+  }
+  if (n->fused && e == cudaSuccess) {
+    const size_t rows = (size_t)max_batch * n->geo.Rp * 8;
+    e = cudaMalloc((void**)&n->pin, 2 * rows * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMemset(n->pin, 0, 2 * rows * sizeof(__nv_bfloat16));
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = cudaMalloc((void**)&n->px[k], 4 * rows * sizeof(__nv_bfloat16));
+      if (e == cudaSuccess) e = cudaMemset(n->px[k], 0, 4 * rows * sizeof(__nv_bfloat16));
+    }
+    if (e == cudaSuccess) e = cudaMalloc((void**)&n->wf, nwf * sizeof(__nv_bfloat16));
+  }
   if (e != cudaSuccess) {
     kp_status r = kp::cuda_error(c, e, "CNN allocation");
     kp_cnn_destroy(n);
@@ -440,6 +491,7 @@ kp_status kp_cnn_get_params(kp_cnn* n, float* host) {
 
 kp_status kp_cnn_forward(kp_cnn* n, int B, const float* in, float* out) {
   if (!n || B < 1 || B > n->maxB || !in || !out) return n ? kp::set_error(n->ctx, KP_ERR_ARG, "CNN forward: bad batch") : KP_ERR_ARG;
+  if (n->fused) return forward_fused(n, B, in, out);
   kp_status s = forward_impl(n, B, in);
   if (s != KP_OK) return s;
   cudaError_t e = cudaMemcpyAsync(out, n->act + n->act_off[n->L - 1], (size_t)B * n->P * n->ch[n->L] * sizeof(float),

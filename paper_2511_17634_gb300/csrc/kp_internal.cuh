@@ -440,6 +440,20 @@ cudaError_t launch_apply(const SysDesc* sys, int nsys, int mode, cudaStream_t st
 cudaError_t launch_factor(const FactorParams& p, cudaStream_t st);
 cudaError_t launch_project_fp64(const ProjParams& p, int ept, int nt, cudaStream_t st);
 cudaError_t launch_advance(int* step, cudaStream_t st, int by = 1, int* zero = nullptr);
+
+// 3x3 convolutions on the tensor cores (kp_conv_tc.cu): padded-column BF16
+// activation layout [B][chunks of 8 channels][Rp rows][8], pixel (i, j) at row
+// halo + i*(H+2) + 1 + j, zero rows elsewhere.
+struct ConvGeom { int H, W, halo, nst, Rp; };
+ConvGeom conv_geom(int H, int W);
+size_t conv_smem_bytes(const ConvGeom& g, int cic, int nout);
+cudaError_t launch_conv_weights(const float* Wl, int cin, int cout, int cic, int nout, __nv_bfloat16* wf,
+                                cudaStream_t st);
+cudaError_t launch_planes_to_padded(const float* X, int B, int C, int chunks, const ConvGeom& g,
+                                    __nv_bfloat16* out, cudaStream_t st);
+cudaError_t launch_conv3x3(const __nv_bfloat16* in, int B, int cic, const __nv_bfloat16* wf, const float* bias,
+                           int cout, int nout, const ConvGeom& g, __nv_bfloat16* out_pad, float* out_f32,
+                           int* err, int sms, cudaStream_t st);
 // Resident blocks per SM of the FP64 solver shape (0 if unknown).
 int gmres_fp64_blocks_per_sm(int ept, int nt, size_t smem);
 // dst[q] = src[perm[q]] (gather) or dst[perm[q]] = src[q] (scatter), planes of n doubles

@@ -94,9 +94,13 @@ def version() -> str:
     return lib().kp_version().decode()
 
 
-def _ptrs(vs):
-    """Host array of device pointers for a 2-D tensor (rows) or a list of tensors."""
+def ptrs(vs):
+    """Host array of device pointers for a 2-D tensor (rows), a list of tensors,
+    or an array of pointers made by an earlier call (returned unchanged)."""
     import torch
+    if isinstance(vs, np.ndarray):
+        assert vs.dtype == np.uint64 and vs.ndim == 1
+        return np.ascontiguousarray(vs)
     if isinstance(vs, torch.Tensor):
         assert vs.is_cuda and vs.dtype == torch.float64 and vs.dim() == 2 and vs.stride(1) == 1
         base = vs.data_ptr()
@@ -128,14 +132,14 @@ class Ops:
 def make_ops(H, W, dt, g2, h, mtilde, fx=None, fy=None):
     """kp_op descriptors for systems of one grid size; dt, g2, h may be
     per-system arrays."""
-    mt = _ptrs(mtilde)
+    mt = ptrs(mtilde)
     n = len(mt)
     ops = np.zeros(n, dtype=OP_DTYPE)
     ops["H"], ops["W"] = H, W
     ops["dt"], ops["g2"], ops["h"] = dt, g2, h
     ops["mt"] = mt
-    ops["fx"] = _ptrs(fx) if fx is not None else 0
-    ops["fy"] = _ptrs(fy) if fy is not None else 0
+    ops["fx"] = ptrs(fx) if fx is not None else 0
+    ops["fy"] = ptrs(fy) if fy is not None else 0
     return Ops(ops, (mtilde, fx, fy))
 
 
@@ -192,26 +196,26 @@ class Context:
         return a.ctypes.data_as(ctypes.c_void_p)
 
     def apply(self, ops, x, y):
-        self._check(lib().kp_apply(self._h, len(ops), self._arr(ops), self._arr(_ptrs(x)),
-                                   self._arr(_ptrs(y))))
+        self._check(lib().kp_apply(self._h, len(ops), self._arr(ops), self._arr(ptrs(x)),
+                                   self._arr(ptrs(y))))
 
     def rhs(self, ops, mprev, b):
-        self._check(lib().kp_rhs(self._h, len(ops), self._arr(ops), self._arr(_ptrs(mprev)),
-                                 self._arr(_ptrs(b))))
+        self._check(lib().kp_rhs(self._h, len(ops), self._arr(ops), self._arr(ptrs(mprev)),
+                                 self._arr(ptrs(b))))
 
     def seed_solve(self, ops, b, x, tol=1e-10, m=40, maxit=1000, info=None):
         if info is None:
             info = info_tensor(len(ops))
-        self._check(lib().kp_seed_solve(self._h, len(ops), self._arr(ops), self._arr(_ptrs(b)),
-                                        self._arr(_ptrs(x)), tol, m, maxit,
+        self._check(lib().kp_seed_solve(self._h, len(ops), self._arr(ops), self._arr(ptrs(b)),
+                                        self._arr(ptrs(x)), tol, m, maxit,
                                         ctypes.c_void_p(info.data_ptr())))
         return info
 
     def refine(self, ops, b, x, tol=1e-8, m=40, maxit=1000, info=None):
         if info is None:
             info = info_tensor(len(ops))
-        self._check(lib().kp_refine(self._h, len(ops), self._arr(ops), self._arr(_ptrs(b)),
-                                    self._arr(_ptrs(x)), tol, m, maxit,
+        self._check(lib().kp_refine(self._h, len(ops), self._arr(ops), self._arr(ptrs(b)),
+                                    self._arr(ptrs(x)), tol, m, maxit,
                                     ctypes.c_void_p(info.data_ptr())))
         return info
 
@@ -220,18 +224,18 @@ class Context:
 
     def project_targets(self, seed_id, timestep, ops, r, x):
         self._check(lib().kp_project_targets(self._h, seed_id, timestep, len(ops), self._arr(ops),
-                                             self._arr(_ptrs(r)), self._arr(_ptrs(x))))
+                                             self._arr(ptrs(r)), self._arr(ptrs(x))))
 
     def project_targets_multi(self, timestep, seed_ids, ops, r, x):
         ids = np.ascontiguousarray(seed_ids, dtype=np.int32)
         self._check(lib().kp_project_targets_multi(self._h, timestep, len(ops), self._arr(ids),
-                                                   self._arr(ops), self._arr(_ptrs(r)),
-                                                   self._arr(_ptrs(x))))
+                                                   self._arr(ops), self._arr(ptrs(r)),
+                                                   self._arr(ptrs(x))))
 
     def residual(self, ops, b, x, r):
         """r = b - A x (FP64)."""
-        self._check(lib().kp_residual(self._h, len(ops), self._arr(ops), self._arr(_ptrs(b)),
-                                      self._arr(_ptrs(x)), self._arr(_ptrs(r))))
+        self._check(lib().kp_residual(self._h, len(ops), self._arr(ops), self._arr(ptrs(b)),
+                                      self._arr(ptrs(x)), self._arr(ptrs(r))))
 
     def project_gemm_bf16(self, B, V, C, K=None):
         """C[t][i] = sum_k B[t][k] V[i][k] on the tensor cores (BF16 in, FP32 out)."""
@@ -400,21 +404,21 @@ class CNN:
 
     def pack_inputs(self, img, seed, tau, out):
         """out [B][6][H*W] float32 from FP64 image and seed-state planes (rows or lists)."""
-        pi, ps = _ptrs(img), _ptrs(seed)
+        pi, ps = ptrs(img), ptrs(seed)
         self.ctx._check(lib().kp_cnn_pack_inputs(self._h, len(pi), pi.ctypes.data_as(ctypes.c_void_p),
                                                  ps.ctypes.data_as(ctypes.c_void_p), float(tau),
                                                  ctypes.c_void_p(out.data_ptr())))
 
     def pack_target(self, a, b, out):
         """out [B][1][H*W] float32 = a - b (FP64 planes)."""
-        pa, pb = _ptrs(a), _ptrs(b)
+        pa, pb = ptrs(a), ptrs(b)
         self.ctx._check(lib().kp_cnn_pack_target(self._h, len(pa), pa.ctypes.data_as(ctypes.c_void_p),
                                                  pb.ctypes.data_as(ctypes.c_void_p),
                                                  ctypes.c_void_p(out.data_ptr())))
 
     def add_guess(self, delta, base, x):
         """x = base + delta (FP64 planes; delta float32 [B][1][H*W])."""
-        pb, px = _ptrs(base), _ptrs(x)
+        pb, px = ptrs(base), ptrs(x)
         self.ctx._check(lib().kp_cnn_add_guess(self._h, len(pb), ctypes.c_void_p(delta.data_ptr()),
                                                pb.ctypes.data_as(ctypes.c_void_p),
                                                px.ctypes.data_as(ctypes.c_void_p)))

@@ -133,12 +133,14 @@ def step_compare(ctx, net, group, T, g2, n, seeds_prev, tgt_prev, tol_seed=1e-10
         x = x0.clone()
         return x0, x, ctx.refine(tops, tb, x, tol=tol, m=m, maxit=1000)
 
-    seed_rows = [sx[int(k)] for k in group.target_seed]
+    # pointer tables of the fixed target -> seed map, built once like a plan
+    seed_rows = kp.ptrs([sx[int(k)] for k in group.target_seed])
+    img_rows = kp.ptrs(img)
     xin = torch.empty((nt, 6, H * W), dtype=torch.float32, device=tgt_prev.device)
     delta = torch.empty((nt, 1, H * W), dtype=torch.float32, device=tgt_prev.device)
 
     def learned_():
-        net.pack_inputs([img[k] for k in range(nt)], seed_rows, n / T, xin)
+        net.pack_inputs(img_rows, seed_rows, n / T, xin)
         for k in range(0, nt, net.max_batch):
             net.forward(xin[k:k + net.max_batch], delta[k:k + net.max_batch])
         x0 = torch.empty_like(tgt_prev)

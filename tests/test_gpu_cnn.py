@@ -94,3 +94,32 @@ def test_training_reduces_loss(kp):
     tg = torch.as_tensor(t.reshape(B, 1, -1), dtype=torch.float32, device="cuda")
     losses = [net.train_step(xin, tg, k + 1, lr=2e-3) for k in range(150)]
     assert losses[-1] < 0.05 * losses[0], (losses[0], losses[-1])
+
+
+@pytest.mark.parametrize("H,W,B", [(7, 5, 1), (40, 30, 3), (128, 128, 10)])
+def test_implicit_gemm_forward_exact_shifts(kp, H, W, B):
+    # two one-tap layers shift the image twice; small integers keep every
+    # product and sum exact in BF16 x BF16 -> FP32, so the tensor-core
+    # implicit-GEMM path (padded-column layout, halo rows, several 512-row
+    # super tiles per CTA at 128x128 x 10) must equal the FP64 reference bit
+    # for bit, for every pair of taps
+    rng = np.random.default_rng(H + W + B)
+    x = rng.integers(0, 4, size=(B, 1, W, H)).astype(np.float64)
+    xin = torch.as_tensor(x.reshape(B, 1, -1), dtype=torch.float32, device="cuda")
+    out = torch.zeros((B, 1, W * H), dtype=torch.float32, device="cuda")
+    ctx = kp.Context(max_n=16384)
+    net = kp.CNN(ctx, H, W, channels=(1, 1, 1), max_batch=B)
+    pairs = [(t1, t2) for t1 in range(9) for t2 in range(9)]
+    if H * W > 4096:
+        pairs = [(0, 8), (8, 0), (1, 7), (5, 3), (4, 4), (2, 6)]
+    for t1, t2 in pairs:
+        w1 = np.zeros((1, 1, 3, 3))
+        w1[0, 0, t1 // 3, t1 % 3] = 1.0
+        w2 = np.zeros((1, 1, 3, 3))
+        w2[0, 0, t2 // 3, t2 % 3] = 2.0
+        p = R.flatten([(w1, np.zeros(1)), (w2, np.array([0.5]))])
+        net.set_params(p)
+        net.forward(xin, out)
+        torch.cuda.synchronize()
+        ref = R.forward(p, (1, 1, 1), x)[-1]
+        assert np.array_equal(out.cpu().numpy().reshape(ref.shape), ref), (t1, t2)

@@ -36,7 +36,7 @@ def kp():
 
 def _static_refine(K, ops, b, x, tol, m, maxit, info, stream):
     L = K.lib()
-    pb, px = K._ptrs(b), K._ptrs(x)
+    pb, px = K.ptrs(b), K.ptrs(x)
     return L.kp_refine_static(len(ops), K.Context._arr(ops), pb.ctypes.data_as(ctypes.c_void_p),
                               px.ctypes.data_as(ctypes.c_void_p), tol, m, maxit,
                               ctypes.c_void_p(info.data_ptr()), ctypes.c_void_p(stream))
