@@ -60,8 +60,12 @@ def parse():
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=12)
     ap.add_argument("--block-threads", type=int, default=0,
-                    help="threads per system for grids <= 1024 points (0 = library default)")
+                    help="threads per system for grids <= 1024 points (0 = library default: 128)")
     ap.add_argument("--reorth", type=int, default=0, help="0 CGS2 (default), 1 DGKS-conditional")
+    ap.add_argument("--blocks-per-sm", type=int, default=0,
+                    help="resident solver blocks per SM for grids <= 1024 points (0 = library default)")
+    ap.add_argument("--smem-vectors", type=int, default=0,
+                    help="Krylov vectors kept in shared memory per system (0 = library default)")
     ap.add_argument("--window", type=int, default=0,
                     help="FP64 march: timesteps per target launch (0 = 16; 1 = per-timestep launches)")
     ap.add_argument("--target-blocks", type=int, default=0,
@@ -359,7 +363,8 @@ def main():
     ctx = kp.Context(max_seeds=max(2 * (1 if mixed else window) * wl.n_seed_planes, 1), max_a=wl.a,
                      max_n=nmax,
                      precision=kp.PREC_MIXED if mixed else kp.PREC_FP64,
-                     block_threads=args.block_threads, reorth=args.reorth)
+                     block_threads=args.block_threads, reorth=args.reorth,
+                     smem_vectors=args.smem_vectors, blocks_per_sm=args.blocks_per_sm)
     dev = torch.device("cuda", torch.cuda.current_device())
     img_s = [torch.as_tensor(g.seeds.reshape(len(g.seeds), -1), device=dev) for g in wl.groups]
     img_t = [torch.as_tensor(g.targets.reshape(len(g.targets), -1), device=dev) for g in wl.groups]
@@ -491,7 +496,9 @@ def main():
             "config": {"workload": wl.name, "T": T, "timesteps_per_march": NS, "targets": nt_planes,
                        "seeds": wl.n_seed_planes, "grid": [g.H for g in wl.groups],
                        "tol": wl.tol, "m": wl.m, "parallelism": f"replicas x{world}",
-                       "block_threads": args.block_threads or 256,
+                       "block_threads": args.block_threads or (256 if mixed else 128),
+                       "smem_vectors": args.smem_vectors or "auto",
+                       "blocks_per_sm": args.blocks_per_sm or "auto",
                        "orthogonalisation": "CGS2" if args.reorth == 0 else "CGS+DGKS",
                        "window": 1 if mixed else window,
                        "l2": "flushed between timed steps (512 MiB write)"},

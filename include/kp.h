@@ -72,7 +72,13 @@ typedef struct {
                         1: second pass only when the first removed more than
                         half of the vector's norm (Daniel-Gragg-Kaufman-Stewart)  */
   int block_threads; /* threads per system for grids of <= 1024 points: 256 (4
-                        points per thread), 128 (8 points per thread), 0 = 256   */
+                        points per thread), 128 (8), 64 (16); 0 = 128 with 4
+                        blocks per SM (FP64) or 256 with 2 (mixed precision) */
+  int blocks_per_sm; /* resident solver blocks per SM for grids of <= 1024
+                        points (caps registers per thread and sizes the
+                        shared-memory window): 256 threads: 2 or 3; 128: 2, 3
+                        or 4; 64: 4; 0 = the default above (2 for an explicit
+                        256 or 128, 4 for 64).  Mixed precision: 2 always.   */
 } kp_options;
 
 /* Operator of one system (Sec. 2.3): A(m~; g^2, dt, h, f).  `mtilde` is the

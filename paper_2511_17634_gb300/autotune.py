@@ -4,7 +4,8 @@ workload by timing a few calibration timesteps of the real march, and caches
 the choice in a JSON file keyed by (device, grid sizes, batch, precision).
 
 Candidates: m in {20, 30, 40, 60} x shared-memory window in {auto, small} x
-threads per system in {256, 128} (grids of up to 1024 points).
+(threads per system, resident blocks per SM) in {(256, 2), (128, 3), (128, 4),
+(64, 4)} (FP64 grids of up to 1024 points; one shape otherwise).
 The timing runs through the C ABI (kp_march_*) on the GPU; only the choice of
 the fastest candidate and the cache are host logic.
 """
@@ -15,7 +16,7 @@ import os
 
 M_CANDIDATES = (20, 30, 40, 60)
 WINDOW_CANDIDATES = (0, 6)      # 0 = automatic (two blocks per SM when N <= 1024)
-THREAD_CANDIDATES = (256, 128)  # threads per system for grids of <= 1024 points
+SHAPE_CANDIDATES = ((256, 2), (128, 3), (128, 4), (64, 4))   # (threads, blocks per SM), N <= 1024
 
 
 def cache_key(device: str, grids, nseed: int, ntgt: int, precision: str, mode: int) -> str:
@@ -46,8 +47,9 @@ def choose(timings: dict):
 
 
 def tune(wl, mode=0, steps=4, cache_path=None, time_fn=None):
-    """Returns {'m', 'smem_vectors', 'block_threads', 'timings'} for workload `wl`
-    (synth.Workload).  time_fn(m, S, threads) -> seconds overrides the GPU timing."""
+    """Returns {'m', 'smem_vectors', 'block_threads', 'blocks_per_sm', 'timings'}
+    for workload `wl` (synth.Workload).  time_fn(m, S, (threads, blocks per SM))
+    -> seconds overrides the GPU timing."""
     precision = wl.precision
     if time_fn is None:
         import torch
@@ -61,15 +63,16 @@ def tune(wl, mode=0, steps=4, cache_path=None, time_fn=None):
         return cache[key]
     if time_fn is None:
         time_fn = _gpu_timer(wl, mode, steps)
-    threads = THREAD_CANDIDATES if max(g.N for g in wl.groups) <= 1024 else (0,)
+    small = max(g.N for g in wl.groups) <= 1024 and precision != "mixed"
+    shapes = SHAPE_CANDIDATES if small else ((0, 0),)
     timings = {}
     for m in M_CANDIDATES:
         for S in WINDOW_CANDIDATES:
-            for nt in threads:
-                timings[(m, S, nt)] = time_fn(m, S, nt)
-    m, S, nt = choose(timings)
-    res = {"m": m, "smem_vectors": S, "block_threads": nt,
-           "timings": {f"m{a}_S{b}_t{c}": t for (a, b, c), t in timings.items()}}
+            for sh in shapes:
+                timings[(m, S, sh)] = time_fn(m, S, sh)
+    m, S, (nt, mb) = choose(timings)
+    res = {"m": m, "smem_vectors": S, "block_threads": nt, "blocks_per_sm": mb,
+           "timings": {f"m{a}_S{b}_t{c[0]}x{c[1]}": t for (a, b, c), t in timings.items()}}
     if cache_path:
         cache[key] = res
         save_cache(cache_path, cache)
@@ -87,9 +90,10 @@ def _gpu_timer(wl, mode, steps):
     nmax = max(g.N for g in wl.groups)
     prec = kp.PREC_MIXED if wl.precision == "mixed" else kp.PREC_FP64
 
-    def run(m, S, nt):
+    def run(m, S, shape):
         ctx = kp.Context(max_seeds=max(2 * wl.n_seed_planes, 1), max_a=min(m, 47), max_n=nmax,
-                         precision=prec, smem_vectors=S, block_threads=nt)
+                         precision=prec, smem_vectors=S, block_threads=shape[0],
+                         blocks_per_sm=shape[1])
         ss = [x.clone() for x in seeds]
         tt = [x.clone() for x in tgts]
         groups = [(ss[k], tt[k], g.target_seed, g.H, g.W) for k, g in enumerate(wl.groups)]

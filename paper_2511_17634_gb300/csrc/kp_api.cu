@@ -38,13 +38,26 @@ kp_status cuda_error(kp_ctx* c, cudaError_t e, const char* what) {
 cudaError_t launch_solver(const GmresParams& p, const Shape& sh, bool mixed, cudaStream_t st) {
   if (sh.cs > 0) return launch_gmres_cluster(p, sh.ept, sh.nt, sh.cs, sh.smem, st);
   return mixed ? launch_gmres_mixed(p, sh.ept, sh.nt, sh.smem, st)
-               : launch_gmres_fp64(p, sh.ept, sh.nt, sh.smem, st);
+               : launch_gmres_fp64(p, sh.ept, sh.nt, sh.minb, sh.smem, st);
 }
 
 kp_status gmres_shape(kp_ctx* c, int nmax, int m, Shape* out, bool mixed, int wmin) {
   Shape sh;
-  if (nmax <= 1024 && c->opt.block_threads == 128) { sh.ept = 8; sh.nt = 128; }
-  else if (nmax <= 1024) { sh.ept = 4; sh.nt = 256; }
+  sh.minb = 1;
+  if (nmax <= 1024) {
+    // default (FP64): 128 threads x 8 points, 4 resident blocks per SM -- more
+    // independent systems per SM hide the per-step barriers and the serial
+    // Givens work better than 256 x 4 at 2 blocks (measured: 4.0 vs 3.3 M
+    // systems/s on the 32x32x3 march)
+    sh.nt = c->opt.block_threads ? c->opt.block_threads : (mixed ? 256 : 128);
+    sh.ept = 1024 / sh.nt;
+    sh.minb = c->opt.blocks_per_sm ? c->opt.blocks_per_sm : (sh.nt == 128 && !c->opt.block_threads ? 4
+                                                             : sh.nt == 64 ? 4 : 2);
+    if (mixed) {                                 // the FP32 solver has the 2-block 256/128 shapes
+      sh.minb = 2;
+      if (sh.nt == 64) { sh.nt = 128; sh.ept = 8; }
+    }
+  }
   else if (nmax <= 4096) { sh.ept = 8; sh.nt = 512; }
   else if (mixed) {
     // a cluster of cs CTAs, each holding W/cs whole columns (<= 2048 points)
@@ -62,8 +75,10 @@ kp_status gmres_shape(kp_ctx* c, int nmax, int m, Shape* out, bool mixed, int wm
   const size_t per = (size_t)npad * (mixed ? sizeof(float) : sizeof(double));
   int S = c->opt.smem_vectors;
   if (S <= 0) {
-    // small systems: leave room for two resident blocks per SM
-    const size_t budget = (npad <= 1024 && !sh.cs) ? c->smem_optin / 2 : c->smem_optin;   // 2 blocks/SM
+    // small systems: leave room for minb resident blocks per SM (1 KB of
+    // shared memory per block is reserved by the hardware)
+    const size_t budget = (npad <= 1024 && !sh.cs) ? c->smem_optin / sh.minb - (sh.minb > 2 ? 1024 : 0)
+                                                   : c->smem_optin;
     S = budget > fixed ? (int)((budget - fixed) / per) : 0;
   }
   S = std::min(S, m + 1);
@@ -258,6 +273,7 @@ void kp_options_default(kp_options* o) {
   o->smem_vectors = 0;
   o->reorth = 0;
   o->block_threads = 0;
+  o->blocks_per_sm = 0;
 }
 
 kp_status kp_create(kp_ctx** out, const kp_options* opt, void* stream) {
@@ -269,8 +285,16 @@ kp_status kp_create(kp_ctx** out, const kp_options* opt, void* stream) {
   if (o.max_seeds < 1 || o.max_a < 1 || o.max_a > kp::kMaxM || o.max_n < 1 || o.max_n > 16384 ||
       (o.precision != KP_PREC_FP64 && o.precision != KP_PREC_MIXED) ||
       o.smem_vectors < 0 || (o.reorth != 0 && o.reorth != 1) ||
-      (o.block_threads != 0 && o.block_threads != 128 && o.block_threads != 256))
+      (o.block_threads != 0 && o.block_threads != 64 && o.block_threads != 128 && o.block_threads != 256))
     return KP_ERR_ARG;
+  {
+    // solver shapes compiled for grids of <= 1024 points: (threads, blocks per SM)
+    const int bt = o.block_threads ? o.block_threads : 128;
+    const int mb = o.blocks_per_sm ? o.blocks_per_sm : (!o.block_threads || bt == 64 ? 4 : 2);
+    const bool ok = (bt == 256 && (mb == 2 || mb == 3)) || (bt == 128 && mb >= 2 && mb <= 4) ||
+                    (bt == 64 && mb == 4);
+    if (!ok || o.blocks_per_sm < 0) return KP_ERR_ARG;
+  }
   kp_ctx* c = new (std::nothrow) kp_ctx();
   if (!c) return KP_ERR_OOM;
   c->opt = o;

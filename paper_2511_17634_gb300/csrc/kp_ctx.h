@@ -71,6 +71,7 @@ namespace kp {
 // Launch shape of the GMRES kernel family for systems of up to nmax unknowns.
 struct Shape {
   int ept = 0, nt = 0, S = 0;
+  int minb = 1;   // resident blocks per SM the kernel is compiled for (launch bounds)
   size_t smem = 0;
   int cs = 0;   // > 0: thread-block cluster of cs CTAs per system (slices of W/cs columns)
 };

@@ -620,10 +620,14 @@ static cudaError_t launch_one(const GmresParams& p, size_t smem, cudaStream_t st
   return cudaGetLastError();
 }
 
-cudaError_t launch_gmres_fp64(const GmresParams& p, int ept, int nt, size_t smem,
+cudaError_t launch_gmres_fp64(const GmresParams& p, int ept, int nt, int minb, size_t smem,
                               cudaStream_t st) {
-  if (ept == 4 && nt == 256) return launch_one<4, 256, 2>(p, smem, st);
-  if (ept == 8 && nt == 128) return launch_one<8, 128, 2>(p, smem, st);
+  if (ept == 4 && nt == 256 && minb == 2) return launch_one<4, 256, 2>(p, smem, st);
+  if (ept == 4 && nt == 256 && minb == 3) return launch_one<4, 256, 3>(p, smem, st);
+  if (ept == 8 && nt == 128 && minb == 2) return launch_one<8, 128, 2>(p, smem, st);
+  if (ept == 8 && nt == 128 && minb == 3) return launch_one<8, 128, 3>(p, smem, st);
+  if (ept == 8 && nt == 128 && minb == 4) return launch_one<8, 128, 4>(p, smem, st);
+  if (ept == 16 && nt == 64 && minb == 4) return launch_one<16, 64, 4>(p, smem, st);
   if (ept == 8 && nt == 512) return launch_one<8, 512, 1>(p, smem, st);
   return cudaErrorInvalidValue;
 }
@@ -647,15 +651,19 @@ cudaError_t launch_advance(int* step, cudaStream_t st, int by, int* zero) {
   return cudaGetLastError();
 }
 
-int gmres_fp64_blocks_per_sm(int ept, int nt, size_t smem) {
+int gmres_fp64_blocks_per_sm(int ept, int nt, int minb, size_t smem) {
   int n = 0;
   cudaError_t e = cudaErrorInvalidValue;
   auto occ = [&](auto k, int threads) {
     e = allow_max_smem(k, smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem);
   };
-  if (ept == 4 && nt == 256) occ(gmres_fp64_kernel<4, 256, 2>, 256);
-  else if (ept == 8 && nt == 128) occ(gmres_fp64_kernel<8, 128, 2>, 128);
+  if (ept == 4 && nt == 256 && minb == 2) occ(gmres_fp64_kernel<4, 256, 2>, 256);
+  else if (ept == 4 && nt == 256 && minb == 3) occ(gmres_fp64_kernel<4, 256, 3>, 256);
+  else if (ept == 8 && nt == 128 && minb == 2) occ(gmres_fp64_kernel<8, 128, 2>, 128);
+  else if (ept == 8 && nt == 128 && minb == 3) occ(gmres_fp64_kernel<8, 128, 3>, 128);
+  else if (ept == 8 && nt == 128 && minb == 4) occ(gmres_fp64_kernel<8, 128, 4>, 128);
+  else if (ept == 16 && nt == 64 && minb == 4) occ(gmres_fp64_kernel<16, 64, 4>, 64);
   else if (ept == 8 && nt == 512) occ(gmres_fp64_kernel<8, 512, 1>, 512);
   return e == cudaSuccess ? n : 0;
 }

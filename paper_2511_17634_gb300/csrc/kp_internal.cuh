@@ -422,7 +422,7 @@ struct ProjTile {
 };
 
 // Launchers (defined in the .cu files; return a cudaError_t of the launch).
-cudaError_t launch_gmres_fp64(const GmresParams& p, int ept, int nt, size_t smem,
+cudaError_t launch_gmres_fp64(const GmresParams& p, int ept, int nt, int minb, size_t smem,
                               cudaStream_t st);
 size_t gmres_fp64_smem_bytes(int ept, int nt, int S, int m);
 size_t gmres_mixed_smem_bytes(int ept, int nt, int S, int m);
@@ -455,7 +455,7 @@ cudaError_t launch_conv3x3(const __nv_bfloat16* in, int B, int cic, const __nv_b
                            int cout, int nout, const ConvGeom& g, __nv_bfloat16* out_pad, float* out_f32,
                            int* err, int sms, cudaStream_t st);
 // Resident blocks per SM of the FP64 solver shape (0 if unknown).
-int gmres_fp64_blocks_per_sm(int ept, int nt, size_t smem);
+int gmres_fp64_blocks_per_sm(int ept, int nt, int minb, size_t smem);
 // dst[q] = src[perm[q]] (gather) or dst[perm[q]] = src[q] (scatter), planes of n doubles
 cudaError_t launch_permute(double* dst, const double* src, const int* perm, int count, int n,
                            int gather, cudaStream_t st);

@@ -360,7 +360,7 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
   if (e == cudaSuccess && P->K > 1) {
     e = dmalloc(&P->queue, 1);
     if (e == cudaSuccess) e = dmalloc(&P->done, nt);
-    const int per_sm = kp::gmres_fp64_blocks_per_sm(P->shT.ept, P->shT.nt, P->shT.smem);
+    const int per_sm = kp::gmres_fp64_blocks_per_sm(P->shT.ept, P->shT.nt, P->shT.minb, P->shT.smem);
     const int slots = (per_sm > 0 ? per_sm : 1) * c->sms;
     P->tgt_grid = std::max(1, std::min(nt, o.target_blocks > 0 ? o.target_blocks : slots));
   }

@@ -31,7 +31,8 @@ class KPError(RuntimeError):
 class _Options(ctypes.Structure):
     _fields_ = [("max_seeds", ctypes.c_int), ("max_a", ctypes.c_int), ("max_n", ctypes.c_int),
                 ("precision", ctypes.c_int), ("smem_vectors", ctypes.c_int),
-                ("reorth", ctypes.c_int), ("block_threads", ctypes.c_int)]
+                ("reorth", ctypes.c_int), ("block_threads", ctypes.c_int),
+                ("blocks_per_sm", ctypes.c_int)]
 
 
 # kp_op: int H, W; double dt, g2, h; const double *mtilde, *fx, *fy
@@ -159,7 +160,7 @@ class Context:
     """A kp_ctx bound to a CUDA stream (default: torch's current stream)."""
 
     def __init__(self, max_seeds=64, max_a=40, max_n=4096, precision=PREC_FP64, smem_vectors=0,
-                 reorth=0, stream=None, block_threads=0):
+                 reorth=0, stream=None, block_threads=0, blocks_per_sm=0):
         import torch
         L = lib()
         o = _Options()
@@ -167,6 +168,7 @@ class Context:
         o.max_seeds, o.max_a, o.max_n = max_seeds, max_a, max_n
         o.precision, o.smem_vectors, o.reorth = precision, smem_vectors, reorth
         o.block_threads = block_threads
+        o.blocks_per_sm = blocks_per_sm
         self._h = ctypes.c_void_p()
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s

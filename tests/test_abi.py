@@ -38,3 +38,24 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(kp, "_lib", None)
     with pytest.raises(ImportError):
         kp.lib()
+
+
+def test_solver_shape_options_validated():
+    # (threads per system, blocks per SM) pairs without a compiled solver are refused
+    from paper_2511_17634_gb300 import kp as K
+    L = K.lib()
+    import ctypes
+    for bt, mb, ok in [(0, 0, True), (256, 3, True), (128, 4, True), (64, 4, True),
+                       (256, 4, False), (64, 2, False), (96, 0, False), (128, -1, False)]:
+        o = K._Options()
+        L.kp_options_default(ctypes.byref(o))
+        o.block_threads, o.blocks_per_sm = bt, mb
+        h = ctypes.c_void_p()
+        st = L.kp_create(ctypes.byref(h), ctypes.byref(o), None)
+        if ok:
+            # no GPU here: creation may fail later at the CUDA step, never at validation
+            assert st != K.ERR_ARG, (bt, mb)
+        else:
+            assert st == K.ERR_ARG, (bt, mb)
+        if h:
+            L.kp_destroy(h)

@@ -95,8 +95,8 @@ def test_march_workload_32x32_sampled(kp, orc):
     assert tm.refine_ms > 0 and tm.launches == 3 * steps + 1
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_march_windows_bit_identical(kp, orc, mode):
+@pytest.mark.parametrize("mode,shape", [(0, (0, 0)), (1, (0, 0)), (0, (128, 3))])
+def test_march_windows_bit_identical(kp, orc, mode, shape):
     # windows of K timesteps with dynamically claimed (timestep, system) items
     # compute every solve exactly as one launch per timestep does: the states,
     # iteration counts and residuals agree bit for bit, including ragged
@@ -106,7 +106,8 @@ def test_march_windows_bit_identical(kp, orc, mode):
     steps = 21
     res = {}
     for K in (1, 8, 3):
-        ctx = kp.Context(max_seeds=2 * K * wl.n_seed_planes, max_a=wl.a, max_n=g.N)
+        ctx = kp.Context(max_seeds=2 * K * wl.n_seed_planes, max_a=wl.a, max_n=g.N,
+                         block_threads=shape[0], blocks_per_sm=shape[1])
         grp = _groups(wl)
         mr = kp.March(ctx, grp, wl.T, wl.g2, mode=mode, tol_seed=wl.tol_seed, tol=wl.tol,
                       m_seed=wl.m_seed, m=wl.m, window=K)

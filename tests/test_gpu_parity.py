@@ -98,7 +98,9 @@ def test_seed_solve_and_basis_match_oracle(kp, orc, reorth, smem_vectors):
         assert np.abs(Vn @ Vn.T - np.eye(Vn.shape[0])).max() <= 1e-12
 
 
-def test_projection_and_refine_match_oracle(kp, orc):
+@pytest.mark.parametrize("shape", [(0, 0), (128, 2), (128, 3), (128, 4), (64, 4), (256, 3)])
+def test_projection_and_refine_match_oracle(kp, orc, shape):
+    # every compiled one-block solver shape (threads per system, blocks per SM)
     wl = synth.config(2, T=1000, ntargets=24)
     g = wl.groups[0]
     H, W, N = g.H, g.W, g.N
@@ -106,7 +108,8 @@ def test_projection_and_refine_match_oracle(kp, orc):
     dt, h, g2 = 1.0 / wl.T, 1.0 / H, float(wl.g2[n])
     ms = g.seeds.reshape(len(g.seeds), -1)
     mt = g.targets.reshape(len(g.targets), -1)
-    ctx = kp.Context(max_a=40, max_n=N, max_seeds=len(ms))
+    ctx = kp.Context(max_a=40, max_n=N, max_seeds=len(ms), block_threads=shape[0],
+                     blocks_per_sm=shape[1])
     sm = _dev(ms)
     sops = kp.make_ops(H, W, dt, g2, h, sm)
     sb = torch.zeros_like(sm)
