@@ -507,8 +507,8 @@ def main():
             "gpu_launches": launches_per_step * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                         "traffic": None if mixed or window != 16 or wl.name != "blobs-32x32x3-10seeds-256targets"
-                         else 18.85e6,
+                         "traffic": None if (mixed or window != 16 or args.block_threads or args.blocks_per_sm
+                                             or wl.name != "blobs-32x32x3-10seeds-256targets") else 23.15e6,
                          "traffic_note": "DRAM bytes per target launch (16 timesteps x 768 systems), ncu "
                                          "capture of the first window; the path is L2-resident",
                          "kernel": "gmres_fp64_kernel (targets: projection + refine)",
