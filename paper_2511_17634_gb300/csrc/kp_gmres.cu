@@ -68,14 +68,14 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
   auto slot = [&](int i) -> double* {
     return i < p.S ? sm.V + (size_t)i * npad : spill + (size_t)(i - p.S) * npad;
   };
-  if (p.pdl == 1) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  if (p.pdl & 1) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   // timesteps of this launch (time march): t0 .. t0 + nstep - 1
   int t0 = 0, nstep = 1;
   if (p.step) {
     t0 = *p.step + p.step_offset;
     nstep = min(p.win > 0 ? p.win : 1, *p.step_end - t0);
     if (nstep <= 0) {                        // pipelined seed step past the run: nothing to do
-      if (p.pdl == 2) asm volatile("griddepcontrol.wait;" ::: "memory");
+      if (p.pdl & 2) asm volatile("griddepcontrol.wait;" ::: "memory");
       return;
     }
   }
@@ -532,7 +532,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
     __syncthreads();                           // shared memory reused by the next item
     if (!p.queue && ++kstep == nstep) { kstep = 0; sysi += gridDim.x; }
   }
-  if (p.pdl == 2) asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (p.pdl & 2) asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // y = A x (mode 0) or b = m^{n-1}/dt - Div_h f (mode 1), one block per system.
@@ -601,7 +601,7 @@ static cudaError_t launch_one(const GmresParams& p, size_t smem, cudaStream_t st
   cudaError_t e = allow_max_smem(k, smem);
   if (e != cudaSuccess) return e;
   const int grid = p.grid > 0 ? p.grid : p.nsys;
-  if (p.pdl == 2) {
+  if (p.pdl & 2) {
     // programmatic dependent launch: the blocks may start while the previous
     // kernel of the stream still runs (it signals at entry)
     cudaLaunchConfig_t cfg = {};
@@ -641,13 +641,13 @@ cudaError_t launch_gmres_fp64_1k_grid(const GmresParams& p, size_t smem, int gri
   return cudaGetLastError();
 }
 
-__global__ void advance_kernel(int* step, int by, int* zero) {
+__global__ void advance_kernel(int* step, int by, int* zero, int nzero) {
   *step += by;
-  if (zero) *zero = 0;
+  for (int k = 0; zero && k < nzero; ++k) zero[k] = 0;
 }
 
-cudaError_t launch_advance(int* step, cudaStream_t st, int by, int* zero) {
-  advance_kernel<<<1, 1, 0, st>>>(step, by, zero);
+cudaError_t launch_advance(int* step, cudaStream_t st, int by, int* zero, int nzero) {
+  advance_kernel<<<1, 1, 0, st>>>(step, by, zero, nzero);
   return cudaGetLastError();
 }
 

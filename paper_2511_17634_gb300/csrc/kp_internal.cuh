@@ -117,9 +117,9 @@ struct GmresParams {
   const int* run_start;
   int* err;                 // bit 1: a dependency wait gave up
   int grid;                 // blocks of the launch (0 = one per system)
-  int pdl;                  // programmatic launch: 1 = let the stream's next launch start
-                            // at once; 2 = launched that way: wait for the prior grid
-                            // (its completion and memory) before exiting
+  int pdl;                  // programmatic launch, bit 0: let the stream's next launch
+                            // start at once; bit 1: launched that way, wait for the
+                            // prior grid (its completion and memory) before exiting
 };
 
 constexpr int kWaitLimit = 1 << 22;   // polls (>= 256 ns apart) before a wait gives up
@@ -439,7 +439,7 @@ cudaError_t launch_gmres_fp64_1k_grid(const GmresParams& p, size_t smem, int gri
 cudaError_t launch_apply(const SysDesc* sys, int nsys, int mode, cudaStream_t st);
 cudaError_t launch_factor(const FactorParams& p, cudaStream_t st);
 cudaError_t launch_project_fp64(const ProjParams& p, int ept, int nt, cudaStream_t st);
-cudaError_t launch_advance(int* step, cudaStream_t st, int by = 1, int* zero = nullptr);
+cudaError_t launch_advance(int* step, cudaStream_t st, int by = 1, int* zero = nullptr, int nzero = 1);
 
 // 3x3 convolutions on the tensor cores (kp_conv_tc.cu): padded-column BF16
 // activation layout [B][chunks of 8 channels][Rp rows][8], pixel (i, j) at row

@@ -79,19 +79,30 @@ struct kp_march_plan {
   int host_step[3] = {0, 0, 0};              // source of the counter reset (outlives the copy)
   // windows of K timesteps (FP64): K = 1 is the per-timestep scheme above
   int K = 1;
-  int* queue = nullptr;                      // item counter of the target launch
+  int* queue = nullptr;                      // [2] item counters of the target launches
   int* done = nullptr;                       // [nt] steps completed in this run
-  int tgt_grid = 0;                          // persistent target blocks
+  // target classes: in window mode, grids of <= 1024 points and larger ones
+  // get their own solver shape and persistent launch (targets of a class are
+  // contiguous in the descriptor arrays); otherwise one class = all targets
+  struct TClass {
+    kp::Shape sh;
+    int first = 0, count = 0, grid = 0;
+    size_t spill_off = 0;                    // in the target part of the workspace
+  };
+  int ncls = 1;
+  TClass cls[2];
 };
 
 namespace {
 
-kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset) {
+kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset, int ci = 0) {
   kp_ctx* c = P->ctx;
   kp::GmresParams g{};
-  const kp::Shape& sh = seeds ? P->shS : P->shT;
-  g.sys = P->desc[par] + (seeds ? 0 : P->ns);
-  g.nsys = seeds ? P->ns : P->nt;
+  const kp_march_plan::TClass& tc = P->cls[ci];
+  const kp::Shape& sh = seeds ? P->shS : tc.sh;
+  const int first = seeds ? 0 : P->ns + tc.first;
+  g.sys = P->desc[par] + first;
+  g.nsys = seeds ? P->ns : tc.count;
   g.tol = seeds ? P->opt.tol_seed : P->opt.tol;
   g.m = seeds ? P->opt.m_seed : P->opt.m;
   g.maxit = P->opt.maxit;
@@ -103,9 +114,9 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset)
     spS = (size_t)P->ns * (P->shS.cs ? P->shS.cs : 1) * (P->opt.m_seed + 1 - P->shS.S) * P->shS.ept *
           P->shS.nt;
   if (P->mixed)
-    g.spill32 = (sh.S < g.m + 1) ? P->spill32 + (seeds ? 0 : spS) : nullptr;
+    g.spill32 = (sh.S < g.m + 1) ? P->spill32 + (seeds ? 0 : spS + tc.spill_off) : nullptr;
   else
-    g.spill = (sh.S < g.m + 1) ? P->spill + (seeds ? 0 : spS) : nullptr;
+    g.spill = (sh.S < g.m + 1) ? P->spill + (seeds ? 0 : spS + tc.spill_off) : nullptr;
   g.slotV32 = c->slotV32;
   g.info = nullptr;
   g.step = P->step;
@@ -126,15 +137,15 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset)
     // window: descriptors and slot sets chosen per timestep on the device
     g.win = P->K;
     g.slot_sets = 2 * P->K;
-    g.sys_par[0] = P->desc[0] + (seeds ? 0 : P->ns);
-    g.sys_par[1] = P->desc[1] + (seeds ? 0 : P->ns);
+    g.sys_par[0] = P->desc[0] + first;
+    g.sys_par[1] = P->desc[1] + first;
     g.sys_shift = seeds ? 1 : 0;
     g.step_offset = seeds ? offset : 0;
     if (!seeds) {
-      g.queue = P->queue;
-      g.done = P->done;
+      g.queue = P->queue + ci;
+      g.done = P->done + tc.first;
       g.run_start = P->step + 2;
-      g.grid = P->tgt_grid;
+      g.grid = tc.grid;
     }
   }
   if (seeds) {
@@ -202,7 +213,7 @@ kp_status enqueue_step(kp_march_plan* P, int par, cudaEvent_t* ev, int* launches
       }
     }
     kp::GmresParams g = solver_params(P, false, par, 0);
-    if (e == cudaSuccess) e = launch_solver(P, g, P->shT, P->st);
+    if (e == cudaSuccess) e = launch_solver(P, g, P->cls[0].sh, P->st);
     ++nl;
     if (ev && e == cudaSuccess) e = cudaEventRecord(ev[3], P->st);
   }
@@ -229,20 +240,24 @@ kp_status enqueue_window(kp_march_plan* P, cudaEvent_t* ev, int* launches) {
   if (P->ns > 0) {
     if (ev) e = cudaEventRecord(ev[0], P->st);
     kp::GmresParams g = solver_params(P, true, 0, P->K);
-    g.pdl = pdl ? 1 : 0;
+    g.pdl = pdl ? 1 : 0;                     // signal at entry
     if (e == cudaSuccess) e = launch_solver(P, g, P->shS, P->st);
     ++nl;
     if (ev && e == cudaSuccess) e = cudaEventRecord(ev[1], P->st);
   }
   if (P->nt > 0 && e == cudaSuccess) {
     if (ev) e = cudaEventRecord(ev[2], P->st);
-    kp::GmresParams g = solver_params(P, false, 0, 0);
-    g.pdl = pdl ? 2 : 0;
-    if (e == cudaSuccess) e = launch_solver(P, g, P->shT, P->st);
-    ++nl;
+    // class launches chained the same way: each signals at entry so the next
+    // one fills the SMs it leaves, and waits at exit for its predecessor
+    for (int ci = 0; ci < P->ncls && e == cudaSuccess; ++ci) {
+      kp::GmresParams g = solver_params(P, false, 0, 0, ci);
+      if (ev == nullptr) g.pdl = ((P->ns > 0 || ci > 0) ? 2 : 0) | (ci + 1 < P->ncls ? 1 : 0);
+      e = launch_solver(P, g, P->cls[ci].sh, P->st);
+      ++nl;
+    }
     if (ev && e == cudaSuccess) e = cudaEventRecord(ev[3], P->st);
   }
-  if (e == cudaSuccess) { e = kp::launch_advance(P->step, P->st, P->K, P->queue); ++nl; }
+  if (e == cudaSuccess) { e = kp::launch_advance(P->step, P->st, P->K, P->queue, P->ncls); ++nl; }
   if (launches) *launches = nl;
   return e == cudaSuccess ? KP_OK : kp::cuda_error(P->ctx, e, "march window enqueue");
 }
@@ -357,19 +372,58 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
   if (e == cudaSuccess) e = dmalloc(&P->step, 3);
   if (e == cudaSuccess) e = dmalloc(&P->err, 1);
   if (e == cudaSuccess) e = cudaMemset(P->err, 0, sizeof(int));
+  // target classes (window mode with both small and larger grids: two)
+  std::vector<int> cls_of(ngroups, 0);
+  P->cls[0].sh = P->shT;
+  P->cls[0].count = nt;
+  if (P->K > 1 && nt > 0) {
+    int nsmall = 0, nbig = 0;
+    int nmaxA = 0, nmaxB = 0;
+    double wA = 0, wB = 0;
+    for (int gi = 0; gi < ngroups; ++gi) {
+      const int N = groups[gi].H * groups[gi].W;
+      if (!groups[gi].ntgt) continue;
+      if (N <= 1024) { nsmall += groups[gi].ntgt; nmaxA = std::max(nmaxA, N); wA += (double)groups[gi].ntgt * N; }
+      else { nbig += groups[gi].ntgt; nmaxB = std::max(nmaxB, N); wB += (double)groups[gi].ntgt * N; }
+    }
+    if (nsmall && nbig) {
+      // larger grids first (class 0), launched with their share of the SMs;
+      // the small-grid launch (class 1) takes the rest and the SMs they free
+      P->ncls = 2;
+      for (int gi = 0; gi < ngroups; ++gi) cls_of[gi] = groups[gi].H * groups[gi].W <= 1024 ? 1 : 0;
+      kp_status s2 = kp::gmres_shape(c, nmaxB, o.m, &P->cls[0].sh, false, 0);
+      if (s2 == KP_OK) s2 = kp::gmres_shape(c, nmaxA, o.m, &P->cls[1].sh, false, 0);
+      if (s2 != KP_OK) { kp_march_destroy(P); return s2; }
+      P->cls[0].first = 0;
+      P->cls[0].count = nbig;
+      P->cls[1].first = nbig;
+      P->cls[1].count = nsmall;
+      const int share = (int)(c->sms * wB / (wA + wB) + 0.5);
+      P->cls[0].grid = std::max(1, std::min(std::min(nbig, c->sms - 1), share));
+    }
+    for (int ci = 0; ci < P->ncls; ++ci) {
+      kp_march_plan::TClass& tc = P->cls[ci];
+      const int per_sm = kp::gmres_fp64_blocks_per_sm(tc.sh.ept, tc.sh.nt, tc.sh.minb, tc.sh.smem);
+      const int slots = (per_sm > 0 ? per_sm : 1) * c->sms;
+      if (P->ncls == 1 || ci == 1) tc.grid = std::min(tc.count, o.target_blocks > 0 ? o.target_blocks : slots);
+      tc.grid = std::max(1, tc.grid);
+    }
+  }
   if (e == cudaSuccess && P->K > 1) {
-    e = dmalloc(&P->queue, 1);
+    e = dmalloc(&P->queue, 2);
     if (e == cudaSuccess) e = dmalloc(&P->done, nt);
-    const int per_sm = kp::gmres_fp64_blocks_per_sm(P->shT.ept, P->shT.nt, P->shT.minb, P->shT.smem);
-    const int slots = (per_sm > 0 ? per_sm : 1) * c->sms;
-    P->tgt_grid = std::max(1, std::min(nt, o.target_blocks > 0 ? o.target_blocks : slots));
   }
   if (e == cudaSuccess) e = dmalloc(&P->acc, o.T);
   // one Krylov workspace per branch: seed blocks first, then target blocks
   size_t spS = 0, spT = 0;
   const int csS = P->shS.cs ? P->shS.cs : 1, csT = P->shT.cs ? P->shT.cs : 1;
   if (ns && P->shS.S < o.m_seed + 1) spS = (size_t)ns * csS * (o.m_seed + 1 - P->shS.S) * P->shS.ept * P->shS.nt;
-  if (nt && P->shT.S < o.m + 1) spT = (size_t)nt * csT * (o.m + 1 - P->shT.S) * P->shT.ept * P->shT.nt;
+  for (int ci = 0; ci < P->ncls; ++ci) {
+    kp_march_plan::TClass& tc = P->cls[ci];
+    tc.spill_off = spT;
+    if (tc.count && tc.sh.S < o.m + 1)
+      spT += (size_t)tc.count * csT * (o.m + 1 - tc.sh.S) * tc.sh.ept * tc.sh.nt;
+  }
   if (e == cudaSuccess && spS + spT) {
     if (P->mixed) e = dmalloc(&P->spill32, spS + spT);
     else e = dmalloc(&P->spill, spS + spT);
@@ -400,9 +454,17 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
   }
   if (e == cudaSuccess) e = dmalloc(&P->perm, nt);
   if (e == cudaSuccess) e = cudaMemcpy(P->perm, hperm.data(), nt * sizeof(int), cudaMemcpyHostToDevice);
+  // first descriptor of each group's targets: class by class, groups in order
+  std::vector<int> dfirst(ngroups, 0);
+  {
+    int q = 0;
+    for (int ci = 0; ci < P->ncls; ++ci)
+      for (int gi = 0; gi < ngroups; ++gi)
+        if (cls_of[gi] == ci) { dfirst[gi] = q; q += groups[gi].ntgt; }
+  }
   for (int par = 0; par < 2 && e == cudaSuccess; ++par) {
     std::vector<SysDesc> hd((size_t)ns + nt);
-    int si = 0, ti = 0, seed_base = 0;
+    int si = 0, seed_base = 0;
     for (int gi = 0; gi < ngroups; ++gi) {
       const kp_group& g = groups[gi];
       const int N = g.H * g.W;
@@ -416,7 +478,7 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
         d.slot = 0;
         hd[si] = d;
       }
-      for (int k = 0; k < g.ntgt; ++k, ++ti) {
+      for (int k = 0, ti = dfirst[gi]; k < g.ntgt; ++k, ++ti) {
         const size_t off = P->tgt_off[gi] + (size_t)k * N;
         SysDesc d{};
         d.H = g.H; d.W = g.W; d.dt = dt; d.g2 = 0.0; d.h = 1.0 / g.H;
@@ -558,7 +620,7 @@ kp_status kp_march_run(kp_march_plan* P, int n0, int steps, kp_step_stats* stats
   P->host_step[2] = n0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(P->step, P->host_step, 3 * sizeof(int), cudaMemcpyHostToDevice, P->st);
   if (e == cudaSuccess && P->done) e = cudaMemsetAsync(P->done, 0, (size_t)P->nt * sizeof(int), P->st);
-  if (e == cudaSuccess && P->queue) e = cudaMemsetAsync(P->queue, 0, sizeof(int), P->st);
+  if (e == cudaSuccess && P->queue) e = cudaMemsetAsync(P->queue, 0, 2 * sizeof(int), P->st);
   if (e == cudaSuccess) e = cudaMemsetAsync(P->acc + n0, 0, (size_t)steps * sizeof(kp::StepAcc), P->st);
   std::vector<cudaEvent_t> ev;
   int launches = 0;

@@ -128,3 +128,32 @@ def test_march_windows_bit_identical(kp, orc, mode, shape):
                             mode=mode, tol_seed=wl.tol_seed, m_seed=wl.m_seed, a=wl.a,
                             tol_ref=wl.tol, m_ref=wl.m)
     assert np.abs(res[8][1] - omt).max() / np.abs(omt).max() <= 1e-6
+
+
+def test_march_windows_two_size_classes(kp, orc):
+    # grids of <= 1024 points and larger ones in one plan: in window mode each
+    # size class has its own solver shape and persistent launch (chained
+    # programmatically); results match the oracle and do not depend on K
+    gA = synth.make_group(91, 24, 24, 2, 2, 5, tag=1)
+    gB = synth.make_group(92, 40, 40, 1, 1, 3, tag=2)
+    T = 1000
+    g2 = synth.beta_schedule(T)
+    wl = synth.Workload("two-classes", T, g2, [gA, gB])
+    steps = 20
+    finals = {}
+    for K in (8, 3):
+        ctx = kp.Context(max_seeds=2 * K * 5, max_a=30, max_n=1600)
+        grp = _groups(wl)
+        mr = kp.March(ctx, grp, T, g2, mode=0, tol_seed=1e-10, tol=1e-12, m_seed=30, m=30, window=K)
+        st, tm = mr.run(0, steps, stats=True, timing=True)
+        assert tm.launches == 4 * (-(-steps // K)) + 1        # seeds + 2 classes + advance
+        assert all(s.not_converged == 0 for s in st)
+        finals[K] = [(x[0].cpu().numpy(), x[1].cpu().numpy()) for x in grp]
+        mr.close()
+        ctx.close()
+    for a, b in zip(finals[8], finals[3]):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for k, g in enumerate(wl.groups):
+        oms, omt, _ = orc.march(g.H, g.W, T, g2, g.seeds, g.targets, g.target_seed, steps=steps,
+                                tol_seed=1e-10, m_seed=30, a=30, tol_ref=1e-12, m_ref=30)
+        assert np.abs(finals[8][k][1] - omt).max() <= 1e-9 * np.abs(omt).max()
