@@ -48,7 +48,18 @@ BF16_PEAK_TFLOPS = _measured_peak("bf16_tflops", 1900.0)
 METRIC = "target systems solved/s to rel. residual 1e-8, projected vs plain GMRES, 1 GB300"
 
 
-def parse():
+def max_over_ranks(x, dist, device):
+    """The largest value of x over all ranks (x itself on one rank): the
+    whole-job time is the slowest rank's."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -72,9 +83,12 @@ def parse():
                     help="FP64 march windows: persistent target blocks (0 = all resident slots)")
     ap.add_argument("--march-steps", type=int, default=0,
                     help="timesteps per timed march (0 = all T; fewer only for profiling runs)")
+    ap.add_argument("--schedule", choices=("beta", "paper"), default="beta",
+                    help="g^2 schedule: linear beta 1e-4..0.02 (workloads, default) or the paper's "
+                         "constant g = 0.5")
     ap.add_argument("--learned", action="store_true",
                     help="128x128x3 learned-guess measurement (bounded sample)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 class Clocks:
@@ -206,6 +220,16 @@ def oracle_step_error(wl, prev, last, step, nsample=32):
 
 
 def workload(args, rank=0):
+    wl = _workload(args, rank)
+    if args.schedule == "paper":
+        # the paper's experiments: constant g = 0.5 (Sec. 5) instead of the
+        # linear beta schedule of the workloads
+        wl.g2 = synth.constant_g2(wl.T, 0.5)
+        wl.name += "-g0.5"
+    return wl
+
+
+def _workload(args, rank=0):
     wl = synth.config(args.config, T=args.T, ntargets=args.ntargets)
     if rank:
         # each replica solves its own targets (weak scaling, no exchange)
@@ -400,11 +424,7 @@ def main():
             e1.record(stream)
             torch.cuda.synchronize()
             total += e0.elapsed_time(e1) / 1000.0
-        if dist:
-            t = torch.tensor([total], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
-        return total
+        return max_over_ranks(total, dist, dev)
 
     common = dict(T=T, g2=wl.g2, tol_seed=wl.tol_seed, tol=wl.tol, m_seed=wl.m_seed, m=wl.m,
                   maxit=1000, window=window, target_blocks=args.target_blocks)
@@ -461,10 +481,7 @@ def main():
         torch.cuda.synchronize()
         if k > 0:
             e2e_total += e0.elapsed_time(e1) / 1000.0
-    if dist:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(e2e_total, dist, dev)
     e2e_value = world * nt_planes * NS * e2e_steps / e2e_total
 
     err = None

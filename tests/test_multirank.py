@@ -1,0 +1,60 @@
+"""The N > 1 replica path of bench.py on CPU: two gloo ranks get the same
+seeds and disjoint targets of the same shape (weak scaling, no data exchange),
+and the job time is the maximum over ranks."""
+import hashlib
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def _port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _digest(a):
+    return hashlib.sha1(np.ascontiguousarray(a).tobytes()).hexdigest()
+
+
+def _worker(rank, world, port, q, argv):
+    import sys
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    args = bench.parse(argv)
+    wl = bench.workload(args, rank)
+    seeds = [_digest(g.seeds) for g in wl.groups]
+    tgts = [_digest(g.targets) for g in wl.groups]
+    shapes = [g.targets.shape for g in wl.groups]
+    t = bench.max_over_ranks(1.5 + rank, dist, torch.device("cpu"))
+    q.put((rank, seeds, tgts, shapes, t))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("argv", [["--config", "2", "--ntargets", "8", "--T", "10"],
+                                  ["--config", "3", "--ntargets", "6", "--T", "10"]])
+def test_two_ranks_shard_targets_and_take_max_time(argv):
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q, argv)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (_, s0, t0, sh0, m0), (_, s1, t1, sh1, m1) = out
+    assert s0 == s1                                   # same seeds on every rank
+    assert all(a != b for a, b in zip(t0, t1))        # each rank its own targets
+    assert sh0 == sh1                                 # of the same shape
+    assert m0 == m1 == 2.5                            # the slowest rank's time
