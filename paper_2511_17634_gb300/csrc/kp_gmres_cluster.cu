@@ -82,13 +82,15 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
   float* capV = capture ? p.capV32 + (size_t)cidx * (p.cap_a + 1) * p.cap_ld : nullptr;
   double* capH = capture ? p.capH + (size_t)cidx * (p.cap_a + 1) * p.cap_a : nullptr;
 
-  double qx[EPT], qy[EPT];
+  // FP32 q_x, q_y for the Krylov operator; FP64 E and N coefficients
+  // cE = q_x - c, cN = q_y - c for the residual (cW = -2c - cE, cS = -2c - cN)
+  double cEx[EPT], cNy[EPT];
   float qxf[EPT], qyf[EPT];
   unsigned msk[EPT];
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
     const int l = tid + k * NT, pp = base + l;
-    qx[k] = qy[k] = 0.0;
+    double qx = 0.0, qy = 0.0;
     msk[k] = 0;
     if (l < SL) {
       const int i = pp / H, j = pp - i * H;
@@ -98,16 +100,20 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
       const double mS = (j > 0) ? d.mt[pp - 1] : 0.0;
       const double fxp = d.fx ? d.fx[pp] : 0.0;
       const double fyp = d.fy ? d.fy[pp] : 0.0;
-      qx[k] = fxp * i2h - ee * (mE - mW);
-      qy[k] = fyp * i2h - ee * (mN - mS);
+      qx = fxp * i2h - ee * (mE - mW);
+      qy = fyp * i2h - ee * (mN - mS);
       msk[k] = (i + 1 < W ? 1u : 0u) | (i > 0 ? 2u : 0u) | (j + 1 < H ? 4u : 0u) | (j > 0 ? 8u : 0u);
     }
-    qxf[k] = (float)qx[k];
-    qyf[k] = (float)qy[k];
+    cEx[k] = qx - cc;
+    cNy[k] = qy - cc;
+    qxf[k] = (float)qx;
+    qyf[k] = (float)qy;
   }
   const double* xs_next = rank + 1 < CS ? cluster.map_shared_rank(xs, rank + 1) : nullptr;
   const double* xs_prev = rank > 0 ? cluster.map_shared_rank(xs, rank - 1) : nullptr;
-  auto apply64 = [&](double (&out)[EPT]) {
+  // r = b - A x in FP64 (A x = cd x + cE (xE - xW) - 2c xW + cN (xN - xS) - 2c xS)
+  const double c2 = 2.0 * cc;
+  auto residual_of = [&](double (&out)[EPT]) {
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
       const int l = tid + k * NT;
@@ -117,7 +123,10 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
         const double xW = (msk[k] & 2u) ? (l - H >= 0 ? xs[l - H] : xs_prev[l - H + SL]) : 0.0;
         const double xN = (msk[k] & 4u) ? xs[l + 1] : 0.0;
         const double xS = (msk[k] & 8u) ? xs[l - 1] : 0.0;
-        out[k] = cd * xs[l] - cc * (xE + xW + xN + xS) + qx[k] * (xE - xW) + qy[k] * (xN - xS);
+        double t = fma(-cd, xs[l], d.b[base + l] * bsc);
+        t = fma(-cEx[k], xE - xW, t);
+        t = fma(-cNy[k], xN - xS, t);
+        out[k] = fma(c2, xW + xS, t);
       }
     }
   };
@@ -217,14 +226,7 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
   }
   cluster.sync();                                 // x slices visible cluster-wide
   double r[EPT];
-  auto residual = [&]() {
-    apply64(r);
-#pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-      const int l = tid + k * NT;
-      r[k] = (l < SL) ? bval(l) - r[k] : 0.0;
-    }
-  };
+  auto residual = [&]() { residual_of(r); };
   if (p.x0_mode == X0_ZERO) {
 #pragma unroll
     for (int k = 0; k < EPT; ++k) r[k] = bval(tid + k * NT);

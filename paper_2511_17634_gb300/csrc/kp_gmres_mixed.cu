@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
   const int m = p.m;
   const int ld = m + 1;
   SmemM sm = carve_m(smem_raw, npad, NWARPS, m, p.S);
+  float* red32 = reinterpret_cast<float*>(sm.red);   // FP32 per-warp partials
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float* spill = p.spill32 ? p.spill32 + (size_t)blockIdx.x * (m + 1 - p.S) * npad : nullptr;
   auto slot = [&](int i) -> float* {
@@ -99,14 +100,16 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
     float* capV = capture ? p.capV32 + (size_t)cidx * (p.cap_a + 1) * p.cap_ld : nullptr;
     double* capH = capture ? p.capH + (size_t)cidx * (p.cap_a + 1) * p.cap_a : nullptr;
 
-    // q_x, q_y per point (FP64 and FP32 copies) and neighbour masks
-    double qx[EPT], qy[EPT];
+    // q_x, q_y per point (FP32 copies for the Krylov operator), the FP64 E and N
+    // coefficients cE = q_x - c, cN = q_y - c for the residual (W and S follow:
+    // cW = -2c - cE, cS = -2c - cN), and neighbour masks
+    double cEx[EPT], cNy[EPT];
     float qxf[EPT], qyf[EPT];
     unsigned msk[EPT];                          // bit0 E, bit1 W, bit2 N, bit3 S present
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
       const int pp = tid + k * NT;
-      qx[k] = qy[k] = 0.0;
+      double qx = 0.0, qy = 0.0;
       msk[k] = 0;
       if (pp < N) {
         const int i = pp / H, j = pp - i * H;
@@ -116,14 +119,19 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
         const double mS = (j > 0) ? d.mt[pp - 1] : 0.0;
         const double fxp = d.fx ? d.fx[pp] : 0.0;
         const double fyp = d.fy ? d.fy[pp] : 0.0;
-        qx[k] = fxp * i2h - ee * (mE - mW);
-        qy[k] = fyp * i2h - ee * (mN - mS);
+        qx = fxp * i2h - ee * (mE - mW);
+        qy = fyp * i2h - ee * (mN - mS);
         msk[k] = (i + 1 < W ? 1u : 0u) | (i > 0 ? 2u : 0u) | (j + 1 < H ? 4u : 0u) | (j > 0 ? 8u : 0u);
       }
-      qxf[k] = (float)qx[k];
-      qyf[k] = (float)qy[k];
+      cEx[k] = qx - cc;
+      cNy[k] = qy - cc;
+      qxf[k] = (float)qx;
+      qyf[k] = (float)qy;
     }
-    auto apply64 = [&](const double* v, double (&out)[EPT]) {
+    // r = b - A v in FP64 with the masked neighbours:
+    // A v = cd v + cE (vE - vW) - 2c vW + cN (vN - vS) - 2c vS
+    const double c2 = 2.0 * cc;
+    auto residual_of = [&](const double* v, double (&out)[EPT]) {
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
         const int pp = tid + k * NT;
@@ -133,7 +141,10 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
           const double xW = (msk[k] & 2u) ? v[pp - H] : 0.0;
           const double xN = (msk[k] & 4u) ? v[pp + 1] : 0.0;
           const double xS = (msk[k] & 8u) ? v[pp - 1] : 0.0;
-          out[k] = cd * v[pp] - cc * (xE + xW + xN + xS) + qx[k] * (xE - xW) + qy[k] * (xN - xS);
+          double t = fma(-cd, v[pp], d.b[pp] * bsc);
+          t = fma(-cEx[k], xE - xW, t);
+          t = fma(-cNy[k], xN - xS, t);
+          out[k] = fma(c2, xW + xS, t);
         }
       }
     };
@@ -182,7 +193,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
           float bv[EPT];
 #pragma unroll
           for (int k = 0; k < EPT; ++k) bv[k] = (float)bval(tid + k * NT);
-          block_partials_f32<NT>(nv, [&](int i) {
+          block_partials_f32x<NT>(nv, [&](int i) {
             const float* vi = V + (size_t)i * p.slot_ld;
             float s = 0.f;
 #pragma unroll
@@ -191,9 +202,8 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
               if (pp < N) s = fmaf(vi[pp], bv[k], s);
             }
             return s;
-          }, sm.red);
-          if (warp == 0)
-            for (int i = lane; i < nv; i += 32) sm.hb[i] = cross_warp<NT>(sm.red, i);
+          }, red32);
+          if (warp == 0) cross_warp_f32<NT>(red32, nv, sm.hb, lane);
         }
         if (warp == 0) {
           __syncwarp();
@@ -216,14 +226,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
     }
     __syncthreads();
     double r[EPT];
-    auto residual = [&]() {
-      apply64(sm.xs, r);
-#pragma unroll
-      for (int k = 0; k < EPT; ++k) {
-        const int pp = tid + k * NT;
-        r[k] = (pp < N) ? bval(pp) - r[k] : 0.0;
-      }
-    };
+    auto residual = [&]() { residual_of(sm.xs, r); };
     if (p.x0_mode == X0_ZERO) {
 #pragma unroll
       for (int k = 0; k < EPT; ++k) r[k] = bval(tid + k * NT);
@@ -326,13 +329,15 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
           }
           return s;
         };
-        block_partials_f32<NT>(nh + 1, dots, sm.red);
+        block_partials_f32x<NT>(nh + 1, dots, red32);
         if (warp == 0) {
+          cross_warp_f32<NT>(red32, nh + 1, sm.hb, lane);
+          __syncwarp();
           double sq = 0.0;
-          for (int i = lane; i <= nh; i += 32) {
-            const double s = cross_warp<NT>(sm.red, i);
-            sm.hb[i] = s;
-            if (i < nh) { sm.Hr[i + j * ld] = s; sq += s * s; }
+          for (int i = lane; i < nh; i += 32) {
+            const double s = sm.hb[i];
+            sm.Hr[i + j * ld] = s;
+            sq += s * s;
           }
           sq = warp_sum(sq);
           if (lane == 0) {
@@ -351,13 +356,15 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
           for (int k = 0; k < EPT; ++k) w[k] = fmaf(-hi, vi[tid + k * NT], w[k]);
         }
         if (sm.fl[0]) {
-          block_partials_f32<NT>(nh + 1, dots, sm.red);
+          block_partials_f32x<NT>(nh + 1, dots, red32);
           if (warp == 0) {
+            cross_warp_f32<NT>(red32, nh + 1, sm.hb, lane);
+            __syncwarp();
             double sq = 0.0;
-            for (int i = lane; i <= nh; i += 32) {
-              const double s = cross_warp<NT>(sm.red, i);
-              sm.hb[i] = s;
-              if (i < nh) { sm.Hr[i + j * ld] += s; sq += s * s; }
+            for (int i = lane; i < nh; i += 32) {
+              const double s = sm.hb[i];
+              sm.Hr[i + j * ld] += s;
+              sq += s * s;
             }
             sq = warp_sum(sq);
             if (lane == 0) {
@@ -375,13 +382,17 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
             for (int k = 0; k < EPT; ++k) w[k] = fmaf(-hi, vi[tid + k * NT], w[k]);
           }
           if (sm.fl[3]) {
-            block_partials_f32<NT>(1, [&](int) {
+            block_partials_f32x<NT>(1, [&](int) {
               float s = 0.f;
 #pragma unroll
               for (int k = 0; k < EPT; ++k) s = fmaf(w[k], w[k], s);
               return s;
-            }, sm.red);
-            if (tid == 0) givens_step(j, cross_warp<NT>(sm.red, 0));
+            }, red32);
+            if (warp == 0) {
+              cross_warp_f32<NT>(red32, 1, sm.sc + 5, lane);
+              __syncwarp();
+              if (lane == 0) givens_step(j, sm.sc[5]);
+            }
             __syncthreads();
           }
         }

@@ -312,6 +312,39 @@ __device__ __forceinline__ void block_partials_f32(int nv, F&& partial, double* 
   __syncthreads();
 }
 
+// As block_partials_f32, with the per-warp partials kept in FP32 (red32[warp][i]).
+template <int NT, typename F>
+__device__ __forceinline__ void block_partials_f32x(int nv, F&& partial, float* red32) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i0 = 0; i0 < nv; i0 += 8) {
+    float a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = (i0 + k < nv) ? partial(i0 + k) : 0.f;
+    const float s = warp_reduce8f(a, lane);
+    const int v = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+    if ((lane & 3) == 0 && i0 + v < nv) red32[warp * kMaxV + i0 + v] = s;
+  }
+  __syncthreads();
+}
+
+// Cross-warp sums of nv values from FP32 partials, by all 32 lanes of one
+// warp: each round holds the NT/32 partials of 32/(NT/32) values in lane
+// groups and adds them in an FP32 butterfly; dst[i] = the sum, as a double.
+// Runs on the FP32 pipe (one conversion per value) instead of NT/32 - 1
+// dependent FP64 adds on a few lanes.
+template <int NT>
+__device__ __forceinline__ void cross_warp_f32(const float* red32, int nv, double* dst, int lane) {
+  constexpr int NW = NT / 32;
+  constexpr int PER = 32 / NW;
+  for (int i0 = 0; i0 < nv; i0 += PER) {
+    const int i = i0 + lane / NW, w = lane % NW;
+    float v = (i < nv) ? red32[w * kMaxV + i] : 0.f;
+#pragma unroll
+    for (int o = NW / 2; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if (w == 0 && i < nv) dst[i] = (double)v;
+  }
+}
+
 // Cross-warp sum of value i (called by warp 0 lanes).
 template <int NT>
 __device__ __forceinline__ double cross_warp(const double* red, int i) {
