@@ -289,7 +289,7 @@ def run_learned(args):
     B.build()
     T = 1000
     g2 = synth.beta_schedule(T)
-    ntr, nev = 8, args.ntargets or 64
+    ntr, nev = 8, args.ntargets or 512
     tr = synth.make_group(1239, 128, 128, 3, 16, ntr, tag=0, target_offset=100000)
     ev = synth.make_group(1239, 128, 128, 3, 16, nev, tag=0)
     ctx = kp.Context(max_seeds=2 * tr.seeds.shape[0], max_a=40, max_n=16384,

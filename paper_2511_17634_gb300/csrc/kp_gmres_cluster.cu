@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
   // shared-memory carve (identical offsets in every CTA of the cluster)
   double* xs = smem_raw;                          // [npad] FP64 slice of x
   double* red = xs + npad;                        // [NWARPS][kMaxV]
+  float* red32 = reinterpret_cast<float*>(red);    // FP32 per-warp partials (same space)
   double* hb = red + NWARPS * kMaxV;              // [kMaxV] cluster sums
   double* cpart = hb + kMaxV;                     // [2][kMaxV] per-CTA partials
   double* Hr = cpart + 2 * kMaxV;                 // [(m+1) m]
@@ -151,9 +152,13 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
   int buf = 0;
   // cluster-wide sums of nv values whose per-warp partials are in red;
   // result in hb[0..nv) of every CTA (identical, rank order)
-  auto cluster_sum = [&](int nv) {
-    if (warp == 0)
-      for (int i = lane; i < nv; i += 32) cpart[buf * kMaxV + i] = cross_warp<NT>(red, i);
+  // (f32: the partials are FP32, summed across warps on the FP32 pipe)
+  auto cluster_sum = [&](int nv, bool f32) {
+    if (warp == 0) {
+      if (f32) cross_warp_f32<NT>(red32, nv, cpart + buf * kMaxV, lane);
+      else
+        for (int i = lane; i < nv; i += 32) cpart[buf * kMaxV + i] = cross_warp<NT>(red, i);
+    }
     cluster.sync();
     if (warp == 0) {
       for (int i = lane; i < nv; i += 32) {
@@ -193,7 +198,7 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
         float bv[EPT];
 #pragma unroll
         for (int k = 0; k < EPT; ++k) bv[k] = (float)bval(tid + k * NT);
-        block_partials_f32<NT>(nv, [&](int i) {
+        block_partials_f32x<NT>(nv, [&](int i) {
           const float* vi = Vs + (size_t)i * p.slot_ld;
           float s = 0.f;
 #pragma unroll
@@ -202,8 +207,8 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
             if (l < SL) s = fmaf(vi[l], bv[k], s);
           }
           return s;
-        }, red);
-        cluster_sum(nv);
+        }, red32);
+        cluster_sum(nv, true);
       }
       if (warp == 0) {
         __syncwarp();
@@ -242,7 +247,7 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
     }
     return s;
   }, red);
-  cluster_sum(2);
+  cluster_sum(2, false);
   const double bnorm = sqrt(hb[0]);
   double beta = sqrt(hb[1]);
   int steps = 0, status = KP_NOT_CONVERGED, outer = 0;
@@ -322,8 +327,8 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
         }
         return s;
       };
-      block_partials_f32<NT>(nh + 1, dots, red);
-      cluster_sum(nh + 1);
+      block_partials_f32x<NT>(nh + 1, dots, red32);
+      cluster_sum(nh + 1, true);
       if (warp == 0) {
         double sq = 0.0;
         for (int i = lane; i < nh; i += 32) { Hr[i + j * ld] = hb[i]; sq += hb[i] * hb[i]; }
@@ -344,8 +349,8 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
         for (int k = 0; k < EPT; ++k) w[k] = fmaf(-hi, vi[tid + k * NT], w[k]);
       }
       if (fl[0]) {
-        block_partials_f32<NT>(nh + 1, dots, red);
-        cluster_sum(nh + 1);
+        block_partials_f32x<NT>(nh + 1, dots, red32);
+        cluster_sum(nh + 1, true);
         if (warp == 0) {
           double sq = 0.0;
           for (int i = lane; i < nh; i += 32) { Hr[i + j * ld] += hb[i]; sq += hb[i] * hb[i]; }
@@ -365,13 +370,13 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
           for (int k = 0; k < EPT; ++k) w[k] = fmaf(-hi, vi[tid + k * NT], w[k]);
         }
         if (fl[3]) {
-          block_partials_f32<NT>(1, [&](int) {
+          block_partials_f32x<NT>(1, [&](int) {
             float s = 0.f;
 #pragma unroll
             for (int k = 0; k < EPT; ++k) s = fmaf(w[k], w[k], s);
             return s;
-          }, red);
-          cluster_sum(1);
+          }, red32);
+          cluster_sum(1, true);
           if (tid == 0) givens_step(j, hb[0]);
           __syncthreads();
         }
@@ -442,7 +447,7 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
       for (int k = 0; k < EPT; ++k) s += r[k] * r[k];
       return s;
     }, red);
-    cluster_sum(1);
+    cluster_sum(1, false);
     beta = sqrt(hb[0]);
     ++outer;
   }
