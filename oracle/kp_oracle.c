@@ -28,6 +28,10 @@
  *     b_proj = V^T b_i, solve A_proj alpha = b_proj, x0 = V alpha, then an
  *     iterative solve of A_i x = b_i from x0 (GMRES(m) again).
  *
+ *   - End of Sec. 2.3 and Sec. 4.1: the score of each solved timestep by
+ *     central differences and one explicit step of the probability-flow ODE
+ *     that embeds it (orc_score, orc_embed_step).
+ *
  * Storage convention: an H x W channel is a vector of N = H*W doubles with
  * index p = i*H + j, i in [0,W) the x (east-west) index and j in [0,H) the
  * y (north-south) index.  North = (i, j+1) = p+1, south = p-1, east =
@@ -453,4 +457,34 @@ void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, dou
     free(C); free(b); free(x); free(r);
   }
   free(basis); free(hess); free(used); free(nxt);
+}
+
+
+/*
+ * Score of a solved timestep by central differences (end of Sec. 2.3), with
+ * the zero padding of the discretisation outside the grid:
+ *   sx(i,j) = (m_{i+1,j} - m_{i-1,j}) / (2h),   sy(i,j) = (m_{i,j+1} - m_{i,j-1}) / (2h).
+ * The printed formula divides by 2; a central-difference derivative with grid
+ * spacing h divides by 2h, which is what is used here.
+ */
+void orc_score(int H, int W, double h, const double* m, double* sx, double* sy) {
+  for (int i = 0; i < W; ++i)
+    for (int j = 0; j < H; ++j) {
+      sx[i * H + j] = (at(m, H, W, i + 1, j) - at(m, H, W, i - 1, j)) / (2.0 * h);
+      sy[i * H + j] = (at(m, H, W, i, j + 1) - at(m, H, W, i, j - 1)) / (2.0 * h);
+    }
+}
+
+/*
+ * One explicit (forward Euler) step of the probability-flow ODE of Sec. 4.1,
+ * dx/dt = f - g^2/2 grad m, with f = 0:
+ *   x^n = x^{n-1} + dt * (-(g^{n-1})^2 / 2) * grad m^{n-1},
+ * for the two components (ex, ey) of x, in place.  g2prev = (g^{n-1})^2.
+ */
+void orc_embed_step(int N, double dt, double g2prev, const double* sx, const double* sy, double* ex,
+                    double* ey) {
+  for (int p = 0; p < N; ++p) {
+    ex[p] += dt * (-0.5 * g2prev * sx[p]);
+    ey[p] += dt * (-0.5 * g2prev * sy[p]);
+  }
 }

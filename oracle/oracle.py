@@ -77,6 +77,8 @@ def lib():
         L.orc_dense_lu_solve.restype = _i
         L.orc_march_step.argtypes = [_i, _i, _d, _d, _d, _i, _pd, _i, _pd, _pi, _i, _d, _i,
                                      _i, _d, _i, _i, _pi, _pi, _pd, _pi, _pd]
+        L.orc_score.argtypes = [_i, _i, _d, _pd, _pd, _pd]
+        L.orc_embed_step.argtypes = [_i, _d, _d, _pd, _pd, _pd, _pd]
         _lib = L
     return _lib
 
@@ -260,3 +262,39 @@ def march(H, W, T, g2, seeds, targets, target_seed, steps=None, **kw):
     for n in range(steps if steps is not None else T):
         stats.append(march_step(H, W, dt, h, float(g2[n]), ms, mt, target_seed, **kw))
     return ms, mt, stats
+
+
+def score(H, W, h, m):
+    """Central-difference score (sx, sy) of one solved channel (end of Sec. 2.3,
+    divided by 2h), zero padding outside the grid."""
+    m = np.ascontiguousarray(np.asarray(m, dtype=np.float64).reshape(-1))
+    sx = np.zeros(H * W)
+    sy = np.zeros(H * W)
+    lib().orc_score(H, W, h, _p(m), _p(sx), _p(sy))
+    return sx, sy
+
+
+def embed_step(dt, g2prev, sx, sy, ex, ey):
+    """x^n = x^{n-1} + dt * (-(g^{n-1})^2 / 2) grad m^{n-1} (Sec. 4.1, f = 0), in place."""
+    lib().orc_embed_step(len(ex), dt, g2prev, _p(sx), _p(sy), _p(ex), _p(ey))
+
+
+def march_scores(H, W, T, g2, seeds, targets, target_seed, steps=None, **kw):
+    """The march of `march` plus, for every target and timestep n, the score
+    of m^n and the probability-flow embedding x^n (x^0 = 0), which advances
+    with grad m^{n-1} and (g^{n-1})^2 (taken as (g^1)^2 for n = 1).
+    Returns (m_seed, m_target, scores [steps][ntgt][2][N], embedding [ntgt][2][N])."""
+    dt, h = 1.0 / T, 1.0 / H
+    ms = np.array(seeds, dtype=np.float64).reshape(len(seeds), -1).copy()
+    mt = np.array(targets, dtype=np.float64).reshape(len(targets), -1).copy()
+    nt, N = mt.shape
+    emb = np.zeros((nt, 2, N))
+    scores = []
+    for n in range(steps if steps is not None else T):
+        g2prev = float(g2[max(n - 1, 0)])
+        for k in range(nt):
+            sx, sy = score(H, W, h, mt[k])
+            embed_step(dt, g2prev, sx, sy, emb[k, 0], emb[k, 1])
+        march_step(H, W, dt, h, float(g2[n]), ms, mt, target_seed, **kw)
+        scores.append(np.stack([np.stack(score(H, W, h, mt[k])) for k in range(nt)]))
+    return ms, mt, np.stack(scores), emb
