@@ -445,6 +445,21 @@ def main():
     launches_per_step = tm.launches
 
     out = {}
+    if not mixed:
+        # score extraction + probability-flow embedding fused into the target
+        # solves (every timestep's score kept: T x targets x 2 x N doubles)
+        sc = torch.empty((NS,) + (sum(x.shape[0] * 2 * x.shape[1] for x in st_t),), dtype=torch.float64,
+                         device=dev)
+        emb = torch.zeros(sum(x.shape[0] * 2 * x.shape[1] for x in st_t), dtype=torch.float64, device=dev)
+        pls = kp.March(ctx, groups, mode=kp.MARCH_PROJECTED, score=sc, embed=emb, **common)
+        t = timed(pls, max(1, args.steps // 2), 1)
+        out["with_score_extraction"] = {
+            "value": world * nt_planes * NS * max(1, args.steps // 2) / t, "unit": "systems/s",
+            "score_bytes_per_march": sc.numel() * 8,
+            "note": "projected + refine with the central-difference score of every solved "
+                    "timestep and the probability-flow embedding written from the solve epilogue"}
+        pls.close()
+        del sc, emb
     if not args.no_baselines:
         for name, mode in (("plain_x0_zero", kp.MARCH_PLAIN), ("plain_warm_start", kp.MARCH_WARM)):
             pl = kp.March(ctx, groups, mode=mode, **common)

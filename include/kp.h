@@ -321,6 +321,18 @@ typedef struct {
                             Mixed precision and cluster shapes always use 1.     */
   int target_blocks;     /* window mode: persistent target blocks; 0 = every
                             resident slot of the GPU                              */
+  /* Score extraction and probability-flow embedding (end of Sec. 2.3 and Sec.
+   * 4.1), fused into the target solves (FP64 plans only), both optional:
+   * score: device, [T][targets][2][H*W] FP64 -- for timestep n (1-based) and
+   *   every target, in group order and the caller's target order within a
+   *   group, sx = (m_{i+1,j} - m_{i-1,j}) / (2h) then sy = (m_{i,j+1} -
+   *   m_{i,j-1}) / (2h) of m^n, zero outside the grid; a run writes the
+   *   timesteps it solves.
+   * embed: device, [targets][2][H*W] FP64 state x, advanced at timestep n by
+   *   x += -dt (g^{n-1})^2 / 2 * grad m^{n-1} ((g^0)^2 = (g^1)^2); the caller
+   *   sets x^0 (zero in the paper).  Must be given with score.          */
+  double* score;
+  double* embed;
 } kp_march_opts;
 
 /* Per-timestep totals, filled on the host by kp_march_run. */

@@ -159,7 +159,7 @@ kp_status upload(kp_ctx* c, const std::vector<SysDesc>& h, SysDesc** out) {
 }
 
 SysDesc make_desc(const kp_op& o, const double* b, double* x, int slot) {
-  SysDesc d;
+  SysDesc d{};
   d.mt = o.mtilde;
   d.fx = o.fx;
   d.fy = o.fy;

@@ -498,6 +498,31 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
       const int pp = tid + k * NT;
       if (pp < N) d.x[pp] = sm.xs[pp];
     }
+    if (p.score_stride && d.score) {
+      // score of m^n by central differences (end of Sec. 2.3, divided by 2h,
+      // zero outside the grid) and one probability-flow step of the embedding
+      // (Sec. 4.1, f = 0): x^n = x^{n-1} - dt (g^{n-1})^2 / 2 grad m^{n-1},
+      // with m^{n-1} this item's input and (g^0)^2 taken as (g^1)^2
+      const double i2h = 0.5 / hh;
+      const double g2prev = p.step ? p.g2_sched[tstep > 0 ? tstep - 1 : 0] : d.g2;
+      const double ce = -0.5 * d.dt * g2prev;
+      double* sc = d.score + (size_t)tstep * p.score_stride;
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int pp = tid + k * NT;
+        if (pp < N) {
+          const int i = pp / H, j = pp - i * H;
+          const double xe = i + 1 < W ? sm.xs[pp + H] : 0.0, xw = i > 0 ? sm.xs[pp - H] : 0.0;
+          const double xn = j + 1 < H ? sm.xs[pp + 1] : 0.0, xs_ = j > 0 ? sm.xs[pp - 1] : 0.0;
+          sc[pp] = (xe - xw) * i2h;
+          sc[N + pp] = (xn - xs_) * i2h;
+          const double me = i + 1 < W ? d.mt[pp + H] : 0.0, mw = i > 0 ? d.mt[pp - H] : 0.0;
+          const double mn = j + 1 < H ? d.mt[pp + 1] : 0.0, ms = j > 0 ? d.mt[pp - 1] : 0.0;
+          d.emb[pp] = fma(ce, (me - mw) * i2h, d.emb[pp]);
+          d.emb[N + pp] = fma(ce, (mn - ms) * i2h, d.emb[N + pp]);
+        }
+      }
+    }
     if (tid == 0) {
       const double rel = bnorm > 0.0 ? beta / bnorm : 0.0;
       if (p.info) {

@@ -23,6 +23,8 @@ struct SysDesc {
   double dt, g2, h;
   int slot;   // basis slot (projection) / unused
   int pad_;
+  double* score;   // march targets, optional: this system's [2][N] score plane set of timestep 0
+  double* emb;     // march targets, optional: this system's [2][N] probability-flow embedding
 };
 
 // Metadata of one stored seed basis.
@@ -117,6 +119,8 @@ struct GmresParams {
   const int* run_start;
   int* err;                 // bit 1: a dependency wait gave up
   int grid;                 // blocks of the launch (0 = one per system)
+  size_t score_stride;      // > 0: write the score of each solved timestep to
+                            // d.score + tstep * score_stride and advance d.emb
   int pdl;                  // programmatic launch, bit 0: let the stream's next launch
                             // start at once; bit 1: launched that way, wait for the
                             // prior grid (its completion and memory) before exiting

@@ -91,6 +91,7 @@ struct kp_march_plan {
   };
   int ncls = 1;
   TClass cls[2];
+  size_t score_stride = 0;                   // elements per timestep of the score output
 };
 
 namespace {
@@ -163,6 +164,7 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset,
     g.factor = 1;
     g.acc_kind = 0;
   } else {
+    g.score_stride = P->score_stride;
     g.x0_mode = P->opt.mode == KP_MARCH_PROJECTED ? (P->ns ? kp::X0_PROJECT : kp::X0_ZERO)
               : P->opt.mode == KP_MARCH_WARM ? kp::X0_WARM : kp::X0_ZERO;
     g.acc_kind = 1;
@@ -304,6 +306,7 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
   *out = nullptr;
   const kp_march_opts& o = *opt;
   if (o.T < 1 || !o.g2 || o.mode < 0 || o.mode > 2 || o.m_seed < 1 || o.m_seed > kp::kMaxM ||
+      (o.score != nullptr) != (o.embed != nullptr) ||
       o.m < 1 || o.m > kp::kMaxM || o.maxit < 0 || !(o.tol >= 0) || !(o.tol_seed >= 0))
     return kp::set_error(c, KP_ERR_ARG, "bad march options");
   kp_march_plan* P = new kp_march_plan();
@@ -348,6 +351,10 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
     return kp::set_error(c, KP_ERR_UNSUPPORTED, "grids above 4096 unknowns: one grid size per plan");
   }
   if (s != KP_OK) { kp_march_destroy(P); return s; }
+  if (o.score && (P->mixed || P->shT.cs)) {
+    kp_march_destroy(P);
+    return kp::set_error(c, KP_ERR_UNSUPPORTED, "score extraction needs the FP64 one-block solver");
+  }
   // window length: FP64 one-block solvers only; 2K slot sets must fit
   if (!P->mixed && !P->shS.cs && !P->shT.cs && o.window != 1 && P->nt > 0) {
     int K = o.window > 0 ? o.window : 8;
@@ -462,6 +469,14 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
       for (int gi = 0; gi < ngroups; ++gi)
         if (cls_of[gi] == ci) { dfirst[gi] = q; q += groups[gi].ntgt; }
   }
+  // score / embedding layout: groups in order, the caller's targets within a group
+  std::vector<size_t> score_off(ngroups, 0);
+  size_t score_stride = 0;
+  for (int gi = 0; gi < ngroups; ++gi) {
+    score_off[gi] = score_stride;
+    score_stride += (size_t)groups[gi].ntgt * 2 * groups[gi].H * groups[gi].W;
+  }
+  P->score_stride = o.score ? score_stride : 0;
   for (int par = 0; par < 2 && e == cudaSuccess; ++par) {
     std::vector<SysDesc> hd((size_t)ns + nt);
     int si = 0, seed_base = 0;
@@ -488,6 +503,10 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
         const int u = hperm[P->tgt_base[gi] + k];   // user index of internal target k
         const int sd = (g.tgt_seed && g.tgt_seed[u] >= 0 && g.tgt_seed[u] < g.nseed) ? g.tgt_seed[u] : 0;
         d.slot = seed_base + sd;               // parity offset added on the device
+        if (o.score) {
+          d.score = o.score + score_off[gi] + (size_t)u * 2 * N;
+          d.emb = o.embed + score_off[gi] + (size_t)u * 2 * N;
+        }
         hd[(size_t)ns + ti] = d;
       }
       seed_base += g.nseed;

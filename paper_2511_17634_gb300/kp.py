@@ -279,7 +279,8 @@ class _MarchOpts(ctypes.Structure):
     _fields_ = [("T", ctypes.c_int), ("g2", ctypes.c_void_p), ("mode", ctypes.c_int),
                 ("tol_seed", ctypes.c_double), ("tol", ctypes.c_double), ("m_seed", ctypes.c_int),
                 ("m", ctypes.c_int), ("maxit", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("window", ctypes.c_int), ("target_blocks", ctypes.c_int)]
+                ("window", ctypes.c_int), ("target_blocks", ctypes.c_int),
+                ("score", ctypes.c_void_p), ("embed", ctypes.c_void_p)]
 
 
 class StepStats(ctypes.Structure):
@@ -314,7 +315,8 @@ class March:
     target_seed int array, H, W).  The tensors are updated in place by run()."""
 
     def __init__(self, ctx, groups, T, g2, mode=MARCH_PROJECTED, tol_seed=1e-10, tol=1e-8,
-                 m_seed=40, m=40, maxit=1000, use_graph=True, window=0, target_blocks=0):
+                 m_seed=40, m=40, maxit=1000, use_graph=True, window=0, target_blocks=0,
+                 score=None, embed=None):
         L = _march_lib()
         self.ctx = ctx
         self._keep = []
@@ -329,8 +331,17 @@ class March:
             arr[k].tgt_seed = ts.ctypes.data if len(ts) else None
         g2 = np.ascontiguousarray(g2, dtype=np.float64)
         self._keep.append(g2)
+        # optional score output [T][targets][2][H*W] and embedding state
+        # [targets][2][H*W] (CUDA float64, groups in order)
+        for a in (score, embed):
+            if a is not None:
+                import torch
+                assert a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()
+                self._keep.append(a)
         o = _MarchOpts(T, g2.ctypes.data, mode, tol_seed, tol, m_seed, m, maxit, int(use_graph),
-                       int(window), int(target_blocks))
+                       int(window), int(target_blocks),
+                       score.data_ptr() if score is not None else None,
+                       embed.data_ptr() if embed is not None else None)
         self.T = T
         self._h = ctypes.c_void_p()
         ctx._check(L.kp_march_create(ctx._h, len(groups), ctypes.cast(arr, ctypes.c_void_p),

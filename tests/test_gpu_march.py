@@ -157,3 +157,41 @@ def test_march_windows_two_size_classes(kp, orc):
         oms, omt, _ = orc.march(g.H, g.W, T, g2, g.seeds, g.targets, g.target_seed, steps=steps,
                                 tol_seed=1e-10, m_seed=30, a=30, tol_ref=1e-12, m_ref=30)
         assert np.abs(finals[8][k][1] - omt).max() <= 1e-9 * np.abs(omt).max()
+
+
+@pytest.mark.parametrize("window", [1, 4])
+def test_march_score_and_embedding_match_oracle(kp, orc, window):
+    # score of every solved timestep and the probability-flow embedding, fused
+    # into the target solves, against the oracle's march_scores (whole
+    # config-1 trajectory, per-timestep and windowed launches)
+    wl = synth.config(1)
+    g = wl.groups[0]
+    steps = wl.T
+    N = g.N
+    nt = len(g.targets)
+    ctx = kp.Context(max_seeds=2 * window * len(g.seeds) + 2, max_a=wl.a, max_n=N)
+    grp = _groups(wl)
+    score = torch.full((wl.T, nt, 2, N), float("nan"), dtype=torch.float64, device="cuda")
+    emb = torch.zeros((nt, 2, N), dtype=torch.float64, device="cuda")
+    mr = kp.March(ctx, grp, wl.T, wl.g2, mode=0, tol_seed=1e-10, tol=1e-12, m_seed=wl.m_seed,
+                  m=wl.m, window=window, score=score, embed=emb)
+    mr.run(0, 17)
+    mr.run(17, steps - 17)
+    torch.cuda.synchronize()
+    _, omt, S, E = orc.march_scores(g.H, g.W, wl.T, wl.g2, g.seeds, g.targets, g.target_seed,
+                                    steps=steps, tol_seed=1e-10, m_seed=wl.m_seed, a=wl.a,
+                                    tol_ref=1e-12, m_ref=wl.m)
+    sc = score.cpu().numpy()
+    assert np.isfinite(sc).all()                      # every timestep written
+    scale = np.abs(S).max()
+    assert np.abs(sc - S).max() <= 1e-8 * scale
+    assert np.abs(emb.cpu().numpy() - E).max() <= 1e-8 * np.abs(E).max()
+
+
+def test_march_score_needs_both_buffers(kp):
+    wl = synth.config(1)
+    g = wl.groups[0]
+    ctx = kp.Context(max_seeds=4, max_a=wl.a, max_n=g.N)
+    score = torch.zeros((wl.T, len(g.targets), 2, g.N), dtype=torch.float64, device="cuda")
+    with pytest.raises(kp.KPError):
+        kp.March(ctx, _groups(wl), wl.T, wl.g2, score=score)
