@@ -399,12 +399,43 @@ int orc_dense_lu_solve(int n, double* A, double* b, double* x) {
  *            from x0 = 0 to tol_seed, keeping the first-cycle basis (a vectors).
  *   targets: mode 0 (projected): x0 = V_a H_a^{-1} V_a^T b_i with the basis of
  *            seed target_seed[i]; mode 1 (plain): x0 = 0; mode 2 (warm):
- *            x0 = m_i^{n-1}; then GMRES(m_ref) on A_i to tol_ref.
+ *            x0 = m_i^{n-1}; mode 3 (exact Galerkin): x0 = V_a G^{-1} V_a^T b_i
+ *            with G = V_a^T A_i V_a; then GMRES(m_ref) on A_i to tol_ref.
  * mseed/mtgt hold m^{n-1} on entry and m^n on return ([count][N]).
  * seed_it/tgt_it receive Arnoldi steps, tgt_res the final relative residual,
  * tgt_status the GMRES status (0 converged).  OpenMP (if compiled in) runs
  * independent systems in parallel; each system's arithmetic is unchanged.
  */
+/*
+ * Sec. 3, Phase 2 without the seed-matrix shortcut: the Galerkin projection
+ * with the target's own operator A_i (coefficients C) onto the seed's basis,
+ *   G = V_a^T A_i V_a (a x a),  c = V_a^T r,  G alpha = c,  x0 = xinit + V_a alpha.
+ * The paper replaces G by the seed's H_a = V_a^T A_seed V_a; this is the
+ * exact version it approximates.  G is solved by dense LU with partial
+ * pivoting.  Returns 0, or 1 if G is singular (then x0 = xinit).
+ */
+int orc_project_galerkin(int H, int W, const double* C, int a, const double* V, const double* r,
+                         const double* xinit, double* x0) {
+  int N = H * W;
+  for (int k = 0; k < N; ++k) x0[k] = xinit ? xinit[k] : 0.0;
+  if (a <= 0) return 0;
+  double* G = (double*)malloc(sizeof(double) * a * a);
+  double* c = (double*)malloc(sizeof(double) * a);
+  double* alpha = (double*)malloc(sizeof(double) * a);
+  double* Av = (double*)malloc(sizeof(double) * N);
+  for (int k = 0; k < a; ++k) {
+    orc_apply(H, W, C, V + (size_t)k * N, Av);
+    for (int l = 0; l < a; ++l) G[l * a + k] = dot(N, V + (size_t)l * N, Av);   /* row-major */
+  }
+  for (int l = 0; l < a; ++l) c[l] = dot(N, V + (size_t)l * N, r);
+  int rc = orc_dense_lu_solve(a, G, c, alpha);
+  if (rc == 0)
+    for (int i = 0; i < a; ++i)
+      for (int k = 0; k < N; ++k) x0[k] += alpha[i] * V[(size_t)i * N + k];
+  free(G); free(c); free(alpha); free(Av);
+  return rc == 0 ? 0 : 1;
+}
+
 void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, double* mseed,
                     int ntgt, double* mtgt, const int* target_seed, int mode, double tol_seed,
                     int m_seed, int a, double tol_ref, int m_ref, int maxit, int* seed_it,
@@ -444,6 +475,9 @@ void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, dou
                   hess + (size_t)s * (a + 1) * a, b, NULL, x);
     } else if (mode == 2) {
       memcpy(x, mt, sizeof(double) * N);
+    } else if (mode == 3) {
+      int s = target_seed[t];
+      orc_project_galerkin(H, W, C, used[s], basis + (size_t)s * N * (a + 1), b, NULL, x);
     }
     if (tgt_x0res) {
       orc_apply(H, W, C, x, r);

@@ -78,6 +78,8 @@ def lib():
         L.orc_march_step.argtypes = [_i, _i, _d, _d, _d, _i, _pd, _i, _pd, _pi, _i, _d, _i,
                                      _i, _d, _i, _i, _pi, _pi, _pd, _pi, _pd]
         L.orc_score.argtypes = [_i, _i, _d, _pd, _pd, _pd]
+        L.orc_project_galerkin.argtypes = [_i, _i, _pd, _i, _pd, _pd, _pd, _pd]
+        L.orc_project_galerkin.restype = _i
         L.orc_embed_step.argtypes = [_i, _d, _d, _pd, _pd, _pd, _pd]
         _lib = L
     return _lib
@@ -223,7 +225,19 @@ def dense_lu_solve(A, b):
     return x
 
 
-MODE_PROJECTED, MODE_PLAIN, MODE_WARM = 0, 1, 2
+MODE_PROJECTED, MODE_PLAIN, MODE_WARM, MODE_GALERKIN = 0, 1, 2, 3
+
+
+def project_galerkin(H, W, C, V, a, r, xinit=None):
+    """Sec. 3, Phase 2 with the target's own operator: x0 = xinit + V_a G^{-1}
+    V_a^T r, G = V_a^T A_i V_a (C: the target's coefficients, as from coeffs).
+    Returns (x0, singular)."""
+    N = H * W
+    Vc = np.ascontiguousarray(np.asarray(V, dtype=np.float64)[:a].reshape(-1))
+    x0 = np.zeros(N)
+    rc = lib().orc_project_galerkin(H, W, _p(_f64(C)), a, _p(Vc), _p(_f64(r)), _p(_f64(xinit)),
+                                    _p(x0))
+    return x0, bool(rc)
 
 
 @dataclass

@@ -322,3 +322,35 @@ def test_march_step_equals_seed_gmres(orc):
     C = orc.coeffs(H, W, wl.g2[0], 1 / wl.T, 1 / H, m0)
     r = orc.gmres(H, W, C, orc.rhs(H, W, 1 / wl.T, 1 / H, m0), tol=1e-10, m=40, maxit=1000)
     assert np.array_equal(r.x, ms[0])
+
+
+def test_exact_galerkin_projection_pins(orc):
+    # G = V^T A_i V: the residual of x0 is orthogonal to the basis (Galerkin
+    # condition), and with the seed's own operator it equals the paper's
+    # projection through H_a
+    from paper_2511_17634_gb300 import synth
+    wl = synth.config(2, T=1000, ntargets=4)
+    g = wl.groups[0]
+    H, W, N = g.H, g.W, g.N
+    dt, h, g2 = 1.0 / wl.T, 1.0 / H, float(wl.g2[300])
+    ms = g.seeds.reshape(len(g.seeds), -1)[0]
+    mt = g.targets.reshape(len(g.targets), -1)[1]
+    Cs = orc.coeffs(H, W, g2, dt, h, ms)
+    r = orc.gmres(H, W, Cs, orc.rhs(H, W, dt, h, ms), tol=1e-10, m=40, maxit=400, capture=40)
+    Ct = orc.coeffs(H, W, g2, dt, h, mt)
+    b = orc.rhs(H, W, dt, h, mt)
+    x0, sing = orc.project_galerkin(H, W, Ct, r.V, r.a, b)
+    assert not sing
+    res = b - orc.apply(H, W, Ct, x0)
+    assert np.abs(r.V[:r.a] @ res).max() <= 1e-11 * np.linalg.norm(b)
+    xs, _ = orc.project_galerkin(H, W, Cs, r.V, r.a, b)
+    xp, _ = orc.project(r.V, r.Hbar, r.a, r.has_next, b)
+    assert np.abs(xs - xp).max() <= 1e-10 * np.abs(xp).max()
+    # residual form: x1 = xi + V G^-1 V^T (b - A xi) also satisfies the
+    # Galerkin condition, and equals x0 when xi lies in span(V)
+    xi = np.linspace(0, 1, N)
+    x1, _ = orc.project_galerkin(H, W, Ct, r.V, r.a, b - orc.apply(H, W, Ct, xi), xinit=xi)
+    assert np.abs(r.V[:r.a] @ (b - orc.apply(H, W, Ct, x1))).max() <= 1e-11 * np.linalg.norm(b)
+    xv = r.V[:r.a].T @ np.random.default_rng(1).normal(size=r.a)
+    x2, _ = orc.project_galerkin(H, W, Ct, r.V, r.a, b - orc.apply(H, W, Ct, xv), xinit=xv)
+    assert np.abs(x2 - x0).max() <= 1e-9 * np.abs(x0).max()
