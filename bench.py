@@ -461,7 +461,10 @@ def main():
         pls.close()
         del sc, emb
     if not args.no_baselines:
-        for name, mode in (("plain_x0_zero", kp.MARCH_PLAIN), ("plain_warm_start", kp.MARCH_WARM)):
+        modes = [("plain_x0_zero", kp.MARCH_PLAIN), ("plain_warm_start", kp.MARCH_WARM)]
+        if not mixed:
+            modes.append(("projected_exact_galerkin", kp.MARCH_GALERKIN))
+        for name, mode in modes:
             pl = kp.March(ctx, groups, mode=mode, **common)
             t = timed(pl, max(1, args.steps // 2), 1)
             reset()

@@ -297,7 +297,13 @@ kp_status kp_basis_get(kp_ctx* ctx, int seed_id, int timestep, int* a_out, int* 
  * timestep per launch) or 2K sets (windows of K timesteps), so max_seeds must
  * be at least 2 x nseed_total, and 2K x nseed_total for a window of K.
  * ------------------------------------------------------------------------ */
-typedef enum { KP_MARCH_PROJECTED = 0, KP_MARCH_PLAIN = 1, KP_MARCH_WARM = 2 } kp_march_mode;
+typedef enum {
+  KP_MARCH_PROJECTED = 0,   /* the paper: x0 = V_a H_a^{-1} V_a^T b (seed's H_a)          */
+  KP_MARCH_PLAIN = 1,       /* x0 = 0                                                      */
+  KP_MARCH_WARM = 2,        /* x0 = m^{n-1}                                                */
+  KP_MARCH_GALERKIN = 3     /* exact Galerkin with the target's own operator:
+                               x0 = V_a (V_a^T A_i V_a)^{-1} V_a^T b (FP64 plans only)    */
+} kp_march_mode;
 
 typedef struct {
   int H, W;

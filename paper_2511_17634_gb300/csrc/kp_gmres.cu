@@ -238,6 +238,80 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
         proj_flops = (unsigned long long)(2 * nv + 2 * a) * (unsigned long long)N;
       }
     }
+    if (p.x0_mode == X0_GALERKIN) {
+      // Sec. 3, Phase 2 without the seed-matrix shortcut: G = V_a^T A_i V_a
+      // with this target's own operator, G alpha = V_a^T b, x0 = V_a alpha
+      const int sl = d.slot + parity_base;
+      const SlotMeta mt = p.slotMeta[sl];
+      const int a = mt.a;
+      if (mt.timestep == tstep && mt.N == N && a > 0 && a * a <= (m + 1) * m) {
+        const double* V = p.slotV + (size_t)sl * (p.max_a + 1) * p.slot_ld;
+        double* G = sm.Hr;                       // a x a, column-major
+        for (int k = 0; k < a; ++k) {
+          const double* vk = V + (size_t)k * p.slot_ld;
+          double av[EPT];
+#pragma unroll
+          for (int e = 0; e < EPT; ++e) {
+            const int pp = tid + e * NT;
+            av[e] = 0.0;
+            if (pp < N) {
+              const int pe = min(pp + H, N - 1), pw = max(pp - H, 0);
+              const int pn = min(pp + 1, N - 1), ps = max(pp - 1, 0);
+              double t = cd * vk[pp];
+              t = fma(cE[e], vk[pe], t);
+              t = fma(cW[e], vk[pw], t);
+              t = fma(cN[e], vk[pn], t);
+              av[e] = fma(cS[e], vk[ps], t);
+            }
+          }
+          block_partials<NT>(a, [&](int l) {
+            const double* vl = V + (size_t)l * p.slot_ld;
+            double s = 0.0;
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+              const int pp = tid + e * NT;
+              if (pp < N) s = fma(vl[pp], av[e], s);
+            }
+            return s;
+          }, sm.red);
+          if (warp == 0)
+            for (int l = lane; l < a; l += 32) G[l + k * a] = cross_warp<NT>(sm.red, l);
+          __syncthreads();                       // partials of the next column reuse red
+        }
+        double bv[EPT];
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) bv[e] = bval(tid + e * NT);
+        block_partials<NT>(a, [&](int l) {
+          const double* vl = V + (size_t)l * p.slot_ld;
+          double s = 0.0;
+#pragma unroll
+          for (int e = 0; e < EPT; ++e) {
+            const int pp = tid + e * NT;
+            if (pp < N) s = fma(vl[pp], bv[e], s);
+          }
+          return s;
+        }, sm.red);
+        if (warp == 0) {
+          for (int l = lane; l < a; l += 32) sm.hb[l] = cross_warp<NT>(sm.red, l);
+          __syncwarp();
+          const bool ok = lu_solve_warp(G, a, sm.hb, lane);
+          if (lane == 0) sm.fl[5] = ok;
+        }
+        __syncthreads();
+        if (sm.fl[5]) {
+#pragma unroll
+          for (int e = 0; e < EPT; ++e) {
+            const int pp = tid + e * NT;
+            if (pp < N) {
+              double xv = 0.0;
+              for (int i = 0; i < a; ++i) xv = fma(sm.hb[i], V[(size_t)i * p.slot_ld + pp], xv);
+              sm.xs[pp] = xv;
+            }
+          }
+        }
+        proj_flops = (unsigned long long)(a * (9 + 2 * a) + 4 * a) * (unsigned long long)N;
+      }
+    }
     __syncthreads();
     double w[EPT];
     auto residual = [&]() { residual_of(sm.xs, w); };

@@ -146,7 +146,52 @@ __device__ __forceinline__ void st_release_gpu(int* a, int v) {
 
 constexpr int kVbRows = 48;   // rows per seed slot of the BF16 basis (tensor-core N tile)
 
-enum { X0_READ = 0, X0_ZERO = 1, X0_WARM = 2, X0_PROJECT = 3 };
+enum { X0_READ = 0, X0_ZERO = 1, X0_WARM = 2, X0_PROJECT = 3, X0_GALERKIN = 4 };
+
+// Solves G y = c (G: n x n column-major in shared memory, c: length n) by LU
+// with partial pivoting on one warp (lanes own rows); y overwrites c, G is
+// overwritten.  Returns false (on every lane) if a pivot is exactly zero.
+__device__ __forceinline__ bool lu_solve_warp(double* G, int n, double* c, int lane) {
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + lane; i < n; i += 32) {
+      const double v = fabs(G[i + k * n]);
+      if (v > best) { best = v; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (!(best > 0.0)) return false;
+    if (bi != k) {
+      for (int j = lane; j < n; j += 32) {
+        const double t = G[k + j * n];
+        G[k + j * n] = G[bi + j * n];
+        G[bi + j * n] = t;
+      }
+      if (lane == 0) { const double t = c[k]; c[k] = c[bi]; c[bi] = t; }
+    }
+    __syncwarp();
+    const double ip = 1.0 / G[k + k * n];
+    for (int i = k + 1 + lane; i < n; i += 32) {
+      const double l = G[i + k * n] * ip;
+      for (int j = k + 1; j < n; ++j) G[i + j * n] = fma(-l, G[k + j * n], G[i + j * n]);
+      c[i] = fma(-l, c[k], c[i]);
+    }
+    __syncwarp();
+  }
+  if (lane == 0)
+    for (int i = n - 1; i >= 0; --i) {
+      double s = c[i];
+      for (int j = i + 1; j < n; ++j) s = fma(-G[i + j * n], c[j], s);
+      c[i] = s / G[i + i * n];
+    }
+  __syncwarp();
+  return true;
+}
 
 struct ProjParams {
   const SysDesc* sys;

@@ -166,6 +166,7 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset,
   } else {
     g.score_stride = P->score_stride;
     g.x0_mode = P->opt.mode == KP_MARCH_PROJECTED ? (P->ns ? kp::X0_PROJECT : kp::X0_ZERO)
+              : P->opt.mode == KP_MARCH_GALERKIN ? (P->ns ? kp::X0_GALERKIN : kp::X0_ZERO)
               : P->opt.mode == KP_MARCH_WARM ? kp::X0_WARM : kp::X0_ZERO;
     g.acc_kind = 1;
     if (P->Cp) {
@@ -305,7 +306,7 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
   if (!out || !opt || ngroups < 1 || !groups) return kp::set_error(c, KP_ERR_ARG, "bad march arguments");
   *out = nullptr;
   const kp_march_opts& o = *opt;
-  if (o.T < 1 || !o.g2 || o.mode < 0 || o.mode > 2 || o.m_seed < 1 || o.m_seed > kp::kMaxM ||
+  if (o.T < 1 || !o.g2 || o.mode < 0 || o.mode > 3 || o.m_seed < 1 || o.m_seed > kp::kMaxM ||
       (o.score != nullptr) != (o.embed != nullptr) ||
       o.m < 1 || o.m > kp::kMaxM || o.maxit < 0 || !(o.tol >= 0) || !(o.tol_seed >= 0))
     return kp::set_error(c, KP_ERR_ARG, "bad march options");
@@ -322,7 +323,7 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
       kp_march_destroy(P);
       return kp::set_error(c, KP_ERR_ARG, "group %d: bad sizes or pointers", gi);
     }
-    if (o.mode == KP_MARCH_PROJECTED)
+    if (o.mode == KP_MARCH_PROJECTED || o.mode == KP_MARCH_GALERKIN)
       for (int t = 0; t < g.ntgt; ++t)
         if (g.tgt_seed[t] < 0 || g.tgt_seed[t] >= g.nseed) {
           kp_march_destroy(P);
@@ -351,6 +352,10 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
     return kp::set_error(c, KP_ERR_UNSUPPORTED, "grids above 4096 unknowns: one grid size per plan");
   }
   if (s != KP_OK) { kp_march_destroy(P); return s; }
+  if (o.mode == KP_MARCH_GALERKIN && (P->mixed || P->shT.cs)) {
+    kp_march_destroy(P);
+    return kp::set_error(c, KP_ERR_UNSUPPORTED, "exact Galerkin projection needs the FP64 one-block solver");
+  }
   if (o.score && (P->mixed || P->shT.cs)) {
     kp_march_destroy(P);
     return kp::set_error(c, KP_ERR_UNSUPPORTED, "score extraction needs the FP64 one-block solver");
@@ -453,7 +458,7 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
       P->tgt_base.push_back(base);
       std::vector<int> ord(g.ntgt);
       for (int k = 0; k < g.ntgt; ++k) ord[k] = k;
-      if (o.mode == KP_MARCH_PROJECTED)
+      if (o.mode == KP_MARCH_PROJECTED || o.mode == KP_MARCH_GALERKIN)
         std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return g.tgt_seed[x] < g.tgt_seed[y]; });
       for (int k = 0; k < g.ntgt; ++k) hperm[base + k] = ord[k];
       base += g.ntgt;

@@ -266,7 +266,7 @@ class Context:
 
 
 # ---------------------------------------------------------------- time march
-MARCH_PROJECTED, MARCH_PLAIN, MARCH_WARM = 0, 1, 2
+MARCH_PROJECTED, MARCH_PLAIN, MARCH_WARM, MARCH_GALERKIN = 0, 1, 2, 3
 
 
 class _Group(ctypes.Structure):

@@ -28,7 +28,7 @@ def _groups(wl):
     return out
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 @pytest.mark.parametrize("use_graph", [True, False])
 def test_march_matches_oracle_tiny(kp, orc, mode, use_graph):
     wl = synth.config(1)
@@ -195,3 +195,24 @@ def test_march_score_needs_both_buffers(kp):
     score = torch.zeros((wl.T, len(g.targets), 2, g.N), dtype=torch.float64, device="cuda")
     with pytest.raises(kp.KPError):
         kp.March(ctx, _groups(wl), wl.T, wl.g2, score=score)
+
+
+def test_march_exact_galerkin_sampled(kp, orc):
+    # exact Galerkin initial guess (target's own operator) at the benchmark's
+    # size and launch configuration (windows, 128x4 shape), against the oracle
+    wl = synth.config(2, T=1000, ntargets=24)
+    g = wl.groups[0]
+    steps = 5
+    ctx = kp.Context(max_seeds=2 * 8 * wl.n_seed_planes, max_a=wl.a, max_n=g.N)
+    grp = _groups(wl)
+    mr = kp.March(ctx, grp, wl.T, wl.g2, mode=3, tol_seed=wl.tol_seed, tol=1e-10,
+                  m_seed=wl.m_seed, m=wl.m, window=8)
+    st, _ = mr.run(0, steps, stats=True)
+    torch.cuda.synchronize()
+    _, omt, ost = orc.march(g.H, g.W, wl.T, wl.g2, g.seeds, g.targets, g.target_seed, steps=steps,
+                            mode=3, tol_seed=wl.tol_seed, m_seed=wl.m_seed, a=wl.a, tol_ref=1e-10,
+                            m_ref=wl.m)
+    assert np.abs(grp[0][1].cpu().numpy() - omt).max() <= 1e-8 * np.abs(omt).max()
+    gpu_it = np.array([s.tgt_iters for s in st])
+    orc_it = np.array([o.tgt_iters.sum() for o in ost])
+    assert np.abs(gpu_it - orc_it).max() <= len(g.targets)
