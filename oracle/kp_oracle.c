@@ -401,6 +401,10 @@ int orc_dense_lu_solve(int n, double* A, double* b, double* x) {
  *            seed target_seed[i]; mode 1 (plain): x0 = 0; mode 2 (warm):
  *            x0 = m_i^{n-1}; mode 3 (exact Galerkin): x0 = V_a G^{-1} V_a^T b_i
  *            with G = V_a^T A_i V_a; then GMRES(m_ref) on A_i to tol_ref.
+ * picard > 1 adds Picard iterations k = 2..picard (Sec. 2.3, m~ = m^{n,(k-1)}):
+ * the coefficients are rebuilt from the latest iterate, the right-hand side
+ * stays m^{n-1}/dt and GMRES starts from that iterate; the seed basis is the
+ * one of the first solve.
  * mseed/mtgt hold m^{n-1} on entry and m^n on return ([count][N]).
  * seed_it/tgt_it receive Arnoldi steps, tgt_res the final relative residual,
  * tgt_status the GMRES status (0 converged).  OpenMP (if compiled in) runs
@@ -439,7 +443,8 @@ int orc_project_galerkin(int H, int W, const double* C, int a, const double* V, 
 void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, double* mseed,
                     int ntgt, double* mtgt, const int* target_seed, int mode, double tol_seed,
                     int m_seed, int a, double tol_ref, int m_ref, int maxit, int* seed_it,
-                    int* tgt_it, double* tgt_res, int* tgt_status, double* tgt_x0res) {
+                    int* tgt_it, double* tgt_res, int* tgt_status, double* tgt_x0res, int picard) {
+  int K = picard > 1 ? picard : 1;
   int N = H * W;
   int lda = a + 1;
   double* basis = (double*)calloc((size_t)nseed * N * (a + 1), sizeof(double));
@@ -457,6 +462,14 @@ void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, dou
     orc_rhs(H, W, dt, h, ms, NULL, NULL, b);
     orc_gmres(H, W, C, b, x, tol_seed, m_seed, maxit, &seed_it[s], &rr, NULL, a,
               basis + (size_t)s * N * (a + 1), hess + (size_t)s * (a + 1) * a, &used[s], &nxt[s]);
+    /* Picard iterations k = 2..K (Sec. 2.3): lag the nonlinear term on the
+     * latest iterate, same right-hand side, warm start from that iterate */
+    for (int k = 1; k < K; ++k) {
+      int it = 0;
+      orc_coeffs(H, W, g2, dt, h, x, NULL, NULL, C);
+      orc_gmres(H, W, C, b, x, tol_seed, m_seed, maxit, &it, &rr, NULL, 0, NULL, NULL, NULL, NULL);
+      seed_it[s] += it;
+    }
     memcpy(ms, x, sizeof(double) * N);
     free(C); free(b); free(x);
   }
@@ -487,6 +500,13 @@ void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, dou
     }
     tgt_status[t] = orc_gmres(H, W, C, b, x, tol_ref, m_ref, maxit, &tgt_it[t], &tgt_res[t],
                               NULL, 0, NULL, NULL, NULL, NULL);
+    for (int k = 1; k < K; ++k) {               /* Picard iterations, as for the seeds */
+      int it = 0;
+      orc_coeffs(H, W, g2, dt, h, x, NULL, NULL, C);
+      tgt_status[t] = orc_gmres(H, W, C, b, x, tol_ref, m_ref, maxit, &it, &tgt_res[t], NULL, 0,
+                                NULL, NULL, NULL, NULL);
+      tgt_it[t] += it;
+    }
     memcpy(mt, x, sizeof(double) * N);
     free(C); free(b); free(x); free(r);
   }

@@ -76,7 +76,7 @@ def lib():
         L.orc_dense_lu_solve.argtypes = [_i, _pd, _pd, _pd]
         L.orc_dense_lu_solve.restype = _i
         L.orc_march_step.argtypes = [_i, _i, _d, _d, _d, _i, _pd, _i, _pd, _pi, _i, _d, _i,
-                                     _i, _d, _i, _i, _pi, _pi, _pd, _pi, _pd]
+                                     _i, _d, _i, _i, _pi, _pi, _pd, _pi, _pd, _i]
         L.orc_score.argtypes = [_i, _i, _d, _pd, _pd, _pd]
         L.orc_project_galerkin.argtypes = [_i, _i, _pd, _i, _pd, _pd, _pd, _pd]
         L.orc_project_galerkin.restype = _i
@@ -250,10 +250,10 @@ class StepStats:
 
 
 def march_step(H, W, dt, h, g2, mseed, mtgt, target_seed, mode=MODE_PROJECTED,
-               tol_seed=1e-10, m_seed=40, a=40, tol_ref=1e-8, m_ref=40, maxit=1000):
+               tol_seed=1e-10, m_seed=40, a=40, tol_ref=1e-8, m_ref=40, maxit=1000, picard=1):
     """One timestep of Sec. 2.3 + Sec. 3 for seeds and targets of one grid
-    size (f = 0).  ``mseed`` (nseed, N) and ``mtgt`` (ntgt, N) are updated in
-    place from m^{n-1} to m^n."""
+    size (f = 0), with `picard` lagged-linearisation iterations.  ``mseed``
+    (nseed, N) and ``mtgt`` (ntgt, N) are updated in place from m^{n-1} to m^n."""
     assert mseed.dtype == np.float64 and mseed.flags["C_CONTIGUOUS"]
     assert mtgt.dtype == np.float64 and mtgt.flags["C_CONTIGUOUS"]
     ns, nt = mseed.shape[0], mtgt.shape[0]
@@ -262,7 +262,8 @@ def march_step(H, W, dt, h, g2, mseed, mtgt, target_seed, mode=MODE_PROJECTED,
                    np.zeros(nt, np.int32), np.zeros(nt))
     lib().orc_march_step(H, W, dt, h, g2, ns, _p(mseed), nt, _p(mtgt), _p(ts), mode,
                          tol_seed, m_seed, a, tol_ref, m_ref, maxit, _p(st.seed_iters),
-                         _p(st.tgt_iters), _p(st.tgt_res), _p(st.tgt_status), _p(st.tgt_x0res))
+                         _p(st.tgt_iters), _p(st.tgt_res), _p(st.tgt_status), _p(st.tgt_x0res),
+                         int(picard))
     return st
 
 

@@ -354,3 +354,33 @@ def test_exact_galerkin_projection_pins(orc):
     xv = r.V[:r.a].T @ np.random.default_rng(1).normal(size=r.a)
     x2, _ = orc.project_galerkin(H, W, Ct, r.V, r.a, b - orc.apply(H, W, Ct, xv), xinit=xv)
     assert np.abs(x2 - x0).max() <= 1e-9 * np.abs(x0).max()
+
+
+def test_picard_iterations_pins(orc):
+    # K = 1 is the one-solve step; more Picard iterations converge to the
+    # fixed point A(m^n) m^n = m^{n-1}/dt of the implicit step; with g = 0 the
+    # operator does not depend on m~ and extra iterations change nothing
+    H, W = 9, 7
+    N = H * W
+    rng = np.random.default_rng(4)
+    m0 = rng.uniform(0, 1, (2, N))
+    dt, h, g2 = 0.02, 1.0 / H, 0.4
+    kw = dict(mode=1, tol_seed=1e-13, m_seed=40, a=40, tol_ref=1e-13, m_ref=40)
+    ref = m0.copy(); s1 = m0[:1].copy()
+    orc.march_step(H, W, dt, h, g2, s1, ref, [0, 0], **kw)
+    one = m0.copy(); s2 = m0[:1].copy()
+    orc.march_step(H, W, dt, h, g2, s2, one, [0, 0], picard=1, **kw)
+    assert np.array_equal(one, ref)
+    res = []
+    for K in (1, 2, 4, 8):
+        x = m0.copy(); s = m0[:1].copy()
+        orc.march_step(H, W, dt, h, g2, s, x, [0, 0], picard=K, **kw)
+        C = orc.coeffs(H, W, g2, dt, h, x[0])          # A(m^n) from the result itself
+        r = orc.apply(H, W, C, x[0]) - orc.rhs(H, W, dt, h, m0[0])
+        res.append(np.linalg.norm(r) / np.linalg.norm(m0[0] / dt))
+    assert res[1] < 0.2 * res[0] and res[3] < 1e-10
+    x0 = m0.copy(); xs = m0[:1].copy()
+    orc.march_step(H, W, dt, h, 0.0, xs, x0, [0, 0], **kw)
+    x3 = m0.copy(); xs3 = m0[:1].copy()
+    orc.march_step(H, W, dt, h, 0.0, xs3, x3, [0, 0], picard=3, **kw)
+    assert np.allclose(x3, x0, rtol=1e-12, atol=0)
