@@ -460,6 +460,16 @@ def main():
                     "timestep and the probability-flow embedding written from the solve epilogue"}
         pls.close()
         del sc, emb
+        # three Picard iterations per timestep (the lagged term re-linearised
+        # on the latest iterate, Sec. 2.3) -- a different discretisation, timed
+        plp = kp.March(ctx, groups, mode=kp.MARCH_PROJECTED, picard=3, **common)
+        t = timed(plp, max(1, args.steps // 2), 1)
+        reset()
+        stp, _ = plp.run(0, NS, stats=True)
+        out["picard_3_iterations"] = {
+            "value": world * nt_planes * NS * max(1, args.steps // 2) / t, "unit": "systems/s",
+            "iters_per_solve": sum(s.tgt_iters for s in stp) / (nt_planes * NS)}
+        plp.close()
     if not args.no_baselines:
         modes = [("plain_x0_zero", kp.MARCH_PLAIN), ("plain_warm_start", kp.MARCH_WARM)]
         if not mixed:

@@ -339,6 +339,10 @@ typedef struct {
    *   sets x^0 (zero in the paper).  Must be given with score.          */
   double* score;
   double* embed;
+  int picard;            /* Picard iterations per timestep (Sec. 2.3): 0 or 1 = one
+                            solve with m~ = m^{n-1}; K > 1 re-solves with m~ the
+                            latest iterate, same right-hand side, warm start; the
+                            stored seed basis is the first solve's.  FP64 plans. */
 } kp_march_opts;
 
 /* Per-timestep totals, filled on the host by kp_march_run. */

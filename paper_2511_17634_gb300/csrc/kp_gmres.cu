@@ -120,33 +120,37 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
     const double ee = g2 / (8.0 * hh * hh);
     const double cd = 1.0 / d.dt + 2.0 * g2 / (hh * hh);
     const double i2h = 1.0 / (2.0 * hh);
-    const bool capture = p.capV != nullptr;
+    bool capture = p.capV != nullptr;          // first solve of the timestep only
     const int cidx = p.factor ? parity_base + sysi : sysi;   // capture record (or seed slot)
     double* capV = capture ? p.capV + (size_t)cidx * (p.cap_a + 1) * p.cap_ld : nullptr;
     double* capH = capture ? p.capH + (size_t)cidx * (p.cap_a + 1) * p.cap_a : nullptr;
 
-    // stencil coefficients (Sec. 2.3, listing after Eq. 11); zero where the
+    // stencil coefficients (Sec. 2.3, listing after Eq. 11) from the lagged
+    // field m~ (m^{n-1}, or the latest Picard iterate); zero where the
     // neighbour lies outside the grid
     double cE[EPT], cW[EPT], cN[EPT], cS[EPT];
+    auto set_coeffs = [&](const double* mtl) {
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-      const int pp = tid + k * NT;
-      cE[k] = cW[k] = cN[k] = cS[k] = 0.0;
-      if (pp < N) {
-        const int i = pp / H, j = pp - i * H;
-        const double mE = (i + 1 < W) ? d.mt[pp + H] : 0.0;
-        const double mW = (i > 0) ? d.mt[pp - H] : 0.0;
-        const double mN = (j + 1 < H) ? d.mt[pp + 1] : 0.0;
-        const double mS = (j > 0) ? d.mt[pp - 1] : 0.0;
-        const double fxp = d.fx ? d.fx[pp] : 0.0;
-        const double fyp = d.fy ? d.fy[pp] : 0.0;
-        const double dmx = mE - mW, dmy = mN - mS;
-        if (i + 1 < W) cE[k] = -cc + fxp * i2h - ee * dmx;
-        if (i > 0) cW[k] = -cc - fxp * i2h + ee * dmx;
-        if (j + 1 < H) cN[k] = -cc + fyp * i2h - ee * dmy;
-        if (j > 0) cS[k] = -cc - fyp * i2h + ee * dmy;
+      for (int k = 0; k < EPT; ++k) {
+        const int pp = tid + k * NT;
+        cE[k] = cW[k] = cN[k] = cS[k] = 0.0;
+        if (pp < N) {
+          const int i = pp / H, j = pp - i * H;
+          const double mE = (i + 1 < W) ? mtl[pp + H] : 0.0;
+          const double mW = (i > 0) ? mtl[pp - H] : 0.0;
+          const double mN = (j + 1 < H) ? mtl[pp + 1] : 0.0;
+          const double mS = (j > 0) ? mtl[pp - 1] : 0.0;
+          const double fxp = d.fx ? d.fx[pp] : 0.0;
+          const double fyp = d.fy ? d.fy[pp] : 0.0;
+          const double dmx = mE - mW, dmy = mN - mS;
+          if (i + 1 < W) cE[k] = -cc + fxp * i2h - ee * dmx;
+          if (i > 0) cW[k] = -cc - fxp * i2h + ee * dmx;
+          if (j + 1 < H) cN[k] = -cc + fyp * i2h - ee * dmy;
+          if (j > 0) cS[k] = -cc - fyp * i2h + ee * dmy;
+        }
       }
-    }
+    };
+    set_coeffs(d.mt);
     // r = b - A v, the product chain started from b (one multiply, five fused
     // multiply-adds per point)
     auto residual_of = [&](const double* v, double (&out)[EPT]) {
@@ -315,146 +319,132 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
     __syncthreads();
     double w[EPT];
     auto residual = [&]() { residual_of(sm.xs, w); };
-    if (p.x0_mode == X0_ZERO) {                // r = b, no operator application needed
-#pragma unroll
-      for (int k = 0; k < EPT; ++k) w[k] = bval(tid + k * NT);
-    } else {
-      residual();
-    }
-    block_partials<NT>(2, [&](int i) {
-      double s = 0.0;
-#pragma unroll
-      for (int k = 0; k < EPT; ++k) {
-        const double bv = bval(tid + k * NT);
-        s += (i == 0) ? bv * bv : w[k] * w[k];
-      }
-      return s;
-    }, sm.red);
-    if (tid == 0) {
-      sm.sc[0] = sqrt(cross_warp<NT>(sm.red, 0));
-      sm.sc[1] = sqrt(cross_warp<NT>(sm.red, 1));
-    }
-    __syncthreads();
-    const double bnorm = sm.sc[0];
-    double beta = sm.sc[1];
-
     int steps = 0, status = KP_NOT_CONVERGED, cycle = 0;
-    if (bnorm == 0.0) {
+    double bnorm = 0.0, beta = 0.0;
+    const int npic = p.picard > 1 ? p.picard : 1;
+    for (int pk = 0; pk < npic; ++pk) {
+      if (pk > 0) {
+        // Picard iteration k = pk + 1 (Sec. 2.3): the nonlinear term lagged on
+        // the latest iterate m^{n,(k-1)} (in shared memory), the same right-hand
+        // side, GMRES warm-started from that iterate
+        __syncthreads();
+        set_coeffs(sm.xs);
+        status = KP_NOT_CONVERGED;
+        capture = false;                         // the stored basis is the first solve's
+      }
+      if (pk == 0 && p.x0_mode == X0_ZERO) {     // r = b, no operator application needed
 #pragma unroll
-      for (int k = 0; k < EPT; ++k) sm.xs[tid + k * NT] = 0.0;
-      beta = 0.0;
-      status = KP_OK;
-    }
-    while (status == KP_NOT_CONVERGED) {
-      if (beta <= p.tol * bnorm) { status = KP_OK; break; }
-      if (!isfinite(beta)) { status = KP_BREAKDOWN; break; }
-      if (steps >= p.maxit) break;
-      {
-        const double ib = 1.0 / beta;
-        double* v0 = slot(0);
+        for (int k = 0; k < EPT; ++k) w[k] = bval(tid + k * NT);
+      } else {
+        residual();
+      }
+      block_partials<NT>(2, [&](int i) {
+        double s = 0.0;
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
-          const int pp = tid + k * NT;
-          v0[pp] = w[k] * ib;
-          if (capture && cycle == 0 && pp < N) capV[pp] = w[k] * ib;
+          const double bv = bval(tid + k * NT);
+          s += (i == 0) ? bv * bv : w[k] * w[k];
         }
-        if (tid == 0) sm.g[0] = beta;
+        return s;
+      }, sm.red);
+      if (tid == 0) {
+        sm.sc[0] = sqrt(cross_warp<NT>(sm.red, 0));
+        sm.sc[1] = sqrt(cross_warp<NT>(sm.red, 1));
       }
-      int kdone = 0;
-      int brk = 0;
-      // Givens update of Hessenberg column j once h_{j+1,j}^2 = hn2 is known
-      // (one lane): rotations, residual estimate, convergence flags.
-      auto givens_step = [&](int j, double hn2) {
-        const double ihn = hn2 > 0.0 ? rsqrt(hn2) : 0.0;
-        const double hn = hn2 * ihn;
-        const int b = !(hn > 1e-14 * sqrt(sm.sc[2]));
-        sm.Hr[j + j * ld] += cd;                 // H_A = H_{A - cd I} + cd I
-        sm.Hr[(j + 1) + j * ld] = hn;
-        if (capture && cycle == 0 && j < p.cap_a) {
-          for (int i = 0; i <= j + 1; ++i) capH[i + j * (p.cap_a + 1)] = sm.Hr[i + j * ld];
-        }
-        for (int i = 0; i < j; ++i) {
-          const double t1 = sm.Hr[i + j * ld], t2 = sm.Hr[(i + 1) + j * ld];
-          sm.Hr[i + j * ld] = sm.cs[i] * t1 + sm.sn[i] * t2;
-          sm.Hr[(i + 1) + j * ld] = -sm.sn[i] * t1 + sm.cs[i] * t2;
-        }
-        const double a0 = sm.Hr[j + j * ld];
-        const double rr = a0 * a0 + hn2;
-        const double ir = rsqrt(rr);
-        const double c = a0 * ir, s = hn * ir;
-        sm.cs[j] = c;
-        sm.sn[j] = s;
-        sm.Hr[j + j * ld] = rr * ir;
-        sm.rinv[j] = ir;
-        sm.Hr[(j + 1) + j * ld] = 0.0;
-        sm.g[j + 1] = -s * sm.g[j];
-        sm.g[j] = c * sm.g[j];
-        const double res = fabs(sm.g[j + 1]);
-        sm.sc[3] = ihn;
-        sm.fl[1] = b;
-        sm.fl[2] = (res <= p.tol * bnorm) || b || (steps >= p.maxit) || (j + 1 == m);
-      };
-      for (int j = 0; j < m; ++j) {
-        __syncthreads();                       // v_j complete
-        apply_off(slot(j), w);
-        ++steps;
-        const int nh = j + 1;
-        auto dots = [&](int i) {
-          double s = 0.0;
-          if (i < nh) {
-            const double* vi = slot(i);
+      __syncthreads();
+      bnorm = sm.sc[0];
+      beta = sm.sc[1];
+
+      if (bnorm == 0.0) {
 #pragma unroll
-            for (int k = 0; k < EPT; ++k) s += vi[tid + k * NT] * w[k];
-          } else {
+        for (int k = 0; k < EPT; ++k) sm.xs[tid + k * NT] = 0.0;
+        beta = 0.0;
+        status = KP_OK;
+      }
+      while (status == KP_NOT_CONVERGED) {
+        if (beta <= p.tol * bnorm) { status = KP_OK; break; }
+        if (!isfinite(beta)) { status = KP_BREAKDOWN; break; }
+        if (steps >= p.maxit) break;
+        {
+          const double ib = 1.0 / beta;
+          double* v0 = slot(0);
 #pragma unroll
-            for (int k = 0; k < EPT; ++k) s += w[k] * w[k];
+          for (int k = 0; k < EPT; ++k) {
+            const int pp = tid + k * NT;
+            v0[pp] = w[k] * ib;
+            if (capture && cycle == 0 && pp < N) capV[pp] = w[k] * ib;
           }
-          return s;
+          if (tid == 0) sm.g[0] = beta;
+        }
+        int kdone = 0;
+        int brk = 0;
+        // Givens update of Hessenberg column j once h_{j+1,j}^2 = hn2 is known
+        // (one lane): rotations, residual estimate, convergence flags.
+        auto givens_step = [&](int j, double hn2) {
+          const double ihn = hn2 > 0.0 ? rsqrt(hn2) : 0.0;
+          const double hn = hn2 * ihn;
+          const int b = !(hn > 1e-14 * sqrt(sm.sc[2]));
+          sm.Hr[j + j * ld] += cd;                 // H_A = H_{A - cd I} + cd I
+          sm.Hr[(j + 1) + j * ld] = hn;
+          if (capture && cycle == 0 && j < p.cap_a) {
+            for (int i = 0; i <= j + 1; ++i) capH[i + j * (p.cap_a + 1)] = sm.Hr[i + j * ld];
+          }
+          for (int i = 0; i < j; ++i) {
+            const double t1 = sm.Hr[i + j * ld], t2 = sm.Hr[(i + 1) + j * ld];
+            sm.Hr[i + j * ld] = sm.cs[i] * t1 + sm.sn[i] * t2;
+            sm.Hr[(i + 1) + j * ld] = -sm.sn[i] * t1 + sm.cs[i] * t2;
+          }
+          const double a0 = sm.Hr[j + j * ld];
+          const double rr = a0 * a0 + hn2;
+          const double ir = rsqrt(rr);
+          const double c = a0 * ir, s = hn * ir;
+          sm.cs[j] = c;
+          sm.sn[j] = s;
+          sm.Hr[j + j * ld] = rr * ir;
+          sm.rinv[j] = ir;
+          sm.Hr[(j + 1) + j * ld] = 0.0;
+          sm.g[j + 1] = -s * sm.g[j];
+          sm.g[j] = c * sm.g[j];
+          const double res = fabs(sm.g[j + 1]);
+          sm.sc[3] = ihn;
+          sm.fl[1] = b;
+          sm.fl[2] = (res <= p.tol * bnorm) || b || (steps >= p.maxit) || (j + 1 == m);
         };
-        // CGS pass 1: h_i = <v_i, w> and ||w||^2 in one batched reduction
-        block_partials<NT>(nh + 1, dots, sm.red);
-        if (warp == 0) {
-          double sq = 0.0;
-          for (int i = lane; i <= nh; i += 32) {
-            const double s = cross_warp<NT>(sm.red, i);
-            sm.hb[i] = s;
-            if (i < nh) { sm.Hr[i + j * ld] = s; sq += s * s; }
-          }
-          sq = warp_sum(sq);
-          if (lane == 0) {
-            const double ww0 = sm.hb[nh];
-            sm.sc[2] = ww0;
-            // second pass always (CGS2), or only when the first removed over
-            // half of ||w||^2 (DGKS); without it ||w_1||^2 = ||w||^2 - ||h||^2
-            const int pass2 = (p.reorth == 0) || (ww0 - sq < 0.5 * ww0);
-            sm.fl[0] = pass2;
-            if (!pass2) givens_step(j, ww0 - sq);
-          }
-        }
-        __syncthreads();
-        for (int i = 0; i < nh; ++i) {
-          const double hi = sm.hb[i];
-          const double* vi = slot(i);
+        for (int j = 0; j < m; ++j) {
+          __syncthreads();                       // v_j complete
+          apply_off(slot(j), w);
+          ++steps;
+          const int nh = j + 1;
+          auto dots = [&](int i) {
+            double s = 0.0;
+            if (i < nh) {
+              const double* vi = slot(i);
 #pragma unroll
-          for (int k = 0; k < EPT; ++k) w[k] = fma(-hi, vi[tid + k * NT], w[k]);
-        }
-        if (sm.fl[0]) {
-          // CGS pass 2 (reorthogonalisation) with ||w_1||^2 in the same reduction;
-          // ||w_2||^2 = ||w_1||^2 - ||h_2||^2 (h_2 = O(eps) after pass 1), checked
+              for (int k = 0; k < EPT; ++k) s += vi[tid + k * NT] * w[k];
+            } else {
+#pragma unroll
+              for (int k = 0; k < EPT; ++k) s += w[k] * w[k];
+            }
+            return s;
+          };
+          // CGS pass 1: h_i = <v_i, w> and ||w||^2 in one batched reduction
           block_partials<NT>(nh + 1, dots, sm.red);
           if (warp == 0) {
             double sq = 0.0;
             for (int i = lane; i <= nh; i += 32) {
               const double s = cross_warp<NT>(sm.red, i);
               sm.hb[i] = s;
-              if (i < nh) { sm.Hr[i + j * ld] += s; sq += s * s; }
+              if (i < nh) { sm.Hr[i + j * ld] = s; sq += s * s; }
             }
             sq = warp_sum(sq);
             if (lane == 0) {
-              const double ww1 = sm.hb[nh];
-              const int exact = sq > 0.25 * ww1;     // large correction: recompute the norm
-              sm.fl[3] = exact;
-              if (!exact) givens_step(j, ww1 - sq);
+              const double ww0 = sm.hb[nh];
+              sm.sc[2] = ww0;
+              // second pass always (CGS2), or only when the first removed over
+              // half of ||w||^2 (DGKS); without it ||w_1||^2 = ||w||^2 - ||h||^2
+              const int pass2 = (p.reorth == 0) || (ww0 - sq < 0.5 * ww0);
+              sm.fl[0] = pass2;
+              if (!pass2) givens_step(j, ww0 - sq);
             }
           }
           __syncthreads();
@@ -464,109 +454,136 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
 #pragma unroll
             for (int k = 0; k < EPT; ++k) w[k] = fma(-hi, vi[tid + k * NT], w[k]);
           }
-          if (sm.fl[3]) {
-            block_partials<NT>(1, [&](int) {
-              double s = 0.0;
-#pragma unroll
-              for (int k = 0; k < EPT; ++k) s += w[k] * w[k];
-              return s;
-            }, sm.red);
-            if (tid == 0) givens_step(j, cross_warp<NT>(sm.red, 0));
+          if (sm.fl[0]) {
+            // CGS pass 2 (reorthogonalisation) with ||w_1||^2 in the same reduction;
+            // ||w_2||^2 = ||w_1||^2 - ||h_2||^2 (h_2 = O(eps) after pass 1), checked
+            block_partials<NT>(nh + 1, dots, sm.red);
+            if (warp == 0) {
+              double sq = 0.0;
+              for (int i = lane; i <= nh; i += 32) {
+                const double s = cross_warp<NT>(sm.red, i);
+                sm.hb[i] = s;
+                if (i < nh) { sm.Hr[i + j * ld] += s; sq += s * s; }
+              }
+              sq = warp_sum(sq);
+              if (lane == 0) {
+                const double ww1 = sm.hb[nh];
+                const int exact = sq > 0.25 * ww1;     // large correction: recompute the norm
+                sm.fl[3] = exact;
+                if (!exact) givens_step(j, ww1 - sq);
+              }
+            }
             __syncthreads();
+            for (int i = 0; i < nh; ++i) {
+              const double hi = sm.hb[i];
+              const double* vi = slot(i);
+#pragma unroll
+              for (int k = 0; k < EPT; ++k) w[k] = fma(-hi, vi[tid + k * NT], w[k]);
+            }
+            if (sm.fl[3]) {
+              block_partials<NT>(1, [&](int) {
+                double s = 0.0;
+#pragma unroll
+                for (int k = 0; k < EPT; ++k) s += w[k] * w[k];
+                return s;
+              }, sm.red);
+              if (tid == 0) givens_step(j, cross_warp<NT>(sm.red, 0));
+              __syncthreads();
+            }
+          }
+          brk = sm.fl[1];
+          kdone = j + 1;
+          if (!brk) {
+            const double ih = sm.sc[3];
+            double* vn = slot(j + 1);
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) {
+              const int pp = tid + k * NT;
+              vn[pp] = w[k] * ih;
+              if (capture && cycle == 0 && j + 1 <= p.cap_a && pp < N)
+                capV[(size_t)(j + 1) * p.cap_ld + pp] = w[k] * ih;
+            }
+          }
+          if (sm.fl[2]) break;
+        }
+        // y = R^{-1} g: column-oriented back substitution on warp 0 (lane l owns
+        // rows l and l+32), reciprocal pivots stored by the Givens step
+        if (warp == 0) {
+          double g0 = (lane < kdone) ? sm.g[lane] : 0.0;
+          double g1 = (lane + 32 < kdone) ? sm.g[lane + 32] : 0.0;
+          for (int i = kdone - 1; i >= 0; --i) {
+            const double gi = __shfl_sync(kFull, i < 32 ? g0 : g1, i & 31);
+            const double yi = gi * sm.rinv[i];
+            if (lane == 0) sm.y[i] = yi;
+            if (lane < i) g0 = fma(-sm.Hr[lane + i * ld], yi, g0);
+            if (lane + 32 < i) g1 = fma(-sm.Hr[(lane + 32) + i * ld], yi, g1);
           }
         }
-        brk = sm.fl[1];
-        kdone = j + 1;
-        if (!brk) {
-          const double ih = sm.sc[3];
-          double* vn = slot(j + 1);
-#pragma unroll
-          for (int k = 0; k < EPT; ++k) {
-            const int pp = tid + k * NT;
-            vn[pp] = w[k] * ih;
-            if (capture && cycle == 0 && j + 1 <= p.cap_a && pp < N)
-              capV[(size_t)(j + 1) * p.cap_ld + pp] = w[k] * ih;
+        if (tid == 0) {
+          if (capture && cycle == 0) {
+            const int a = kdone < p.cap_a ? kdone : p.cap_a;
+            const int hn = (a < kdone) || !brk;
+            if (p.factor) {
+              // fused basis store: factor H_a of the slot just written
+              SlotMeta mt;
+              const int sl = cidx;
+              double* rot = p.slotRot + (size_t)sl * 3 * p.max_a;
+              factor_hessenberg(capH, p.cap_a + 1, a, hn,
+                                p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a, rot,
+                                rot + 2 * p.max_a, &mt.lsq, &mt.nrot);
+              mt.a = a;
+              mt.has_next = hn;
+              mt.timestep = tstep;
+              mt.N = N;
+              mt.pad_[0] = mt.pad_[1] = 0;
+              p.slotMeta[sl] = mt;
+            } else {
+              p.capMeta[sysi].a = a;
+              p.capMeta[sysi].has_next = hn;
+              p.capMeta[sysi].N = N;
+              p.capMeta[sysi].valid = 1;
+            }
           }
         }
-        if (sm.fl[2]) break;
+        __syncthreads();
+        for (int i = 0; i < kdone; ++i) {
+          const double yi = sm.y[i];
+          const double* vi = slot(i);
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) sm.xs[tid + k * NT] = fma(yi, vi[tid + k * NT], sm.xs[tid + k * NT]);
+        }
+        __syncthreads();
+        residual();                              // true FP64 residual
+        block_partials<NT>(1, [&](int) {
+          double s = 0.0;
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) s += w[k] * w[k];
+          return s;
+        }, sm.red);
+        if (tid == 0) sm.sc[1] = sqrt(cross_warp<NT>(sm.red, 0));
+        __syncthreads();
+        beta = sm.sc[1];
+        ++cycle;
       }
-      // y = R^{-1} g: column-oriented back substitution on warp 0 (lane l owns
-      // rows l and l+32), reciprocal pivots stored by the Givens step
-      if (warp == 0) {
-        double g0 = (lane < kdone) ? sm.g[lane] : 0.0;
-        double g1 = (lane + 32 < kdone) ? sm.g[lane + 32] : 0.0;
-        for (int i = kdone - 1; i >= 0; --i) {
-          const double gi = __shfl_sync(kFull, i < 32 ? g0 : g1, i & 31);
-          const double yi = gi * sm.rinv[i];
-          if (lane == 0) sm.y[i] = yi;
-          if (lane < i) g0 = fma(-sm.Hr[lane + i * ld], yi, g0);
-          if (lane + 32 < i) g1 = fma(-sm.Hr[(lane + 32) + i * ld], yi, g1);
+      if (pk == 0 && capture && cycle == 0 && tid == 0) {   // converged before any step: empty basis
+        if (p.factor) {
+          SlotMeta mt;
+          mt.a = 0;
+          mt.has_next = 0;
+          mt.timestep = tstep;
+          mt.N = N;
+          mt.lsq = 0;
+          mt.nrot = 0;
+          mt.pad_[0] = mt.pad_[1] = 0;
+          p.slotMeta[cidx] = mt;
+        } else {
+          p.capMeta[sysi].a = 0;
+          p.capMeta[sysi].has_next = 0;
+          p.capMeta[sysi].N = N;
+          p.capMeta[sysi].valid = 1;
         }
       }
-      if (tid == 0) {
-        if (capture && cycle == 0) {
-          const int a = kdone < p.cap_a ? kdone : p.cap_a;
-          const int hn = (a < kdone) || !brk;
-          if (p.factor) {
-            // fused basis store: factor H_a of the slot just written
-            SlotMeta mt;
-            const int sl = cidx;
-            double* rot = p.slotRot + (size_t)sl * 3 * p.max_a;
-            factor_hessenberg(capH, p.cap_a + 1, a, hn,
-                              p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a, rot,
-                              rot + 2 * p.max_a, &mt.lsq, &mt.nrot);
-            mt.a = a;
-            mt.has_next = hn;
-            mt.timestep = tstep;
-            mt.N = N;
-            mt.pad_[0] = mt.pad_[1] = 0;
-            p.slotMeta[sl] = mt;
-          } else {
-            p.capMeta[sysi].a = a;
-            p.capMeta[sysi].has_next = hn;
-            p.capMeta[sysi].N = N;
-            p.capMeta[sysi].valid = 1;
-          }
-        }
-      }
-      __syncthreads();
-      for (int i = 0; i < kdone; ++i) {
-        const double yi = sm.y[i];
-        const double* vi = slot(i);
-#pragma unroll
-        for (int k = 0; k < EPT; ++k) sm.xs[tid + k * NT] = fma(yi, vi[tid + k * NT], sm.xs[tid + k * NT]);
-      }
-      __syncthreads();
-      residual();                              // true FP64 residual
-      block_partials<NT>(1, [&](int) {
-        double s = 0.0;
-#pragma unroll
-        for (int k = 0; k < EPT; ++k) s += w[k] * w[k];
-        return s;
-      }, sm.red);
-      if (tid == 0) sm.sc[1] = sqrt(cross_warp<NT>(sm.red, 0));
-      __syncthreads();
-      beta = sm.sc[1];
-      ++cycle;
-    }
-    if (capture && cycle == 0 && tid == 0) {   // converged before any step: empty basis
-      if (p.factor) {
-        SlotMeta mt;
-        mt.a = 0;
-        mt.has_next = 0;
-        mt.timestep = tstep;
-        mt.N = N;
-        mt.lsq = 0;
-        mt.nrot = 0;
-        mt.pad_[0] = mt.pad_[1] = 0;
-        p.slotMeta[cidx] = mt;
-      } else {
-        p.capMeta[sysi].a = 0;
-        p.capMeta[sysi].has_next = 0;
-        p.capMeta[sysi].N = N;
-        p.capMeta[sysi].valid = 1;
-      }
-    }
+    }                                          // Picard iterations
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
       const int pp = tid + k * NT;

@@ -121,6 +121,7 @@ struct GmresParams {
   int grid;                 // blocks of the launch (0 = one per system)
   size_t score_stride;      // > 0: write the score of each solved timestep to
                             // d.score + tstep * score_stride and advance d.emb
+  int picard;               // > 1: Picard iterations per system (FP64 solver)
   int pdl;                  // programmatic launch, bit 0: let the stream's next launch
                             // start at once; bit 1: launched that way, wait for the
                             // prior grid (its completion and memory) before exiting

@@ -134,6 +134,7 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset,
   g.slot_parity_stride = P->ns;
   g.acc = P->acc;
   g.err = P->err;
+  g.picard = P->opt.picard;
   if (P->K > 1) {
     // window: descriptors and slot sets chosen per timestep on the device
     g.win = P->K;
@@ -307,7 +308,7 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
   *out = nullptr;
   const kp_march_opts& o = *opt;
   if (o.T < 1 || !o.g2 || o.mode < 0 || o.mode > 3 || o.m_seed < 1 || o.m_seed > kp::kMaxM ||
-      (o.score != nullptr) != (o.embed != nullptr) ||
+      (o.score != nullptr) != (o.embed != nullptr) || o.picard < 0 ||
       o.m < 1 || o.m > kp::kMaxM || o.maxit < 0 || !(o.tol >= 0) || !(o.tol_seed >= 0))
     return kp::set_error(c, KP_ERR_ARG, "bad march options");
   kp_march_plan* P = new kp_march_plan();
@@ -352,6 +353,10 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
     return kp::set_error(c, KP_ERR_UNSUPPORTED, "grids above 4096 unknowns: one grid size per plan");
   }
   if (s != KP_OK) { kp_march_destroy(P); return s; }
+  if (o.picard > 1 && (P->mixed || P->shT.cs || P->shS.cs)) {
+    kp_march_destroy(P);
+    return kp::set_error(c, KP_ERR_UNSUPPORTED, "Picard iterations need the FP64 one-block solver");
+  }
   if (o.mode == KP_MARCH_GALERKIN && (P->mixed || P->shT.cs)) {
     kp_march_destroy(P);
     return kp::set_error(c, KP_ERR_UNSUPPORTED, "exact Galerkin projection needs the FP64 one-block solver");

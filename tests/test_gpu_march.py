@@ -216,3 +216,28 @@ def test_march_exact_galerkin_sampled(kp, orc):
     gpu_it = np.array([s.tgt_iters for s in st])
     orc_it = np.array([o.tgt_iters.sum() for o in ost])
     assert np.abs(gpu_it - orc_it).max() <= len(g.targets)
+
+
+@pytest.mark.parametrize("window", [1, 4])
+def test_march_picard_iterations_match_oracle(kp, orc, window):
+    # K = 3 Picard iterations per timestep (lagged term on the latest iterate)
+    # for seeds and targets, whole config-1 trajectory, against the oracle
+    wl = synth.config(1)
+    g = wl.groups[0]
+    ctx = kp.Context(max_seeds=2 * window * len(g.seeds) + 2, max_a=wl.a, max_n=g.N)
+    grp = _groups(wl)
+    mr = kp.March(ctx, grp, wl.T, wl.g2, mode=0, tol_seed=1e-11, tol=1e-12, m_seed=wl.m_seed,
+                  m=wl.m, window=window, picard=3)
+    st, _ = mr.run(0, wl.T, stats=True)
+    torch.cuda.synchronize()
+    oms, omt, _ = orc.march(g.H, g.W, wl.T, wl.g2, g.seeds, g.targets, g.target_seed,
+                            tol_seed=1e-11, m_seed=wl.m_seed, a=wl.a, tol_ref=1e-12, m_ref=wl.m,
+                            picard=3)
+    assert np.abs(grp[0][1].cpu().numpy() - omt).max() <= 1e-9 * np.abs(omt).max()
+    assert np.abs(grp[0][0].cpu().numpy() - oms).max() <= 1e-9 * np.abs(oms).max()
+    # the extra iterations ran (more steps than one solve per timestep) and
+    # moved the answer (the lagged term changed)
+    _, mt1, one = orc.march(g.H, g.W, wl.T, wl.g2, g.seeds, g.targets, g.target_seed,
+                            tol_seed=1e-11, m_seed=wl.m_seed, a=wl.a, tol_ref=1e-12, m_ref=wl.m)
+    assert sum(s.tgt_iters for s in st) > sum(o.tgt_iters.sum() for o in one)
+    assert np.abs(omt - mt1).max() > 1e-12 * np.abs(omt).max()
