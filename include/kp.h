@@ -369,7 +369,11 @@ kp_status kp_march_create(kp_ctx* ctx, int ngroups, const kp_group* groups,
 /* Runs timesteps n0+1 .. n0+steps (0 <= n0, n0+steps <= T) from the states in
  * the groups' buffers and leaves the result there.  stats (host, [steps]) and
  * timing may be NULL; when either is given the call waits for the GPU.  With
- * timing != NULL each kernel is bracketed by CUDA events (no graph). */
+ * timing != NULL each kernel is bracketed by CUDA events (no graph).
+ * Errors: KP_ERR_ARG for timesteps outside 1..T; KP_ERR_CUDA for a failed
+ * launch or copy; KP_ERR_TIMEOUT (reported by the first call that waits for
+ * the GPU, i.e. one with stats or timing) when a window's bounded wait for a
+ * system's previous timestep gave up -- the states are then not trustworthy. */
 kp_status kp_march_run(kp_march_plan* plan, int n0, int steps, kp_step_stats* stats,
                        kp_march_timing* timing);
 kp_status kp_march_destroy(kp_march_plan* plan);
