@@ -171,6 +171,28 @@ def oracle_sample(wl, steps, threads):
     return nsys, wall
 
 
+HBM_PEAK_GBS = _measured_peak("hbm_gbs", 6800.0)
+
+
+def method_minimum(wl, mixed, value):
+    """The HBM-bound floor of the method (about (2 s + a s / n_t) N bytes per
+    system, s = 8 for FP64, 4 for FP32 bases) against the measured copy
+    bandwidth, and how far the measured throughput is from it."""
+    s = 4 if mixed else 8
+    tot_b, tot_sys = 0.0, 0
+    for g in wl.groups:
+        nt = g.targets.shape[0]
+        nseed = max(g.seeds.shape[0], 1)
+        per_seed = nt / nseed
+        tot_b += nt * (2 * s + wl.a * s / max(per_seed, 1.0)) * g.N
+        tot_sys += nt
+    bps = tot_b / tot_sys
+    bound = HBM_PEAK_GBS * 1e9 / bps
+    return {"bytes_per_system": bps, "bound_systems_per_s": bound, "frac": value / bound,
+            "peak_gbs": HBM_PEAK_GBS, "peak_source": "measured copy bandwidth",
+            "note": "the solver is bound by its FP64 pipe (roofline above), far from this floor"}
+
+
 def oracle_error(wl, finals, steps, nsample=32):
     """Relative error ||x_gpu - x_orc|| / ||x_orc|| of the final states (after
     `steps` timesteps) of `nsample` target channels spread over the workload,
@@ -558,6 +580,10 @@ def main():
                                          "capture of the first window; the path is L2-resident",
                          "kernel": "gmres_fp64_kernel (targets: projection + refine)",
                          "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz"},
+            # HBM bytes the method cannot avoid per target system: read m^{n-1}
+            # (it is both b and m~), write m^n, plus its share of the seed basis
+            # read (a vectors over the targets of a seed); s = bytes per value
+            "method_minimum": method_minimum(wl, mixed, value),
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
             "iters_per_solve": tgt_iters / (nt_planes * NS),
