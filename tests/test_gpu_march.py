@@ -241,3 +241,23 @@ def test_march_picard_iterations_match_oracle(kp, orc, window):
                             tol_seed=1e-11, m_seed=wl.m_seed, a=wl.a, tol_ref=1e-12, m_ref=wl.m)
     assert sum(s.tgt_iters for s in st) > sum(o.tgt_iters.sum() for o in one)
     assert np.abs(omt - mt1).max() > 1e-12 * np.abs(omt).max()
+
+
+def test_march_without_seeds_windowed(kp, orc):
+    # a plan of targets only (plain GMRES from zero, no seed chains, windows
+    # of 4 timesteps and a ragged last window) against the oracle
+    g = synth.make_group(95, 20, 18, 2, 1, 6, tag=3)
+    T = 30
+    g2 = synth.beta_schedule(T)
+    ctx = kp.Context(max_seeds=1, max_a=30, max_n=g.N)
+    s = torch.zeros((0, g.N), dtype=torch.float64, device="cuda")
+    t = torch.as_tensor(g.targets.reshape(len(g.targets), -1).copy(), device="cuda")
+    mr = kp.March(ctx, [(s, t, np.zeros(len(t), np.int32), g.H, g.W)], T, g2, mode=1,
+                  tol=1e-12, m=30, window=4)
+    st, tm = mr.run(0, T, stats=True, timing=True)
+    torch.cuda.synchronize()
+    assert tm.launches == 2 * (-(-T // 4))                 # target launch + advance per window
+    _, omt, _ = orc.march(g.H, g.W, T, g2, g.seeds[:1], g.targets, np.zeros(len(t), np.int32),
+                          mode=1, tol_ref=1e-12, m_ref=30)
+    assert np.abs(t.cpu().numpy() - omt).max() <= 1e-9 * np.abs(omt).max()
+    assert all(x.seed_iters == 0 for x in st)
