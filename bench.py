@@ -83,6 +83,10 @@ def parse(argv=None):
                     help="FP64 march windows: persistent target blocks (0 = all resident slots)")
     ap.add_argument("--march-steps", type=int, default=0,
                     help="timesteps per timed march (0 = all T; fewer only for profiling runs)")
+    ap.add_argument("--autotune", dest="autotune", action="store_true", default=None,
+                    help="pick m, shared-memory window and solver shape by timing calibration "
+                         "timesteps first (default: on for the uneven-size workload, config 3)")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false")
     ap.add_argument("--schedule", choices=("beta", "paper"), default="beta",
                     help="g^2 schedule: linear beta 1e-4..0.02 (workloads, default) or the paper's "
                          "constant g = 0.5")
@@ -406,6 +410,16 @@ def main():
     nmax = max(g.N for g in wl.groups)
     mixed = wl.precision == "mixed"
     window = args.window if args.window > 0 else 16
+    tuned = None
+    if args.autotune or (args.autotune is None and args.config == 3):
+        # restart length, shared-memory window and solver shape picked by timing
+        # calibration timesteps of this march (cached per device and workload)
+        from paper_2511_17634_gb300 import autotune
+        tuned = autotune.tune(wl, mode=kp.MARCH_PROJECTED, steps=4,
+                              cache_path=os.path.join(os.path.expanduser("~"), ".cache", "kp_autotune.json"))
+        wl.m = tuned["m"]
+        args.smem_vectors = tuned["smem_vectors"]
+        args.block_threads, args.blocks_per_sm = tuned["block_threads"], tuned["blocks_per_sm"]
     ctx = kp.Context(max_seeds=max(2 * (1 if mixed else window) * wl.n_seed_planes, 1), max_a=wl.a,
                      max_n=nmax,
                      precision=kp.PREC_MIXED if mixed else kp.PREC_FP64,
@@ -568,6 +582,8 @@ def main():
                        "blocks_per_sm": args.blocks_per_sm or "auto",
                        "orthogonalisation": "CGS2" if args.reorth == 0 else "CGS+DGKS",
                        "window": 1 if mixed else window,
+                       "autotuned": None if tuned is None else {k: tuned[k] for k in (
+                           "m", "smem_vectors", "block_threads", "blocks_per_sm")},
                        "l2": "flushed between timed steps (512 MiB write)"},
             "e2e": {"value": e2e_value, "unit": "systems/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

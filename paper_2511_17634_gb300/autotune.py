@@ -90,15 +90,19 @@ def _gpu_timer(wl, mode, steps):
     nmax = max(g.N for g in wl.groups)
     prec = kp.PREC_MIXED if wl.precision == "mixed" else kp.PREC_FP64
 
+    # the march the workload will run: windows of 16 timesteps in FP64 (one
+    # per launch in mixed precision), the workload's basis length a
+    window = 1 if wl.precision == "mixed" else 16
+
     def run(m, S, shape):
-        ctx = kp.Context(max_seeds=max(2 * wl.n_seed_planes, 1), max_a=min(m, 47), max_n=nmax,
+        ctx = kp.Context(max_seeds=max(2 * window * wl.n_seed_planes, 1), max_a=wl.a, max_n=nmax,
                          precision=prec, smem_vectors=S, block_threads=shape[0],
                          blocks_per_sm=shape[1])
         ss = [x.clone() for x in seeds]
         tt = [x.clone() for x in tgts]
         groups = [(ss[k], tt[k], g.target_seed, g.H, g.W) for k, g in enumerate(wl.groups)]
         plan = kp.March(ctx, groups, wl.T, wl.g2, mode=mode, tol_seed=wl.tol_seed, tol=wl.tol,
-                        m_seed=wl.m_seed, m=m, maxit=1000)
+                        m_seed=wl.m_seed, m=m, maxit=1000, window=window)
         plan.run(0, steps)                       # warm-up (graphs, caches)
         best = float("inf")
         for _ in range(2):
