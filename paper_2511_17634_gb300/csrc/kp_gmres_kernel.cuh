@@ -1,0 +1,697 @@
+// kp_gmres_kernel.cuh -- the FP64 batched GMRES(m) kernel template and its
+// launcher, shared by kp_gmres.cu (the lean instantiations) and
+// kp_gmres_feat.cu (FEAT = true: the exact-Galerkin initial guess, Picard
+// iterations and the fused score / embedding epilogue).  The optional paths
+// are compiled only into the FEAT variant, so the default solver keeps its
+// registers for the hot loop; both variants compile in parallel.
+//
+// GB300 design notes (FP64 runs at 1/64 of the FP32 rate on this part, about
+// 2 FP64 FMA per clock per SM, so FP64 instructions -- not HBM bytes -- bound
+// this kernel):
+//  * The operator is applied matrix-free.  Each thread keeps the four
+//    off-diagonal coefficients of its EPT grid points in registers (computed
+//    once per solve from the lagged field m~), the diagonal is a scalar, and
+//    out-of-grid neighbours get a zero coefficient and a clamped index, so the
+//    stencil is 1 MUL + 4 FMA per point with no branches.
+//  * Krylov vectors v_0..v_{S-1} live in shared memory; the stencil reads its
+//    neighbours there.  Vectors beyond S go to a per-block device workspace.
+//  * Orthogonalisation is classical Gram-Schmidt applied twice (CGS2): every
+//    pass is one batched reduction of all <v_i, w> at once instead of j
+//    sequential reductions.  Reductions are warp reduce-scatter butterflies
+//    over 8 values (about one FP64 add per value per lane instead of five)
+//    followed by one cross-warp sum.
+//  * Hessenberg, Givens rotations and the least-squares solve stay in FP64 on
+//    one lane; the true residual b - A x is recomputed in FP64 at every restart.
+#pragma once
+
+#include "kp_internal.cuh"
+
+namespace kp {
+namespace {
+
+struct Smem {
+  double* V;     // [S][npad]
+  double* xs;    // [npad]
+  double* red;   // [NWARPS][kMaxV]
+  double* hb;    // [kMaxV]
+  double* Hr;    // [(m+1) * m] rotated Hessenberg, column-major, ld m+1
+  double* g;     // [m+1]
+  double* cs;    // [m]
+  double* sn;    // [m]
+  double* y;     // [m]
+  double* rinv;  // [m] reciprocal pivots of the rotated Hessenberg
+  double* sc;    // [8] scalars
+  int* fl;       // [8] flags
+};
+
+__device__ __forceinline__ Smem carve(double* base, int S, int npad, int nwarps, int m) {
+  Smem s;
+  s.V = base;
+  s.xs = s.V + (size_t)S * npad;
+  s.red = s.xs + npad;
+  s.hb = s.red + nwarps * kMaxV;
+  s.Hr = s.hb + kMaxV;
+  s.g = s.Hr + (m + 1) * m;
+  s.cs = s.g + (m + 1);
+  s.sn = s.cs + m;
+  s.y = s.sn + m;
+  s.rinv = s.y + m;
+  s.sc = s.rinv + m;
+  s.fl = reinterpret_cast<int*>(s.sc + 8);
+  return s;
+}
+
+template <int EPT, int NT, int MINB, bool FEAT>
+__global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams p) {
+  constexpr int NWARPS = NT / 32;
+  extern __shared__ __align__(16) double smem_raw[];
+  const int npad = EPT * NT;
+  const int m = p.m;
+  const int ld = m + 1;
+  Smem sm = carve(smem_raw, p.S, npad, NWARPS, m);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  double* spill = p.spill ? p.spill + (size_t)blockIdx.x * (m + 1 - p.S) * npad : nullptr;
+  auto slot = [&](int i) -> double* {
+    return i < p.S ? sm.V + (size_t)i * npad : spill + (size_t)(i - p.S) * npad;
+  };
+  if (p.pdl & 1) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  // timesteps of this launch (time march): t0 .. t0 + nstep - 1
+  int t0 = 0, nstep = 1;
+  if (p.step) {
+    t0 = *p.step + p.step_offset;
+    nstep = min(p.win > 0 ? p.win : 1, *p.step_end - t0);
+    if (nstep <= 0) {                        // pipelined seed step past the run: nothing to do
+      if (p.pdl & 2) asm volatile("griddepcontrol.wait;" ::: "memory");
+      return;
+    }
+  }
+  const double bsc = p.b_scale;
+  const int nitems = p.nsys * nstep;
+  int sysi = blockIdx.x, kstep = 0;          // static schedule: a block marches its systems
+  for (;;) {
+    if (p.queue) {
+      // dynamic schedule over (timestep, system) items, timestep-major: a
+      // block that finishes early takes the next item instead of idling
+      // until the slowest system of its wave is done
+      if (tid == 0) sm.fl[6] = atomicAdd(p.queue, 1);
+      __syncthreads();
+      const int item = sm.fl[6];
+      if (item >= nitems) break;
+      kstep = item / p.nsys;
+      sysi = item - kstep * p.nsys;
+    } else if (sysi >= p.nsys) {
+      break;
+    }
+    const int tstep = t0 + kstep;
+    if (p.done) {
+      // m^{n-1} of this system comes from its previous item, claimed earlier
+      // by a block that is therefore running: wait for its release
+      const int need = tstep - *p.run_start;
+      if (tid == 0) {
+        int it = 0;
+        while (ld_acquire_gpu(p.done + sysi) < need) {
+          if (++it > kWaitLimit) { atomicOr(p.err, 2); break; }
+          __nanosleep(256);
+        }
+      }
+      __syncthreads();
+      (void)ld_acquire_gpu(p.done + sysi);    // orders this thread's loads of m^{n-1}
+    }
+    const int parity_base = slot_set_base(p, tstep);
+    const SysDesc d = p.sys_par[0] ? p.sys_par[(tstep + p.sys_shift) & 1][sysi] : p.sys[sysi];
+    const int H = d.H, W = d.W, N = H * W;
+    const double hh = d.h;
+    const double g2 = p.step ? p.g2_sched[tstep] : d.g2;
+    const double cc = g2 / (2.0 * hh * hh);
+    const double ee = g2 / (8.0 * hh * hh);
+    const double cd = 1.0 / d.dt + 2.0 * g2 / (hh * hh);
+    const double i2h = 1.0 / (2.0 * hh);
+    bool capture = p.capV != nullptr;          // first solve of the timestep only
+    const int cidx = p.factor ? parity_base + sysi : sysi;   // capture record (or seed slot)
+    double* capV = capture ? p.capV + (size_t)cidx * (p.cap_a + 1) * p.cap_ld : nullptr;
+    double* capH = capture ? p.capH + (size_t)cidx * (p.cap_a + 1) * p.cap_a : nullptr;
+
+    // stencil coefficients (Sec. 2.3, listing after Eq. 11) from the lagged
+    // field m~ (m^{n-1}, or the latest Picard iterate); zero where the
+    // neighbour lies outside the grid
+    double cE[EPT], cW[EPT], cN[EPT], cS[EPT];
+    auto set_coeffs = [&](const double* mtl) {
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int pp = tid + k * NT;
+        cE[k] = cW[k] = cN[k] = cS[k] = 0.0;
+        if (pp < N) {
+          const int i = pp / H, j = pp - i * H;
+          const double mE = (i + 1 < W) ? mtl[pp + H] : 0.0;
+          const double mW = (i > 0) ? mtl[pp - H] : 0.0;
+          const double mN = (j + 1 < H) ? mtl[pp + 1] : 0.0;
+          const double mS = (j > 0) ? mtl[pp - 1] : 0.0;
+          const double fxp = d.fx ? d.fx[pp] : 0.0;
+          const double fyp = d.fy ? d.fy[pp] : 0.0;
+          const double dmx = mE - mW, dmy = mN - mS;
+          if (i + 1 < W) cE[k] = -cc + fxp * i2h - ee * dmx;
+          if (i > 0) cW[k] = -cc - fxp * i2h + ee * dmx;
+          if (j + 1 < H) cN[k] = -cc + fyp * i2h - ee * dmy;
+          if (j > 0) cS[k] = -cc - fyp * i2h + ee * dmy;
+        }
+      }
+    };
+    set_coeffs(d.mt);
+    // r = b - A v, the product chain started from b (one multiply, five fused
+    // multiply-adds per point)
+    auto residual_of = [&](const double* v, double (&out)[EPT]) {
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int pp = tid + k * NT;
+        if (pp < N) {
+          const int pe = min(pp + H, N - 1), pw = max(pp - H, 0);
+          const int pn = min(pp + 1, N - 1), ps = max(pp - 1, 0);
+          double t = fma(-cd, v[pp], d.b[pp] * bsc);
+          t = fma(-cE[k], v[pe], t);
+          t = fma(-cW[k], v[pw], t);
+          t = fma(-cN[k], v[pn], t);
+          out[k] = fma(-cS[k], v[ps], t);
+        } else {
+          out[k] = 0.0;
+        }
+      }
+    };
+    // Arnoldi runs on the shifted operator A - cd I (the constant diagonal
+    // removed): the same Krylov space, with H_A = H + cd I restored in the
+    // Hessenberg column.  A ~ (1/dt) I + small, so A v_j is nearly parallel to
+    // v_j and the unshifted Gram-Schmidt would cancel most of it.
+    auto apply_off = [&](const double* v, double (&out)[EPT]) {
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int pp = tid + k * NT;
+        if (pp < N) {
+          const int pe = min(pp + H, N - 1), pw = max(pp - H, 0);
+          const int pn = min(pp + 1, N - 1), ps = max(pp - 1, 0);
+          out[k] = cE[k] * v[pe] + cW[k] * v[pw] + cN[k] * v[pn] + cS[k] * v[ps];
+        } else {
+          out[k] = 0.0;
+        }
+      }
+    };
+    auto bval = [&](int pp) { return (pp < N) ? d.b[pp] * bsc : 0.0; };
+
+    // initial guess -> shared memory
+    unsigned long long proj_flops = 0;
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int pp = tid + k * NT;
+      double x0 = 0.0;
+      if (pp < N) {
+        if (p.x0_mode == X0_READ) x0 = d.x[pp];
+        else if (p.x0_mode == X0_WARM) x0 = d.mt[pp];
+      }
+      sm.xs[pp] = x0;
+    }
+    if (p.x0_mode == X0_PROJECT) {
+      // Sec. 3, Phase 2: x0 = V_a H_a^{-1} V_a^T b with the seed's stored basis
+      const int sl = d.slot + parity_base;
+      const SlotMeta mt = p.slotMeta[sl];
+      if (mt.timestep == tstep && mt.N == N && mt.a > 0) {            // uniform per block
+        const int a = mt.a;
+        const int nv = mt.lsq ? a + 1 : a;
+        const double* V = p.slotV + (size_t)sl * (p.max_a + 1) * p.slot_ld;
+        double bv[EPT];
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) bv[k] = bval(tid + k * NT);
+        block_partials<NT>(nv, [&](int i) {
+          const double* vi = V + (size_t)i * p.slot_ld;
+          double s = 0.0;
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) {
+            const int pp = tid + k * NT;
+            if (pp < N) s += vi[pp] * bv[k];
+          }
+          return s;
+        }, sm.red);
+        if (warp == 0) {
+          for (int i = lane; i < nv; i += 32) sm.hb[i] = cross_warp<NT>(sm.red, i);
+          __syncwarp();
+          const double* rot = p.slotRot + (size_t)sl * 3 * p.max_a;
+          solve_projected_warp(sm.hb, a, mt.nrot, p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a,
+                               p.max_a + 1, rot, rot + 2 * p.max_a, lane);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          const int pp = tid + k * NT;
+          if (pp < N) {
+            double xv = 0.0;
+            for (int i = 0; i < a; ++i) xv = fma(sm.hb[i], V[(size_t)i * p.slot_ld + pp], xv);
+            sm.xs[pp] = xv;
+          }
+        }
+        proj_flops = (unsigned long long)(2 * nv + 2 * a) * (unsigned long long)N;
+      }
+    }
+    if (FEAT && p.x0_mode == X0_GALERKIN) {
+      // Sec. 3, Phase 2 without the seed-matrix shortcut: G = V_a^T A_i V_a
+      // with this target's own operator, G alpha = V_a^T b, x0 = V_a alpha
+      const int sl = d.slot + parity_base;
+      const SlotMeta mt = p.slotMeta[sl];
+      const int a = mt.a;
+      if (mt.timestep == tstep && mt.N == N && a > 0 && a * a <= (m + 1) * m) {
+        const double* V = p.slotV + (size_t)sl * (p.max_a + 1) * p.slot_ld;
+        double* G = sm.Hr;                       // a x a, column-major
+        for (int k = 0; k < a; ++k) {
+          const double* vk = V + (size_t)k * p.slot_ld;
+          double av[EPT];
+#pragma unroll
+          for (int e = 0; e < EPT; ++e) {
+            const int pp = tid + e * NT;
+            av[e] = 0.0;
+            if (pp < N) {
+              const int pe = min(pp + H, N - 1), pw = max(pp - H, 0);
+              const int pn = min(pp + 1, N - 1), ps = max(pp - 1, 0);
+              double t = cd * vk[pp];
+              t = fma(cE[e], vk[pe], t);
+              t = fma(cW[e], vk[pw], t);
+              t = fma(cN[e], vk[pn], t);
+              av[e] = fma(cS[e], vk[ps], t);
+            }
+          }
+          block_partials<NT>(a, [&](int l) {
+            const double* vl = V + (size_t)l * p.slot_ld;
+            double s = 0.0;
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+              const int pp = tid + e * NT;
+              if (pp < N) s = fma(vl[pp], av[e], s);
+            }
+            return s;
+          }, sm.red);
+          if (warp == 0)
+            for (int l = lane; l < a; l += 32) G[l + k * a] = cross_warp<NT>(sm.red, l);
+          __syncthreads();                       // partials of the next column reuse red
+        }
+        double bv[EPT];
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) bv[e] = bval(tid + e * NT);
+        block_partials<NT>(a, [&](int l) {
+          const double* vl = V + (size_t)l * p.slot_ld;
+          double s = 0.0;
+#pragma unroll
+          for (int e = 0; e < EPT; ++e) {
+            const int pp = tid + e * NT;
+            if (pp < N) s = fma(vl[pp], bv[e], s);
+          }
+          return s;
+        }, sm.red);
+        if (warp == 0) {
+          for (int l = lane; l < a; l += 32) sm.hb[l] = cross_warp<NT>(sm.red, l);
+          __syncwarp();
+          const bool ok = lu_solve_warp(G, a, sm.hb, lane);
+          if (lane == 0) sm.fl[5] = ok;
+        }
+        __syncthreads();
+        if (sm.fl[5]) {
+#pragma unroll
+          for (int e = 0; e < EPT; ++e) {
+            const int pp = tid + e * NT;
+            if (pp < N) {
+              double xv = 0.0;
+              for (int i = 0; i < a; ++i) xv = fma(sm.hb[i], V[(size_t)i * p.slot_ld + pp], xv);
+              sm.xs[pp] = xv;
+            }
+          }
+        }
+        proj_flops = (unsigned long long)(a * (9 + 2 * a) + 4 * a) * (unsigned long long)N;
+      }
+    }
+    __syncthreads();
+    double w[EPT];
+    auto residual = [&]() { residual_of(sm.xs, w); };
+    int steps = 0, status = KP_NOT_CONVERGED, cycle = 0;
+    double bnorm = 0.0, beta = 0.0;
+    const int npic = (FEAT && p.picard > 1) ? p.picard : 1;
+    for (int pk = 0; pk < npic; ++pk) {
+      if (FEAT && pk > 0) {
+        // Picard iteration k = pk + 1 (Sec. 2.3): the nonlinear term lagged on
+        // the latest iterate m^{n,(k-1)} (in shared memory), the same right-hand
+        // side, GMRES warm-started from that iterate
+        __syncthreads();
+        set_coeffs(sm.xs);
+        status = KP_NOT_CONVERGED;
+        capture = false;                         // the stored basis is the first solve's
+      }
+      if (pk == 0 && p.x0_mode == X0_ZERO) {     // r = b, no operator application needed
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) w[k] = bval(tid + k * NT);
+      } else {
+        residual();
+      }
+      block_partials<NT>(2, [&](int i) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          const double bv = bval(tid + k * NT);
+          s += (i == 0) ? bv * bv : w[k] * w[k];
+        }
+        return s;
+      }, sm.red);
+      if (tid == 0) {
+        sm.sc[0] = sqrt(cross_warp<NT>(sm.red, 0));
+        sm.sc[1] = sqrt(cross_warp<NT>(sm.red, 1));
+      }
+      __syncthreads();
+      bnorm = sm.sc[0];
+      beta = sm.sc[1];
+
+      if (bnorm == 0.0) {
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) sm.xs[tid + k * NT] = 0.0;
+        beta = 0.0;
+        status = KP_OK;
+      }
+      while (status == KP_NOT_CONVERGED) {
+        if (beta <= p.tol * bnorm) { status = KP_OK; break; }
+        if (!isfinite(beta)) { status = KP_BREAKDOWN; break; }
+        if (steps >= p.maxit) break;
+        {
+          const double ib = 1.0 / beta;
+          double* v0 = slot(0);
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) {
+            const int pp = tid + k * NT;
+            v0[pp] = w[k] * ib;
+            if (capture && cycle == 0 && pp < N) capV[pp] = w[k] * ib;
+          }
+          if (tid == 0) sm.g[0] = beta;
+        }
+        int kdone = 0;
+        int brk = 0;
+        // Givens update of Hessenberg column j once h_{j+1,j}^2 = hn2 is known
+        // (one lane): rotations, residual estimate, convergence flags.
+        auto givens_step = [&](int j, double hn2) {
+          const double ihn = hn2 > 0.0 ? rsqrt(hn2) : 0.0;
+          const double hn = hn2 * ihn;
+          const int b = !(hn > 1e-14 * sqrt(sm.sc[2]));
+          sm.Hr[j + j * ld] += cd;                 // H_A = H_{A - cd I} + cd I
+          sm.Hr[(j + 1) + j * ld] = hn;
+          if (capture && cycle == 0 && j < p.cap_a) {
+            for (int i = 0; i <= j + 1; ++i) capH[i + j * (p.cap_a + 1)] = sm.Hr[i + j * ld];
+          }
+          for (int i = 0; i < j; ++i) {
+            const double t1 = sm.Hr[i + j * ld], t2 = sm.Hr[(i + 1) + j * ld];
+            sm.Hr[i + j * ld] = sm.cs[i] * t1 + sm.sn[i] * t2;
+            sm.Hr[(i + 1) + j * ld] = -sm.sn[i] * t1 + sm.cs[i] * t2;
+          }
+          const double a0 = sm.Hr[j + j * ld];
+          const double rr = a0 * a0 + hn2;
+          const double ir = rsqrt(rr);
+          const double c = a0 * ir, s = hn * ir;
+          sm.cs[j] = c;
+          sm.sn[j] = s;
+          sm.Hr[j + j * ld] = rr * ir;
+          sm.rinv[j] = ir;
+          sm.Hr[(j + 1) + j * ld] = 0.0;
+          sm.g[j + 1] = -s * sm.g[j];
+          sm.g[j] = c * sm.g[j];
+          const double res = fabs(sm.g[j + 1]);
+          sm.sc[3] = ihn;
+          sm.fl[1] = b;
+          sm.fl[2] = (res <= p.tol * bnorm) || b || (steps >= p.maxit) || (j + 1 == m);
+        };
+        for (int j = 0; j < m; ++j) {
+          __syncthreads();                       // v_j complete
+          apply_off(slot(j), w);
+          ++steps;
+          const int nh = j + 1;
+          auto dots = [&](int i) {
+            double s = 0.0;
+            if (i < nh) {
+              const double* vi = slot(i);
+#pragma unroll
+              for (int k = 0; k < EPT; ++k) s += vi[tid + k * NT] * w[k];
+            } else {
+#pragma unroll
+              for (int k = 0; k < EPT; ++k) s += w[k] * w[k];
+            }
+            return s;
+          };
+          // CGS pass 1: h_i = <v_i, w> and ||w||^2 in one batched reduction
+          block_partials<NT>(nh + 1, dots, sm.red);
+          if (warp == 0) {
+            double sq = 0.0;
+            for (int i = lane; i <= nh; i += 32) {
+              const double s = cross_warp<NT>(sm.red, i);
+              sm.hb[i] = s;
+              if (i < nh) { sm.Hr[i + j * ld] = s; sq += s * s; }
+            }
+            sq = warp_sum(sq);
+            if (lane == 0) {
+              const double ww0 = sm.hb[nh];
+              sm.sc[2] = ww0;
+              // second pass always (CGS2), or only when the first removed over
+              // half of ||w||^2 (DGKS); without it ||w_1||^2 = ||w||^2 - ||h||^2
+              const int pass2 = (p.reorth == 0) || (ww0 - sq < 0.5 * ww0);
+              sm.fl[0] = pass2;
+              if (!pass2) givens_step(j, ww0 - sq);
+            }
+          }
+          __syncthreads();
+          for (int i = 0; i < nh; ++i) {
+            const double hi = sm.hb[i];
+            const double* vi = slot(i);
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) w[k] = fma(-hi, vi[tid + k * NT], w[k]);
+          }
+          if (sm.fl[0]) {
+            // CGS pass 2 (reorthogonalisation) with ||w_1||^2 in the same reduction;
+            // ||w_2||^2 = ||w_1||^2 - ||h_2||^2 (h_2 = O(eps) after pass 1), checked
+            block_partials<NT>(nh + 1, dots, sm.red);
+            if (warp == 0) {
+              double sq = 0.0;
+              for (int i = lane; i <= nh; i += 32) {
+                const double s = cross_warp<NT>(sm.red, i);
+                sm.hb[i] = s;
+                if (i < nh) { sm.Hr[i + j * ld] += s; sq += s * s; }
+              }
+              sq = warp_sum(sq);
+              if (lane == 0) {
+                const double ww1 = sm.hb[nh];
+                const int exact = sq > 0.25 * ww1;     // large correction: recompute the norm
+                sm.fl[3] = exact;
+                if (!exact) givens_step(j, ww1 - sq);
+              }
+            }
+            __syncthreads();
+            for (int i = 0; i < nh; ++i) {
+              const double hi = sm.hb[i];
+              const double* vi = slot(i);
+#pragma unroll
+              for (int k = 0; k < EPT; ++k) w[k] = fma(-hi, vi[tid + k * NT], w[k]);
+            }
+            if (sm.fl[3]) {
+              block_partials<NT>(1, [&](int) {
+                double s = 0.0;
+#pragma unroll
+                for (int k = 0; k < EPT; ++k) s += w[k] * w[k];
+                return s;
+              }, sm.red);
+              if (tid == 0) givens_step(j, cross_warp<NT>(sm.red, 0));
+              __syncthreads();
+            }
+          }
+          brk = sm.fl[1];
+          kdone = j + 1;
+          if (!brk) {
+            const double ih = sm.sc[3];
+            double* vn = slot(j + 1);
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) {
+              const int pp = tid + k * NT;
+              vn[pp] = w[k] * ih;
+              if (capture && cycle == 0 && j + 1 <= p.cap_a && pp < N)
+                capV[(size_t)(j + 1) * p.cap_ld + pp] = w[k] * ih;
+            }
+          }
+          if (sm.fl[2]) break;
+        }
+        // y = R^{-1} g: column-oriented back substitution on warp 0 (lane l owns
+        // rows l and l+32), reciprocal pivots stored by the Givens step
+        if (warp == 0) {
+          double g0 = (lane < kdone) ? sm.g[lane] : 0.0;
+          double g1 = (lane + 32 < kdone) ? sm.g[lane + 32] : 0.0;
+          for (int i = kdone - 1; i >= 0; --i) {
+            const double gi = __shfl_sync(kFull, i < 32 ? g0 : g1, i & 31);
+            const double yi = gi * sm.rinv[i];
+            if (lane == 0) sm.y[i] = yi;
+            if (lane < i) g0 = fma(-sm.Hr[lane + i * ld], yi, g0);
+            if (lane + 32 < i) g1 = fma(-sm.Hr[(lane + 32) + i * ld], yi, g1);
+          }
+        }
+        if (tid == 0) {
+          if (capture && cycle == 0) {
+            const int a = kdone < p.cap_a ? kdone : p.cap_a;
+            const int hn = (a < kdone) || !brk;
+            if (p.factor) {
+              // fused basis store: factor H_a of the slot just written
+              SlotMeta mt;
+              const int sl = cidx;
+              double* rot = p.slotRot + (size_t)sl * 3 * p.max_a;
+              factor_hessenberg(capH, p.cap_a + 1, a, hn,
+                                p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a, rot,
+                                rot + 2 * p.max_a, &mt.lsq, &mt.nrot);
+              mt.a = a;
+              mt.has_next = hn;
+              mt.timestep = tstep;
+              mt.N = N;
+              mt.pad_[0] = mt.pad_[1] = 0;
+              p.slotMeta[sl] = mt;
+            } else {
+              p.capMeta[sysi].a = a;
+              p.capMeta[sysi].has_next = hn;
+              p.capMeta[sysi].N = N;
+              p.capMeta[sysi].valid = 1;
+            }
+          }
+        }
+        __syncthreads();
+        for (int i = 0; i < kdone; ++i) {
+          const double yi = sm.y[i];
+          const double* vi = slot(i);
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) sm.xs[tid + k * NT] = fma(yi, vi[tid + k * NT], sm.xs[tid + k * NT]);
+        }
+        __syncthreads();
+        residual();                              // true FP64 residual
+        block_partials<NT>(1, [&](int) {
+          double s = 0.0;
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) s += w[k] * w[k];
+          return s;
+        }, sm.red);
+        if (tid == 0) sm.sc[1] = sqrt(cross_warp<NT>(sm.red, 0));
+        __syncthreads();
+        beta = sm.sc[1];
+        ++cycle;
+      }
+      if (pk == 0 && capture && cycle == 0 && tid == 0) {   // converged before any step: empty basis
+        if (p.factor) {
+          SlotMeta mt;
+          mt.a = 0;
+          mt.has_next = 0;
+          mt.timestep = tstep;
+          mt.N = N;
+          mt.lsq = 0;
+          mt.nrot = 0;
+          mt.pad_[0] = mt.pad_[1] = 0;
+          p.slotMeta[cidx] = mt;
+        } else {
+          p.capMeta[sysi].a = 0;
+          p.capMeta[sysi].has_next = 0;
+          p.capMeta[sysi].N = N;
+          p.capMeta[sysi].valid = 1;
+        }
+      }
+    }                                          // Picard iterations
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int pp = tid + k * NT;
+      if (pp < N) d.x[pp] = sm.xs[pp];
+    }
+    if (FEAT && p.score_stride && d.score) {
+      // score of m^n by central differences (end of Sec. 2.3, divided by 2h,
+      // zero outside the grid) and one probability-flow step of the embedding
+      // (Sec. 4.1, f = 0): x^n = x^{n-1} - dt (g^{n-1})^2 / 2 grad m^{n-1},
+      // with m^{n-1} this item's input and (g^0)^2 taken as (g^1)^2
+      const double i2h = 0.5 / hh;
+      const double g2prev = p.step ? p.g2_sched[tstep > 0 ? tstep - 1 : 0] : d.g2;
+      const double ce = -0.5 * d.dt * g2prev;
+      double* sc = d.score + (size_t)tstep * p.score_stride;
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int pp = tid + k * NT;
+        if (pp < N) {
+          const int i = pp / H, j = pp - i * H;
+          const double xe = i + 1 < W ? sm.xs[pp + H] : 0.0, xw = i > 0 ? sm.xs[pp - H] : 0.0;
+          const double xn = j + 1 < H ? sm.xs[pp + 1] : 0.0, xs_ = j > 0 ? sm.xs[pp - 1] : 0.0;
+          sc[pp] = (xe - xw) * i2h;
+          sc[N + pp] = (xn - xs_) * i2h;
+          const double me = i + 1 < W ? d.mt[pp + H] : 0.0, mw = i > 0 ? d.mt[pp - H] : 0.0;
+          const double mn = j + 1 < H ? d.mt[pp + 1] : 0.0, ms = j > 0 ? d.mt[pp - 1] : 0.0;
+          d.emb[pp] = fma(ce, (me - mw) * i2h, d.emb[pp]);
+          d.emb[N + pp] = fma(ce, (mn - ms) * i2h, d.emb[N + pp]);
+        }
+      }
+    }
+    if (tid == 0) {
+      const double rel = bnorm > 0.0 ? beta / bnorm : 0.0;
+      if (p.info) {
+        kp_info inf;
+        inf.iters = steps;
+        inf.status = status;
+        inf.rel_res = rel;
+        p.info[sysi] = inf;
+      }
+      if (p.acc) {
+        StepAcc* a = p.acc + tstep;
+        const unsigned long long fl = gmres_flops(steps, m) * (unsigned long long)N;
+        if (p.acc_kind == 0) {
+          atomicAdd(&a->seed_iters, (unsigned long long)steps);
+          atomicAdd(&a->seed_flops, fl);
+        } else {
+          atomicAdd(&a->tgt_iters, (unsigned long long)steps);
+          atomicAdd(&a->tgt_flops, fl);
+          atomicMax(&a->tgt_max_iters, (unsigned int)steps);
+          atomicMax(&a->max_res_bits, (unsigned long long)__double_as_longlong(rel));
+          if (proj_flops) atomicAdd(&a->proj_flops, proj_flops);
+        }
+        if (status != KP_OK) atomicAdd(&a->not_converged, 1u);
+      }
+    }
+    if (p.done) {                              // release m^n of this system
+      __threadfence();
+      __syncthreads();
+      if (tid == 0) st_release_gpu(p.done + sysi, tstep + 1 - *p.run_start);
+    }
+    __syncthreads();                           // shared memory reused by the next item
+    if (!p.queue && ++kstep == nstep) { kstep = 0; sysi += gridDim.x; }
+  }
+  if (p.pdl & 2) asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+// Raise the kernel's dynamic shared-memory limit to the device maximum, so
+// that launches with different windows (seeds, targets) never lower it.
+template <typename K>
+static cudaError_t allow_max_smem(K k, size_t smem) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if (smem > (size_t)optin) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+}
+
+template <int EPT, int NT, int MINB, bool FEAT>
+static cudaError_t launch_one(const GmresParams& p, size_t smem, cudaStream_t st) {
+  auto k = gmres_fp64_kernel<EPT, NT, MINB, FEAT>;
+  cudaError_t e = allow_max_smem(k, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = p.grid > 0 ? p.grid : p.nsys;
+  if (p.pdl & 2) {
+    // programmatic dependent launch: the blocks may start while the previous
+    // kernel of the stream still runs (it signals at entry)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, p);
+  }
+  k<<<grid, NT, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+}  // namespace kp

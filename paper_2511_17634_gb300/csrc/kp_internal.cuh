@@ -507,6 +507,9 @@ struct ProjTile {
 // Launchers (defined in the .cu files; return a cudaError_t of the launch).
 cudaError_t launch_gmres_fp64(const GmresParams& p, int ept, int nt, int minb, size_t smem,
                               cudaStream_t st);
+// The same with the optional paths compiled in (exact Galerkin, Picard, score).
+cudaError_t launch_gmres_fp64_feat(const GmresParams& p, int ept, int nt, int minb, size_t smem,
+                                   cudaStream_t st);
 size_t gmres_fp64_smem_bytes(int ept, int nt, int S, int m);
 size_t gmres_mixed_smem_bytes(int ept, int nt, int S, int m);
 cudaError_t launch_gmres_mixed(const GmresParams& p, int ept, int nt, size_t smem,
