@@ -24,6 +24,9 @@
  *     basis; this oracle uses restarted GMRES(m) with modified Gram-Schmidt
  *     Arnoldi (reorthogonalised) and Givens rotations (Saad, Iterative Methods, 2003, Alg. 6.9)
  *     and keeps the first cycle's Arnoldi vectors and Hessenberg matrix.
+ *     orc_bicgstab is the paper's BiCGSTAB as an alternative: its key
+ *     vectors, orthonormalised, form V_a, and A_proj = V_a^T A_seed V_a is
+ *     then formed explicitly (orc_project_dense).
  *   - Sec. 3, Phase 2: A_proj = V^T A_seed V (equal to H_a from Arnoldi),
  *     b_proj = V^T b_i, solve A_proj alpha = b_proj, x0 = V alpha, then an
  *     iterative solve of A_i x = b_i from x0 (GMRES(m) again).
@@ -45,6 +48,8 @@
 #define ORC_OK 0
 #define ORC_NOT_CONVERGED 1
 #define ORC_ERR_ARG -1
+
+int orc_dense_lu_solve(int n, double* A, double* b, double* x);
 
 /* Value of a grid field at (i, j), zero outside the grid (zero padding). */
 static double at(const double* f, int H, int W, int i, int j) {
@@ -298,6 +303,133 @@ done:
 }
 
 /*
+ * Sec. 3, Phase 1 as the paper states it: BiCGSTAB (van der Vorst 1992) on
+ * A x = b, A given by stencil coefficients C.  Each iteration k forms the
+ * search direction p_k, v = A p_k, the intermediate residual s_k = r_{k-1} -
+ * alpha v, t = A s_k, the smoothing step omega = <t,s>/<t,t> and the residual
+ * r_k = s_k - omega t; x gains alpha p_k + omega s_k.  Stops when the updated
+ * residual satisfies ||r|| <= tol ||b|| (or ||s|| does, after the half step),
+ * then checks the true residual b - A x and, if it is still above tol ||b||,
+ * restarts from it (shadow residual reset to that residual).  A zero rho or
+ * omega also ends the sweep and restarts.  At most maxit iterations.
+ *
+ * Basis (the paper keeps the key vectors of the iteration): during the first
+ * sweep, r_0 and then s_k, r_k of every iteration, in that order, all lying in
+ * the Krylov space of A and r_0 (the j-th kept vector in K_{j+1}).  Each is
+ * orthogonalised against the vectors kept so far by modified Gram-Schmidt
+ * run twice and kept, normalised, if what remains is above 1e-10 of its
+ * norm, until cap_a vectors are kept.  capV: column-major N x cap_a;
+ * *cap_used = vectors kept.
+ *
+ *  x        in: initial guess, out: final iterate.
+ *  iters    out: BiCGSTAB iterations (two operator applications each).
+ *  rel_res  out: ||b - A x|| / ||b|| of the returned x.
+ * Returns ORC_OK or ORC_NOT_CONVERGED.
+ */
+static void keep_vector(int N, const double* u, int cap_a, double* capV, int* used, double* w) {
+  if (!capV || *used >= cap_a) return;
+  double n0 = nrm2(N, u);
+  if (!(n0 > 0.0)) return;
+  memcpy(w, u, sizeof(double) * N);
+  for (int sweep = 0; sweep < 2; ++sweep)
+    for (int i = 0; i < *used; ++i) {
+      const double* vi = capV + (size_t)i * N;
+      double h = dot(N, w, vi);
+      for (int k = 0; k < N; ++k) w[k] -= h * vi[k];
+    }
+  double n1 = nrm2(N, w);
+  if (!(n1 > 1e-10 * n0)) return;
+  double* vn = capV + (size_t)(*used) * N;
+  for (int k = 0; k < N; ++k) vn[k] = w[k] / n1;
+  ++*used;
+}
+
+int orc_bicgstab(int H, int W, const double* C, const double* b, double* x, double tol,
+                 int maxit, int* iters, double* rel_res, int cap_a, double* capV, int* cap_used) {
+  int N = H * W;
+  double* r = (double*)calloc((size_t)N, sizeof(double));
+  double* rh = (double*)calloc((size_t)N, sizeof(double));
+  double* p = (double*)calloc((size_t)N, sizeof(double));
+  double* v = (double*)calloc((size_t)N, sizeof(double));
+  double* sv = (double*)calloc((size_t)N, sizeof(double));
+  double* t = (double*)calloc((size_t)N, sizeof(double));
+  double* w = (double*)calloc((size_t)N, sizeof(double));
+  int status = ORC_NOT_CONVERGED, it = 0, sweep = 0;
+  int used = 0;
+  double bnorm = nrm2(N, b), rn = 0.0;
+  if (bnorm == 0.0) {
+    for (int k = 0; k < N; ++k) x[k] = 0.0;
+    status = ORC_OK;
+  }
+  while (status != ORC_OK) {
+    orc_apply(H, W, C, x, r);                          /* true residual */
+    for (int k = 0; k < N; ++k) r[k] = b[k] - r[k];
+    rn = nrm2(N, r);
+    if (rn <= tol * bnorm) { status = ORC_OK; break; }
+    if (it >= maxit) break;
+    int keep = (sweep == 0);
+    if (keep) keep_vector(N, r, cap_a, capV, &used, w);
+    memcpy(rh, r, sizeof(double) * N);
+    memset(p, 0, sizeof(double) * N);
+    memset(v, 0, sizeof(double) * N);
+    double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+    while (it < maxit) {
+      double rho = dot(N, rh, r);
+      if (rho == 0.0) break;
+      double beta = (rho / rho_old) * (alpha / omega);
+      for (int k = 0; k < N; ++k) p[k] = r[k] + beta * (p[k] - omega * v[k]);
+      orc_apply(H, W, C, p, v);
+      alpha = rho / dot(N, rh, v);
+      for (int k = 0; k < N; ++k) sv[k] = r[k] - alpha * v[k];
+      ++it;
+      if (keep) keep_vector(N, sv, cap_a, capV, &used, w);
+      if (nrm2(N, sv) <= tol * bnorm) {
+        for (int k = 0; k < N; ++k) x[k] += alpha * p[k];
+        break;
+      }
+      orc_apply(H, W, C, sv, t);
+      double tt = dot(N, t, t);
+      omega = tt > 0.0 ? dot(N, t, sv) / tt : 0.0;
+      for (int k = 0; k < N; ++k) x[k] += alpha * p[k] + omega * sv[k];
+      for (int k = 0; k < N; ++k) r[k] = sv[k] - omega * t[k];
+      if (keep) keep_vector(N, r, cap_a, capV, &used, w);
+      if (nrm2(N, r) <= tol * bnorm || omega == 0.0) break;
+      rho_old = rho;
+    }
+    ++sweep;
+  }
+  *iters = it;
+  *rel_res = bnorm > 0.0 ? rn / bnorm : 0.0;
+  if (cap_used) *cap_used = used;
+  free(r); free(rh); free(p); free(v); free(sv); free(t); free(w);
+  return status;
+}
+
+/*
+ * Phase 2 of Sec. 3 for a seed basis without a Hessenberg relation (the
+ * BiCGSTAB basis): A_proj = V_a^T A_seed V_a is formed explicitly (Aproj,
+ * row-major a x a, as the caller built it from the seed's operator),
+ *   c = V_a^T r,  A_proj alpha = c (dense LU, partial pivoting),  x0 = xinit + V_a alpha.
+ * V: column-major N x a.  Returns 0, or 1 if A_proj is singular (x0 = xinit).
+ */
+int orc_project_dense(int N, int a, const double* V, const double* Aproj, const double* r,
+                      const double* xinit, double* x0) {
+  for (int k = 0; k < N; ++k) x0[k] = xinit ? xinit[k] : 0.0;
+  if (a <= 0) return 0;
+  double* A = (double*)malloc(sizeof(double) * a * a);
+  double* c = (double*)malloc(sizeof(double) * a);
+  double* alpha = (double*)malloc(sizeof(double) * a);
+  memcpy(A, Aproj, sizeof(double) * a * a);
+  for (int l = 0; l < a; ++l) c[l] = dot(N, V + (size_t)l * N, r);
+  int rc = orc_dense_lu_solve(a, A, c, alpha);
+  if (rc == 0)
+    for (int i = 0; i < a; ++i)
+      for (int k = 0; k < N; ++k) x0[k] += alpha[i] * V[(size_t)i * N + k];
+  free(A); free(c); free(alpha);
+  return rc == 0 ? 0 : 1;
+}
+
+/*
  * Phase 2 of Sec. 3: Galerkin projection of one target onto a stored seed
  * basis.  V is N x (a+1) column-major (v_{a+1} present iff has_next), Hbar
  * the unrotated (a+1) x a Hessenberg matrix of the seed's Arnoldi process
@@ -396,9 +528,12 @@ int orc_dense_lu_solve(int n, double* A, double* b, double* x) {
  * One timestep n of the method for a set of seed and target channels that
  * share one grid size (Sec. 2.3 and Sec. 3, both phases):
  *   seeds:   A_s(m~ = m_s^{n-1}) m_s^n = m_s^{n-1}/dt (f = 0), GMRES(m_seed)
- *            from x0 = 0 to tol_seed, keeping the first-cycle basis (a vectors).
+ *            from x0 = 0 to tol_seed, keeping the first-cycle basis (a vectors);
+ *            with seed_solver = 1, BiCGSTAB instead (the paper's Phase 1),
+ *            keeping its key vectors (orc_bicgstab) and A_proj = V^T A_s V.
  *   targets: mode 0 (projected): x0 = V_a H_a^{-1} V_a^T b_i with the basis of
- *            seed target_seed[i]; mode 1 (plain): x0 = 0; mode 2 (warm):
+ *            seed target_seed[i] (x0 = V_a A_proj^{-1} V_a^T b_i after
+ *            BiCGSTAB seeds); mode 1 (plain): x0 = 0; mode 2 (warm):
  *            x0 = m_i^{n-1}; mode 3 (exact Galerkin): x0 = V_a G^{-1} V_a^T b_i
  *            with G = V_a^T A_i V_a; then GMRES(m_ref) on A_i to tol_ref.
  * picard > 1 adds Picard iterations k = 2..picard (Sec. 2.3, m~ = m^{n,(k-1)}):
@@ -443,12 +578,14 @@ int orc_project_galerkin(int H, int W, const double* C, int a, const double* V, 
 void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, double* mseed,
                     int ntgt, double* mtgt, const int* target_seed, int mode, double tol_seed,
                     int m_seed, int a, double tol_ref, int m_ref, int maxit, int* seed_it,
-                    int* tgt_it, double* tgt_res, int* tgt_status, double* tgt_x0res, int picard) {
+                    int* tgt_it, double* tgt_res, int* tgt_status, double* tgt_x0res, int picard,
+                    int seed_solver) {
   int K = picard > 1 ? picard : 1;
   int N = H * W;
   int lda = a + 1;
   double* basis = (double*)calloc((size_t)nseed * N * (a + 1), sizeof(double));
   double* hess = (double*)calloc((size_t)nseed * (a + 1) * a, sizeof(double));
+  double* aproj = (double*)calloc((size_t)nseed * (a > 0 ? a * a : 1), sizeof(double));
   int* used = (int*)calloc((size_t)(nseed > 0 ? nseed : 1), sizeof(int));
   int* nxt = (int*)calloc((size_t)(nseed > 0 ? nseed : 1), sizeof(int));
 #pragma omp parallel for schedule(dynamic, 1)
@@ -460,8 +597,22 @@ void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, dou
     double rr;
     orc_coeffs(H, W, g2, dt, h, ms, NULL, NULL, C);
     orc_rhs(H, W, dt, h, ms, NULL, NULL, b);
-    orc_gmres(H, W, C, b, x, tol_seed, m_seed, maxit, &seed_it[s], &rr, NULL, a,
-              basis + (size_t)s * N * (a + 1), hess + (size_t)s * (a + 1) * a, &used[s], &nxt[s]);
+    if (seed_solver == 1) {
+      double* Vs = basis + (size_t)s * N * (a + 1);
+      orc_bicgstab(H, W, C, b, x, tol_seed, maxit, &seed_it[s], &rr, a, Vs, &used[s]);
+      nxt[s] = 0;
+      /* A_proj = V^T A_seed V (row-major used x used) */
+      int u = used[s];
+      double* Av = (double*)malloc(sizeof(double) * N);
+      for (int k = 0; k < u; ++k) {
+        orc_apply(H, W, C, Vs + (size_t)k * N, Av);
+        for (int l = 0; l < u; ++l) aproj[(size_t)s * a * a + (size_t)l * u + k] = dot(N, Vs + (size_t)l * N, Av);
+      }
+      free(Av);
+    } else {
+      orc_gmres(H, W, C, b, x, tol_seed, m_seed, maxit, &seed_it[s], &rr, NULL, a,
+                basis + (size_t)s * N * (a + 1), hess + (size_t)s * (a + 1) * a, &used[s], &nxt[s]);
+    }
     /* Picard iterations k = 2..K (Sec. 2.3): lag the nonlinear term on the
      * latest iterate, same right-hand side, warm start from that iterate */
     for (int k = 1; k < K; ++k) {
@@ -482,7 +633,11 @@ void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, dou
     double* mt = mtgt + (size_t)t * N;
     orc_coeffs(H, W, g2, dt, h, mt, NULL, NULL, C);
     orc_rhs(H, W, dt, h, mt, NULL, NULL, b);
-    if (mode == 0) {
+    if (mode == 0 && seed_solver == 1) {
+      int s = target_seed[t];
+      orc_project_dense(N, used[s], basis + (size_t)s * N * (a + 1), aproj + (size_t)s * a * a, b,
+                        NULL, x);
+    } else if (mode == 0) {
       int s = target_seed[t];
       orc_project(N, used[s], lda, nxt[s], basis + (size_t)s * N * (a + 1),
                   hess + (size_t)s * (a + 1) * a, b, NULL, x);
@@ -510,7 +665,7 @@ void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, dou
     memcpy(mt, x, sizeof(double) * N);
     free(C); free(b); free(x); free(r);
   }
-  free(basis); free(hess); free(used); free(nxt);
+  free(basis); free(hess); free(aproj); free(used); free(nxt);
 }
 
 

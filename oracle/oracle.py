@@ -14,7 +14,10 @@ follows.  The stencil, right-hand side and CSR assembly are pinned by the
 consistency test against the continuous PDE (Eq. 5, linearised as in Sec. 2.3)
 on quadratic fields, where the central differences are exact; GMRES and the
 projection are pinned by dense LU, the discrete-sine closed form, the Arnoldi
-identities and the FOM residual formula (tests/test_oracle_pins.py).
+identities and the FOM residual formula; BiCGSTAB by dense solves, finite
+termination, and its key vectors spanning the Arnoldi spaces; the explicit
+A_proj projection by its basis invariance against the Hessenberg one
+(tests/test_oracle_pins.py).
 """
 from __future__ import annotations
 
@@ -76,7 +79,11 @@ def lib():
         L.orc_dense_lu_solve.argtypes = [_i, _pd, _pd, _pd]
         L.orc_dense_lu_solve.restype = _i
         L.orc_march_step.argtypes = [_i, _i, _d, _d, _d, _i, _pd, _i, _pd, _pi, _i, _d, _i,
-                                     _i, _d, _i, _i, _pi, _pi, _pd, _pi, _pd, _i]
+                                     _i, _d, _i, _i, _pi, _pi, _pd, _pi, _pd, _i, _i]
+        L.orc_bicgstab.argtypes = [_i, _i, _pd, _pd, _pd, _d, _i, _pi, _pd, _i, _pd, _pi]
+        L.orc_bicgstab.restype = _i
+        L.orc_project_dense.argtypes = [_i, _i, _pd, _pd, _pd, _pd, _pd]
+        L.orc_project_dense.restype = _i
         L.orc_score.argtypes = [_i, _i, _d, _pd, _pd, _pd]
         L.orc_project_galerkin.argtypes = [_i, _i, _pd, _i, _pd, _pd, _pd, _pd]
         L.orc_project_galerkin.restype = _i
@@ -213,6 +220,45 @@ def project(V, Hbar, a, has_next, r, xinit=None):
     return x0, bool(lsq)
 
 
+@dataclass
+class BicgResult:
+    x: np.ndarray
+    status: int
+    iters: int
+    rel_res: float
+    V: np.ndarray      # (a', N): the kept key vectors, orthonormal rows
+
+
+def bicgstab(H, W, C, b, x0=None, tol=1e-10, maxit=1000, capture=0):
+    """BiCGSTAB (van der Vorst 1992; Sec. 3, Phase 1 as printed) with true-residual
+    restarts; with ``capture=a`` keeps up to a orthonormalised key vectors
+    r_0, s_1, r_1, s_2, ... of the first sweep."""
+    N = H * W
+    C = np.ascontiguousarray(C, dtype=np.float64).reshape(-1)
+    b = _f64(b)
+    x = np.zeros(N) if x0 is None else _f64(x0).copy()
+    it = np.zeros(1, dtype=np.int32)
+    rr = np.zeros(1)
+    used = np.zeros(1, dtype=np.int32)
+    capV = np.zeros(max(capture, 1) * N)
+    st = lib().orc_bicgstab(H, W, _p(C), _p(b), _p(x), tol, maxit, _p(it), _p(rr), capture,
+                            _p(capV) if capture > 0 else None, _p(used))
+    return BicgResult(x=x, status=st, iters=int(it[0]), rel_res=float(rr[0]),
+                      V=capV.reshape(-1, N)[: int(used[0])].copy())
+
+
+def project_dense(V, Aproj, r, xinit=None):
+    """Sec. 3, Phase 2 with an explicit A_proj (a x a): x0 = xinit + V_a
+    A_proj^{-1} V_a^T r.  V: (a, N) rows.  Returns (x0, singular)."""
+    V = np.ascontiguousarray(np.asarray(V, dtype=np.float64))
+    a, N = V.shape
+    A = np.ascontiguousarray(np.asarray(Aproj, dtype=np.float64).reshape(a, a))
+    x0 = np.zeros(N)
+    rc = lib().orc_project_dense(N, a, _p(V.reshape(-1)), _p(A.reshape(-1)), _p(_f64(r)),
+                                 _p(_f64(xinit)), _p(x0))
+    return x0, bool(rc)
+
+
 def dense_lu_solve(A, b):
     """Dense LU with partial pivoting (tiny systems)."""
     n = A.shape[0]
@@ -249,11 +295,17 @@ class StepStats:
     tgt_x0res: np.ndarray
 
 
+SEED_GMRES, SEED_BICGSTAB = 0, 1
+
+
 def march_step(H, W, dt, h, g2, mseed, mtgt, target_seed, mode=MODE_PROJECTED,
-               tol_seed=1e-10, m_seed=40, a=40, tol_ref=1e-8, m_ref=40, maxit=1000, picard=1):
+               tol_seed=1e-10, m_seed=40, a=40, tol_ref=1e-8, m_ref=40, maxit=1000, picard=1,
+               seed_solver=SEED_GMRES):
     """One timestep of Sec. 2.3 + Sec. 3 for seeds and targets of one grid
-    size (f = 0), with `picard` lagged-linearisation iterations.  ``mseed``
-    (nseed, N) and ``mtgt`` (ntgt, N) are updated in place from m^{n-1} to m^n."""
+    size (f = 0), with `picard` lagged-linearisation iterations; the seeds are
+    solved by GMRES (Arnoldi basis) or BiCGSTAB (Sec. 3, Phase 1 as printed:
+    its key vectors, A_proj = V^T A_seed V).  ``mseed`` (nseed, N) and ``mtgt``
+    (ntgt, N) are updated in place from m^{n-1} to m^n."""
     assert mseed.dtype == np.float64 and mseed.flags["C_CONTIGUOUS"]
     assert mtgt.dtype == np.float64 and mtgt.flags["C_CONTIGUOUS"]
     ns, nt = mseed.shape[0], mtgt.shape[0]
@@ -263,7 +315,7 @@ def march_step(H, W, dt, h, g2, mseed, mtgt, target_seed, mode=MODE_PROJECTED,
     lib().orc_march_step(H, W, dt, h, g2, ns, _p(mseed), nt, _p(mtgt), _p(ts), mode,
                          tol_seed, m_seed, a, tol_ref, m_ref, maxit, _p(st.seed_iters),
                          _p(st.tgt_iters), _p(st.tgt_res), _p(st.tgt_status), _p(st.tgt_x0res),
-                         int(picard))
+                         int(picard), int(seed_solver))
     return st
 
 

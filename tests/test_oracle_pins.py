@@ -384,3 +384,134 @@ def test_picard_iterations_pins(orc):
     x3 = m0.copy(); xs3 = m0[:1].copy()
     orc.march_step(H, W, dt, h, 0.0, xs3, x3, [0, 0], picard=3, **kw)
     assert np.allclose(x3, x0, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("H,W", [(3, 3), (4, 5), (8, 8)])
+def test_bicgstab_matches_dense_solve(orc, H, W):
+    # Sec. 3, Phase 1 as printed: BiCGSTAB reaches the solution of the
+    # nonsymmetric five-point system (drift f != 0) that a dense solve gives
+    rng = np.random.default_rng(40 + H * W)
+    dt, h, g2 = 0.01, 1 / H, 0.25
+    C = orc.coeffs(H, W, g2, dt, h, rng.uniform(0, 1, H * W), rng.normal(size=H * W),
+                   rng.normal(size=H * W))
+    A = np.stack([orc.apply(H, W, C, e) for e in np.eye(H * W)], axis=1)
+    assert np.abs(A - A.T).max() > 1e-3 * np.abs(A).max()          # really nonsymmetric
+    b = rng.normal(size=H * W)
+    x_np = np.linalg.solve(A, b)
+    r = orc.bicgstab(H, W, C, b, tol=1e-13, maxit=500)
+    assert r.status == 0 and r.iters <= 2 * H * W
+    assert np.linalg.norm(r.x - x_np) <= 1e-11 * np.linalg.norm(x_np)
+    assert abs(np.linalg.norm(b - A @ r.x) / np.linalg.norm(b) - r.rel_res) <= 1e-14
+
+
+@pytest.mark.parametrize("H,W", [(2, 3), (3, 3), (4, 5), (8, 8)])
+def test_bicgstab_finite_termination(orc, H, W):
+    # like BiCG, BiCGSTAB ends in at most N iterations in exact arithmetic (no
+    # breakdown); on strongly convective systems (large drift, dt = 1, far
+    # from the identity) rounding costs it a few more, never hundreds
+    rng = np.random.default_rng(40 + H * W)
+    N = H * W
+    b = rng.normal(size=N)
+    for dt in (1.0, 100.0):
+        C = orc.coeffs(H, W, 4.0, dt, 1 / H, rng.uniform(0, 1, N), 30 * rng.normal(size=N),
+                       30 * rng.normal(size=N))
+        r = orc.bicgstab(H, W, C, b, tol=1e-13, maxit=500)
+        assert r.status == 0 and r.iters <= 1.5 * N + 2
+
+
+def test_bicgstab_hard_system_and_restart(orc):
+    # the worse-conditioned g = 0.5 system needs many iterations; with a
+    # small iteration cap it stops short and reports it, and resuming from
+    # the returned iterate finishes the solve
+    H = W = 16
+    C, b, A = _hard_system(orc)
+    r = orc.bicgstab(H, W, C, b, tol=1e-12, maxit=400)
+    assert r.status == 0 and r.rel_res <= 1e-12
+    assert np.linalg.norm(r.x - np.linalg.solve(A, b)) <= 1e-10 * np.linalg.norm(r.x)
+    part = orc.bicgstab(H, W, C, b, tol=1e-12, maxit=2)
+    assert part.status == orc.NOT_CONVERGED and part.iters == 2
+    rest = orc.bicgstab(H, W, C, b, x0=part.x, tol=1e-12, maxit=400)
+    assert rest.status == 0 and np.linalg.norm(rest.x - r.x) <= 1e-10 * np.linalg.norm(r.x)
+
+
+def test_bicgstab_key_vectors_span_the_krylov_spaces(orc):
+    # the j-th kept vector (r_0, s_1, r_1, s_2, ...) lies in K_{j+1}(A, r_0):
+    # the first j kept vectors span the same space as the first j Arnoldi
+    # vectors of GMRES from the same start (x0 = 0, r_0 = b)
+    H = W = 16
+    C, b, A = _hard_system(orc)
+    rb = orc.bicgstab(H, W, C, b, tol=1e-12, maxit=400, capture=8)
+    rg = orc.gmres(H, W, C, b, tol=1e-13, m=40, maxit=400, capture=8)
+    Vb, Vg = rb.V.T, rg.V.T
+    assert Vb.shape[1] == 8
+    assert np.abs(Vb.T @ Vb - np.eye(8)).max() <= 1e-12
+    assert np.allclose(Vb[:, 0], b / np.linalg.norm(b), rtol=0, atol=1e-15)
+    for j in range(1, 8):
+        Q = Vg[:, :j]
+        assert np.linalg.norm(Vb[:, :j] - Q @ (Q.T @ Vb[:, :j])) <= 1e-12
+        assert np.linalg.norm(Vb[:, j] - Q @ (Q.T @ Vb[:, j])) >= 0.5     # and grows
+
+
+def test_dense_projection_pins(orc):
+    # x0 = V (V^T A V)^{-1} V^T b depends only on span(V): on the BiCGSTAB
+    # basis (explicit A_proj) it equals the paper's Hessenberg projection on
+    # the GMRES basis of the same Krylov space, satisfies the Galerkin
+    # condition, and reaches the exact solution on a full basis
+    H = W = 16
+    C, b, A = _hard_system(orc)
+    for a in (2, 4):
+        rb = orc.bicgstab(H, W, C, b, tol=1e-12, maxit=400, capture=a)
+        rg = orc.gmres(H, W, C, b, tol=1e-13, m=40, maxit=400, capture=a)
+        V = rb.V
+        Ap = V @ A @ V.T
+        xd, sing = orc.project_dense(V, Ap, b)
+        assert not sing
+        xh, _ = orc.project(rg.V, rg.Hbar, rg.a, rg.has_next, b)
+        assert np.linalg.norm(xd - xh) <= 1e-12 * np.linalg.norm(xh)
+        assert np.abs(V @ (b - A @ xd)).max() <= 1e-11 * np.linalg.norm(b)
+        # a transposed A_proj is a different (wrong) projection
+        xt, _ = orc.project_dense(V, Ap.T, b)
+        assert np.linalg.norm(xt - xh) >= 1e-3 * np.linalg.norm(xh)
+    Hs, Ws = 3, 3
+    rng = np.random.default_rng(12)
+    Cs = orc.coeffs(Hs, Ws, 0.25, 0.01, 1 / 3, rng.uniform(0, 1, 9), rng.normal(size=9),
+                    rng.normal(size=9))
+    As = np.stack([orc.apply(Hs, Ws, Cs, e) for e in np.eye(9)], axis=1)
+    Q, _ = np.linalg.qr(rng.normal(size=(9, 9)))
+    bs = rng.normal(size=9)
+    x9, _ = orc.project_dense(Q.T, Q.T @ As @ Q, bs, xinit=np.zeros(9))
+    assert np.linalg.norm(x9 - np.linalg.solve(As, bs)) <= 1e-12 * np.linalg.norm(x9)
+
+
+def test_march_bicgstab_seeds(orc):
+    # the march with the paper's BiCGSTAB seeds reaches the same trajectory as
+    # with GMRES seeds (both refine to 1e-12), the seed states too, and the
+    # projected guesses are as good (targets need as many refine steps)
+    wl = synth.config(1, T=8)
+    g = wl.groups[0]
+    kw = dict(m_seed=30, a=30, m_ref=30, tol_ref=1e-12, tol_seed=1e-12)
+    msg, mtg, stg = orc.march(g.H, g.W, wl.T, wl.g2, g.seeds, g.targets, g.target_seed, **kw)
+    msb, mtb, stb = orc.march(g.H, g.W, wl.T, wl.g2, g.seeds, g.targets, g.target_seed,
+                              seed_solver=orc.SEED_BICGSTAB, **kw)
+    assert all((s.tgt_status == 0).all() for s in stb)
+    assert np.abs(mtb - mtg).max() <= 1e-9 * np.abs(mtg).max()
+    assert np.abs(msb - msg).max() <= 1e-9 * np.abs(msg).max()
+    x0b = np.concatenate([s.tgt_x0res for s in stb])
+    x0g = np.concatenate([s.tgt_x0res for s in stg])
+    assert np.all(x0b < 1) and np.median(x0b) <= 10 * np.median(x0g)
+    # the first step's guesses are x0 = V (V^T A_seed V)^{-1} V^T b_i with the
+    # seed's BiCGSTAB key vectors, A_proj formed from the dense operator here
+    H, W, N = g.H, g.W, g.N
+    dt, h = 1.0 / wl.T, 1.0 / H
+    m0 = g.seeds.reshape(len(g.seeds), -1)
+    tg = g.targets.reshape(len(g.targets), -1)
+    for t in range(len(tg)):
+        s0 = m0[g.target_seed[t]]
+        Cs = orc.coeffs(H, W, wl.g2[0], dt, h, s0)
+        As = np.stack([orc.apply(H, W, Cs, e) for e in np.eye(N)], axis=1)
+        V = orc.bicgstab(H, W, Cs, orc.rhs(H, W, dt, h, s0), tol=1e-12, maxit=1000, capture=30).V
+        bt = orc.rhs(H, W, dt, h, tg[t])
+        x0, _ = orc.project_dense(V, V @ As @ V.T, bt)
+        Ct = orc.coeffs(H, W, wl.g2[0], dt, h, tg[t])
+        res = np.linalg.norm(bt - orc.apply(H, W, Ct, x0)) / np.linalg.norm(bt)
+        assert abs(res - stb[0].tgt_x0res[t]) <= 1e-9 * res
