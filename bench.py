@@ -506,6 +506,19 @@ def main():
             "value": world * nt_planes * NS * max(1, args.steps // 2) / t, "unit": "systems/s",
             "iters_per_solve": sum(s.tgt_iters for s in stp) / (nt_planes * NS)}
         plp.close()
+        # the paper's own Phase 1: BiCGSTAB seeds, their key vectors as the
+        # basis and the explicit A_proj = V^T A_seed V for the targets
+        plb = kp.March(ctx, groups, mode=kp.MARCH_PROJECTED, seed_solver=kp.SEED_BICGSTAB, **common)
+        t = timed(plb, max(1, args.steps // 2), 1)
+        reset()
+        stb, tmb = plb.run(0, NS, stats=True, timing=True)
+        out["bicgstab_seeds"] = {
+            "value": world * nt_planes * NS * max(1, args.steps // 2) / t, "unit": "systems/s",
+            "iters_per_solve": sum(s.tgt_iters for s in stb) / (nt_planes * NS),
+            "seed_iters_per_solve": sum(s.seed_iters for s in stb) / (wl.n_seed_planes * NS),
+            "kernel_ms_per_march": {"seed_solve_and_store": tmb.seed_ms,
+                                    "project_and_refine": tmb.refine_ms}}
+        plb.close()
     if not args.no_baselines:
         modes = [("plain_x0_zero", kp.MARCH_PLAIN), ("plain_warm_start", kp.MARCH_WARM)]
         if not mixed:

@@ -305,6 +305,17 @@ typedef enum {
                                x0 = V_a (V_a^T A_i V_a)^{-1} V_a^T b (FP64 plans only)    */
 } kp_march_mode;
 
+/* Phase 1 (Sec. 3) seed solver of a march.  BiCGSTAB is the method the paper
+ * names: the orthonormalised key vectors of its first sweep (r_0, then s_k
+ * and r_k of every iteration, each kept if it adds a direction, up to max_a)
+ * are the stored basis, and A_proj = V^T A_seed V is formed explicitly and
+ * solved by LU per target.  maxit counts BiCGSTAB iterations; m_seed must be
+ * >= 4 (it sizes the solver workspace).  FP64 plans, one Picard iteration. */
+typedef enum {
+  KP_SEED_GMRES = 0,        /* restarted GMRES(m_seed), first-cycle Arnoldi basis */
+  KP_SEED_BICGSTAB = 1      /* BiCGSTAB (van der Vorst 1992), key-vector basis     */
+} kp_seed_solver;
+
 typedef struct {
   int H, W;
   int nseed, ntgt;
@@ -343,6 +354,7 @@ typedef struct {
                             solve with m~ = m^{n-1}; K > 1 re-solves with m~ the
                             latest iterate, same right-hand side, warm start; the
                             stored seed basis is the first solve's.  FP64 plans. */
+  int seed_solver;       /* kp_seed_solver: how Phase 1 (Sec. 3) solves the seeds */
 } kp_march_opts;
 
 /* Per-timestep totals, filled on the host by kp_march_run. */

@@ -57,21 +57,22 @@ size_t gmres_fp64_smem_bytes(int ept, int nt, int S, int m) {
 
 cudaError_t launch_gmres_fp64(const GmresParams& p, int ept, int nt, int minb, size_t smem,
                               cudaStream_t st) {
-  if (p.x0_mode == X0_GALERKIN || p.score_stride || p.picard > 1)
+  if (p.bicg && p.capV) return launch_gmres_fp64_bicg(p, ept, nt, minb, smem, st);
+  if (p.x0_mode == X0_GALERKIN || p.score_stride || p.picard > 1 || p.bicg)
     return launch_gmres_fp64_feat(p, ept, nt, minb, smem, st);
-  if (ept == 4 && nt == 256 && minb == 2) return launch_one<4, 256, 2, false>(p, smem, st);
-  if (ept == 4 && nt == 256 && minb == 3) return launch_one<4, 256, 3, false>(p, smem, st);
-  if (ept == 8 && nt == 128 && minb == 2) return launch_one<8, 128, 2, false>(p, smem, st);
-  if (ept == 8 && nt == 128 && minb == 3) return launch_one<8, 128, 3, false>(p, smem, st);
-  if (ept == 8 && nt == 128 && minb == 4) return launch_one<8, 128, 4, false>(p, smem, st);
-  if (ept == 16 && nt == 64 && minb == 4) return launch_one<16, 64, 4, false>(p, smem, st);
-  if (ept == 8 && nt == 512) return launch_one<8, 512, 1, false>(p, smem, st);
+  if (ept == 4 && nt == 256 && minb == 2) return launch_one<4, 256, 2, kVarLean>(p, smem, st);
+  if (ept == 4 && nt == 256 && minb == 3) return launch_one<4, 256, 3, kVarLean>(p, smem, st);
+  if (ept == 8 && nt == 128 && minb == 2) return launch_one<8, 128, 2, kVarLean>(p, smem, st);
+  if (ept == 8 && nt == 128 && minb == 3) return launch_one<8, 128, 3, kVarLean>(p, smem, st);
+  if (ept == 8 && nt == 128 && minb == 4) return launch_one<8, 128, 4, kVarLean>(p, smem, st);
+  if (ept == 16 && nt == 64 && minb == 4) return launch_one<16, 64, 4, kVarLean>(p, smem, st);
+  if (ept == 8 && nt == 512) return launch_one<8, 512, 1, kVarLean>(p, smem, st);
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_gmres_fp64_1k_grid(const GmresParams& p, size_t smem, int grid,
                                       cudaStream_t st) {
-  auto k = gmres_fp64_kernel<4, 256, 2, false>;
+  auto k = gmres_fp64_kernel<4, 256, 2, kVarLean>;
   cudaError_t e = allow_max_smem(k, smem);
   if (e != cudaSuccess) return e;
   k<<<grid, 256, smem, st>>>(p);
@@ -95,13 +96,13 @@ int gmres_fp64_blocks_per_sm(int ept, int nt, int minb, size_t smem) {
     e = allow_max_smem(k, smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem);
   };
-  if (ept == 4 && nt == 256 && minb == 2) occ(gmres_fp64_kernel<4, 256, 2, false>, 256);
-  else if (ept == 4 && nt == 256 && minb == 3) occ(gmres_fp64_kernel<4, 256, 3, false>, 256);
-  else if (ept == 8 && nt == 128 && minb == 2) occ(gmres_fp64_kernel<8, 128, 2, false>, 128);
-  else if (ept == 8 && nt == 128 && minb == 3) occ(gmres_fp64_kernel<8, 128, 3, false>, 128);
-  else if (ept == 8 && nt == 128 && minb == 4) occ(gmres_fp64_kernel<8, 128, 4, false>, 128);
-  else if (ept == 16 && nt == 64 && minb == 4) occ(gmres_fp64_kernel<16, 64, 4, false>, 64);
-  else if (ept == 8 && nt == 512) occ(gmres_fp64_kernel<8, 512, 1, false>, 512);
+  if (ept == 4 && nt == 256 && minb == 2) occ(gmres_fp64_kernel<4, 256, 2, kVarLean>, 256);
+  else if (ept == 4 && nt == 256 && minb == 3) occ(gmres_fp64_kernel<4, 256, 3, kVarLean>, 256);
+  else if (ept == 8 && nt == 128 && minb == 2) occ(gmres_fp64_kernel<8, 128, 2, kVarLean>, 128);
+  else if (ept == 8 && nt == 128 && minb == 3) occ(gmres_fp64_kernel<8, 128, 3, kVarLean>, 128);
+  else if (ept == 8 && nt == 128 && minb == 4) occ(gmres_fp64_kernel<8, 128, 4, kVarLean>, 128);
+  else if (ept == 16 && nt == 64 && minb == 4) occ(gmres_fp64_kernel<16, 64, 4, kVarLean>, 64);
+  else if (ept == 8 && nt == 512) occ(gmres_fp64_kernel<8, 512, 1, kVarLean>, 512);
   return e == cudaSuccess ? n : 0;
 }
 

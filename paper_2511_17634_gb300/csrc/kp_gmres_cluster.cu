@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
         mt.has_next = hn;
         mt.timestep = tstep;
         mt.N = N;
-        mt.pad_[0] = mt.pad_[1] = 0;
+        mt.dense = mt.pad_ = 0;
         p.slotMeta[cidx] = mt;
       } else {
         p.capMeta[sysi].a = a;
@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
     if (p.factor) {
       SlotMeta mt;
       mt.a = 0; mt.has_next = 0; mt.timestep = tstep; mt.N = N; mt.lsq = 0; mt.nrot = 0;
-      mt.pad_[0] = mt.pad_[1] = 0;
+      mt.dense = mt.pad_ = 0;
       p.slotMeta[cidx] = mt;
     } else {
       p.capMeta[sysi].a = 0;

@@ -1,9 +1,10 @@
 // kp_gmres_kernel.cuh -- the FP64 batched GMRES(m) kernel template and its
-// launcher, shared by kp_gmres.cu (the lean instantiations) and
-// kp_gmres_feat.cu (FEAT = true: the exact-Galerkin initial guess, Picard
-// iterations and the fused score / embedding epilogue).  The optional paths
-// are compiled only into the FEAT variant, so the default solver keeps its
-// registers for the hot loop; both variants compile in parallel.
+// launcher, shared by kp_gmres.cu (the lean instantiations), kp_gmres_feat.cu
+// (the exact-Galerkin initial guess, Picard iterations, the fused score /
+// embedding epilogue and the projection through an explicit A_proj) and
+// kp_gmres_bicg.cu (BiCGSTAB seed solves).  The optional paths are compiled
+// only into their variants, so the default solver keeps its registers for the
+// hot loop; the variants compile in parallel.
 //
 // GB300 design notes (FP64 runs at 1/64 of the FP32 rate on this part, about
 // 2 FP64 FMA per clock per SM, so FP64 instructions -- not HBM bytes -- bound
@@ -61,8 +62,15 @@ __device__ __forceinline__ Smem carve(double* base, int S, int npad, int nwarps,
   return s;
 }
 
-template <int EPT, int NT, int MINB, bool FEAT>
+// VAR selects the code compiled into an instantiation: kVarLean (the plain
+// solver), kVarFeat (plus exact Galerkin, Picard, score / embedding and the
+// projection through an explicit A_proj), kVarBicg (BiCGSTAB seed solves).
+enum { kVarLean = 0, kVarFeat = 1, kVarBicg = 2 };
+
+template <int EPT, int NT, int MINB, int VAR>
 __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams p) {
+  constexpr bool FEAT = VAR == kVarFeat;
+  constexpr bool BICG = VAR == kVarBicg;
   constexpr int NWARPS = NT / 32;
   extern __shared__ __align__(16) double smem_raw[];
   const int npad = EPT * NT;
@@ -231,9 +239,25 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
         if (warp == 0) {
           for (int i = lane; i < nv; i += 32) sm.hb[i] = cross_warp<NT>(sm.red, i);
           __syncwarp();
-          const double* rot = p.slotRot + (size_t)sl * 3 * p.max_a;
-          solve_projected_warp(sm.hb, a, mt.nrot, p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a,
-                               p.max_a + 1, rot, rot + 2 * p.max_a, lane);
+          const double* R = p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a;
+          if (FEAT && mt.dense) {
+            // BiCGSTAB seed basis: A_proj alpha = c with the stored explicit
+            // A_proj = V^T A_seed V, LU with partial pivoting on this warp
+            bool ok = a * a <= (m + 1) * m;
+            if (ok) {
+              for (int e = lane; e < a * a; e += 32) {
+                const int l = e % a, k = e / a;
+                sm.Hr[l + k * a] = R[l + (size_t)k * (p.max_a + 1)];
+              }
+              __syncwarp();
+              ok = lu_solve_warp(sm.Hr, a, sm.hb, lane);
+            }
+            if (!ok)
+              for (int i = lane; i < a; i += 32) sm.hb[i] = 0.0;
+          } else {
+            const double* rot = p.slotRot + (size_t)sl * 3 * p.max_a;
+            solve_projected_warp(sm.hb, a, mt.nrot, R, p.max_a + 1, rot, rot + 2 * p.max_a, lane);
+          }
         }
         __syncthreads();
 #pragma unroll
@@ -327,7 +351,238 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
     auto residual = [&]() { residual_of(sm.xs, w); };
     int steps = 0, status = KP_NOT_CONVERGED, cycle = 0;
     double bnorm = 0.0, beta = 0.0;
-    const int npic = (FEAT && p.picard > 1) ? p.picard : 1;
+    unsigned long long bicg_fl = 0;            // flops per unknown of a BiCGSTAB seed solve
+    const bool bicg = BICG && capture;
+    if (BICG && bicg) {
+      // Sec. 3, Phase 1 as printed: BiCGSTAB (van der Vorst 1992) on the seed,
+      // restarted from the true residual when the updated one has drifted.
+      // The key vectors of the first sweep (r_0, then s_k and r_k of every
+      // iteration), orthonormalised by CGS2 against the ones kept before, are
+      // the stored basis V_a; A_proj = V_a^T A V_a is formed explicitly for
+      // the targets (BiCGSTAB has no Hessenberg relation).
+      double* rh = slot(0);                    // shadow residual
+      double* rv = slot(1);                    // r
+      double* pv = slot(2);                    // search direction p
+      double* vv = slot(3);                    // A p
+      double* sv = slot(4);                    // intermediate residual s
+      // block sums of nv values fn(i) into sm.hb[0..nv)
+      auto reduce = [&](int nv, auto&& fn) {
+        block_partials<NT>(nv, fn, sm.red);
+        if (warp == 0)
+          for (int i = lane; i < nv; i += 32) sm.hb[i] = cross_warp<NT>(sm.red, i);
+        __syncthreads();
+      };
+      auto apply_full = [&](const double* v) {   // w = A v
+        apply_off(v, w);
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          const int pp = tid + k * NT;
+          w[k] = pp < N ? fma(cd, v[pp], w[k]) : 0.0;
+        }
+      };
+      int nkeep = 0;
+      // keep u (this thread's points) as basis vector nkeep if it adds a direction
+      auto keep = [&](const double* u) {
+        if (nkeep >= p.cap_a) return;
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          const int pp = tid + k * NT;
+          w[k] = pp < N ? u[pp] : 0.0;
+        }
+        double n0 = 0.0;
+        for (int pass = 0; pass < 2; ++pass) {
+          reduce(nkeep + 1, [&](int i) {
+            double s = 0.0;
+            if (i < nkeep) {
+              const double* vi = capV + (size_t)i * p.cap_ld;
+#pragma unroll
+              for (int k = 0; k < EPT; ++k) {
+                const int pp = tid + k * NT;
+                if (pp < N) s = fma(vi[pp], w[k], s);
+              }
+            } else {
+#pragma unroll
+              for (int k = 0; k < EPT; ++k) s = fma(w[k], w[k], s);
+            }
+            return s;
+          });
+          if (pass == 0) n0 = sm.hb[nkeep];
+          for (int i = 0; i < nkeep; ++i) {
+            const double hi = sm.hb[i];
+            const double* vi = capV + (size_t)i * p.cap_ld;
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) {
+              const int pp = tid + k * NT;
+              if (pp < N) w[k] = fma(-hi, vi[pp], w[k]);
+            }
+          }
+        }
+        reduce(1, [&](int) {
+          double s = 0.0;
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) s = fma(w[k], w[k], s);
+          return s;
+        });
+        const double n1 = sm.hb[0];
+        bicg_fl += 8ull * nkeep + 7ull;
+        if (!(n1 > 1e-20 * n0)) return;        // no new direction (norm ratio 1e-10)
+        const double inv = 1.0 / sqrt(n1);
+        double* vn = capV + (size_t)nkeep * p.cap_ld;
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          const int pp = tid + k * NT;
+          if (pp < N) vn[pp] = w[k] * inv;
+        }
+        ++nkeep;
+      };
+      int sweep = 0;
+      for (;;) {
+        // true residual r = b - A x (x = 0 for the first sweep of a seed)
+        if (sweep == 0 && p.x0_mode == X0_ZERO) {
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) w[k] = bval(tid + k * NT);
+        } else {
+          __syncthreads();
+          residual();
+        }
+        reduce(2, [&](int i) {
+          double s = 0.0;
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) {
+            const double bv = bval(tid + k * NT);
+            s += (i == 0) ? bv * bv : w[k] * w[k];
+          }
+          return s;
+        });
+        bnorm = sqrt(sm.hb[0]);
+        beta = sqrt(sm.hb[1]);
+        bicg_fl += 12;
+        if (beta <= p.tol * bnorm) { status = KP_OK; break; }
+        if (!isfinite(beta)) { status = KP_BREAKDOWN; break; }
+        if (steps >= p.maxit) break;
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          const int pp = tid + k * NT;
+          rh[pp] = w[k];
+          rv[pp] = w[k];
+          pv[pp] = 0.0;
+          vv[pp] = 0.0;
+        }
+        const bool keeping = sweep == 0;
+        if (keeping) keep(rv);
+        double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+        const int steps0 = steps;
+        while (steps < p.maxit) {
+          reduce(1, [&](int) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) s = fma(rh[tid + k * NT], rv[tid + k * NT], s);
+            return s;
+          });
+          const double rho = sm.hb[0];
+          if (rho == 0.0) break;
+          const double bt = (rho / rho_old) * (alpha / omega);
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) {
+            const int pp = tid + k * NT;
+            pv[pp] = fma(bt, fma(-omega, vv[pp], pv[pp]), rv[pp]);
+          }
+          __syncthreads();                     // p complete for the stencil
+          apply_full(pv);
+          reduce(1, [&](int) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) s = fma(rh[tid + k * NT], w[k], s);
+            return s;
+          });
+          alpha = rho / sm.hb[0];
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) {
+            const int pp = tid + k * NT;
+            vv[pp] = w[k];
+            sv[pp] = fma(-alpha, w[k], rv[pp]);
+          }
+          ++steps;
+          bicg_fl += 42;
+          reduce(1, [&](int) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) s = fma(sv[tid + k * NT], sv[tid + k * NT], s);
+            return s;
+          });
+          if (sqrt(sm.hb[0]) <= p.tol * bnorm) {
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) {
+              const int pp = tid + k * NT;
+              sm.xs[pp] = fma(alpha, pv[pp], sm.xs[pp]);
+            }
+            if (keeping) keep(sv);
+            break;
+          }
+          __syncthreads();                     // s complete for the stencil
+          apply_full(sv);                      // t = A s
+          reduce(2, [&](int i) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) s = fma(w[k], i == 0 ? sv[tid + k * NT] : w[k], s);
+            return s;
+          });
+          omega = sm.hb[1] > 0.0 ? sm.hb[0] / sm.hb[1] : 0.0;
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) {
+            const int pp = tid + k * NT;
+            sm.xs[pp] = fma(omega, sv[pp], fma(alpha, pv[pp], sm.xs[pp]));
+            rv[pp] = fma(-omega, w[k], sv[pp]);
+          }
+          if (keeping) { keep(sv); keep(rv); }
+          reduce(1, [&](int) {
+            double s = 0.0;
+#pragma unroll
+            for (int k = 0; k < EPT; ++k) s = fma(rv[tid + k * NT], rv[tid + k * NT], s);
+            return s;
+          });
+          if (sqrt(sm.hb[0]) <= p.tol * bnorm || omega == 0.0) break;
+          rho_old = rho;
+        }
+        if (steps == steps0) { status = KP_BREAKDOWN; break; }   // a sweep without progress
+        ++sweep;
+      }
+      // A_proj = V_a^T A V_a, column by column, into the seed's slot
+      const int a = nkeep;
+      const int sl = cidx;
+      double* R = p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a;
+      __syncthreads();                         // kept vectors complete for the stencil
+      for (int kc = 0; kc < a; ++kc) {
+        apply_full(capV + (size_t)kc * p.cap_ld);
+        reduce(a, [&](int l) {
+          const double* vl = capV + (size_t)l * p.cap_ld;
+          double s = 0.0;
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) {
+            const int pp = tid + k * NT;
+            if (pp < N) s = fma(vl[pp], w[k], s);
+          }
+          return s;
+        });
+        for (int l = tid; l < a; l += NT) R[l + (size_t)kc * (p.max_a + 1)] = sm.hb[l];
+      }
+      bicg_fl += (unsigned long long)a * (9 + 2 * a);
+      if (tid == 0) {
+        SlotMeta mt;
+        mt.a = a;
+        mt.has_next = 0;
+        mt.timestep = tstep;
+        mt.N = N;
+        mt.lsq = 0;
+        mt.nrot = 0;
+        mt.dense = 1;
+        mt.pad_ = 0;
+        p.slotMeta[sl] = mt;
+      }
+      __syncthreads();
+    }
+    const int npic = bicg ? 0 : (FEAT && p.picard > 1) ? p.picard : 1;
+
     for (int pk = 0; pk < npic; ++pk) {
       if (FEAT && pk > 0) {
         // Picard iteration k = pk + 1 (Sec. 2.3): the nonlinear term lagged on
@@ -541,7 +796,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
               mt.has_next = hn;
               mt.timestep = tstep;
               mt.N = N;
-              mt.pad_[0] = mt.pad_[1] = 0;
+              mt.dense = mt.pad_ = 0;
               p.slotMeta[sl] = mt;
             } else {
               p.capMeta[sysi].a = a;
@@ -580,7 +835,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
           mt.N = N;
           mt.lsq = 0;
           mt.nrot = 0;
-          mt.pad_[0] = mt.pad_[1] = 0;
+          mt.dense = mt.pad_ = 0;
           p.slotMeta[cidx] = mt;
         } else {
           p.capMeta[sysi].a = 0;
@@ -631,7 +886,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
       }
       if (p.acc) {
         StepAcc* a = p.acc + tstep;
-        const unsigned long long fl = gmres_flops(steps, m) * (unsigned long long)N;
+        const unsigned long long fl = (bicg ? bicg_fl : gmres_flops(steps, m)) * (unsigned long long)N;
         if (p.acc_kind == 0) {
           atomicAdd(&a->seed_iters, (unsigned long long)steps);
           atomicAdd(&a->seed_flops, fl);
@@ -668,9 +923,9 @@ static cudaError_t allow_max_smem(K k, size_t smem) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
 
-template <int EPT, int NT, int MINB, bool FEAT>
+template <int EPT, int NT, int MINB, int VAR>
 static cudaError_t launch_one(const GmresParams& p, size_t smem, cudaStream_t st) {
-  auto k = gmres_fp64_kernel<EPT, NT, MINB, FEAT>;
+  auto k = gmres_fp64_kernel<EPT, NT, MINB, VAR>;
   cudaError_t e = allow_max_smem(k, smem);
   if (e != cudaSuccess) return e;
   const int grid = p.grid > 0 ? p.grid : p.nsys;

@@ -439,7 +439,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
           mt.has_next = hn;
           mt.timestep = tstep;
           mt.N = N;
-          mt.pad_[0] = mt.pad_[1] = 0;
+          mt.dense = mt.pad_ = 0;
           p.slotMeta[sl] = mt;
         } else {
           p.capMeta[sysi].a = a;
@@ -475,7 +475,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
       if (p.factor) {
         SlotMeta mt;
         mt.a = 0; mt.has_next = 0; mt.timestep = tstep; mt.N = N; mt.lsq = 0; mt.nrot = 0;
-        mt.pad_[0] = mt.pad_[1] = 0;
+        mt.dense = mt.pad_ = 0;
         p.slotMeta[cidx] = mt;
       } else {
         p.capMeta[sysi].a = 0;

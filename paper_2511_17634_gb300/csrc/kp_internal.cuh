@@ -35,7 +35,9 @@ struct SlotMeta {
   int N;
   int lsq;        // projection solves the (a'+1) x a' least-squares problem
   int nrot;       // Givens rotations applied to c before the triangular solve
-  int pad_[2];
+  int dense;      // 1: slotR holds the explicit A_proj = V^T A_seed V (a x a,
+                  // ld max_a + 1) of a BiCGSTAB basis instead of a QR of H_a
+  int pad_;
 };
 
 // Per-timestep totals accumulated by the solver blocks (time march).
@@ -122,6 +124,8 @@ struct GmresParams {
   size_t score_stride;      // > 0: write the score of each solved timestep to
                             // d.score + tstep * score_stride and advance d.emb
   int picard;               // > 1: Picard iterations per system (FP64 solver)
+  int bicg;                 // 1: seed solves by BiCGSTAB (dense A_proj slots);
+                            // the FP64 solver's feature variant runs both sides
   int pdl;                  // programmatic launch, bit 0: let the stream's next launch
                             // start at once; bit 1: launched that way, wait for the
                             // prior grid (its completion and memory) before exiting
@@ -507,8 +511,11 @@ struct ProjTile {
 // Launchers (defined in the .cu files; return a cudaError_t of the launch).
 cudaError_t launch_gmres_fp64(const GmresParams& p, int ept, int nt, int minb, size_t smem,
                               cudaStream_t st);
-// The same with the optional paths compiled in (exact Galerkin, Picard, score).
+// The same with the optional paths compiled in (exact Galerkin, Picard, score,
+// explicit A_proj), and the BiCGSTAB seed solver.
 cudaError_t launch_gmres_fp64_feat(const GmresParams& p, int ept, int nt, int minb, size_t smem,
+                                   cudaStream_t st);
+cudaError_t launch_gmres_fp64_bicg(const GmresParams& p, int ept, int nt, int minb, size_t smem,
                                    cudaStream_t st);
 size_t gmres_fp64_smem_bytes(int ept, int nt, int S, int m);
 size_t gmres_mixed_smem_bytes(int ept, int nt, int S, int m);

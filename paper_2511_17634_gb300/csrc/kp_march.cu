@@ -135,6 +135,7 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset,
   g.acc = P->acc;
   g.err = P->err;
   g.picard = P->opt.picard;
+  g.bicg = P->opt.seed_solver == KP_SEED_BICGSTAB;
   if (P->K > 1) {
     // window: descriptors and slot sets chosen per timestep on the device
     g.win = P->K;
@@ -360,6 +361,13 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
   if (o.mode == KP_MARCH_GALERKIN && (P->mixed || P->shT.cs)) {
     kp_march_destroy(P);
     return kp::set_error(c, KP_ERR_UNSUPPORTED, "exact Galerkin projection needs the FP64 one-block solver");
+  }
+  if (o.seed_solver != KP_SEED_GMRES &&
+      (o.seed_solver != KP_SEED_BICGSTAB || P->mixed || P->shS.cs || P->shT.cs || o.picard > 1 ||
+       o.m_seed < 4)) {
+    kp_march_destroy(P);
+    return kp::set_error(c, KP_ERR_UNSUPPORTED, "BiCGSTAB seeds need the FP64 one-block solver, "
+                         "one Picard iteration and m_seed >= 4");
   }
   if (o.score && (P->mixed || P->shT.cs)) {
     kp_march_destroy(P);

@@ -54,7 +54,7 @@ __global__ void factor_kernel(FactorParams p) {
   mt.N = N;
   mt.lsq = lsq;
   mt.nrot = nrot;
-  mt.pad_[0] = mt.pad_[1] = 0;
+  mt.dense = mt.pad_ = 0;
   p.meta[p.seed_id] = mt;
 }
 

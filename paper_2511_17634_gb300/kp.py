@@ -267,6 +267,7 @@ class Context:
 
 # ---------------------------------------------------------------- time march
 MARCH_PROJECTED, MARCH_PLAIN, MARCH_WARM, MARCH_GALERKIN = 0, 1, 2, 3
+SEED_GMRES, SEED_BICGSTAB = 0, 1
 
 
 class _Group(ctypes.Structure):
@@ -280,7 +281,8 @@ class _MarchOpts(ctypes.Structure):
                 ("tol_seed", ctypes.c_double), ("tol", ctypes.c_double), ("m_seed", ctypes.c_int),
                 ("m", ctypes.c_int), ("maxit", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("window", ctypes.c_int), ("target_blocks", ctypes.c_int),
-                ("score", ctypes.c_void_p), ("embed", ctypes.c_void_p), ("picard", ctypes.c_int)]
+                ("score", ctypes.c_void_p), ("embed", ctypes.c_void_p), ("picard", ctypes.c_int),
+                ("seed_solver", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
@@ -316,7 +318,7 @@ class March:
 
     def __init__(self, ctx, groups, T, g2, mode=MARCH_PROJECTED, tol_seed=1e-10, tol=1e-8,
                  m_seed=40, m=40, maxit=1000, use_graph=True, window=0, target_blocks=0,
-                 score=None, embed=None, picard=1):
+                 score=None, embed=None, picard=1, seed_solver=0):
         L = _march_lib()
         self.ctx = ctx
         self._keep = []
@@ -341,7 +343,8 @@ class March:
         o = _MarchOpts(T, g2.ctypes.data, mode, tol_seed, tol, m_seed, m, maxit, int(use_graph),
                        int(window), int(target_blocks),
                        score.data_ptr() if score is not None else None,
-                       embed.data_ptr() if embed is not None else None, int(picard))
+                       embed.data_ptr() if embed is not None else None, int(picard),
+                       int(seed_solver))
         self.T = T
         self._h = ctypes.c_void_p()
         ctx._check(L.kp_march_create(ctx._h, len(groups), ctypes.cast(arr, ctypes.c_void_p),

@@ -261,3 +261,66 @@ def test_march_without_seeds_windowed(kp, orc):
                           mode=1, tol_ref=1e-12, m_ref=30)
     assert np.abs(t.cpu().numpy() - omt).max() <= 1e-9 * np.abs(omt).max()
     assert all(x.seed_iters == 0 for x in st)
+
+
+@pytest.mark.parametrize("window", [1, 0])
+def test_march_bicgstab_seeds_match_oracle(kp, orc, window):
+    # the paper's Phase 1: BiCGSTAB seeds, their key vectors as the basis and
+    # the explicit A_proj for the targets, against the oracle's march
+    wl = synth.config(1)
+    g = wl.groups[0]
+    ctx = kp.Context(max_seeds=8, max_a=wl.a, max_n=g.N)
+    grp = _groups(wl)
+    mr = kp.March(ctx, grp, wl.T, wl.g2, mode=0, tol_seed=1e-12, tol=1e-12, m_seed=wl.m_seed,
+                  m=wl.m, maxit=1000, window=window, seed_solver=kp.SEED_BICGSTAB)
+    stats, _ = mr.run(0, wl.T, stats=True)
+    torch.cuda.synchronize()
+    oms, omt, ost = orc.march(g.H, g.W, wl.T, wl.g2, g.seeds, g.targets, g.target_seed,
+                              mode=0, tol_seed=1e-12, m_seed=wl.m_seed, a=wl.a, tol_ref=1e-12,
+                              m_ref=wl.m, seed_solver=orc.SEED_BICGSTAB)
+    assert np.abs(grp[0][1].cpu().numpy() - omt).max() <= 1e-9 * np.abs(omt).max()
+    assert np.abs(grp[0][0].cpu().numpy() - oms).max() <= 1e-9 * np.abs(oms).max()
+    assert all(s.not_converged == 0 for s in stats)
+    assert max(s.max_rel_res for s in stats) <= 1e-12
+    # the projected guesses are the oracle's: the refine needs as many steps
+    gpu_it = np.array([s.tgt_iters for s in stats])
+    orc_it = np.array([st.tgt_iters.sum() for st in ost])
+    assert np.abs(gpu_it - orc_it).max() <= len(g.targets)
+    seed_it = np.array([s.seed_iters for s in stats])
+    orc_sit = np.array([st.seed_iters.sum() for st in ost])
+    assert np.abs(seed_it - orc_sit).max() <= len(g.seeds)
+
+
+def test_march_bicgstab_seeds_32x32_windowed(kp, orc):
+    # the benchmark's grid and launch shape with BiCGSTAB seeds, windows of 4
+    wl = synth.config(2, T=1000, ntargets=40)
+    g = wl.groups[0]
+    steps = 8
+    ctx = kp.Context(max_seeds=8 * wl.n_seed_planes, max_a=wl.a, max_n=g.N)
+    grp = _groups(wl)
+    mr = kp.March(ctx, grp, wl.T, wl.g2, mode=0, tol_seed=wl.tol_seed, tol=wl.tol,
+                  m_seed=wl.m_seed, m=wl.m, window=4, seed_solver=kp.SEED_BICGSTAB)
+    stats, _ = mr.run(0, steps, stats=True)
+    torch.cuda.synchronize()
+    assert all(s.max_rel_res <= 1e-8 and s.not_converged == 0 for s in stats)
+    oms, omt, ost = orc.march(g.H, g.W, wl.T, wl.g2, g.seeds, g.targets, g.target_seed, steps=steps,
+                              tol_seed=wl.tol_seed, m_seed=wl.m_seed, a=wl.a, tol_ref=wl.tol,
+                              m_ref=wl.m, seed_solver=orc.SEED_BICGSTAB)
+    assert np.abs(grp[0][1].cpu().numpy() - omt).max() <= 1e-6 * np.abs(omt).max()
+    gpu_it = np.array([s.tgt_iters for s in stats])
+    orc_it = np.array([st.tgt_iters.sum() for st in ost])
+    assert np.abs(gpu_it - orc_it).max() <= len(g.targets)
+
+
+def test_march_bicgstab_seeds_rejected_combinations(kp):
+    wl = synth.config(1)
+    g = wl.groups[0]
+    grp = _groups(wl)
+    ctx = kp.Context(max_seeds=8, max_a=wl.a, max_n=g.N)
+    with pytest.raises(RuntimeError):
+        kp.March(ctx, grp, wl.T, wl.g2, mode=0, picard=2, seed_solver=kp.SEED_BICGSTAB)
+    with pytest.raises(RuntimeError):
+        kp.March(ctx, grp, wl.T, wl.g2, mode=0, seed_solver=7)
+    mctx = kp.Context(max_seeds=8, max_a=wl.a, max_n=g.N, precision=kp.PREC_MIXED)
+    with pytest.raises(RuntimeError):
+        kp.March(mctx, grp, wl.T, wl.g2, mode=0, seed_solver=kp.SEED_BICGSTAB)
