@@ -430,6 +430,36 @@ int orc_project_dense(int N, int a, const double* V, const double* Aproj, const 
 }
 
 /*
+ * Seed cycling with subspace expansion (Sec. 5.2 runs it with a new seed every
+ * 50 images and the subspace capped at a = 20; the paragraph the source of
+ * Sec. 3 leaves commented out describes accumulating the key vectors of each
+ * new seed into an increasingly rich basis).  The basis served by a new seed
+ * is built from its own basis vectors Vown (a_own of them) first, then the
+ * previous accumulated basis Vprev (a_prev), each vector orthogonalised by
+ * modified Gram-Schmidt run twice against those kept and kept, normalised, if
+ * more than 1e-10 of its norm remains, until cap_a vectors are kept; so the
+ * newest seed's space is always whole and older ones fill what room is left.
+ * A_proj = V^T A_seed V is then formed with the new seed's operator C
+ * (row-major count x count).  V, Vown, Vprev: column-major N x (count).
+ * Returns the number of vectors kept.
+ */
+int orc_accumulate(int H, int W, const double* C, int a_own, const double* Vown, int a_prev,
+                   const double* Vprev, int cap_a, double* V, double* Aproj) {
+  int N = H * W;
+  int used = 0;
+  double* w = (double*)malloc(sizeof(double) * N);
+  for (int k = 0; k < a_own; ++k) keep_vector(N, Vown + (size_t)k * N, cap_a, V, &used, w);
+  for (int k = 0; k < a_prev; ++k) keep_vector(N, Vprev + (size_t)k * N, cap_a, V, &used, w);
+  double* Av = (double*)malloc(sizeof(double) * N);
+  for (int k = 0; k < used; ++k) {
+    orc_apply(H, W, C, V + (size_t)k * N, Av);
+    for (int l = 0; l < used; ++l) Aproj[(size_t)l * used + k] = dot(N, V + (size_t)l * N, Av);
+  }
+  free(w); free(Av);
+  return used;
+}
+
+/*
  * Phase 2 of Sec. 3: Galerkin projection of one target onto a stored seed
  * basis.  V is N x (a+1) column-major (v_{a+1} present iff has_next), Hbar
  * the unrotated (a+1) x a Hessenberg matrix of the seed's Arnoldi process
@@ -533,7 +563,9 @@ int orc_dense_lu_solve(int n, double* A, double* b, double* x) {
  *            keeping its key vectors (orc_bicgstab) and A_proj = V^T A_s V.
  *   targets: mode 0 (projected): x0 = V_a H_a^{-1} V_a^T b_i with the basis of
  *            seed target_seed[i] (x0 = V_a A_proj^{-1} V_a^T b_i after
- *            BiCGSTAB seeds); mode 1 (plain): x0 = 0; mode 2 (warm):
+ *            BiCGSTAB seeds, and after seeds with a predecessor in seed_prev,
+ *            which serve the accumulated basis of orc_accumulate); mode 1
+ *            (plain): x0 = 0; mode 2 (warm):
  *            x0 = m_i^{n-1}; mode 3 (exact Galerkin): x0 = V_a G^{-1} V_a^T b_i
  *            with G = V_a^T A_i V_a; then GMRES(m_ref) on A_i to tol_ref.
  * picard > 1 adds Picard iterations k = 2..picard (Sec. 2.3, m~ = m^{n,(k-1)}):
@@ -579,7 +611,7 @@ void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, dou
                     int ntgt, double* mtgt, const int* target_seed, int mode, double tol_seed,
                     int m_seed, int a, double tol_ref, int m_ref, int maxit, int* seed_it,
                     int* tgt_it, double* tgt_res, int* tgt_status, double* tgt_x0res, int picard,
-                    int seed_solver) {
+                    int seed_solver, const int* seed_prev) {
   int K = picard > 1 ? picard : 1;
   int N = H * W;
   int lda = a + 1;
@@ -588,6 +620,9 @@ void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, dou
   double* aproj = (double*)calloc((size_t)nseed * (a > 0 ? a * a : 1), sizeof(double));
   int* used = (int*)calloc((size_t)(nseed > 0 ? nseed : 1), sizeof(int));
   int* nxt = (int*)calloc((size_t)(nseed > 0 ? nseed : 1), sizeof(int));
+  int* dense = (int*)calloc((size_t)(nseed > 0 ? nseed : 1), sizeof(int));
+  double* mprev = (double*)malloc(sizeof(double) * (size_t)(nseed > 0 ? nseed : 1) * N);
+  memcpy(mprev, mseed, sizeof(double) * (size_t)nseed * N);
 #pragma omp parallel for schedule(dynamic, 1)
   for (int s = 0; s < nseed; ++s) {
     double* C = (double*)malloc(sizeof(double) * 5 * N);
@@ -601,6 +636,7 @@ void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, dou
       double* Vs = basis + (size_t)s * N * (a + 1);
       orc_bicgstab(H, W, C, b, x, tol_seed, maxit, &seed_it[s], &rr, a, Vs, &used[s]);
       nxt[s] = 0;
+      dense[s] = 1;
       /* A_proj = V^T A_seed V (row-major used x used) */
       int u = used[s];
       double* Av = (double*)malloc(sizeof(double) * N);
@@ -624,6 +660,22 @@ void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, dou
     memcpy(ms, x, sizeof(double) * N);
     free(C); free(b); free(x);
   }
+  /* seed cycling: each seed with a predecessor serves the accumulated basis
+   * (its own vectors, then the predecessor's accumulated ones), in seed order */
+  for (int s = 0; seed_prev && s < nseed; ++s) {
+    int q = seed_prev[s];
+    if (q < 0 || q >= s) continue;
+    double* C = (double*)malloc(sizeof(double) * 5 * N);
+    double* Vn = (double*)calloc((size_t)N * (a + 1), sizeof(double));
+    orc_coeffs(H, W, g2, dt, h, mprev + (size_t)s * N, NULL, NULL, C);
+    int u = orc_accumulate(H, W, C, used[s], basis + (size_t)s * N * (a + 1), used[q],
+                           basis + (size_t)q * N * (a + 1), a, Vn, aproj + (size_t)s * a * a);
+    memcpy(basis + (size_t)s * N * (a + 1), Vn, sizeof(double) * (size_t)N * (a + 1));
+    used[s] = u;
+    nxt[s] = 0;
+    dense[s] = 1;
+    free(C); free(Vn);
+  }
 #pragma omp parallel for schedule(dynamic, 1)
   for (int t = 0; t < ntgt; ++t) {
     double* C = (double*)malloc(sizeof(double) * 5 * N);
@@ -633,7 +685,7 @@ void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, dou
     double* mt = mtgt + (size_t)t * N;
     orc_coeffs(H, W, g2, dt, h, mt, NULL, NULL, C);
     orc_rhs(H, W, dt, h, mt, NULL, NULL, b);
-    if (mode == 0 && seed_solver == 1) {
+    if (mode == 0 && dense[target_seed[t]]) {
       int s = target_seed[t];
       orc_project_dense(N, used[s], basis + (size_t)s * N * (a + 1), aproj + (size_t)s * a * a, b,
                         NULL, x);
@@ -665,7 +717,7 @@ void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, dou
     memcpy(mt, x, sizeof(double) * N);
     free(C); free(b); free(x); free(r);
   }
-  free(basis); free(hess); free(aproj); free(used); free(nxt);
+  free(basis); free(hess); free(aproj); free(used); free(nxt); free(dense); free(mprev);
 }
 
 

@@ -79,7 +79,9 @@ def lib():
         L.orc_dense_lu_solve.argtypes = [_i, _pd, _pd, _pd]
         L.orc_dense_lu_solve.restype = _i
         L.orc_march_step.argtypes = [_i, _i, _d, _d, _d, _i, _pd, _i, _pd, _pi, _i, _d, _i,
-                                     _i, _d, _i, _i, _pi, _pi, _pd, _pi, _pd, _i, _i]
+                                     _i, _d, _i, _i, _pi, _pi, _pd, _pi, _pd, _i, _i, _pi]
+        L.orc_accumulate.argtypes = [_i, _i, _pd, _i, _pd, _i, _pd, _i, _pd, _pd]
+        L.orc_accumulate.restype = _i
         L.orc_bicgstab.argtypes = [_i, _i, _pd, _pd, _pd, _d, _i, _pi, _pd, _i, _pd, _pi]
         L.orc_bicgstab.restype = _i
         L.orc_project_dense.argtypes = [_i, _i, _pd, _pd, _pd, _pd, _pd]
@@ -259,6 +261,20 @@ def project_dense(V, Aproj, r, xinit=None):
     return x0, bool(rc)
 
 
+def accumulate(H, W, C, Vown, Vprev, cap_a):
+    """Seed cycling (Sec. 5.2): the new seed's basis rows Vown first, then the
+    previous accumulated rows Vprev, orthonormalised, capped at cap_a; returns
+    (V rows, A_proj = V A_seed V^T) with C the new seed's coefficients."""
+    N = H * W
+    Vo = np.ascontiguousarray(np.asarray(Vown, dtype=np.float64).reshape(-1, N))
+    Vp = np.ascontiguousarray(np.asarray(Vprev, dtype=np.float64).reshape(-1, N))
+    V = np.zeros(max(cap_a, 1) * N)
+    A = np.zeros(max(cap_a, 1) ** 2)
+    u = lib().orc_accumulate(H, W, _p(_f64(C)), Vo.shape[0], _p(Vo.reshape(-1)), Vp.shape[0],
+                             _p(Vp.reshape(-1)), cap_a, _p(V), _p(A))
+    return V.reshape(-1, N)[:u].copy(), A[: u * u].reshape(u, u).copy()
+
+
 def dense_lu_solve(A, b):
     """Dense LU with partial pivoting (tiny systems)."""
     n = A.shape[0]
@@ -300,12 +316,14 @@ SEED_GMRES, SEED_BICGSTAB = 0, 1
 
 def march_step(H, W, dt, h, g2, mseed, mtgt, target_seed, mode=MODE_PROJECTED,
                tol_seed=1e-10, m_seed=40, a=40, tol_ref=1e-8, m_ref=40, maxit=1000, picard=1,
-               seed_solver=SEED_GMRES):
+               seed_solver=SEED_GMRES, seed_prev=None):
     """One timestep of Sec. 2.3 + Sec. 3 for seeds and targets of one grid
     size (f = 0), with `picard` lagged-linearisation iterations; the seeds are
     solved by GMRES (Arnoldi basis) or BiCGSTAB (Sec. 3, Phase 1 as printed:
-    its key vectors, A_proj = V^T A_seed V).  ``mseed`` (nseed, N) and ``mtgt``
-    (ntgt, N) are updated in place from m^{n-1} to m^n."""
+    its key vectors, A_proj = V^T A_seed V); ``seed_prev`` (seed cycling, Sec.
+    5.2) links each seed to its predecessor (-1: none), whose accumulated basis
+    it extends (``accumulate``).  ``mseed`` (nseed, N) and ``mtgt`` (ntgt, N)
+    are updated in place from m^{n-1} to m^n."""
     assert mseed.dtype == np.float64 and mseed.flags["C_CONTIGUOUS"]
     assert mtgt.dtype == np.float64 and mtgt.flags["C_CONTIGUOUS"]
     ns, nt = mseed.shape[0], mtgt.shape[0]
@@ -315,7 +333,9 @@ def march_step(H, W, dt, h, g2, mseed, mtgt, target_seed, mode=MODE_PROJECTED,
     lib().orc_march_step(H, W, dt, h, g2, ns, _p(mseed), nt, _p(mtgt), _p(ts), mode,
                          tol_seed, m_seed, a, tol_ref, m_ref, maxit, _p(st.seed_iters),
                          _p(st.tgt_iters), _p(st.tgt_res), _p(st.tgt_status), _p(st.tgt_x0res),
-                         int(picard), int(seed_solver))
+                         int(picard), int(seed_solver),
+                         _p(np.ascontiguousarray(seed_prev, dtype=np.int32))
+                         if seed_prev is not None else None)
     return st
 
 

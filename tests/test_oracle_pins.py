@@ -515,3 +515,76 @@ def test_march_bicgstab_seeds(orc):
         Ct = orc.coeffs(H, W, wl.g2[0], dt, h, tg[t])
         res = np.linalg.norm(bt - orc.apply(H, W, Ct, x0)) / np.linalg.norm(bt)
         assert abs(res - stb[0].tgt_x0res[t]) <= 1e-9 * res
+
+
+def _span_gap(A, B):
+    # largest distance of a column of B from span(A) (A: orthonormal columns)
+    return np.linalg.norm(B - A @ (A.T @ B), axis=0).max()
+
+
+def test_accumulate_pins(orc):
+    # seed cycling (Sec. 5.2): the new seed's space first and whole, older
+    # vectors fill the rest up to the cap, nothing dependent is kept
+    H = W = 16
+    N = H * W
+    C, b, A = _hard_system(orc)
+    rng = np.random.default_rng(21)
+    Q, _ = np.linalg.qr(rng.normal(size=(N, 12)))
+    Vown, Vprev = Q[:, :5].T, Q[:, 5:12].T            # rows, independent spaces
+    V, Ap = orc.accumulate(H, W, C, Vown, Vprev, 40)
+    assert V.shape[0] == 12
+    assert np.abs(V @ V.T - np.eye(12)).max() <= 1e-13
+    assert _span_gap(V[:5].T, Vown.T) <= 1e-13                  # own space first
+    assert _span_gap(V.T, Q) <= 1e-13                            # everything kept
+    assert np.abs(Ap - V @ A @ V.T).max() <= 1e-12 * np.abs(A).max()
+    # a cap below the total keeps the own space and the first older vectors
+    Vc, _ = orc.accumulate(H, W, C, Vown, Vprev, 8)
+    assert Vc.shape[0] == 8 and _span_gap(Vc[:5].T, Vown.T) <= 1e-13
+    assert _span_gap(Vc.T, Vprev[:3].T) <= 1e-12
+    # the same space again adds nothing; a mixed one adds only what is new
+    Vs, _ = orc.accumulate(H, W, C, Vown, Vown[::-1] * 2.0, 40)
+    assert Vs.shape[0] == 5
+    Vm, _ = orc.accumulate(H, W, C, Vown, np.vstack([Vown[1] + Vown[2], Vprev[0]]), 40)
+    assert Vm.shape[0] == 6 and _span_gap(Vm.T, Vprev[:1].T) <= 1e-13
+    # Galerkin condition with the seed's operator, for the seed's own rhs
+    x0, sing = orc.project_dense(V, Ap, b)
+    assert not sing and np.abs(V @ (b - A @ x0)).max() <= 1e-11 * np.linalg.norm(b)
+
+
+def test_march_seed_cycling(orc):
+    # a chain of three seeds (0 <- 1 <- 2): the guesses of the targets of seed
+    # 2 come from the span of all three seeds' GMRES bases with seed 2's
+    # operator; the trajectory is the plain march's (all refined to 1e-12)
+    wl = synth.config(2, T=1000, ntargets=6)
+    g = wl.groups[0]
+    H, W, N = g.H, g.W, g.N
+    seeds = g.seeds.reshape(len(g.seeds), -1)[[0, 3, 6]]        # three channels 0 of three templates
+    tg = g.targets.reshape(len(g.targets), -1)[:6]
+    ts = np.array([0, 1, 2, 2, 1, 0], dtype=np.int32)
+    prev = np.array([-1, 0, 1], dtype=np.int32)
+    n = 400
+    dt, h, g2 = 1.0 / wl.T, 1.0 / H, float(wl.g2[n])
+    kw = dict(mode=0, tol_seed=1e-10, m_seed=40, a=40, tol_ref=1e-12, m_ref=40)
+    ms, mt = seeds.copy(), tg.copy()
+    st = orc.march_step(H, W, dt, h, g2, ms, mt, ts, seed_prev=prev, **kw)
+    ms0, mt0 = seeds.copy(), tg.copy()
+    orc.march_step(H, W, dt, h, g2, ms0, mt0, ts, mode=1, tol_seed=1e-10, m_seed=40, a=40,
+                   tol_ref=1e-12, m_ref=40)
+    assert np.abs(mt - mt0).max() <= 1e-9 * np.abs(mt0).max()
+    assert np.array_equal(ms, ms0)                              # seeds are solved as before
+    bases = []
+    for s in range(3):
+        Cs = orc.coeffs(H, W, g2, dt, h, seeds[s])
+        r = orc.gmres(H, W, Cs, orc.rhs(H, W, dt, h, seeds[s]), tol=1e-10, m=40, maxit=1000,
+                      capture=40)
+        bases.append(r.V[:r.a])
+    C2 = orc.coeffs(H, W, g2, dt, h, seeds[2])
+    A2 = np.stack([orc.apply(H, W, C2, e) for e in np.eye(N)], axis=1)
+    Q, _ = np.linalg.qr(np.vstack(bases).T)                      # any orthonormal basis of the span
+    for t in (2, 3):
+        bt = orc.rhs(H, W, dt, h, tg[t])
+        x0, _ = orc.project_dense(Q.T, Q.T @ A2 @ Q, bt)
+        Ct = orc.coeffs(H, W, g2, dt, h, tg[t])
+        res = np.linalg.norm(bt - orc.apply(H, W, Ct, x0)) / np.linalg.norm(bt)
+        assert abs(res - st.tgt_x0res[t]) <= 1e-12 * res
+    assert sum(b.shape[0] for b in bases) <= 40
