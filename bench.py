@@ -519,6 +519,32 @@ def main():
             "kernel_ms_per_march": {"seed_solve_and_store": tmb.seed_ms,
                                     "project_and_refine": tmb.refine_ms}}
         plb.close()
+        # seed cycling (Sec. 5.2): the seeds of each channel linked in template
+        # order, each serving its own basis followed by its predecessor's
+        cgroups = []
+        for k, g in enumerate(wl.groups):
+            C = g.channels
+            nk = len(g.seeds) // C
+            prev = np.array([(q - 1) * C + ch if q > 0 else -1 for q in range(nk) for ch in range(C)],
+                            dtype=np.int32)
+            cgroups.append(groups[k] + (prev,))
+        # the subspace capped at a = 20 as in Sec. 5.2 (its own context)
+        cctx = kp.Context(max_seeds=max(2 * window * wl.n_seed_planes, 1), max_a=20,
+                          max_n=max(g.N for g in wl.groups), precision=kp.PREC_FP64,
+                          block_threads=args.block_threads, blocks_per_sm=args.blocks_per_sm,
+                          smem_vectors=args.smem_vectors, reorth=args.reorth)
+        plc = kp.March(cctx, cgroups, mode=kp.MARCH_PROJECTED, **common)
+        t = timed(plc, max(1, args.steps // 2), 1)
+        reset()
+        stc, tmc = plc.run(0, NS, stats=True, timing=True)
+        out["seed_cycling"] = {
+            "value": world * nt_planes * NS * max(1, args.steps // 2) / t, "unit": "systems/s",
+            "iters_per_solve": sum(s.tgt_iters for s in stc) / (nt_planes * NS),
+            "kernel_ms_per_march": {"seed_solve_store_and_accumulate": tmc.seed_ms,
+                                    "project_and_refine": tmc.refine_ms},
+            "note": "one chain per channel over the template seeds, served basis capped at a = 20"}
+        plc.close()
+        cctx.close()
     if not args.no_baselines:
         modes = [("plain_x0_zero", kp.MARCH_PLAIN), ("plain_warm_start", kp.MARCH_WARM)]
         if not mixed:

@@ -322,6 +322,14 @@ typedef struct {
   double* m_seed;        /* device [nseed][H*W]: m^{n0} in, m^{n0+steps} out   */
   double* m_tgt;         /* device [ntgt][H*W]                                   */
   const int* tgt_seed;   /* host [ntgt]: seed (index within this group) per target */
+  /* Seed cycling with subspace expansion (Sec. 5.2: a new seed every h images,
+   * the subspace capped at a), optional: host [nseed] or NULL.  seed_prev[s]
+   * is the seed (index within this group, < s) whose basis seed s extends, or
+   * -1.  Every timestep, the basis that seed s serves its targets becomes its
+   * own basis vectors followed by the predecessor's served basis,
+   * orthonormalised, capped at max_a, with A_proj = V^T A_s V formed with seed
+   * s's operator (dense slot, LU per target).  FP64 plans. */
+  const int* seed_prev;
 } kp_group;
 
 typedef struct {

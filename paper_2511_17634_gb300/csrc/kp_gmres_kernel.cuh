@@ -138,6 +138,10 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
     const int cidx = p.factor ? parity_base + sysi : sysi;   // capture record (or seed slot)
     double* capV = capture ? p.capV + (size_t)cidx * (p.cap_a + 1) * p.cap_ld : nullptr;
     double* capH = capture ? p.capH + (size_t)cidx * (p.cap_a + 1) * p.cap_a : nullptr;
+    if (capture && p.capM) {                   // the slot's operator, for seed cycling
+      double* cm = p.capM + (size_t)cidx * p.cap_ld;
+      for (int pp = tid; pp < N; pp += NT) cm[pp] = d.mt[pp];
+    }
 
     // stencil coefficients (Sec. 2.3, listing after Eq. 11) from the lagged
     // field m~ (m^{n-1}, or the latest Picard iterate); zero where the

@@ -78,6 +78,8 @@ struct GmresParams {
   // first-cycle capture (seed solve); capV null = no capture
   double* capV;     // [nsys][cap_a + 1][cap_ld]
   double* capH;     // [nsys][(cap_a + 1) * cap_a] column-major, ld cap_a + 1
+  double* capM;     // seed cycling: [slot][cap_ld] the lagged field m~ of the
+                    // solve that filled the slot (its operator), or null
   CapMeta* capMeta; // [nsys]
   int cap_a;
   int cap_ld;
@@ -124,8 +126,9 @@ struct GmresParams {
   size_t score_stride;      // > 0: write the score of each solved timestep to
                             // d.score + tstep * score_stride and advance d.emb
   int picard;               // > 1: Picard iterations per system (FP64 solver)
-  int bicg;                 // 1: seed solves by BiCGSTAB (dense A_proj slots);
-                            // the FP64 solver's feature variant runs both sides
+  int bicg;                 // 1: seed solves by BiCGSTAB (dense A_proj slots)
+  int dense_slots;          // targets: slots may hold an explicit A_proj (BiCGSTAB
+                            // seeds, seed cycling): the feature variant projects
   int pdl;                  // programmatic launch, bit 0: let the stream's next launch
                             // start at once; bit 1: launched that way, wait for the
                             // prior grid (its completion and memory) before exiting
@@ -533,6 +536,34 @@ cudaError_t launch_apply(const SysDesc* sys, int nsys, int mode, cudaStream_t st
 cudaError_t launch_factor(const FactorParams& p, cudaStream_t st);
 cudaError_t launch_project_fp64(const ProjParams& p, int ept, int nt, cudaStream_t st);
 cudaError_t launch_advance(int* step, cudaStream_t st, int by = 1, int* zero = nullptr, int nzero = 1);
+
+// Seed cycling (kp_cycle.cu): per timestep of a launch and per seed, the
+// basis the seed serves its targets, written to separate output slots (the
+// solver's slots keep each seed's own basis): a seed without predecessor
+// serves its own slot as it is; a linked one serves its own basis vectors
+// followed by those of its predecessors, newest first, orthonormalised (CGS2)
+// and capped at max_a, with the explicit A_proj = V^T A_seed V (dense slot).
+struct CycleParams {
+  const SysDesc* sys;       // seed descriptors (H, W, h, dt, f), plan order
+  const int* prev;          // [ns] predecessor of each plan seed, or -1
+  int ns;
+  const double* slotV;      // [slots][max_a + 1][ld] the seeds' own bases
+  const SlotMeta* slotMeta;
+  const double* slotR;      // [slots][(max_a + 1) * max_a]
+  const double* slotM;      // [slots][ld] lagged field of each slot's seed solve
+  double* outV;             // served bases, same layout
+  SlotMeta* outMeta;
+  double* outR;
+  int max_a, ld;
+  const int* step;          // timesteps *step + step_offset .. + win - 1, below step_end
+  int step_offset, win;
+  const int* step_end;
+  const double* g2_sched;
+  int slot_sets;            // slot of seed s at t: (t mod slot_sets) * ns + s
+};
+constexpr int kCycleThreads = 256;
+constexpr int kCycleMaxN = 4096;
+cudaError_t launch_cycle(const CycleParams& p, int nmax, int grid, cudaStream_t st);   // nmax: largest seed grid
 
 // 3x3 convolutions on the tensor cores (kp_conv_tc.cu): padded-column BF16
 // activation layout [B][chunks of 8 channels][Rp rows][8], pixel (i, j) at row

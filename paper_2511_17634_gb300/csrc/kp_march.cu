@@ -92,6 +92,14 @@ struct kp_march_plan {
   int ncls = 1;
   TClass cls[2];
   size_t score_stride = 0;                   // elements per timestep of the score output
+  // seed cycling: predecessor of each plan seed (device), the lagged field of
+  // each slot's seed solve, and the served slots the targets read
+  bool cycling = false;
+  int* cyc_prev = nullptr;                   // [ns]
+  double* slotM = nullptr;                   // [max_seeds][max_n]
+  double* cycV = nullptr;                    // [max_seeds][max_a + 1][max_n]
+  double* cycR = nullptr;                    // [max_seeds][(max_a + 1) * max_a]
+  kp::SlotMeta* cycMeta = nullptr;           // [max_seeds]
 };
 
 namespace {
@@ -136,6 +144,13 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset,
   g.err = P->err;
   g.picard = P->opt.picard;
   g.bicg = P->opt.seed_solver == KP_SEED_BICGSTAB;
+  g.dense_slots = !seeds && (g.bicg || P->cycling);
+  if (seeds) g.capM = P->slotM;
+  if (!seeds && P->cycling) {                // targets read the served slots
+    g.slotV = P->cycV;
+    g.slotMeta = P->cycMeta;
+    g.slotR = P->cycR;
+  }
   if (P->K > 1) {
     // window: descriptors and slot sets chosen per timestep on the device
     g.win = P->K;
@@ -186,6 +201,36 @@ cudaError_t launch_solver(kp_march_plan* P, const kp::GmresParams& g, const kp::
   return kp::launch_solver(g, sh, P->mixed, st);
 }
 
+// Seed cycling for the timesteps of the seed launch with the same offset
+// (window: K of them; per-timestep scheme: one): the served slots.
+cudaError_t launch_cycle(kp_march_plan* P, int offset, cudaStream_t st) {
+  if (!P->cycling) return cudaSuccess;
+  kp_ctx* c = P->ctx;
+  kp::CycleParams q{};
+  q.sys = P->desc[0];
+  q.prev = P->cyc_prev;
+  q.ns = P->ns;
+  q.slotV = c->slotV;
+  q.slotMeta = c->slotMeta;
+  q.slotR = c->slotR;
+  q.slotM = P->slotM;
+  q.outV = P->cycV;
+  q.outMeta = P->cycMeta;
+  q.outR = P->cycR;
+  q.max_a = c->opt.max_a;
+  q.ld = c->opt.max_n;
+  q.step = P->step;
+  q.step_offset = offset;
+  q.win = P->K;
+  q.step_end = P->step + 1;
+  q.g2_sched = P->g2;
+  q.slot_sets = P->K > 1 ? 2 * P->K : 0;
+  int nmax = 0;
+  for (const kp_group& g : P->groups)
+    if (g.nseed) nmax = std::max(nmax, g.H * g.W);
+  return kp::launch_cycle(q, nmax, P->K * P->ns, st);
+}
+
 // Target step n and seed step n+1 for parity p = n & 1.  With ev (timing
 // mode) the two launches run one after the other between events
 // ev[0..1] (seeds) and ev[2..3] (targets); otherwise on two branches.
@@ -203,6 +248,7 @@ kp_status enqueue_step(kp_march_plan* P, int par, cudaEvent_t* ev, int* launches
     kp::GmresParams g = solver_params(P, true, par, 1);
     if (e == cudaSuccess) e = launch_solver(P, g, P->shS, sst);
     ++nl;
+    if (P->cycling && e == cudaSuccess) { e = launch_cycle(P, 1, sst); ++nl; }
     if (ev && e == cudaSuccess) e = cudaEventRecord(ev[1], sst);
   }
   if (P->nt > 0 && e == cudaSuccess) {
@@ -248,6 +294,9 @@ kp_status enqueue_window(kp_march_plan* P, cudaEvent_t* ev, int* launches) {
     g.pdl = pdl ? 1 : 0;                     // signal at entry
     if (e == cudaSuccess) e = launch_solver(P, g, P->shS, P->st);
     ++nl;
+    // seed cycling of the next window: timed with the seeds; otherwise after
+    // the target launch, which keeps its programmatic start on the seeds
+    if (ev && P->cycling && e == cudaSuccess) { e = launch_cycle(P, P->K, P->st); ++nl; }
     if (ev && e == cudaSuccess) e = cudaEventRecord(ev[1], P->st);
   }
   if (P->nt > 0 && e == cudaSuccess) {
@@ -262,6 +311,7 @@ kp_status enqueue_window(kp_march_plan* P, cudaEvent_t* ev, int* launches) {
     }
     if (ev && e == cudaSuccess) e = cudaEventRecord(ev[3], P->st);
   }
+  if (!ev && P->ns > 0 && P->cycling && e == cudaSuccess) { e = launch_cycle(P, P->K, P->st); ++nl; }
   if (e == cudaSuccess) { e = kp::launch_advance(P->step, P->st, P->K, P->queue, P->ncls); ++nl; }
   if (launches) *launches = nl;
   return e == cudaSuccess ? KP_OK : kp::cuda_error(P->ctx, e, "march window enqueue");
@@ -286,6 +336,11 @@ kp_status kp_march_destroy(kp_march_plan* P) {
   cudaFree(P->acc);
   cudaFree(P->spill);
   cudaFree(P->spill32);
+  cudaFree(P->cyc_prev);
+  cudaFree(P->slotM);
+  cudaFree(P->cycV);
+  cudaFree(P->cycR);
+  cudaFree(P->cycMeta);
   cudaFree(P->perm);
   cudaFree(P->Bb);
   cudaFree(P->Cp);
@@ -369,6 +424,28 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
     return kp::set_error(c, KP_ERR_UNSUPPORTED, "BiCGSTAB seeds need the FP64 one-block solver, "
                          "one Picard iteration and m_seed >= 4");
   }
+  // seed cycling: predecessors in plan seed indices
+  std::vector<int> cyc_prev(std::max(P->ns, 1), -1);
+  {
+    int base = 0;
+    for (int gi = 0; gi < ngroups; ++gi) {
+      const kp_group& g = groups[gi];
+      for (int sidx = 0; sidx < g.nseed; ++sidx) {
+        const int q = g.seed_prev ? g.seed_prev[sidx] : -1;
+        if (q < -1 || q >= sidx) {
+          kp_march_destroy(P);
+          return kp::set_error(c, KP_ERR_ARG, "group %d seed %d: predecessor %d not in -1..%d", gi,
+                               sidx, q, sidx - 1);
+        }
+        if (q >= 0) { cyc_prev[base + sidx] = base + q; P->cycling = true; }
+      }
+      base += g.nseed;
+    }
+  }
+  if (P->cycling && (P->mixed || P->shS.cs || P->shT.cs)) {
+    kp_march_destroy(P);
+    return kp::set_error(c, KP_ERR_UNSUPPORTED, "seed cycling needs the FP64 one-block solver");
+  }
   if (o.score && (P->mixed || P->shT.cs)) {
     kp_march_destroy(P);
     return kp::set_error(c, KP_ERR_UNSUPPORTED, "score extraction needs the FP64 one-block solver");
@@ -439,6 +516,19 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
     if (e == cudaSuccess) e = dmalloc(&P->done, nt);
   }
   if (e == cudaSuccess) e = dmalloc(&P->acc, o.T);
+  if (e == cudaSuccess && P->cycling) {
+    const size_t slots = (size_t)c->opt.max_seeds, a = (size_t)c->opt.max_a, n = (size_t)c->opt.max_n;
+    e = dmalloc(&P->cyc_prev, (size_t)P->ns);
+    if (e == cudaSuccess) e = dmalloc(&P->slotM, slots * n);
+    if (e == cudaSuccess) e = dmalloc(&P->cycV, slots * (a + 1) * n);
+    if (e == cudaSuccess) e = dmalloc(&P->cycR, slots * (a + 1) * a);
+    if (e == cudaSuccess) e = dmalloc(&P->cycMeta, slots);
+    if (e == cudaSuccess)   // no slot is served before its first timestep
+      e = cudaMemset(P->cycMeta, 0xff, slots * sizeof(kp::SlotMeta));
+    if (e == cudaSuccess)
+      e = cudaMemcpy(P->cyc_prev, cyc_prev.data(), (size_t)P->ns * sizeof(int), cudaMemcpyHostToDevice);
+  }
+
   // one Krylov workspace per branch: seed blocks first, then target blocks
   size_t spS = 0, spT = 0;
   const int csS = P->shS.cs ? P->shS.cs : 1, csT = P->shT.cs ? P->shT.cs : 1;
@@ -675,8 +765,9 @@ kp_status kp_march_run(kp_march_plan* P, int n0, int steps, kp_step_stats* stats
     kp::GmresParams g = solver_params(P, true, 1 - q0, 0);
     if (timing) e = cudaEventRecord(ev[(size_t)nwin * 4], P->st);
     if (e == cudaSuccess) e = launch_solver(P, g, P->shS, P->st);
-    if (timing && e == cudaSuccess) e = cudaEventRecord(ev[(size_t)nwin * 4 + 1], P->st);
     ++launches;
+    if (P->cycling && e == cudaSuccess) { e = launch_cycle(P, 0, P->st); ++launches; }
+    if (timing && e == cudaSuccess) e = cudaEventRecord(ev[(size_t)nwin * 4 + 1], P->st);
   }
   for (int k = 0; k < nwin && e == cudaSuccess && r == KP_OK; ++k) {
     const int par = K > 1 ? 0 : (n0 + k) & 1;

@@ -273,7 +273,7 @@ SEED_GMRES, SEED_BICGSTAB = 0, 1
 class _Group(ctypes.Structure):
     _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("nseed", ctypes.c_int),
                 ("ntgt", ctypes.c_int), ("m_seed", ctypes.c_void_p), ("m_tgt", ctypes.c_void_p),
-                ("tgt_seed", ctypes.c_void_p)]
+                ("tgt_seed", ctypes.c_void_p), ("seed_prev", ctypes.c_void_p)]
 
 
 class _MarchOpts(ctypes.Structure):
@@ -314,7 +314,9 @@ def _march_lib():
 class March:
     """Time march over groups of (seed, target) channel planes of one grid size
     each.  groups: list of (seeds (ns, N) tensor, targets (nt, N) tensor,
-    target_seed int array, H, W).  The tensors are updated in place by run()."""
+    target_seed int array, H, W[, seed_prev int array]); seed_prev links each
+    seed to the one whose basis it extends (seed cycling, -1: none).  The
+    tensors are updated in place by run()."""
 
     def __init__(self, ctx, groups, T, g2, mode=MARCH_PROJECTED, tol_seed=1e-10, tol=1e-8,
                  m_seed=40, m=40, maxit=1000, use_graph=True, window=0, target_blocks=0,
@@ -323,9 +325,15 @@ class March:
         self.ctx = ctx
         self._keep = []
         arr = (_Group * len(groups))()
-        for k, (s, t, ts, H, W) in enumerate(groups):
+        for k, grp in enumerate(groups):
+            s, t, ts, H, W = grp[:5]
+            sp = grp[5] if len(grp) > 5 else None
             ts = np.ascontiguousarray(ts, dtype=np.int32)
             self._keep += [s, t, ts]
+            if sp is not None:
+                sp = np.ascontiguousarray(sp, dtype=np.int32)
+                self._keep.append(sp)
+                arr[k].seed_prev = sp.ctypes.data
             arr[k].H, arr[k].W = H, W
             arr[k].nseed, arr[k].ntgt = s.shape[0], t.shape[0]
             arr[k].m_seed = s.data_ptr() if s.numel() else None

@@ -324,3 +324,69 @@ def test_march_bicgstab_seeds_rejected_combinations(kp):
     mctx = kp.Context(max_seeds=8, max_a=wl.a, max_n=g.N, precision=kp.PREC_MIXED)
     with pytest.raises(RuntimeError):
         kp.March(mctx, grp, wl.T, wl.g2, mode=0, seed_solver=kp.SEED_BICGSTAB)
+
+
+def _chains(ntemplates, channels):
+    # seed k*channels + ch extends seed (k-1)*channels + ch: one chain per channel
+    return np.array([(k - 1) * channels + ch if k > 0 else -1
+                     for k in range(ntemplates) for ch in range(channels)], dtype=np.int32)
+
+
+@pytest.mark.parametrize("window,solver", [(1, 0), (0, 0), (0, 1)])
+def test_march_seed_cycling_matches_oracle(kp, orc, window, solver):
+    # seed cycling (Sec. 5.2): every seed with a predecessor serves its own
+    # basis followed by the predecessor's served one, with its own A_proj
+    g = synth.make_group(91, 12, 10, 2, 3, 6, tag=3)
+    T = 12
+    g2 = synth.beta_schedule(T)
+    prev = _chains(3, 2)
+    ctx = kp.Context(max_seeds=48, max_a=20, max_n=g.N)
+    s = torch.as_tensor(g.seeds.reshape(len(g.seeds), -1).copy(), device="cuda")
+    t = torch.as_tensor(g.targets.reshape(len(g.targets), -1).copy(), device="cuda")
+    mr = kp.March(ctx, [(s, t, g.target_seed, g.H, g.W, prev)], T, g2, mode=0, tol_seed=1e-12,
+                  tol=1e-12, m_seed=20, m=20, maxit=1000, window=window, seed_solver=solver)
+    stats, _ = mr.run(0, T, stats=True)
+    torch.cuda.synchronize()
+    oms, omt, ost = orc.march(g.H, g.W, T, g2, g.seeds, g.targets, g.target_seed, mode=0,
+                              tol_seed=1e-12, m_seed=20, a=20, tol_ref=1e-12, m_ref=20,
+                              seed_solver=solver, seed_prev=prev)
+    assert np.abs(t.cpu().numpy() - omt).max() <= 1e-9 * np.abs(omt).max()
+    assert np.abs(s.cpu().numpy() - oms).max() <= 1e-9 * np.abs(oms).max()
+    assert all(x.not_converged == 0 and x.max_rel_res <= 1e-12 for x in stats)
+    gpu_it = np.array([x.tgt_iters for x in stats])
+    orc_it = np.array([x.tgt_iters.sum() for x in ost])
+    assert np.abs(gpu_it - orc_it).max() <= len(g.targets)
+
+
+def test_march_seed_cycling_32x32_windowed(kp, orc):
+    # the benchmark's workload with one chain of the ten template seeds per
+    # channel, windows of 4, against the oracle's cycling march
+    wl = synth.config(2, T=1000, ntargets=40)
+    g = wl.groups[0]
+    steps = 8
+    prev = _chains(10, 3)
+    ctx = kp.Context(max_seeds=8 * wl.n_seed_planes, max_a=wl.a, max_n=g.N)
+    s = torch.as_tensor(g.seeds.reshape(len(g.seeds), -1).copy(), device="cuda")
+    t = torch.as_tensor(g.targets.reshape(len(g.targets), -1).copy(), device="cuda")
+    mr = kp.March(ctx, [(s, t, g.target_seed, g.H, g.W, prev)], wl.T, wl.g2, mode=0,
+                  tol_seed=wl.tol_seed, tol=wl.tol, m_seed=wl.m_seed, m=wl.m, window=4)
+    stats, _ = mr.run(0, steps, stats=True)
+    torch.cuda.synchronize()
+    assert all(x.max_rel_res <= 1e-8 and x.not_converged == 0 for x in stats)
+    oms, omt, ost = orc.march(g.H, g.W, wl.T, wl.g2, g.seeds, g.targets, g.target_seed, steps=steps,
+                              tol_seed=wl.tol_seed, m_seed=wl.m_seed, a=wl.a, tol_ref=wl.tol,
+                              m_ref=wl.m, seed_prev=prev)
+    assert np.abs(t.cpu().numpy() - omt).max() <= 1e-6 * np.abs(omt).max()
+    gpu_it = np.array([x.tgt_iters for x in stats])
+    orc_it = np.array([x.tgt_iters.sum() for x in ost])
+    assert np.abs(gpu_it - orc_it).max() <= len(g.targets)
+
+
+def test_march_seed_cycling_rejects_bad_links(kp):
+    g = synth.make_group(91, 12, 10, 2, 3, 6, tag=3)
+    ctx = kp.Context(max_seeds=48, max_a=20, max_n=g.N)
+    s = torch.as_tensor(g.seeds.reshape(len(g.seeds), -1).copy(), device="cuda")
+    t = torch.as_tensor(g.targets.reshape(len(g.targets), -1).copy(), device="cuda")
+    bad = np.array([-1, 0, 2, 1, 2, 3], dtype=np.int32)           # seed 2 names itself
+    with pytest.raises(RuntimeError):
+        kp.March(ctx, [(s, t, g.target_seed, g.H, g.W, bad)], 12, synth.beta_schedule(12))
