@@ -147,7 +147,28 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
     // field m~ (m^{n-1}, or the latest Picard iterate); zero where the
     // neighbour lies outside the grid
     double cE[EPT], cW[EPT], cN[EPT], cS[EPT];
+    const bool drift = d.fx != nullptr || d.fy != nullptr;
     auto set_coeffs = [&](const double* mtl) {
+      if (!drift) {                              // f = 0 (the method's systems): two terms each
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          const int pp = tid + k * NT;
+          cE[k] = cW[k] = cN[k] = cS[k] = 0.0;
+          if (pp < N) {
+            const int i = pp / H, j = pp - i * H;
+            const double mE = (i + 1 < W) ? mtl[pp + H] : 0.0;
+            const double mW = (i > 0) ? mtl[pp - H] : 0.0;
+            const double mN = (j + 1 < H) ? mtl[pp + 1] : 0.0;
+            const double mS = (j > 0) ? mtl[pp - 1] : 0.0;
+            const double dmx = mE - mW, dmy = mN - mS;
+            if (i + 1 < W) cE[k] = fma(-ee, dmx, -cc);
+            if (i > 0) cW[k] = fma(ee, dmx, -cc);
+            if (j + 1 < H) cN[k] = fma(-ee, dmy, -cc);
+            if (j > 0) cS[k] = fma(ee, dmy, -cc);
+          }
+        }
+        return;
+      }
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
         const int pp = tid + k * NT;
@@ -227,9 +248,12 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
         const int a = mt.a;
         const int nv = mt.lsq ? a + 1 : a;
         const double* V = p.slotV + (size_t)sl * (p.max_a + 1) * p.slot_ld;
-        double bv[EPT];
+        double bv[EPT];                          // b / bsc: the scale goes on the sums
 #pragma unroll
-        for (int k = 0; k < EPT; ++k) bv[k] = bval(tid + k * NT);
+        for (int k = 0; k < EPT; ++k) {
+          const int pp = tid + k * NT;
+          bv[k] = pp < N ? d.b[pp] : 0.0;
+        }
         block_partials<NT>(nv, [&](int i) {
           const double* vi = V + (size_t)i * p.slot_ld;
           double s = 0.0;
@@ -241,7 +265,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
           return s;
         }, sm.red);
         if (warp == 0) {
-          for (int i = lane; i < nv; i += 32) sm.hb[i] = cross_warp<NT>(sm.red, i);
+          for (int i = lane; i < nv; i += 32) sm.hb[i] = bsc * cross_warp<NT>(sm.red, i);
           __syncwarp();
           const double* R = p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a;
           if (FEAT && mt.dense) {
@@ -607,13 +631,14 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
         double s = 0.0;
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
-          const double bv = bval(tid + k * NT);
+          const int pp = tid + k * NT;
+          const double bv = pp < N ? d.b[pp] : 0.0;     // ||b|| = bsc ||b / bsc||
           s += (i == 0) ? bv * bv : w[k] * w[k];
         }
         return s;
       }, sm.red);
       if (tid == 0) {
-        sm.sc[0] = sqrt(cross_warp<NT>(sm.red, 0));
+        sm.sc[0] = fabs(bsc) * sqrt(cross_warp<NT>(sm.red, 0));
         sm.sc[1] = sqrt(cross_warp<NT>(sm.red, 1));
       }
       __syncthreads();
@@ -648,7 +673,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
         auto givens_step = [&](int j, double hn2) {
           const double ihn = hn2 > 0.0 ? rsqrt(hn2) : 0.0;
           const double hn = hn2 * ihn;
-          const int b = !(hn > 1e-14 * sqrt(sm.sc[2]));
+          const int b = !(hn2 > 1e-28 * sm.sc[2]);  // h_{j+1,j} <= 1e-14 ||A v_j||
           sm.Hr[j + j * ld] += cd;                 // H_A = H_{A - cd I} + cd I
           sm.Hr[(j + 1) + j * ld] = hn;
           if (capture && cycle == 0 && j < p.cap_a) {
