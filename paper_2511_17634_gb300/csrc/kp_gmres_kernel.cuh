@@ -730,9 +730,15 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
             if (lane == 0) {
               const double ww0 = sm.hb[nh];
               sm.sc[2] = ww0;
+              // ||w_1||^2 = ||w||^2 - ||h||^2, accurate to a few ulps of ||w||^2
+              // while at most half of it is removed; otherwise the second pass
+              // measures ||w_1||^2 in its reduction
+              const int big = ww0 - sq < 0.5 * ww0;
+              sm.fl[4] = big;
+              sm.sc[4] = ww0 - sq;
               // second pass always (CGS2), or only when the first removed over
-              // half of ||w||^2 (DGKS); without it ||w_1||^2 = ||w||^2 - ||h||^2
-              const int pass2 = (p.reorth == 0) || (ww0 - sq < 0.5 * ww0);
+              // half of ||w||^2 (DGKS)
+              const int pass2 = (p.reorth == 0) || big;
               sm.fl[0] = pass2;
               if (!pass2) givens_step(j, ww0 - sq);
             }
@@ -745,19 +751,21 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
             for (int k = 0; k < EPT; ++k) w[k] = fma(-hi, vi[tid + k * NT], w[k]);
           }
           if (sm.fl[0]) {
-            // CGS pass 2 (reorthogonalisation) with ||w_1||^2 in the same reduction;
+            // CGS pass 2 (reorthogonalisation), with ||w_1||^2 in the same
+            // reduction when pass 1 removed most of ||w||^2;
             // ||w_2||^2 = ||w_1||^2 - ||h_2||^2 (h_2 = O(eps) after pass 1), checked
-            block_partials<NT>(nh + 1, dots, sm.red);
+            const int big = sm.fl[4];
+            block_partials<NT>(big ? nh + 1 : nh, dots, sm.red);
             if (warp == 0) {
               double sq = 0.0;
-              for (int i = lane; i <= nh; i += 32) {
+              for (int i = lane; i < (big ? nh + 1 : nh); i += 32) {
                 const double s = cross_warp<NT>(sm.red, i);
                 sm.hb[i] = s;
                 if (i < nh) { sm.Hr[i + j * ld] += s; sq += s * s; }
               }
               sq = warp_sum(sq);
               if (lane == 0) {
-                const double ww1 = sm.hb[nh];
+                const double ww1 = big ? sm.hb[nh] : sm.sc[4];
                 const int exact = sq > 0.25 * ww1;     // large correction: recompute the norm
                 sm.fl[3] = exact;
                 if (!exact) givens_step(j, ww1 - sq);
