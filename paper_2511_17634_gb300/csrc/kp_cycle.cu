@@ -139,14 +139,16 @@ __global__ void __launch_bounds__(kCycleThreads) cycle_kernel(const CycleParams 
   __syncthreads();                             // kept vectors complete for the stencil
 
   // A_proj = V^T A_s V with the seed's operator (Sec. 2.3 coefficients from
-  // the lagged field of its solve, zero outside the grid)
+  // the lagged field of its solve, zero outside the grid), divided by the
+  // right-hand-side scale as the solvers apply it
   const double* mt = p.slotM + (size_t)ss * p.ld;
   const double hh = d.h;
   const double g2 = p.g2_sched[t];
-  const double cc = g2 / (2.0 * hh * hh);
-  const double ee = g2 / (8.0 * hh * hh);
-  const double cd = 1.0 / d.dt + 2.0 * g2 / (hh * hh);
-  const double i2h = 1.0 / (2.0 * hh);
+  const double osc = p.b_scale != 0.0 ? 1.0 / p.b_scale : 1.0;
+  const double cc = g2 / (2.0 * hh * hh) * osc;
+  const double ee = g2 / (8.0 * hh * hh) * osc;
+  const double cd = (1.0 / d.dt + 2.0 * g2 / (hh * hh)) * osc;
+  const double i2h = osc / (2.0 * hh);
   double* R = p.outR + (size_t)ss * rstride;
   for (int kc = 0; kc < cnt; ++kc) {
     const double* v = Vo + (size_t)kc * p.ld;

@@ -130,10 +130,14 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
     const int H = d.H, W = d.W, N = H * W;
     const double hh = d.h;
     const double g2 = p.step ? p.g2_sched[tstep] : d.g2;
-    const double cc = g2 / (2.0 * hh * hh);
-    const double ee = g2 / (8.0 * hh * hh);
-    const double cd = 1.0 / d.dt + 2.0 * g2 / (hh * hh);
-    const double i2h = 1.0 / (2.0 * hh);
+    // the system is solved as (A / s) x = b / s with s = b_scale (the march's
+    // 1/dt): the right-hand side is read as stored and the scale goes on the
+    // four operator constants, once per solve
+    const double osc = bsc != 0.0 ? 1.0 / bsc : 1.0;
+    const double cc = g2 / (2.0 * hh * hh) * osc;
+    const double ee = g2 / (8.0 * hh * hh) * osc;
+    const double cd = (1.0 / d.dt + 2.0 * g2 / (hh * hh)) * osc;
+    const double i2h = osc / (2.0 * hh);
     bool capture = p.capV != nullptr;          // first solve of the timestep only
     const int cidx = p.factor ? parity_base + sysi : sysi;   // capture record (or seed slot)
     double* capV = capture ? p.capV + (size_t)cidx * (p.cap_a + 1) * p.cap_ld : nullptr;
@@ -199,7 +203,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
         if (pp < N) {
           const int pe = min(pp + H, N - 1), pw = max(pp - H, 0);
           const int pn = min(pp + 1, N - 1), ps = max(pp - 1, 0);
-          double t = fma(-cd, v[pp], d.b[pp] * bsc);
+          double t = fma(-cd, v[pp], d.b[pp]);
           t = fma(-cE[k], v[pe], t);
           t = fma(-cW[k], v[pw], t);
           t = fma(-cN[k], v[pn], t);
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
         }
       }
     };
-    auto bval = [&](int pp) { return (pp < N) ? d.b[pp] * bsc : 0.0; };
+    auto bval = [&](int pp) { return (pp < N) ? d.b[pp] : 0.0; };
 
     // initial guess -> shared memory
     unsigned long long proj_flops = 0;
@@ -248,7 +252,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
         const int a = mt.a;
         const int nv = mt.lsq ? a + 1 : a;
         const double* V = p.slotV + (size_t)sl * (p.max_a + 1) * p.slot_ld;
-        double bv[EPT];                          // b / bsc: the scale goes on the sums
+        double bv[EPT];
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
           const int pp = tid + k * NT;
@@ -265,7 +269,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
           return s;
         }, sm.red);
         if (warp == 0) {
-          for (int i = lane; i < nv; i += 32) sm.hb[i] = bsc * cross_warp<NT>(sm.red, i);
+          for (int i = lane; i < nv; i += 32) sm.hb[i] = cross_warp<NT>(sm.red, i);
           __syncwarp();
           const double* R = p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a;
           if (FEAT && mt.dense) {
@@ -632,13 +636,13 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
           const int pp = tid + k * NT;
-          const double bv = pp < N ? d.b[pp] : 0.0;     // ||b|| = bsc ||b / bsc||
+          const double bv = pp < N ? d.b[pp] : 0.0;
           s += (i == 0) ? bv * bv : w[k] * w[k];
         }
         return s;
       }, sm.red);
       if (tid == 0) {
-        sm.sc[0] = fabs(bsc) * sqrt(cross_warp<NT>(sm.red, 0));
+        sm.sc[0] = sqrt(cross_warp<NT>(sm.red, 0));
         sm.sc[1] = sqrt(cross_warp<NT>(sm.red, 1));
       }
       __syncthreads();

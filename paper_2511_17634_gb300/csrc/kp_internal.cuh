@@ -559,6 +559,7 @@ struct CycleParams {
   int step_offset, win;
   const int* step_end;
   const double* g2_sched;
+  double b_scale;           // the solvers' right-hand-side scale: A_proj of A / b_scale
   int slot_sets;            // slot of seed s at t: (t mod slot_sets) * ns + s
 };
 constexpr int kCycleThreads = 256;

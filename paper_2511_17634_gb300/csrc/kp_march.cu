@@ -224,6 +224,7 @@ cudaError_t launch_cycle(kp_march_plan* P, int offset, cudaStream_t st) {
   q.win = P->K;
   q.step_end = P->step + 1;
   q.g2_sched = P->g2;
+  q.b_scale = (double)P->opt.T;                 // as the solvers' b_scale
   q.slot_sets = P->K > 1 ? 2 * P->K : 0;
   int nmax = 0;
   for (const kp_group& g : P->groups)
