@@ -73,10 +73,13 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
   const int base = rank * SL;
   const double hh = d.h;
   const double g2 = p.step ? p.g2_sched[tstep] : d.g2;
-  const double cc = g2 / (2.0 * hh * hh);
-  const double ee = g2 / (8.0 * hh * hh);
-  const double cd = 1.0 / d.dt + 2.0 * g2 / (hh * hh);
-  const double i2h = 1.0 / (2.0 * hh);
+  // solved as (A / s) x = b / s with s = b_scale: the scale goes on the
+  // operator constants once per solve instead of on every point of b
+  const double osc = bsc != 0.0 ? 1.0 / bsc : 1.0;
+  const double cc = g2 / (2.0 * hh * hh) * osc;
+  const double ee = g2 / (8.0 * hh * hh) * osc;
+  const double cd = (1.0 / d.dt + 2.0 * g2 / (hh * hh)) * osc;
+  const double i2h = osc / (2.0 * hh);
   const float ccf = (float)cc;
   const bool capture = p.capV32 != nullptr;
   const int cidx = p.factor ? parity_base + sysi : sysi;
@@ -124,7 +127,7 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
         const double xW = (msk[k] & 2u) ? (l - H >= 0 ? xs[l - H] : xs_prev[l - H + SL]) : 0.0;
         const double xN = (msk[k] & 4u) ? xs[l + 1] : 0.0;
         const double xS = (msk[k] & 8u) ? xs[l - 1] : 0.0;
-        double t = fma(-cd, xs[l], d.b[base + l] * bsc);
+        double t = fma(-cd, xs[l], d.b[base + l]);
         t = fma(-cEx[k], xE - xW, t);
         t = fma(-cNy[k], xN - xS, t);
         out[k] = fma(c2, xW + xS, t);
@@ -148,7 +151,7 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
       }
     }
   };
-  auto bval = [&](int l) { return (l < SL) ? d.b[base + l] * bsc : 0.0; };
+  auto bval = [&](int l) { return (l < SL) ? d.b[base + l] : 0.0; };
   int buf = 0;
   // cluster-wide sums of nv values whose per-warp partials are in red;
   // result in hb[0..nv) of every CTA (identical, rank order)
@@ -470,7 +473,7 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
     if (l < SL) {
       d.x[base + l] = xs[l];
       if (p.bnext)
-        p.bnext[(size_t)sysi * p.bnext_ld + base + l] = __float2bfloat16_rn((float)(xs[l] * bsc));
+        p.bnext[(size_t)sysi * p.bnext_ld + base + l] = __float2bfloat16_rn((float)xs[l]);
     }
   }
   if (tid == 0 && rank == 0) {

@@ -90,11 +90,15 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
     const int H = d.H, W = d.W, N = H * W;
     const double hh = d.h;
     const double g2 = p.step ? p.g2_sched[tstep] : d.g2;
-    const double cc = g2 / (2.0 * hh * hh);
-    const double ee = g2 / (8.0 * hh * hh);
-    const double cd = 1.0 / d.dt + 2.0 * g2 / (hh * hh);
-    const double i2h = 1.0 / (2.0 * hh);
+    // solved as (A / s) x = b / s with s = b_scale: the scale goes on the
+    // operator constants once per solve instead of on every point of b
+    const double osc = bsc != 0.0 ? 1.0 / bsc : 1.0;
+    const double cc = g2 / (2.0 * hh * hh) * osc;
+    const double ee = g2 / (8.0 * hh * hh) * osc;
+    const double cd = (1.0 / d.dt + 2.0 * g2 / (hh * hh)) * osc;
+    const double i2h = osc / (2.0 * hh);
     const float ccf = (float)cc;
+    const bool drift = d.fx != nullptr || d.fy != nullptr;
     const bool capture = p.capV32 != nullptr;
     const int cidx = p.factor ? parity_base + sysi : sysi;
     float* capV = capture ? p.capV32 + (size_t)cidx * (p.cap_a + 1) * p.cap_ld : nullptr;
@@ -117,10 +121,15 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
         const double mW = (i > 0) ? d.mt[pp - H] : 0.0;
         const double mN = (j + 1 < H) ? d.mt[pp + 1] : 0.0;
         const double mS = (j > 0) ? d.mt[pp - 1] : 0.0;
-        const double fxp = d.fx ? d.fx[pp] : 0.0;
-        const double fyp = d.fy ? d.fy[pp] : 0.0;
-        qx = fxp * i2h - ee * (mE - mW);
-        qy = fyp * i2h - ee * (mN - mS);
+        if (drift) {
+          const double fxp = d.fx ? d.fx[pp] : 0.0;
+          const double fyp = d.fy ? d.fy[pp] : 0.0;
+          qx = fxp * i2h - ee * (mE - mW);
+          qy = fyp * i2h - ee * (mN - mS);
+        } else {                                // f = 0: the method's systems
+          qx = -ee * (mE - mW);
+          qy = -ee * (mN - mS);
+        }
         msk[k] = (i + 1 < W ? 1u : 0u) | (i > 0 ? 2u : 0u) | (j + 1 < H ? 4u : 0u) | (j > 0 ? 8u : 0u);
       }
       cEx[k] = qx - cc;
@@ -141,7 +150,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
           const double xW = (msk[k] & 2u) ? v[pp - H] : 0.0;
           const double xN = (msk[k] & 4u) ? v[pp + 1] : 0.0;
           const double xS = (msk[k] & 8u) ? v[pp - 1] : 0.0;
-          double t = fma(-cd, v[pp], d.b[pp] * bsc);
+          double t = fma(-cd, v[pp], d.b[pp]);
           t = fma(-cEx[k], xE - xW, t);
           t = fma(-cNy[k], xN - xS, t);
           out[k] = fma(c2, xW + xS, t);
@@ -162,7 +171,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
         }
       }
     };
-    auto bval = [&](int pp) { return (pp < N) ? d.b[pp] * bsc : 0.0; };
+    auto bval = [&](int pp) { return (pp < N) ? d.b[pp] : 0.0; };
 
     // initial guess (FP64)
 #pragma unroll
@@ -489,7 +498,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
       const int pp = tid + k * NT;
       if (pp < N) {
         d.x[pp] = sm.xs[pp];
-        if (p.bnext) p.bnext[(size_t)sysi * p.bnext_ld + pp] = __float2bfloat16_rn((float)(sm.xs[pp] * bsc));
+        if (p.bnext) p.bnext[(size_t)sysi * p.bnext_ld + pp] = __float2bfloat16_rn((float)sm.xs[pp]);
       }
     }
     if (tid == 0) {

@@ -741,7 +741,7 @@ kp_status kp_march_run(kp_march_plan* P, int n0, int steps, kp_step_stats* stats
                              (int)N, 1, P->st);
     if (e == cudaSuccess && g.ntgt && P->Bb)
       e = kp::launch_to_bf16(P->Bb + (size_t)P->tgt_base[gi] * c->vb_ld, c->vb_ld,
-                             P->Tt[q0] + P->tgt_off[gi], g.ntgt, (int)N, (double)P->opt.T, P->st);
+                             P->Tt[q0] + P->tgt_off[gi], g.ntgt, (int)N, 1.0, P->st);   // b as stored
   }
   P->host_step[0] = n0;
   P->host_step[1] = n0 + steps;
