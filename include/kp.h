@@ -383,7 +383,15 @@ typedef struct {
 typedef struct kp_march_plan kp_march_plan;
 
 /* Builds the plan: device state, descriptors and (if use_graph) the graphs.
- * The group arrays are read now; their device buffers are used by every run. */
+ * The group arrays are read now; their device buffers are used by every run.
+ * Errors: KP_ERR_ARG for bad sizes, pointers, options, seed indices or
+ * predecessors (seed_prev[s] outside -1..s-1), or more seeds than max_seeds / 2
+ * (max_seeds / (2K) limits the window K); KP_ERR_UNSUPPORTED for grids above
+ * 4096 unknowns in several groups, and for Picard iterations, exact Galerkin,
+ * score extraction, BiCGSTAB seeds or seed cycling outside the FP64 one-block
+ * solver (BiCGSTAB also needs one Picard iteration and m_seed >= 4);
+ * KP_ERR_CUDA / KP_ERR_OOM for failed allocations, copies or graph captures.
+ * On error *plan is NULL and nothing is left allocated. */
 kp_status kp_march_create(kp_ctx* ctx, int ngroups, const kp_group* groups,
                           const kp_march_opts* opt, kp_march_plan** plan);
 /* Runs timesteps n0+1 .. n0+steps (0 <= n0, n0+steps <= T) from the states in
