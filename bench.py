@@ -91,6 +91,8 @@ def parse(argv=None):
     ap.add_argument("--schedule", choices=("beta", "paper"), default="beta",
                     help="g^2 schedule: linear beta 1e-4..0.02 (workloads, default) or the paper's "
                          "constant g = 0.5")
+    ap.add_argument("--cluster-size", type=int, default=0,
+                    help="mixed precision: CTAs per system (2, 4, 8) also for grids of <= 4096 points")
     ap.add_argument("--learned", action="store_true",
                     help="128x128x3 learned-guess measurement (bounded sample)")
     return ap.parse_args(argv)
@@ -425,7 +427,8 @@ def main():
                      max_n=nmax,
                      precision=kp.PREC_MIXED if mixed else kp.PREC_FP64,
                      block_threads=args.block_threads, reorth=args.reorth,
-                     smem_vectors=args.smem_vectors, blocks_per_sm=args.blocks_per_sm)
+                     smem_vectors=args.smem_vectors, blocks_per_sm=args.blocks_per_sm,
+                     cluster_size=args.cluster_size)
     dev = torch.device("cuda", torch.cuda.current_device())
     img_s = [torch.as_tensor(g.seeds.reshape(len(g.seeds), -1), device=dev) for g in wl.groups]
     img_t = [torch.as_tensor(g.targets.reshape(len(g.targets), -1), device=dev) for g in wl.groups]

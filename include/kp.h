@@ -79,6 +79,10 @@ typedef struct {
                         shared-memory window): 256 threads: 2 or 3; 128: 2, 3
                         or 4; 64: 4; 0 = the default above (2 for an explicit
                         256 or 128, 4 for 64).  Mixed precision: 2 always.   */
+  int cluster_size;  /* mixed precision, grids of 1025..16384 points: solve each
+                        system on a cluster of this many CTAs (2, 4 or 8; W
+                        divisible by it, <= 2048 points per CTA); 0 = clusters
+                        only above 4096 points (one 512-thread block below) */
 } kp_options;
 
 /* Operator of one system (Sec. 2.3): A(m~; g^2, dt, h, f).  `mtilde` is the

@@ -58,12 +58,16 @@ kp_status gmres_shape(kp_ctx* c, int nmax, int m, Shape* out, bool mixed, int wm
       if (sh.nt == 64) { sh.nt = 128; sh.ept = 8; }
     }
   }
-  else if (nmax <= 4096) { sh.ept = 8; sh.nt = 512; }
+  else if (nmax <= 4096 && !(mixed && c->opt.cluster_size)) { sh.ept = 8; sh.nt = 512; }
   else if (mixed) {
     // a cluster of cs CTAs, each holding W/cs whole columns (<= 2048 points)
     sh.ept = 8; sh.nt = 256;
-    for (int cs : {2, 4, 8})
-      if ((nmax + cs - 1) / cs <= 2048) { sh.cs = cs; break; }
+    if (c->opt.cluster_size) {
+      if ((nmax + c->opt.cluster_size - 1) / c->opt.cluster_size <= 2048) sh.cs = c->opt.cluster_size;
+    } else {
+      for (int cs : {2, 4, 8})
+        if ((nmax + cs - 1) / cs <= 2048) { sh.cs = cs; break; }
+    }
     if (!sh.cs || wmin <= 0 || wmin % sh.cs)
       return set_error(c, KP_ERR_UNSUPPORTED, "N=%d: needs W divisible by the cluster size and N <= 16384", nmax);
   }
@@ -274,6 +278,7 @@ void kp_options_default(kp_options* o) {
   o->reorth = 0;
   o->block_threads = 0;
   o->blocks_per_sm = 0;
+  o->cluster_size = 0;
 }
 
 kp_status kp_create(kp_ctx** out, const kp_options* opt, void* stream) {
@@ -285,7 +290,8 @@ kp_status kp_create(kp_ctx** out, const kp_options* opt, void* stream) {
   if (o.max_seeds < 1 || o.max_a < 1 || o.max_a > kp::kMaxM || o.max_n < 1 || o.max_n > 16384 ||
       (o.precision != KP_PREC_FP64 && o.precision != KP_PREC_MIXED) ||
       o.smem_vectors < 0 || (o.reorth != 0 && o.reorth != 1) ||
-      (o.block_threads != 0 && o.block_threads != 64 && o.block_threads != 128 && o.block_threads != 256))
+      (o.block_threads != 0 && o.block_threads != 64 && o.block_threads != 128 && o.block_threads != 256) ||
+      (o.cluster_size != 0 && o.cluster_size != 2 && o.cluster_size != 4 && o.cluster_size != 8))
     return KP_ERR_ARG;
   {
     // solver shapes compiled for grids of <= 1024 points: (threads, blocks per SM)

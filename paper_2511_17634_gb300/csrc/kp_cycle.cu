@@ -46,7 +46,8 @@ __global__ void __launch_bounds__(kCycleThreads) cycle_kernel(const CycleParams 
     for (int e = tid; e < nv * p.ld; e += NT) Vo[e] = Vs[e];
     const double* Rs = p.slotR + (size_t)ss * rstride;
     double* Ro = p.outR + (size_t)ss * rstride;
-    for (int e = tid; e < (int)rstride; e += NT) Ro[e] = Rs[e];
+    const int nr = ms.timestep == t ? (p.max_a + 1) * min(ms.a, p.max_a) : 0;   // a columns
+    for (int e = tid; e < nr; e += NT) Ro[e] = Rs[e];
     if (tid == 0) p.outMeta[ss] = ms;
     return;
   }

@@ -59,3 +59,23 @@ def test_solver_shape_options_validated():
             assert st == K.ERR_ARG, (bt, mb)
         if h:
             L.kp_destroy(h)
+
+
+def test_cluster_size_option_validated():
+    # CTAs per system for mixed precision: 0 (automatic), 2, 4 or 8
+    from paper_2511_17634_gb300 import kp as K
+    L = K.lib()
+    import ctypes
+    for cs, ok in [(0, True), (2, True), (4, True), (8, True), (3, False), (16, False), (-2, False)]:
+        o = K._Options()
+        L.kp_options_default(ctypes.byref(o))
+        assert o.cluster_size == 0
+        o.cluster_size = cs
+        h = ctypes.c_void_p()
+        st = L.kp_create(ctypes.byref(h), ctypes.byref(o), None)
+        if ok:
+            assert st != K.ERR_ARG, cs
+        else:
+            assert st == K.ERR_ARG, cs
+        if h:
+            L.kp_destroy(h)

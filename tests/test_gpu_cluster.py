@@ -64,3 +64,26 @@ def test_cluster_march_128x128_sampled(kp, orc):
     rel = np.linalg.norm(t_.cpu().numpy() - omt, axis=1) / np.linalg.norm(omt, axis=1)
     print(f"128x128 mixed vs FP64 oracle: max {rel.max():.2e} median {np.median(rel):.2e}")
     assert rel.max() <= 1e-6
+
+
+@pytest.mark.parametrize("cs", [2, 4])
+def test_cluster_forced_on_64x64(kp, orc, cs):
+    # a 4096-point grid on a cluster of cs CTAs (kp_options.cluster_size)
+    # instead of one 512-thread block: same tolerance against the oracle
+    H = W = 64
+    N = H * W
+    rng = np.random.default_rng(cs)
+    n = 3
+    mt = rng.uniform(0, 1, (n, N))
+    b = rng.normal(size=(n, N))
+    ctx = kp.Context(max_n=N, precision=kp.PREC_MIXED, cluster_size=cs)
+    dm, db = _dev(mt), _dev(b)
+    ops = kp.make_ops(H, W, 1e-3, 0.02, 1 / H, dm)
+    x = torch.zeros_like(db)
+    it, st, rr = kp.decode_info(ctx.refine(ops, db, x, tol=1e-10, m=40, maxit=600))
+    torch.cuda.synchronize()
+    assert (st == 0).all() and (rr <= 1e-10).all(), (st, rr)
+    for k in range(n):
+        C = orc.coeffs(H, W, 0.02, 1e-3, 1 / H, mt[k])
+        xr = x[k].cpu().numpy()
+        assert np.linalg.norm(b[k] - orc.apply(H, W, C, xr)) <= 1.01e-10 * np.linalg.norm(b[k])
