@@ -367,6 +367,13 @@ typedef struct {
                             latest iterate, same right-hand side, warm start; the
                             stored seed basis is the first solve's.  FP64 plans. */
   int seed_solver;       /* kp_seed_solver: how Phase 1 (Sec. 3) solves the seeds */
+  int wait_probe;        /* testing aid for the bounded device waits, 0 normally.
+                            1 (window plans, K > 1): every target item waits for a
+                            release of its system that never comes, so each wait
+                            gives up after 2^14 polls; the next kp_march_run call
+                            that waits for the GPU returns KP_ERR_TIMEOUT (the
+                            states are then not trustworthy) and the context stays
+                            usable. */
 } kp_march_opts;
 
 /* Per-timestep totals, filled on the host by kp_march_run. */

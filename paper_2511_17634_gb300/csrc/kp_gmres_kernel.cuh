@@ -114,11 +114,12 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
     if (p.done) {
       // m^{n-1} of this system comes from its previous item, claimed earlier
       // by a block that is therefore running: wait for its release
-      const int need = tstep - *p.run_start;
+      const int need = tstep - *p.run_start + p.wait_bias;
+      const int limit = p.wait_limit > 0 ? p.wait_limit : kWaitLimit;
       if (tid == 0) {
         int it = 0;
         while (ld_acquire_gpu(p.done + sysi) < need) {
-          if (++it > kWaitLimit) { atomicOr(p.err, 2); break; }
+          if (++it > limit) { atomicOr(p.err, 2); break; }
           __nanosleep(256);
         }
       }

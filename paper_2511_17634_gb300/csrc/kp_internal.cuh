@@ -121,6 +121,8 @@ struct GmresParams {
                             // null = static (each block marches its systems through the window)
   int* done;                // [nsys] timesteps completed since *run_start (dynamic schedule)
   const int* run_start;
+  int wait_bias;            // testing aid: added to every awaited count (1: never released)
+  int wait_limit;           // polls before a wait gives up; 0 = kWaitLimit
   int* err;                 // bit 1: a dependency wait gave up
   int grid;                 // blocks of the launch (0 = one per system)
   size_t score_stride;      // > 0: write the score of each solved timestep to

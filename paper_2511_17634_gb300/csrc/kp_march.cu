@@ -163,6 +163,10 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset,
       g.queue = P->queue + ci;
       g.done = P->done + tc.first;
       g.run_start = P->step + 2;
+      if (P->opt.wait_probe) {               // testing aid: every wait runs out, quickly
+        g.wait_bias = 1;
+        g.wait_limit = 1 << 14;
+      }
       g.grid = tc.grid;
     }
   }

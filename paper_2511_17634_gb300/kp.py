@@ -283,7 +283,7 @@ class _MarchOpts(ctypes.Structure):
                 ("m", ctypes.c_int), ("maxit", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("window", ctypes.c_int), ("target_blocks", ctypes.c_int),
                 ("score", ctypes.c_void_p), ("embed", ctypes.c_void_p), ("picard", ctypes.c_int),
-                ("seed_solver", ctypes.c_int)]
+                ("seed_solver", ctypes.c_int), ("wait_probe", ctypes.c_int)]
 
 
 class StepStats(ctypes.Structure):
@@ -321,7 +321,7 @@ class March:
 
     def __init__(self, ctx, groups, T, g2, mode=MARCH_PROJECTED, tol_seed=1e-10, tol=1e-8,
                  m_seed=40, m=40, maxit=1000, use_graph=True, window=0, target_blocks=0,
-                 score=None, embed=None, picard=1, seed_solver=0):
+                 score=None, embed=None, picard=1, seed_solver=0, wait_probe=False):
         L = _march_lib()
         self.ctx = ctx
         self._keep = []
@@ -353,7 +353,7 @@ class March:
                        int(window), int(target_blocks),
                        score.data_ptr() if score is not None else None,
                        embed.data_ptr() if embed is not None else None, int(picard),
-                       int(seed_solver))
+                       int(seed_solver), int(wait_probe))
         self.T = T
         self._h = ctypes.c_void_p()
         ctx._check(L.kp_march_create(ctx._h, len(groups), ctypes.cast(arr, ctypes.c_void_p),

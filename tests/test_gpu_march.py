@@ -390,3 +390,29 @@ def test_march_seed_cycling_rejects_bad_links(kp):
     bad = np.array([-1, 0, 2, 1, 2, 3], dtype=np.int32)           # seed 2 names itself
     with pytest.raises(RuntimeError):
         kp.March(ctx, [(s, t, g.target_seed, g.H, g.W, bad)], 12, synth.beta_schedule(12))
+
+
+def test_march_bounded_wait_gives_up_and_context_survives(kp, orc):
+    # every target item waits for a release that never comes (testing aid):
+    # the waits give up, the run reports KP_ERR_TIMEOUT, and a normal plan on
+    # the same context afterwards still matches the oracle
+    wl = synth.config(1)
+    g = wl.groups[0]
+    ctx = kp.Context(max_seeds=8, max_a=wl.a, max_n=g.N)
+    grp = _groups(wl)
+    bad = kp.March(ctx, grp, wl.T, wl.g2, mode=0, tol_seed=1e-10, tol=1e-12, m_seed=wl.m_seed,
+                   m=wl.m, window=2, wait_probe=True)
+    with pytest.raises(kp.KPError) as ei:
+        bad.run(0, 4, stats=True)
+    assert ei.value.status == kp.ERR_TIMEOUT
+    bad.close()
+    grp = _groups(wl)
+    mr = kp.March(ctx, grp, wl.T, wl.g2, mode=0, tol_seed=1e-10, tol=1e-12, m_seed=wl.m_seed,
+                  m=wl.m, window=2)
+    stats, _ = mr.run(0, 6, stats=True)
+    torch.cuda.synchronize()
+    oms, omt, _ = orc.march(g.H, g.W, wl.T, wl.g2, g.seeds, g.targets, g.target_seed, steps=6,
+                            mode=0, tol_seed=1e-10, m_seed=wl.m_seed, a=wl.a, tol_ref=1e-12,
+                            m_ref=wl.m)
+    assert np.abs(grp[0][1].cpu().numpy() - omt).max() <= 1e-9 * np.abs(omt).max()
+    assert all(s.not_converged == 0 for s in stats)
