@@ -416,3 +416,27 @@ def test_march_bounded_wait_gives_up_and_context_survives(kp, orc):
                             m_ref=wl.m)
     assert np.abs(grp[0][1].cpu().numpy() - omt).max() <= 1e-9 * np.abs(omt).max()
     assert all(s.not_converged == 0 for s in stats)
+
+
+def test_march_seed_cycling_4096_point_grid(kp, orc):
+    # the cycling kernel's 16-points-per-thread instance (grids of 1025..4096
+    # points) on a 64x64 chain of three seeds, against the oracle
+    g = synth.make_group(93, 64, 64, 1, 3, 4, tag=5)
+    T = 6
+    g2 = synth.beta_schedule(T)
+    prev = _chains(3, 1)
+    ctx = kp.Context(max_seeds=12, max_a=20, max_n=g.N)
+    s = torch.as_tensor(g.seeds.reshape(len(g.seeds), -1).copy(), device="cuda")
+    t = torch.as_tensor(g.targets.reshape(len(g.targets), -1).copy(), device="cuda")
+    mr = kp.March(ctx, [(s, t, g.target_seed, g.H, g.W, prev)], T, g2, mode=0, tol_seed=1e-12,
+                  tol=1e-12, m_seed=20, m=20, maxit=1000, window=2)
+    stats, _ = mr.run(0, T, stats=True)
+    torch.cuda.synchronize()
+    oms, omt, ost = orc.march(g.H, g.W, T, g2, g.seeds, g.targets, g.target_seed, mode=0,
+                              tol_seed=1e-12, m_seed=20, a=20, tol_ref=1e-12, m_ref=20,
+                              seed_prev=prev)
+    assert np.abs(t.cpu().numpy() - omt).max() <= 1e-9 * np.abs(omt).max()
+    assert all(x.not_converged == 0 and x.max_rel_res <= 1e-12 for x in stats)
+    gpu_it = np.array([x.tgt_iters for x in stats])
+    orc_it = np.array([x.tgt_iters.sum() for x in ost])
+    assert np.abs(gpu_it - orc_it).max() <= len(g.targets)
