@@ -641,7 +641,7 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved_eq, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s" if not mixed else "TFLOP/s (FP64 + FP32 x FP64/FP32 peak ratio)",
                          "frac": achieved_eq / FP64_PEAK_TFLOPS,
-                         "traffic": 23.78e6 if captured else None,
+                         "traffic": 23.81e6 if captured else None,
                          "traffic_note": ("DRAM bytes per target launch (16 timesteps x 768 systems), ncu "
                                           "capture of the first window; the path is L2-resident"
                                           if captured else "no ncu capture of this workload and shape"),
