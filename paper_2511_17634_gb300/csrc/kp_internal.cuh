@@ -563,6 +563,7 @@ struct CycleParams {
   const double* g2_sched;
   double b_scale;           // the solvers' right-hand-side scale: A_proj of A / b_scale
   int slot_sets;            // slot of seed s at t: (t mod slot_sets) * ns + s
+  float* scratch;           // [gridDim.x][max_a][ld] FP32 kept vectors
 };
 constexpr int kCycleThreads = 256;
 constexpr int kCycleMaxN = 4096;

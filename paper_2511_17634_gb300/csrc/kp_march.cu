@@ -100,6 +100,7 @@ struct kp_march_plan {
   double* cycV = nullptr;                    // [max_seeds][max_a + 1][max_n]
   double* cycR = nullptr;                    // [max_seeds][(max_a + 1) * max_a]
   kp::SlotMeta* cycMeta = nullptr;           // [max_seeds]
+  float* cycS = nullptr;                     // [K * ns][max_a][max_n] FP32 workspace
 };
 
 namespace {
@@ -230,6 +231,7 @@ cudaError_t launch_cycle(kp_march_plan* P, int offset, cudaStream_t st) {
   q.g2_sched = P->g2;
   q.b_scale = (double)P->opt.T;                 // as the solvers' b_scale
   q.slot_sets = P->K > 1 ? 2 * P->K : 0;
+  q.scratch = P->cycS;
   int nmax = 0;
   for (const kp_group& g : P->groups)
     if (g.nseed) nmax = std::max(nmax, g.H * g.W);
@@ -346,6 +348,7 @@ kp_status kp_march_destroy(kp_march_plan* P) {
   cudaFree(P->cycV);
   cudaFree(P->cycR);
   cudaFree(P->cycMeta);
+  cudaFree(P->cycS);
   cudaFree(P->perm);
   cudaFree(P->Bb);
   cudaFree(P->Cp);
@@ -528,6 +531,7 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
     if (e == cudaSuccess) e = dmalloc(&P->cycV, slots * (a + 1) * n);
     if (e == cudaSuccess) e = dmalloc(&P->cycR, slots * (a + 1) * a);
     if (e == cudaSuccess) e = dmalloc(&P->cycMeta, slots);
+    if (e == cudaSuccess) e = dmalloc(&P->cycS, (size_t)P->K * P->ns * a * n);
     if (e == cudaSuccess)   // no slot is served before its first timestep
       e = cudaMemset(P->cycMeta, 0xff, slots * sizeof(kp::SlotMeta));
     if (e == cudaSuccess)
