@@ -1,8 +1,8 @@
 // kp_gmres_kernel.cuh -- the FP64 batched GMRES(m) kernel template and its
-// launcher, shared by kp_gmres.cu (the lean instantiations), kp_gmres_feat.cu
-// (the exact-Galerkin initial guess, Picard iterations, the fused score /
-// embedding epilogue and the projection through an explicit A_proj) and
-// kp_gmres_bicg.cu (BiCGSTAB seed solves).  The optional paths are compiled
+// launcher, shared by kp_gmres.cu (the lean instantiations), kp_gmres_dense.cu
+// (the projection through an explicit A_proj), kp_gmres_feat.cu (that, the
+// exact-Galerkin initial guess, Picard iterations and the fused score /
+// embedding epilogue) and kp_gmres_bicg.cu (BiCGSTAB seed solves).  The optional paths are compiled
 // only into their variants, so the default solver keeps its registers for the
 // hot loop; the variants compile in parallel.
 //
@@ -63,14 +63,16 @@ __device__ __forceinline__ Smem carve(double* base, int S, int npad, int nwarps,
 }
 
 // VAR selects the code compiled into an instantiation: kVarLean (the plain
-// solver), kVarFeat (plus exact Galerkin, Picard, score / embedding and the
-// projection through an explicit A_proj), kVarBicg (BiCGSTAB seed solves).
-enum { kVarLean = 0, kVarFeat = 1, kVarBicg = 2 };
+// solver), kVarDense (plus the projection through an explicit A_proj, for
+// BiCGSTAB and cycled seed bases), kVarFeat (plus exact Galerkin, Picard and
+// the score / embedding epilogue), kVarBicg (BiCGSTAB seed solves).
+enum { kVarLean = 0, kVarFeat = 1, kVarBicg = 2, kVarDense = 3 };
 
 template <int EPT, int NT, int MINB, int VAR>
 __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams p) {
   constexpr bool FEAT = VAR == kVarFeat;
   constexpr bool BICG = VAR == kVarBicg;
+  constexpr bool DENSE = VAR == kVarFeat || VAR == kVarDense;
   constexpr int NWARPS = NT / 32;
   extern __shared__ __align__(16) double smem_raw[];
   const int npad = EPT * NT;
@@ -273,7 +275,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
           for (int i = lane; i < nv; i += 32) sm.hb[i] = cross_warp<NT>(sm.red, i);
           __syncwarp();
           const double* R = p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a;
-          if (FEAT && mt.dense) {
+          if (DENSE && mt.dense) {
             // BiCGSTAB seed basis: A_proj alpha = c with the stored explicit
             // A_proj = V^T A_seed V, LU with partial pivoting on this warp
             bool ok = a * a <= (m + 1) * m;
