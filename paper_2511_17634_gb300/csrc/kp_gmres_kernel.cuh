@@ -1,8 +1,9 @@
 // kp_gmres_kernel.cuh -- the FP64 batched GMRES(m) kernel template and its
 // launcher, shared by kp_gmres.cu (the lean instantiations), kp_gmres_dense.cu
-// (the projection through an explicit A_proj), kp_gmres_feat.cu (that, the
-// exact-Galerkin initial guess, Picard iterations and the fused score /
-// embedding epilogue) and kp_gmres_bicg.cu (BiCGSTAB seed solves).  The optional paths are compiled
+// (the projection through an explicit A_proj), kp_gmres_score.cu (the fused
+// score / embedding epilogue), kp_gmres_feat.cu (both, the exact-Galerkin
+// initial guess and Picard iterations) and kp_gmres_bicg.cu (BiCGSTAB seed
+// solves).  The optional paths are compiled
 // only into their variants, so the default solver keeps its registers for the
 // hot loop; the variants compile in parallel.
 //
@@ -64,15 +65,17 @@ __device__ __forceinline__ Smem carve(double* base, int S, int npad, int nwarps,
 
 // VAR selects the code compiled into an instantiation: kVarLean (the plain
 // solver), kVarDense (plus the projection through an explicit A_proj, for
-// BiCGSTAB and cycled seed bases), kVarFeat (plus exact Galerkin, Picard and
-// the score / embedding epilogue), kVarBicg (BiCGSTAB seed solves).
-enum { kVarLean = 0, kVarFeat = 1, kVarBicg = 2, kVarDense = 3 };
+// BiCGSTAB and cycled seed bases), kVarScore (plus the score / embedding
+// epilogue), kVarFeat (all of these, exact Galerkin and Picard), kVarBicg
+// (BiCGSTAB seed solves).
+enum { kVarLean = 0, kVarFeat = 1, kVarBicg = 2, kVarDense = 3, kVarScore = 4 };
 
 template <int EPT, int NT, int MINB, int VAR>
 __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams p) {
   constexpr bool FEAT = VAR == kVarFeat;
   constexpr bool BICG = VAR == kVarBicg;
   constexpr bool DENSE = VAR == kVarFeat || VAR == kVarDense;
+  constexpr bool SCORE = VAR == kVarFeat || VAR == kVarScore;
   constexpr int NWARPS = NT / 32;
   extern __shared__ __align__(16) double smem_raw[];
   const int npad = EPT * NT;
@@ -894,7 +897,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
       const int pp = tid + k * NT;
       if (pp < N) d.x[pp] = sm.xs[pp];
     }
-    if (FEAT && p.score_stride && d.score) {
+    if (SCORE && p.score_stride && d.score) {
       // score of m^n by central differences (end of Sec. 2.3, divided by 2h,
       // zero outside the grid) and one probability-flow step of the embedding
       // (Sec. 4.1, f = 0): x^n = x^{n-1} - dt (g^{n-1})^2 / 2 grad m^{n-1},
