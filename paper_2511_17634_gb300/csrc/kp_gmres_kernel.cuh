@@ -904,7 +904,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
       // with m^{n-1} this item's input and (g^0)^2 taken as (g^1)^2
       const double i2h = 0.5 / hh;
       const double g2prev = p.step ? p.g2_sched[tstep > 0 ? tstep - 1 : 0] : d.g2;
-      const double ce = -0.5 * d.dt * g2prev;
+      const double cei = -0.5 * d.dt * g2prev * i2h;   // the Euler factor times 1/(2h)
       double* sc = d.score + (size_t)tstep * p.score_stride;
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
@@ -917,8 +917,8 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
           sc[N + pp] = (xn - xs_) * i2h;
           const double me = i + 1 < W ? d.mt[pp + H] : 0.0, mw = i > 0 ? d.mt[pp - H] : 0.0;
           const double mn = j + 1 < H ? d.mt[pp + 1] : 0.0, ms = j > 0 ? d.mt[pp - 1] : 0.0;
-          d.emb[pp] = fma(ce, (me - mw) * i2h, d.emb[pp]);
-          d.emb[N + pp] = fma(ce, (mn - ms) * i2h, d.emb[N + pp]);
+          d.emb[pp] = fma(cei, me - mw, d.emb[pp]);
+          d.emb[N + pp] = fma(cei, mn - ms, d.emb[N + pp]);
         }
       }
     }
