@@ -158,7 +158,30 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
     // neighbour lies outside the grid
     double cE[EPT], cW[EPT], cN[EPT], cS[EPT];
     const bool drift = d.fx != nullptr || d.fy != nullptr;
-    auto set_coeffs = [&](const double* mtl) {
+    // score output (end of Sec. 2.3) and probability-flow embedding (Sec. 4.1):
+    // the central differences of the input m^{n-1} are the ones the lagged
+    // coefficients need, so the score of m^{n-1} (timestep n-1 of the output)
+    // and the embedding step x += -dt (g^{n-1})^2 / 2 grad m^{n-1} are written
+    // from here; the last timestep of a run writes the score of its own
+    // solution in the epilogue
+    const bool score_on = SCORE && p.score_stride && d.score;
+    const double s_i2h = SCORE ? 0.5 / hh : 0.0;
+    double cei = 0.0;                            // the Euler factor times 1/(2h)
+    double* sc_in = nullptr;                     // score of the input, timestep tstep - 1
+    if (SCORE && score_on) {
+      const double g2prev = p.step ? p.g2_sched[tstep > 0 ? tstep - 1 : 0] : d.g2;
+      cei = -0.5 * d.dt * g2prev * s_i2h;        // (g^0)^2 taken as (g^1)^2
+      if (tstep > 0) sc_in = d.score + (size_t)(tstep - 1) * p.score_stride;
+    }
+    auto score_in = [&](int pp, double dmx, double dmy) {
+      if (sc_in) {
+        sc_in[pp] = dmx * s_i2h;
+        sc_in[N + pp] = dmy * s_i2h;
+      }
+      d.emb[pp] = fma(cei, dmx, d.emb[pp]);
+      d.emb[N + pp] = fma(cei, dmy, d.emb[N + pp]);
+    };
+    auto set_coeffs = [&](const double* mtl, bool input) {
       if (!drift) {                              // f = 0 (the method's systems): two terms each
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
@@ -171,6 +194,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
             const double mN = (j + 1 < H) ? mtl[pp + 1] : 0.0;
             const double mS = (j > 0) ? mtl[pp - 1] : 0.0;
             const double dmx = mE - mW, dmy = mN - mS;
+            if (SCORE && score_on && input) score_in(pp, dmx, dmy);
             if (i + 1 < W) cE[k] = fma(-ee, dmx, -cc);
             if (i > 0) cW[k] = fma(ee, dmx, -cc);
             if (j + 1 < H) cN[k] = fma(-ee, dmy, -cc);
@@ -192,6 +216,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
           const double fxp = d.fx ? d.fx[pp] : 0.0;
           const double fyp = d.fy ? d.fy[pp] : 0.0;
           const double dmx = mE - mW, dmy = mN - mS;
+          if (SCORE && score_on && input) score_in(pp, dmx, dmy);
           if (i + 1 < W) cE[k] = -cc + fxp * i2h - ee * dmx;
           if (i > 0) cW[k] = -cc - fxp * i2h + ee * dmx;
           if (j + 1 < H) cN[k] = -cc + fyp * i2h - ee * dmy;
@@ -199,7 +224,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
         }
       }
     };
-    set_coeffs(d.mt);
+    set_coeffs(d.mt, true);
     // r = b - A v, the product chain started from b (one multiply, five fused
     // multiply-adds per point)
     auto residual_of = [&](const double* v, double (&out)[EPT]) {
@@ -627,7 +652,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
         // the latest iterate m^{n,(k-1)} (in shared memory), the same right-hand
         // side, GMRES warm-started from that iterate
         __syncthreads();
-        set_coeffs(sm.xs);
+        set_coeffs(sm.xs, false);
         status = KP_NOT_CONVERGED;
         capture = false;                         // the stored basis is the first solve's
       }
@@ -897,14 +922,9 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
       const int pp = tid + k * NT;
       if (pp < N) d.x[pp] = sm.xs[pp];
     }
-    if (SCORE && p.score_stride && d.score) {
-      // score of m^n by central differences (end of Sec. 2.3, divided by 2h,
-      // zero outside the grid) and one probability-flow step of the embedding
-      // (Sec. 4.1, f = 0): x^n = x^{n-1} - dt (g^{n-1})^2 / 2 grad m^{n-1},
-      // with m^{n-1} this item's input and (g^0)^2 taken as (g^1)^2
-      const double i2h = 0.5 / hh;
-      const double g2prev = p.step ? p.g2_sched[tstep > 0 ? tstep - 1 : 0] : d.g2;
-      const double cei = -0.5 * d.dt * g2prev * i2h;   // the Euler factor times 1/(2h)
+    if (SCORE && score_on && tstep == *p.step_end - 1) {
+      // last timestep of the run: the score of its own solution m^n (the
+      // next run's first item writes the same values again from its input)
       double* sc = d.score + (size_t)tstep * p.score_stride;
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
@@ -913,12 +933,8 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
           const int i = pp / H, j = pp - i * H;
           const double xe = i + 1 < W ? sm.xs[pp + H] : 0.0, xw = i > 0 ? sm.xs[pp - H] : 0.0;
           const double xn = j + 1 < H ? sm.xs[pp + 1] : 0.0, xs_ = j > 0 ? sm.xs[pp - 1] : 0.0;
-          sc[pp] = (xe - xw) * i2h;
-          sc[N + pp] = (xn - xs_) * i2h;
-          const double me = i + 1 < W ? d.mt[pp + H] : 0.0, mw = i > 0 ? d.mt[pp - H] : 0.0;
-          const double mn = j + 1 < H ? d.mt[pp + 1] : 0.0, ms = j > 0 ? d.mt[pp - 1] : 0.0;
-          d.emb[pp] = fma(cei, me - mw, d.emb[pp]);
-          d.emb[N + pp] = fma(cei, mn - ms, d.emb[N + pp]);
+          sc[pp] = (xe - xw) * s_i2h;
+          sc[N + pp] = (xn - xs_) * s_i2h;
         }
       }
     }
