@@ -356,7 +356,9 @@ typedef struct {
    *   every target, in group order and the caller's target order within a
    *   group, sx = (m_{i+1,j} - m_{i-1,j}) / (2h) then sy = (m_{i,j+1} -
    *   m_{i,j-1}) / (2h) of m^n, zero outside the grid; a run writes the
-   *   timesteps it solves.
+   *   timesteps it solves (and, for n0 >= 1, timestep n0 again from its
+   *   starting state: the same values when that state is the previous
+   *   run's result).
    * embed: device, [targets][2][H*W] FP64 state x, advanced at timestep n by
    *   x += -dt (g^{n-1})^2 / 2 * grad m^{n-1} ((g^0)^2 = (g^1)^2); the caller
    *   sets x^0 (zero in the paper).  Must be given with score.          */
