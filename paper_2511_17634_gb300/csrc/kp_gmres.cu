@@ -58,8 +58,9 @@ size_t gmres_fp64_smem_bytes(int ept, int nt, int S, int m) {
 cudaError_t launch_gmres_fp64(const GmresParams& p, int ept, int nt, int minb, size_t smem,
                               cudaStream_t st) {
   if (p.bicg && p.capV) return launch_gmres_fp64_bicg(p, ept, nt, minb, smem, st);
-  if (p.x0_mode == X0_GALERKIN || p.picard > 1 || (p.score_stride && p.dense_slots))
-    return launch_gmres_fp64_feat(p, ept, nt, minb, smem, st);
+  const int nfeat = (p.score_stride != 0) + (p.dense_slots != 0) + (p.picard > 1);
+  if (p.x0_mode == X0_GALERKIN || nfeat > 1) return launch_gmres_fp64_feat(p, ept, nt, minb, smem, st);
+  if (p.picard > 1) return launch_gmres_fp64_picard(p, ept, nt, minb, smem, st);
   if (p.score_stride) return launch_gmres_fp64_score(p, ept, nt, minb, smem, st);
   if (p.dense_slots) return launch_gmres_fp64_dense(p, ept, nt, minb, smem, st);
   if (ept == 4 && nt == 256 && minb == 2) return launch_one<4, 256, 2, kVarLean>(p, smem, st);

@@ -1,9 +1,9 @@
 // kp_gmres_kernel.cuh -- the FP64 batched GMRES(m) kernel template and its
 // launcher, shared by kp_gmres.cu (the lean instantiations), kp_gmres_dense.cu
 // (the projection through an explicit A_proj), kp_gmres_score.cu (the fused
-// score / embedding epilogue), kp_gmres_feat.cu (both, the exact-Galerkin
-// initial guess and Picard iterations) and kp_gmres_bicg.cu (BiCGSTAB seed
-// solves).  The optional paths are compiled
+// score / embedding output), kp_gmres_picard.cu (Picard iterations),
+// kp_gmres_feat.cu (all of these and the exact-Galerkin initial guess) and
+// kp_gmres_bicg.cu (BiCGSTAB seed solves).  The optional paths are compiled
 // only into their variants, so the default solver keeps its registers for the
 // hot loop; the variants compile in parallel.
 //
@@ -66,9 +66,9 @@ __device__ __forceinline__ Smem carve(double* base, int S, int npad, int nwarps,
 // VAR selects the code compiled into an instantiation: kVarLean (the plain
 // solver), kVarDense (plus the projection through an explicit A_proj, for
 // BiCGSTAB and cycled seed bases), kVarScore (plus the score / embedding
-// epilogue), kVarFeat (all of these, exact Galerkin and Picard), kVarBicg
-// (BiCGSTAB seed solves).
-enum { kVarLean = 0, kVarFeat = 1, kVarBicg = 2, kVarDense = 3, kVarScore = 4 };
+// epilogue), kVarPicard (plus Picard iterations), kVarFeat (all of these and
+// exact Galerkin), kVarBicg (BiCGSTAB seed solves).
+enum { kVarLean = 0, kVarFeat = 1, kVarBicg = 2, kVarDense = 3, kVarScore = 4, kVarPicard = 5 };
 
 template <int EPT, int NT, int MINB, int VAR>
 __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams p) {
@@ -76,6 +76,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
   constexpr bool BICG = VAR == kVarBicg;
   constexpr bool DENSE = VAR == kVarFeat || VAR == kVarDense;
   constexpr bool SCORE = VAR == kVarFeat || VAR == kVarScore;
+  constexpr bool PICARD = VAR == kVarFeat || VAR == kVarPicard;
   constexpr int NWARPS = NT / 32;
   extern __shared__ __align__(16) double smem_raw[];
   const int npad = EPT * NT;
@@ -644,10 +645,10 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
       }
       __syncthreads();
     }
-    const int npic = bicg ? 0 : (FEAT && p.picard > 1) ? p.picard : 1;
+    const int npic = bicg ? 0 : (PICARD && p.picard > 1) ? p.picard : 1;
 
     for (int pk = 0; pk < npic; ++pk) {
-      if (FEAT && pk > 0) {
+      if (PICARD && pk > 0) {
         // Picard iteration k = pk + 1 (Sec. 2.3): the nonlinear term lagged on
         // the latest iterate m^{n,(k-1)} (in shared memory), the same right-hand
         // side, GMRES warm-started from that iterate

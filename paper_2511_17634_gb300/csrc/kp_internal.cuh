@@ -526,6 +526,8 @@ cudaError_t launch_gmres_fp64_dense(const GmresParams& p, int ept, int nt, int m
                                     cudaStream_t st);
 cudaError_t launch_gmres_fp64_score(const GmresParams& p, int ept, int nt, int minb, size_t smem,
                                     cudaStream_t st);
+cudaError_t launch_gmres_fp64_picard(const GmresParams& p, int ept, int nt, int minb, size_t smem,
+                                     cudaStream_t st);
 size_t gmres_fp64_smem_bytes(int ept, int nt, int S, int m);
 size_t gmres_mixed_smem_bytes(int ept, int nt, int S, int m);
 cudaError_t launch_gmres_mixed(const GmresParams& p, int ept, int nt, size_t smem,
