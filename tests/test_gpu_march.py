@@ -440,3 +440,44 @@ def test_march_seed_cycling_4096_point_grid(kp, orc):
     gpu_it = np.array([x.tgt_iters for x in stats])
     orc_it = np.array([x.tgt_iters.sum() for x in ost])
     assert np.abs(gpu_it - orc_it).max() <= len(g.targets)
+
+
+def test_march_combined_options_match_oracle(kp, orc):
+    # options that share the feature variant of the solver: seed cycling with
+    # the score / embedding output, and the exact Galerkin guess on BiCGSTAB
+    # seed bases, each against the oracle's march
+    g = synth.make_group(91, 12, 10, 2, 3, 6, tag=3)
+    T = 10
+    g2 = synth.beta_schedule(T)
+    prev = _chains(3, 2)
+    N, nt = g.N, len(g.targets)
+    ctx = kp.Context(max_seeds=48, max_a=20, max_n=N)
+    s = torch.as_tensor(g.seeds.reshape(len(g.seeds), -1).copy(), device="cuda")
+    t = torch.as_tensor(g.targets.reshape(len(g.targets), -1).copy(), device="cuda")
+    score = torch.full((T, nt, 2, N), float("nan"), dtype=torch.float64, device="cuda")
+    emb = torch.zeros((nt, 2, N), dtype=torch.float64, device="cuda")
+    mr = kp.March(ctx, [(s, t, g.target_seed, g.H, g.W, prev)], T, g2, mode=0, tol_seed=1e-12,
+                  tol=1e-12, m_seed=20, m=20, window=2, score=score, embed=emb)
+    mr.run(0, T)
+    torch.cuda.synchronize()
+    _, omt, S, E = orc.march_scores(g.H, g.W, T, g2, g.seeds, g.targets, g.target_seed, mode=0,
+                                    tol_seed=1e-12, m_seed=20, a=20, tol_ref=1e-12, m_ref=20,
+                                    seed_prev=prev)
+    assert np.abs(t.cpu().numpy() - omt).max() <= 1e-9 * np.abs(omt).max()
+    assert np.abs(score.cpu().numpy() - S).max() <= 1e-8 * np.abs(S).max()
+    assert np.abs(emb.cpu().numpy() - E).max() <= 1e-8 * np.abs(E).max()
+
+    s = torch.as_tensor(g.seeds.reshape(len(g.seeds), -1).copy(), device="cuda")
+    t = torch.as_tensor(g.targets.reshape(len(g.targets), -1).copy(), device="cuda")
+    mr = kp.March(ctx, [(s, t, g.target_seed, g.H, g.W)], T, g2, mode=kp.MARCH_GALERKIN,
+                  tol_seed=1e-12, tol=1e-12, m_seed=20, m=20, window=2,
+                  seed_solver=kp.SEED_BICGSTAB)
+    stats, _ = mr.run(0, T, stats=True)
+    torch.cuda.synchronize()
+    _, omt, ost = orc.march(g.H, g.W, T, g2, g.seeds, g.targets, g.target_seed, mode=3,
+                            tol_seed=1e-12, m_seed=20, a=20, tol_ref=1e-12, m_ref=20,
+                            seed_solver=orc.SEED_BICGSTAB)
+    assert np.abs(t.cpu().numpy() - omt).max() <= 1e-9 * np.abs(omt).max()
+    gpu_it = np.array([x.tgt_iters for x in stats])
+    orc_it = np.array([x.tgt_iters.sum() for x in ost])
+    assert np.abs(gpu_it - orc_it).max() <= nt
