@@ -89,7 +89,7 @@ void orc_coeffs(int H, int W, double g2, double dt, double h, const double* mt,
 }
 
 /*
- * Right-hand side, Sec. 2.3 (last line of the coefficient listing):
+ * Right-hand side, Sec. 2.3 (given with the coefficients after Eq. 11):
  *   b_{i,j} = m^{n-1}_{i,j}/dt - [(fx_{i+1,j} - fx_{i-1,j}) + (fy_{i,j+1} - fy_{i,j-1})]/(2h)
  */
 void orc_rhs(int H, int W, double dt, double h, const double* mprev, const double* fx,
