@@ -79,3 +79,43 @@ def test_cluster_size_option_validated():
             assert st == K.ERR_ARG, cs
         if h:
             L.kp_destroy(h)
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    # the binding's ctypes structures against the C compiler's layout of the
+    # same structs in include/kp.h: size and the offset of every field
+    import ctypes
+    import subprocess
+    from paper_2511_17634_gb300 import kp as K
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pairs = {"kp_options": K._Options, "kp_group": K._Group, "kp_march_opts": K._MarchOpts,
+             "kp_step_stats": K.StepStats, "kp_march_timing": K.MarchTiming}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "kp.h"', 'int main(void) {']
+    for cname, py in pairs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    cfields = {"H": "H", "W": "W", "dt": "dt", "g2": "g2", "h": "h", "mt": "mtilde", "fx": "fx",
+               "fy": "fy"}
+    lines.append('  printf("kp_op size %zu\\n", sizeof(kp_op));')
+    for name, cf in cfields.items():
+        lines.append(f'  printf("kp_op {name} %zu\\n", offsetof(kp_op, {cf}));')
+    lines += ['  return 0;', '}']
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for ln in out:
+        if ln:
+            parts = ln.split()
+            got[(parts[0], parts[1])] = int(parts[2])
+    for cname, py in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+    assert got[("kp_op", "size")] == K.OP_DTYPE.itemsize
+    for name in cfields:
+        assert got[("kp_op", name)] == K.OP_DTYPE.fields[name][1], name
