@@ -184,11 +184,19 @@ static void givens(double a, double b, double* c, double* s) {
  *           Hessenberg matrix Hbar (capH, column-major (cap_a+1) x cap_a), where
  *           a' = min(cap_a, steps of the first cycle); *cap_used = a' and
  *           *cap_next = 1 if v_{a'+1} exists (no exact breakdown at step a').
+ *  cap_fixed if non-zero (and capV != NULL): the basis has the fixed dimension
+ *           a = min(cap_a, m) of Sec. 3 (V_a^n spans K_a(A^n, r0); Sec. 5.2 runs
+ *           a = 20): the residual test does not end the first cycle before it
+ *           has taken a Arnoldi steps -- only an exact breakdown or maxit does --
+ *           so the kept basis is the whole a-dimensional Krylov space even when
+ *           the solve converges in fewer steps.  The cycle's iterate is then the
+ *           GMRES minimiser over K_a, at least as accurate as the one at the
+ *           step where the test was first met.
  * Returns ORC_OK or ORC_NOT_CONVERGED.
  */
 int orc_gmres(int H, int W, const double* C, const double* b, double* x, double tol, int m,
               int maxit, int* iters, double* rel_res, double* hist, int cap_a, double* capV,
-              double* capH, int* cap_used, int* cap_next) {
+              double* capH, int* cap_used, int* cap_next, int cap_fixed) {
   int N = H * W;
   double* V = (double*)calloc((size_t)N * (m + 1), sizeof(double));
   double* Hh = (double*)calloc((size_t)(m + 1) * m, sizeof(double)); /* rotated, col-major */
@@ -264,7 +272,10 @@ int orc_gmres(int H, int W, const double* C, const double* b, double* x, double 
       g[j] = cs[j] * g[j];
       if (hist) hist[nh++] = fabs(g[j + 1]) / bnorm;
       kdone = j + 1;
-      if (fabs(g[j + 1]) <= tol * bnorm || breakdown || steps >= maxit) break;
+      /* fixed a: the first cycle of a capturing solve reaches a steps before
+       * the residual test may end it */
+      int short_of_a = cap_fixed && capV != NULL && cycle == 0 && cap_a > 0 && kdone < cap_a;
+      if ((fabs(g[j + 1]) <= tol * bnorm && !short_of_a) || breakdown || steps >= maxit) break;
     }
     /* back substitution R y = g */
     for (int i = kdone - 1; i >= 0; --i) {
@@ -568,6 +579,8 @@ int orc_dense_lu_solve(int n, double* A, double* b, double* x) {
  *            (plain): x0 = 0; mode 2 (warm):
  *            x0 = m_i^{n-1}; mode 3 (exact Galerkin): x0 = V_a G^{-1} V_a^T b_i
  *            with G = V_a^T A_i V_a; then GMRES(m_ref) on A_i to tol_ref.
+ * fixed_a != 0: the seed's basis has the fixed dimension a of Sec. 3 (its
+ * first GMRES cycle takes min(a, m_seed) Arnoldi steps; see orc_gmres).
  * picard > 1 adds Picard iterations k = 2..picard (Sec. 2.3, m~ = m^{n,(k-1)}):
  * the coefficients are rebuilt from the latest iterate, the right-hand side
  * stays m^{n-1}/dt and GMRES starts from that iterate; the seed basis is the
@@ -611,7 +624,7 @@ void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, dou
                     int ntgt, double* mtgt, const int* target_seed, int mode, double tol_seed,
                     int m_seed, int a, double tol_ref, int m_ref, int maxit, int* seed_it,
                     int* tgt_it, double* tgt_res, int* tgt_status, double* tgt_x0res, int picard,
-                    int seed_solver, const int* seed_prev) {
+                    int seed_solver, const int* seed_prev, int fixed_a) {
   int K = picard > 1 ? picard : 1;
   int N = H * W;
   int lda = a + 1;
@@ -647,14 +660,15 @@ void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, dou
       free(Av);
     } else {
       orc_gmres(H, W, C, b, x, tol_seed, m_seed, maxit, &seed_it[s], &rr, NULL, a,
-                basis + (size_t)s * N * (a + 1), hess + (size_t)s * (a + 1) * a, &used[s], &nxt[s]);
+                basis + (size_t)s * N * (a + 1), hess + (size_t)s * (a + 1) * a, &used[s], &nxt[s],
+                fixed_a);
     }
     /* Picard iterations k = 2..K (Sec. 2.3): lag the nonlinear term on the
      * latest iterate, same right-hand side, warm start from that iterate */
     for (int k = 1; k < K; ++k) {
       int it = 0;
       orc_coeffs(H, W, g2, dt, h, x, NULL, NULL, C);
-      orc_gmres(H, W, C, b, x, tol_seed, m_seed, maxit, &it, &rr, NULL, 0, NULL, NULL, NULL, NULL);
+      orc_gmres(H, W, C, b, x, tol_seed, m_seed, maxit, &it, &rr, NULL, 0, NULL, NULL, NULL, NULL, 0);
       seed_it[s] += it;
     }
     memcpy(ms, x, sizeof(double) * N);
@@ -706,12 +720,12 @@ void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, dou
       tgt_x0res[t] = sqrt(rn) / nrm2(N, b);
     }
     tgt_status[t] = orc_gmres(H, W, C, b, x, tol_ref, m_ref, maxit, &tgt_it[t], &tgt_res[t],
-                              NULL, 0, NULL, NULL, NULL, NULL);
+                              NULL, 0, NULL, NULL, NULL, NULL, 0);
     for (int k = 1; k < K; ++k) {               /* Picard iterations, as for the seeds */
       int it = 0;
       orc_coeffs(H, W, g2, dt, h, x, NULL, NULL, C);
       tgt_status[t] = orc_gmres(H, W, C, b, x, tol_ref, m_ref, maxit, &it, &tgt_res[t], NULL, 0,
-                                NULL, NULL, NULL, NULL);
+                                NULL, NULL, NULL, NULL, 0);
       tgt_it[t] += it;
     }
     memcpy(mt, x, sizeof(double) * N);

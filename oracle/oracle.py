@@ -72,14 +72,14 @@ def lib():
         L.orc_csr.restype = _i
         L.orc_csr_matvec.argtypes = [_i, _pi, _pi, _pd, _pd, _pd]
         L.orc_gmres.argtypes = [_i, _i, _pd, _pd, _pd, _d, _i, _i, _pi, _pd, _pd, _i,
-                                _pd, _pd, _pi, _pi]
+                                _pd, _pd, _pi, _pi, _i]
         L.orc_gmres.restype = _i
         L.orc_project.argtypes = [_i, _i, _i, _i, _pd, _pd, _pd, _pd, _pd]
         L.orc_project.restype = _i
         L.orc_dense_lu_solve.argtypes = [_i, _pd, _pd, _pd]
         L.orc_dense_lu_solve.restype = _i
         L.orc_march_step.argtypes = [_i, _i, _d, _d, _d, _i, _pd, _i, _pd, _pi, _i, _d, _i,
-                                     _i, _d, _i, _i, _pi, _pi, _pd, _pi, _pd, _i, _i, _pi]
+                                     _i, _d, _i, _i, _pi, _pi, _pd, _pi, _pd, _i, _i, _pi, _i]
         L.orc_accumulate.argtypes = [_i, _i, _pd, _i, _pd, _i, _pd, _i, _pd, _pd]
         L.orc_accumulate.restype = _i
         L.orc_bicgstab.argtypes = [_i, _i, _pd, _pd, _pd, _d, _i, _pi, _pd, _i, _pd, _pi]
@@ -177,10 +177,12 @@ class GmresResult:
     has_next: int = 0
 
 
-def gmres(H, W, C, b, x0=None, tol=1e-10, m=30, maxit=1000, capture=0):
+def gmres(H, W, C, b, x0=None, tol=1e-10, m=30, maxit=1000, capture=0, fixed=False):
     """Restarted GMRES(m), MGS Arnoldi run twice + Givens (Saad 2003, Alg. 6.9); with
     ``capture=a`` keeps the first cycle's basis and Hessenberg (Sec. 3,
-    Phase 1)."""
+    Phase 1).  ``fixed=True`` gives the basis the fixed dimension min(a, m) of
+    Sec. 3 (Sec. 5.2: a = 20): the first cycle keeps taking Arnoldi steps after
+    the residual test is met, until a steps, an exact breakdown or maxit."""
     N = H * W
     C = np.ascontiguousarray(C, dtype=np.float64).reshape(-1)
     b = _f64(b)
@@ -195,7 +197,7 @@ def gmres(H, W, C, b, x0=None, tol=1e-10, m=30, maxit=1000, capture=0):
         capV = np.zeros((capture + 1) * N)
         capH = np.zeros((capture + 1) * capture)
     st = lib().orc_gmres(H, W, _p(C), _p(b), _p(x), tol, m, maxit, _p(it), _p(rr), _p(hist),
-                         capture, _p(capV), _p(capH), _p(used), _p(nxt))
+                         capture, _p(capV), _p(capH), _p(used), _p(nxt), int(bool(fixed)))
     res = GmresResult(x=x, status=st, iters=int(it[0]), rel_res=float(rr[0]),
                       hist=hist[~np.isnan(hist)])
     if capture > 0:
@@ -316,14 +318,15 @@ SEED_GMRES, SEED_BICGSTAB = 0, 1
 
 def march_step(H, W, dt, h, g2, mseed, mtgt, target_seed, mode=MODE_PROJECTED,
                tol_seed=1e-10, m_seed=40, a=40, tol_ref=1e-8, m_ref=40, maxit=1000, picard=1,
-               seed_solver=SEED_GMRES, seed_prev=None):
+               seed_solver=SEED_GMRES, seed_prev=None, fixed_a=False):
     """One timestep of Sec. 2.3 + Sec. 3 for seeds and targets of one grid
     size (f = 0), with `picard` lagged-linearisation iterations; the seeds are
     solved by GMRES (Arnoldi basis) or BiCGSTAB (Sec. 3, Phase 1 as printed:
     its key vectors, A_proj = V^T A_seed V); ``seed_prev`` (seed cycling, Sec.
     5.2) links each seed to its predecessor (-1: none), whose accumulated basis
     it extends (``accumulate``).  ``mseed`` (nseed, N) and ``mtgt`` (ntgt, N)
-    are updated in place from m^{n-1} to m^n."""
+    are updated in place from m^{n-1} to m^n.  ``fixed_a=True``: every seed
+    basis has the fixed dimension min(a, m_seed) of Sec. 3 (see ``gmres``)."""
     assert mseed.dtype == np.float64 and mseed.flags["C_CONTIGUOUS"]
     assert mtgt.dtype == np.float64 and mtgt.flags["C_CONTIGUOUS"]
     ns, nt = mseed.shape[0], mtgt.shape[0]
@@ -335,7 +338,7 @@ def march_step(H, W, dt, h, g2, mseed, mtgt, target_seed, mode=MODE_PROJECTED,
                          _p(st.tgt_iters), _p(st.tgt_res), _p(st.tgt_status), _p(st.tgt_x0res),
                          int(picard), int(seed_solver),
                          _p(np.ascontiguousarray(seed_prev, dtype=np.int32))
-                         if seed_prev is not None else None)
+                         if seed_prev is not None else None, int(bool(fixed_a)))
     return st
 
 
