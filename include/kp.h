@@ -83,6 +83,14 @@ typedef struct {
                         system on a cluster of this many CTAs (2, 4 or 8; W
                         divisible by it, <= 2048 points per CTA); 0 = clusters
                         only above 4096 points (one 512-thread block below) */
+  int fixed_a;       /* basis dimension of the seed solves (Sec. 3: V_a^n spans
+                        the a-dimensional Krylov space; Sec. 5.2 uses a = 20):
+                        0 = the first restart cycle ends when the seed meets its
+                        tolerance, so a' = min(max_a, steps to converge) vectors
+                        are kept; 1 = the first cycle keeps taking Arnoldi steps
+                        until it has exactly a = min(max_a, m) vectors (fewer
+                        only at an exact breakdown or maxit), and its iterate is
+                        the GMRES minimiser over that whole space            */
 } kp_options;
 
 /* Operator of one system (Sec. 2.3): A(m~; g^2, dt, h, f).  `mtilde` is the
@@ -139,7 +147,8 @@ kp_status kp_rhs(kp_ctx* ctx, int nsys, const kp_op* ops, const double* const* m
  * v_1..v_{a'+1} (v_1 = r0/||r0||) and Hessenberg matrix of every system are
  * kept in the context until the next kp_seed_solve, for kp_store_basis.
  * info: device array of nsys kp_info, or NULL.  1 <= m <= 64; the number of
- * kept vectors a' = min(max_a, steps of the first cycle).
+ * kept vectors a' = min(max_a, steps of the first cycle), which is
+ * min(max_a, m) with kp_options.fixed_a = 1 unless Arnoldi breaks down.
  */
 kp_status kp_seed_solve(kp_ctx* ctx, int nsys, const kp_op* ops, const double* const* b,
                         double* const* x, double tol, int m, int maxit, kp_info* info);

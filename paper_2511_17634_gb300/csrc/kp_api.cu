@@ -255,6 +255,7 @@ kp_status run_gmres(kp_ctx* c, int nsys, const kp_op* ops, const double* const* 
     p.capMeta = c->capMeta;
     p.cap_a = c->opt.max_a;
     p.cap_ld = c->opt.max_n;
+    p.fixed_a = c->opt.fixed_a;
   }
   (void)ept; (void)nt; (void)smem;
   e = kp::launch_solver(p, sh, mixed, c->stream);
@@ -279,6 +280,7 @@ void kp_options_default(kp_options* o) {
   o->block_threads = 0;
   o->blocks_per_sm = 0;
   o->cluster_size = 0;
+  o->fixed_a = 0;
 }
 
 kp_status kp_create(kp_ctx** out, const kp_options* opt, void* stream) {
@@ -291,7 +293,8 @@ kp_status kp_create(kp_ctx** out, const kp_options* opt, void* stream) {
       (o.precision != KP_PREC_FP64 && o.precision != KP_PREC_MIXED) ||
       o.smem_vectors < 0 || (o.reorth != 0 && o.reorth != 1) ||
       (o.block_threads != 0 && o.block_threads != 64 && o.block_threads != 128 && o.block_threads != 256) ||
-      (o.cluster_size != 0 && o.cluster_size != 2 && o.cluster_size != 4 && o.cluster_size != 8))
+      (o.cluster_size != 0 && o.cluster_size != 2 && o.cluster_size != 4 && o.cluster_size != 8) ||
+      (o.fixed_a != 0 && o.fixed_a != 1))
     return KP_ERR_ARG;
   {
     // solver shapes compiled for grids of <= 1024 points: (threads, blocks per SM)

@@ -311,7 +311,9 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
       const double res = fabs(gv[j + 1]);
       sc[3] = ihn;
       fl[1] = b;
-      fl[2] = (res <= target) || b || (steps >= p.maxit) || (j + 1 == m);
+      // fixed basis dimension (as in the one-block mixed solver)
+      const bool short_of_a = p.fixed_a && capture && first && j + 1 < p.cap_a;
+      fl[2] = (res <= target && !short_of_a) || b || (steps >= p.maxit) || (j + 1 == m);
     };
     for (int j = 0; j < m; ++j) {
       cluster.sync();                             // v_j slices visible cluster-wide

@@ -734,7 +734,10 @@ __global__ void __launch_bounds__(NT, MINB) gmres_fp64_kernel(const GmresParams 
           const double res = fabs(sm.g[j + 1]);
           sm.sc[3] = ihn;
           sm.fl[1] = b;
-          sm.fl[2] = (res <= p.tol * bnorm) || b || (steps >= p.maxit) || (j + 1 == m);
+          // fixed basis dimension: the capture cycle reaches cap_a steps
+          // before the residual test may end it
+          const bool short_of_a = p.fixed_a && capture && cycle == 0 && j + 1 < p.cap_a;
+          sm.fl[2] = (res <= p.tol * bnorm && !short_of_a) || b || (steps >= p.maxit) || (j + 1 == m);
         };
         for (int j = 0; j < m; ++j) {
           __syncthreads();                       // v_j complete

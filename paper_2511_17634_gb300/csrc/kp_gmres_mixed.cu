@@ -319,7 +319,10 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
         const double res = fabs(sm.g[j + 1]);
         sm.sc[3] = ihn;
         sm.fl[1] = b;
-        sm.fl[2] = (res <= target) || b || (steps >= p.maxit) || (j + 1 == m);
+        // fixed basis dimension: the seed's captured cycle reaches cap_a steps
+        // before the residual test may end it
+        const bool short_of_a = p.fixed_a && capture && first && j + 1 < p.cap_a;
+        sm.fl[2] = (res <= target && !short_of_a) || b || (steps >= p.maxit) || (j + 1 == m);
       };
       for (int j = 0; j < m; ++j) {
         __syncthreads();

@@ -83,6 +83,8 @@ struct GmresParams {
   CapMeta* capMeta; // [nsys]
   int cap_a;
   int cap_ld;
+  int fixed_a;      // 1: the capture cycle takes min(cap_a, m) steps before the
+                    // residual test may end it (fixed basis dimension, Sec. 3)
   // time march: timestep index and g^2 schedule in device memory (graph replay)
   const int* step;          // null = not marching
   const double* g2_sched;   // if step: g2 = g2_sched[*step + step_offset] for every system

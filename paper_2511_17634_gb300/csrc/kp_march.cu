@@ -183,6 +183,7 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset,
     g.capH = c->slotH;
     g.cap_a = c->opt.max_a;
     g.cap_ld = c->opt.max_n;
+    g.fixed_a = c->opt.fixed_a;
     g.factor = 1;
     g.acc_kind = 0;
   } else {

@@ -32,7 +32,8 @@ class _Options(ctypes.Structure):
     _fields_ = [("max_seeds", ctypes.c_int), ("max_a", ctypes.c_int), ("max_n", ctypes.c_int),
                 ("precision", ctypes.c_int), ("smem_vectors", ctypes.c_int),
                 ("reorth", ctypes.c_int), ("block_threads", ctypes.c_int),
-                ("blocks_per_sm", ctypes.c_int), ("cluster_size", ctypes.c_int)]
+                ("blocks_per_sm", ctypes.c_int), ("cluster_size", ctypes.c_int),
+                ("fixed_a", ctypes.c_int)]
 
 
 # kp_op: int H, W; double dt, g2, h; const double *mtilde, *fx, *fy
@@ -160,7 +161,8 @@ class Context:
     """A kp_ctx bound to a CUDA stream (default: torch's current stream)."""
 
     def __init__(self, max_seeds=64, max_a=40, max_n=4096, precision=PREC_FP64, smem_vectors=0,
-                 reorth=0, stream=None, block_threads=0, blocks_per_sm=0, cluster_size=0):
+                 reorth=0, stream=None, block_threads=0, blocks_per_sm=0, cluster_size=0,
+                 fixed_a=False):
         import torch
         L = lib()
         o = _Options()
@@ -170,6 +172,7 @@ class Context:
         o.block_threads = block_threads
         o.blocks_per_sm = blocks_per_sm
         o.cluster_size = cluster_size
+        o.fixed_a = int(bool(fixed_a))
         self._h = ctypes.c_void_p()
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
