@@ -3,6 +3,17 @@ paper): 3x3 convolutions with zero padding, ReLU between layers, MSE loss,
 Adam.  TEST INFRASTRUCTURE ONLY -- used by tests/ to check the GPU forward
 and backward kernels; it shares no code with them.
 
+The network's kernels multiply BF16 operands with FP32 accumulation.  To
+state their error bound rather than guess it, ``forward`` and
+``loss_and_grads`` take an optional ``operand_round``: applied to exactly
+the operands a BF16 tensor-core product would see -- every convolution's
+input planes and weights in the forward pass; the output gradient, the
+layer input and the weights in the two backward products -- while biases,
+the bias gradient and every sum stay FP64.  ``bf16`` is that rounding
+(nearest bfloat16, ties to even).  With it the reference differs from the
+kernels only by FP32 accumulation; without it (the default) it is the
+exact FP64 network.
+
 Planes are arrays [batch][channel][W][H] (x index i first, y index j second,
 the solver's vector order).  A layer's weights are [c_out][c_in][3][3] with
 tap [di+1][dj+1] multiplying the input at (i+di, j+dj); the flat parameter
@@ -27,6 +38,19 @@ def flatten(layers):
     return np.concatenate([np.concatenate([w.ravel(), b.ravel()]) for w, b in layers])
 
 
+def bf16(a):
+    """Round to the nearest bfloat16 (8 significant bits, ties to even), via
+    float32 as a device conversion from an FP32 value does; returns float64."""
+    f = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + np.uint64(0x7FFF) + ((u >> np.uint64(16)) & np.uint64(1))) & np.uint64(0xFFFF0000)
+    return u.astype(np.uint32).view(np.float32).astype(np.float64).reshape(np.shape(a))
+
+
+def _ident(a):
+    return a
+
+
 def conv(x, w, b):
     """z[b,o,i,j] = b[o] + sum_{c,di,dj} w[o,c,di+1,dj+1] x[b,c,i+di,j+dj] (zero outside)."""
     B, C, W, H = x.shape
@@ -39,20 +63,26 @@ def conv(x, w, b):
     return z
 
 
-def forward(params, channels, x):
-    """All layer outputs (post-activation; the last layer is linear)."""
+def forward(params, channels, x, operand_round=None):
+    """All layer outputs (post-activation; the last layer is linear).
+    operand_round (e.g. ``bf16``) rounds each convolution's input planes and
+    weights first."""
+    rnd = operand_round or _ident
     acts = [x]
     layers = unflatten(params, channels)
     for k, (w, b) in enumerate(layers):
-        z = conv(acts[-1], w, b)
+        z = conv(rnd(acts[-1]), rnd(w), b)
         acts.append(np.maximum(z, 0.0) if k + 1 < len(layers) else z)
     return acts
 
 
-def loss_and_grads(params, channels, x, target):
-    """MSE over all outputs and its gradient with respect to every parameter."""
+def loss_and_grads(params, channels, x, target, operand_round=None):
+    """MSE over all outputs and its gradient with respect to every parameter.
+    operand_round rounds the operands of the forward convolutions and of the
+    two backward products (output gradient, layer input, weights)."""
+    rnd = operand_round or _ident
     layers = unflatten(params, channels)
-    acts = forward(params, channels, x)
+    acts = forward(params, channels, x, operand_round)
     out = acts[-1]
     n = out.size
     loss = float(np.mean((out - target) ** 2))
@@ -62,21 +92,23 @@ def loss_and_grads(params, channels, x, target):
         w, b = layers[k]
         xin = acts[k]
         B, C, W, H = xin.shape
-        xp = np.pad(xin, ((0, 0), (0, 0), (1, 1), (1, 1)))
+        xp = np.pad(rnd(xin), ((0, 0), (0, 0), (1, 1), (1, 1)))
+        dzr = rnd(dz)
         dw = np.zeros_like(w)
         for di in (-1, 0, 1):
             for dj in (-1, 0, 1):
-                dw[:, :, di + 1, dj + 1] = np.einsum("boij,bcij->oc", dz,
+                dw[:, :, di + 1, dj + 1] = np.einsum("boij,bcij->oc", dzr,
                                                      xp[:, :, 1 + di:1 + di + W, 1 + dj:1 + dj + H])
         db = dz.sum(axis=(0, 2, 3))
         grads.append((dw, db))
         if k == 0:
             break
-        dzp = np.pad(dz, ((0, 0), (0, 0), (1, 1), (1, 1)))
+        dzp = np.pad(dzr, ((0, 0), (0, 0), (1, 1), (1, 1)))
+        wr = rnd(w)
         dx = np.zeros_like(xin)
         for di in (-1, 0, 1):
             for dj in (-1, 0, 1):
-                dx += np.einsum("oc,boij->bcij", w[:, :, di + 1, dj + 1],
+                dx += np.einsum("oc,boij->bcij", wr[:, :, di + 1, dj + 1],
                                 dzp[:, :, 1 - di:1 - di + W, 1 - dj:1 - dj + H])
         dz = dx * (acts[k] > 0)                  # through the previous ReLU
     return loss, flatten(grads[::-1])
@@ -89,3 +121,43 @@ def adam(params, grads, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     mh = m / (1 - b1 ** t)
     vh = v / (1 - b2 ** t)
     return params - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+# ---------------------------------------------------------------------------
+# The learned initial guess of a target solve at timestep n (not in the
+# paper; the workload's learned-guess configuration).  Reading of "inputs =
+# target image + seed solution at timestep t + t embedding": the target image
+# as the march has carried it to timestep n-1 (its lagged field m_i^{n-1};
+# the image itself at n = 1), the seed's solution m_seed^n of the same
+# timestep, and four time planes.  The network predicts the step's change in
+# units of s_n = dt (g^n)^2 / h^2 (the coefficient of the pixel Laplacian in
+# the implicit step), so the guess is x_init = m_i^{n-1} + s_n * net(...).
+
+def network_inputs(mprev, mseed, n, T):
+    """Planes [B][6][N]: m_i^{n-1}, m_seed^n, sin 2 pi tau, cos 2 pi tau,
+    sin 4 pi tau, cos 4 pi tau with tau = n / T (n = 1..T)."""
+    mprev = np.asarray(mprev, dtype=np.float64)
+    B, N = mprev.shape
+    tau = n / T
+    out = np.empty((B, 6, N))
+    out[:, 0] = mprev
+    out[:, 1] = np.asarray(mseed, dtype=np.float64).reshape(B, N)
+    for k, v in enumerate((np.sin(2 * np.pi * tau), np.cos(2 * np.pi * tau),
+                           np.sin(4 * np.pi * tau), np.cos(4 * np.pi * tau))):
+        out[:, 2 + k] = v
+    return out
+
+
+def guess_scale(T, g2n, H):
+    """s_n = dt (g^n)^2 / h^2 with dt = 1/T, h = 1/H."""
+    return (1.0 / T) * g2n * H * H
+
+
+def learned_guess(params, channels, mprev, mseed, n, T, g2n, H, W, operand_round=None):
+    """x_init = m_i^{n-1} + s_n * net([m_i^{n-1}, m_seed^n, time planes]) for a
+    batch of target channels ([B][N] arrays, N = H*W in the solver order)."""
+    mprev = np.asarray(mprev, dtype=np.float64)
+    B, N = mprev.shape
+    x = network_inputs(mprev, mseed, n, T).reshape(B, 6, W, H)
+    d = forward(params, channels, x, operand_round)[-1].reshape(B, N)
+    return mprev + guess_scale(T, g2n, H) * d

@@ -578,7 +578,11 @@ int orc_dense_lu_solve(int n, double* A, double* b, double* x) {
  *            which serve the accumulated basis of orc_accumulate); mode 1
  *            (plain): x0 = 0; mode 2 (warm):
  *            x0 = m_i^{n-1}; mode 3 (exact Galerkin): x0 = V_a G^{-1} V_a^T b_i
- *            with G = V_a^T A_i V_a; then GMRES(m_ref) on A_i to tol_ref.
+ *            with G = V_a^T A_i V_a; mode 4 (a given initial guess, projected in
+ *            residual form): x0 = xinit_i + V_a H_a^{-1} V_a^T (b_i - A_i xinit_i)
+ *            (the explicit A_proj after BiCGSTAB or cycled seeds); mode 5 (the
+ *            given guess alone): x0 = xinit_i; then GMRES(m_ref) on A_i to tol_ref.
+ *            xinit ([ntgt][N], modes 4 and 5 only) is read, never written.
  * fixed_a != 0: the seed's basis has the fixed dimension a of Sec. 3 (its
  * first GMRES cycle takes min(a, m_seed) Arnoldi steps; see orc_gmres).
  * picard > 1 adds Picard iterations k = 2..picard (Sec. 2.3, m~ = m^{n,(k-1)}):
@@ -624,7 +628,7 @@ void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, dou
                     int ntgt, double* mtgt, const int* target_seed, int mode, double tol_seed,
                     int m_seed, int a, double tol_ref, int m_ref, int maxit, int* seed_it,
                     int* tgt_it, double* tgt_res, int* tgt_status, double* tgt_x0res, int picard,
-                    int seed_solver, const int* seed_prev, int fixed_a) {
+                    int seed_solver, const int* seed_prev, int fixed_a, const double* xinit) {
   int K = picard > 1 ? picard : 1;
   int N = H * W;
   int lda = a + 1;
@@ -699,7 +703,24 @@ void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, dou
     double* mt = mtgt + (size_t)t * N;
     orc_coeffs(H, W, g2, dt, h, mt, NULL, NULL, C);
     orc_rhs(H, W, dt, h, mt, NULL, NULL, b);
-    if (mode == 0 && dense[target_seed[t]]) {
+    if (mode == 4 || mode == 5) {
+      /* a given initial guess; mode 4 projects its residual (Sec. 3, Phase 2
+       * applied to r = b - A x_init) */
+      const double* xi = xinit + (size_t)t * N;
+      if (mode == 5) {
+        memcpy(x, xi, sizeof(double) * N);
+      } else {
+        int s = target_seed[t];
+        orc_apply(H, W, C, xi, r);
+        for (int k = 0; k < N; ++k) r[k] = b[k] - r[k];
+        if (dense[s])
+          orc_project_dense(N, used[s], basis + (size_t)s * N * (a + 1), aproj + (size_t)s * a * a, r,
+                            xi, x);
+        else
+          orc_project(N, used[s], lda, nxt[s], basis + (size_t)s * N * (a + 1),
+                      hess + (size_t)s * (a + 1) * a, r, xi, x);
+      }
+    } else if (mode == 0 && dense[target_seed[t]]) {
       int s = target_seed[t];
       orc_project_dense(N, used[s], basis + (size_t)s * N * (a + 1), aproj + (size_t)s * a * a, b,
                         NULL, x);

@@ -79,7 +79,7 @@ def lib():
         L.orc_dense_lu_solve.argtypes = [_i, _pd, _pd, _pd]
         L.orc_dense_lu_solve.restype = _i
         L.orc_march_step.argtypes = [_i, _i, _d, _d, _d, _i, _pd, _i, _pd, _pi, _i, _d, _i,
-                                     _i, _d, _i, _i, _pi, _pi, _pd, _pi, _pd, _i, _i, _pi, _i]
+                                     _i, _d, _i, _i, _pi, _pi, _pd, _pi, _pd, _i, _i, _pi, _i, _pd]
         L.orc_accumulate.argtypes = [_i, _i, _pd, _i, _pd, _i, _pd, _i, _pd, _pd]
         L.orc_accumulate.restype = _i
         L.orc_bicgstab.argtypes = [_i, _i, _pd, _pd, _pd, _d, _i, _pi, _pd, _i, _pd, _pi]
@@ -290,6 +290,7 @@ def dense_lu_solve(A, b):
 
 
 MODE_PROJECTED, MODE_PLAIN, MODE_WARM, MODE_GALERKIN = 0, 1, 2, 3
+MODE_GUESS_PROJECTED, MODE_GUESS = 4, 5   # a given initial guess, with / without projection
 
 
 def project_galerkin(H, W, C, V, a, r, xinit=None):
@@ -318,7 +319,7 @@ SEED_GMRES, SEED_BICGSTAB = 0, 1
 
 def march_step(H, W, dt, h, g2, mseed, mtgt, target_seed, mode=MODE_PROJECTED,
                tol_seed=1e-10, m_seed=40, a=40, tol_ref=1e-8, m_ref=40, maxit=1000, picard=1,
-               seed_solver=SEED_GMRES, seed_prev=None, fixed_a=False):
+               seed_solver=SEED_GMRES, seed_prev=None, fixed_a=False, xinit=None):
     """One timestep of Sec. 2.3 + Sec. 3 for seeds and targets of one grid
     size (f = 0), with `picard` lagged-linearisation iterations; the seeds are
     solved by GMRES (Arnoldi basis) or BiCGSTAB (Sec. 3, Phase 1 as printed:
@@ -326,11 +327,17 @@ def march_step(H, W, dt, h, g2, mseed, mtgt, target_seed, mode=MODE_PROJECTED,
     5.2) links each seed to its predecessor (-1: none), whose accumulated basis
     it extends (``accumulate``).  ``mseed`` (nseed, N) and ``mtgt`` (ntgt, N)
     are updated in place from m^{n-1} to m^n.  ``fixed_a=True``: every seed
-    basis has the fixed dimension min(a, m_seed) of Sec. 3 (see ``gmres``)."""
+    basis has the fixed dimension min(a, m_seed) of Sec. 3 (see ``gmres``).
+    ``xinit`` (ntgt, N): the targets' initial guesses for modes
+    MODE_GUESS_PROJECTED (x0 = xinit + V_a H_a^{-1} V_a^T (b - A xinit), Sec. 3
+    Phase 2 in residual form) and MODE_GUESS (x0 = xinit)."""
     assert mseed.dtype == np.float64 and mseed.flags["C_CONTIGUOUS"]
     assert mtgt.dtype == np.float64 and mtgt.flags["C_CONTIGUOUS"]
     ns, nt = mseed.shape[0], mtgt.shape[0]
     ts = np.ascontiguousarray(target_seed, dtype=np.int32)
+    if mode in (MODE_GUESS_PROJECTED, MODE_GUESS):
+        assert xinit is not None and xinit.shape == mtgt.shape
+    xi = None if xinit is None else np.ascontiguousarray(xinit, dtype=np.float64)
     st = StepStats(np.zeros(ns, np.int32), np.zeros(nt, np.int32), np.zeros(nt),
                    np.zeros(nt, np.int32), np.zeros(nt))
     lib().orc_march_step(H, W, dt, h, g2, ns, _p(mseed), nt, _p(mtgt), _p(ts), mode,
@@ -338,7 +345,7 @@ def march_step(H, W, dt, h, g2, mseed, mtgt, target_seed, mode=MODE_PROJECTED,
                          _p(st.tgt_iters), _p(st.tgt_res), _p(st.tgt_status), _p(st.tgt_x0res),
                          int(picard), int(seed_solver),
                          _p(np.ascontiguousarray(seed_prev, dtype=np.int32))
-                         if seed_prev is not None else None, int(bool(fixed_a)))
+                         if seed_prev is not None else None, int(bool(fixed_a)), _p(xi))
     return st
 
 
@@ -388,3 +395,35 @@ def march_scores(H, W, T, g2, seeds, targets, target_seed, steps=None, **kw):
         march_step(H, W, dt, h, float(g2[n]), ms, mt, target_seed, **kw)
         scores.append(np.stack([np.stack(score(H, W, h, mt[k])) for k in range(nt)]))
     return ms, mt, np.stack(scores), emb
+
+
+def march_learned(H, W, T, g2, seeds, targets, target_seed, params, channels, steps=None,
+                  project=True, operand_round=None, tol_seed=1e-10, m_seed=40, a=40,
+                  fixed_a=False, maxit=1000, **kw):
+    """The march with the learned initial guess (``cnn_oracle.learned_guess``):
+    at every timestep the seeds are solved first (the same GMRES solve the
+    march step repeats), the network maps [m_i^{n-1}, m_seed^n, time planes]
+    to x_init = m_i^{n-1} + s_n * net, and the targets start from x_init
+    projected in residual form onto the seed basis (``project``; Sec. 3,
+    Phase 2 applied to b - A x_init) or from x_init itself, then GMRES.
+    Returns (m_seed, m_target, list of StepStats)."""
+    from . import cnn_oracle as R
+    dt, h = 1.0 / T, 1.0 / H
+    ms = np.array(seeds, dtype=np.float64).reshape(len(seeds), -1).copy()
+    mt = np.array(targets, dtype=np.float64).reshape(len(targets), -1).copy()
+    ts = np.asarray(target_seed, dtype=np.int64)
+    stats = []
+    for n in range(steps if steps is not None else T):
+        g2n = float(g2[n])
+        snew = np.empty_like(ms)
+        for s in range(len(ms)):
+            C = coeffs(H, W, g2n, dt, h, ms[s])
+            snew[s] = gmres(H, W, C, rhs(H, W, dt, h, ms[s]), tol=tol_seed, m=m_seed, maxit=maxit,
+                            capture=a, fixed=fixed_a).x
+        xin = R.learned_guess(params, channels, mt, snew[ts], n + 1, T, g2n, H, W, operand_round)
+        stats.append(march_step(H, W, dt, h, g2n, ms, mt, target_seed,
+                                mode=MODE_GUESS_PROJECTED if project else MODE_GUESS,
+                                tol_seed=tol_seed, m_seed=m_seed, a=a, maxit=maxit,
+                                fixed_a=fixed_a, xinit=xin, **kw))
+        assert np.array_equal(ms, snew)
+    return ms, mt, stats
