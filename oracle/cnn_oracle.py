@@ -132,19 +132,32 @@ def adam(params, grads, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
 # timestep, and four time planes.  The network predicts the step's change in
 # units of s_n = dt (g^n)^2 / h^2 (the coefficient of the pixel Laplacian in
 # the implicit step), so the guess is x_init = m_i^{n-1} + s_n * net(...).
+#
+# The two fields enter as two planes each, hi = bf16(m) and lo = 256 (m - hi):
+# one BF16 plane carries 8 significant bits (an absolute 2e-3 at m = 0.5),
+# and the step's change is a difference of neighbouring values a few hundred
+# times smaller than m, so one plane would bury it in rounding; the pair
+# carries about 16 bits and the first layer's products recombine it.
+
+def split_hi_lo(m):
+    """(hi, lo) with hi = bf16(m), lo = 256 (m - hi); m = hi + lo / 256."""
+    m = np.asarray(m, dtype=np.float64)
+    hi = bf16(m)
+    return hi, 256.0 * (m - hi)
+
 
 def network_inputs(mprev, mseed, n, T):
-    """Planes [B][6][N]: m_i^{n-1}, m_seed^n, sin 2 pi tau, cos 2 pi tau,
-    sin 4 pi tau, cos 4 pi tau with tau = n / T (n = 1..T)."""
+    """Planes [B][8][N]: m_i^{n-1} (hi, lo), m_seed^n (hi, lo), sin 2 pi tau,
+    cos 2 pi tau, sin 4 pi tau, cos 4 pi tau with tau = n / T (n = 1..T)."""
     mprev = np.asarray(mprev, dtype=np.float64)
     B, N = mprev.shape
     tau = n / T
-    out = np.empty((B, 6, N))
-    out[:, 0] = mprev
-    out[:, 1] = np.asarray(mseed, dtype=np.float64).reshape(B, N)
+    out = np.empty((B, 8, N))
+    out[:, 0], out[:, 1] = split_hi_lo(mprev)
+    out[:, 2], out[:, 3] = split_hi_lo(np.asarray(mseed, dtype=np.float64).reshape(B, N))
     for k, v in enumerate((np.sin(2 * np.pi * tau), np.cos(2 * np.pi * tau),
                            np.sin(4 * np.pi * tau), np.cos(4 * np.pi * tau))):
-        out[:, 2 + k] = v
+        out[:, 4 + k] = v
     return out
 
 
@@ -158,6 +171,6 @@ def learned_guess(params, channels, mprev, mseed, n, T, g2n, H, W, operand_round
     batch of target channels ([B][N] arrays, N = H*W in the solver order)."""
     mprev = np.asarray(mprev, dtype=np.float64)
     B, N = mprev.shape
-    x = network_inputs(mprev, mseed, n, T).reshape(B, 6, W, H)
+    x = network_inputs(mprev, mseed, n, T).reshape(B, 8, W, H)
     d = forward(params, channels, x, operand_round)[-1].reshape(B, N)
     return mprev + guess_scale(T, g2n, H) * d

@@ -90,8 +90,15 @@ def lib():
         L.orc_project_galerkin.argtypes = [_i, _i, _pd, _i, _pd, _pd, _pd, _pd]
         L.orc_project_galerkin.restype = _i
         L.orc_embed_step.argtypes = [_i, _d, _d, _pd, _pd, _pd, _pd]
+        L.orc_set_threads.argtypes = [_i]
         _lib = L
     return _lib
+
+
+def set_threads(n):
+    """Threads of the oracle's OpenMP loops over independent systems (no
+    effect when it was built without OpenMP)."""
+    lib().orc_set_threads(int(n))
 
 
 def _p(a):
@@ -329,8 +336,9 @@ def march_step(H, W, dt, h, g2, mseed, mtgt, target_seed, mode=MODE_PROJECTED,
     are updated in place from m^{n-1} to m^n.  ``fixed_a=True``: every seed
     basis has the fixed dimension min(a, m_seed) of Sec. 3 (see ``gmres``).
     ``xinit`` (ntgt, N): the targets' initial guesses for modes
-    MODE_GUESS_PROJECTED (x0 = xinit + V_a H_a^{-1} V_a^T (b - A xinit), Sec. 3
-    Phase 2 in residual form) and MODE_GUESS (x0 = xinit)."""
+    MODE_GUESS_PROJECTED (start x_s = xinit, or m^{n-1} when its residual is
+    smaller; x0 = x_s + V_a H_a^{-1} V_a^T (b - A x_s), Sec. 3 Phase 2 in
+    residual form) and MODE_GUESS (x0 = xinit)."""
     assert mseed.dtype == np.float64 and mseed.flags["C_CONTIGUOUS"]
     assert mtgt.dtype == np.float64 and mtgt.flags["C_CONTIGUOUS"]
     ns, nt = mseed.shape[0], mtgt.shape[0]
@@ -399,13 +407,15 @@ def march_scores(H, W, T, g2, seeds, targets, target_seed, steps=None, **kw):
 
 def march_learned(H, W, T, g2, seeds, targets, target_seed, params, channels, steps=None,
                   project=True, operand_round=None, tol_seed=1e-10, m_seed=40, a=40,
-                  fixed_a=False, maxit=1000, **kw):
+                  fixed_a=False, maxit=1000, n0=0, **kw):
     """The march with the learned initial guess (``cnn_oracle.learned_guess``):
     at every timestep the seeds are solved first (the same GMRES solve the
     march step repeats), the network maps [m_i^{n-1}, m_seed^n, time planes]
     to x_init = m_i^{n-1} + s_n * net, and the targets start from x_init
-    projected in residual form onto the seed basis (``project``; Sec. 3,
+    judged against the warm start m_i^{n-1} (the smaller residual is kept)
+    and projected in residual form onto the seed basis (``project``; Sec. 3,
     Phase 2 applied to b - A x_init) or from x_init itself, then GMRES.
+    The states are those of timestep n0 (the march runs n0+1 .. n0+steps).
     Returns (m_seed, m_target, list of StepStats)."""
     from . import cnn_oracle as R
     dt, h = 1.0 / T, 1.0 / H
@@ -413,7 +423,7 @@ def march_learned(H, W, T, g2, seeds, targets, target_seed, params, channels, st
     mt = np.array(targets, dtype=np.float64).reshape(len(targets), -1).copy()
     ts = np.asarray(target_seed, dtype=np.int64)
     stats = []
-    for n in range(steps if steps is not None else T):
+    for n in range(n0, n0 + (steps if steps is not None else T - n0)):
         g2n = float(g2[n])
         snew = np.empty_like(ms)
         for s in range(len(ms)):
