@@ -129,7 +129,11 @@ def adam(params, grads, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
 # target image + seed solution at timestep t + t embedding": the target image
 # as the march has carried it to timestep n-1 (its lagged field m_i^{n-1};
 # the image itself at n = 1), the seed's solution m_seed^n of the same
-# timestep, and four time planes.  The network predicts the step's change in
+# timestep, and four time planes tau, 1 - tau, sin(pi tau), cos(pi tau) for
+# tau = n / T (each distinct over 0 < tau <= 1, unlike harmonics of 2 pi tau,
+# which confuse the first timesteps with the last -- while the implicit
+# step's damping of fine detail grows with dt (g^n)^2 over the march).  The
+# network predicts the step's change in
 # units of s_n = dt (g^n)^2 / h^2 (the coefficient of the pixel Laplacian in
 # the implicit step), so the guess is x_init = m_i^{n-1} + s_n * net(...).
 #
@@ -147,16 +151,15 @@ def split_hi_lo(m):
 
 
 def network_inputs(mprev, mseed, n, T):
-    """Planes [B][8][N]: m_i^{n-1} (hi, lo), m_seed^n (hi, lo), sin 2 pi tau,
-    cos 2 pi tau, sin 4 pi tau, cos 4 pi tau with tau = n / T (n = 1..T)."""
+    """Planes [B][8][N]: m_i^{n-1} (hi, lo), m_seed^n (hi, lo), tau, 1 - tau,
+    sin pi tau, cos pi tau with tau = n / T (n = 1..T)."""
     mprev = np.asarray(mprev, dtype=np.float64)
     B, N = mprev.shape
     tau = n / T
     out = np.empty((B, 8, N))
     out[:, 0], out[:, 1] = split_hi_lo(mprev)
     out[:, 2], out[:, 3] = split_hi_lo(np.asarray(mseed, dtype=np.float64).reshape(B, N))
-    for k, v in enumerate((np.sin(2 * np.pi * tau), np.cos(2 * np.pi * tau),
-                           np.sin(4 * np.pi * tau), np.cos(4 * np.pi * tau))):
+    for k, v in enumerate((tau, 1.0 - tau, np.sin(np.pi * tau), np.cos(np.pi * tau))):
         out[:, 4 + k] = v
     return out
 

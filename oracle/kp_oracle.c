@@ -582,12 +582,14 @@ int orc_dense_lu_solve(int n, double* A, double* b, double* x) {
  *            (plain): x0 = 0; mode 2 (warm):
  *            x0 = m_i^{n-1}; mode 3 (exact Galerkin): x0 = V_a G^{-1} V_a^T b_i
  *            with G = V_a^T A_i V_a; mode 4 (a given initial guess, judged and
- *            projected in residual form): the start x_s is xinit_i, or the warm
- *            start m_i^{n-1} when its residual norm is strictly smaller (the
- *            method without the guess is the guess's fallback and its residual
- *            the judge), then x0 = x_s + V_a H_a^{-1} V_a^T (b_i - A_i x_s) (the
- *            explicit A_proj after BiCGSTAB or cycled seeds); mode 5 (the given
- *            guess alone): x0 = xinit_i; then GMRES(m_ref) on A_i to tol_ref.
+ *            projected in residual form): the guess xinit_i is kept unless the
+ *            warm start m_i^{n-1} leaves a strictly smaller residual norm (the
+ *            method without the guess is the guess's fallback and the residual
+ *            the judge); a kept guess is projected, x0 = xinit_i + V_a H_a^{-1}
+ *            V_a^T (b_i - A_i xinit_i) (the explicit A_proj after BiCGSTAB or
+ *            cycled seeds), the fallback starts as mode 2 does, x0 = m_i^{n-1};
+ *            mode 5 (the given guess alone): x0 = xinit_i; then GMRES(m_ref)
+ *            on A_i to tol_ref.
  *            xinit ([ntgt][N], modes 4 and 5 only) is read, never written.
  * fixed_a != 0: the seed's basis has the fixed dimension a of Sec. 3 (its
  * first GMRES cycle takes min(a, m_seed) Arnoldi steps; see orc_gmres).
@@ -722,11 +724,9 @@ void orc_march_step(int H, int W, double dt, double h, double g2, int nseed, dou
         for (int k = 0; k < N; ++k) r[k] = b[k] - r[k];
         orc_apply(H, W, C, mt, rw);                    /* the warm start m^{n-1} */
         for (int k = 0; k < N; ++k) rw[k] = b[k] - rw[k];
-        if (nrm2(N, rw) < nrm2(N, r)) {
-          memcpy(r, rw, sizeof(double) * N);
-          xi = mt;
-        }
-        if (dense[s])
+        if (nrm2(N, rw) < nrm2(N, r))                  /* the fallback, as in mode 2 */
+          memcpy(x, mt, sizeof(double) * N);
+        else if (dense[s])
           orc_project_dense(N, used[s], basis + (size_t)s * N * (a + 1), aproj + (size_t)s * a * a, r,
                             xi, x);
         else

@@ -336,9 +336,9 @@ def march_step(H, W, dt, h, g2, mseed, mtgt, target_seed, mode=MODE_PROJECTED,
     are updated in place from m^{n-1} to m^n.  ``fixed_a=True``: every seed
     basis has the fixed dimension min(a, m_seed) of Sec. 3 (see ``gmres``).
     ``xinit`` (ntgt, N): the targets' initial guesses for modes
-    MODE_GUESS_PROJECTED (start x_s = xinit, or m^{n-1} when its residual is
-    smaller; x0 = x_s + V_a H_a^{-1} V_a^T (b - A x_s), Sec. 3 Phase 2 in
-    residual form) and MODE_GUESS (x0 = xinit)."""
+    MODE_GUESS_PROJECTED (x0 = xinit + V_a H_a^{-1} V_a^T (b - A xinit), Sec. 3
+    Phase 2 in residual form, unless the warm start m^{n-1} leaves a smaller
+    residual than xinit: then x0 = m^{n-1}) and MODE_GUESS (x0 = xinit)."""
     assert mseed.dtype == np.float64 and mseed.flags["C_CONTIGUOUS"]
     assert mtgt.dtype == np.float64 and mtgt.flags["C_CONTIGUOUS"]
     ns, nt = mseed.shape[0], mtgt.shape[0]
@@ -412,9 +412,10 @@ def march_learned(H, W, T, g2, seeds, targets, target_seed, params, channels, st
     at every timestep the seeds are solved first (the same GMRES solve the
     march step repeats), the network maps [m_i^{n-1}, m_seed^n, time planes]
     to x_init = m_i^{n-1} + s_n * net, and the targets start from x_init
-    judged against the warm start m_i^{n-1} (the smaller residual is kept)
-    and projected in residual form onto the seed basis (``project``; Sec. 3,
-    Phase 2 applied to b - A x_init) or from x_init itself, then GMRES.
+    projected in residual form onto the seed basis (``project``; Sec. 3,
+    Phase 2 applied to b - A x_init) -- or from the warm start m_i^{n-1}
+    when that leaves a smaller residual than x_init -- or from x_init
+    itself, then GMRES.
     The states are those of timestep n0 (the march runs n0+1 .. n0+steps).
     Returns (m_seed, m_target, list of StepStats)."""
     from . import cnn_oracle as R

@@ -1,12 +1,11 @@
 """Pins of the oracle's learned-guess march (the workload's learned initial
 guess; Sec. 3, Phase 2 applied to the residual of a given guess).
 
-* Mode 4 (a given guess, judged against the warm start and projected in
-  residual form) from a guess worse than the warm start is the projection of
-  the warm start's residual, from x_init = m^{n-1} too, and from a guess
-  better than it (the explicit Euler step) it projects the guess's own
-  residual; mode 5 (the guess alone) from x_init = m^{n-1} is the warm start
-  (mode 2) bit for bit.
+* Mode 4 (a given guess, judged against the warm start, a kept guess
+  projected in residual form) from a guess worse than the warm start is the
+  warm start (mode 2) bit for bit, and from a guess better than it (the
+  explicit Euler step) it projects the guess's own residual; mode 5 (the
+  guess alone) from x_init = m^{n-1} is the warm start bit for bit.
 * The residual-form projection meets its Galerkin condition with the seed's
   H_a:  V_a^T (r - A_seed (x0 - x_init)) = 0 for r = b - A_i x_init.
 * ``learned_guess``: a one-layer network holding half the five-point pixel
@@ -43,8 +42,13 @@ def test_network_inputs_plane_order_and_time_planes():
         assert np.array_equal(x[:, k], R.bf16(x[:, k]))
         assert np.abs(x[:, k] - m).max() <= 2.0 ** -8 * np.abs(m).max()
         assert np.abs(R.bf16(x[:, k]) + R.bf16(x[:, k + 1]) / 256 - m).max() <= 2.0 ** -16 * np.abs(m).max()
-    # tau = 1/4: sin(pi/2) = 1, cos(pi/2) = 0, sin(pi) = 0, cos(pi) = -1
-    assert np.allclose(x[:, 4:, 0], [[1.0, 0.0, 0.0, -1.0]] * 2, atol=1e-15)
+    # tau = 1/4: tau, 1 - tau, sin(pi/4), cos(pi/4)
+    h = np.sqrt(0.5)
+    assert np.allclose(x[:, 4:, 0], [[0.25, 0.75, h, h]] * 2, atol=1e-15)
+    # the first and the last timestep are told apart on every time plane
+    # but the sine
+    x0, x1 = R.network_inputs(mp, ms, 1, 1000), R.network_inputs(mp, ms, 1000, 1000)
+    assert np.all(np.abs(x0[0, [4, 5, 7], 0] - x1[0, [4, 5, 7], 0]) > 0.99)
     assert R.guess_scale(1000, 0.02, 32) == 0.02 * 1024 / 1000
 
 
@@ -65,12 +69,13 @@ def test_guess_modes_reduce_to_projection_and_warm_start(orc):
                             xinit=xi, tol_ref=1e-10)
         out[name] = (mt, st)
     # x_init = 0 leaves the residual b, far above the warm start's: the judge
-    # keeps the warm start, exactly as when the warm start is the guess
-    assert np.array_equal(out["zero_guess"][0], out["warm_guess"][0])
-    assert np.array_equal(out["zero_guess"][1].tgt_x0res, out["warm_guess"][1].tgt_x0res)
-    assert np.array_equal(out["warm"][0], out["guess_warm"][0])
-    assert np.array_equal(out["warm"][1].tgt_iters, out["guess_warm"][1].tgt_iters)
-    # the projected warm start leaves less residual than the warm start alone
+    # falls back to the warm start, which is then mode 2 exactly
+    for name in ("zero_guess", "guess_warm"):
+        assert np.array_equal(out["warm"][0], out[name][0])
+        assert np.array_equal(out["warm"][1].tgt_iters, out[name][1].tgt_iters)
+        assert np.array_equal(out["warm"][1].tgt_x0res, out[name][1].tgt_x0res)
+    # a guess equal to the warm start is kept (the judge wants strictly less)
+    # and projected: less residual than the warm start alone
     assert (out["warm_guess"][1].tgt_x0res < out["warm"][1].tgt_x0res).all()
 
 
