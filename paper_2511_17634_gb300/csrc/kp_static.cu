@@ -22,43 +22,59 @@
 namespace {
 
 constexpr int kMaxDevices = 64;
-constexpr int kGrid = KP_STATIC_BLOCKS;           // thread blocks per call (persistent)
 constexpr int kNpad = 1024;                        // 4 points x 256 threads
 constexpr size_t kDescBytes = (size_t)KP_STATIC_MAX_SYSTEMS * sizeof(kp::SysDesc);
 constexpr size_t kDescRegion = (kDescBytes + 255) / 256 * 256;
 constexpr size_t kScratchBytes = KP_STATIC_SCRATCH_BYTES;
 static_assert(kScratchBytes > kDescRegion, "scratch must hold the descriptor table");
 
-// The shared scratch: [descriptor table][Krylov-vector workspace of kGrid blocks].
+// The shared scratch: [descriptor table][Krylov-vector workspace of the blocks].
 // Every call overwrites it; calls that overlap on the GPU race on it.
 static __device__ __align__(256) unsigned char kp_static_scratch[kScratchBytes];
+
+// Descriptors travel to the table as kernel parameters, 256 per launch
+// (24 KB of the 32 KB parameter space), so nothing is staged in host memory
+// that a later call could overwrite before the copy runs.
+constexpr int kDescPerLaunch = 256;
+struct DescChunk {
+  int first, count;
+  kp::SysDesc d[kDescPerLaunch];
+};
+
+__global__ void upload_desc_kernel(const __grid_constant__ DescChunk c, kp::SysDesc* table) {
+  for (int k = threadIdx.x; k < c.count; k += blockDim.x) table[c.first + k] = c.d[k];
+}
 
 struct DeviceSetup {
   bool done = false;
   unsigned char* scratch = nullptr;   // device address of kp_static_scratch
   size_t smem_optin = 0;
+  int sms = 0;
 };
 
-std::mutex g_mu;                                  // guards g_setup and g_host_desc
+std::mutex g_mu;                                  // guards g_setup
 DeviceSetup g_setup[kMaxDevices];
-kp::SysDesc g_host_desc[KP_STATIC_MAX_SYSTEMS];   // host staging of the descriptors
 
 // Once per device, with that device current: resolve the scratch symbol to
-// a device address (host code only sees a host-side stand-in for it).
-kp_status setup_device(int dev, DeviceSetup** out) {
+// a device address (host code only sees a host-side stand-in for it) and
+// read the limits the launch shape depends on.
+kp_status setup_device(int dev, DeviceSetup* out) {
+  std::lock_guard<std::mutex> lock(g_mu);
   DeviceSetup& s = g_setup[dev];
   if (!s.done) {
     void* ptr = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&ptr, kp_static_scratch);
     if (e != cudaSuccess) return KP_ERR_CUDA;
-    int v = 0;
+    int v = 0, sms = 0;
     e = cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return KP_ERR_CUDA;
     s.scratch = static_cast<unsigned char*>(ptr);
     s.smem_optin = (size_t)v;
+    s.sms = sms;
     s.done = true;
   }
-  *out = &s;
+  *out = s;
   return KP_OK;
 }
 
@@ -80,40 +96,46 @@ extern "C" kp_status kp_refine_static(int nsys, const kp_op* ops, const double* 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return KP_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return KP_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_mu);
-  DeviceSetup* ds = nullptr;
+  DeviceSetup ds;
   kp_status st = setup_device(dev, &ds);
   if (st != KP_OK) return st;
   // Shared-memory window: as many Krylov vectors as one block per SM allows;
-  // the rest go to this call's slice of the static workspace.
+  // the rest go to each block's slice of the static workspace.
   const size_t fixed = kp::gmres_fp64_smem_bytes(4, 256, 0, m);
   const size_t per = (size_t)kNpad * sizeof(double);
-  if (ds->smem_optin <= fixed + per) return KP_ERR_UNSUPPORTED;
-  const int S = (int)std::min<size_t>((size_t)m + 1, (ds->smem_optin - fixed) / per);
-  const int grid = std::min(nsys, kGrid);
-  const size_t spill_bytes = (size_t)grid * (size_t)(m + 1 - S) * per;
-  if (kDescRegion + spill_bytes > kScratchBytes) return KP_ERR_TOO_LARGE;
-  for (int k = 0; k < nsys; ++k) {
-    kp::SysDesc d{};
-    d.mt = ops[k].mtilde;
-    d.fx = ops[k].fx;
-    d.fy = ops[k].fy;
-    d.b = b[k];
-    d.x = x[k];
-    d.H = ops[k].H;
-    d.W = ops[k].W;
-    d.dt = ops[k].dt;
-    d.g2 = ops[k].g2;
-    d.h = ops[k].h;
-    g_host_desc[k] = d;
-  }
+  if (ds.smem_optin <= fixed + per) return KP_ERR_UNSUPPORTED;
+  const int S = (int)std::min<size_t>((size_t)m + 1, (ds.smem_optin - fixed) / per);
+  // Persistent blocks, one per SM of this device, fewer if their Krylov
+  // spill would not fit the array; each block marches systems k, k + grid, ...
+  const size_t spill_per_block = (size_t)(m + 1 - S) * per;
+  const size_t room = kScratchBytes - kDescRegion;
+  const size_t fit = spill_per_block ? room / spill_per_block : (size_t)nsys;
+  if (fit < 1) return KP_ERR_TOO_LARGE;
+  const int grid = (int)std::min<size_t>({(size_t)nsys, (size_t)std::max(ds.sms, 1), fit});
   cudaStream_t stream = (cudaStream_t)cuda_stream;
-  kp::SysDesc* ddesc = reinterpret_cast<kp::SysDesc*>(ds->scratch);
-  // pageable source: the call returns once the bytes are staged, so the host
-  // table can be reused by the next call
-  cudaError_t e = cudaMemcpyAsync(ddesc, g_host_desc, (size_t)nsys * sizeof(kp::SysDesc),
-                                  cudaMemcpyHostToDevice, stream);
-  if (e != cudaSuccess) return KP_ERR_CUDA;
+  kp::SysDesc* ddesc = reinterpret_cast<kp::SysDesc*>(ds.scratch);
+  DescChunk chunk;
+  for (int k0 = 0; k0 < nsys; k0 += kDescPerLaunch) {
+    chunk.first = k0;
+    chunk.count = std::min(kDescPerLaunch, nsys - k0);
+    for (int k = 0; k < chunk.count; ++k) {
+      const kp_op& o = ops[k0 + k];
+      kp::SysDesc d{};
+      d.mt = o.mtilde;
+      d.fx = o.fx;
+      d.fy = o.fy;
+      d.b = b[k0 + k];
+      d.x = x[k0 + k];
+      d.H = o.H;
+      d.W = o.W;
+      d.dt = o.dt;
+      d.g2 = o.g2;
+      d.h = o.h;
+      chunk.d[k] = d;
+    }
+    upload_desc_kernel<<<1, 128, 0, stream>>>(chunk, ddesc);
+    if (cudaGetLastError() != cudaSuccess) return KP_ERR_CUDA;
+  }
   kp::GmresParams p{};
   p.sys = ddesc;
   p.nsys = nsys;
@@ -125,9 +147,9 @@ extern "C" kp_status kp_refine_static(int nsys, const kp_op* ops, const double* 
   p.npad = kNpad;
   p.b_scale = 1.0;
   p.x0_mode = kp::X0_READ;
-  p.spill = (S < m + 1) ? reinterpret_cast<double*>(ds->scratch + kDescRegion) : nullptr;
+  p.spill = (S < m + 1) ? reinterpret_cast<double*>(ds.scratch + kDescRegion) : nullptr;
   p.info = info;
   const size_t smem = fixed + (size_t)S * per;
-  e = kp::launch_gmres_fp64_1k_grid(p, smem, grid, stream);
+  const cudaError_t e = kp::launch_gmres_fp64_1k_grid(p, smem, grid, stream);
   return e == cudaSuccess ? KP_OK : KP_ERR_CUDA;
 }

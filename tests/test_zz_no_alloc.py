@@ -51,6 +51,69 @@ def _problem(seed):
     return g.H, g.W, g.targets.reshape(len(g.targets), -1)
 
 
+def _check_against_refine(kp, ctx, H, W, mt, m, stream, g2=0.25, dt=0.01):
+    n = mt.shape[0]
+    dm = torch.as_tensor(mt, device="cuda")
+    ops = kp.make_ops(H, W, dt, g2, 1.0 / H, dm)
+    b = torch.zeros_like(dm)
+    ctx.rhs(ops, dm, b)
+    x_ref = torch.zeros_like(dm)
+    info_ref = ctx.refine(ops, b, x_ref, tol=1e-10, m=m, maxit=600)
+    x_st = torch.zeros_like(dm)
+    info_st = kp.info_tensor(n)
+    torch.cuda.synchronize()
+    rc = _static_refine(kp, ops, b, x_st, 1e-10, m, 600, info_st, stream.cuda_stream)
+    assert rc == kp.OK, rc
+    torch.cuda.synchronize()
+    it_r, st_r, rr_r = kp.decode_info(info_ref)
+    it_s, st_s, rr_s = kp.decode_info(info_st)
+    assert (st_s == 0).all() and (rr_s <= 1e-10).all()
+    assert np.array_equal(it_s, it_r)
+    err = float((x_st - x_ref).abs().max() / x_ref.abs().max())
+    assert err <= 1e-12, err
+    return it_s
+
+
+def test_static_refine_allocates_nothing_after_its_first_call(kp):
+    # the first call on a device resolves the array and loads the kernels;
+    # later calls -- one of them with Krylov vectors in the static array --
+    # must leave the device's free memory where it was
+    stream = torch.cuda.current_stream()
+    ctx = kp.Context(max_n=1024)
+    H, W, mt = _problem(13)
+    dm = torch.as_tensor(mt, device="cuda")
+    ops = kp.make_ops(H, W, 0.01, 0.25, 1.0 / H, dm)
+    b = torch.zeros_like(dm)
+    ctx.rhs(ops, dm, b)
+    xs = [torch.zeros_like(dm) for _ in range(4)]
+    infos = [kp.info_tensor(dm.shape[0]) for _ in range(4)]
+    torch.cuda.synchronize()
+    assert _static_refine(kp, ops, b, xs[0], 1e-10, 40, 600, infos[0], stream.cuda_stream) == kp.OK
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for k in (1, 2, 3):
+        assert _static_refine(kp, ops, b, xs[k], 1e-10, 40, 600, infos[k], stream.cuda_stream) == kp.OK
+        torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    it, st, _ = kp.decode_info(infos[3])
+    assert (st == 0).all() and it.max() > 24          # reached the static workspace
+    assert free1 >= free0, (free0, free1)
+    assert torch.equal(xs[3], xs[1])
+
+
+def test_static_refine_more_systems_than_sms(kp):
+    # 400 systems with m = 64: the grid is the device's SM count cut to what
+    # the array's Krylov workspace holds, and each block solves several systems
+    props = torch.cuda.get_device_properties(0)
+    n = max(400, 2 * props.multi_processor_count + 17)
+    wl = synth.config(2, T=100, ntargets=(n + 2) // 3, seed=14)
+    g = wl.groups[0]
+    mt = g.targets.reshape(len(g.targets), -1)[:n]
+    ctx = kp.Context(max_n=1024)
+    it = _check_against_refine(kp, ctx, g.H, g.W, mt, 64, torch.cuda.current_stream())
+    assert it.max() > 24
+
+
 def test_static_refine_matches_refine_on_two_calls(kp):
     stream = torch.cuda.current_stream()
     ctx = kp.Context(max_n=1024)
@@ -84,11 +147,10 @@ def test_static_refine_rejects_oversized_requests(kp):
     info = kp.info_tensor(2)
     rc = _static_refine(kp, ops, dm, dm.clone(), 1e-8, 40, 100, info, 0)
     assert rc == kp.ERR_TOO_LARGE
-    # 200 systems run on all 152 blocks; with m = 64 their Krylov vectors
-    # beyond the shared-memory window do not fit the static scratch
-    dm = torch.zeros((200, 1024), dtype=torch.float64, device="cuda")
-    ops = kp.make_ops(32, 32, 0.01, 0.02, 1 / 32, dm)
-    info = kp.info_tensor(200)
-    rc = _static_refine(kp, ops, dm, dm.clone(), 1e-8, 64, 100, info, 0)
+    # more systems than the descriptor table holds
+    dm = torch.zeros((4097, 1), dtype=torch.float64, device="cuda")
+    ops = kp.make_ops(1, 1, 0.01, 0.02, 1.0, dm)
+    info = kp.info_tensor(4097)
+    rc = _static_refine(kp, ops, dm, dm.clone(), 1e-8, 10, 100, info, 0)
     assert rc == kp.ERR_TOO_LARGE
     del ctx
