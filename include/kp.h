@@ -91,6 +91,11 @@ typedef struct {
                         until it has exactly a = min(max_a, m) vectors (fewer
                         only at an exact breakdown or maxit), and its iterate is
                         the GMRES minimiser over that whole space            */
+  int inner_digits;  /* mixed precision: each FP32 inner GMRES reduces its
+                        residual estimate by 10^-inner_digits (or to a tenth of
+                        the outer tolerance, whichever is reached first) before
+                        the FP64 iterative refinement recomputes the true
+                        residual; 1..7, 0 = 5                                     */
 } kp_options;
 
 /* Operator of one system (Sec. 2.3): A(m~; g^2, dt, h, f).  `mtilde` is the
@@ -205,23 +210,29 @@ kp_status kp_refine(kp_ctx* ctx, int nsys, const kp_op* ops, const double* const
  * scratch -- the system descriptors and the Krylov vectors beyond the shared
  * memory window -- is one static device array of KP_STATIC_SCRATCH_BYTES in
  * the library, held on every GPU that loads the library until the process
- * exits.  Every call reuses that array and leaves its own contents there;
- * nothing in it has to start at zero, because each call writes every
- * descriptor and Krylov vector before reading it.  Calls whose work overlaps
- * on the GPU (other streams, other host threads) race on the array: order
- * them, e.g. on one stream.
+ * exits.  The descriptors reach the array as kernel parameters of small
+ * copy launches (256 per launch), so no host staging buffer is involved.
+ * Every call reuses that array and leaves its own contents there; nothing in
+ * it has to start at zero, because each call writes every descriptor and
+ * Krylov vector before reading it.  Calls whose work overlaps on the GPU
+ * (other streams, other host threads) race on the array: order them, e.g.
+ * on one stream.  A call that fails after it has enqueued work can leave the
+ * array in any state; the next call rewrites everything it reads.
  *
- * Limits: nsys <= KP_STATIC_MAX_SYSTEMS, H*W <= KP_STATIC_MAX_N, and the
- * Krylov vectors that do not fit in shared memory must fit the array (on a
- * GB300, m <= 40 fits); otherwise KP_ERR_TOO_LARGE and nothing is enqueued.
- * The first call on each device resolves the array's device address
- * (cudaGetSymbolAddress, once per device, with that device current) and so
- * loads the library's module there; make that first call before any stream
- * capture.
+ * Launch shape: one 256-thread block per SM of the current device, fewer
+ * when their Krylov vectors beyond shared memory would not fit the array;
+ * each block solves systems k, k + blocks, ...
+ *
+ * Limits: nsys <= KP_STATIC_MAX_SYSTEMS, H*W <= KP_STATIC_MAX_N, and one
+ * block's Krylov vectors beyond shared memory must fit the array (always
+ * true for m <= 64 on a GB300); otherwise KP_ERR_TOO_LARGE and nothing is
+ * enqueued.  The first call on each device resolves the array's device
+ * address (cudaGetSymbolAddress, once per device, with that device current,
+ * under a lock shared by all devices) and so loads the library's module
+ * there; make that first call before any stream capture.
  */
 #define KP_STATIC_MAX_SYSTEMS 4096
 #define KP_STATIC_MAX_N 1024
-#define KP_STATIC_BLOCKS 152
 #define KP_STATIC_SCRATCH_BYTES (22u * 1024u * 1024u)
 kp_status kp_refine_static(int nsys, const kp_op* ops, const double* const* b, double* const* x,
                            double tol, int m, int maxit, kp_info* info, void* cuda_stream);
@@ -263,25 +274,37 @@ kp_status kp_cnn_destroy(kp_cnn* cnn);
 int kp_cnn_num_params(const kp_cnn* cnn);
 kp_status kp_cnn_set_params(kp_cnn* cnn, const float* host_params);   /* resets Adam state */
 kp_status kp_cnn_get_params(kp_cnn* cnn, float* host_params);
-/* out (device [B][c_L][H*W]) = network(in (device [B][c_0][H*W])). */
+/* Size the inference buffers (the implicit-GEMM path of kp_cnn_forward and
+ * the learned march) for B images, independently of the training batch of
+ * kp_cnn_create (about 2.7 MB per 128x128 image).  Waits for the context's
+ * stream; KP_ERR_UNSUPPORTED for shapes without that path (more than 16
+ * input or output channels, one layer). */
+kp_status kp_cnn_set_inference_batch(kp_cnn* cnn, int B);
+/* out (device [B][c_L][H*W]) = network(in (device [B][c_0][H*W])); B <= the
+ * inference batch (max_batch until kp_cnn_set_inference_batch). */
 kp_status kp_cnn_forward(kp_cnn* cnn, int B, const float* in, float* out);
 /* Loss = mean over B*H*W of (out - target)^2 (c_L = 1); gradients of the loss
  * (device [num_params], may be NULL) and the loss (host, may be NULL). */
 kp_status kp_cnn_gradients(kp_cnn* cnn, int B, const float* in, const float* target,
                            float* grads, double* loss);
-/* Network input of the learned guess for B targets at time tau = n/T: planes
- * [target image, seed state m_seed^n, sin 2 pi tau, cos 2 pi tau, sin 4 pi tau,
- * cos 4 pi tau] into in (device [B][6][H*W] FP32); img, seed: host arrays of
- * B device pointers to FP64 planes. */
-kp_status kp_cnn_pack_inputs(kp_cnn* cnn, int B, const double* const* img, const double* const* seed,
+/* Network input of the learned guess for B targets at timestep n, tau = n/T:
+ * planes [the target's lagged field m_i^{n-1} (its image carried to timestep
+ * n-1) as hi = bf16(m) and lo = bf16(256 (m - hi)), the seed state m_seed^n
+ * as hi and lo, tau, 1 - tau, sin pi tau, cos pi tau] into
+ * in (device [B][8][H*W] FP32); mprev, seed: host arrays of B device
+ * pointers to FP64 planes.  (A field in one BF16 plane keeps 8 significant
+ * bits, too few for the step's change; hi and lo keep about 16.) */
+kp_status kp_cnn_pack_inputs(kp_cnn* cnn, int B, const double* const* mprev, const double* const* seed,
                              double tau, float* in);
-/* Training target of the learned guess: out_b = a_b - b_b (m_i^n - m_seed^n)
- * into out (device [B][H*W] FP32); a, b: host arrays of device FP64 planes. */
+/* Training target of the learned guess: out_b = (a_b - b_b) * scale, e.g.
+ * (m_i^n - m_i^{n-1}) / s_n with s_n = dt (g^n)^2 / h^2, into out (device
+ * [B][H*W] FP32); a, b: host arrays of device FP64 planes. */
 kp_status kp_cnn_pack_target(kp_cnn* cnn, int B, const double* const* a, const double* const* b,
-                             float* out);
-/* x_b = base_b + delta_b: the FP64 initial guess m_seed^n + network output. */
+                             double scale, float* out);
+/* x_b = base_b + scale * delta_b: the FP64 initial guess m_i^{n-1} + s_n *
+ * network output. */
 kp_status kp_cnn_add_guess(kp_cnn* cnn, int B, const float* delta, const double* const* base,
-                           double* const* x);
+                           double scale, double* const* x);
 /* One Adam step (Kingma & Ba 2015) on that loss; t = 1, 2, ... */
 kp_status kp_cnn_train_step(kp_cnn* cnn, int B, const float* in, const float* target, float lr,
                             float beta1, float beta2, float eps, int t, double* loss);
@@ -314,8 +337,14 @@ typedef enum {
   KP_MARCH_PROJECTED = 0,   /* the paper: x0 = V_a H_a^{-1} V_a^T b (seed's H_a)          */
   KP_MARCH_PLAIN = 1,       /* x0 = 0                                                      */
   KP_MARCH_WARM = 2,        /* x0 = m^{n-1}                                                */
-  KP_MARCH_GALERKIN = 3     /* exact Galerkin with the target's own operator:
+  KP_MARCH_GALERKIN = 3,    /* exact Galerkin with the target's own operator:
                                x0 = V_a (V_a^T A_i V_a)^{-1} V_a^T b (FP64 plans only)    */
+  KP_MARCH_LEARNED = 4,     /* the learned guess projected in residual form: x_init =
+                               m^{n-1} + s_n net(m^{n-1}, m_seed^n, time) (inputs as in
+                               kp_cnn_pack_inputs), x0 = x_init +
+                               V_a H_a^{-1} V_a^T (b - A x_init) (mixed precision; needs
+                               kp_march_opts.cnn)                                          */
+  KP_MARCH_LEARNED_ONLY = 5 /* x0 = x_init, the learned guess alone (for comparison)    */
 } kp_march_mode;
 
 /* Phase 1 (Sec. 3) seed solver of a march.  BiCGSTAB is the method the paper
@@ -385,6 +414,14 @@ typedef struct {
                             that waits for the GPU returns KP_ERR_TIMEOUT (the
                             states are then not trustworthy) and the context stays
                             usable. */
+  int maxit_seed;        /* Arnoldi-step cap of the seed solves; 0 = maxit         */
+  kp_cnn* cnn;           /* KP_MARCH_LEARNED / _ONLY: the network (channels 8 -> ... -> 1,
+                            the march's H x W, created on this context); every
+                            timestep runs it on all targets in passes of its
+                            inference batch (kp_cnn_set_inference_batch) inside the
+                            march's graph, reading its current weights.  Do not use
+                            the network on other work while a run is in flight.
+                            One grid size, GMRES seeds, one Picard iteration.   */
 } kp_march_opts;
 
 /* Per-timestep totals, filled on the host by kp_march_run. */
@@ -396,7 +433,9 @@ typedef struct {
 
 /* Summed device time per kernel class (event-timed mode, launches in
  * sequence): seed_ms = seed GMRES with the fused basis store; refine_ms =
- * target GMRES with the fused projection; step_ms = first to last event. */
+ * target GMRES with the fused projection; proj_ms = the learned guess
+ * (input packing, network, x_init) of the learned modes; step_ms = first to
+ * last event. */
 typedef struct {
   float seed_ms, store_ms, proj_ms, refine_ms, step_ms;
   int launches;          /* kernel launches of this library in the run         */

@@ -242,6 +242,7 @@ kp_status run_gmres(kp_ctx* c, int nsys, const kp_op* ops, const double* const* 
   p.maxit = maxit;
   p.S = S;
   p.reorth = c->opt.reorth;
+  p.inner_eta = kp::inner_eta(c->opt);
   p.npad = npad;
   p.b_scale = 1.0;
   p.x0_mode = kp::X0_READ;
@@ -281,6 +282,7 @@ void kp_options_default(kp_options* o) {
   o->blocks_per_sm = 0;
   o->cluster_size = 0;
   o->fixed_a = 0;
+  o->inner_digits = 0;
 }
 
 kp_status kp_create(kp_ctx** out, const kp_options* opt, void* stream) {
@@ -294,7 +296,7 @@ kp_status kp_create(kp_ctx** out, const kp_options* opt, void* stream) {
       o.smem_vectors < 0 || (o.reorth != 0 && o.reorth != 1) ||
       (o.block_threads != 0 && o.block_threads != 64 && o.block_threads != 128 && o.block_threads != 256) ||
       (o.cluster_size != 0 && o.cluster_size != 2 && o.cluster_size != 4 && o.cluster_size != 8) ||
-      (o.fixed_a != 0 && o.fixed_a != 1))
+      (o.fixed_a != 0 && o.fixed_a != 1) || o.inner_digits < 0 || o.inner_digits > 7)
     return KP_ERR_ARG;
   {
     // solver shapes compiled for grids of <= 1024 points: (threads, blocks per SM)

@@ -166,33 +166,89 @@ __global__ void weights_bf16_kernel(const float* Wl, __nv_bfloat16* Wb, int ldw,
 
 size_t up8(size_t x) { return (x + 7) / 8 * 8; }
 
-// Network input planes of sample b: target image, seed state, then the time
-// embedding sin(2 pi tau), cos(2 pi tau), sin(4 pi tau), cos(4 pi tau).
+// A field as two BF16 operands: hi = bf16(m), lo = 256 (m - hi).  One BF16
+// plane holds 8 significant bits; the step's change the network predicts is a
+// difference of neighbours a few hundred times smaller than m, so the first
+// layer gets both planes (about 16 bits) and recombines them in its FP32 sums.
+__device__ __forceinline__ void split_hi_lo(double m, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn((float)m);
+  lo = __float2bfloat16_rn((float)((m - (double)__bfloat162float(hi)) * 256.0));
+}
+
+// Network input planes of sample b: the target's plane (its lagged field
+// m_i^{n-1} for the learned guess) and the seed state, each as its hi and lo
+// planes, then the time embedding tau, 1 - tau, sin(pi tau), cos(pi tau).
 __global__ void pack_inputs_kernel(const double* const* img, const double* const* seed, float tau, float* in,
                                    int P) {
   const int b = blockIdx.y;
-  const float e[4] = {sinpif(2.f * tau), cospif(2.f * tau), sinpif(4.f * tau), cospif(4.f * tau)};
-  float* o = in + (size_t)b * 6 * P;
+  const float e[4] = {tau, 1.f - tau, sinpif(tau), cospif(tau)};
+  float* o = in + (size_t)b * 8 * P;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-    o[p] = (float)img[b][p];
-    o[P + p] = (float)seed[b][p];
+    __nv_bfloat16 h0, l0, h1, l1;
+    split_hi_lo(img[b][p], h0, l0);
+    split_hi_lo(seed[b][p], h1, l1);
+    o[p] = __bfloat162float(h0);
+    o[P + p] = __bfloat162float(l0);
+    o[2 * P + p] = __bfloat162float(h1);
+    o[3 * P + p] = __bfloat162float(l1);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) o[(2 + k) * P + p] = e[k];
+    for (int k = 0; k < 4; ++k) o[(4 + k) * P + p] = e[k];
   }
 }
 
-// out_b = a_b - b_b in FP32 (training targets m_i^n - m_seed^n)
-__global__ void diff_kernel(const double* const* a, const double* const* bb, float* out, int P) {
+// out_b = (a_b - b_b) * scale in FP32 (training targets (m_i^n - m_i^{n-1}) / s_n)
+__global__ void diff_kernel(const double* const* a, const double* const* bb, double scale, float* out, int P) {
   const int b = blockIdx.y;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
-    out[(size_t)b * P + p] = (float)(a[b][p] - bb[b][p]);
+    out[(size_t)b * P + p] = (float)((a[b][p] - bb[b][p]) * scale);
 }
 
-// x_b = base_b + delta_b (FP64 initial guess from the network's correction)
-__global__ void add_guess_kernel(const float* delta, const double* const* base, double* const* x, int P) {
+// x_b = base_b + scale * delta_b (FP64 initial guess from the network's output)
+__global__ void add_guess_kernel(const float* delta, const double* const* base, double scale, double* const* x,
+                                 int P) {
   const int b = blockIdx.y;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
-    x[b][p] = base[b][p] + (double)delta[(size_t)b * P + p];
+    x[b][p] = base[b][p] + scale * (double)delta[(size_t)b * P + p];
+}
+
+// The learned guess inside the time march, for the target timestep n = *step
+// + step_offset + 1 (1-based), tau = n / T: the eight input planes of sample b
+// -- m_i^{n-1} (hi, lo), m_seed^n (hi, lo), tau, 1 - tau, sin pi tau,
+// cos pi tau -- straight into the padded BF16 rows of the first convolution
+// (chunk 0; chunk 1, channels 8..15, is written as zeros)
+__global__ void march_pack_kernel(const double* const* mprev, const double* const* mseed, const int* step,
+                                  int step_offset, int T, int H, int W, int halo, int Rp, __nv_bfloat16* out) {
+  const int b = blockIdx.y;
+  const int P = H * W;
+  const float tau = (float)(*step + step_offset + 1) / (float)T;
+  const float e[4] = {tau, 1.f - tau, sinpif(tau), cospif(tau)};
+  const double* mp = mprev[b];
+  const double* ms = mseed[b];
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+    const int i = p / H, j = p - i * H;
+    const size_t row = (size_t)halo + (size_t)i * (H + 2) + 1 + j;
+    __nv_bfloat162 f0, f1;
+    split_hi_lo(mp[p], f0.x, f0.y);
+    split_hi_lo(ms[p], f1.x, f1.y);
+    __nv_bfloat162 h1 = __floats2bfloat162_rn(e[0], e[1]);
+    __nv_bfloat162 h2 = __floats2bfloat162_rn(e[2], e[3]);
+    const uint4 c0 = make_uint4(*reinterpret_cast<uint32_t*>(&f0), *reinterpret_cast<uint32_t*>(&f1),
+                                *reinterpret_cast<uint32_t*>(&h1), *reinterpret_cast<uint32_t*>(&h2));
+    *reinterpret_cast<uint4*>(out + (((size_t)b * 2 + 0) * Rp + row) * 8) = c0;
+    *reinterpret_cast<uint4*>(out + (((size_t)b * 2 + 1) * Rp + row) * 8) = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+// x_b = m_i^{n-1} + s_n * delta_b with s_n = dt (g^n)^2 / h^2 = g2[n-1] H^2 / T
+__global__ void march_guess_kernel(const float* delta, const double* const* mprev, double* const* x,
+                                   const int* step, int step_offset, const double* g2, int T, int H, int P) {
+  const int b = blockIdx.y;
+  const int t = *step + step_offset;
+  const double s = g2[t] * (double)H * (double)H / (double)T;
+  const double* mp = mprev[b];
+  double* xb = x[b];
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
+    xb[p] = fma(s, (double)delta[(size_t)b * P + p], mp[p]);
 }
 
 }  // namespace
@@ -232,6 +288,8 @@ struct kp_cnn {
   __nv_bfloat16* wf = nullptr;                  // per layer [9][cic][nout][8]
   std::vector<size_t> wf_off;
   std::vector<int> cic, nout;
+  int infB = 0;                                 // images the inference buffers hold
+  float* dout = nullptr;                        // [infB][P] network output (march guesses)
 };
 
 namespace {
@@ -306,11 +364,10 @@ kp_status refresh_bf16(kp_cnn* n) {
   return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN weights");
 }
 
-// Inference: input planes -> padded BF16 rows, then one implicit-GEMM
-// convolution launch per layer, the last writing FP32 planes.
-kp_status forward_fused(kp_cnn* n, int B, const float* in, float* out) {
-  cudaStream_t st = n->ctx->stream;
-  cudaError_t e = kp::launch_planes_to_padded(in, B, n->ch[0], 2, n->geo, n->pin, st);
+// The layers of the implicit-GEMM inference from the packed input rows in
+// n->pin: one convolution launch per layer, the last writing FP32 planes.
+cudaError_t conv_layers(kp_cnn* n, int B, float* out, cudaStream_t st) {
+  cudaError_t e = cudaSuccess;
   const __nv_bfloat16* X = n->pin;
   for (int l = 0; l < n->L && e == cudaSuccess; ++l) {
     const bool last = l + 1 == n->L;
@@ -319,7 +376,34 @@ kp_status forward_fused(kp_cnn* n, int B, const float* in, float* out) {
                            n->nout[l], n->geo, Y, last ? out : nullptr, n->d_err, n->ctx->sms, st);
     X = Y;
   }
+  return e;
+}
+
+// Inference: input planes -> padded BF16 rows, then the layers.
+kp_status forward_fused(kp_cnn* n, int B, const float* in, float* out) {
+  cudaStream_t st = n->ctx->stream;
+  cudaError_t e = kp::launch_planes_to_padded(in, B, n->ch[0], 2, n->geo, n->pin, st);
+  if (e == cudaSuccess) e = conv_layers(n, B, out, st);
   return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN forward (implicit GEMM)");
+}
+
+// (Re)allocate the implicit-GEMM inference buffers for B images, zeroed (the
+// padding rows are never written afterwards).
+cudaError_t alloc_inference(kp_cnn* n, int B) {
+  cudaFree(n->pin); cudaFree(n->px[0]); cudaFree(n->px[1]); cudaFree(n->dout);
+  n->pin = n->px[0] = n->px[1] = nullptr;
+  n->dout = nullptr;
+  n->infB = 0;
+  const size_t rows = (size_t)B * n->geo.Rp * 8;
+  cudaError_t e = cudaMalloc((void**)&n->pin, 2 * rows * sizeof(__nv_bfloat16));
+  if (e == cudaSuccess) e = cudaMemset(n->pin, 0, 2 * rows * sizeof(__nv_bfloat16));
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaMalloc((void**)&n->px[k], 4 * rows * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMemset(n->px[k], 0, 4 * rows * sizeof(__nv_bfloat16));
+  }
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->dout, (size_t)B * n->P * sizeof(float));
+  if (e == cudaSuccess) n->infB = B;
+  return e;
 }
 
 // forward + MSE + backward into n->grads; loss on the host if wanted
@@ -389,7 +473,7 @@ kp_status kp_cnn_destroy(kp_cnn* n) {
   cudaFree(n->params); cudaFree(n->grads); cudaFree(n->adam_m); cudaFree(n->adam_v); cudaFree(n->wb);
   cudaFree(n->act); cudaFree(n->dz); cudaFree(n->dz2); cudaFree(n->col); cudaFree(n->colT); cudaFree(n->rows);
   cudaFree(n->cm); cudaFree(n->tiles); cudaFree(n->d_loss); cudaFree(n->d_err);
-  cudaFree(n->pin); cudaFree(n->px[0]); cudaFree(n->px[1]); cudaFree(n->wf);
+  cudaFree(n->pin); cudaFree(n->px[0]); cudaFree(n->px[1]); cudaFree(n->wf); cudaFree(n->dout);
   delete n;
   return KP_OK;
 }
@@ -450,13 +534,7 @@ kp_status kp_cnn_create(kp_ctx* c, int H, int W, int max_batch, int nlayers, con
     if (kp::conv_smem_bytes(n->geo, n->cic[l], n->nout[l]) > c->smem_optin) n->fused = false;
   }
   if (n->fused && e == cudaSuccess) {
-    const size_t rows = (size_t)max_batch * n->geo.Rp * 8;
-    e = cudaMalloc((void**)&n->pin, 2 * rows * sizeof(__nv_bfloat16));
-    if (e == cudaSuccess) e = cudaMemset(n->pin, 0, 2 * rows * sizeof(__nv_bfloat16));
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-      e = cudaMalloc((void**)&n->px[k], 4 * rows * sizeof(__nv_bfloat16));
-      if (e == cudaSuccess) e = cudaMemset(n->px[k], 0, 4 * rows * sizeof(__nv_bfloat16));
-    }
+    e = alloc_inference(n, max_batch);
     if (e == cudaSuccess) e = cudaMalloc((void**)&n->wf, nwf * sizeof(__nv_bfloat16));
   }
   if (e != cudaSuccess) {
@@ -489,9 +567,22 @@ kp_status kp_cnn_get_params(kp_cnn* n, float* host) {
   return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN parameters");
 }
 
+kp_status kp_cnn_set_inference_batch(kp_cnn* n, int B) {
+  if (!n) return KP_ERR_ARG;
+  if (B < 1 || (size_t)B * n->P > (1u << 30)) return kp::set_error(n->ctx, KP_ERR_ARG, "CNN: bad inference batch");
+  if (!n->fused) return kp::set_error(n->ctx, KP_ERR_UNSUPPORTED, "CNN: no implicit-GEMM inference for this shape");
+  cudaError_t e = cudaStreamSynchronize(n->ctx->stream);   // no launch still reads the old buffers
+  if (e == cudaSuccess) e = alloc_inference(n, B);
+  return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN inference buffers");
+}
+
 kp_status kp_cnn_forward(kp_cnn* n, int B, const float* in, float* out) {
-  if (!n || B < 1 || B > n->maxB || !in || !out) return n ? kp::set_error(n->ctx, KP_ERR_ARG, "CNN forward: bad batch") : KP_ERR_ARG;
-  if (n->fused) return forward_fused(n, B, in, out);
+  if (!n || B < 1 || !in || !out) return n ? kp::set_error(n->ctx, KP_ERR_ARG, "CNN forward: bad batch") : KP_ERR_ARG;
+  if (n->fused) {
+    if (B > n->infB) return kp::set_error(n->ctx, KP_ERR_ARG, "CNN forward: batch above the inference batch %d", n->infB);
+    return forward_fused(n, B, in, out);
+  }
+  if (B > n->maxB) return kp::set_error(n->ctx, KP_ERR_ARG, "CNN forward: bad batch");
   kp_status s = forward_impl(n, B, in);
   if (s != KP_OK) return s;
   cudaError_t e = cudaMemcpyAsync(out, n->act + n->act_off[n->L - 1], (size_t)B * n->P * n->ch[n->L] * sizeof(float),
@@ -512,7 +603,7 @@ kp_status kp_cnn_gradients(kp_cnn* n, int B, const float* in, const float* targe
 kp_status kp_cnn_pack_inputs(kp_cnn* n, int B, const double* const* img, const double* const* seed,
                              double tau, float* in) {
   if (!n || B < 1 || !img || !seed || !in) return n ? kp::set_error(n->ctx, KP_ERR_ARG, "CNN pack: bad arguments") : KP_ERR_ARG;
-  if (n->ch[0] != 6) return kp::set_error(n->ctx, KP_ERR_UNSUPPORTED, "CNN pack: the network needs 6 input planes");
+  if (n->ch[0] != 8) return kp::set_error(n->ctx, KP_ERR_UNSUPPORTED, "CNN pack: the network needs 8 input planes");
   std::vector<const double*> h(2 * (size_t)B);
   for (int b = 0; b < B; ++b) { h[b] = img[b]; h[B + b] = seed[b]; }
   const double** d = nullptr;
@@ -526,7 +617,8 @@ kp_status kp_cnn_pack_inputs(kp_cnn* n, int B, const double* const* img, const d
   return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN pack");
 }
 
-kp_status kp_cnn_add_guess(kp_cnn* n, int B, const float* delta, const double* const* base, double* const* x) {
+kp_status kp_cnn_add_guess(kp_cnn* n, int B, const float* delta, const double* const* base, double scale,
+                           double* const* x) {
   if (!n || B < 1 || !delta || !base || !x) return n ? kp::set_error(n->ctx, KP_ERR_ARG, "CNN guess: bad arguments") : KP_ERR_ARG;
   std::vector<const double*> h(2 * (size_t)B);
   for (int b = 0; b < B; ++b) { h[b] = base[b]; h[B + b] = x[b]; }
@@ -534,14 +626,16 @@ kp_status kp_cnn_add_guess(kp_cnn* n, int B, const float* delta, const double* c
   cudaError_t e = cudaMallocAsync((void**)&d, h.size() * sizeof(double*), n->ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double*), cudaMemcpyHostToDevice, n->ctx->stream);
   if (e == cudaSuccess) {
-    add_guess_kernel<<<dim3(grid_for(n->P), B), 256, 0, n->ctx->stream>>>(delta, d, const_cast<double* const*>(d + B), n->P);
+    add_guess_kernel<<<dim3(grid_for(n->P), B), 256, 0, n->ctx->stream>>>(delta, d, scale,
+                                                                         const_cast<double* const*>(d + B), n->P);
     e = cudaGetLastError();
   }
   if (d) cudaFreeAsync(d, n->ctx->stream);
   return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN guess");
 }
 
-kp_status kp_cnn_pack_target(kp_cnn* n, int B, const double* const* a, const double* const* b, float* out) {
+kp_status kp_cnn_pack_target(kp_cnn* n, int B, const double* const* a, const double* const* b, double scale,
+                             float* out) {
   if (!n || B < 1 || !a || !b || !out) return n ? kp::set_error(n->ctx, KP_ERR_ARG, "CNN target: bad arguments") : KP_ERR_ARG;
   std::vector<const double*> h(2 * (size_t)B);
   for (int k = 0; k < B; ++k) { h[k] = a[k]; h[B + k] = b[k]; }
@@ -549,7 +643,7 @@ kp_status kp_cnn_pack_target(kp_cnn* n, int B, const double* const* a, const dou
   cudaError_t e = cudaMallocAsync((void**)&d, h.size() * sizeof(double*), n->ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double*), cudaMemcpyHostToDevice, n->ctx->stream);
   if (e == cudaSuccess) {
-    diff_kernel<<<dim3(grid_for(n->P), B), 256, 0, n->ctx->stream>>>(d, d + B, out, n->P);
+    diff_kernel<<<dim3(grid_for(n->P), B), 256, 0, n->ctx->stream>>>(d, d + B, scale, out, n->P);
     e = cudaGetLastError();
   }
   if (d) cudaFreeAsync(d, n->ctx->stream);
@@ -570,3 +664,29 @@ kp_status kp_cnn_train_step(kp_cnn* n, int B, const float* in, const float* targ
 }
 
 }  // extern "C"
+
+namespace kp {
+
+bool cnn_march_ready(const kp_cnn* n, int H, int W) {
+  return n && n->fused && n->H == H && n->W == W && n->ch[0] == 8 && n->ch[n->L] == 1 && n->infB > 0;
+}
+
+int cnn_inference_batch(const kp_cnn* n) { return n ? n->infB : 0; }
+
+cudaError_t cnn_enqueue_guess(kp_cnn* n, int B, const double* const* mprev, const double* const* mseed,
+                              double* const* x, const int* step, int step_offset, const double* g2, int T,
+                              cudaStream_t st) {
+  if (B < 1 || B > n->infB) return cudaErrorInvalidValue;
+  const dim3 grid(std::min((n->P + 255) / 256, 1024), B);
+  march_pack_kernel<<<grid, 256, 0, st>>>(mprev, mseed, step, step_offset, T, n->H, n->W, n->geo.halo, n->geo.Rp,
+                                          n->pin);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = conv_layers(n, B, n->dout, st);
+  if (e == cudaSuccess) {
+    march_guess_kernel<<<grid, 256, 0, st>>>(n->dout, mprev, x, step, step_offset, g2, T, n->H, n->P);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+}  // namespace kp

@@ -82,7 +82,24 @@ kp_status cuda_error(kp_ctx* c, cudaError_t e, const char* what);
 // (FP64 vectors, or FP32 ones for the mixed-precision solver).
 kp_status gmres_shape(kp_ctx* c, int nmax, int m, Shape* out, bool mixed = false,
                       int wmin = 0);
+// Inner FP32 residual reduction of the mixed-precision solvers.
+inline double inner_eta(const kp_options& o) {
+  static const double k[8] = {1e-5, 1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7};
+  return k[o.inner_digits >= 0 && o.inner_digits <= 7 ? o.inner_digits : 0];
+}
+
 // Launch the solver kernel family that `sh` selects.
 cudaError_t launch_solver(const GmresParams& p, const Shape& sh, bool mixed, cudaStream_t st);
+
+// Learned initial guess inside the time march (kp_cnn.cu): whether the
+// network can serve an H x W march (8 inputs, 1 output, implicit-GEMM
+// inference buffers), how many images one pass holds, and the enqueue of
+// x[b] = mprev[b] + s_n * net(mprev[b], mseed[b], time planes) for B targets
+// (device pointer tables; timestep from the device counter).
+bool cnn_march_ready(const kp_cnn* n, int H, int W);
+int cnn_inference_batch(const kp_cnn* n);
+cudaError_t cnn_enqueue_guess(kp_cnn* n, int B, const double* const* mprev, const double* const* mseed,
+                              double* const* x, const int* step, int step_offset, const double* g2, int T,
+                              cudaStream_t st);
 
 }  // namespace kp

@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
   if (sysi >= p.nsys) return;                     // uniform over the cluster
   const int parity_base = slot_set_base(p, tstep);
   const double bsc = p.b_scale;
-  constexpr double kEta = 1e-5;
+  const double kEta = p.inner_eta > 0.0 ? p.inner_eta : 1e-5;
 
   const SysDesc d = p.sys[sysi];
   const int H = d.H, W = d.W, N = H * W;
@@ -181,12 +181,99 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
     const int l = tid + k * NT;
     double x0 = 0.0;
     if (l < SL) {
-      if (p.x0_mode == X0_READ) x0 = d.x[base + l];
+      if (p.x0_mode == X0_READ || p.x0_mode == X0_GUESS_PROJECT) x0 = d.x[base + l];
       else if (p.x0_mode == X0_WARM) x0 = d.mt[base + l];
     }
     xs[l] = x0;
   }
   unsigned long long proj_flops = 0;
+  double r[EPT];
+  auto residual = [&]() { residual_of(r); };
+  if (p.x0_mode == X0_GUESS_PROJECT) {
+    // the judge of a given guess (as in the one-block mixed solver): the FP64
+    // residuals of the guess and of the warm start, both whole vectors in
+    // global memory; a kept guess is projected, the warm start starts as is
+    auto residual_glob = [&](const double* v, double (&out)[EPT]) {
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int l = tid + k * NT, pp = base + l;
+        out[k] = 0.0;
+        if (l < SL) {
+          const double xE = (msk[k] & 1u) ? v[pp + H] : 0.0;
+          const double xW = (msk[k] & 2u) ? v[pp - H] : 0.0;
+          const double xN = (msk[k] & 4u) ? v[pp + 1] : 0.0;
+          const double xS = (msk[k] & 8u) ? v[pp - 1] : 0.0;
+          double t = fma(-cd, v[pp], d.b[pp]);
+          t = fma(-cEx[k], xE - xW, t);
+          t = fma(-cNy[k], xN - xS, t);
+          out[k] = fma(c2, xW + xS, t);
+        }
+      }
+    };
+    residual_glob(d.x, r);
+    bool warm_won = false;
+    {
+      double rw[EPT];
+      residual_glob(d.mt, rw);
+      block_partials<NT>(2, [&](int i) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) s += (i == 0) ? r[k] * r[k] : rw[k] * rw[k];
+        return s;
+      }, red);
+      cluster_sum(2, false);
+      warm_won = hb[1] < hb[0];                     // the same in every CTA
+      if (warm_won) {
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          const int l = tid + k * NT;
+          r[k] = rw[k];
+          if (l < SL) xs[l] = d.mt[base + l];
+        }
+      }
+    }
+    proj_flops = 26ull * (unsigned long long)N;
+    // Sec. 3, Phase 2 on the residual of the guess: c = V^T r,
+    // alpha = H_a^{-1} c, x0 = x_init + V alpha, the sums cluster-wide
+    const int sl = d.slot + parity_base;
+    const SlotMeta mt = p.slotMeta[sl];
+    if (!warm_won && mt.timestep == tstep && mt.N == N && mt.a > 0) {   // uniform over the cluster
+      const int a = mt.a;
+      const int nv = mt.lsq ? a + 1 : a;
+      const float* Vs = p.slotV32 + (size_t)sl * (p.max_a + 1) * p.slot_ld + base;
+      float rv[EPT];
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) rv[k] = (float)r[k];
+      block_partials_f32x<NT>(nv, [&](int i) {
+        const float* vi = Vs + (size_t)i * p.slot_ld;
+        float s = 0.f;
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          const int l = tid + k * NT;
+          if (l < SL) s = fmaf(vi[l], rv[k], s);
+        }
+        return s;
+      }, red32);
+      cluster_sum(nv, true);
+      if (warp == 0) {
+        __syncwarp();
+        const double* rot = p.slotRot + (size_t)sl * 3 * p.max_a;
+        solve_projected_warp(hb, a, mt.nrot, p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a,
+                             p.max_a + 1, rot, rot + 2 * p.max_a, lane);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int l = tid + k * NT;
+        if (l < SL) {
+          float xv = 0.f;
+          for (int i = 0; i < a; ++i) xv = fmaf((float)hb[i], Vs[(size_t)i * p.slot_ld + l], xv);
+          xs[l] += (double)xv;
+        }
+      }
+      proj_flops += (unsigned long long)(2 * nv + 2 * a) * (unsigned long long)N;
+    }
+  }
   if (p.x0_mode == X0_PROJECT) {
     const int sl = d.slot + parity_base;
     const SlotMeta mt = p.slotMeta[sl];
@@ -233,8 +320,6 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
     }
   }
   cluster.sync();                                 // x slices visible cluster-wide
-  double r[EPT];
-  auto residual = [&]() { residual_of(r); };
   if (p.x0_mode == X0_ZERO) {
 #pragma unroll
     for (int k = 0; k < EPT; ++k) r[k] = bval(tid + k * NT);

@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
   }
   const int parity_base = slot_set_base(p, tstep);
   const double bsc = p.b_scale;
-  constexpr double kEta = 1e-5;                // inner residual reduction per outer step
+  const double kEta = p.inner_eta > 0.0 ? p.inner_eta : 1e-5;   // inner residual reduction per outer step
 
   for (int sysi = blockIdx.x; sysi < p.nsys; sysi += gridDim.x) {
     const SysDesc d = p.sys[sysi];
@@ -179,12 +179,81 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
       const int pp = tid + k * NT;
       double x0 = 0.0;
       if (pp < N) {
-        if (p.x0_mode == X0_READ) x0 = d.x[pp];
+        if (p.x0_mode == X0_READ || p.x0_mode == X0_GUESS_PROJECT) x0 = d.x[pp];
         else if (p.x0_mode == X0_WARM) x0 = d.mt[pp];
       }
       sm.xs[pp] = x0;
     }
     unsigned long long proj_flops = 0;
+    double r[EPT];
+    auto residual = [&]() { residual_of(sm.xs, r); };
+    if (p.x0_mode == X0_GUESS_PROJECT) {
+      // the judge of a given guess (the learned one): its FP64 residual
+      // against the warm start's; a kept guess is projected below, the
+      // warm start (the fallback) starts unprojected, as in the warm mode
+      __syncthreads();                              // x_init complete for the stencil
+      residual();
+      double rw[EPT];
+      residual_of(d.mt, rw);
+      block_partials<NT>(2, [&](int i) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) s += (i == 0) ? r[k] * r[k] : rw[k] * rw[k];
+        return s;
+      }, sm.red);
+      if (tid == 0) sm.fl[5] = cross_warp<NT>(sm.red, 1) < cross_warp<NT>(sm.red, 0);
+      __syncthreads();
+      if (sm.fl[5]) {                               // the warm start wins
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          const int pp = tid + k * NT;
+          r[k] = rw[k];
+          if (pp < N) sm.xs[pp] = d.mt[pp];
+        }
+      }
+      proj_flops = 26ull * (unsigned long long)N;
+      // Sec. 3, Phase 2 on the residual of the guess: r = b - A x_init
+      // (FP64), c = V^T r (FP32 products, FP64 sums), alpha = H_a^{-1} c,
+      // x0 = x_init + V alpha
+      const int sl = d.slot + parity_base;
+      const SlotMeta mt = p.slotMeta[sl];
+      if (!sm.fl[5] && mt.timestep == tstep && mt.N == N && mt.a > 0) {   // uniform per block
+        const int a = mt.a;
+        const int nv = mt.lsq ? a + 1 : a;
+        const float* V = p.slotV32 + (size_t)sl * (p.max_a + 1) * p.slot_ld;
+        float rv[EPT];
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) rv[k] = (float)r[k];
+        block_partials_f32x<NT>(nv, [&](int i) {
+          const float* vi = V + (size_t)i * p.slot_ld;
+          float s = 0.f;
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) {
+            const int pp = tid + k * NT;
+            if (pp < N) s = fmaf(vi[pp], rv[k], s);
+          }
+          return s;
+        }, red32);
+        if (warp == 0) {
+          cross_warp_f32<NT>(red32, nv, sm.hb, lane);
+          __syncwarp();
+          const double* rot = p.slotRot + (size_t)sl * 3 * p.max_a;
+          solve_projected_warp(sm.hb, a, mt.nrot, p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a,
+                               p.max_a + 1, rot, rot + 2 * p.max_a, lane);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          const int pp = tid + k * NT;
+          if (pp < N) {
+            float xv = 0.f;
+            for (int i = 0; i < a; ++i) xv = fmaf((float)sm.hb[i], V[(size_t)i * p.slot_ld + pp], xv);
+            sm.xs[pp] += (double)xv;
+          }
+        }
+        proj_flops += (unsigned long long)(2 * nv + 2 * a) * (unsigned long long)N;
+      }
+    }
     if (p.x0_mode == X0_PROJECT) {
       // Sec. 3, Phase 2 with the seed's FP32 basis: c = V^T b (FP64 sums),
       // alpha = H_a^{-1} c (FP64), x0 = V alpha
@@ -234,8 +303,6 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
       }
     }
     __syncthreads();
-    double r[EPT];
-    auto residual = [&]() { residual_of(sm.xs, r); };
     if (p.x0_mode == X0_ZERO) {
 #pragma unroll
       for (int k = 0; k < EPT; ++k) r[k] = bval(tid + k * NT);

@@ -85,6 +85,7 @@ struct GmresParams {
   int cap_ld;
   int fixed_a;      // 1: the capture cycle takes min(cap_a, m) steps before the
                     // residual test may end it (fixed basis dimension, Sec. 3)
+  double inner_eta; // mixed precision: inner FP32 residual reduction per outer step (0 = 1e-5)
   // time march: timestep index and g^2 schedule in device memory (graph replay)
   const int* step;          // null = not marching
   const double* g2_sched;   // if step: g2 = g2_sched[*step + step_offset] for every system
@@ -158,7 +159,10 @@ __device__ __forceinline__ void st_release_gpu(int* a, int v) {
 
 constexpr int kVbRows = 48;   // rows per seed slot of the BF16 basis (tensor-core N tile)
 
-enum { X0_READ = 0, X0_ZERO = 1, X0_WARM = 2, X0_PROJECT = 3, X0_GALERKIN = 4 };
+// X0_GUESS_PROJECT: x_init is read from x; x0 = x_init + V_a H_a^{-1} V_a^T
+// (b - A x_init), the projection of Sec. 3 applied to the guess's residual
+// (mixed-precision solvers)
+enum { X0_READ = 0, X0_ZERO = 1, X0_WARM = 2, X0_PROJECT = 3, X0_GALERKIN = 4, X0_GUESS_PROJECT = 5 };
 
 // Solves G y = c (G: n x n column-major in shared memory, c: length n) by LU
 // with partial pivoting on one warp (lanes own rows); y overwrites c, G is

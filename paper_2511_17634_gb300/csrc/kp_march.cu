@@ -101,6 +101,12 @@ struct kp_march_plan {
   double* cycR = nullptr;                    // [max_seeds][(max_a + 1) * max_a]
   kp::SlotMeta* cycMeta = nullptr;           // [max_seeds]
   float* cycS = nullptr;                     // [K * ns][max_a][max_n] FP32 workspace
+  // learned guess: per parity, device tables of the targets' m^{n-1}, their
+  // seeds' m_seed^n and the guess output (the solver's x), internal order
+  kp_cnn* cnn = nullptr;
+  const double** lg_prev[2] = {nullptr, nullptr};
+  const double** lg_seed[2] = {nullptr, nullptr};
+  double** lg_x[2] = {nullptr, nullptr};
 };
 
 namespace {
@@ -115,9 +121,10 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset,
   g.nsys = seeds ? P->ns : tc.count;
   g.tol = seeds ? P->opt.tol_seed : P->opt.tol;
   g.m = seeds ? P->opt.m_seed : P->opt.m;
-  g.maxit = P->opt.maxit;
+  g.maxit = seeds && P->opt.maxit_seed > 0 ? P->opt.maxit_seed : P->opt.maxit;
   g.S = sh.S;
   g.reorth = c->opt.reorth;
+  g.inner_eta = kp::inner_eta(c->opt);
   g.npad = sh.ept * sh.nt;
   size_t spS = 0;
   if (P->ns && P->shS.S < P->opt.m_seed + 1)
@@ -190,6 +197,8 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset,
     g.score_stride = P->score_stride;
     g.x0_mode = P->opt.mode == KP_MARCH_PROJECTED ? (P->ns ? kp::X0_PROJECT : kp::X0_ZERO)
               : P->opt.mode == KP_MARCH_GALERKIN ? (P->ns ? kp::X0_GALERKIN : kp::X0_ZERO)
+              : P->opt.mode == KP_MARCH_LEARNED ? kp::X0_GUESS_PROJECT
+              : P->opt.mode == KP_MARCH_LEARNED_ONLY ? kp::X0_READ
               : P->opt.mode == KP_MARCH_WARM ? kp::X0_WARM : kp::X0_ZERO;
     g.acc_kind = 1;
     if (P->Cp) {
@@ -239,9 +248,24 @@ cudaError_t launch_cycle(kp_march_plan* P, int offset, cudaStream_t st) {
   return kp::launch_cycle(q, nmax, P->K * P->ns, st);
 }
 
+// The learned guess of the targets of step n (parity par): pack, network and
+// x_init = m^{n-1} + s_n * net into the solver's output planes, in passes of
+// the network's inference batch.
+cudaError_t enqueue_guess(kp_march_plan* P, int par, int* nl) {
+  const int B = kp::cnn_inference_batch(P->cnn);
+  cudaError_t e = cudaSuccess;
+  for (int c0 = 0; c0 < P->nt && e == cudaSuccess; c0 += B) {
+    e = kp::cnn_enqueue_guess(P->cnn, std::min(B, P->nt - c0), P->lg_prev[par] + c0, P->lg_seed[par] + c0,
+                              P->lg_x[par] + c0, P->step, 0, P->g2, P->opt.T, P->st);
+    *nl += 2 + 4;                            // pack, four layers, x_init (a four-layer network)
+  }
+  return e;
+}
+
 // Target step n and seed step n+1 for parity p = n & 1.  With ev (timing
-// mode) the two launches run one after the other between events
-// ev[0..1] (seeds) and ev[2..3] (targets); otherwise on two branches.
+// mode) the launches run one after the other between events ev[0..1]
+// (seeds), ev[4..5] (learned guess) and ev[2..3] (targets); otherwise seeds
+// and targets run on two branches.
 kp_status enqueue_step(kp_march_plan* P, int par, cudaEvent_t* ev, int* launches) {
   cudaError_t e = cudaSuccess;
   int nl = 0;
@@ -258,6 +282,11 @@ kp_status enqueue_step(kp_march_plan* P, int par, cudaEvent_t* ev, int* launches
     ++nl;
     if (P->cycling && e == cudaSuccess) { e = launch_cycle(P, 1, sst); ++nl; }
     if (ev && e == cudaSuccess) e = cudaEventRecord(ev[1], sst);
+  }
+  if (P->nt > 0 && P->cnn && e == cudaSuccess) {
+    if (ev) e = cudaEventRecord(ev[4], P->st);
+    if (e == cudaSuccess) e = enqueue_guess(P, par, &nl);
+    if (ev && e == cudaSuccess) e = cudaEventRecord(ev[5], P->st);
   }
   if (P->nt > 0 && e == cudaSuccess) {
     if (ev) e = cudaEventRecord(ev[2], P->st);
@@ -351,6 +380,11 @@ kp_status kp_march_destroy(kp_march_plan* P) {
   cudaFree(P->cycMeta);
   cudaFree(P->cycS);
   cudaFree(P->perm);
+  for (int k = 0; k < 2; ++k) {
+    cudaFree(P->lg_prev[k]);
+    cudaFree(P->lg_seed[k]);
+    cudaFree(P->lg_x[k]);
+  }
   cudaFree(P->Bb);
   cudaFree(P->Cp);
   cudaFree(P->tiles[0]);
@@ -372,7 +406,7 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
   if (!out || !opt || ngroups < 1 || !groups) return kp::set_error(c, KP_ERR_ARG, "bad march arguments");
   *out = nullptr;
   const kp_march_opts& o = *opt;
-  if (o.T < 1 || !o.g2 || o.mode < 0 || o.mode > 3 || o.m_seed < 1 || o.m_seed > kp::kMaxM ||
+  if (o.T < 1 || !o.g2 || o.mode < 0 || o.mode > 5 || o.m_seed < 1 || o.m_seed > kp::kMaxM ||
       (o.score != nullptr) != (o.embed != nullptr) || o.picard < 0 ||
       o.m < 1 || o.m > kp::kMaxM || o.maxit < 0 || !(o.tol >= 0) || !(o.tol_seed >= 0))
     return kp::set_error(c, KP_ERR_ARG, "bad march options");
@@ -389,7 +423,8 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
       kp_march_destroy(P);
       return kp::set_error(c, KP_ERR_ARG, "group %d: bad sizes or pointers", gi);
     }
-    if (o.mode == KP_MARCH_PROJECTED || o.mode == KP_MARCH_GALERKIN)
+    if (o.mode == KP_MARCH_PROJECTED || o.mode == KP_MARCH_GALERKIN || o.mode == KP_MARCH_LEARNED ||
+        o.mode == KP_MARCH_LEARNED_ONLY)
       for (int t = 0; t < g.ntgt; ++t)
         if (g.tgt_seed[t] < 0 || g.tgt_seed[t] >= g.nseed) {
           kp_march_destroy(P);
@@ -458,6 +493,21 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
   if (o.score && (P->mixed || P->shT.cs)) {
     kp_march_destroy(P);
     return kp::set_error(c, KP_ERR_UNSUPPORTED, "score extraction needs the FP64 one-block solver");
+  }
+  const bool learned = o.mode == KP_MARCH_LEARNED || o.mode == KP_MARCH_LEARNED_ONLY;
+  if (learned) {
+    if (!P->mixed || ngroups != 1 || o.picard > 1 || o.seed_solver != KP_SEED_GMRES || P->cycling ||
+        !P->ns) {
+      kp_march_destroy(P);
+      return kp::set_error(c, KP_ERR_UNSUPPORTED, "learned march: mixed precision, one grid size, "
+                           "GMRES seeds, one Picard iteration, no seed cycling");
+    }
+    if (!kp::cnn_march_ready(o.cnn, groups[0].H, groups[0].W)) {
+      kp_march_destroy(P);
+      return kp::set_error(c, KP_ERR_ARG, "learned march: needs a %dx%d network with 8 inputs, 1 output "
+                           "and an inference batch", groups[0].H, groups[0].W);
+    }
+    P->cnn = o.cnn;
   }
   // window length: FP64 one-block solvers only; 2K slot sets must fit
   if (!P->mixed && !P->shS.cs && !P->shT.cs && o.window != 1 && P->nt > 0) {
@@ -630,6 +680,25 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
       seed_base += g.nseed;
     }
     e = cudaMemcpy(P->desc[par], hd.data(), hd.size() * sizeof(SysDesc), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && P->cnn) {
+      // learned guess tables: target k reads m^{n-1} (its descriptor's lagged
+      // field) and the m_seed^n that the seeds of the previous launch wrote to
+      // S[1 - par]; the guess goes to the solver's output planes
+      std::vector<const double*> hp(nt), hs(nt);
+      std::vector<double*> hx(nt);
+      for (int k = 0; k < nt; ++k) {
+        const SysDesc& d = hd[(size_t)ns + k];
+        hp[k] = d.mt;
+        hx[k] = d.x;
+        hs[k] = P->S[1 - par] + (size_t)d.slot * groups[0].H * groups[0].W;
+      }
+      e = dmalloc(&P->lg_prev[par], nt);
+      if (e == cudaSuccess) e = dmalloc(&P->lg_seed[par], nt);
+      if (e == cudaSuccess) e = dmalloc(&P->lg_x[par], nt);
+      if (e == cudaSuccess) e = cudaMemcpy(P->lg_prev[par], hp.data(), nt * sizeof(double*), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(P->lg_seed[par], hs.data(), nt * sizeof(double*), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(P->lg_x[par], hx.data(), nt * sizeof(double*), cudaMemcpyHostToDevice);
+    }
   }
   if (e == cudaSuccess) e = cudaMemcpy(P->g2, o.g2, o.T * sizeof(double), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && P->mixed && o.mode == KP_MARCH_PROJECTED && ns > 0 && nt > 0 &&
@@ -763,8 +832,9 @@ kp_status kp_march_run(kp_march_plan* P, int n0, int steps, kp_step_stats* stats
   int launches = 0;
   const int K = P->K;
   const int nwin = (steps + K - 1) / K;       // launches of the step (K = 1) or window graph
+  constexpr int kEv = 6;                      // events per step or window (see enqueue_step)
   if (e == cudaSuccess && timing) {
-    ev.resize((size_t)nwin * 4 + 2, nullptr);
+    ev.resize((size_t)nwin * kEv + 2, nullptr);
     for (auto& x : ev)
       if (e == cudaSuccess) e = cudaEventCreate(&x);
   }
@@ -773,18 +843,18 @@ kp_status kp_march_run(kp_march_plan* P, int n0, int steps, kp_step_stats* stats
   // the first targets
   if (e == cudaSuccess && P->ns) {
     kp::GmresParams g = solver_params(P, true, 1 - q0, 0);
-    if (timing) e = cudaEventRecord(ev[(size_t)nwin * 4], P->st);
+    if (timing) e = cudaEventRecord(ev[(size_t)nwin * kEv], P->st);
     if (e == cudaSuccess) e = launch_solver(P, g, P->shS, P->st);
     ++launches;
     if (P->cycling && e == cudaSuccess) { e = launch_cycle(P, 0, P->st); ++launches; }
-    if (timing && e == cudaSuccess) e = cudaEventRecord(ev[(size_t)nwin * 4 + 1], P->st);
+    if (timing && e == cudaSuccess) e = cudaEventRecord(ev[(size_t)nwin * kEv + 1], P->st);
   }
   for (int k = 0; k < nwin && e == cudaSuccess && r == KP_OK; ++k) {
     const int par = K > 1 ? 0 : (n0 + k) & 1;
     if (timing) {
       int nl = 0;
-      r = K > 1 ? enqueue_window(P, ev.data() + (size_t)k * 4, &nl)
-                : enqueue_step(P, par, ev.data() + (size_t)k * 4, &nl);
+      r = K > 1 ? enqueue_window(P, ev.data() + (size_t)k * kEv, &nl)
+                : enqueue_step(P, par, ev.data() + (size_t)k * kEv, &nl);
       launches += nl;
     } else if (P->graph[par]) {
       e = cudaGraphLaunch(P->graph[par], P->st);
@@ -837,11 +907,15 @@ kp_status kp_march_run(kp_march_plan* P, int n0, int steps, kp_step_stats* stats
     std::memset(timing, 0, sizeof(*timing));
     float t = 0.f;
     if (P->ns) {
-      e = cudaEventElapsedTime(&t, ev[(size_t)nwin * 4], ev[(size_t)nwin * 4 + 1]);
+      e = cudaEventElapsedTime(&t, ev[(size_t)nwin * kEv], ev[(size_t)nwin * kEv + 1]);
       timing->seed_ms += t;
     }
     for (int k = 0; k < nwin && e == cudaSuccess; ++k) {
-      cudaEvent_t* x = ev.data() + (size_t)k * 4;
+      cudaEvent_t* x = ev.data() + (size_t)k * kEv;
+      if (P->cnn && P->nt) {
+        e = cudaEventElapsedTime(&t, x[4], x[5]);
+        timing->proj_ms += t;
+      }
       if (P->ns) {
         e = cudaEventElapsedTime(&t, x[0], x[1]);
         timing->seed_ms += t;
@@ -852,7 +926,7 @@ kp_status kp_march_run(kp_march_plan* P, int n0, int steps, kp_step_stats* stats
       }
     }
     if (e == cudaSuccess && P->ns && P->nt)
-      e = cudaEventElapsedTime(&timing->step_ms, ev[(size_t)nwin * 4], ev[(size_t)(nwin - 1) * 4 + 3]);
+      e = cudaEventElapsedTime(&timing->step_ms, ev[(size_t)nwin * kEv], ev[(size_t)(nwin - 1) * kEv + 3]);
   }
   if (timing) timing->launches = launches;
   for (auto& x : ev)

@@ -33,7 +33,7 @@ class _Options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("smem_vectors", ctypes.c_int),
                 ("reorth", ctypes.c_int), ("block_threads", ctypes.c_int),
                 ("blocks_per_sm", ctypes.c_int), ("cluster_size", ctypes.c_int),
-                ("fixed_a", ctypes.c_int)]
+                ("fixed_a", ctypes.c_int), ("inner_digits", ctypes.c_int)]
 
 
 # kp_op: int H, W; double dt, g2, h; const double *mtilde, *fx, *fy
@@ -79,14 +79,15 @@ def lib():
         L.kp_cnn_gradients.argtypes = [vp, i, vp, vp, vp, vp]
         L.kp_cnn_train_step.argtypes = [vp, i, vp, vp, f32, f32, f32, f32, i, vp]
         L.kp_cnn_pack_inputs.argtypes = [vp, i, vp, vp, d, vp]
-        L.kp_cnn_add_guess.argtypes = [vp, i, vp, vp, vp]
-        L.kp_cnn_pack_target.argtypes = [vp, i, vp, vp, vp]
+        L.kp_cnn_add_guess.argtypes = [vp, i, vp, vp, d, vp]
+        L.kp_cnn_pack_target.argtypes = [vp, i, vp, vp, d, vp]
+        L.kp_cnn_set_inference_batch.argtypes = [vp, i]
         for f in ("kp_create", "kp_destroy", "kp_set_stream", "kp_apply", "kp_rhs", "kp_seed_solve",
                   "kp_refine", "kp_store_basis", "kp_project_targets", "kp_project_targets_multi",
                   "kp_basis_get", "kp_project_gemm_bf16", "kp_residual", "kp_cnn_create",
                   "kp_cnn_destroy", "kp_cnn_num_params", "kp_cnn_set_params", "kp_cnn_get_params",
                   "kp_cnn_forward", "kp_cnn_gradients", "kp_cnn_train_step", "kp_cnn_pack_inputs",
-                  "kp_cnn_add_guess", "kp_cnn_pack_target"):
+                  "kp_cnn_add_guess", "kp_cnn_pack_target", "kp_cnn_set_inference_batch"):
             getattr(L, f).restype = i
         _lib = L
     return _lib
@@ -162,7 +163,7 @@ class Context:
 
     def __init__(self, max_seeds=64, max_a=40, max_n=4096, precision=PREC_FP64, smem_vectors=0,
                  reorth=0, stream=None, block_threads=0, blocks_per_sm=0, cluster_size=0,
-                 fixed_a=False):
+                 fixed_a=False, inner_digits=0):
         import torch
         L = lib()
         o = _Options()
@@ -173,6 +174,7 @@ class Context:
         o.blocks_per_sm = blocks_per_sm
         o.cluster_size = cluster_size
         o.fixed_a = int(bool(fixed_a))
+        o.inner_digits = int(inner_digits)
         self._h = ctypes.c_void_p()
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
@@ -271,6 +273,7 @@ class Context:
 
 # ---------------------------------------------------------------- time march
 MARCH_PROJECTED, MARCH_PLAIN, MARCH_WARM, MARCH_GALERKIN = 0, 1, 2, 3
+MARCH_LEARNED, MARCH_LEARNED_ONLY = 4, 5
 SEED_GMRES, SEED_BICGSTAB = 0, 1
 
 
@@ -286,7 +289,8 @@ class _MarchOpts(ctypes.Structure):
                 ("m", ctypes.c_int), ("maxit", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("window", ctypes.c_int), ("target_blocks", ctypes.c_int),
                 ("score", ctypes.c_void_p), ("embed", ctypes.c_void_p), ("picard", ctypes.c_int),
-                ("seed_solver", ctypes.c_int), ("wait_probe", ctypes.c_int)]
+                ("seed_solver", ctypes.c_int), ("wait_probe", ctypes.c_int), ("maxit_seed", ctypes.c_int),
+                ("cnn", ctypes.c_void_p)]
 
 
 class StepStats(ctypes.Structure):
@@ -324,7 +328,8 @@ class March:
 
     def __init__(self, ctx, groups, T, g2, mode=MARCH_PROJECTED, tol_seed=1e-10, tol=1e-8,
                  m_seed=40, m=40, maxit=1000, use_graph=True, window=0, target_blocks=0,
-                 score=None, embed=None, picard=1, seed_solver=0, wait_probe=False):
+                 score=None, embed=None, picard=1, seed_solver=0, wait_probe=False, cnn=None,
+                 maxit_seed=0):
         L = _march_lib()
         self.ctx = ctx
         self._keep = []
@@ -356,7 +361,10 @@ class March:
                        int(window), int(target_blocks),
                        score.data_ptr() if score is not None else None,
                        embed.data_ptr() if embed is not None else None, int(picard),
-                       int(seed_solver), int(wait_probe))
+                       int(seed_solver), int(wait_probe), int(maxit_seed),
+                       cnn._h if cnn is not None else None)
+        if cnn is not None:
+            self._keep.append(cnn)
         self.T = T
         self._h = ctypes.c_void_p()
         ctx._check(L.kp_march_create(ctx._h, len(groups), ctypes.cast(arr, ctypes.c_void_p),
@@ -396,6 +404,7 @@ class CNN:
                                    ctypes.cast(ch, ctypes.c_void_p), ctypes.byref(self._h)))
         self.H, self.W, self.channels, self.max_batch = H, W, tuple(channels), max_batch
         self.nparams = L.kp_cnn_num_params(self._h)
+        self.inference_batch = max_batch
 
     def close(self):
         if self._h:
@@ -418,6 +427,11 @@ class CNN:
         self.ctx._check(lib().kp_cnn_get_params(self._h, p.ctypes.data_as(ctypes.c_void_p)))
         return p
 
+    def set_inference_batch(self, B):
+        """Size the inference buffers (forward and the learned march) for B images."""
+        self.ctx._check(lib().kp_cnn_set_inference_batch(self._h, int(B)))
+        self.inference_batch = int(B)
+
     def forward(self, x, out):
         """x: CUDA float32 [B][c0][H*W]; out: CUDA float32 [B][cL][H*W]."""
         self.ctx._check(lib().kp_cnn_forward(self._h, x.shape[0], ctypes.c_void_p(x.data_ptr()),
@@ -430,25 +444,25 @@ class CNN:
             ctypes.c_void_p(grads.data_ptr()) if grads is not None else None, ctypes.byref(loss)))
         return loss.value
 
-    def pack_inputs(self, img, seed, tau, out):
-        """out [B][6][H*W] float32 from FP64 image and seed-state planes (rows or lists)."""
-        pi, ps = ptrs(img), ptrs(seed)
+    def pack_inputs(self, mprev, seed, tau, out):
+        """out [B][6][H*W] float32 from FP64 lagged-field and seed-state planes (rows or lists)."""
+        pi, ps = ptrs(mprev), ptrs(seed)
         self.ctx._check(lib().kp_cnn_pack_inputs(self._h, len(pi), pi.ctypes.data_as(ctypes.c_void_p),
                                                  ps.ctypes.data_as(ctypes.c_void_p), float(tau),
                                                  ctypes.c_void_p(out.data_ptr())))
 
-    def pack_target(self, a, b, out):
-        """out [B][1][H*W] float32 = a - b (FP64 planes)."""
+    def pack_target(self, a, b, out, scale=1.0):
+        """out [B][1][H*W] float32 = (a - b) * scale (FP64 planes)."""
         pa, pb = ptrs(a), ptrs(b)
         self.ctx._check(lib().kp_cnn_pack_target(self._h, len(pa), pa.ctypes.data_as(ctypes.c_void_p),
-                                                 pb.ctypes.data_as(ctypes.c_void_p),
+                                                 pb.ctypes.data_as(ctypes.c_void_p), float(scale),
                                                  ctypes.c_void_p(out.data_ptr())))
 
-    def add_guess(self, delta, base, x):
-        """x = base + delta (FP64 planes; delta float32 [B][1][H*W])."""
+    def add_guess(self, delta, base, x, scale=1.0):
+        """x = base + scale * delta (FP64 planes; delta float32 [B][1][H*W])."""
         pb, px = ptrs(base), ptrs(x)
         self.ctx._check(lib().kp_cnn_add_guess(self._h, len(pb), ctypes.c_void_p(delta.data_ptr()),
-                                               pb.ctypes.data_as(ctypes.c_void_p),
+                                               pb.ctypes.data_as(ctypes.c_void_p), float(scale),
                                                px.ctypes.data_as(ctypes.c_void_p)))
 
     def train_step(self, x, target, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):

@@ -1,7 +1,23 @@
 """The learned-guess network's GPU kernels (im2col + tcgen05 GEMM forward,
-input and weight gradients, Adam) against the FP64 reference.  BF16
-operands with FP32 accumulation: outputs within 3e-2 and gradients within
-5e-2 relative (L2), set by BF16's 2^-9 rounding through four layers."""
+input and weight gradients, Adam) against the FP64 reference.
+
+Error bound.  The kernels multiply BF16 operands (8 significant bits, unit
+roundoff u = 2^-8) and accumulate in FP32.  The reference run with the same
+operands rounded to BF16 (``cnn_oracle.bf16`` at the points a tensor-core
+product sees them) differs from the kernels by FP32 accumulation -- K <= 9 *
+32 = 288 products per output (forward) and B * H * W per weight gradient,
+each sum within K * 2^-24 of the sum of its magnitudes -- and by isolated
+rounding flips: an activation whose FP32 sum lies within ~1e-7 of a BF16
+rounding boundary rounds to the neighbouring BF16 value in the FP64
+reference (probability ~2e-7 / 2^-8 per activation), which moves that one
+operand by u and its 7x7 output neighbourhood accordingly.  So the bulk is
+checked elementwise (90 % of outputs within 1e-5 of the output rms) and the
+whole at 2e-3 (L2, outputs and each parameter tensor's gradient).  Against
+the unrounded FP64 network
+the difference is the BF16 operand rounding itself (u per operand, summed
+over four layers and amplified by cancellation in each sum); the test
+asserts it stays within 1.5x of what the rounded reference shows and under
+3e-2 / 5e-2."""
 import numpy as np
 import pytest
 
@@ -66,18 +82,32 @@ def test_forward_and_gradients_match_reference(kp, H, W, B):
     grads = torch.zeros(net.nparams, dtype=torch.float32, device="cuda")
     loss = net.gradients(xin, tg, grads)
     torch.cuda.synchronize()
-    ref_out = R.forward(p, ch, x)[-1]
-    assert _rel(out.cpu().numpy().reshape(ref_out.shape), ref_out) <= 3e-2
-    ref_loss, ref_g = R.loss_and_grads(p, ch, x, t)
+    # the FP32 input planes are what the kernels round to BF16
+    x32 = x.astype(np.float32).astype(np.float64)
+    gout = out.cpu().numpy().astype(np.float64).reshape(B, 1, W, H)
+    ref_out = R.forward(p, ch, x32)[-1]
+    bf_out = R.forward(p, ch, x32, operand_round=R.bf16)[-1]
+    e_bf, e64, e_rnd = _rel(gout, bf_out), _rel(gout, ref_out), _rel(bf_out, ref_out)
+    bulk = np.quantile(np.abs(gout - bf_out), 0.9) / np.sqrt(np.mean(bf_out ** 2))
+    print(f"forward: vs BF16-operand reference {e_bf:.2e} (90th percentile {bulk:.1e} of rms), "
+          f"vs FP64 {e64:.2e} (rounding alone {e_rnd:.2e})")
+    assert bulk <= 1e-5 and e_bf <= 2e-3
+    assert e64 <= max(1.5 * e_rnd, 1e-4) and e64 <= 3e-2
+    t32 = t.astype(np.float32).astype(np.float64)
+    ref_loss, ref_g = R.loss_and_grads(p, ch, x32, t32)
+    bf_loss, bf_g = R.loss_and_grads(p, ch, x32, t32, operand_round=R.bf16)
+    assert abs(loss - bf_loss) <= 2e-3 * bf_loss
     assert abs(loss - ref_loss) <= 3e-2 * ref_loss
     g = grads.cpu().numpy().astype(np.float64)
     o = 0
     for ci, co in zip(ch[:-1], ch[1:]):
         nw = co * ci * 9
-        gw, rw = g[o:o + nw], ref_g[o:o + nw]
-        gb, rb = g[o + nw:o + nw + co], ref_g[o + nw:o + nw + co]
-        assert _rel(gw, rw) <= 5e-2, ("weights", ci, co, _rel(gw, rw))
-        assert _rel(gb, rb) <= 5e-2, ("bias", ci, co, _rel(gb, rb))
+        for name, sl in (("weights", slice(o, o + nw)), ("bias", slice(o + nw, o + nw + co))):
+            eb, e6, er = _rel(g[sl], bf_g[sl]), _rel(g[sl], ref_g[sl]), _rel(bf_g[sl], ref_g[sl])
+            print(f"{name} {ci}->{co}: vs BF16-operand reference {eb:.2e}, vs FP64 {e6:.2e} "
+                  f"(rounding alone {er:.2e})")
+            assert eb <= 2e-3, (name, ci, co, eb)
+            assert e6 <= max(1.5 * er, 1e-4) and e6 <= 5e-2, (name, ci, co, e6, er)
         o += nw + co
 
 
@@ -94,6 +124,43 @@ def test_training_reduces_loss(kp):
     tg = torch.as_tensor(t.reshape(B, 1, -1), dtype=torch.float32, device="cuda")
     losses = [net.train_step(xin, tg, k + 1, lr=2e-3) for k in range(150)]
     assert losses[-1] < 0.05 * losses[0], (losses[0], losses[-1])
+
+
+def test_adam_steps_match_reference(kp):
+    # kp_cnn_train_step = the network's gradients + one Adam step on the FP32
+    # master weights (Kingma & Ba 2015, with the bias corrections 1 - b^t).
+    # The reference Adam (cnn_oracle.adam, FP64) is applied to the GPU's own
+    # gradients at the same weights, so the comparison isolates the optimiser:
+    # FP32 arithmetic bounds the difference by ~1e-6 lr per weight; a wrong
+    # bias correction or a missing square root moves weights by O(lr).
+    rng = np.random.default_rng(21)
+    H, W, B = 12, 10, 2
+    ch = (6, 32, 32, 32, 1)
+    x = rng.uniform(0, 1, size=(B, 6, W, H))
+    t = rng.normal(scale=0.3, size=(B, 1, W, H))
+    ctx = kp.Context(max_n=4096)
+    net = kp.CNN(ctx, H, W, channels=ch, max_batch=B)
+    net.set_params(_init(ch, rng))
+    xin = torch.as_tensor(x.reshape(B, 6, -1), dtype=torch.float32, device="cuda")
+    tg = torch.as_tensor(t.reshape(B, 1, -1), dtype=torch.float32, device="cuda")
+    grads = torch.zeros(net.nparams, dtype=torch.float32, device="cuda")
+    lr, b1, b2, eps = 3e-3, 0.9, 0.999, 1e-8
+    m = np.zeros(net.nparams)
+    v = np.zeros(net.nparams)
+    for step in range(1, 5):
+        p_now = net.get_params().astype(np.float64)
+        net.gradients(xin, tg, grads)
+        torch.cuda.synchronize()
+        gk = grads.cpu().numpy().astype(np.float64)
+        p_ref, m, v = R.adam(p_now, gk, m, v, step, lr=lr, b1=b1, b2=b2, eps=eps)
+        net.train_step(xin, tg, step, lr=lr, beta1=b1, beta2=b2, eps=eps)
+        torch.cuda.synchronize()
+        p_gpu = net.get_params().astype(np.float64)
+        dev = np.abs(p_gpu - p_ref)
+        print(f"Adam step {step}: max |p_gpu - p_ref| = {dev.max():.2e} (lr {lr})")
+        assert dev.max() <= 1e-4 * lr + 1e-6 * np.abs(p_ref).max(), step
+        # the step moved the weights by about lr: the bound is meaningful
+        assert np.median(np.abs(p_gpu - p_now)) >= 0.1 * lr
 
 
 @pytest.mark.parametrize("H,W,B", [(7, 5, 1), (40, 30, 3), (128, 128, 10)])
