@@ -96,6 +96,9 @@ typedef struct {
                         the outer tolerance, whichever is reached first) before
                         the FP64 iterative refinement recomputes the true
                         residual; 1..7, 0 = 5                                     */
+  int cluster_blocks_per_sm; /* cluster solver (grids above 4096 points): resident
+                        CTAs per SM, 1 or 2; 0 = 2 (two systems share the SMs, a
+                        smaller shared-memory window of Krylov vectors)          */
 } kp_options;
 
 /* Operator of one system (Sec. 2.3): A(m~; g^2, dt, h, f).  `mtilde` is the

@@ -36,7 +36,7 @@ kp_status cuda_error(kp_ctx* c, cudaError_t e, const char* what) {
 }
 
 cudaError_t launch_solver(const GmresParams& p, const Shape& sh, bool mixed, cudaStream_t st) {
-  if (sh.cs > 0) return launch_gmres_cluster(p, sh.ept, sh.nt, sh.cs, sh.smem, st);
+  if (sh.cs > 0) return launch_gmres_cluster(p, sh.ept, sh.nt, sh.cs, sh.minb, sh.smem, st);
   return mixed ? launch_gmres_mixed(p, sh.ept, sh.nt, sh.smem, st)
                : launch_gmres_fp64(p, sh.ept, sh.nt, sh.minb, sh.smem, st);
 }
@@ -70,6 +70,7 @@ kp_status gmres_shape(kp_ctx* c, int nmax, int m, Shape* out, bool mixed, int wm
     }
     if (!sh.cs || wmin <= 0 || wmin % sh.cs)
       return set_error(c, KP_ERR_UNSUPPORTED, "N=%d: needs W divisible by the cluster size and N <= 16384", nmax);
+    sh.minb = c->opt.cluster_blocks_per_sm ? c->opt.cluster_blocks_per_sm : 2;
   }
   else return set_error(c, KP_ERR_UNSUPPORTED, "N=%d: FP64 grids above 4096 unknowns are not supported (use the mixed-precision mode)", nmax);
   const int npad = sh.ept * sh.nt;
@@ -81,8 +82,11 @@ kp_status gmres_shape(kp_ctx* c, int nmax, int m, Shape* out, bool mixed, int wm
   if (S <= 0) {
     // small systems: leave room for minb resident blocks per SM (1 KB of
     // shared memory per block is reserved by the hardware)
-    const size_t budget = (npad <= 1024 && !sh.cs) ? c->smem_optin / sh.minb - (sh.minb > 2 ? 1024 : 0)
-                                                   : c->smem_optin;
+    // (clusters: every CTA of a system's cluster sits on its own SM, and MINB
+    // systems' CTAs share one)
+    const size_t budget = sh.cs ? c->smem_optin / sh.minb - (sh.minb >= 2 ? 1024 : 0)
+                        : npad <= 1024 ? c->smem_optin / sh.minb - (sh.minb > 2 ? 1024 : 0)
+                                       : c->smem_optin;
     S = budget > fixed ? (int)((budget - fixed) / per) : 0;
   }
   S = std::min(S, m + 1);
@@ -283,6 +287,7 @@ void kp_options_default(kp_options* o) {
   o->cluster_size = 0;
   o->fixed_a = 0;
   o->inner_digits = 0;
+  o->cluster_blocks_per_sm = 0;
 }
 
 kp_status kp_create(kp_ctx** out, const kp_options* opt, void* stream) {
@@ -296,7 +301,8 @@ kp_status kp_create(kp_ctx** out, const kp_options* opt, void* stream) {
       o.smem_vectors < 0 || (o.reorth != 0 && o.reorth != 1) ||
       (o.block_threads != 0 && o.block_threads != 64 && o.block_threads != 128 && o.block_threads != 256) ||
       (o.cluster_size != 0 && o.cluster_size != 2 && o.cluster_size != 4 && o.cluster_size != 8) ||
-      (o.fixed_a != 0 && o.fixed_a != 1) || o.inner_digits < 0 || o.inner_digits > 7)
+      (o.fixed_a != 0 && o.fixed_a != 1) || o.inner_digits < 0 || o.inner_digits > 7 ||
+      o.cluster_blocks_per_sm < 0 || o.cluster_blocks_per_sm > 2)
     return KP_ERR_ARG;
   {
     // solver shapes compiled for grids of <= 1024 points: (threads, blocks per SM)

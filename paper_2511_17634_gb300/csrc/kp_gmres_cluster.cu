@@ -22,8 +22,12 @@ namespace cg = cooperative_groups;
 namespace kp {
 namespace {
 
-template <int EPT, int NT, int CS>
-__global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams p) {
+// MINB resident CTAs per SM: 2 (the default) lets two systems' clusters
+// share the SMs, so one system's barriers and serial FP64 work overlap the
+// other's vector work (registers capped at 128, a smaller shared-memory
+// window); 1 gives one CTA the whole SM.
+template <int EPT, int NT, int CS, int MINB>
+__global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresParams p) {
   constexpr int NWARPS = NT / 32;
   extern __shared__ __align__(16) double smem_raw[];
   cg::cluster_group cluster = cg::this_cluster();
@@ -593,9 +597,9 @@ __global__ void __launch_bounds__(NT, 1) gmres_cluster_kernel(const GmresParams 
   cluster.sync();                                 // no CTA leaves while others read its memory
 }
 
-template <int EPT, int NT, int CS>
+template <int EPT, int NT, int CS, int MINB>
 cudaError_t launch_c(const GmresParams& p, size_t smem, cudaStream_t st) {
-  auto k = gmres_cluster_kernel<EPT, NT, CS>;
+  auto k = gmres_cluster_kernel<EPT, NT, CS, MINB>;
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -629,11 +633,18 @@ size_t gmres_cluster_smem_bytes(int ept, int nt, int S, int m) {
   return doubles * sizeof(double) + 8 * sizeof(int) + (size_t)S * npad * sizeof(float);
 }
 
-cudaError_t launch_gmres_cluster(const GmresParams& p, int ept, int nt, int cs, size_t smem,
+cudaError_t launch_gmres_cluster(const GmresParams& p, int ept, int nt, int cs, int minb, size_t smem,
                                  cudaStream_t st) {
-  if (ept == 8 && nt == 256 && cs == 8) return launch_c<8, 256, 8>(p, smem, st);
-  if (ept == 8 && nt == 256 && cs == 2) return launch_c<8, 256, 2>(p, smem, st);
-  if (ept == 8 && nt == 256 && cs == 4) return launch_c<8, 256, 4>(p, smem, st);
+  if (ept != 8 || nt != 256) return cudaErrorInvalidValue;
+  if (minb == 2) {
+    if (cs == 8) return launch_c<8, 256, 8, 2>(p, smem, st);
+    if (cs == 4) return launch_c<8, 256, 4, 2>(p, smem, st);
+    if (cs == 2) return launch_c<8, 256, 2, 2>(p, smem, st);
+  } else {
+    if (cs == 8) return launch_c<8, 256, 8, 1>(p, smem, st);
+    if (cs == 4) return launch_c<8, 256, 4, 1>(p, smem, st);
+    if (cs == 2) return launch_c<8, 256, 2, 1>(p, smem, st);
+  }
   return cudaErrorInvalidValue;
 }
 

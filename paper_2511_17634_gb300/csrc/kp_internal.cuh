@@ -540,7 +540,7 @@ cudaError_t launch_gmres_mixed(const GmresParams& p, int ept, int nt, size_t sme
                                cudaStream_t st);
 size_t gmres_cluster_smem_bytes(int ept, int nt, int S, int m);
 // Cluster of cs CTAs per system (grids above 4096 unknowns, mixed precision).
-cudaError_t launch_gmres_cluster(const GmresParams& p, int ept, int nt, int cs, size_t smem,
+cudaError_t launch_gmres_cluster(const GmresParams& p, int ept, int nt, int cs, int minb, size_t smem,
                                  cudaStream_t st);
 // The N <= 1024 instantiation (4 points x 256 threads) on an explicit grid;
 // the kernel strides over systems, block b using Krylov workspace slice b.

@@ -33,7 +33,8 @@ class _Options(ctypes.Structure):
                 ("precision", ctypes.c_int), ("smem_vectors", ctypes.c_int),
                 ("reorth", ctypes.c_int), ("block_threads", ctypes.c_int),
                 ("blocks_per_sm", ctypes.c_int), ("cluster_size", ctypes.c_int),
-                ("fixed_a", ctypes.c_int), ("inner_digits", ctypes.c_int)]
+                ("fixed_a", ctypes.c_int), ("inner_digits", ctypes.c_int),
+                ("cluster_blocks_per_sm", ctypes.c_int)]
 
 
 # kp_op: int H, W; double dt, g2, h; const double *mtilde, *fx, *fy
@@ -163,7 +164,7 @@ class Context:
 
     def __init__(self, max_seeds=64, max_a=40, max_n=4096, precision=PREC_FP64, smem_vectors=0,
                  reorth=0, stream=None, block_threads=0, blocks_per_sm=0, cluster_size=0,
-                 fixed_a=False, inner_digits=0):
+                 fixed_a=False, inner_digits=0, cluster_blocks_per_sm=0):
         import torch
         L = lib()
         o = _Options()
@@ -175,6 +176,7 @@ class Context:
         o.cluster_size = cluster_size
         o.fixed_a = int(bool(fixed_a))
         o.inner_digits = int(inner_digits)
+        o.cluster_blocks_per_sm = int(cluster_blocks_per_sm)
         self._h = ctypes.c_void_p()
         s = stream if stream is not None else torch.cuda.current_stream()
         self.stream = s
