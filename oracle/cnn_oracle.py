@@ -129,19 +129,25 @@ def adam(params, grads, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
 # target image + seed solution at timestep t + t embedding": the target image
 # as the march has carried it to timestep n-1 (its lagged field m_i^{n-1};
 # the image itself at n = 1), the seed's solution m_seed^n of the same
-# timestep, and four time planes tau, 1 - tau, sin(pi tau), cos(pi tau) for
-# tau = n / T (each distinct over 0 < tau <= 1, unlike harmonics of 2 pi tau,
-# which confuse the first timesteps with the last -- while the implicit
-# step's damping of fine detail grows with dt (g^n)^2 over the march).  The
-# network predicts the step's change in
-# units of s_n = dt (g^n)^2 / h^2 (the coefficient of the pixel Laplacian in
-# the implicit step), so the guess is x_init = m_i^{n-1} + s_n * net(...).
+# timestep, four time planes tau, 1 - tau, sin(pi tau), cos(pi tau) for
+# tau = n / T (each distinct over 0 < tau <= 1), and, derived from the
+# target image and t, the residual the step leaves at the image,
+# r = m^{n-1}/dt - A m^{n-1} (A of Sec. 2.3 at timestep n, lagged on m^{n-1}),
+# scaled to unit rms: r_hat = r / rho, rho = ||r|| / sqrt(N).  The step's
+# change solves A (m^n - m^{n-1}) = r, so in units of dt rho it is the
+# near-identity local operator (dt A)^{-1} applied to r_hat -- of order one
+# at every timestep, although rho falls by orders of magnitude over the
+# march as the images smooth.  The guess is
+#     x_init = m_i^{n-1} + dt rho * net(...).
 #
-# The two fields enter as two planes each, hi = bf16(m) and lo = 256 (m - hi):
+# The fields enter as two planes each, hi = bf16(v) and lo = 256 (v - hi):
 # one BF16 plane carries 8 significant bits (an absolute 2e-3 at m = 0.5),
 # and the step's change is a difference of neighbouring values a few hundred
 # times smaller than m, so one plane would bury it in rounding; the pair
 # carries about 16 bits and the first layer's products recombine it.
+
+NIN = 10       # input planes of the learned guess
+
 
 def split_hi_lo(m):
     """(hi, lo) with hi = bf16(m), lo = 256 (m - hi); m = hi + lo / 256."""
@@ -150,30 +156,44 @@ def split_hi_lo(m):
     return hi, 256.0 * (m - hi)
 
 
-def network_inputs(mprev, mseed, n, T):
-    """Planes [B][8][N]: m_i^{n-1} (hi, lo), m_seed^n (hi, lo), tau, 1 - tau,
-    sin pi tau, cos pi tau with tau = n / T (n = 1..T)."""
+def step_residual(mprev, g2n, T, H, W):
+    """r = m/dt - A(m~ = m) m per channel (Sec. 2.3, f = 0) and rho =
+    ||r|| / sqrt(N); rows of mprev are channels in the solver order."""
+    from . import oracle as O
+    mprev = np.asarray(mprev, dtype=np.float64)
+    dt, h = 1.0 / T, 1.0 / H
+    r = np.empty_like(mprev)
+    for k in range(mprev.shape[0]):
+        C = O.coeffs(H, W, g2n, dt, h, mprev[k])
+        r[k] = O.rhs(H, W, dt, h, mprev[k]) - O.apply(H, W, C, mprev[k])
+    rho = np.sqrt(np.mean(r * r, axis=1))
+    return r, rho
+
+
+def network_inputs(mprev, mseed, n, T, g2n, H, W):
+    """Planes [B][10][N]: m_i^{n-1} (hi, lo), m_seed^n (hi, lo), tau, 1 - tau,
+    sin pi tau, cos pi tau with tau = n / T (n = 1..T), r_hat (hi, lo); and
+    rho per channel (see step_residual)."""
     mprev = np.asarray(mprev, dtype=np.float64)
     B, N = mprev.shape
     tau = n / T
-    out = np.empty((B, 8, N))
+    r, rho = step_residual(mprev, g2n, T, H, W)
+    rhat = np.where(rho[:, None] > 0, r / np.where(rho > 0, rho, 1.0)[:, None], 0.0)
+    out = np.empty((B, NIN, N))
     out[:, 0], out[:, 1] = split_hi_lo(mprev)
     out[:, 2], out[:, 3] = split_hi_lo(np.asarray(mseed, dtype=np.float64).reshape(B, N))
     for k, v in enumerate((tau, 1.0 - tau, np.sin(np.pi * tau), np.cos(np.pi * tau))):
         out[:, 4 + k] = v
-    return out
-
-
-def guess_scale(T, g2n, H):
-    """s_n = dt (g^n)^2 / h^2 with dt = 1/T, h = 1/H."""
-    return (1.0 / T) * g2n * H * H
+    out[:, 8], out[:, 9] = split_hi_lo(rhat)
+    return out, rho
 
 
 def learned_guess(params, channels, mprev, mseed, n, T, g2n, H, W, operand_round=None):
-    """x_init = m_i^{n-1} + s_n * net([m_i^{n-1}, m_seed^n, time planes]) for a
-    batch of target channels ([B][N] arrays, N = H*W in the solver order)."""
+    """x_init = m_i^{n-1} + dt rho * net([m_i^{n-1}, m_seed^n, time planes,
+    r_hat]) for a batch of target channels ([B][N] arrays, N = H*W in the
+    solver order)."""
     mprev = np.asarray(mprev, dtype=np.float64)
     B, N = mprev.shape
-    x = network_inputs(mprev, mseed, n, T).reshape(B, 8, W, H)
-    d = forward(params, channels, x, operand_round)[-1].reshape(B, N)
-    return mprev + guess_scale(T, g2n, H) * d
+    x, rho = network_inputs(mprev, mseed, n, T, g2n, H, W)
+    d = forward(params, channels, x.reshape(B, NIN, W, H), operand_round)[-1].reshape(B, N)
+    return mprev + (1.0 / T) * rho[:, None] * d

@@ -4,15 +4,15 @@ guess; Sec. 3, Phase 2 applied to the residual of a given guess).
 * Mode 4 (a given guess, judged against the warm start, a kept guess
   projected in residual form) from a guess worse than the warm start is the
   warm start (mode 2) bit for bit, and from a guess better than it (the
-  explicit Euler step) it projects the guess's own residual; mode 5 (the
+  Richardson step) it projects the guess's own residual; mode 5 (the
   guess alone) from x_init = m^{n-1} is the warm start bit for bit.
 * The residual-form projection meets its Galerkin condition with the seed's
   H_a:  V_a^T (r - A_seed (x0 - x_init)) = 0 for r = b - A_i x_init.
-* ``learned_guess``: a one-layer network holding half the five-point pixel
-  Laplacian on the m^{n-1} plane turns the guess into the explicit Euler
-  step m + (s_n / 2) L m of the linear part (s_n = dt g^2 / h^2), computed
-  here with numpy, which leaves about a quarter of the warm start's
-  residual -- half or twice the scale leave about half or more.
+* ``network_inputs``: the residual planes are the step's residual at the
+  image, b - A m^{n-1}, scaled to unit rms (checked against the oracle's
+  operator), and a one-layer network passing them through turns the guess
+  into the Richardson step m + dt (b - A m): the rms scale and the dt
+  factor are pinned by it.
 * A zero network is the warm start: the learned march without projection
   is the warm march, and with projection it reaches the plain trajectory.
 """
@@ -22,34 +22,43 @@ from oracle import cnn_oracle as R
 from paper_2511_17634_gb300 import synth
 
 
-def _laplace_net():
-    # channels (8, 1): tap [di+1][dj+1] multiplies m[i+di, j+dj]; half the
-    # pixel Laplacian on the hi plane and on the lo plane / 256 acts on m
-    L = 0.5 * np.array([[0, 1, 0], [1, -4, 1], [0, 1, 0]], dtype=float)
-    w = np.zeros((1, 8, 3, 3))
-    w[0, 0] = L
-    w[0, 1] = L / 256.0
-    return R.flatten([(w, np.zeros(1))]), (8, 1)
+def _richardson_net():
+    # channels (10, 1): the centre tap passes r_hat (its hi plane, and its lo
+    # plane / 256), so net = r_hat and the guess is m + dt r, one Richardson
+    # step from the warm start
+    w = np.zeros((1, R.NIN, 3, 3))
+    w[0, 8, 1, 1] = 1.0
+    w[0, 9, 1, 1] = 1.0 / 256.0
+    return R.flatten([(w, np.zeros(1))]), (R.NIN, 1)
 
 
-def test_network_inputs_plane_order_and_time_planes():
+def test_network_inputs_planes(orc):
     rng = np.random.default_rng(1)
-    mp, ms = rng.uniform(0, 1, size=(2, 12)), rng.uniform(0, 1, size=(2, 12))
-    x = R.network_inputs(mp, ms, 250, 1000)
-    assert x.shape == (2, 8, 12)
+    H, W, T, n, g2 = 4, 3, 1000, 250, 0.3
+    mp, ms = rng.uniform(0, 1, size=(2, H * W)), rng.uniform(0, 1, size=(2, H * W))
+    x, rho = R.network_inputs(mp, ms, n, T, g2, H, W)
+    assert x.shape == (2, R.NIN, H * W)
     # hi planes are bfloat16 values, hi + lo/256 is the field to ~2^-17
     for k, m in ((0, mp), (2, ms)):
         assert np.array_equal(x[:, k], R.bf16(x[:, k]))
         assert np.abs(x[:, k] - m).max() <= 2.0 ** -8 * np.abs(m).max()
         assert np.abs(R.bf16(x[:, k]) + R.bf16(x[:, k + 1]) / 256 - m).max() <= 2.0 ** -16 * np.abs(m).max()
     # tau = 1/4: tau, 1 - tau, sin(pi/4), cos(pi/4)
-    h = np.sqrt(0.5)
-    assert np.allclose(x[:, 4:, 0], [[0.25, 0.75, h, h]] * 2, atol=1e-15)
-    # the first and the last timestep are told apart on every time plane
-    # but the sine
-    x0, x1 = R.network_inputs(mp, ms, 1, 1000), R.network_inputs(mp, ms, 1000, 1000)
+    hq = np.sqrt(0.5)
+    assert np.allclose(x[:, 4:8, 0], [[0.25, 0.75, hq, hq]] * 2, atol=1e-15)
+    x0, _ = R.network_inputs(mp, ms, 1, T, g2, H, W)
+    x1, _ = R.network_inputs(mp, ms, T, T, g2, H, W)
     assert np.all(np.abs(x0[0, [4, 5, 7], 0] - x1[0, [4, 5, 7], 0]) > 0.99)
-    assert R.guess_scale(1000, 0.02, 32) == 0.02 * 1024 / 1000
+    # the residual planes: the step's operator at timestep n, lagged on m,
+    # applied to m itself, scaled to unit rms
+    dt, h = 1.0 / T, 1.0 / H
+    for k in range(2):
+        C = orc.coeffs(H, W, g2, dt, h, mp[k])
+        r = mp[k] / dt - orc.apply(H, W, C, mp[k])
+        assert abs(rho[k] - np.linalg.norm(r) / np.sqrt(H * W)) <= 1e-12 * rho[k]
+        rh = x[k, 8] + x[k, 9] / 256
+        assert np.allclose(rh, r / rho[k], rtol=0, atol=1e-12)
+        assert abs(np.mean(rh ** 2) - 1.0) <= 1e-12
 
 
 def test_guess_modes_reduce_to_projection_and_warm_start(orc):
@@ -80,9 +89,9 @@ def test_guess_modes_reduce_to_projection_and_warm_start(orc):
 
 
 def test_judge_keeps_a_guess_better_than_the_warm_start(orc):
-    # the explicit Euler step (residual ~1/4 of the warm start's) is kept and
-    # its own residual projected: the x0 residual equals that of the
-    # projection computed here from the seed basis
+    # the Richardson step m + dt r (residual well below the warm start's) is
+    # kept and its own residual projected: the x0 residual equals that of
+    # the projection computed here from the seed basis
     wl = synth.config(2, T=1000, ntargets=2)
     g = wl.groups[0]
     H, W = g.H, g.W
@@ -90,7 +99,7 @@ def test_judge_keeps_a_guess_better_than_the_warm_start(orc):
     dt, h, g2 = 1 / wl.T, 1 / H, float(wl.g2[n])
     ms0 = g.seeds.reshape(len(g.seeds), -1).copy()
     mt0 = g.targets.reshape(len(g.targets), -1).copy()
-    p, ch = _laplace_net()
+    p, ch = _richardson_net()
     xi = R.learned_guess(p, ch, mt0, mt0, n + 1, wl.T, g2, H, W)
     ms, mt = ms0.copy(), mt0.copy()
     st = orc.march_step(H, W, dt, h, g2, ms, mt, g.target_seed, mode=orc.MODE_GUESS_PROJECTED, xinit=xi,
@@ -129,38 +138,35 @@ def test_residual_form_projection_galerkin_condition(orc):
     assert np.abs(gal).max() <= 1e-11 * np.linalg.norm(r)
 
 
-def test_laplacian_network_gives_the_explicit_euler_guess(orc):
+
+
+def test_richardson_network_gives_m_plus_dt_r(orc):
     wl = synth.config(2, T=1000, ntargets=3)
     g = wl.groups[0]
-    H, W, N = g.H, g.W, g.N
+    H, W = g.H, g.W
     n = 1000
     dt, h, g2 = 1 / wl.T, 1 / H, float(wl.g2[n - 1])
     mp = g.targets.reshape(len(g.targets), -1)
-    p, ch = _laplace_net()
+    p, ch = _richardson_net()
     xg = R.learned_guess(p, ch, mp, mp, n, wl.T, g2, H, W)
-    s = dt * g2 / (h * h)
     for k in range(len(mp)):
-        m = mp[k].reshape(W, H)
-        mpad = np.pad(m, 1)
-        lap = mpad[2:, 1:-1] + mpad[:-2, 1:-1] + mpad[1:-1, 2:] + mpad[1:-1, :-2] - 4 * m
-        assert np.allclose(xg[k], (m + 0.5 * s * lap).reshape(-1), rtol=0, atol=1e-13)
-        # the same with the network's BF16 operand rounding: hi + lo/256
-        # keeps the Laplacian to a few 1e-5 of itself (one plane would not)
-        xb = R.learned_guess(p, ch, mp[k:k + 1], mp[k:k + 1], n, wl.T, g2, H, W, operand_round=R.bf16)[0]
-        assert np.abs(xb - xg[k]).max() <= 1e-4 * np.abs(xg[k] - mp[k]).max()
         C = orc.coeffs(H, W, g2, dt, h, mp[k])
         b = orc.rhs(H, W, dt, h, mp[k])
-        res_guess = np.linalg.norm(b - orc.apply(H, W, C, xg[k]))
-        res_warm = np.linalg.norm(b - orc.apply(H, W, C, mp[k]))
-        # ~0.25 at the right scale (the nonlinear term is left); half or
-        # twice the scale leaves ~0.47 and ~1.2 of the warm residual
-        assert res_guess <= 0.35 * res_warm, (k, res_guess / res_warm)
+        r = b - orc.apply(H, W, C, mp[k])
+        assert np.allclose(xg[k], mp[k] + dt * r, rtol=0, atol=1e-13)
+        # the same with the network's BF16 operand rounding: hi + lo/256 of
+        # r_hat keeps the step to a few 1e-5 of itself
+        xb = R.learned_guess(p, ch, mp[k:k + 1], mp[k:k + 1], n, wl.T, g2, H, W, operand_round=R.bf16)[0]
+        assert np.abs(xb - xg[k]).max() <= 1e-4 * np.abs(xg[k] - mp[k]).max()
+        # dt A = I + dt K: the Richardson step leaves -dt K r, a fraction of r
+        res = np.linalg.norm(b - orc.apply(H, W, C, xg[k])) / np.linalg.norm(r)
+        assert res <= 0.35, (k, res)
 
 
 def test_zero_network_learned_march_is_the_warm_march(orc):
     wl = synth.config(1, T=6)
     g = wl.groups[0]
-    ch = (8, 4, 1)
+    ch = (R.NIN, 4, 1)
     p = np.zeros(sum(co * ci * 9 + co for ci, co in zip(ch[:-1], ch[1:])))
     kw = dict(m_seed=30, a=30, m_ref=30, tol_ref=1e-12)
     _, warm, _ = orc.march(g.H, g.W, wl.T, wl.g2, g.seeds, g.targets, g.target_seed,
