@@ -290,27 +290,37 @@ kp_status kp_cnn_forward(kp_cnn* cnn, int B, const float* in, float* out);
  * (device [num_params], may be NULL) and the loss (host, may be NULL). */
 kp_status kp_cnn_gradients(kp_cnn* cnn, int B, const float* in, const float* target,
                            float* grads, double* loss);
-/* Network input of the learned guess for B targets at timestep n, tau = n/T:
- * planes [the target's lagged field m_i^{n-1} (its image carried to timestep
- * n-1) as hi = bf16(m) and lo = bf16(256 (m - hi)), the seed state m_seed^n
- * as hi and lo, tau, 1 - tau, sin pi tau, cos pi tau] into
- * in (device [B][8][H*W] FP32); mprev, seed: host arrays of B device
- * pointers to FP64 planes.  (A field in one BF16 plane keeps 8 significant
- * bits, too few for the step's change; hi and lo keep about 16.) */
+/* Network input of the learned guess for B targets at timestep n (1..T),
+ * tau = n/T, dt = 1/T: planes [the target's lagged field m_i^{n-1} (its image
+ * carried to timestep n-1) as hi = bf16(m) and lo = bf16(256 (m - hi)), the
+ * seed state m_seed^n as hi and lo, tau, 1 - tau, sin pi tau, cos pi tau,
+ * the residual the step leaves at the image, r = m/dt - A(m) m (Sec. 2.3 at
+ * g^2 = g2n, f = 0), divided by rho = ||r|| / sqrt(H W), as hi and lo] into
+ * in (device [B][10][H*W] FP32), and rho into rho (device [B]); mprev,
+ * seed: host arrays of B device pointers to FP64 planes.  (A field in one
+ * BF16 plane keeps 8 significant bits, too few for the step's change; hi and
+ * lo keep about 16.) */
 kp_status kp_cnn_pack_inputs(kp_cnn* cnn, int B, const double* const* mprev, const double* const* seed,
-                             double tau, float* in);
-/* Training target of the learned guess: out_b = (a_b - b_b) * scale, e.g.
- * (m_i^n - m_i^{n-1}) / s_n with s_n = dt (g^n)^2 / h^2, into out (device
- * [B][H*W] FP32); a, b: host arrays of device FP64 planes. */
+                             int n, int T, double g2n, float* in, double* rho);
+/* Training target of the learned guess: out_b = (a_b - b_b) * scale / rho_b
+ * (rho NULL: / 1), e.g. (m_i^n - m_i^{n-1}) / (dt rho_b) with scale = 1/dt,
+ * into out (device [B][H*W] FP32); a, b: host arrays of device FP64 planes;
+ * rho: device [B] or NULL. */
 kp_status kp_cnn_pack_target(kp_cnn* cnn, int B, const double* const* a, const double* const* b,
-                             double scale, float* out);
-/* x_b = base_b + scale * delta_b: the FP64 initial guess m_i^{n-1} + s_n *
- * network output. */
+                             const double* rho, double scale, float* out);
+/* x_b = base_b + scale * rho_b * delta_b (rho NULL: 1): the FP64 initial
+ * guess m_i^{n-1} + dt rho_b * network output with scale = dt. */
 kp_status kp_cnn_add_guess(kp_cnn* cnn, int B, const float* delta, const double* const* base,
-                           double scale, double* const* x);
+                           const double* rho, double scale, double* const* x);
 /* One Adam step (Kingma & Ba 2015) on that loss; t = 1, 2, ... */
 kp_status kp_cnn_train_step(kp_cnn* cnn, int B, const float* in, const float* target, float lr,
                             float beta1, float beta2, float eps, int t, double* loss);
+
+/* Measured FMA throughput of this GPU's FP64 and FP32 pipes in TFLOP/s (2
+ * flops per FMA; eight independent chains per thread, every SM filled, timed
+ * with CUDA events on the context's stream): the denominators of the
+ * solvers' ALU roofline.  Waits for the stream; allocates a few KB. */
+kp_status kp_measure_alu_peaks(kp_ctx* ctx, double* fp64_tflops, double* fp32_tflops);
 
 /* Inspect a stored basis (tests, diagnostics).  a_out, has_next_out, host.
  * V (device, N*(a+1) doubles, column k = v_{k+1}) and Hbar (host, (a+1)*a
@@ -343,8 +353,8 @@ typedef enum {
   KP_MARCH_GALERKIN = 3,    /* exact Galerkin with the target's own operator:
                                x0 = V_a (V_a^T A_i V_a)^{-1} V_a^T b (FP64 plans only)    */
   KP_MARCH_LEARNED = 4,     /* the learned guess projected in residual form: x_init =
-                               m^{n-1} + s_n net(m^{n-1}, m_seed^n, time) (inputs as in
-                               kp_cnn_pack_inputs), x0 = x_init +
+                               m^{n-1} + dt rho net(m^{n-1}, m_seed^n, time, r / rho)
+                               (inputs as in kp_cnn_pack_inputs), x0 = x_init +
                                V_a H_a^{-1} V_a^T (b - A x_init) (mixed precision; needs
                                kp_march_opts.cnn)                                          */
   KP_MARCH_LEARNED_ONLY = 5 /* x0 = x_init, the learned guess alone (for comparison)    */
@@ -418,7 +428,7 @@ typedef struct {
                             states are then not trustworthy) and the context stays
                             usable. */
   int maxit_seed;        /* Arnoldi-step cap of the seed solves; 0 = maxit         */
-  kp_cnn* cnn;           /* KP_MARCH_LEARNED / _ONLY: the network (channels 8 -> ... -> 1,
+  kp_cnn* cnn;           /* KP_MARCH_LEARNED / _ONLY: the network (channels 10 -> ... -> 1,
                             the march's H x W, created on this context); every
                             timestep runs it on all targets in passes of its
                             inference batch (kp_cnn_set_inference_batch) inside the

@@ -175,53 +175,112 @@ __device__ __forceinline__ void split_hi_lo(double m, __nv_bfloat16& hi, __nv_bf
   lo = __float2bfloat16_rn((float)((m - (double)__bfloat162float(hi)) * 256.0));
 }
 
+// The residual the step leaves at the image, r = m/dt - A(m~ = m) m at point
+// p (Sec. 2.3, f = 0, zero outside the grid).  With A m = (1/dt + 4c) m_p +
+// sum over the four neighbours of (-c -+ e (m_+ - m_-)) m_nbr, the 1/dt terms
+// cancel exactly: r = -(4c m_p + sum of the neighbour terms) -- no division,
+// and none of the cancellation of the two large 1/dt terms.  c = g2/(2h^2) =
+// g2 H^2 / 2, e = g2 H^2 / 8.
+__device__ __forceinline__ double step_residual_at(const double* m, int p, int H, int W, double g2) {
+  const double hh = (double)H * (double)H;
+  const double c = 0.5 * g2 * hh, e = 0.125 * g2 * hh;
+  const int i = p / H, j = p - i * H;
+  const double mE = i + 1 < W ? m[p + H] : 0.0, mW = i > 0 ? m[p - H] : 0.0;
+  const double mN = j + 1 < H ? m[p + 1] : 0.0, mS = j > 0 ? m[p - 1] : 0.0;
+  const double dx = mE - mW, dy = mN - mS;
+  double t = 4.0 * c * m[p];
+  t = fma(-c - e * dx, mE, t);
+  t = fma(-c + e * dx, mW, t);
+  t = fma(-c - e * dy, mN, t);
+  t = fma(-c + e * dy, mS, t);
+  return -t;
+}
+
+// rho_b = ||r_b|| / sqrt(P), one block per sample; g2 = g2v, or g2s[*step +
+// step_offset] when g2s is given (the march's schedule and counter)
+__global__ void step_residual_rms_kernel(const double* const* m, int H, int W, double dt, double g2v,
+                                         const double* g2s, const int* step, int step_offset, double* rho) {
+  __shared__ double red[32];
+  const int b = blockIdx.x, P = H * W;
+  const double g2 = g2s ? g2s[*step + step_offset] : g2v;
+  double s = 0.0;
+  for (int p = threadIdx.x; p < P; p += blockDim.x) {
+    const double r = step_residual_at(m[b], p, H, W, g2);
+    s = fma(r, r, s);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    rho[b] = sqrt(t / P);
+  }
+}
+
 // Network input planes of sample b: the target's plane (its lagged field
 // m_i^{n-1} for the learned guess) and the seed state, each as its hi and lo
-// planes, then the time embedding tau, 1 - tau, sin(pi tau), cos(pi tau).
-__global__ void pack_inputs_kernel(const double* const* img, const double* const* seed, float tau, float* in,
-                                   int P) {
-  const int b = blockIdx.y;
+// planes, the time embedding tau, 1 - tau, sin(pi tau), cos(pi tau), and the
+// step's residual at the target's plane scaled to unit rms (hi, lo).
+__global__ void pack_inputs_kernel(const double* const* img, const double* const* seed, float tau, double dt,
+                                   double g2, const double* rho, int H, int W, float* in) {
+  const int b = blockIdx.y, P = H * W;
   const float e[4] = {tau, 1.f - tau, sinpif(tau), cospif(tau)};
-  float* o = in + (size_t)b * 8 * P;
+  const double ir = rho[b] > 0.0 ? 1.0 / rho[b] : 0.0;
+  float* o = in + (size_t)b * 10 * P;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
-    __nv_bfloat16 h0, l0, h1, l1;
+    __nv_bfloat16 h0, l0, h1, l1, h2, l2;
     split_hi_lo(img[b][p], h0, l0);
     split_hi_lo(seed[b][p], h1, l1);
+    split_hi_lo(step_residual_at(img[b], p, H, W, g2) * ir, h2, l2);
     o[p] = __bfloat162float(h0);
     o[P + p] = __bfloat162float(l0);
     o[2 * P + p] = __bfloat162float(h1);
     o[3 * P + p] = __bfloat162float(l1);
 #pragma unroll
     for (int k = 0; k < 4; ++k) o[(4 + k) * P + p] = e[k];
+    o[8 * P + p] = __bfloat162float(h2);
+    o[9 * P + p] = __bfloat162float(l2);
   }
 }
 
-// out_b = (a_b - b_b) * scale in FP32 (training targets (m_i^n - m_i^{n-1}) / s_n)
-__global__ void diff_kernel(const double* const* a, const double* const* bb, double scale, float* out, int P) {
+// out_b = (a_b - b_b) * scale / rho_b in FP32 (training targets
+// (m_i^n - m_i^{n-1}) / (dt rho_b); rho NULL = 1)
+__global__ void diff_kernel(const double* const* a, const double* const* bb, const double* rho, double scale,
+                            float* out, int P) {
   const int b = blockIdx.y;
+  const double s = rho ? (rho[b] > 0.0 ? scale / rho[b] : 0.0) : scale;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
-    out[(size_t)b * P + p] = (float)((a[b][p] - bb[b][p]) * scale);
+    out[(size_t)b * P + p] = (float)((a[b][p] - bb[b][p]) * s);
 }
 
-// x_b = base_b + scale * delta_b (FP64 initial guess from the network's output)
-__global__ void add_guess_kernel(const float* delta, const double* const* base, double scale, double* const* x,
-                                 int P) {
+// x_b = base_b + scale * rho_b * delta_b (FP64 initial guess from the
+// network's output; rho NULL = 1)
+__global__ void add_guess_kernel(const float* delta, const double* const* base, const double* rho, double scale,
+                                 double* const* x, int P) {
   const int b = blockIdx.y;
+  const double s = rho ? scale * rho[b] : scale;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
-    x[b][p] = base[b][p] + scale * (double)delta[(size_t)b * P + p];
+    x[b][p] = base[b][p] + s * (double)delta[(size_t)b * P + p];
 }
 
 // The learned guess inside the time march, for the target timestep n = *step
-// + step_offset + 1 (1-based), tau = n / T: the eight input planes of sample b
+// + step_offset + 1 (1-based), tau = n / T: the ten input planes of sample b
 // -- m_i^{n-1} (hi, lo), m_seed^n (hi, lo), tau, 1 - tau, sin pi tau,
-// cos pi tau -- straight into the padded BF16 rows of the first convolution
-// (chunk 0; chunk 1, channels 8..15, is written as zeros)
+// cos pi tau, the step's residual scaled by 1 / rho_b (hi, lo) -- straight
+// into the padded BF16 rows of the first convolution (chunk 0: channels
+// 0..7; chunk 1: 8, 9 and zeros)
 __global__ void march_pack_kernel(const double* const* mprev, const double* const* mseed, const int* step,
-                                  int step_offset, int T, int H, int W, int halo, int Rp, __nv_bfloat16* out) {
+                                  int step_offset, const double* g2s, const double* rho, int T, int H, int W,
+                                  int halo, int Rp, __nv_bfloat16* out) {
   const int b = blockIdx.y;
   const int P = H * W;
-  const float tau = (float)(*step + step_offset + 1) / (float)T;
+  const int t = *step + step_offset;
+  const float tau = (float)(t + 1) / (float)T;
   const float e[4] = {tau, 1.f - tau, sinpif(tau), cospif(tau)};
+  const double g2 = g2s[t];
+  const double ir = rho[b] > 0.0 ? 1.0 / rho[b] : 0.0;
   const double* mp = mprev[b];
   const double* ms = mseed[b];
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
@@ -234,17 +293,19 @@ __global__ void march_pack_kernel(const double* const* mprev, const double* cons
     __nv_bfloat162 h2 = __floats2bfloat162_rn(e[2], e[3]);
     const uint4 c0 = make_uint4(*reinterpret_cast<uint32_t*>(&f0), *reinterpret_cast<uint32_t*>(&f1),
                                 *reinterpret_cast<uint32_t*>(&h1), *reinterpret_cast<uint32_t*>(&h2));
+    __nv_bfloat162 f2;
+    split_hi_lo(step_residual_at(mp, p, H, W, g2) * ir, f2.x, f2.y);
     *reinterpret_cast<uint4*>(out + (((size_t)b * 2 + 0) * Rp + row) * 8) = c0;
-    *reinterpret_cast<uint4*>(out + (((size_t)b * 2 + 1) * Rp + row) * 8) = make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(out + (((size_t)b * 2 + 1) * Rp + row) * 8) =
+        make_uint4(*reinterpret_cast<uint32_t*>(&f2), 0u, 0u, 0u);
   }
 }
 
-// x_b = m_i^{n-1} + s_n * delta_b with s_n = dt (g^n)^2 / h^2 = g2[n-1] H^2 / T
+// x_b = m_i^{n-1} + dt rho_b * delta_b
 __global__ void march_guess_kernel(const float* delta, const double* const* mprev, double* const* x,
-                                   const int* step, int step_offset, const double* g2, int T, int H, int P) {
+                                   const double* rho, int T, int P) {
   const int b = blockIdx.y;
-  const int t = *step + step_offset;
-  const double s = g2[t] * (double)H * (double)H / (double)T;
+  const double s = rho[b] / (double)T;
   const double* mp = mprev[b];
   double* xb = x[b];
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
@@ -290,6 +351,7 @@ struct kp_cnn {
   std::vector<int> cic, nout;
   int infB = 0;                                 // images the inference buffers hold
   float* dout = nullptr;                        // [infB][P] network output (march guesses)
+  double* rho = nullptr;                        // [max(infB, maxB)] rms of each sample's step residual
 };
 
 namespace {
@@ -390,9 +452,10 @@ kp_status forward_fused(kp_cnn* n, int B, const float* in, float* out) {
 // (Re)allocate the implicit-GEMM inference buffers for B images, zeroed (the
 // padding rows are never written afterwards).
 cudaError_t alloc_inference(kp_cnn* n, int B) {
-  cudaFree(n->pin); cudaFree(n->px[0]); cudaFree(n->px[1]); cudaFree(n->dout);
+  cudaFree(n->pin); cudaFree(n->px[0]); cudaFree(n->px[1]); cudaFree(n->dout); cudaFree(n->rho);
   n->pin = n->px[0] = n->px[1] = nullptr;
   n->dout = nullptr;
+  n->rho = nullptr;
   n->infB = 0;
   const size_t rows = (size_t)B * n->geo.Rp * 8;
   cudaError_t e = cudaMalloc((void**)&n->pin, 2 * rows * sizeof(__nv_bfloat16));
@@ -402,6 +465,7 @@ cudaError_t alloc_inference(kp_cnn* n, int B) {
     if (e == cudaSuccess) e = cudaMemset(n->px[k], 0, 4 * rows * sizeof(__nv_bfloat16));
   }
   if (e == cudaSuccess) e = cudaMalloc((void**)&n->dout, (size_t)B * n->P * sizeof(float));
+  if (e == cudaSuccess) e = cudaMalloc((void**)&n->rho, (size_t)std::max(B, n->maxB) * sizeof(double));
   if (e == cudaSuccess) n->infB = B;
   return e;
 }
@@ -474,6 +538,7 @@ kp_status kp_cnn_destroy(kp_cnn* n) {
   cudaFree(n->act); cudaFree(n->dz); cudaFree(n->dz2); cudaFree(n->col); cudaFree(n->colT); cudaFree(n->rows);
   cudaFree(n->cm); cudaFree(n->tiles); cudaFree(n->d_loss); cudaFree(n->d_err);
   cudaFree(n->pin); cudaFree(n->px[0]); cudaFree(n->px[1]); cudaFree(n->wf); cudaFree(n->dout);
+  cudaFree(n->rho);
   delete n;
   return KP_OK;
 }
@@ -600,25 +665,29 @@ kp_status kp_cnn_gradients(kp_cnn* n, int B, const float* in, const float* targe
   return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN gradients");
 }
 
-kp_status kp_cnn_pack_inputs(kp_cnn* n, int B, const double* const* img, const double* const* seed,
-                             double tau, float* in) {
-  if (!n || B < 1 || !img || !seed || !in) return n ? kp::set_error(n->ctx, KP_ERR_ARG, "CNN pack: bad arguments") : KP_ERR_ARG;
-  if (n->ch[0] != 8) return kp::set_error(n->ctx, KP_ERR_UNSUPPORTED, "CNN pack: the network needs 8 input planes");
+kp_status kp_cnn_pack_inputs(kp_cnn* n, int B, const double* const* img, const double* const* seed, int step,
+                             int T, double g2n, float* in, double* rho) {
+  if (!n || B < 1 || !img || !seed || !in || !rho || T < 1 || step < 1 || step > T || !(g2n >= 0.0))
+    return n ? kp::set_error(n->ctx, KP_ERR_ARG, "CNN pack: bad arguments") : KP_ERR_ARG;
+  if (n->ch[0] != 10) return kp::set_error(n->ctx, KP_ERR_UNSUPPORTED, "CNN pack: the network needs 10 input planes");
   std::vector<const double*> h(2 * (size_t)B);
   for (int b = 0; b < B; ++b) { h[b] = img[b]; h[B + b] = seed[b]; }
   const double** d = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&d, h.size() * sizeof(double*), n->ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double*), cudaMemcpyHostToDevice, n->ctx->stream);
   if (e == cudaSuccess) {
-    pack_inputs_kernel<<<dim3(grid_for(n->P), B), 256, 0, n->ctx->stream>>>(d, d + B, (float)tau, in, n->P);
+    const double dt = 1.0 / T;
+    step_residual_rms_kernel<<<B, 256, 0, n->ctx->stream>>>(d, n->H, n->W, dt, g2n, nullptr, nullptr, 0, rho);
+    pack_inputs_kernel<<<dim3(grid_for(n->P), B), 256, 0, n->ctx->stream>>>(d, d + B, (float)step / (float)T, dt,
+                                                                           g2n, rho, n->H, n->W, in);
     e = cudaGetLastError();
   }
   if (d) cudaFreeAsync(d, n->ctx->stream);
   return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN pack");
 }
 
-kp_status kp_cnn_add_guess(kp_cnn* n, int B, const float* delta, const double* const* base, double scale,
-                           double* const* x) {
+kp_status kp_cnn_add_guess(kp_cnn* n, int B, const float* delta, const double* const* base, const double* rho,
+                           double scale, double* const* x) {
   if (!n || B < 1 || !delta || !base || !x) return n ? kp::set_error(n->ctx, KP_ERR_ARG, "CNN guess: bad arguments") : KP_ERR_ARG;
   std::vector<const double*> h(2 * (size_t)B);
   for (int b = 0; b < B; ++b) { h[b] = base[b]; h[B + b] = x[b]; }
@@ -626,7 +695,7 @@ kp_status kp_cnn_add_guess(kp_cnn* n, int B, const float* delta, const double* c
   cudaError_t e = cudaMallocAsync((void**)&d, h.size() * sizeof(double*), n->ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double*), cudaMemcpyHostToDevice, n->ctx->stream);
   if (e == cudaSuccess) {
-    add_guess_kernel<<<dim3(grid_for(n->P), B), 256, 0, n->ctx->stream>>>(delta, d, scale,
+    add_guess_kernel<<<dim3(grid_for(n->P), B), 256, 0, n->ctx->stream>>>(delta, d, rho, scale,
                                                                          const_cast<double* const*>(d + B), n->P);
     e = cudaGetLastError();
   }
@@ -634,8 +703,8 @@ kp_status kp_cnn_add_guess(kp_cnn* n, int B, const float* delta, const double* c
   return e == cudaSuccess ? KP_OK : kp::cuda_error(n->ctx, e, "CNN guess");
 }
 
-kp_status kp_cnn_pack_target(kp_cnn* n, int B, const double* const* a, const double* const* b, double scale,
-                             float* out) {
+kp_status kp_cnn_pack_target(kp_cnn* n, int B, const double* const* a, const double* const* b, const double* rho,
+                             double scale, float* out) {
   if (!n || B < 1 || !a || !b || !out) return n ? kp::set_error(n->ctx, KP_ERR_ARG, "CNN target: bad arguments") : KP_ERR_ARG;
   std::vector<const double*> h(2 * (size_t)B);
   for (int k = 0; k < B; ++k) { h[k] = a[k]; h[B + k] = b[k]; }
@@ -643,7 +712,7 @@ kp_status kp_cnn_pack_target(kp_cnn* n, int B, const double* const* a, const dou
   cudaError_t e = cudaMallocAsync((void**)&d, h.size() * sizeof(double*), n->ctx->stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double*), cudaMemcpyHostToDevice, n->ctx->stream);
   if (e == cudaSuccess) {
-    diff_kernel<<<dim3(grid_for(n->P), B), 256, 0, n->ctx->stream>>>(d, d + B, scale, out, n->P);
+    diff_kernel<<<dim3(grid_for(n->P), B), 256, 0, n->ctx->stream>>>(d, d + B, rho, scale, out, n->P);
     e = cudaGetLastError();
   }
   if (d) cudaFreeAsync(d, n->ctx->stream);
@@ -668,7 +737,7 @@ kp_status kp_cnn_train_step(kp_cnn* n, int B, const float* in, const float* targ
 namespace kp {
 
 bool cnn_march_ready(const kp_cnn* n, int H, int W) {
-  return n && n->fused && n->H == H && n->W == W && n->ch[0] == 8 && n->ch[n->L] == 1 && n->infB > 0;
+  return n && n->fused && n->H == H && n->W == W && n->ch[0] == 10 && n->ch[n->L] == 1 && n->infB > 0;
 }
 
 int cnn_inference_batch(const kp_cnn* n) { return n ? n->infB : 0; }
@@ -678,12 +747,13 @@ cudaError_t cnn_enqueue_guess(kp_cnn* n, int B, const double* const* mprev, cons
                               cudaStream_t st) {
   if (B < 1 || B > n->infB) return cudaErrorInvalidValue;
   const dim3 grid(std::min((n->P + 255) / 256, 1024), B);
-  march_pack_kernel<<<grid, 256, 0, st>>>(mprev, mseed, step, step_offset, T, n->H, n->W, n->geo.halo, n->geo.Rp,
-                                          n->pin);
+  step_residual_rms_kernel<<<B, 256, 0, st>>>(mprev, n->H, n->W, 1.0 / T, 0.0, g2, step, step_offset, n->rho);
+  march_pack_kernel<<<grid, 256, 0, st>>>(mprev, mseed, step, step_offset, g2, n->rho, T, n->H, n->W, n->geo.halo,
+                                          n->geo.Rp, n->pin);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = conv_layers(n, B, n->dout, st);
   if (e == cudaSuccess) {
-    march_guess_kernel<<<grid, 256, 0, st>>>(n->dout, mprev, x, step, step_offset, g2, T, n->H, n->P);
+    march_guess_kernel<<<grid, 256, 0, st>>>(n->dout, mprev, x, n->rho, T, n->P);
     e = cudaGetLastError();
   }
   return e;

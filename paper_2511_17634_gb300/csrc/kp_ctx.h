@@ -92,9 +92,9 @@ inline double inner_eta(const kp_options& o) {
 cudaError_t launch_solver(const GmresParams& p, const Shape& sh, bool mixed, cudaStream_t st);
 
 // Learned initial guess inside the time march (kp_cnn.cu): whether the
-// network can serve an H x W march (8 inputs, 1 output, implicit-GEMM
+// network can serve an H x W march (10 inputs, 1 output, implicit-GEMM
 // inference buffers), how many images one pass holds, and the enqueue of
-// x[b] = mprev[b] + s_n * net(mprev[b], mseed[b], time planes) for B targets
+// x[b] = mprev[b] + dt rho_b net(mprev[b], mseed[b], time planes, r_hat) for B targets
 // (device pointer tables; timestep from the device counter).
 bool cnn_march_ready(const kp_cnn* n, int H, int W);
 int cnn_inference_batch(const kp_cnn* n);

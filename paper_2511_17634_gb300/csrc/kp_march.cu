@@ -257,7 +257,7 @@ cudaError_t enqueue_guess(kp_march_plan* P, int par, int* nl) {
   for (int c0 = 0; c0 < P->nt && e == cudaSuccess; c0 += B) {
     e = kp::cnn_enqueue_guess(P->cnn, std::min(B, P->nt - c0), P->lg_prev[par] + c0, P->lg_seed[par] + c0,
                               P->lg_x[par] + c0, P->step, 0, P->g2, P->opt.T, P->st);
-    *nl += 2 + 4;                            // pack, four layers, x_init (a four-layer network)
+    *nl += 3 + 4;                            // residual rms, pack, four layers, x_init (four layers)
   }
   return e;
 }
@@ -504,7 +504,7 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
     }
     if (!kp::cnn_march_ready(o.cnn, groups[0].H, groups[0].W)) {
       kp_march_destroy(P);
-      return kp::set_error(c, KP_ERR_ARG, "learned march: needs a %dx%d network with 8 inputs, 1 output "
+      return kp::set_error(c, KP_ERR_ARG, "learned march: needs a %dx%d network with 10 inputs, 1 output "
                            "and an inference batch", groups[0].H, groups[0].W);
     }
     P->cnn = o.cnn;

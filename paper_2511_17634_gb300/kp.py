@@ -70,6 +70,7 @@ def lib():
         L.kp_basis_get.argtypes = [vp, i, i, ctypes.POINTER(i), ctypes.POINTER(i), vp, vp]
         L.kp_project_gemm_bf16.argtypes = [vp, i, i, i, vp, i, vp, i, vp, i]
         L.kp_residual.argtypes = [vp, i, vp, vp, vp, vp]
+        L.kp_measure_alu_peaks.argtypes = [vp, ctypes.POINTER(d), ctypes.POINTER(d)]
         f32 = ctypes.c_float
         L.kp_cnn_create.argtypes = [vp, i, i, i, i, vp, ctypes.POINTER(vp)]
         L.kp_cnn_destroy.argtypes = [vp]
@@ -79,13 +80,13 @@ def lib():
         L.kp_cnn_forward.argtypes = [vp, i, vp, vp]
         L.kp_cnn_gradients.argtypes = [vp, i, vp, vp, vp, vp]
         L.kp_cnn_train_step.argtypes = [vp, i, vp, vp, f32, f32, f32, f32, i, vp]
-        L.kp_cnn_pack_inputs.argtypes = [vp, i, vp, vp, d, vp]
-        L.kp_cnn_add_guess.argtypes = [vp, i, vp, vp, d, vp]
-        L.kp_cnn_pack_target.argtypes = [vp, i, vp, vp, d, vp]
+        L.kp_cnn_pack_inputs.argtypes = [vp, i, vp, vp, i, i, d, vp, vp]
+        L.kp_cnn_add_guess.argtypes = [vp, i, vp, vp, vp, d, vp]
+        L.kp_cnn_pack_target.argtypes = [vp, i, vp, vp, vp, d, vp]
         L.kp_cnn_set_inference_batch.argtypes = [vp, i]
         for f in ("kp_create", "kp_destroy", "kp_set_stream", "kp_apply", "kp_rhs", "kp_seed_solve",
                   "kp_refine", "kp_store_basis", "kp_project_targets", "kp_project_targets_multi",
-                  "kp_basis_get", "kp_project_gemm_bf16", "kp_residual", "kp_cnn_create",
+                  "kp_basis_get", "kp_project_gemm_bf16", "kp_residual", "kp_measure_alu_peaks", "kp_cnn_create",
                   "kp_cnn_destroy", "kp_cnn_num_params", "kp_cnn_set_params", "kp_cnn_get_params",
                   "kp_cnn_forward", "kp_cnn_gradients", "kp_cnn_train_step", "kp_cnn_pack_inputs",
                   "kp_cnn_add_guess", "kp_cnn_pack_target", "kp_cnn_set_inference_batch"):
@@ -241,6 +242,12 @@ class Context:
         self._check(lib().kp_project_targets_multi(self._h, timestep, len(ops), self._arr(ids),
                                                    self._arr(ops), self._arr(ptrs(r)),
                                                    self._arr(ptrs(x))))
+
+    def measure_alu_peaks(self):
+        """(FP64, FP32) FMA throughput of this GPU in TFLOP/s, measured."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._check(lib().kp_measure_alu_peaks(self._h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def residual(self, ops, b, x, r):
         """r = b - A x (FP64)."""
@@ -446,26 +453,33 @@ class CNN:
             ctypes.c_void_p(grads.data_ptr()) if grads is not None else None, ctypes.byref(loss)))
         return loss.value
 
-    def pack_inputs(self, mprev, seed, tau, out):
-        """out [B][6][H*W] float32 from FP64 lagged-field and seed-state planes (rows or lists)."""
+    def pack_inputs(self, mprev, seed, n, T, g2n, out, rho):
+        """out [B][10][H*W] float32 from FP64 lagged-field and seed-state planes
+        (rows or lists) at timestep n of T with (g^n)^2 = g2n; rho (CUDA
+        float64 [B]) receives each sample's step-residual rms."""
         pi, ps = ptrs(mprev), ptrs(seed)
         self.ctx._check(lib().kp_cnn_pack_inputs(self._h, len(pi), pi.ctypes.data_as(ctypes.c_void_p),
-                                                 ps.ctypes.data_as(ctypes.c_void_p), float(tau),
-                                                 ctypes.c_void_p(out.data_ptr())))
+                                                 ps.ctypes.data_as(ctypes.c_void_p), int(n), int(T),
+                                                 float(g2n), ctypes.c_void_p(out.data_ptr()),
+                                                 ctypes.c_void_p(rho.data_ptr())))
 
-    def pack_target(self, a, b, out, scale=1.0):
-        """out [B][1][H*W] float32 = (a - b) * scale (FP64 planes)."""
+    def pack_target(self, a, b, out, scale=1.0, rho=None):
+        """out [B][1][H*W] float32 = (a - b) * scale / rho_b (FP64 planes; rho
+        CUDA float64 [B] or None)."""
         pa, pb = ptrs(a), ptrs(b)
         self.ctx._check(lib().kp_cnn_pack_target(self._h, len(pa), pa.ctypes.data_as(ctypes.c_void_p),
-                                                 pb.ctypes.data_as(ctypes.c_void_p), float(scale),
-                                                 ctypes.c_void_p(out.data_ptr())))
+                                                 pb.ctypes.data_as(ctypes.c_void_p),
+                                                 ctypes.c_void_p(rho.data_ptr()) if rho is not None else None,
+                                                 float(scale), ctypes.c_void_p(out.data_ptr())))
 
-    def add_guess(self, delta, base, x, scale=1.0):
-        """x = base + scale * delta (FP64 planes; delta float32 [B][1][H*W])."""
+    def add_guess(self, delta, base, x, scale=1.0, rho=None):
+        """x = base + scale * rho_b * delta (FP64 planes; delta float32
+        [B][1][H*W]; rho CUDA float64 [B] or None)."""
         pb, px = ptrs(base), ptrs(x)
         self.ctx._check(lib().kp_cnn_add_guess(self._h, len(pb), ctypes.c_void_p(delta.data_ptr()),
-                                               pb.ctypes.data_as(ctypes.c_void_p), float(scale),
-                                               px.ctypes.data_as(ctypes.c_void_p)))
+                                               pb.ctypes.data_as(ctypes.c_void_p),
+                                               ctypes.c_void_p(rho.data_ptr()) if rho is not None else None,
+                                               float(scale), px.ctypes.data_as(ctypes.c_void_p)))
 
     def train_step(self, x, target, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8):
         loss = ctypes.c_double()

@@ -1,21 +1,24 @@
 """Learned initial guess for the target solves (not in the paper).
 
 A small 3x3 convolutional network (kp.CNN, trained with the library's own
-tensor-core kernels) maps [m_i^{n-1}, m_seed^n, time embedding] -- the
-target's image as the march has carried it to timestep n-1, the seed's
-solution of timestep n (each as a hi and a lo BF16 plane), and tau = n/T,
-1 - tau, sin(pi tau), cos(pi tau) -- to the step's
-change in units of s_n = dt (g^n)^2 / h^2, the coefficient of the pixel
-Laplacian in the implicit step.  The target's initial guess is
+tensor-core kernels) maps [m_i^{n-1}, m_seed^n, time embedding, r_hat] --
+the target's image as the march has carried it to timestep n-1, the seed's
+solution of timestep n, tau = n/T, 1 - tau, sin(pi tau), cos(pi tau), and
+the residual the step leaves at the image, r = m^{n-1}/dt - A m^{n-1}, over
+its rms rho (the fields each as a hi and a lo BF16 plane) -- to the step's
+change in units of dt rho.  The step's change solves A (m^n - m^{n-1}) = r,
+so in those units it is the near-identity operator (dt A)^{-1} applied to
+r_hat, of order one at every timestep although rho falls by orders of
+magnitude as the images smooth.  The target's initial guess is
 
-    x_init = m_i^{n-1} + s_n * net(...),
+    x_init = m_i^{n-1} + dt rho * net(...),
 
-projected in residual form onto the seed's Krylov basis (x0 = x_init +
-V_a H_a^{-1} V_a^T (b - A x_init), Sec. 3 Phase 2) and refined by GMRES to
-the same tolerance as every other solve, so the network changes the cost of
-a solve, never its accuracy.  In the time march (kp.MARCH_LEARNED) packing,
-inference, the guess, the projection and the refine all run on the GPU
-inside the march's per-timestep graph.
+judged against the warm start m_i^{n-1} by FP64 residual norm, projected in
+residual form onto the seed's Krylov basis when kept (x0 = x_init + V_a
+H_a^{-1} V_a^T (b - A x_init), Sec. 3 Phase 2), and refined by GMRES to the
+same tolerance as every other solve, so the network changes the cost of a
+solve, never its accuracy.  In the time march (kp.MARCH_LEARNED) all of it
+runs on the GPU inside the march's per-timestep graph.
 
 Host orchestration only (pair generation, the training loop, timing of the
 march modes): every arithmetic step runs in the CUDA library.
@@ -26,12 +29,7 @@ import numpy as np
 
 from . import kp
 
-CHANNELS = (8, 32, 32, 32, 1)
-
-
-def guess_scale(T, g2n, H):
-    """s_n = dt (g^n)^2 / h^2 with dt = 1/T, h = 1/H."""
-    return float(g2n) * H * H / T
+CHANNELS = (10, 32, 32, 32, 1)
 
 
 def init_params(seed=0, channels=CHANNELS):
@@ -52,9 +50,10 @@ def generate_pairs(ctx, net, group, T, g2, steps, every, tol_seed=1e-10, tol=1e-
                    mode=kp.MARCH_PROJECTED):
     """Run the method (a march of the group's seeds and targets) over
     `steps` timesteps and, at every `every`-th timestep n, record the network
-    input [m_i^{n-1} (hi, lo), m_seed^n (hi, lo), time planes] and the
-    training target (m_i^n - m_i^{n-1}) / s_n of every target channel.
-    Returns float32 CUDA tensors (inputs [pairs][8][P], targets [pairs][1][P])."""
+    input [m_i^{n-1} (hi, lo), m_seed^n (hi, lo), time planes, r_hat (hi, lo)]
+    and the training target (m_i^n - m_i^{n-1}) / (dt rho) of every target
+    channel.  Returns float32 CUDA tensors (inputs [pairs][10][P], targets
+    [pairs][1][P])."""
     import torch
     H, W = group.H, group.W
     P = H * W
@@ -72,10 +71,11 @@ def generate_pairs(ctx, net, group, T, g2, steps, every, tol_seed=1e-10, tol=1e-
         plan.run(n - 1, 1)
         done = n
         seed_rows = [s[int(k)] for k in group.target_seed]
-        x = torch.empty((nt, 8, P), dtype=torch.float32, device=dev)
+        x = torch.empty((nt, CHANNELS[0], P), dtype=torch.float32, device=dev)
         y = torch.empty((nt, 1, P), dtype=torch.float32, device=dev)
-        net.pack_inputs(prev, seed_rows, n / T, x)
-        net.pack_target(t, prev, y, scale=1.0 / guess_scale(T, g2[n - 1], H))
+        rho = torch.empty(nt, dtype=torch.float64, device=dev)
+        net.pack_inputs(prev, seed_rows, n, T, float(g2[n - 1]), x, rho)
+        net.pack_target(t, prev, y, scale=float(T), rho=rho)        # (m^n - m^{n-1}) / (dt rho)
         ins.append(x)
         outs.append(y)
     plan.close()
