@@ -33,8 +33,20 @@ sys.path.insert(0, ROOT)
 
 from paper_2511_17634_gb300 import synth  # noqa: E402
 
-FP64_PEAK_TFLOPS = 152 * 2070e6 * 4 / 1e12   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 2070e6 * 256 / 1e12  # 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz
+# ALU roofline denominators: measured on the GPU by kp_measure_alu_peaks at the
+# start of a run (set_alu_peaks); these derived figures (152 SMs x 2 FP64 /
+# 128 FP32 FMA per clock x 2 flop x 2.07 GHz) stand in only until then
+FP64_PEAK_TFLOPS = 152 * 2070e6 * 4 / 1e12
+FP32_PEAK_TFLOPS = 152 * 2070e6 * 256 / 1e12
+ALU_PEAK_SOURCE = "derived: 152 SM x 2 FP64 / 128 FP32 FMA/clk x 2.07 GHz"
+
+
+def set_alu_peaks(ctx):
+    """Measure the FP64 and FP32 FMA peaks on this GPU (kp_measure_alu_peaks)."""
+    global FP64_PEAK_TFLOPS, FP32_PEAK_TFLOPS, ALU_PEAK_SOURCE
+    FP64_PEAK_TFLOPS, FP32_PEAK_TFLOPS = ctx.measure_alu_peaks()
+    ALU_PEAK_SOURCE = ("measured at the start of this run: FMA chains on every SM "
+                       "(kp_measure_alu_peaks), FP64 and FP32")
 
 
 def _measured_peak(key, fallback):
@@ -459,6 +471,8 @@ def run_north_star(args):
     ns_planes = wl0.n_seed_planes
     ctx = kp.Context(max_seeds=2 * ns_planes, max_a=wl0.a, max_n=wl0.groups[0].N, precision=kp.PREC_MIXED,
                      inner_digits=args.inner_digits)
+    if ALU_PEAK_SOURCE.startswith("derived"):
+        set_alu_peaks(ctx)
     wl, g, net, train_info = learned_setup(kp, ctx, args, rank)
     H, W, T = g.H, g.W, wl.T
     nt = g.targets.shape[0]
@@ -628,8 +642,7 @@ def run_north_star(args):
                    "unit": "TFLOP/s (FP64 + FP32 x FP64/FP32 peak ratio)", "frac": sol_eq / FP64_PEAK_TFLOPS,
                    "traffic": None, "kernel": "gmres_cluster_kernel (targets: judge, projection, refine)",
                    "fp64_tflops": sol_tf64, "fp32_tflops": sol_tf32,
-                   "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz; FP32: 152 SM x 128 FMA/clk x "
-                                  "2.07 GHz"}
+                   "peak_source": ALU_PEAK_SOURCE, "peak_fp32": FP32_PEAK_TFLOPS}
     cnn_peak = BF16_SUSTAINED_TFLOPS
     cnn_roof = {"bound": "tensor", "achieved": cnn_tf, "peak": cnn_peak, "unit": "TFLOP/s",
                 "frac": cnn_tf / cnn_peak, "traffic": None,
@@ -743,6 +756,8 @@ def bench_small(args, dist, init=False):
                      block_threads=args.block_threads, reorth=args.reorth,
                      smem_vectors=args.smem_vectors, blocks_per_sm=args.blocks_per_sm,
                      cluster_size=args.cluster_size)
+    if ALU_PEAK_SOURCE.startswith("derived"):
+        set_alu_peaks(ctx)
     dev = torch.device("cuda", torch.cuda.current_device())
     img_s = [torch.as_tensor(g.seeds.reshape(len(g.seeds), -1), device=dev) for g in wl.groups]
     img_t = [torch.as_tensor(g.targets.reshape(len(g.targets), -1), device=dev) for g in wl.groups]
@@ -986,8 +1001,7 @@ def bench_small(args, dist, init=False):
                                           if captured else "no ncu capture of this workload and shape"),
                          "kernel": ("gmres_mixed_kernel" if mixed else "gmres_fp64_kernel")
                                    + " (targets: projection + refine)",
-                         "peak_source": "derived: 152 SM x 2 FP64 FMA/clk x 2.07 GHz"
-                                        + ("; FP32: 152 SM x 128 FMA/clk x 2.07 GHz" if mixed else "")},
+                         "peak_source": ALU_PEAK_SOURCE, "peak_fp32": FP32_PEAK_TFLOPS},
             # HBM bytes the method cannot avoid per target system: read m^{n-1}
             # (it is both b and m~), write m^n, plus its share of the seed basis
             # read (a vectors over the targets of a seed); s = bytes per value

@@ -15,7 +15,7 @@
 //
 //   Z[r][co] = bias[co] + sum_t sum_c X[r + off(t)][c] W[co][c][t]
 //
-// One CTA (persistent) processes super tiles of 4 x 128 padded rows: a
+// One CTA (persistent) processes super tiles of 8 x 128 padded rows: a
 // producer thread stages the input rows of a super tile plus halos with bulk
 // copies (cp.async.bulk, two stages), one thread issues 9 taps x (C_in / 16)
 // MMAs (M = 128 rows, N = 16 or 32 output channels, K = 16) per 128-row tile
@@ -32,7 +32,8 @@
 namespace kp {
 namespace {
 
-constexpr int kMT = 4;                  // 128-row tiles per super tile
+constexpr int kMT = 8;                  // 128-row tiles per super tile (input window re-read
+                                        // factor (1024 + 2 halo) / 1024 = 1.26 at 128x128)
 constexpr int kConvThreads = 192;       // warps 0-3 epilogue, 4 producer, 5 MMA issuer
 constexpr long long kConvSpin = 1ll << 26;
 
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3x3_tc_kernel(const ConvA
   uint64_t* tempty = bars + 4;    // [2] epilogue finished reading a TMEM buffer
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 6);
   volatile int* abort = reinterpret_cast<volatile int*>(bars + 7);
-  constexpr uint32_t kCols = 2 * kMT * NOUT;   // 256 or 128 TMEM columns
+  constexpr uint32_t kCols = 2 * kMT * NOUT;   // 512 or 256 TMEM columns
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int total = a.B * a.nst;
 
