@@ -317,6 +317,240 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3x3_tc_kernel(const ConvA
   }
 }
 
+// ---------------------------------------------------------------------------
+// Column-aligned variant for 64 < H <= 128: one 128-row tile is the pixel
+// rows j = 0..127 of one image column, so the column shift di of tap (di, dj)
+// moves a whole tile.  The A tile of input column s shifted by dj then feeds
+// all three column taps at once: with B = [W(-1,dj); W(0,dj); W(+1,dj)]
+// (N = 3 x NOUT), the three NOUT-wide groups of the product belong to output
+// columns s+1, s, s-1, and with the output accumulators laid out in
+// descending column order in TMEM (output column o at NOUT (K-1-(o-i0))) those
+// three are adjacent: one MMA of N = 3 NOUT accumulates into all of them.
+// Per output column and K step that is 3 MMAs of N = 3 NOUT reading three A
+// tiles instead of 9 MMAs of N = NOUT reading nine, so the shared-memory
+// operand traffic per useful multiply-add falls by about 2x.
+//
+// A super tile is kCT output columns [i0, i0 + Kv) of one sample; its input
+// window is columns i0-1 .. i0+Kv (whole padded columns, zero rows included).
+// The first MMA of an input column overwrites the groups whose output column
+// it touches first (accumulate flag 0) and accumulates the others, so TMEM
+// needs no clearing.  Rows j >= H of a tile (H < 128) read the next column or
+// the slack rows at the end of the stage and land in discarded D rows.
+constexpr int kCT = 8;                  // output columns per super tile
+
+template <int CIC, int NOUT>
+struct ColLayout {
+  static __host__ __device__ uint32_t L(int H) {
+    return (uint32_t)((kCT + 2) * (H + 2) + (H < 128 ? 128 - H : 0));
+  }
+  static __host__ __device__ uint32_t stage_bytes(int H) { return CIC * L(H) * 16u; }
+  static __host__ __device__ uint32_t w_bytes() { return 9u * CIC * NOUT * 16u; }
+  static __host__ __device__ uint32_t bar_off(int H) { return 2 * stage_bytes(H) + w_bytes(); }
+  static __host__ __device__ size_t total(int H) { return bar_off(H) + 128 + 128; }
+};
+
+template <int CIC, int NOUT, bool F32OUT>
+__global__ void __launch_bounds__(kConvThreads, 1) conv3x3_col_kernel(const ConvArgs a) {
+  static_assert(F32OUT || NOUT == 32, "hidden layers write 4 chunks of 8 channels");
+  using Lay = ColLayout<CIC, NOUT>;
+  extern __shared__ __align__(128) unsigned char cs[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(cs) + 127) & ~(uintptr_t)127);
+  const uint32_t L = Lay::L(a.H);
+  const uint32_t SB = Lay::stage_bytes(a.H);
+  unsigned char* stage0 = base;
+  unsigned char* wsm = base + 2 * SB;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + Lay::bar_off(a.H));
+  uint64_t* full = bars;          // [2] input stage landed
+  uint64_t* mdone = bars + 2;     // [2] MMAs of a super tile done (stage and TMEM buffer)
+  uint64_t* tempty = bars + 4;    // [2] epilogue finished reading a TMEM buffer
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 6);
+  volatile int* abort = reinterpret_cast<volatile int*>(bars + 7);
+  constexpr uint32_t kCols = 2 * kCT * NOUT;   // 512 or 256 TMEM columns
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int HP = a.H + 2;
+  const int nct = (a.W + kCT - 1) / kCT;
+  const int total = a.B * nct;
+
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) {
+      bar_init(&full[s], 1);
+      bar_init(&mdone[s], 1);
+      bar_init(&tempty[s], 4);
+    }
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // weights -> shared memory as [dj][chunk][(di + 1) NOUT + co][8] from the
+  // tap-major global layout [t = 3 (di + 1) + dj + 1][chunk][co][8]
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(a.wf);
+    uint4* dst = reinterpret_cast<uint4*>(wsm);
+    for (uint32_t q = tid; q < Lay::w_bytes() / 16; q += kConvThreads) {
+      const uint32_t co = q % NOUT, c8 = (q / NOUT) % CIC, t = q / (NOUT * CIC);
+      dst[((t % 3) * CIC + c8) * 3 * NOUT + (t / 3) * NOUT + co] = src[q];
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(kCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 4) {
+    if (lane == 0) {
+      // producer: plane rows of input columns i0-1 .. i0+Kv of every chunk
+      // plane (column i starts at plane row halo + i HP; column -1 is the
+      // zero halo, and column W lies inside the zero tail)
+      uint32_t issued = 0;
+      int it = 0;
+      for (int st = blockIdx.x; st < total; st += gridDim.x, ++it) {
+        const int s = it & 1;
+        const uint32_t u = (uint32_t)it >> 1;
+        if (u > 0 && !bar_wait(&mdone[s], (u - 1) & 1, abort)) { *abort = 1; break; }
+        const int b = st / nct;
+        const int i0 = (st - b * nct) * kCT;
+        const int kv = min(kCT, a.W - i0);
+        const size_t q0 = (size_t)(a.halo + (i0 - 1) * HP);
+        const uint32_t rows = (uint32_t)(kv + 2) * HP;
+        bar_expect(&full[s], CIC * rows * 16);
+        for (int c = 0; c < CIC; ++c)
+          bulk_g2s(stage0 + s * SB + (size_t)c * L * 16, a.in + (((size_t)b * CIC + c) * a.Rp + q0) * 8, rows * 16,
+                   &full[s]);
+        issued = (uint32_t)it + 1;
+      }
+      if (*abort) {
+        volatile int never = 0;
+        for (uint32_t k = issued > 2 ? issued - 2 : 0; k < issued; ++k)
+          (void)bar_wait(&full[k & 1], (k >> 1) & 1, &never);
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      uint32_t committed = 0;
+      int it = 0;
+      for (int st = blockIdx.x; st < total; st += gridDim.x, ++it) {
+        const int s = it & 1;
+        const uint32_t u = (uint32_t)it >> 1;
+        if (!bar_wait(&full[s], u & 1, abort)) { *abort = 1; break; }
+        if (u > 0 && !bar_wait(&tempty[s], (u - 1) & 1, abort)) { *abort = 1; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int b = st / nct;
+        const int i0 = (st - b * nct) * kCT;
+        const int kv = min(kCT, a.W - i0);
+        const uint32_t sa = su32(stage0 + s * SB);
+        const uint32_t sw = su32(wsm);
+        const uint32_t dbase = tmem + (uint32_t)(s * kCT * NOUT);
+        int last = i0 - 1;                          // largest output column written so far
+#pragma unroll 1
+        for (int c = i0 - 1; c <= i0 + kv; ++c) {   // input column
+          if (c < 0 || c >= a.W) continue;          // zero columns add nothing
+          // groups g = di + 1 in [g0, g1] reach output columns c + 1 - g
+          // inside the tile; [g0, gn) are written for the first time
+          const int g0 = max(0, c + 2 - i0 - kv), g1 = min(2, c + 1 - i0);
+          const int gn = min(g1 + 1, max(g0, c + 1 - last));
+          last = c + 1 - g0;
+          const uint32_t arow = (uint32_t)(c - i0 + 1) * HP + 1;
+#pragma unroll
+          for (int dj = 0; dj < 3; ++dj) {
+#pragma unroll
+            for (int kc = 0; kc < CIC / 2; ++kc) {
+              const uint64_t ad =
+                  desc_plain(sa + (uint32_t)(2 * kc) * L * 16 + (arow + (uint32_t)dj - 1) * 16, L * 16, 128);
+              const uint32_t wrow = (uint32_t)((dj * CIC + 2 * kc) * 3 * NOUT);
+              // [ga, gb] with accumulate flag acc: one MMA of N = (gb-ga+1) NOUT
+              auto issue = [&](int ga, int gb, uint32_t acc) {
+                const uint64_t bd = desc_plain(sw + (wrow + (uint32_t)(ga * NOUT)) * 16, 3 * NOUT * 16, 128);
+                const uint32_t d = dbase + (uint32_t)(NOUT * (kCT - 1 - (c + 1 - ga - i0)));
+                mma_f16(d, ad, bd, idesc_f16(128, (gb - ga + 1) * NOUT), acc);
+              };
+              if (dj == 0 && kc == 0) {
+                if (gn > g0) issue(g0, gn - 1, 0u);
+                if (gn <= g1) issue(gn, g1, 1u);
+              } else {
+                issue(g0, g1, 1u);
+              }
+            }
+          }
+        }
+        mma_commit_to(&mdone[s]);
+        committed = (uint32_t)it + 1;
+      }
+      if (*abort && committed > 0) {
+        const uint32_t k = committed - 1;
+        volatile int never = 0;
+        (void)bar_wait(&mdone[k & 1], (k >> 1) & 1, &never);
+      }
+    }
+  } else {
+    // epilogue: warp w reads TMEM lanes 32w..32w+31 = pixel rows j of each
+    // output column
+    int it = 0;
+    for (int st = blockIdx.x; st < total; st += gridDim.x, ++it) {
+      const int s = it & 1;
+      const uint32_t u = (uint32_t)it >> 1;
+      if (!bar_wait(&mdone[s], u & 1, abort)) { *abort = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int b = st / nct;
+      const int i0 = (st - b * nct) * kCT;
+      const int kv = min(kCT, a.W - i0);
+      const int j = warp * 32 + lane;
+      const bool valid_j = j < a.H;
+#pragma unroll 1
+      for (int q = 0; q < kv; ++q) {
+        const int o = i0 + q;
+        const uint32_t taddr =
+            tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * kCT * NOUT + NOUT * (kCT - 1 - q));
+        float v[NOUT];
+#pragma unroll
+        for (int c0 = 0; c0 < NOUT; c0 += 16) {
+          float w16[16];
+          tmem_ld_x16(taddr + (uint32_t)c0, w16);
+#pragma unroll
+          for (int k = 0; k < 16; ++k) v[c0 + k] = w16[k];
+        }
+        if (!valid_j) continue;
+        if (F32OUT) {
+#pragma unroll
+          for (int co = 0; co < NOUT; ++co)
+            if (co < a.cout)
+              a.out_f32[((size_t)b * a.cout + co) * a.H * a.W + (size_t)o * a.H + j] = v[co] + a.bias[co];
+        } else {
+          const size_t prow = (size_t)a.halo + (size_t)o * HP + 1 + j;
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            uint32_t pk[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int c0 = cc * 8 + 2 * e;
+              const float x0 = c0 < a.cout ? fmaxf(v[c0] + a.bias[c0], 0.f) : 0.f;
+              const float x1 = c0 + 1 < a.cout ? fmaxf(v[c0 + 1] + a.bias[c0 + 1], 0.f) : 0.f;
+              __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
+              pk[e] = *reinterpret_cast<uint32_t*>(&h2);
+            }
+            *reinterpret_cast<uint4*>(a.out_pad + (((size_t)b * 4 + cc) * a.Rp + prow) * 8) =
+                make_uint4(pk[0], pk[1], pk[2], pk[3]);
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) bar_arrive(&tempty[s]);
+    }
+  }
+  __syncthreads();
+  if (tid == 0 && *abort) atomicOr(a.err, 1);
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+  }
+}
+
 // Wf[t][c8][co][e] = W[co][c8*8+e][t] (0 outside C_in x C_out)
 __global__ void conv_weights_kernel(const float* Wl, int cin, int cout, int cic, int nout, __nv_bfloat16* wf) {
   const int n = 9 * cic * nout * 8;
@@ -366,6 +600,21 @@ cudaError_t launch_conv_t(const ConvArgs& a, int sms, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int CIC, int NOUT, bool F32OUT>
+cudaError_t launch_col_t(const ConvArgs& a, int sms, cudaStream_t st) {
+  auto k = conv3x3_col_kernel<CIC, NOUT, F32OUT>;
+  const size_t smem = ColLayout<CIC, NOUT>::total(a.H);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int total = a.B * ((a.W + kCT - 1) / kCT);
+  k<<<std::min(total, sms), kConvThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+// the column-aligned kernel needs a whole column in one 128-row tile and wastes
+// the rows past H, so it serves 64 < H <= 128
+bool use_col(const ConvGeom& g) { return g.H > 64 && g.H <= 128; }
+
 }  // namespace
 
 ConvGeom conv_geom(int H, int W) {
@@ -381,6 +630,13 @@ ConvGeom conv_geom(int H, int W) {
 }
 
 size_t conv_smem_bytes(const ConvGeom& g, int cic, int nout) {
+  if (use_col(g)) {
+    if (cic == 2 && nout == 32) return ColLayout<2, 32>::total(g.H);
+    if (cic == 4 && nout == 32) return ColLayout<4, 32>::total(g.H);
+    if (cic == 4 && nout == 16) return ColLayout<4, 16>::total(g.H);
+    if (cic == 2 && nout == 16) return ColLayout<2, 16>::total(g.H);
+    return 0;
+  }
   if (cic == 2 && nout == 32) return ConvLayout<2, 32>::total(g.halo);
   if (cic == 4 && nout == 32) return ConvLayout<4, 32>::total(g.halo);
   if (cic == 4 && nout == 16) return ConvLayout<4, 16>::total(g.halo);
@@ -409,6 +665,13 @@ cudaError_t launch_conv3x3(const __nv_bfloat16* in, int B, int cic, const __nv_b
   ConvArgs a;
   a.in = in; a.wf = wf; a.bias = bias; a.out_pad = out_pad; a.out_f32 = out_f32;
   a.B = B; a.H = g.H; a.W = g.W; a.halo = g.halo; a.Rp = g.Rp; a.nst = g.nst; a.cout = cout; a.err = err;
+  if (use_col(g)) {
+    if (!out_f32 && cic == 2 && nout == 32) return launch_col_t<2, 32, false>(a, sms, st);
+    if (!out_f32 && cic == 4 && nout == 32) return launch_col_t<4, 32, false>(a, sms, st);
+    if (out_f32 && cic == 4 && nout == 16) return launch_col_t<4, 16, true>(a, sms, st);
+    if (out_f32 && cic == 2 && nout == 16) return launch_col_t<2, 16, true>(a, sms, st);
+    return cudaErrorInvalidValue;
+  }
   if (!out_f32 && cic == 2 && nout == 32) return launch_conv_t<2, 32, false>(a, sms, st);
   if (!out_f32 && cic == 4 && nout == 32) return launch_conv_t<4, 32, false>(a, sms, st);
   if (out_f32 && cic == 4 && nout == 16) return launch_conv_t<4, 16, true>(a, sms, st);

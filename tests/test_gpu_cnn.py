@@ -65,7 +65,7 @@ def test_tap_orientation_exact(kp):
     assert np.array_equal(out.cpu().numpy().reshape(ref.shape), ref)
 
 
-@pytest.mark.parametrize("H,W,B", [(16, 16, 2), (28, 20, 3)])
+@pytest.mark.parametrize("H,W,B", [(16, 16, 2), (28, 20, 3), (80, 9, 2)])
 def test_forward_and_gradients_match_reference(kp, H, W, B):
     rng = np.random.default_rng(H * W + B)
     ch = (6, 32, 32, 32, 1)
@@ -163,13 +163,16 @@ def test_adam_steps_match_reference(kp):
         assert np.median(np.abs(p_gpu - p_now)) >= 0.1 * lr
 
 
-@pytest.mark.parametrize("H,W,B", [(7, 5, 1), (40, 30, 3), (128, 128, 10)])
+@pytest.mark.parametrize("H,W,B", [(7, 5, 1), (40, 30, 3), (72, 19, 1), (100, 37, 2), (128, 21, 2),
+                                   (128, 128, 10)])
 def test_implicit_gemm_forward_exact_shifts(kp, H, W, B):
     # two one-tap layers shift the image twice; small integers keep every
     # product and sum exact in BF16 x BF16 -> FP32, so the tensor-core
-    # implicit-GEMM path (padded-column layout, halo rows, several 512-row
-    # super tiles per CTA at 128x128 x 10) must equal the FP64 reference bit
-    # for bit, for every pair of taps
+    # implicit-GEMM path must equal the FP64 reference bit for bit, for every
+    # pair of taps: the row-tiled kernel (H <= 64: 128-row tiles across
+    # columns) and the column-aligned kernel (64 < H <= 128: one column per
+    # tile, the three column taps in one MMA; a ragged last super tile of
+    # columns when W is not a multiple of 8, rows past H discarded)
     rng = np.random.default_rng(H + W + B)
     x = rng.integers(0, 4, size=(B, 1, W, H)).astype(np.float64)
     xin = torch.as_tensor(x.reshape(B, 1, -1), dtype=torch.float32, device="cuda")
