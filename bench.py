@@ -470,7 +470,7 @@ def run_north_star(args):
     wl0 = synth.config(5, T=args.T, ntargets=1)           # sizes only (the seeds are cheap)
     ns_planes = wl0.n_seed_planes
     ctx = kp.Context(max_seeds=2 * ns_planes, max_a=wl0.a, max_n=wl0.groups[0].N, precision=kp.PREC_MIXED,
-                     inner_digits=args.inner_digits)
+                     inner_digits=args.inner_digits, reorth=args.reorth)
     if ALU_PEAK_SOURCE.startswith("derived"):
         set_alu_peaks(ctx)
     wl, g, net, train_info = learned_setup(kp, ctx, args, rank)
@@ -658,6 +658,7 @@ def run_north_star(args):
                    "T": T, "targets": nt, "seeds": wl.n_seed_planes, "grid": [H, W],
                    "timesteps_per_step": SLICE, "anchor_timesteps": anchors, "tol": wl.tol, "m": wl.m,
                    "inference_batch": net.inference_batch, "inner_digits": args.inner_digits or 5,
+                   "orthogonalisation": "CGS2" if args.reorth == 0 else "CGS+DGKS",
                    "parallelism": f"replicas x{world}",
                    "l2": "not flushed: each step's states (1.6 GB) exceed L2"},
         "e2e": {"value": e2e_value, "unit": "systems/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

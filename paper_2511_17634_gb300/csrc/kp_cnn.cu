@@ -166,13 +166,17 @@ __global__ void weights_bf16_kernel(const float* Wl, __nv_bfloat16* Wb, int ldw,
 
 size_t up8(size_t x) { return (x + 7) / 8 * 8; }
 
-// A field as two BF16 operands: hi = bf16(m), lo = 256 (m - hi).  One BF16
-// plane holds 8 significant bits; the step's change the network predicts is a
-// difference of neighbours a few hundred times smaller than m, so the first
-// layer gets both planes (about 16 bits) and recombines them in its FP32 sums.
-__device__ __forceinline__ void split_hi_lo(double m, __nv_bfloat16& hi, __nv_bfloat16& lo) {
-  hi = __float2bfloat16_rn((float)m);
-  lo = __float2bfloat16_rn((float)((m - (double)__bfloat162float(hi)) * 256.0));
+// A field as two BF16 operands: hi = bf16(f), lo = bf16(256 (f - hi)) of its
+// FP32 value f.  One BF16 plane holds 8 significant bits; the step's change the
+// network predicts is a difference of neighbours a few hundred times smaller
+// than m, so the first layer gets both planes (about 16 bits) and recombines
+// them in its FP32 sums.  f - hi is exact in FP32 (both are multiples of f's
+// ulp and |f - hi| is at most half a BF16 ulp of f), so the split costs FP32
+// arithmetic only; from the FP64 field it differs from splitting m itself only
+// where 256 (f - hi) is a BF16 rounding tie (one lo ulp, 2^-17 of m).
+__device__ __forceinline__ void split_hi_lo(float f, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(f);
+  lo = __float2bfloat16_rn((f - __bfloat162float(hi)) * 256.f);
 }
 
 // The residual the step leaves at the image, r = m/dt - A(m~ = m) m at point
@@ -197,16 +201,21 @@ __device__ __forceinline__ double step_residual_at(const double* m, int p, int H
 }
 
 // rho_b = ||r_b|| / sqrt(P), one block per sample; g2 = g2v, or g2s[*step +
-// step_offset] when g2s is given (the march's schedule and counter)
+// step_offset] when g2s is given (the march's schedule and counter).  The FP32
+// value of r goes to rout[b * rld + p] for the packing kernels, which then need
+// no FP64 arithmetic (the FP64 pipe, not HBM, bounds this part on GB300).
 __global__ void step_residual_rms_kernel(const double* const* m, int H, int W, double dt, double g2v,
-                                         const double* g2s, const int* step, int step_offset, double* rho) {
+                                         const double* g2s, const int* step, int step_offset, double* rho,
+                                         float* rout, size_t rld) {
   __shared__ double red[32];
   const int b = blockIdx.x, P = H * W;
   const double g2 = g2s ? g2s[*step + step_offset] : g2v;
+  float* ro = rout + (size_t)b * rld;
   double s = 0.0;
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
     const double r = step_residual_at(m[b], p, H, W, g2);
     s = fma(r, r, s);
+    ro[p] = (float)r;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -222,18 +231,20 @@ __global__ void step_residual_rms_kernel(const double* const* m, int H, int W, d
 // Network input planes of sample b: the target's plane (its lagged field
 // m_i^{n-1} for the learned guess) and the seed state, each as its hi and lo
 // planes, the time embedding tau, 1 - tau, sin(pi tau), cos(pi tau), and the
-// step's residual at the target's plane scaled to unit rms (hi, lo).
-__global__ void pack_inputs_kernel(const double* const* img, const double* const* seed, float tau, double dt,
-                                   double g2, const double* rho, int H, int W, float* in) {
-  const int b = blockIdx.y, P = H * W;
+// step's residual at the target's plane scaled to unit rms (hi, lo).  Plane 8
+// holds the FP32 residual on entry (step_residual_rms_kernel) and is
+// overwritten by the same thread.
+__global__ void pack_inputs_kernel(const double* const* img, const double* const* seed, float tau,
+                                   const double* rho, int P, float* in) {
+  const int b = blockIdx.y;
   const float e[4] = {tau, 1.f - tau, sinpif(tau), cospif(tau)};
-  const double ir = rho[b] > 0.0 ? 1.0 / rho[b] : 0.0;
+  const float ir = rho[b] > 0.0 ? (float)(1.0 / rho[b]) : 0.f;
   float* o = in + (size_t)b * 10 * P;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
     __nv_bfloat16 h0, l0, h1, l1, h2, l2;
-    split_hi_lo(img[b][p], h0, l0);
-    split_hi_lo(seed[b][p], h1, l1);
-    split_hi_lo(step_residual_at(img[b], p, H, W, g2) * ir, h2, l2);
+    split_hi_lo((float)img[b][p], h0, l0);
+    split_hi_lo((float)seed[b][p], h1, l1);
+    split_hi_lo(o[8 * P + p] * ir, h2, l2);
     o[p] = __bfloat162float(h0);
     o[P + p] = __bfloat162float(l0);
     o[2 * P + p] = __bfloat162float(h1);
@@ -268,33 +279,32 @@ __global__ void add_guess_kernel(const float* delta, const double* const* base, 
 // The learned guess inside the time march, for the target timestep n = *step
 // + step_offset + 1 (1-based), tau = n / T: the ten input planes of sample b
 // -- m_i^{n-1} (hi, lo), m_seed^n (hi, lo), tau, 1 - tau, sin pi tau,
-// cos pi tau, the step's residual scaled by 1 / rho_b (hi, lo) -- straight
-// into the padded BF16 rows of the first convolution (chunk 0: channels
-// 0..7; chunk 1: 8, 9 and zeros)
-__global__ void march_pack_kernel(const double* const* mprev, const double* const* mseed, const int* step,
-                                  int step_offset, const double* g2s, const double* rho, int T, int H, int W,
+// cos pi tau, the step's residual (FP32 in r, step_residual_rms_kernel)
+// scaled by 1 / rho_b (hi, lo) -- straight into the padded BF16 rows of the
+// first convolution (chunk 0: channels 0..7; chunk 1: 8, 9 and zeros)
+__global__ void march_pack_kernel(const double* const* mprev, const double* const* mseed, const float* r,
+                                  const int* step, int step_offset, const double* rho, int T, int H, int W,
                                   int halo, int Rp, __nv_bfloat16* out) {
   const int b = blockIdx.y;
   const int P = H * W;
   const int t = *step + step_offset;
   const float tau = (float)(t + 1) / (float)T;
   const float e[4] = {tau, 1.f - tau, sinpif(tau), cospif(tau)};
-  const double g2 = g2s[t];
-  const double ir = rho[b] > 0.0 ? 1.0 / rho[b] : 0.0;
+  const float ir = rho[b] > 0.0 ? (float)(1.0 / rho[b]) : 0.f;
   const double* mp = mprev[b];
   const double* ms = mseed[b];
+  const float* rb = r + (size_t)b * P;
+  __nv_bfloat162 h1 = __floats2bfloat162_rn(e[0], e[1]);
+  __nv_bfloat162 h2 = __floats2bfloat162_rn(e[2], e[3]);
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
     const int i = p / H, j = p - i * H;
     const size_t row = (size_t)halo + (size_t)i * (H + 2) + 1 + j;
-    __nv_bfloat162 f0, f1;
-    split_hi_lo(mp[p], f0.x, f0.y);
-    split_hi_lo(ms[p], f1.x, f1.y);
-    __nv_bfloat162 h1 = __floats2bfloat162_rn(e[0], e[1]);
-    __nv_bfloat162 h2 = __floats2bfloat162_rn(e[2], e[3]);
+    __nv_bfloat162 f0, f1, f2;
+    split_hi_lo((float)mp[p], f0.x, f0.y);
+    split_hi_lo((float)ms[p], f1.x, f1.y);
+    split_hi_lo(rb[p] * ir, f2.x, f2.y);
     const uint4 c0 = make_uint4(*reinterpret_cast<uint32_t*>(&f0), *reinterpret_cast<uint32_t*>(&f1),
                                 *reinterpret_cast<uint32_t*>(&h1), *reinterpret_cast<uint32_t*>(&h2));
-    __nv_bfloat162 f2;
-    split_hi_lo(step_residual_at(mp, p, H, W, g2) * ir, f2.x, f2.y);
     *reinterpret_cast<uint4*>(out + (((size_t)b * 2 + 0) * Rp + row) * 8) = c0;
     *reinterpret_cast<uint4*>(out + (((size_t)b * 2 + 1) * Rp + row) * 8) =
         make_uint4(*reinterpret_cast<uint32_t*>(&f2), 0u, 0u, 0u);
@@ -677,9 +687,10 @@ kp_status kp_cnn_pack_inputs(kp_cnn* n, int B, const double* const* img, const d
   if (e == cudaSuccess) e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double*), cudaMemcpyHostToDevice, n->ctx->stream);
   if (e == cudaSuccess) {
     const double dt = 1.0 / T;
-    step_residual_rms_kernel<<<B, 256, 0, n->ctx->stream>>>(d, n->H, n->W, dt, g2n, nullptr, nullptr, 0, rho);
-    pack_inputs_kernel<<<dim3(grid_for(n->P), B), 256, 0, n->ctx->stream>>>(d, d + B, (float)step / (float)T, dt,
-                                                                           g2n, rho, n->H, n->W, in);
+    step_residual_rms_kernel<<<B, 256, 0, n->ctx->stream>>>(d, n->H, n->W, dt, g2n, nullptr, nullptr, 0, rho,
+                                                            in + 8 * (size_t)n->P, 10 * (size_t)n->P);
+    pack_inputs_kernel<<<dim3(grid_for(n->P), B), 256, 0, n->ctx->stream>>>(d, d + B, (float)step / (float)T,
+                                                                           rho, n->P, in);
     e = cudaGetLastError();
   }
   if (d) cudaFreeAsync(d, n->ctx->stream);
@@ -747,9 +758,12 @@ cudaError_t cnn_enqueue_guess(kp_cnn* n, int B, const double* const* mprev, cons
                               cudaStream_t st) {
   if (B < 1 || B > n->infB) return cudaErrorInvalidValue;
   const dim3 grid(std::min((n->P + 255) / 256, 1024), B);
-  step_residual_rms_kernel<<<B, 256, 0, st>>>(mprev, n->H, n->W, 1.0 / T, 0.0, g2, step, step_offset, n->rho);
-  march_pack_kernel<<<grid, 256, 0, st>>>(mprev, mseed, step, step_offset, g2, n->rho, T, n->H, n->W, n->geo.halo,
-                                          n->geo.Rp, n->pin);
+  // the FP32 residual goes through the network's output buffer, which the
+  // last layer overwrites afterwards
+  step_residual_rms_kernel<<<B, 256, 0, st>>>(mprev, n->H, n->W, 1.0 / T, 0.0, g2, step, step_offset, n->rho,
+                                              n->dout, (size_t)n->P);
+  march_pack_kernel<<<grid, 256, 0, st>>>(mprev, mseed, n->dout, step, step_offset, n->rho, T, n->H, n->W,
+                                          n->geo.halo, n->geo.Rp, n->pin);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = conv_layers(n, B, n->dout, st);
   if (e == cudaSuccess) {

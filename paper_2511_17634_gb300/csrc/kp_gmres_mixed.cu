@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
     unsigned long long proj_flops = 0;
     double r[EPT];
     auto residual = [&]() { residual_of(sm.xs, r); };
+    bool r_current = false;                         // r already holds b - A x0 (FP64)
     if (p.x0_mode == X0_GUESS_PROJECT) {
       // the judge of a given guess (the learned one): its FP64 residual
       // against the warm start's; a kept guess is projected below, the
@@ -211,6 +212,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
           if (pp < N) sm.xs[pp] = d.mt[pp];
         }
       }
+      r_current = true;
       proj_flops = 26ull * (unsigned long long)N;
       // Sec. 3, Phase 2 on the residual of the guess: r = b - A x_init
       // (FP64), c = V^T r (FP32 products, FP64 sums), alpha = H_a^{-1} c,
@@ -251,6 +253,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
             sm.xs[pp] += (double)xv;
           }
         }
+        r_current = false;
         proj_flops += (unsigned long long)(2 * nv + 2 * a) * (unsigned long long)N;
       }
     }
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
     if (p.x0_mode == X0_ZERO) {
 #pragma unroll
       for (int k = 0; k < EPT; ++k) r[k] = bval(tid + k * NT);
-    } else {
+    } else if (!r_current) {
       residual();
     }
     block_partials<NT>(2, [&](int i) {
