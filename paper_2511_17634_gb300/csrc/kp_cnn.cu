@@ -19,9 +19,18 @@
 
 #include "kp.h"
 #include "kp_ctx.h"
+#include "kp_dd.cuh"
 #include "kp_internal.cuh"
 
 namespace {
+
+using kp::dd;
+using kp::dd_add;
+using kp::dd_add_f;
+using kp::dd_from_double;
+using kp::dd_mul;
+using kp::dd_sub;
+using kp::dd_to_double;
 
 constexpr int kMaxLayers = 8;
 
@@ -182,41 +191,44 @@ __device__ __forceinline__ void split_hi_lo(float f, __nv_bfloat16& hi, __nv_bfl
 // The residual the step leaves at the image, r = m/dt - A(m~ = m) m at point
 // p (Sec. 2.3, f = 0, zero outside the grid).  With A m = (1/dt + 4c) m_p +
 // sum over the four neighbours of (-c -+ e (m_+ - m_-)) m_nbr, the 1/dt terms
-// cancel exactly: r = -(4c m_p + sum of the neighbour terms) -- no division,
-// and none of the cancellation of the two large 1/dt terms.  c = g2/(2h^2) =
-// g2 H^2 / 2, e = g2 H^2 / 8.
-__device__ __forceinline__ double step_residual_at(const double* m, int p, int H, int W, double g2) {
-  const double hh = (double)H * (double)H;
-  const double c = 0.5 * g2 * hh, e = 0.125 * g2 * hh;
+// cancel exactly and the rest collects into
+//   r = c (m_E + m_W + m_N + m_S - 4 m_p) + e ((m_E - m_W)^2 + (m_N - m_S)^2),
+// c = g2/(2h^2) = g2 H^2 / 2, e = g2 H^2 / 8 -- no division, and none of the
+// cancellation of the two large 1/dt terms.  Evaluated in double-float on the
+// FP32 pipe (kp_dd.cuh; about 2^-44 of c |m| absolute), the FP64 field split
+// without FP64 instructions.
+__device__ __forceinline__ dd step_residual_at(const double* m, int p, int H, int W, dd c, dd e) {
   const int i = p / H, j = p - i * H;
-  const double mE = i + 1 < W ? m[p + H] : 0.0, mW = i > 0 ? m[p - H] : 0.0;
-  const double mN = j + 1 < H ? m[p + 1] : 0.0, mS = j > 0 ? m[p - 1] : 0.0;
-  const double dx = mE - mW, dy = mN - mS;
-  double t = 4.0 * c * m[p];
-  t = fma(-c - e * dx, mE, t);
-  t = fma(-c + e * dx, mW, t);
-  t = fma(-c - e * dy, mN, t);
-  t = fma(-c + e * dy, mS, t);
-  return -t;
+  const dd z = {0.f, 0.f};
+  const dd mC = dd_from_double(m[p]);
+  const dd mE = i + 1 < W ? dd_from_double(m[p + H]) : z, mW = i > 0 ? dd_from_double(m[p - H]) : z;
+  const dd mN = j + 1 < H ? dd_from_double(m[p + 1]) : z, mS = j > 0 ? dd_from_double(m[p - 1]) : z;
+  const dd lap = dd_sub(dd_add(dd_add(mE, mW), dd_add(mN, mS)), dd{4.f * mC.hi, 4.f * mC.lo});
+  const dd dx = dd_sub(mE, mW), dy = dd_sub(mN, mS);
+  return dd_add(dd_mul(c, lap), dd_mul(e, dd_add(dd_mul(dx, dx), dd_mul(dy, dy))));
 }
 
 // rho_b = ||r_b|| / sqrt(P), one block per sample; g2 = g2v, or g2s[*step +
 // step_offset] when g2s is given (the march's schedule and counter).  The FP32
-// value of r goes to rout[b * rld + p] for the packing kernels, which then need
-// no FP64 arithmetic (the FP64 pipe, not HBM, bounds this part on GB300).
+// value of r goes to rout[b * rld + p] for the packing kernels.  The squares
+// are summed in double-float per thread; no FP64 instruction runs per point
+// (the FP64 pipe, not HBM, bounds this part on GB300).
 __global__ void step_residual_rms_kernel(const double* const* m, int H, int W, double dt, double g2v,
                                          const double* g2s, const int* step, int step_offset, double* rho,
                                          float* rout, size_t rld) {
   __shared__ double red[32];
   const int b = blockIdx.x, P = H * W;
   const double g2 = g2s ? g2s[*step + step_offset] : g2v;
+  const double hh = (double)H * (double)H;
+  const dd c = dd_from_double(0.5 * g2 * hh), e = dd_from_double(0.125 * g2 * hh);
   float* ro = rout + (size_t)b * rld;
-  double s = 0.0;
+  dd acc = {0.f, 0.f};
   for (int p = threadIdx.x; p < P; p += blockDim.x) {
-    const double r = step_residual_at(m[b], p, H, W, g2);
-    s = fma(r, r, s);
-    ro[p] = (float)r;
+    const dd r = step_residual_at(m[b], p, H, W, c, e);
+    acc = dd_add(acc, dd_mul(r, r));
+    ro[p] = r.hi;
   }
+  double s = dd_to_double(acc);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;

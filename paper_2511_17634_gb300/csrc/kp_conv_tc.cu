@@ -337,6 +337,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3x3_tc_kernel(const ConvA
 // needs no clearing.  Rows j >= H of a tile (H < 128) read the next column or
 // the slack rows at the end of the stage and land in discarded D rows.
 constexpr int kCT = 8;                  // output columns per super tile
+constexpr int kColEpiWarps = 8;         // two epilogue warps per TMEM lane quadrant
+constexpr int kColThreads = 32 * (kColEpiWarps + 2);   // + producer warp + MMA warp
 
 template <int CIC, int NOUT>
 struct ColLayout {
@@ -350,7 +352,7 @@ struct ColLayout {
 };
 
 template <int CIC, int NOUT, bool F32OUT>
-__global__ void __launch_bounds__(kConvThreads, 1) conv3x3_col_kernel(const ConvArgs a) {
+__global__ void __launch_bounds__(kColThreads, 1) conv3x3_col_kernel(const ConvArgs a) {
   static_assert(F32OUT || NOUT == 32, "hidden layers write 4 chunks of 8 channels");
   using Lay = ColLayout<CIC, NOUT>;
   extern __shared__ __align__(128) unsigned char cs[];
@@ -375,7 +377,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3x3_col_kernel(const Conv
     for (int s = 0; s < 2; ++s) {
       bar_init(&full[s], 1);
       bar_init(&mdone[s], 1);
-      bar_init(&tempty[s], 4);
+      bar_init(&tempty[s], kColEpiWarps);
     }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3x3_col_kernel(const Conv
   {
     const uint4* src = reinterpret_cast<const uint4*>(a.wf);
     uint4* dst = reinterpret_cast<uint4*>(wsm);
-    for (uint32_t q = tid; q < Lay::w_bytes() / 16; q += kConvThreads) {
+    for (uint32_t q = tid; q < Lay::w_bytes() / 16; q += kColThreads) {
       const uint32_t co = q % NOUT, c8 = (q / NOUT) % CIC, t = q / (NOUT * CIC);
       dst[((t % 3) * CIC + c8) * 3 * NOUT + (t / 3) * NOUT + co] = src[q];
     }
@@ -402,7 +404,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3x3_col_kernel(const Conv
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 4) {
+  if (warp == kColEpiWarps) {
     if (lane == 0) {
       // producer: plane rows of input columns i0-1 .. i0+Kv of every chunk
       // plane (column i starts at plane row halo + i HP; column -1 is the
@@ -430,7 +432,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3x3_col_kernel(const Conv
           (void)bar_wait(&full[k & 1], (k >> 1) & 1, &never);
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == kColEpiWarps + 1) {
     if (lane == 0) {
       uint32_t committed = 0;
       int it = 0;
@@ -488,8 +490,8 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3x3_col_kernel(const Conv
       }
     }
   } else {
-    // epilogue: warp w reads TMEM lanes 32w..32w+31 = pixel rows j of each
-    // output column
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = pixel rows j of
+    // every (kColEpiWarps / 4)-th output column, starting at column w / 4
     int it = 0;
     for (int st = blockIdx.x; st < total; st += gridDim.x, ++it) {
       const int s = it & 1;
@@ -499,13 +501,14 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3x3_col_kernel(const Conv
       const int b = st / nct;
       const int i0 = (st - b * nct) * kCT;
       const int kv = min(kCT, a.W - i0);
-      const int j = warp * 32 + lane;
+      const int quad = warp & 3;
+      const int j = quad * 32 + lane;
       const bool valid_j = j < a.H;
 #pragma unroll 1
-      for (int q = 0; q < kv; ++q) {
+      for (int q = warp >> 2; q < kv; q += kColEpiWarps / 4) {
         const int o = i0 + q;
         const uint32_t taddr =
-            tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(s * kCT * NOUT + NOUT * (kCT - 1 - q));
+            tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(s * kCT * NOUT + NOUT * (kCT - 1 - q));
         float v[NOUT];
 #pragma unroll
         for (int c0 = 0; c0 < NOUT; c0 += 16) {
@@ -607,7 +610,7 @@ cudaError_t launch_col_t(const ConvArgs& a, int sms, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int total = a.B * ((a.W + kCT - 1) / kCT);
-  k<<<std::min(total, sms), kConvThreads, smem, st>>>(a);
+  k<<<std::min(total, sms), kColThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

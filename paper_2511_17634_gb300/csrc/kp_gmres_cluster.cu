@@ -11,10 +11,17 @@
 //    barrier, double-buffered partials), so all CTAs hold bit-identical
 //    coefficients and run the FP64 Hessenberg / Givens updates redundantly
 //    instead of broadcasting them.
-//  * Same arithmetic and stopping rules as the one-block mixed kernel: FP32
-//    Krylov inside FP64 iterative refinement on the FP64 true residual.
+//  * Same stopping rules as the one-block mixed kernel: FP32 Krylov inside
+//    iterative refinement on the true residual.  The refinement's
+//    high-precision arithmetic -- x, the operator coefficients, b - A x --
+//    is double-float (kp_dd.cuh, about 48 bits) on the FP32 pipe instead of
+//    FP64: on GB300 the FP64 pipe issues 2 operations per clock per SM and
+//    the FP64 residuals, judge and coefficient set-up held it busy over half
+//    of the kernel.  The residual's error is a few units of 2^-44 times
+//    ||b||, far under every tolerance the solver is asked for (>= 1e-12).
 #include <cooperative_groups.h>
 
+#include "kp_dd.cuh"
 #include "kp_internal.cuh"
 
 namespace cg = cooperative_groups;
@@ -36,8 +43,9 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
   const int m = p.m;
   const int ld = m + 1;
   // shared-memory carve (identical offsets in every CTA of the cluster)
-  double* xs = smem_raw;                          // [npad] FP64 slice of x
-  double* red = xs + npad;                        // [NWARPS][kMaxV]
+  float* xh = reinterpret_cast<float*>(smem_raw);  // [npad] slice of x, double-float hi
+  float* xl = xh + npad;                           // [npad] and lo parts
+  double* red = smem_raw + npad;                  // [NWARPS][kMaxV]
   float* red32 = reinterpret_cast<float*>(red);    // FP32 per-warp partials (same space)
   double* hb = red + NWARPS * kMaxV;              // [kMaxV] cluster sums
   double* cpart = hb + kMaxV;                     // [2][kMaxV] per-CTA partials
@@ -90,51 +98,75 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
   float* capV = capture ? p.capV32 + (size_t)cidx * (p.cap_a + 1) * p.cap_ld : nullptr;
   double* capH = capture ? p.capH + (size_t)cidx * (p.cap_a + 1) * p.cap_a : nullptr;
 
-  // FP32 q_x, q_y for the Krylov operator; FP64 E and N coefficients
-  // cE = q_x - c, cN = q_y - c for the residual (cW = -2c - cE, cS = -2c - cN)
-  double cEx[EPT], cNy[EPT];
+  // FP32 q_x, q_y for the Krylov operator; double-float E and N coefficients
+  // cE = q_x - c, cN = q_y - c for the residual (cW = -2c - cE, cS = -2c - cN),
+  // from the FP64 field split without FP64 instructions.  In the judge mode
+  // (a given guess) the warm start's residual norm comes out of the same
+  // loads: sw = sum of r_warm^2 over this thread's points.
+  const bool judge = p.x0_mode == X0_GUESS_PROJECT;
+  const dd ccd = dd_from_double(cc), eed = dd_from_double(ee), cdd = dd_from_double(cd), i2hd = dd_from_double(i2h);
+  const dd c2d = dd_from_double(2.0 * cc);
+  dd cE[EPT], cN[EPT];
   float qxf[EPT], qyf[EPT];
-  unsigned msk[EPT];
+  unsigned msk = 0;                               // 4 neighbour bits per point
+  float sw = 0.f;
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
     const int l = tid + k * NT, pp = base + l;
-    double qx = 0.0, qy = 0.0;
-    msk[k] = 0;
+    dd qx = {0.f, 0.f}, qy = {0.f, 0.f};
     if (l < SL) {
       const int i = pp / H, j = pp - i * H;
-      const double mE = (i + 1 < W) ? d.mt[pp + H] : 0.0;
-      const double mW = (i > 0) ? d.mt[pp - H] : 0.0;
-      const double mN = (j + 1 < H) ? d.mt[pp + 1] : 0.0;
-      const double mS = (j > 0) ? d.mt[pp - 1] : 0.0;
-      const double fxp = d.fx ? d.fx[pp] : 0.0;
-      const double fyp = d.fy ? d.fy[pp] : 0.0;
-      qx = fxp * i2h - ee * (mE - mW);
-      qy = fyp * i2h - ee * (mN - mS);
-      msk[k] = (i + 1 < W ? 1u : 0u) | (i > 0 ? 2u : 0u) | (j + 1 < H ? 4u : 0u) | (j > 0 ? 8u : 0u);
+      const unsigned mk = (i + 1 < W ? 1u : 0u) | (i > 0 ? 2u : 0u) | (j + 1 < H ? 4u : 0u) | (j > 0 ? 8u : 0u);
+      msk |= mk << (4 * k);
+      const dd mE = dd_from_double((mk & 1u) ? d.mt[pp + H] : 0.0);
+      const dd mW = dd_from_double((mk & 2u) ? d.mt[pp - H] : 0.0);
+      const dd mN = dd_from_double((mk & 4u) ? d.mt[pp + 1] : 0.0);
+      const dd mS = dd_from_double((mk & 8u) ? d.mt[pp - 1] : 0.0);
+      qx = dd_mul(eed, dd_sub(mW, mE));
+      qy = dd_mul(eed, dd_sub(mS, mN));
+      if (d.fx) qx = dd_add(qx, dd_mul(dd_from_double(d.fx[pp]), i2hd));
+      if (d.fy) qy = dd_add(qy, dd_mul(dd_from_double(d.fy[pp]), i2hd));
+      cE[k] = dd_sub(qx, ccd);
+      cN[k] = dd_sub(qy, ccd);
+      if (judge) {
+        const dd mC = dd_from_double(d.mt[pp]);
+        dd t = dd_sub(dd_from_double(d.b[pp]), dd_mul(cdd, mC));
+        t = dd_sub(t, dd_mul(cE[k], dd_sub(mE, mW)));
+        t = dd_sub(t, dd_mul(cN[k], dd_sub(mN, mS)));
+        t = dd_add(t, dd_mul(c2d, dd_add(mW, mS)));
+        sw = fmaf(t.hi, t.hi, sw);
+      }
+    } else {
+      cE[k] = cN[k] = dd{0.f, 0.f};
     }
-    cEx[k] = qx - cc;
-    cNy[k] = qy - cc;
-    qxf[k] = (float)qx;
-    qyf[k] = (float)qy;
+    qxf[k] = qx.hi;
+    qyf[k] = qy.hi;
   }
-  const double* xs_next = rank + 1 < CS ? cluster.map_shared_rank(xs, rank + 1) : nullptr;
-  const double* xs_prev = rank > 0 ? cluster.map_shared_rank(xs, rank - 1) : nullptr;
-  // r = b - A x in FP64 (A x = cd x + cE (xE - xW) - 2c xW + cN (xN - xS) - 2c xS)
-  const double c2 = 2.0 * cc;
-  auto residual_of = [&](double (&out)[EPT]) {
+  auto mbits = [&](int k) { return (msk >> (4 * k)) & 15u; };
+  const float* xh_next = rank + 1 < CS ? cluster.map_shared_rank(xh, rank + 1) : nullptr;
+  const float* xh_prev = rank > 0 ? cluster.map_shared_rank(xh, rank - 1) : nullptr;
+  const float* xl_next = rank + 1 < CS ? cluster.map_shared_rank(xl, rank + 1) : nullptr;
+  const float* xl_prev = rank > 0 ? cluster.map_shared_rank(xl, rank - 1) : nullptr;
+  // r = b - A x in double-float (A x = cd x + cE (xE - xW) - 2c xW + cN (xN -
+  // xS) - 2c xS); out = its hi part, which is all the FP32 Krylov and the
+  // norms need
+  auto residual_of = [&](float (&out)[EPT]) {
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
       const int l = tid + k * NT;
-      out[k] = 0.0;
+      out[k] = 0.f;
       if (l < SL) {
-        const double xE = (msk[k] & 1u) ? (l + H < SL ? xs[l + H] : xs_next[l + H - SL]) : 0.0;
-        const double xW = (msk[k] & 2u) ? (l - H >= 0 ? xs[l - H] : xs_prev[l - H + SL]) : 0.0;
-        const double xN = (msk[k] & 4u) ? xs[l + 1] : 0.0;
-        const double xS = (msk[k] & 8u) ? xs[l - 1] : 0.0;
-        double t = fma(-cd, xs[l], d.b[base + l]);
-        t = fma(-cEx[k], xE - xW, t);
-        t = fma(-cNy[k], xN - xS, t);
-        out[k] = fma(c2, xW + xS, t);
+        const unsigned mk = mbits(k);
+        const dd z = {0.f, 0.f};
+        const dd xE = (mk & 1u) ? (l + H < SL ? dd{xh[l + H], xl[l + H]} : dd{xh_next[l + H - SL], xl_next[l + H - SL]}) : z;
+        const dd xW = (mk & 2u) ? (l - H >= 0 ? dd{xh[l - H], xl[l - H]} : dd{xh_prev[l - H + SL], xl_prev[l - H + SL]}) : z;
+        const dd xN = (mk & 4u) ? dd{xh[l + 1], xl[l + 1]} : z;
+        const dd xS = (mk & 8u) ? dd{xh[l - 1], xl[l - 1]} : z;
+        dd t = dd_sub(dd_from_double(d.b[base + l]), dd_mul(cdd, dd{xh[l], xl[l]}));
+        t = dd_sub(t, dd_mul(cE[k], dd_sub(xE, xW)));
+        t = dd_sub(t, dd_mul(cN[k], dd_sub(xN, xS)));
+        t = dd_add(t, dd_mul(c2d, dd_add(xW, xS)));
+        out[k] = t.hi;
       }
     }
   };
@@ -147,15 +179,16 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
       const int l = tid + k * NT;
       out[k] = 0.f;
       if (l < SL) {
-        const float xE = (msk[k] & 1u) ? (l + H < SL ? v[l + H] : vn[l + H - SL]) : 0.f;
-        const float xW = (msk[k] & 2u) ? (l - H >= 0 ? v[l - H] : vp[l - H + SL]) : 0.f;
-        const float xN = (msk[k] & 4u) ? v[l + 1] : 0.f;
-        const float xS = (msk[k] & 8u) ? v[l - 1] : 0.f;
+        const unsigned mk = mbits(k);
+        const float xE = (mk & 1u) ? (l + H < SL ? v[l + H] : vn[l + H - SL]) : 0.f;
+        const float xW = (mk & 2u) ? (l - H >= 0 ? v[l - H] : vp[l - H + SL]) : 0.f;
+        const float xN = (mk & 4u) ? v[l + 1] : 0.f;
+        const float xS = (mk & 8u) ? v[l - 1] : 0.f;
         out[k] = -ccf * (xE + xW + xN + xS) + qxf[k] * (xE - xW) + qyf[k] * (xN - xS);
       }
     }
   };
-  auto bval = [&](int l) { return (l < SL) ? d.b[base + l] : 0.0; };
+  auto bhi = [&](int l) { return (l < SL) ? dd_from_double(d.b[base + l]).hi : 0.f; };
   int buf = 0;
   // cluster-wide sums of nv values whose per-warp partials are in red;
   // result in hb[0..nv) of every CTA (identical, rank order)
@@ -179,63 +212,41 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
     buf ^= 1;
   };
 
-  // initial guess
+  // initial guess, split into double-float without FP64 instructions
+  auto load_x = [&](const double* src) {
 #pragma unroll
-  for (int k = 0; k < EPT; ++k) {
-    const int l = tid + k * NT;
-    double x0 = 0.0;
-    if (l < SL) {
-      if (p.x0_mode == X0_READ || p.x0_mode == X0_GUESS_PROJECT) x0 = d.x[base + l];
-      else if (p.x0_mode == X0_WARM) x0 = d.mt[base + l];
+    for (int k = 0; k < EPT; ++k) {
+      const int l = tid + k * NT;
+      const dd v = (src && l < SL) ? dd_from_double(src[base + l]) : dd{0.f, 0.f};
+      xh[l] = v.hi;
+      xl[l] = v.lo;
     }
-    xs[l] = x0;
-  }
+  };
+  load_x(p.x0_mode == X0_READ || judge ? d.x : p.x0_mode == X0_WARM ? d.mt : nullptr);
   unsigned long long proj_flops = 0;
-  double r[EPT];
+  float r[EPT];
   auto residual = [&]() { residual_of(r); };
-  if (p.x0_mode == X0_GUESS_PROJECT) {
-    // the judge of a given guess (as in the one-block mixed solver): the FP64
-    // residuals of the guess and of the warm start, both whole vectors in
-    // global memory; a kept guess is projected, the warm start starts as is
-    auto residual_glob = [&](const double* v, double (&out)[EPT]) {
+  bool r_current = false;                         // r already holds b - A x0
+  if (judge) {
+    // the judge of a given guess (as in the one-block mixed solver): the
+    // guess's true residual against the warm start's (sw, from the set-up);
+    // a kept guess is projected, the warm start starts as is
+    cluster.sync();                               // x_init slices visible cluster-wide
+    residual();
+    block_partials_f32x<NT>(2, [&](int i) {
+      float s = 0.f;
+      if (i == 0) {
 #pragma unroll
-      for (int k = 0; k < EPT; ++k) {
-        const int l = tid + k * NT, pp = base + l;
-        out[k] = 0.0;
-        if (l < SL) {
-          const double xE = (msk[k] & 1u) ? v[pp + H] : 0.0;
-          const double xW = (msk[k] & 2u) ? v[pp - H] : 0.0;
-          const double xN = (msk[k] & 4u) ? v[pp + 1] : 0.0;
-          const double xS = (msk[k] & 8u) ? v[pp - 1] : 0.0;
-          double t = fma(-cd, v[pp], d.b[pp]);
-          t = fma(-cEx[k], xE - xW, t);
-          t = fma(-cNy[k], xN - xS, t);
-          out[k] = fma(c2, xW + xS, t);
-        }
+        for (int k = 0; k < EPT; ++k) s = fmaf(r[k], r[k], s);
+      } else {
+        s = sw;
       }
-    };
-    residual_glob(d.x, r);
-    bool warm_won = false;
-    {
-      double rw[EPT];
-      residual_glob(d.mt, rw);
-      block_partials<NT>(2, [&](int i) {
-        double s = 0.0;
-#pragma unroll
-        for (int k = 0; k < EPT; ++k) s += (i == 0) ? r[k] * r[k] : rw[k] * rw[k];
-        return s;
-      }, red);
-      cluster_sum(2, false);
-      warm_won = hb[1] < hb[0];                     // the same in every CTA
-      if (warm_won) {
-#pragma unroll
-        for (int k = 0; k < EPT; ++k) {
-          const int l = tid + k * NT;
-          r[k] = rw[k];
-          if (l < SL) xs[l] = d.mt[base + l];
-        }
-      }
-    }
+      return s;
+    }, red32);
+    cluster_sum(2, true);                         // (its barrier also ends every read of x_init)
+    const bool warm_won = hb[1] < hb[0];          // the same in every CTA
+    if (warm_won) load_x(d.mt);
+    r_current = !warm_won;
     proj_flops = 26ull * (unsigned long long)N;
     // Sec. 3, Phase 2 on the residual of the guess: c = V^T r,
     // alpha = H_a^{-1} c, x0 = x_init + V alpha, the sums cluster-wide
@@ -245,16 +256,13 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
       const int a = mt.a;
       const int nv = mt.lsq ? a + 1 : a;
       const float* Vs = p.slotV32 + (size_t)sl * (p.max_a + 1) * p.slot_ld + base;
-      float rv[EPT];
-#pragma unroll
-      for (int k = 0; k < EPT; ++k) rv[k] = (float)r[k];
       block_partials_f32x<NT>(nv, [&](int i) {
         const float* vi = Vs + (size_t)i * p.slot_ld;
         float s = 0.f;
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
           const int l = tid + k * NT;
-          if (l < SL) s = fmaf(vi[l], rv[k], s);
+          if (l < SL) s = fmaf(vi[l], r[k], s);
         }
         return s;
       }, red32);
@@ -264,6 +272,8 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
         const double* rot = p.slotRot + (size_t)sl * 3 * p.max_a;
         solve_projected_warp(hb, a, mt.nrot, p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a,
                              p.max_a + 1, rot, rot + 2 * p.max_a, lane);
+        __syncwarp();
+        for (int i = lane; i < a; i += 32) red32[i] = (float)hb[i];   // alpha in FP32, converted once
       }
       __syncthreads();
 #pragma unroll
@@ -271,10 +281,13 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
         const int l = tid + k * NT;
         if (l < SL) {
           float xv = 0.f;
-          for (int i = 0; i < a; ++i) xv = fmaf((float)hb[i], Vs[(size_t)i * p.slot_ld + l], xv);
-          xs[l] += (double)xv;
+          for (int i = 0; i < a; ++i) xv = fmaf(red32[i], Vs[(size_t)i * p.slot_ld + l], xv);
+          const dd xn = dd_add_f(dd{xh[l], xl[l]}, xv);
+          xh[l] = xn.hi;
+          xl[l] = xn.lo;
         }
       }
+      r_current = false;
       proj_flops += (unsigned long long)(2 * nv + 2 * a) * (unsigned long long)N;
     }
   }
@@ -291,7 +304,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
       } else {
         float bv[EPT];
 #pragma unroll
-        for (int k = 0; k < EPT; ++k) bv[k] = (float)bval(tid + k * NT);
+        for (int k = 0; k < EPT; ++k) bv[k] = bhi(tid + k * NT);
         block_partials_f32x<NT>(nv, [&](int i) {
           const float* vi = Vs + (size_t)i * p.slot_ld;
           float s = 0.f;
@@ -309,6 +322,8 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
         const double* rot = p.slotRot + (size_t)sl * 3 * p.max_a;
         solve_projected_warp(hb, a, mt.nrot, p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a,
                              p.max_a + 1, rot, rot + 2 * p.max_a, lane);
+        __syncwarp();
+        for (int i = lane; i < a; i += 32) red32[i] = (float)hb[i];   // alpha in FP32, converted once
       }
       __syncthreads();
 #pragma unroll
@@ -316,8 +331,9 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
         const int l = tid + k * NT;
         if (l < SL) {
           float xv = 0.f;
-          for (int i = 0; i < a; ++i) xv = fmaf((float)hb[i], Vs[(size_t)i * p.slot_ld + l], xv);
-          xs[l] = (double)xv;
+          for (int i = 0; i < a; ++i) xv = fmaf(red32[i], Vs[(size_t)i * p.slot_ld + l], xv);
+          xh[l] = xv;
+          xl[l] = 0.f;
         }
       }
       proj_flops = (unsigned long long)(2 * nv + 2 * a) * (unsigned long long)N;
@@ -326,26 +342,26 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
   cluster.sync();                                 // x slices visible cluster-wide
   if (p.x0_mode == X0_ZERO) {
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) r[k] = bval(tid + k * NT);
-  } else {
+    for (int k = 0; k < EPT; ++k) r[k] = bhi(tid + k * NT);
+  } else if (!r_current) {
     residual();
   }
-  block_partials<NT>(2, [&](int i) {
-    double s = 0.0;
+  block_partials_f32x<NT>(2, [&](int i) {
+    float s = 0.f;
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
-      const double bv = bval(tid + k * NT);
-      s += (i == 0) ? bv * bv : r[k] * r[k];
+      const float v = (i == 0) ? bhi(tid + k * NT) : r[k];
+      s = fmaf(v, v, s);
     }
     return s;
-  }, red);
-  cluster_sum(2, false);
+  }, red32);
+  cluster_sum(2, true);
   const double bnorm = sqrt(hb[0]);
   double beta = sqrt(hb[1]);
   int steps = 0, status = KP_NOT_CONVERGED, outer = 0;
   if (bnorm == 0.0) {
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) xs[tid + k * NT] = 0.0;
+    for (int k = 0; k < EPT; ++k) xh[tid + k * NT] = xl[tid + k * NT] = 0.f;
     beta = 0.0;
     status = KP_OK;
   }
@@ -357,12 +373,12 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
     const bool first = (outer == 0);
     const double target = (capture && first) ? p.tol * bnorm : fmax(kEta * beta, 0.1 * p.tol * bnorm);
     {
-      const double ib = 1.0 / beta;
+      const float ib = (float)(1.0 / beta);
       float* v0 = vloc(0);
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
         const int l = tid + k * NT;
-        const float v = (float)(r[k] * ib);
+        const float v = r[k] * ib;
         v0[l] = v;
         if (capture && first && l < SL) {
           capV[base + l] = v;
@@ -499,7 +515,10 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
       for (int i = kdone - 1; i >= 0; --i) {
         const double gi = __shfl_sync(kFull, i < 32 ? g0 : g1, i & 31);
         const double yi = gi * rinv[i];
-        if (lane == 0) yv[i] = yi;
+        if (lane == 0) {
+          yv[i] = yi;
+          red32[i] = (float)yi;                     // y in FP32 for the update, converted once
+        }
         if (lane < i) g0 = fma(-Hr[lane + i * ld], yi, g0);
         if (lane + 32 < i) g1 = fma(-Hr[(lane + 32) + i * ld], yi, g1);
       }
@@ -530,18 +549,20 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
     for (int k = 0; k < EPT; ++k) {
       const int l = tid + k * NT;
       float dv = 0.f;
-      for (int i = 0; i < kdone; ++i) dv = fmaf((float)yv[i], vloc(i)[l], dv);
-      xs[l] += (double)dv;
+      for (int i = 0; i < kdone; ++i) dv = fmaf(red32[i], vloc(i)[l], dv);
+      const dd xn = dd_add_f(dd{xh[l], xl[l]}, dv);
+      xh[l] = xn.hi;
+      xl[l] = xn.lo;
     }
     cluster.sync();                               // x slices visible cluster-wide
     residual();
-    block_partials<NT>(1, [&](int) {
-      double s = 0.0;
+    block_partials_f32x<NT>(1, [&](int) {
+      float s = 0.f;
 #pragma unroll
-      for (int k = 0; k < EPT; ++k) s += r[k] * r[k];
+      for (int k = 0; k < EPT; ++k) s = fmaf(r[k], r[k], s);
       return s;
-    }, red);
-    cluster_sum(1, false);
+    }, red32);
+    cluster_sum(1, true);
     beta = sqrt(hb[0]);
     ++outer;
   }
@@ -562,9 +583,9 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
   for (int k = 0; k < EPT; ++k) {
     const int l = tid + k * NT;
     if (l < SL) {
-      d.x[base + l] = xs[l];
+      d.x[base + l] = dd_to_double(dd{xh[l], xl[l]});
       if (p.bnext)
-        p.bnext[(size_t)sysi * p.bnext_ld + base + l] = __float2bfloat16_rn((float)xs[l]);
+        p.bnext[(size_t)sysi * p.bnext_ld + base + l] = __float2bfloat16_rn(xh[l]);
     }
   }
   if (tid == 0 && rank == 0) {

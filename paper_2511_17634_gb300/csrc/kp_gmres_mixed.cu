@@ -242,6 +242,8 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
           const double* rot = p.slotRot + (size_t)sl * 3 * p.max_a;
           solve_projected_warp(sm.hb, a, mt.nrot, p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a,
                                p.max_a + 1, rot, rot + 2 * p.max_a, lane);
+          __syncwarp();
+          for (int i = lane; i < a; i += 32) red32[i] = (float)sm.hb[i];   // alpha in FP32, converted once
         }
         __syncthreads();
 #pragma unroll
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
           const int pp = tid + k * NT;
           if (pp < N) {
             float xv = 0.f;
-            for (int i = 0; i < a; ++i) xv = fmaf((float)sm.hb[i], V[(size_t)i * p.slot_ld + pp], xv);
+            for (int i = 0; i < a; ++i) xv = fmaf(red32[i], V[(size_t)i * p.slot_ld + pp], xv);
             sm.xs[pp] += (double)xv;
           }
         }
@@ -291,6 +293,8 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
           const double* rot = p.slotRot + (size_t)sl * 3 * p.max_a;
           solve_projected_warp(sm.hb, a, mt.nrot, p.slotR + (size_t)sl * (p.max_a + 1) * p.max_a,
                                p.max_a + 1, rot, rot + 2 * p.max_a, lane);
+          __syncwarp();
+          for (int i = lane; i < a; i += 32) red32[i] = (float)sm.hb[i];   // alpha in FP32, converted once
         }
         __syncthreads();
 #pragma unroll
@@ -298,7 +302,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
           const int pp = tid + k * NT;
           if (pp < N) {
             float xv = 0.f;
-            for (int i = 0; i < a; ++i) xv = fmaf((float)sm.hb[i], V[(size_t)i * p.slot_ld + pp], xv);
+            for (int i = 0; i < a; ++i) xv = fmaf(red32[i], V[(size_t)i * p.slot_ld + pp], xv);
             sm.xs[pp] = (double)xv;
           }
         }
@@ -502,7 +506,10 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
         for (int i = kdone - 1; i >= 0; --i) {
           const double gi = __shfl_sync(kFull, i < 32 ? g0 : g1, i & 31);
           const double yi = gi * sm.rinv[i];
-          if (lane == 0) sm.y[i] = yi;
+          if (lane == 0) {
+            sm.y[i] = yi;
+            red32[i] = (float)yi;                   // y in FP32 for the update, converted once
+          }
           if (lane < i) g0 = fma(-sm.Hr[lane + i * ld], yi, g0);
           if (lane + 32 < i) g1 = fma(-sm.Hr[(lane + 32) + i * ld], yi, g1);
         }
@@ -536,7 +543,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
       for (int k = 0; k < EPT; ++k) {
         const int pp = tid + k * NT;
         float dv = 0.f;
-        for (int i = 0; i < kdone; ++i) dv = fmaf((float)sm.y[i], slot(i)[pp], dv);
+        for (int i = 0; i < kdone; ++i) dv = fmaf(red32[i], slot(i)[pp], dv);
         sm.xs[pp] += (double)dv;
       }
       __syncthreads();

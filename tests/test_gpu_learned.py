@@ -65,6 +65,47 @@ def _richardson_net(kp, ctx, H, W, B):
     return net
 
 
+def test_pack_inputs_match_oracle_planes(kp, orc):
+    # the ten input planes at the learned-guess workload's grid against
+    # cnn_oracle.network_inputs: the GPU splits the FP32 value of each field
+    # (the oracle the FP64 one) and computes the step residual in
+    # double-float; the hi planes are the same BF16 values, the lo planes
+    # after the network's BF16 rounding differ in about 1 % of the pixels by
+    # one lo ulp (or by the FP32 rounding of the field where that is all the
+    # lo plane holds), rho agrees to 1e-9, the residual planes recombine to
+    # r_hat within the lo plane's resolution
+    from oracle import cnn_oracle as R
+    from paper_2511_17634_gb300 import learned
+    wl = synth.config(5, T=1000, ntargets=2)
+    g = wl.groups[0]
+    H, W, N, T = g.H, g.W, g.N, wl.T
+    n = 700
+    g2n = float(wl.g2[n - 1])
+    mt = g.targets.reshape(len(g.targets), -1)
+    ms = g.seeds.reshape(len(g.seeds), -1)[np.asarray(g.target_seed)]
+    B = len(mt)
+    ctx = kp.Context(max_n=N)
+    net = kp.CNN(ctx, H, W, channels=learned.CHANNELS, max_batch=B)
+    x = torch.empty((B, R.NIN, N), dtype=torch.float32, device="cuda")
+    rho = torch.empty(B, dtype=torch.float64, device="cuda")
+    net.pack_inputs(_dev(mt), [_dev(ms[k]) for k in range(B)], n, T, g2n, x, rho)
+    torch.cuda.synchronize()
+    xg, rg = x.cpu().numpy().astype(np.float64), rho.cpu().numpy()
+    xo, ro = R.network_inputs(mt, ms, n, T, g2n, H, W)
+    assert np.abs(rg - ro).max() <= 1e-9 * ro.max()
+    for k, field in ((0, mt), (2, ms)):
+        assert np.array_equal(xg[:, k], xo[:, k])
+        # one lo ulp where 256 (f - hi) is a BF16 tie, or 256 |m - f| where
+        # the FP32 rounding of m decides the lo plane alone (f - hi = 0)
+        lo_o = R.bf16(xo[:, k + 1])
+        assert (xg[:, k + 1] != lo_o).mean() <= 2e-2
+        assert np.all(np.abs(xg[:, k + 1] - lo_o) <= 2.0 ** -7 * np.abs(lo_o) + 2.0 ** -15 * np.abs(field))
+        assert np.abs(xg[:, k] + xg[:, k + 1] / 256 - field).max() <= 2.0 ** -16 * np.abs(field).max()
+    assert np.allclose(xg[:, 4:8], xo[:, 4:8], rtol=0, atol=3e-7)
+    rh = xo[:, 8] + xo[:, 9] / 256
+    assert np.abs(xg[:, 8] + xg[:, 9] / 256 - rh).max() <= 2.0 ** -15 * np.abs(rh).max()
+
+
 def test_learned_march_guess_and_projection_match_oracle(kp, orc):
     # one timestep with the targets capped at 0 Arnoldi steps (the seeds
     # solve): the targets' states after the step are their starts -- the
