@@ -351,7 +351,11 @@ typedef enum {
   KP_MARCH_PLAIN = 1,       /* x0 = 0                                                      */
   KP_MARCH_WARM = 2,        /* x0 = m^{n-1}                                                */
   KP_MARCH_GALERKIN = 3,    /* exact Galerkin with the target's own operator:
-                               x0 = V_a (V_a^T A_i V_a)^{-1} V_a^T b (FP64 plans only)    */
+                               x0 = V_a (V_a^T A_i V_a)^{-1} V_a^T b.  FP64 plans: G in the
+                               solver; mixed precision (grids <= 4096 points, max_a + 1 <=
+                               48): G = G0(seed basis) + Q_i P^T, the target's coefficient
+                               row times the basis products on the tensor cores (BF16,
+                               FP32 accumulation), c = V^T b likewise                     */
   KP_MARCH_LEARNED = 4,     /* the learned guess projected in residual form: x_init =
                                m^{n-1} + dt rho net(m^{n-1}, m_seed^n, time, r / rho)
                                (inputs as in kp_cnn_pack_inputs), x0 = x_init +

@@ -309,6 +309,45 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
         proj_flops = (unsigned long long)(2 * nv + 2 * a) * (unsigned long long)N;
       }
     }
+    if (p.x0_mode == X0_GALERKIN && p.gram) {
+      // Sec. 3, Phase 2 without the seed-matrix shortcut: G alpha = V_a^T b
+      // with G = V_a^T A_i V_a of this target's own operator, assembled from
+      // the seed basis part G0 and this target's tensor-core part (kp_gram.cu),
+      // x0 = V_a alpha; c = V^T b from the projection GEMM
+      const int sl = d.slot + parity_base;
+      const SlotMeta mt = p.slotMeta[sl];
+      const int a = mt.a, A = p.gram_a;
+      if (mt.timestep == tstep && mt.N == N && a > 0 && a <= A && a * a <= (m + 1) * m && p.cproj) {
+        const float* V = p.slotV32 + (size_t)sl * (p.max_a + 1) * p.slot_ld;
+        const float* g0 = p.gram0 + (size_t)sl * A * A;
+        const float* gi = p.gram + (size_t)sysi * A * A;
+        double* G = sm.Hr;                          // a x a, column-major: G[l + k a] = v_l^T A v_k
+        for (int e = tid; e < a * a; e += NT) {
+          const int l = e % a, k = e / a;
+          G[e] = (double)g0[l * A + k] + (double)gi[l * A + k];
+        }
+        if (tid < a) sm.hb[tid] = (double)p.cproj[(size_t)sysi * p.cproj_ld + tid];
+        __syncthreads();
+        if (warp == 0) {
+          const bool ok = lu_solve_warp(G, a, sm.hb, lane);
+          for (int i = lane; i < a; i += 32) red32[i] = (float)sm.hb[i];
+          if (lane == 0) sm.fl[5] = ok;
+        }
+        __syncthreads();
+        if (sm.fl[5]) {
+#pragma unroll
+          for (int k = 0; k < EPT; ++k) {
+            const int pp = tid + k * NT;
+            if (pp < N) {
+              float xv = 0.f;
+              for (int i = 0; i < a; ++i) xv = fmaf(red32[i], V[(size_t)i * p.slot_ld + pp], xv);
+              sm.xs[pp] = (double)xv;
+            }
+          }
+        }
+        proj_flops = (unsigned long long)(2 * a) * (unsigned long long)N;
+      }
+    }
     __syncthreads();
     if (p.x0_mode == X0_ZERO) {
 #pragma unroll

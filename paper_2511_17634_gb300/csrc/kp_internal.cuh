@@ -137,6 +137,12 @@ struct GmresParams {
   int pdl;                  // programmatic launch, bit 0: let the stream's next launch
                             // start at once; bit 1: launched that way, wait for the
                             // prior grid (its completion and memory) before exiting
+  // exact Galerkin in mixed precision (X0_GALERKIN, one-block mixed solver):
+  // G_i[p][q] = gram0[slot][p * gram_a + q] + gram[target][p * gram_a + q]
+  // (kp_gram.cu), c = V^T b in cproj
+  const float* gram0;
+  const float* gram;
+  int gram_a;
 };
 
 constexpr int kWaitLimit = 1 << 22;   // polls (>= 256 ns apart) before a wait gives up
@@ -606,6 +612,30 @@ size_t proj_gemm_smem_bytes();
 // Tensor map of a row-major BF16 matrix (rows x cols, row stride ld elements)
 // read in boxes of box_rows x 64 with 128-byte swizzle.
 cudaError_t make_bf16_map(void* map, const void* base, int rows, int cols, int ld, int box_rows);
+// Target Gram matrices of exact Galerkin projection in mixed precision
+// (kp_gram.cu): per timestep, the product rows P and G0 of every seed basis of
+// the timestep's slot set, and the coefficient rows Q of every target; the
+// GEMM C = Q P^T runs on launch_proj_gemm_bf16.
+struct GramParams {
+  const SysDesc* seeds;       // [ns] grid of each seed (slot index within the set)
+  const SysDesc* targets;     // [nt]
+  int ns, nt;
+  int A;                      // Gram dimension bound (pairs p * A + q)
+  int max_a, slot_ld, max_n;
+  const int* step;            // current target timestep (device counter)
+  const double* g2_sched;
+  double b_scale;
+  const SlotMeta* slotMeta;
+  const float* slotV32;
+  __nv_bfloat16* Pb;          // [2 ns A^2][p_ld] rows v_p o Dx v_q | v_p o Dy v_q
+  int p_ld;
+  float* G0;                  // [2 ns][A^2]
+  __nv_bfloat16* Qb;          // [nt][q_ld] rows qx_i | qy_i
+  int q_ld;
+};
+cudaError_t launch_gram_products(const GramParams& gp, cudaStream_t st);
+cudaError_t launch_gram_coeff(const GramParams& gp, cudaStream_t st);
+
 cudaError_t launch_proj_gemm_bf16(const CUtensorMap& mapB, const CUtensorMap& mapV,
                                   const ProjTile* tiles, int ntiles, int K, float* C, int ldc,
                                   int* err, int grid, cudaStream_t st);

@@ -72,6 +72,16 @@ struct kp_march_plan {
   std::vector<CUtensorMap> mapB, mapV;       // per group
   int* err = nullptr;
   int gemm_grid = 0;
+  // exact Galerkin in mixed precision: per-timestep Gram matrices with the
+  // target-dependent part on the tensor cores (kp_gram.cu)
+  int gram_A = 0, p_ld = 0, q_ld = 0;
+  __nv_bfloat16* Pb = nullptr;               // [2 ns A^2][p_ld] product rows of the seed bases
+  float* G0 = nullptr;                       // [2 ns][A^2]
+  __nv_bfloat16* Qb = nullptr;               // [nt][q_ld] coefficient rows of the targets
+  float* Cg = nullptr;                       // [nt][A^2] = Q P^T
+  kp::ProjTile* gtiles[2] = {nullptr, nullptr};
+  std::vector<int> gtile_off, gtile_cnt;     // per group
+  std::vector<CUtensorMap> mapQ, mapP;       // per group
   SysDesc* desc[2] = {nullptr, nullptr};     // per parity p: seeds (step n+1), targets (step n)
   kp::Shape shS, shT;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -207,6 +217,11 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset,
       g.bnext = P->Bb;                       // BF16 b of the next timestep
       g.bnext_ld = c->vb_ld;
     }
+    if (P->G0) {
+      g.gram0 = P->G0;                       // Galerkin: G = G0 (seed basis) + C (target)
+      g.gram = P->Cg;
+      g.gram_a = P->gram_A;
+    }
   }
   return g;
 }
@@ -262,6 +277,43 @@ cudaError_t enqueue_guess(kp_march_plan* P, int par, int* nl) {
   return e;
 }
 
+// Exact Galerkin in mixed precision, targets of step n (parity par): the
+// product rows and G0 of the step's seed bases, the targets' coefficient rows,
+// and C = Q P^T per group on the tensor cores.
+cudaError_t enqueue_gram(kp_march_plan* P, int par, int* nl) {
+  kp_ctx* c = P->ctx;
+  kp::GramParams gp{};
+  gp.seeds = P->desc[par];
+  gp.targets = P->desc[par] + P->ns;
+  gp.ns = P->ns;
+  gp.nt = P->nt;
+  gp.A = P->gram_A;
+  gp.max_a = c->opt.max_a;
+  gp.slot_ld = c->opt.max_n;
+  for (const kp_group& g : P->groups) gp.max_n = std::max(gp.max_n, g.H * g.W);
+  gp.step = P->step;
+  gp.g2_sched = P->g2;
+  gp.b_scale = (double)P->opt.T;
+  gp.slotMeta = c->slotMeta;
+  gp.slotV32 = c->slotV32;
+  gp.Pb = P->Pb;
+  gp.p_ld = P->p_ld;
+  gp.G0 = P->G0;
+  gp.Qb = P->Qb;
+  gp.q_ld = P->q_ld;
+  cudaError_t e = kp::launch_gram_products(gp, P->st);
+  if (e == cudaSuccess) e = kp::launch_gram_coeff(gp, P->st);
+  *nl += 2;
+  for (size_t gi = 0; gi < P->groups.size() && e == cudaSuccess; ++gi) {
+    if (!P->gtile_cnt[gi]) continue;
+    e = kp::launch_proj_gemm_bf16(P->mapQ[gi], P->mapP[gi], P->gtiles[par] + P->gtile_off[gi], P->gtile_cnt[gi],
+                                  2 * P->groups[gi].H * P->groups[gi].W, P->Cg, P->gram_A * P->gram_A, P->err,
+                                  std::min(P->gtile_cnt[gi], P->gemm_grid), P->st);
+    ++*nl;
+  }
+  return e;
+}
+
 // Target step n and seed step n+1 for parity p = n & 1.  With ev (timing
 // mode) the launches run one after the other between events ev[0..1]
 // (seeds), ev[4..5] (learned guess) and ev[2..3] (targets); otherwise seeds
@@ -300,6 +352,7 @@ kp_status enqueue_step(kp_march_plan* P, int par, cudaEvent_t* ev, int* launches
         ++nl;
       }
     }
+    if (P->G0 && e == cudaSuccess) e = enqueue_gram(P, par, &nl);
     kp::GmresParams g = solver_params(P, false, par, 0);
     if (e == cudaSuccess) e = launch_solver(P, g, P->cls[0].sh, P->st);
     ++nl;
@@ -389,6 +442,12 @@ kp_status kp_march_destroy(kp_march_plan* P) {
   cudaFree(P->Cp);
   cudaFree(P->tiles[0]);
   cudaFree(P->tiles[1]);
+  cudaFree(P->Pb);
+  cudaFree(P->G0);
+  cudaFree(P->Qb);
+  cudaFree(P->Cg);
+  cudaFree(P->gtiles[0]);
+  cudaFree(P->gtiles[1]);
   cudaFree(P->err);
   cudaFree(P->queue);
   cudaFree(P->done);
@@ -457,9 +516,19 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
     kp_march_destroy(P);
     return kp::set_error(c, KP_ERR_UNSUPPORTED, "Picard iterations need the FP64 one-block solver");
   }
-  if (o.mode == KP_MARCH_GALERKIN && (P->mixed || P->shT.cs)) {
+  if (o.mode == KP_MARCH_GALERKIN && P->mixed) {
+    // mixed precision: the Gram matrices on the tensor cores (kp_gram.cu) for
+    // the one-block solver's grids (<= 4096 points)
+    bool ok = !P->shT.cs && c->opt.max_a + 1 <= kp::kVbRows && c->opt.max_a <= kp::kMaxV;
+    for (int gi = 0; gi < ngroups; ++gi) ok = ok && groups[gi].H * groups[gi].W <= 4096;
+    if (!ok) {
+      kp_march_destroy(P);
+      return kp::set_error(c, KP_ERR_UNSUPPORTED, "mixed-precision exact Galerkin needs grids of <= 4096 points "
+                           "(one-block solver) and max_a + 1 <= %d", kp::kVbRows);
+    }
+  } else if (o.mode == KP_MARCH_GALERKIN && P->shT.cs) {
     kp_march_destroy(P);
-    return kp::set_error(c, KP_ERR_UNSUPPORTED, "exact Galerkin projection needs the FP64 one-block solver");
+    return kp::set_error(c, KP_ERR_UNSUPPORTED, "exact Galerkin projection needs a one-block solver");
   }
   if (o.seed_solver != KP_SEED_GMRES &&
       (o.seed_solver != KP_SEED_BICGSTAB || P->mixed || P->shS.cs || P->shT.cs || o.picard > 1 ||
@@ -701,8 +770,8 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
     }
   }
   if (e == cudaSuccess) e = cudaMemcpy(P->g2, o.g2, o.T * sizeof(double), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && P->mixed && o.mode == KP_MARCH_PROJECTED && ns > 0 && nt > 0 &&
-      c->opt.max_a + 1 <= kp::kVbRows) {
+  if (e == cudaSuccess && P->mixed && (o.mode == KP_MARCH_PROJECTED || o.mode == KP_MARCH_GALERKIN) && ns > 0 &&
+      nt > 0 && c->opt.max_a + 1 <= kp::kVbRows) {
     // tensor-core projection: BF16 right-hand sides, c = V^T b, tile lists
     const int vb_ld = c->vb_ld;
     e = dmalloc(&P->Bb, (size_t)nt * vb_ld);
@@ -748,6 +817,66 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
       e = dmalloc(&P->tiles[par], tl[par].size());
       if (e == cudaSuccess)
         e = cudaMemcpy(P->tiles[par], tl[par].data(), tl[par].size() * sizeof(kp::ProjTile),
+                       cudaMemcpyHostToDevice);
+    }
+    P->gemm_grid = c->sms;
+  }
+  if (e == cudaSuccess && P->mixed && o.mode == KP_MARCH_GALERKIN && ns > 0 && nt > 0) {
+    // Gram matrices: product rows of the seed bases (pairs p * A + q, both
+    // slot sets), coefficient rows of the targets, C = Q P^T tiles per run of
+    // targets sharing a seed and per 48 pairs
+    const int A = c->opt.max_a;
+    int nmax = 0;
+    for (int gi = 0; gi < ngroups; ++gi) nmax = std::max(nmax, groups[gi].H * groups[gi].W);
+    P->gram_A = A;
+    P->p_ld = P->q_ld = (2 * nmax + 7) / 8 * 8;
+    const size_t pairs = (size_t)A * A;
+    e = dmalloc(&P->Pb, (size_t)2 * ns * pairs * P->p_ld);
+    if (e == cudaSuccess) e = cudaMemset(P->Pb, 0, (size_t)2 * ns * pairs * P->p_ld * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = dmalloc(&P->G0, (size_t)2 * ns * pairs);
+    if (e == cudaSuccess) e = dmalloc(&P->Qb, (size_t)nt * P->q_ld);
+    if (e == cudaSuccess) e = cudaMemset(P->Qb, 0, (size_t)nt * P->q_ld * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = dmalloc(&P->Cg, (size_t)nt * pairs);
+    std::vector<kp::ProjTile> tl[2];
+    int seed_base = 0;
+    P->mapQ.resize(ngroups);
+    P->mapP.resize(ngroups);
+    for (int gi = 0; gi < ngroups && e == cudaSuccess; ++gi) {
+      const kp_group& g = groups[gi];
+      const int K2 = 2 * g.H * g.W;
+      P->gtile_off.push_back((int)tl[0].size());
+      int k = 0;
+      while (k < g.ntgt) {
+        const int sd = g.tgt_seed[hperm[P->tgt_base[gi] + k]];
+        int end = k;
+        while (end < g.ntgt && g.tgt_seed[hperm[P->tgt_base[gi] + end]] == sd) ++end;
+        for (int q = k; q < end; q += 128)
+          for (int pb = 0; pb < (int)pairs; pb += 48)
+            for (int par = 0; par < 2; ++par) {
+              kp::ProjTile t;
+              t.row0 = q;
+              t.vrow0 = (int)((size_t)(par * ns + seed_base + sd) * pairs) + pb;
+              t.crow0 = P->tgt_base[gi] + q;
+              t.count = std::min(128, end - q);
+              t.nv = std::min(48, (int)pairs - pb);
+              t.ccol0 = pb;
+              t.kc0 = t.kc1 = 0;
+              t.atomic = 0;
+              tl[par].push_back(t);
+            }
+        k = end;
+      }
+      P->gtile_cnt.push_back((int)tl[0].size() - P->gtile_off.back());
+      if (g.ntgt) e = kp::make_bf16_map(&P->mapQ[gi], P->Qb + (size_t)P->tgt_base[gi] * P->q_ld, g.ntgt, K2,
+                                        P->q_ld, 128);
+      if (e == cudaSuccess)
+        e = kp::make_bf16_map(&P->mapP[gi], P->Pb, (int)(2 * ns * pairs), K2, P->p_ld, 48);
+      seed_base += g.nseed;
+    }
+    for (int par = 0; par < 2 && e == cudaSuccess; ++par) {
+      e = dmalloc(&P->gtiles[par], tl[par].size());
+      if (e == cudaSuccess)
+        e = cudaMemcpy(P->gtiles[par], tl[par].data(), tl[par].size() * sizeof(kp::ProjTile),
                        cudaMemcpyHostToDevice);
     }
     P->gemm_grid = c->sms;
