@@ -112,7 +112,9 @@ def parse(argv=None):
                     help="g^2 schedule: linear beta 1e-4..0.02 (workloads, default) or the paper's "
                          "constant g = 0.5")
     ap.add_argument("--cluster-size", type=int, default=0,
-                    help="mixed precision: CTAs per system (2, 4, 8) also for grids of <= 4096 points")
+                    help="mixed precision: CTAs per system (2, 4, 8, 16; also for grids of <= 4096 points)")
+    ap.add_argument("--cluster-blocks-per-sm", type=int, default=0,
+                    help="cluster solver: resident CTAs per SM (1, 2; 16-CTA clusters 2, 4; 0 = default)")
     ap.add_argument("--train-epochs", type=int, default=16,
                     help="learned-guess workload: epochs over the ~2000 training pairs")
     ap.add_argument("--inference-batch", type=int, default=4096,
@@ -479,7 +481,8 @@ def run_north_star(args):
     # cancellation (measured 8 % faster than CGS2 at the same steps per solve)
     reorth = 1 if args.reorth is None else args.reorth
     ctx = kp.Context(max_seeds=2 * ns_planes, max_a=wl0.a, max_n=wl0.groups[0].N, precision=kp.PREC_MIXED,
-                     inner_digits=args.inner_digits, reorth=reorth)
+                     inner_digits=args.inner_digits, reorth=reorth, cluster_size=args.cluster_size,
+                     cluster_blocks_per_sm=args.cluster_blocks_per_sm)
     if ALU_PEAK_SOURCE.startswith("derived"):
         set_alu_peaks(ctx)
     wl, g, net, train_info = learned_setup(kp, ctx, args, rank)
@@ -929,9 +932,9 @@ def bench_small(args, dist, init=False):
                                                      "iters_per_solve": tgt_iters / (nt_planes * NS)}
         out["basis_dimension_sweep"] = sweep
     if not args.no_baselines:
-        modes = [("plain_x0_zero", kp.MARCH_PLAIN), ("plain_warm_start", kp.MARCH_WARM)]
-        if not mixed:
-            modes.append(("projected_exact_galerkin", kp.MARCH_GALERKIN))
+        # exact Galerkin: FP64 Gram in the solver, or (mixed) the tensor-core Gram
+        modes = [("plain_x0_zero", kp.MARCH_PLAIN), ("plain_warm_start", kp.MARCH_WARM),
+                 ("projected_exact_galerkin", kp.MARCH_GALERKIN)]
         for name, mode in modes:
             pl = kp.March(ctx, groups, mode=mode, **common)
             t = timed(pl, max(1, args.steps // 2), 1)

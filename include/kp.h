@@ -80,9 +80,11 @@ typedef struct {
                         or 4; 64: 4; 0 = the default above (2 for an explicit
                         256 or 128, 4 for 64).  Mixed precision: 2 always.   */
   int cluster_size;  /* mixed precision, grids of 1025..16384 points: solve each
-                        system on a cluster of this many CTAs (2, 4 or 8; W
-                        divisible by it, <= 2048 points per CTA); 0 = clusters
-                        only above 4096 points (one 512-thread block below) */
+                        system on a cluster of this many CTAs (2, 4 or 8 of 256
+                        threads, <= 2048 points per CTA; or 16 of 128 threads,
+                        <= 1024 points per CTA -- a non-portable cluster size;
+                        W divisible by it); 0 = clusters only above 4096 points
+                        (one 512-thread block below), of 2, 4 or 8 CTAs      */
   int fixed_a;       /* basis dimension of the seed solves (Sec. 3: V_a^n spans
                         the a-dimensional Krylov space; Sec. 5.2 uses a = 20):
                         0 = the first restart cycle ends when the seed meets its
@@ -97,8 +99,10 @@ typedef struct {
                         the FP64 iterative refinement recomputes the true
                         residual; 1..7, 0 = 5                                     */
   int cluster_blocks_per_sm; /* cluster solver (grids above 4096 points): resident
-                        CTAs per SM, 1 or 2; 0 = 2 (two systems share the SMs, a
-                        smaller shared-memory window of Krylov vectors)          */
+                        CTAs per SM, 1 or 2 (16-CTA clusters: 2 or 4); 0 = 2
+                        (16-CTA clusters: 4) -- several systems share the SMs,
+                        each with a smaller shared-memory window of Krylov
+                        vectors                                                  */
 } kp_options;
 
 /* Operator of one system (Sec. 2.3): A(m~; g^2, dt, h, f).  `mtilde` is the

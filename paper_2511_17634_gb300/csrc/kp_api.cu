@@ -60,17 +60,20 @@ kp_status gmres_shape(kp_ctx* c, int nmax, int m, Shape* out, bool mixed, int wm
   }
   else if (nmax <= 4096 && !(mixed && c->opt.cluster_size)) { sh.ept = 8; sh.nt = 512; }
   else if (mixed) {
-    // a cluster of cs CTAs, each holding W/cs whole columns (<= 2048 points)
-    sh.ept = 8; sh.nt = 256;
+    // a cluster of cs CTAs, each holding W/cs whole columns (<= 2048 points;
+    // 16-CTA clusters: 128 threads and <= 1024 points per CTA)
+    sh.ept = 8; sh.nt = c->opt.cluster_size == 16 ? 128 : 256;
     if (c->opt.cluster_size) {
-      if ((nmax + c->opt.cluster_size - 1) / c->opt.cluster_size <= 2048) sh.cs = c->opt.cluster_size;
+      if ((nmax + c->opt.cluster_size - 1) / c->opt.cluster_size <= sh.ept * sh.nt) sh.cs = c->opt.cluster_size;
     } else {
       for (int cs : {2, 4, 8})
         if ((nmax + cs - 1) / cs <= 2048) { sh.cs = cs; break; }
     }
     if (!sh.cs || wmin <= 0 || wmin % sh.cs)
       return set_error(c, KP_ERR_UNSUPPORTED, "N=%d: needs W divisible by the cluster size and N <= 16384", nmax);
-    sh.minb = c->opt.cluster_blocks_per_sm ? c->opt.cluster_blocks_per_sm : 2;
+    sh.minb = c->opt.cluster_blocks_per_sm ? c->opt.cluster_blocks_per_sm : (sh.cs == 16 ? 4 : 2);
+    if (sh.cs == 16 ? (sh.minb != 2 && sh.minb != 4) : sh.minb > 2)
+      return set_error(c, KP_ERR_UNSUPPORTED, "cluster of %d CTAs: %d CTAs per SM not built", sh.cs, sh.minb);
   }
   else return set_error(c, KP_ERR_UNSUPPORTED, "N=%d: FP64 grids above 4096 unknowns are not supported (use the mixed-precision mode)", nmax);
   const int npad = sh.ept * sh.nt;
@@ -300,9 +303,10 @@ kp_status kp_create(kp_ctx** out, const kp_options* opt, void* stream) {
       (o.precision != KP_PREC_FP64 && o.precision != KP_PREC_MIXED) ||
       o.smem_vectors < 0 || (o.reorth != 0 && o.reorth != 1) ||
       (o.block_threads != 0 && o.block_threads != 64 && o.block_threads != 128 && o.block_threads != 256) ||
-      (o.cluster_size != 0 && o.cluster_size != 2 && o.cluster_size != 4 && o.cluster_size != 8) ||
+      (o.cluster_size != 0 && o.cluster_size != 2 && o.cluster_size != 4 && o.cluster_size != 8 &&
+       o.cluster_size != 16) ||
       (o.fixed_a != 0 && o.fixed_a != 1) || o.inner_digits < 0 || o.inner_digits > 7 ||
-      o.cluster_blocks_per_sm < 0 || o.cluster_blocks_per_sm > 2)
+      o.cluster_blocks_per_sm < 0 || o.cluster_blocks_per_sm > 4)
     return KP_ERR_ARG;
   {
     // solver shapes compiled for grids of <= 1024 points: (threads, blocks per SM)

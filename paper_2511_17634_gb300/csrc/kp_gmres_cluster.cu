@@ -627,6 +627,7 @@ cudaError_t launch_c(const GmresParams& p, size_t smem, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   if (smem > (size_t)optin) return cudaErrorInvalidValue;
   e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess && CS > 8) e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(p.nsys * CS));
@@ -656,7 +657,16 @@ size_t gmres_cluster_smem_bytes(int ept, int nt, int S, int m) {
 
 cudaError_t launch_gmres_cluster(const GmresParams& p, int ept, int nt, int cs, int minb, size_t smem,
                                  cudaStream_t st) {
-  if (ept != 8 || nt != 256) return cudaErrorInvalidValue;
+  if (ept != 8) return cudaErrorInvalidValue;
+  if (nt == 128) {
+    // 16-CTA clusters of 128 threads (1024 points per CTA): up to four
+    // systems' CTAs per SM
+    if (cs != 16) return cudaErrorInvalidValue;
+    if (minb == 4) return launch_c<8, 128, 16, 4>(p, smem, st);
+    if (minb == 2) return launch_c<8, 128, 16, 2>(p, smem, st);
+    return cudaErrorInvalidValue;
+  }
+  if (nt != 256) return cudaErrorInvalidValue;
   if (minb == 2) {
     if (cs == 8) return launch_c<8, 256, 8, 2>(p, smem, st);
     if (cs == 4) return launch_c<8, 256, 4, 2>(p, smem, st);
