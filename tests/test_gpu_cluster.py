@@ -87,3 +87,29 @@ def test_cluster_forced_on_64x64(kp, orc, cs):
         C = orc.coeffs(H, W, 0.02, 1e-3, 1 / H, mt[k])
         xr = x[k].cpu().numpy()
         assert np.linalg.norm(b[k] - orc.apply(H, W, C, xr)) <= 1.01e-10 * np.linalg.norm(b[k])
+
+
+@pytest.mark.parametrize("minb", [4, 2])
+def test_cluster_of_16_ctas_128x128(kp, orc, minb):
+    # kp_options.cluster_size = 16: 128-thread CTAs of 8 columns (1024 points)
+    # each, a non-portable cluster size, two or four systems' CTAs per SM;
+    # the same tolerance and solutions as the 8-CTA default
+    H = W = 128
+    N = H * W
+    rng = np.random.default_rng(16 + minb)
+    n = 3
+    mt = rng.uniform(0, 1, (n, N))
+    b = rng.normal(size=(n, N))
+    ctx = kp.Context(max_n=N, precision=kp.PREC_MIXED, cluster_size=16, cluster_blocks_per_sm=minb)
+    dm, db = _dev(mt), _dev(b)
+    ops = kp.make_ops(H, W, 1e-3, 0.02, 1 / H, dm)
+    x = torch.zeros_like(db)
+    it, st, rr = kp.decode_info(ctx.refine(ops, db, x, tol=1e-10, m=40, maxit=600))
+    torch.cuda.synchronize()
+    assert (st == 0).all() and (rr <= 1e-10).all(), (st, rr)
+    for k in range(n):
+        C = orc.coeffs(H, W, 0.02, 1e-3, 1 / H, mt[k])
+        xr = x[k].cpu().numpy()
+        assert np.linalg.norm(b[k] - orc.apply(H, W, C, xr)) <= 1.01e-10 * np.linalg.norm(b[k])
+        ref = orc.gmres(H, W, C, b[k], tol=1e-13, m=40, maxit=800)
+        assert np.linalg.norm(xr - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
