@@ -323,16 +323,6 @@ __global__ void march_pack_kernel(const double* const* mprev, const double* cons
   }
 }
 
-// x_b = m_i^{n-1} + dt rho_b * delta_b
-__global__ void march_guess_kernel(const float* delta, const double* const* mprev, double* const* x,
-                                   const double* rho, int T, int P) {
-  const int b = blockIdx.y;
-  const double s = rho[b] / (double)T;
-  const double* mp = mprev[b];
-  double* xb = x[b];
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x)
-    xb[p] = fma(s, (double)delta[(size_t)b * P + p], mp[p]);
-}
 
 }  // namespace
 
@@ -766,22 +756,18 @@ bool cnn_march_ready(const kp_cnn* n, int H, int W) {
 int cnn_inference_batch(const kp_cnn* n) { return n ? n->infB : 0; }
 
 cudaError_t cnn_enqueue_guess(kp_cnn* n, int B, const double* const* mprev, const double* const* mseed,
-                              double* const* x, const int* step, int step_offset, const double* g2, int T,
-                              cudaStream_t st) {
+                              float* delta, double* rho, const int* step, int step_offset, const double* g2,
+                              int T, cudaStream_t st) {
   if (B < 1 || B > n->infB) return cudaErrorInvalidValue;
   const dim3 grid(std::min((n->P + 255) / 256, 1024), B);
   // the FP32 residual goes through the network's output buffer, which the
-  // last layer overwrites afterwards
-  step_residual_rms_kernel<<<B, 256, 0, st>>>(mprev, n->H, n->W, 1.0 / T, 0.0, g2, step, step_offset, n->rho,
+  // packing kernel has read before any layer runs
+  step_residual_rms_kernel<<<B, 256, 0, st>>>(mprev, n->H, n->W, 1.0 / T, 0.0, g2, step, step_offset, rho,
                                               n->dout, (size_t)n->P);
-  march_pack_kernel<<<grid, 256, 0, st>>>(mprev, mseed, n->dout, step, step_offset, n->rho, T, n->H, n->W,
+  march_pack_kernel<<<grid, 256, 0, st>>>(mprev, mseed, n->dout, step, step_offset, rho, T, n->H, n->W,
                                           n->geo.halo, n->geo.Rp, n->pin);
   cudaError_t e = cudaGetLastError();
-  if (e == cudaSuccess) e = conv_layers(n, B, n->dout, st);
-  if (e == cudaSuccess) {
-    march_guess_kernel<<<grid, 256, 0, st>>>(n->dout, mprev, x, n->rho, T, n->P);
-    e = cudaGetLastError();
-  }
+  if (e == cudaSuccess) e = conv_layers(n, B, delta, st);
   return e;
 }
 

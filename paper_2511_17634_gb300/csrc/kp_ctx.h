@@ -94,12 +94,14 @@ cudaError_t launch_solver(const GmresParams& p, const Shape& sh, bool mixed, cud
 // Learned initial guess inside the time march (kp_cnn.cu): whether the
 // network can serve an H x W march (10 inputs, 1 output, implicit-GEMM
 // inference buffers), how many images one pass holds, and the enqueue of
-// x[b] = mprev[b] + dt rho_b net(mprev[b], mseed[b], time planes, r_hat) for B targets
-// (device pointer tables; timestep from the device counter).
+// the network's part of x[b] = mprev[b] + dt rho_b net(mprev[b], mseed[b],
+// time planes, r_hat) for B targets (device pointer tables; timestep from the
+// device counter): net -> delta[b * H W ..] (FP32) and rho_b -> rho[b]; the
+// solver forms x from them.
 bool cnn_march_ready(const kp_cnn* n, int H, int W);
 int cnn_inference_batch(const kp_cnn* n);
 cudaError_t cnn_enqueue_guess(kp_cnn* n, int B, const double* const* mprev, const double* const* mseed,
-                              double* const* x, const int* step, int step_offset, const double* g2, int T,
-                              cudaStream_t st);
+                              float* delta, double* rho, const int* step, int step_offset, const double* g2,
+                              int T, cudaStream_t st);
 
 }  // namespace kp

@@ -222,7 +222,21 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
       xl[l] = v.lo;
     }
   };
-  load_x(p.x0_mode == X0_READ || judge ? d.x : p.x0_mode == X0_WARM ? d.mt : nullptr);
+  if (p.gdelta && (p.x0_mode == X0_READ || judge)) {
+    // the learned guess x_init = m~ + dt rho net, from the network's FP32
+    // output, in double-float
+    const float s = (float)(p.grho[sysi] / p.gdiv);
+    const float* dl = p.gdelta + (size_t)sysi * p.gdelta_ld + base;
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int l = tid + k * NT;
+      const dd v = l < SL ? dd_add_f(dd_from_double(d.mt[base + l]), s * dl[l]) : dd{0.f, 0.f};
+      xh[l] = v.hi;
+      xl[l] = v.lo;
+    }
+  } else {
+    load_x(p.x0_mode == X0_READ || judge ? d.x : p.x0_mode == X0_WARM ? d.mt : nullptr);
+  }
   unsigned long long proj_flops = 0;
   float r[EPT];
   auto residual = [&]() { residual_of(r); };

@@ -179,7 +179,9 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
       const int pp = tid + k * NT;
       double x0 = 0.0;
       if (pp < N) {
-        if (p.x0_mode == X0_READ || p.x0_mode == X0_GUESS_PROJECT) x0 = d.x[pp];
+        if (p.gdelta && (p.x0_mode == X0_READ || p.x0_mode == X0_GUESS_PROJECT))   // learned guess
+          x0 = fma(p.grho[sysi] / p.gdiv, (double)p.gdelta[(size_t)sysi * p.gdelta_ld + pp], d.mt[pp]);
+        else if (p.x0_mode == X0_READ || p.x0_mode == X0_GUESS_PROJECT) x0 = d.x[pp];
         else if (p.x0_mode == X0_WARM) x0 = d.mt[pp];
       }
       sm.xs[pp] = x0;

@@ -143,6 +143,13 @@ struct GmresParams {
   const float* gram0;
   const float* gram;
   int gram_a;
+  // learned guess (X0_READ / X0_GUESS_PROJECT in a march): if gdelta is set,
+  // x_init of system s is m~ + (grho[s] / gdiv) gdelta[s * gdelta_ld + p]
+  // (the network's output in units of dt rho, gdiv = T), formed in the solver
+  const float* gdelta;
+  int gdelta_ld;
+  const double* grho;
+  double gdiv;
 };
 
 constexpr int kWaitLimit = 1 << 22;   // polls (>= 256 ns apart) before a wait gives up

@@ -111,12 +111,13 @@ struct kp_march_plan {
   double* cycR = nullptr;                    // [max_seeds][(max_a + 1) * max_a]
   kp::SlotMeta* cycMeta = nullptr;           // [max_seeds]
   float* cycS = nullptr;                     // [K * ns][max_a][max_n] FP32 workspace
-  // learned guess: per parity, device tables of the targets' m^{n-1}, their
-  // seeds' m_seed^n and the guess output (the solver's x), internal order
+  // learned guess: per parity, device tables of the targets' m^{n-1} and their
+  // seeds' m_seed^n, internal order
   kp_cnn* cnn = nullptr;
   const double** lg_prev[2] = {nullptr, nullptr};
   const double** lg_seed[2] = {nullptr, nullptr};
-  double** lg_x[2] = {nullptr, nullptr};
+  float* gdelta = nullptr;                   // [nt][H W] network output of the step's targets
+  double* grho = nullptr;                    // [nt] their step-residual rms
 };
 
 namespace {
@@ -222,6 +223,12 @@ kp::GmresParams solver_params(kp_march_plan* P, bool seeds, int par, int offset,
       g.gram = P->Cg;
       g.gram_a = P->gram_A;
     }
+    if (P->gdelta) {                         // learned guess: x_init = m + (rho / T) net
+      g.gdelta = P->gdelta;
+      g.gdelta_ld = P->groups[0].H * P->groups[0].W;
+      g.grho = P->grho;
+      g.gdiv = (double)P->opt.T;
+    }
   }
   return g;
 }
@@ -270,9 +277,10 @@ cudaError_t enqueue_guess(kp_march_plan* P, int par, int* nl) {
   const int B = kp::cnn_inference_batch(P->cnn);
   cudaError_t e = cudaSuccess;
   for (int c0 = 0; c0 < P->nt && e == cudaSuccess; c0 += B) {
+    const size_t plane = (size_t)P->groups[0].H * P->groups[0].W;
     e = kp::cnn_enqueue_guess(P->cnn, std::min(B, P->nt - c0), P->lg_prev[par] + c0, P->lg_seed[par] + c0,
-                              P->lg_x[par] + c0, P->step, 0, P->g2, P->opt.T, P->st);
-    *nl += 3 + 4;                            // residual rms, pack, four layers, x_init (four layers)
+                              P->gdelta + (size_t)c0 * plane, P->grho + c0, P->step, 0, P->g2, P->opt.T, P->st);
+    *nl += 2 + 4;                            // residual rms, pack, four layers (x_init in the solver)
   }
   return e;
 }
@@ -436,8 +444,9 @@ kp_status kp_march_destroy(kp_march_plan* P) {
   for (int k = 0; k < 2; ++k) {
     cudaFree(P->lg_prev[k]);
     cudaFree(P->lg_seed[k]);
-    cudaFree(P->lg_x[k]);
   }
+  cudaFree(P->gdelta);
+  cudaFree(P->grho);
   cudaFree(P->Bb);
   cudaFree(P->Cp);
   cudaFree(P->tiles[0]);
@@ -752,21 +761,20 @@ kp_status kp_march_create(kp_ctx* c, int ngroups, const kp_group* groups, const 
     if (e == cudaSuccess && P->cnn) {
       // learned guess tables: target k reads m^{n-1} (its descriptor's lagged
       // field) and the m_seed^n that the seeds of the previous launch wrote to
-      // S[1 - par]; the guess goes to the solver's output planes
+      // S[1 - par]; the network's output goes to gdelta, from which the
+      // solver forms x_init
       std::vector<const double*> hp(nt), hs(nt);
-      std::vector<double*> hx(nt);
       for (int k = 0; k < nt; ++k) {
         const SysDesc& d = hd[(size_t)ns + k];
         hp[k] = d.mt;
-        hx[k] = d.x;
         hs[k] = P->S[1 - par] + (size_t)d.slot * groups[0].H * groups[0].W;
       }
-      e = dmalloc(&P->lg_prev[par], nt);
+      if (e == cudaSuccess && !P->gdelta) e = dmalloc(&P->gdelta, (size_t)nt * groups[0].H * groups[0].W);
+      if (e == cudaSuccess && !P->grho) e = dmalloc(&P->grho, nt);
+      if (e == cudaSuccess) e = dmalloc(&P->lg_prev[par], nt);
       if (e == cudaSuccess) e = dmalloc(&P->lg_seed[par], nt);
-      if (e == cudaSuccess) e = dmalloc(&P->lg_x[par], nt);
       if (e == cudaSuccess) e = cudaMemcpy(P->lg_prev[par], hp.data(), nt * sizeof(double*), cudaMemcpyHostToDevice);
       if (e == cudaSuccess) e = cudaMemcpy(P->lg_seed[par], hs.data(), nt * sizeof(double*), cudaMemcpyHostToDevice);
-      if (e == cudaSuccess) e = cudaMemcpy(P->lg_x[par], hx.data(), nt * sizeof(double*), cudaMemcpyHostToDevice);
     }
   }
   if (e == cudaSuccess) e = cudaMemcpy(P->g2, o.g2, o.T * sizeof(double), cudaMemcpyHostToDevice);
