@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
   double* rinv = yv + m;
   double* sc = rinv + m;                          // [8]
   int* fl = reinterpret_cast<int*>(sc + 8);       // [8]
-  float* V = reinterpret_cast<float*>(fl + 8);    // [S][npad]
+  float* hbf = reinterpret_cast<float*>(fl + 8);  // [kMaxV] the cluster sums in FP32
+  float* V = hbf + kMaxV;                         // [S][npad]
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int sysi = blockIdx.x / CS;
   const int cta0 = blockIdx.x - rank;             // first CTA of this cluster
@@ -206,6 +207,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
 #pragma unroll
         for (int r = 0; r < CS; ++r) s += cluster.map_shared_rank(cpart + buf * kMaxV, r)[i];
         hb[i] = s;
+        hbf[i] = (float)s;                        // converted once for the vector updates
       }
     }
     __syncthreads();
@@ -387,7 +389,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
     const bool first = (outer == 0);
     const double target = (capture && first) ? p.tol * bnorm : fmax(kEta * beta, 0.1 * p.tol * bnorm);
     {
-      const float ib = (float)(1.0 / beta);
+      const float ib = 1.f / (float)beta;
       float* v0 = vloc(0);
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
@@ -467,7 +469,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
       }
       __syncthreads();
       for (int i = 0; i < nh; ++i) {
-        const float hi = (float)hb[i];
+        const float hi = hbf[i];
         const float* vi = vloc(i);
 #pragma unroll
         for (int k = 0; k < EPT; ++k) w[k] = fmaf(-hi, vi[tid + k * NT], w[k]);
@@ -488,7 +490,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
         }
         __syncthreads();
         for (int i = 0; i < nh; ++i) {
-          const float hi = (float)hb[i];
+          const float hi = hbf[i];
           const float* vi = vloc(i);
 #pragma unroll
           for (int k = 0; k < EPT; ++k) w[k] = fmaf(-hi, vi[tid + k * NT], w[k]);
@@ -666,7 +668,7 @@ size_t gmres_cluster_smem_bytes(int ept, int nt, int S, int m) {
   const int npad = ept * nt;
   const size_t doubles = (size_t)npad + (nt / 32) * kMaxV + kMaxV + 2 * kMaxV +
                          (size_t)(m + 1) * m + (m + 1) + 4 * m + 8;
-  return doubles * sizeof(double) + 8 * sizeof(int) + (size_t)S * npad * sizeof(float);
+  return doubles * sizeof(double) + 8 * sizeof(int) + kMaxV * sizeof(float) + (size_t)S * npad * sizeof(float);
 }
 
 cudaError_t launch_gmres_cluster(const GmresParams& p, int ept, int nt, int cs, int minb, size_t smem,
