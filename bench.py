@@ -124,6 +124,8 @@ def parse(argv=None):
     ap.add_argument("--cpu-sample-targets", type=int, default=8,
                     help="learned-guess workload: target channels per anchor in the CPU oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", choices=("fp64", "mixed"), default=None,
+                    help="one-block workloads: override the workload's solver precision")
     ap.add_argument("--modes", type=lambda s: s.split(","), default=None,
                     help="learned-guess workload: comparison modes to time besides learned_projected "
                          "(plain_x0_zero,plain_warm_start,projected_paper,learned_only; default all)")
@@ -759,6 +761,8 @@ def bench_small(args, dist, init=False):
     from paper_2511_17634_gb300 import kp
 
     wl = workload(args, rank)
+    if args.precision:
+        wl.precision = args.precision
     T = wl.T
     NS = args.march_steps if 0 < args.march_steps < T else T   # timesteps per timed march
     nmax = max(g.N for g in wl.groups)
