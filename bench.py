@@ -588,29 +588,62 @@ def run_north_star(args):
                 plan.close()
     head = res["learned_projected"]
     value = head["value"]
-    # end to end through the public API: each step's states from pinned host
-    # memory, the slice, the final states back to pinned host memory
+    # end to end through the public API, pipelined as a serving loop runs it:
+    # each step's states come from pinned host memory on a copy stream while
+    # the previous step computes, and its final states go back to pinned host
+    # memory while the next one computes.  Two plans on two sets of device
+    # states, so a copy never touches the states of a running step; every
+    # step's copies are inside the timed region (fill and drain included).
     hs = [(a.cpu().pin_memory(), b.cpu().pin_memory()) for a, b in snaps]
-    out_t = torch.empty_like(hs[0][1]).pin_memory()
+    outs = [torch.empty_like(hs[0][1]).pin_memory() for _ in range(2)]
     h2d = hs[0][0].numel() * 8 + hs[0][1].numel() * 8
-    d2h = out_t.numel() * 8
-    e2e_total = 0.0
-    for j in range(len(anchors) + 1):
+    d2h = outs[0].numel() * 8
+    bufs = [(s_buf, t_buf), (s_buf.clone(), t_buf.clone())]
+    plans = [keep, kp.March(ctx, [(bufs[1][0], bufs[1][1], g.target_seed, H, W)], T, wl.g2,
+                            mode=kp.MARCH_LEARNED, cnn=net, **common)]
+    plans[1].run(anchors[0], SLICE)                 # graph instantiation outside the timing
+    cs = torch.cuda.Stream()
+    ready = [torch.cuda.Event() for _ in range(2)]
+    done_ev = [torch.cuda.Event() for _ in range(2)]
+    free = [torch.cuda.Event() for _ in range(2)]
+    nsteps = 2 * len(anchors)
+
+    def copy_in(j):
+        sb, tb = bufs[j % 2]
         q = j % len(anchors)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        s_buf.copy_(hs[q][0], non_blocking=True)
-        t_buf.copy_(hs[q][1], non_blocking=True)
-        keep.run(anchors[q], SLICE)
-        out_t.copy_(t_buf, non_blocking=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        if j > 0:
-            e2e_total += e0.elapsed_time(e1) / 1000.0
+        with torch.cuda.stream(cs):
+            if j >= 2:
+                cs.wait_event(free[j % 2])           # results of step j - 2 are out
+            sb.copy_(hs[q][0], non_blocking=True)
+            tb.copy_(hs[q][1], non_blocking=True)
+            ready[j % 2].record(cs)
+
+    def copy_out(j):
+        with torch.cuda.stream(cs):
+            cs.wait_event(done_ev[j % 2])
+            outs[j % 2].copy_(bufs[j % 2][1], non_blocking=True)
+            free[j % 2].record(cs)
+
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cs.wait_event(e0)
+    copy_in(0)
+    for j in range(nsteps):
+        if j + 1 < nsteps:
+            copy_in(j + 1)
+        stream.wait_event(ready[j % 2])
+        plans[j % 2].run(anchors[j % len(anchors)], SLICE)
+        done_ev[j % 2].record(stream)
+        copy_out(j)
+    stream.wait_event(free[(nsteps - 1) % 2])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plans[1].close()
+    e2e_total = e0.elapsed_time(e1) / 1000.0
     e2e_total = max_over_ranks(e2e_total, dist, dev)
-    e2e_value = nsys_step * len(anchors) / e2e_total
+    e2e_value = nsys_step * nsteps / e2e_total
     # per-solve error of the learned path against the oracle's FP64 GMRES on
     # the same systems (the same m^{n-1}), 32 sampled targets at every anchor
     err = None
