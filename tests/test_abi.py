@@ -62,11 +62,12 @@ def test_solver_shape_options_validated():
 
 
 def test_cluster_size_option_validated():
-    # CTAs per system for mixed precision: 0 (automatic), 2, 4 or 8
+    # CTAs per system for mixed precision: 0 (automatic), 2, 4, 8 or 16
     from paper_2511_17634_gb300 import kp as K
     L = K.lib()
     import ctypes
-    for cs, ok in [(0, True), (2, True), (4, True), (8, True), (3, False), (16, False), (-2, False)]:
+    for cs, ok in [(0, True), (2, True), (4, True), (8, True), (16, True), (3, False), (32, False),
+                   (-2, False)]:
         o = K._Options()
         L.kp_options_default(ctypes.byref(o))
         assert o.cluster_size == 0
