@@ -124,6 +124,8 @@ def parse(argv=None):
     ap.add_argument("--cpu-sample-targets", type=int, default=8,
                     help="learned-guess workload: target channels per anchor in the CPU oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--channels", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
+                    help="learned-guess network widths, e.g. 10,32,32,32,1 (default 10,16,16,1)")
     ap.add_argument("--precision", choices=("fp64", "mixed"), default=None,
                     help="one-block workloads: override the workload's solver precision")
     ap.add_argument("--modes", type=lambda s: s.split(","), default=None,
@@ -401,6 +403,20 @@ def cnn_flops_per_pixel(channels):
     return 2 * 9 * sum(a * b for a, b in zip(channels[:-1], channels[1:]))
 
 
+def cnn_bytes_per_pixel(channels):
+    """HBM bytes per pixel the learned guess cannot avoid as a layer-by-layer
+    pipeline: the step residual (read m, write r), the packing (read m, the
+    seed, r; write the BF16 input rows), and every layer's BF16 input and
+    output rows once (8-channel chunks of 16 bytes, 2 or 4 per row), the last
+    layer's output in FP32."""
+    chunks = [2 if c <= 16 else 4 for c in channels]
+    b = (8 + 4) + (8 + 8 + 4 + 16 * chunks[0])
+    for layer in range(len(channels) - 1):
+        last = layer == len(channels) - 2
+        b += 16 * chunks[layer] + (4 * channels[-1] if last else 16 * chunks[layer + 1])
+    return b
+
+
 def learned_setup(kp, ctx, args, rank):
     """The learned-guess workload: images, and a network trained on ~2000
     pairs the method generated from training targets disjoint from the
@@ -416,8 +432,9 @@ def learned_setup(kp, ctx, args, rank):
         wl.groups[0] = g
     tr = synth.make_group(1239, g.H, g.W, g.channels, g.seeds.shape[0] // g.channels, 8, tag=0,
                           target_offset=100000)
-    net = kp.CNN(ctx, g.H, g.W, channels=learned.CHANNELS, max_batch=16)
-    net.set_params(learned.init_params(1))
+    ch = args.channels or learned.CHANNELS
+    net = kp.CNN(ctx, g.H, g.W, channels=ch, max_batch=16)
+    net.set_params(learned.init_params(1, ch))
     t0 = time.perf_counter()
     every = max(1, wl.T // 84)
     xs, ys = learned.generate_pairs(ctx, net, tr, wl.T, wl.g2, steps=wl.T, every=every)
@@ -450,7 +467,8 @@ def cpu_learned_sample(args, wl, g, params, snaps_host, threads):
         ts = np.array([remap[int(g.target_seed[q])] for q in pick], dtype=np.int32)
         t0 = time.perf_counter()
         O.march_learned(g.H, g.W, wl.T, wl.g2, s_all[seeds].copy(), t_all[pick].copy(), ts, params,
-                        learned.CHANNELS, steps=1, n0=n0, tol_ref=wl.tol, m_ref=wl.m, m_seed=wl.m_seed, a=wl.a)
+                        args.channels or learned.CHANNELS, steps=1, n0=n0, tol_ref=wl.tol, m_ref=wl.m,
+                        m_seed=wl.m_seed, a=wl.a)
         wall += time.perf_counter() - t0
         nsys += per
     return nsys, wall
@@ -682,7 +700,7 @@ def run_north_star(args):
                          "whole march), the trained network's weights; OpenMP over systems in the C solver, "
                          "numpy for the network"}
     # roofline of the dominant kernel class of the headline slice
-    fpp = cnn_flops_per_pixel(learned.CHANNELS)
+    fpp = cnn_flops_per_pixel(args.channels or learned.CHANNELS)
     cnn_tf = nt * SLICE * len(anchors) * H * W * fpp / (head["guess_ms"] / 1e3) / 1e12 if head["guess_ms"] else 0.0
     # the solver runs on the FP32 pipe: FP32 Krylov flops, plus the
     # refinement's high-precision flops (true residuals, the judge's residual,
@@ -699,11 +717,18 @@ def run_north_star(args):
                    "kernel": "gmres_cluster_kernel (targets: judge, projection, refine)",
                    "hp_tflops": hp_fl / sec / 1e12, "fp32_tflops": f32_fl / sec / 1e12,
                    "peak_source": ALU_PEAK_SOURCE}
-    cnn_peak = BF16_SUSTAINED_TFLOPS
-    cnn_roof = {"bound": "tensor", "achieved": cnn_tf, "peak": cnn_peak, "unit": "TFLOP/s",
-                "frac": cnn_tf / cnn_peak, "traffic": None,
-                "kernel": "conv3x3_col_kernel x4 + input packing + x_init (the learned guess, all targets)",
-                "peak_source": "measured cuBLAS bf16, sustained (the network runs inside the march)"}
+    # the learned guess is bound by its activations' HBM traffic (each layer
+    # reads and writes BF16 rows of 16 or 32 channels); its tensor rate beside
+    bpp = cnn_bytes_per_pixel(args.channels or learned.CHANNELS)
+    cnn_gbs = (nt * SLICE * len(anchors) * H * W * bpp / (head["guess_ms"] / 1e3) / 1e9
+               if head["guess_ms"] else 0.0)
+    cnn_roof = {"bound": "hbm", "achieved": cnn_gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                "frac": cnn_gbs / HBM_PEAK_GBS, "traffic": None,
+                "kernel": "step residual + input packing + conv3x3_col_kernel per layer (the learned guess, "
+                          "all targets)",
+                "algorithmic_bytes_per_pixel": bpp, "tensor_tflops": cnn_tf,
+                "tensor_frac_of_sustained_bf16": cnn_tf / BF16_SUSTAINED_TFLOPS,
+                "peak_source": "measured copy bandwidth"}
     dominant = "solver" if head["refine_ms"] >= head["guess_ms"] else "network"
     line = {
         "metric": METRIC, "value": value, "unit": "systems/s", "n_gpus": world, "steps": args.steps,
@@ -714,6 +739,7 @@ def run_north_star(args):
                    "T": T, "targets": nt, "seeds": wl.n_seed_planes, "grid": [H, W],
                    "timesteps_per_step": SLICE, "anchor_timesteps": anchors, "tol": wl.tol, "m": wl.m,
                    "inference_batch": net.inference_batch, "inner_digits": args.inner_digits or 5,
+                   "network_channels": list(args.channels or learned.CHANNELS),
                    "orthogonalisation": "CGS2" if reorth == 0 else "CGS+DGKS",
                    "parallelism": f"replicas x{world}",
                    "l2": "not flushed: each step's states (1.6 GB) exceed L2"},

@@ -604,8 +604,9 @@ kp_status kp_cnn_create(kp_ctx* c, int H, int W, int max_batch, int nlayers, con
   n->geo = kp::conv_geom(H, W);
   size_t nwf = 0;
   for (int l = 0; l < nlayers; ++l) {
-    n->cic.push_back(l == 0 ? 2 : 4);
-    n->nout.push_back(l + 1 == nlayers ? 16 : 32);
+    // input chunk planes (8 channels each, K = 16 per MMA) and output width
+    n->cic.push_back(l == 0 || n->ch[l] <= 16 ? 2 : 4);
+    n->nout.push_back(l + 1 == nlayers || n->ch[l + 1] <= 16 ? 16 : 32);
     n->wf_off.push_back(nwf);
     nwf += (size_t)9 * n->cic[l] * n->nout[l] * 8;
     if (kp::conv_smem_bytes(n->geo, n->cic[l], n->nout[l]) > c->smem_optin) n->fused = false;

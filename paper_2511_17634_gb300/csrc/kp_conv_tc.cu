@@ -146,7 +146,7 @@ struct ConvLayout {
 
 template <int CIC, int NOUT, bool F32OUT>
 __global__ void __launch_bounds__(kConvThreads, 1) conv3x3_tc_kernel(const ConvArgs a) {
-  static_assert(F32OUT || NOUT == 32, "hidden layers write 4 chunks of 8 channels");
+  static_assert(F32OUT || NOUT == 32 || NOUT == 16, "hidden layers write NOUT / 8 chunks of 8 channels");
   using Lay = ConvLayout<CIC, NOUT>;
   extern __shared__ __align__(128) unsigned char cs[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(cs) + 127) & ~(uintptr_t)127);
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3x3_tc_kernel(const ConvA
           }
         } else {
 #pragma unroll
-          for (int cc = 0; cc < 4; ++cc) {
+          for (int cc = 0; cc < NOUT / 8; ++cc) {
             uint32_t pk[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3x3_tc_kernel(const ConvA
               __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
               pk[e] = *reinterpret_cast<uint32_t*>(&h2);
             }
-            uint4* dst = reinterpret_cast<uint4*>(a.out_pad + (((size_t)b * 4 + cc) * a.Rp + a.halo + R) * 8);
+            uint4* dst = reinterpret_cast<uint4*>(a.out_pad + (((size_t)b * (NOUT / 8) + cc) * a.Rp + a.halo + R) * 8);
             *dst = make_uint4(pk[0], pk[1], pk[2], pk[3]);
           }
         }
@@ -353,7 +353,7 @@ struct ColLayout {
 
 template <int CIC, int NOUT, bool F32OUT>
 __global__ void __launch_bounds__(kColThreads, 1) conv3x3_col_kernel(const ConvArgs a) {
-  static_assert(F32OUT || NOUT == 32, "hidden layers write 4 chunks of 8 channels");
+  static_assert(F32OUT || NOUT == 32 || NOUT == 16, "hidden layers write NOUT / 8 chunks of 8 channels");
   using Lay = ColLayout<CIC, NOUT>;
   extern __shared__ __align__(128) unsigned char cs[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(cs) + 127) & ~(uintptr_t)127);
@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(kColThreads, 1) conv3x3_col_kernel(const ConvA
         } else {
           const size_t prow = (size_t)a.halo + (size_t)o * HP + 1 + j;
 #pragma unroll
-          for (int cc = 0; cc < 4; ++cc) {
+          for (int cc = 0; cc < NOUT / 8; ++cc) {
             uint32_t pk[4];
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
@@ -536,7 +536,7 @@ __global__ void __launch_bounds__(kColThreads, 1) conv3x3_col_kernel(const ConvA
               __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
               pk[e] = *reinterpret_cast<uint32_t*>(&h2);
             }
-            *reinterpret_cast<uint4*>(a.out_pad + (((size_t)b * 4 + cc) * a.Rp + prow) * 8) =
+            *reinterpret_cast<uint4*>(a.out_pad + (((size_t)b * (NOUT / 8) + cc) * a.Rp + prow) * 8) =
                 make_uint4(pk[0], pk[1], pk[2], pk[3]);
           }
         }
@@ -671,12 +671,14 @@ cudaError_t launch_conv3x3(const __nv_bfloat16* in, int B, int cic, const __nv_b
   if (use_col(g)) {
     if (!out_f32 && cic == 2 && nout == 32) return launch_col_t<2, 32, false>(a, sms, st);
     if (!out_f32 && cic == 4 && nout == 32) return launch_col_t<4, 32, false>(a, sms, st);
+    if (!out_f32 && cic == 2 && nout == 16) return launch_col_t<2, 16, false>(a, sms, st);
     if (out_f32 && cic == 4 && nout == 16) return launch_col_t<4, 16, true>(a, sms, st);
     if (out_f32 && cic == 2 && nout == 16) return launch_col_t<2, 16, true>(a, sms, st);
     return cudaErrorInvalidValue;
   }
   if (!out_f32 && cic == 2 && nout == 32) return launch_conv_t<2, 32, false>(a, sms, st);
   if (!out_f32 && cic == 4 && nout == 32) return launch_conv_t<4, 32, false>(a, sms, st);
+  if (!out_f32 && cic == 2 && nout == 16) return launch_conv_t<2, 16, false>(a, sms, st);
   if (out_f32 && cic == 4 && nout == 16) return launch_conv_t<4, 16, true>(a, sms, st);
   if (out_f32 && cic == 2 && nout == 16) return launch_conv_t<2, 16, true>(a, sms, st);
   return cudaErrorInvalidValue;

@@ -38,10 +38,12 @@ def _dev(a):
 
 
 def _random_net(kp, learned, ctx, H, W, B, seed):
-    # a network whose guess differs clearly from the warm start
+    # a network whose guess differs clearly from the warm start: an output of
+    # rms well above one (in units of dt rho) moves the guess farther than the
+    # step's change, so its residual is several times the warm start's
     p = learned.init_params(seed)
     nlast = learned.CHANNELS[-2] * 9
-    p[-(nlast + 1):-1] *= 100.0
+    p[-(nlast + 1):-1] *= 1000.0
     net = kp.CNN(ctx, H, W, channels=learned.CHANNELS, max_batch=4)
     net.set_params(p)
     net.set_inference_batch(B)
