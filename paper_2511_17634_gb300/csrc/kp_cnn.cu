@@ -31,6 +31,7 @@ using kp::dd_from_double;
 using kp::dd_mul;
 using kp::dd_sub;
 using kp::dd_to_double;
+using kp::f32_nearest;
 
 constexpr int kMaxLayers = 8;
 
@@ -250,12 +251,12 @@ __global__ void pack_inputs_kernel(const double* const* img, const double* const
                                    const double* rho, int P, float* in) {
   const int b = blockIdx.y;
   const float e[4] = {tau, 1.f - tau, sinpif(tau), cospif(tau)};
-  const float ir = rho[b] > 0.0 ? (float)(1.0 / rho[b]) : 0.f;
+  const float ir = rho[b] > 0.0 ? 1.f / f32_nearest(rho[b]) : 0.f;
   float* o = in + (size_t)b * 10 * P;
   for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
     __nv_bfloat16 h0, l0, h1, l1, h2, l2;
-    split_hi_lo((float)img[b][p], h0, l0);
-    split_hi_lo((float)seed[b][p], h1, l1);
+    split_hi_lo(f32_nearest(img[b][p]), h0, l0);
+    split_hi_lo(f32_nearest(seed[b][p]), h1, l1);
     split_hi_lo(o[8 * P + p] * ir, h2, l2);
     o[p] = __bfloat162float(h0);
     o[P + p] = __bfloat162float(l0);
@@ -302,7 +303,7 @@ __global__ void march_pack_kernel(const double* const* mprev, const double* cons
   const int t = *step + step_offset;
   const float tau = (float)(t + 1) / (float)T;
   const float e[4] = {tau, 1.f - tau, sinpif(tau), cospif(tau)};
-  const float ir = rho[b] > 0.0 ? (float)(1.0 / rho[b]) : 0.f;
+  const float ir = rho[b] > 0.0 ? 1.f / f32_nearest(rho[b]) : 0.f;
   const double* mp = mprev[b];
   const double* ms = mseed[b];
   const float* rb = r + (size_t)b * P;
@@ -312,8 +313,8 @@ __global__ void march_pack_kernel(const double* const* mprev, const double* cons
     const int i = p / H, j = p - i * H;
     const size_t row = (size_t)halo + (size_t)i * (H + 2) + 1 + j;
     __nv_bfloat162 f0, f1, f2;
-    split_hi_lo((float)mp[p], f0.x, f0.y);
-    split_hi_lo((float)ms[p], f1.x, f1.y);
+    split_hi_lo(f32_nearest(mp[p]), f0.x, f0.y);
+    split_hi_lo(f32_nearest(ms[p]), f1.x, f1.y);
     split_hi_lo(rb[p] * ir, f2.x, f2.y);
     const uint4 c0 = make_uint4(*reinterpret_cast<uint32_t*>(&f0), *reinterpret_cast<uint32_t*>(&f1),
                                 *reinterpret_cast<uint32_t*>(&h1), *reinterpret_cast<uint32_t*>(&h2));

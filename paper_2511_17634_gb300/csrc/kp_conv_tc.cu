@@ -345,9 +345,12 @@ struct ColLayout {
   static __host__ __device__ uint32_t L(int H) {
     return (uint32_t)((kCT + 2) * (H + 2) + (H < 128 ? 128 - H : 0));
   }
+  // input stages: four of the two-chunk windows (41.6 KB at 128x128), two of
+  // the four-chunk ones; the TMEM accumulator is double-buffered either way
+  static constexpr int NS = CIC == 2 ? 4 : 2;
   static __host__ __device__ uint32_t stage_bytes(int H) { return CIC * L(H) * 16u; }
   static __host__ __device__ uint32_t w_bytes() { return 9u * CIC * NOUT * 16u; }
-  static __host__ __device__ uint32_t bar_off(int H) { return 2 * stage_bytes(H) + w_bytes(); }
+  static __host__ __device__ uint32_t bar_off(int H) { return NS * stage_bytes(H) + w_bytes(); }
   static __host__ __device__ size_t total(int H) { return bar_off(H) + 128 + 128; }
 };
 
@@ -360,13 +363,15 @@ __global__ void __launch_bounds__(kColThreads, 1) conv3x3_col_kernel(const ConvA
   const uint32_t L = Lay::L(a.H);
   const uint32_t SB = Lay::stage_bytes(a.H);
   unsigned char* stage0 = base;
-  unsigned char* wsm = base + 2 * SB;
+  constexpr int NS = Lay::NS;
+  unsigned char* wsm = base + NS * SB;
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + Lay::bar_off(a.H));
-  uint64_t* full = bars;          // [2] input stage landed
-  uint64_t* mdone = bars + 2;     // [2] MMAs of a super tile done (stage and TMEM buffer)
-  uint64_t* tempty = bars + 4;    // [2] epilogue finished reading a TMEM buffer
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 6);
-  volatile int* abort = reinterpret_cast<volatile int*>(bars + 7);
+  uint64_t* full = bars;          // [NS] input stage landed
+  uint64_t* sfree = bars + NS;    // [NS] MMAs reading an input stage done
+  uint64_t* tfull = bars + 2 * NS;      // [2] MMAs of a super tile done (TMEM buffer ready)
+  uint64_t* tempty = bars + 2 * NS + 2; // [2] epilogue finished reading a TMEM buffer
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 4);
+  volatile int* abort = reinterpret_cast<volatile int*>(bars + 2 * NS + 5);
   constexpr uint32_t kCols = 2 * kCT * NOUT;   // 512 or 256 TMEM columns
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int HP = a.H + 2;
@@ -374,10 +379,13 @@ __global__ void __launch_bounds__(kColThreads, 1) conv3x3_col_kernel(const ConvA
   const int total = a.B * nct;
 
   if (tid == 0) {
-    for (int s = 0; s < 2; ++s) {
+    for (int s = 0; s < NS; ++s) {
       bar_init(&full[s], 1);
-      bar_init(&mdone[s], 1);
-      bar_init(&tempty[s], kColEpiWarps);
+      bar_init(&sfree[s], 1);
+    }
+    for (int t = 0; t < 2; ++t) {
+      bar_init(&tfull[t], 1);
+      bar_init(&tempty[t], kColEpiWarps);
     }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -412,9 +420,9 @@ __global__ void __launch_bounds__(kColThreads, 1) conv3x3_col_kernel(const ConvA
       uint32_t issued = 0;
       int it = 0;
       for (int st = blockIdx.x; st < total; st += gridDim.x, ++it) {
-        const int s = it & 1;
-        const uint32_t u = (uint32_t)it >> 1;
-        if (u > 0 && !bar_wait(&mdone[s], (u - 1) & 1, abort)) { *abort = 1; break; }
+        const int s = it % NS;
+        const uint32_t u = (uint32_t)(it / NS);
+        if (u > 0 && !bar_wait(&sfree[s], (u - 1) & 1, abort)) { *abort = 1; break; }
         const int b = st / nct;
         const int i0 = (st - b * nct) * kCT;
         const int kv = min(kCT, a.W - i0);
@@ -428,8 +436,8 @@ __global__ void __launch_bounds__(kColThreads, 1) conv3x3_col_kernel(const ConvA
       }
       if (*abort) {
         volatile int never = 0;
-        for (uint32_t k = issued > 2 ? issued - 2 : 0; k < issued; ++k)
-          (void)bar_wait(&full[k & 1], (k >> 1) & 1, &never);
+        for (uint32_t k = issued > (uint32_t)NS ? issued - NS : 0; k < issued; ++k)
+          (void)bar_wait(&full[k % NS], (k / NS) & 1, &never);
       }
     }
   } else if (warp == kColEpiWarps + 1) {
@@ -437,17 +445,17 @@ __global__ void __launch_bounds__(kColThreads, 1) conv3x3_col_kernel(const ConvA
       uint32_t committed = 0;
       int it = 0;
       for (int st = blockIdx.x; st < total; st += gridDim.x, ++it) {
-        const int s = it & 1;
-        const uint32_t u = (uint32_t)it >> 1;
+        const int s = it % NS, tb = it & 1;
+        const uint32_t u = (uint32_t)(it / NS), ut = (uint32_t)it >> 1;
         if (!bar_wait(&full[s], u & 1, abort)) { *abort = 1; break; }
-        if (u > 0 && !bar_wait(&tempty[s], (u - 1) & 1, abort)) { *abort = 1; break; }
+        if (ut > 0 && !bar_wait(&tempty[tb], (ut - 1) & 1, abort)) { *abort = 1; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int b = st / nct;
         const int i0 = (st - b * nct) * kCT;
         const int kv = min(kCT, a.W - i0);
         const uint32_t sa = su32(stage0 + s * SB);
         const uint32_t sw = su32(wsm);
-        const uint32_t dbase = tmem + (uint32_t)(s * kCT * NOUT);
+        const uint32_t dbase = tmem + (uint32_t)(tb * kCT * NOUT);
         int last = i0 - 1;                          // largest output column written so far
 #pragma unroll 1
         for (int c = i0 - 1; c <= i0 + kv; ++c) {   // input column
@@ -480,13 +488,14 @@ __global__ void __launch_bounds__(kColThreads, 1) conv3x3_col_kernel(const ConvA
             }
           }
         }
-        mma_commit_to(&mdone[s]);
+        mma_commit_to(&sfree[s]);                   // the input stage may be refilled
+        mma_commit_to(&tfull[tb]);                  // the accumulators are ready
         committed = (uint32_t)it + 1;
       }
       if (*abort && committed > 0) {
         const uint32_t k = committed - 1;
         volatile int never = 0;
-        (void)bar_wait(&mdone[k & 1], (k >> 1) & 1, &never);
+        (void)bar_wait(&tfull[k & 1], (k >> 1) & 1, &never);
       }
     }
   } else {
@@ -494,9 +503,9 @@ __global__ void __launch_bounds__(kColThreads, 1) conv3x3_col_kernel(const ConvA
     // every (kColEpiWarps / 4)-th output column, starting at column w / 4
     int it = 0;
     for (int st = blockIdx.x; st < total; st += gridDim.x, ++it) {
-      const int s = it & 1;
-      const uint32_t u = (uint32_t)it >> 1;
-      if (!bar_wait(&mdone[s], u & 1, abort)) { *abort = 1; break; }
+      const int tb = it & 1;
+      const uint32_t ut = (uint32_t)it >> 1;
+      if (!bar_wait(&tfull[tb], ut & 1, abort)) { *abort = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int b = st / nct;
       const int i0 = (st - b * nct) * kCT;
@@ -508,7 +517,7 @@ __global__ void __launch_bounds__(kColThreads, 1) conv3x3_col_kernel(const ConvA
       for (int q = warp >> 2; q < kv; q += kColEpiWarps / 4) {
         const int o = i0 + q;
         const uint32_t taddr =
-            tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(s * kCT * NOUT + NOUT * (kCT - 1 - q));
+            tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(tb * kCT * NOUT + NOUT * (kCT - 1 - q));
         float v[NOUT];
 #pragma unroll
         for (int c0 = 0; c0 < NOUT; c0 += 16) {
@@ -543,7 +552,7 @@ __global__ void __launch_bounds__(kColThreads, 1) conv3x3_col_kernel(const ConvA
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) bar_arrive(&tempty[s]);
+      if (lane == 0) bar_arrive(&tempty[tb]);
     }
   }
   __syncthreads();

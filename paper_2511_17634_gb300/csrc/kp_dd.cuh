@@ -80,4 +80,18 @@ __device__ __forceinline__ dd dd_from_double(double x) {
 
 __device__ __forceinline__ double dd_to_double(dd x) { return (double)x.hi + (double)x.lo; }
 
+// The FP32 value nearest to x (ties to even) by integer operations on its bit
+// pattern -- the top 24 significant bits, rounded on the 29 below -- for x in
+// the normal FP32 range; other values go through the conversion instruction.
+__device__ __forceinline__ float f32_nearest(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned int uh = (unsigned int)(u >> 32), ul = (unsigned int)u;
+  const int e = (int)((uh >> 20) & 0x7FFu);
+  if (e < 897 || e > 1150) return __double2float_rn(x);
+  unsigned int f = (uh & 0x80000000u) | ((unsigned int)(e - 896) << 23) | ((uh & 0xFFFFFu) << 3) | (ul >> 29);
+  const unsigned int rem = ul & 0x1FFFFFFFu;
+  f += (rem > 0x10000000u || (rem == 0x10000000u && (f & 1u))) ? 1u : 0u;
+  return __uint_as_float(f);
+}
+
 }  // namespace kp
