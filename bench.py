@@ -125,7 +125,7 @@ def parse(argv=None):
                     help="learned-guess workload: target channels per anchor in the CPU oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--channels", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
-                    help="learned-guess network widths, e.g. 10,32,32,32,1 (default 10,16,16,1)")
+                    help="learned-guess network widths, e.g. 10,16,16,1 (default 10,32,32,32,1)")
     ap.add_argument("--precision", choices=("fp64", "mixed"), default=None,
                     help="one-block workloads: override the workload's solver precision")
     ap.add_argument("--modes", type=lambda s: s.split(","), default=None,
