@@ -135,7 +135,11 @@ def parse(argv=None):
                     help="learned-guess workload: timesteps whose march states start the slices "
                          "(default 0,250,500,750)")
     ap.add_argument("--no-secondary", action="store_true",
-                    help="learned-guess workload: skip the 32x32x3 FP64 secondary line")
+                    help="learned-guess workload: skip the secondary lines (32x32x3 FP64, 64x64x3 mixed, "
+                         "uneven sizes)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="one-block workloads: skip the optional FP64 paths (score, Picard, BiCGSTAB seeds, "
+                         "seed cycling) and the basis-dimension sweep")
     return ap.parse_args(argv)
 
 
@@ -782,6 +786,13 @@ def main():
             sec = bench_small(a2, dist)
             if rank == 0:
                 line["secondary_32x32x3_fp64"] = sec
+            # the mixed-precision 64x64x3 workload and the batched uneven sizes
+            # (autotuned), projected vs plain GMRES on each
+            for key, cfg in (("secondary_64x64x3_mixed", "4"), ("secondary_uneven_fp64", "3")):
+                a = parse(["--config", cfg, "--steps", "2", "--warmup", "3", "--no-extras"])
+                sec = bench_small(a, dist)
+                if rank == 0:
+                    line[key] = sec
     else:
         line = bench_small(args, None, init=True)
         dist = line.pop("_dist", None) if line else None
@@ -905,7 +916,7 @@ def bench_small(args, dist, init=False):
     launches_per_step = tm.launches
 
     out = {}
-    if not mixed:
+    if not mixed and not args.no_extras:
         # score extraction + probability-flow embedding fused into the target
         # solves (every timestep's score kept: T x targets x 2 x N doubles)
         sc = torch.empty((NS,) + (sum(x.shape[0] * 2 * x.shape[1] for x in st_t),), dtype=torch.float64,
@@ -969,7 +980,7 @@ def bench_small(args, dist, init=False):
             "note": "one chain per channel over the template seeds, served basis capped at a = 20"}
         plc.close()
         cctx.close()
-    if not mixed and not args.no_baselines:
+    if not mixed and not args.no_baselines and not args.no_extras:
         # the basis dimension of Sec. 3 (V_a^n spans K_a; Sec. 5.2 fixes a = 20):
         # the seed's first cycle takes exactly a Arnoldi steps (kp_options.fixed_a)
         # instead of stopping at convergence (a' of 5-8 vectors here)
@@ -1064,7 +1075,10 @@ def bench_small(args, dist, init=False):
             "ms_per_step": 1000 * t_proj / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 Krylov + f64 refinement" if mixed else "f64",
-            "data": "synthetic (seeded blob images shaped like the paper's 32x32 CIFAR-10 set)",
+            "data": "synthetic (seeded blob images shaped like the paper's "
+                    + ("64x64 CelebA set)" if nmax == 4096 and len(wl.groups) == 1
+                       else "28x28 / 32x32 / 64x64 image sets)" if len(wl.groups) > 1
+                       else "32x32 CIFAR-10 set)"),
             "config": {"workload": wl.name, "T": T, "timesteps_per_march": NS, "targets": nt_planes,
                        "seeds": wl.n_seed_planes, "grid": [g.H for g in wl.groups],
                        "tol": wl.tol, "m": wl.m, "parallelism": f"replicas x{world}",
