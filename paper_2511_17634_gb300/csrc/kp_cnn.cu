@@ -213,7 +213,11 @@ __device__ __forceinline__ dd step_residual_at(const double* m, int p, int H, in
 // step_offset] when g2s is given (the march's schedule and counter).  The FP32
 // value of r goes to rout[b * rld + p] for the packing kernels.  The squares
 // are summed in double-float per thread; no FP64 instruction runs per point
-// (the FP64 pipe, not HBM, bounds this part on GB300).
+// (the FP64 pipe, not HBM, bounds this part on GB300).  Blocks of 1024
+// threads: with one block per plane, fewer and larger blocks keep the last
+// wave short (1536 planes are 5 waves of 2 blocks per SM, not 1.3 waves of 8).
+constexpr int kRmsThreads = 1024;
+
 __global__ void step_residual_rms_kernel(const double* const* m, int H, int W, double dt, double g2v,
                                          const double* g2s, const int* step, int step_offset, double* rho,
                                          float* rout, size_t rld) {
@@ -691,7 +695,7 @@ kp_status kp_cnn_pack_inputs(kp_cnn* n, int B, const double* const* img, const d
   if (e == cudaSuccess) e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double*), cudaMemcpyHostToDevice, n->ctx->stream);
   if (e == cudaSuccess) {
     const double dt = 1.0 / T;
-    step_residual_rms_kernel<<<B, 256, 0, n->ctx->stream>>>(d, n->H, n->W, dt, g2n, nullptr, nullptr, 0, rho,
+    step_residual_rms_kernel<<<B, kRmsThreads, 0, n->ctx->stream>>>(d, n->H, n->W, dt, g2n, nullptr, nullptr, 0, rho,
                                                             in + 8 * (size_t)n->P, 10 * (size_t)n->P);
     pack_inputs_kernel<<<dim3(grid_for(n->P), B), 256, 0, n->ctx->stream>>>(d, d + B, (float)step / (float)T,
                                                                            rho, n->P, in);
@@ -764,7 +768,7 @@ cudaError_t cnn_enqueue_guess(kp_cnn* n, int B, const double* const* mprev, cons
   const dim3 grid(std::min((n->P + 255) / 256, 1024), B);
   // the FP32 residual goes through the network's output buffer, which the
   // packing kernel has read before any layer runs
-  step_residual_rms_kernel<<<B, 256, 0, st>>>(mprev, n->H, n->W, 1.0 / T, 0.0, g2, step, step_offset, rho,
+  step_residual_rms_kernel<<<B, kRmsThreads, 0, st>>>(mprev, n->H, n->W, 1.0 / T, 0.0, g2, step, step_offset, rho,
                                               n->dout, (size_t)n->P);
   march_pack_kernel<<<grid, 256, 0, st>>>(mprev, mseed, n->dout, step, step_offset, rho, T, n->H, n->W,
                                           n->geo.halo, n->geo.Rp, n->pin);

@@ -96,12 +96,14 @@ __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// (no memory clobber: the MMA reads shared memory through the async proxy,
+// and volatile asm keeps it ordered after the barrier waits and fences and
+// before the commit that publishes its completion)
 __device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc)
-      : "memory");
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 __device__ __forceinline__ void mma_commit_to(uint64_t* b) {
@@ -453,31 +455,37 @@ __global__ void __launch_bounds__(kColThreads, 1) conv3x3_col_kernel(const ConvA
         const int b = st / nct;
         const int i0 = (st - b * nct) * kCT;
         const int kv = min(kCT, a.W - i0);
-        const uint32_t sa = su32(stage0 + s * SB);
-        const uint32_t sw = su32(wsm);
+        // descriptors: only the start-address field (bits 0..13, the address
+        // in 16-byte units) differs between the MMAs of a tile, and it never
+        // carries out of its 14 bits (shared-memory addresses are below
+        // 256 KB), so each MMA's descriptors are the tile's base descriptors
+        // plus an offset in 16-byte rows
+        const uint64_t abase = desc_plain(su32(stage0 + s * SB), L * 16, 128);
+        const uint64_t bbase = desc_plain(su32(wsm), 3 * NOUT * 16, 128);
         const uint32_t dbase = tmem + (uint32_t)(tb * kCT * NOUT);
         int last = i0 - 1;                          // largest output column written so far
+        const int cb = max(i0 - 1, 0), ce = min(i0 + kv, a.W - 1);   // input columns inside the image
 #pragma unroll 1
-        for (int c = i0 - 1; c <= i0 + kv; ++c) {   // input column
-          if (c < 0 || c >= a.W) continue;          // zero columns add nothing
+        for (int c = cb; c <= ce; ++c) {
           // groups g = di + 1 in [g0, g1] reach output columns c + 1 - g
           // inside the tile; [g0, gn) are written for the first time
           const int g0 = max(0, c + 2 - i0 - kv), g1 = min(2, c + 1 - i0);
           const int gn = min(g1 + 1, max(g0, c + 1 - last));
           last = c + 1 - g0;
-          const uint32_t arow = (uint32_t)(c - i0 + 1) * HP + 1;
+          // A rows of input column c shifted by dj - 1: (c - i0 + 1) HP + dj
+          const uint64_t acol = abase + (uint64_t)((c - i0 + 1) * HP);
+          // accumulators of output column c + 1 - ga at dcol + NOUT ga (mod 2^32)
+          const uint32_t dcol = dbase + (uint32_t)(NOUT * (kCT - 2 - c + i0));
 #pragma unroll
           for (int dj = 0; dj < 3; ++dj) {
 #pragma unroll
             for (int kc = 0; kc < CIC / 2; ++kc) {
-              const uint64_t ad =
-                  desc_plain(sa + (uint32_t)(2 * kc) * L * 16 + (arow + (uint32_t)dj - 1) * 16, L * 16, 128);
-              const uint32_t wrow = (uint32_t)((dj * CIC + 2 * kc) * 3 * NOUT);
+              const uint64_t ad = acol + (uint64_t)(2 * kc * L + dj);
+              const uint64_t bw = bbase + (uint64_t)((dj * CIC + 2 * kc) * 3 * NOUT);
               // [ga, gb] with accumulate flag acc: one MMA of N = (gb-ga+1) NOUT
               auto issue = [&](int ga, int gb, uint32_t acc) {
-                const uint64_t bd = desc_plain(sw + (wrow + (uint32_t)(ga * NOUT)) * 16, 3 * NOUT * 16, 128);
-                const uint32_t d = dbase + (uint32_t)(NOUT * (kCT - 1 - (c + 1 - ga - i0)));
-                mma_f16(d, ad, bd, idesc_f16(128, (gb - ga + 1) * NOUT), acc);
+                mma_f16(dcol + (uint32_t)(NOUT * ga), ad, bw + (uint64_t)(ga * NOUT),
+                        idesc_f16(128, (gb - ga + 1) * NOUT), acc);
               };
               if (dj == 0 && kc == 0) {
                 if (gn > g0) issue(g0, gn - 1, 0u);

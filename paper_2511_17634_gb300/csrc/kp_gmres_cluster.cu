@@ -192,9 +192,11 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
   auto bhi = [&](int l) { return (l < SL) ? dd_from_double(d.b[base + l]).hi : 0.f; };
   int buf = 0;
   // cluster-wide sums of nv values whose per-warp partials are in red;
-  // result in hb[0..nv) of every CTA (identical, rank order)
-  // (f32: the partials are FP32, summed across warps on the FP32 pipe)
-  auto cluster_sum = [&](int nv, bool f32) {
+  // result in hb[0..nv) of every CTA (identical: the same pairwise sum of the
+  // CS partials in every CTA).  f32: the partials are FP32, summed across
+  // warps on the FP32 pipe.  tail(): warp 0's work on the sums (Hessenberg
+  // column, Givens step), run before the CTA barrier that publishes them.
+  auto cluster_sum = [&](int nv, bool f32, auto&& tail) {
     if (warp == 0) {
       if (f32) cross_warp_f32<NT>(red32, nv, cpart + buf * kMaxV, lane);
       else
@@ -203,16 +205,23 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
     cluster.sync();
     if (warp == 0) {
       for (int i = lane; i < nv; i += 32) {
-        double s = 0.0;
+        double v[CS];
 #pragma unroll
-        for (int r = 0; r < CS; ++r) s += cluster.map_shared_rank(cpart + buf * kMaxV, r)[i];
-        hb[i] = s;
-        hbf[i] = (float)s;                        // converted once for the vector updates
+        for (int r = 0; r < CS; ++r) v[r] = cluster.map_shared_rank(cpart + buf * kMaxV, r)[i];
+#pragma unroll
+        for (int w = 1; w < CS; w *= 2)
+#pragma unroll
+          for (int r = 0; r + w < CS; r += 2 * w) v[r] += v[r + w];
+        hb[i] = v[0];
+        hbf[i] = (float)v[0];                     // converted once for the vector updates
       }
+      __syncwarp();
+      tail();
     }
     __syncthreads();
     buf ^= 1;
   };
+  auto no_tail = [] {};
 
   // initial guess, split into double-float without FP64 instructions
   auto load_x = [&](const double* src) {
@@ -259,7 +268,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
       }
       return s;
     }, red32);
-    cluster_sum(2, true);                         // (its barrier also ends every read of x_init)
+    cluster_sum(2, true, no_tail);               // (its barrier also ends every read of x_init)
     const bool warm_won = hb[1] < hb[0];          // the same in every CTA
     if (warm_won) load_x(d.mt);
     r_current = !warm_won;
@@ -282,7 +291,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
         }
         return s;
       }, red32);
-      cluster_sum(nv, true);
+      cluster_sum(nv, true, no_tail);
       if (warp == 0) {
         __syncwarp();
         const double* rot = p.slotRot + (size_t)sl * 3 * p.max_a;
@@ -331,7 +340,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
           }
           return s;
         }, red32);
-        cluster_sum(nv, true);
+        cluster_sum(nv, true, no_tail);
       }
       if (warp == 0) {
         __syncwarp();
@@ -371,7 +380,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
     }
     return s;
   }, red32);
-  cluster_sum(2, true);
+  cluster_sum(2, true, no_tail);
   const double bnorm = sqrt(hb[0]);
   double beta = sqrt(hb[1]);
   int steps = 0, status = KP_NOT_CONVERGED, outer = 0;
@@ -407,7 +416,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
     auto givens_step = [&](int j, double hn2) {
       const double ihn = hn2 > 0.0 ? rsqrt(hn2) : 0.0;
       const double hn = hn2 * ihn;
-      const int b = !(hn > 1e-7 * sqrt(sc[2]));
+      const int b = !(hn2 > 1e-14 * sc[2]);      // hn <= 1e-7 ||w_0||: breakdown
       Hr[j + j * ld] += cd;                       // H_A = H_(A - cd I) + cd I
       Hr[(j + 1) + j * ld] = hn;
       if (capture && first && j < p.cap_a && rank == 0) {
@@ -454,11 +463,11 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
         return s;
       };
       block_partials_f32x<NT>(nh + 1, dots, red32);
-      cluster_sum(nh + 1, true);
-      if (warp == 0) {
+      cluster_sum(nh + 1, true, [&] {
         double sq = 0.0;
         for (int i = lane; i < nh; i += 32) { Hr[i + j * ld] = hb[i]; sq += hb[i] * hb[i]; }
         sq = warp_sum(sq);
+        __syncwarp();
         if (lane == 0) {
           const double ww0 = hb[nh];
           sc[2] = ww0;
@@ -466,8 +475,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
           fl[0] = pass2;
           if (!pass2) givens_step(j, ww0 - sq);
         }
-      }
-      __syncthreads();
+      });
       for (int i = 0; i < nh; ++i) {
         const float hi = hbf[i];
         const float* vi = vloc(i);
@@ -476,19 +484,18 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
       }
       if (fl[0]) {
         block_partials_f32x<NT>(nh + 1, dots, red32);
-        cluster_sum(nh + 1, true);
-        if (warp == 0) {
+        cluster_sum(nh + 1, true, [&] {
           double sq = 0.0;
           for (int i = lane; i < nh; i += 32) { Hr[i + j * ld] += hb[i]; sq += hb[i] * hb[i]; }
           sq = warp_sum(sq);
+          __syncwarp();
           if (lane == 0) {
             const double ww1 = hb[nh];
             const int exact = sq > 0.25 * ww1;
             fl[3] = exact;
             if (!exact) givens_step(j, ww1 - sq);
           }
-        }
-        __syncthreads();
+        });
         for (int i = 0; i < nh; ++i) {
           const float hi = hbf[i];
           const float* vi = vloc(i);
@@ -502,9 +509,9 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
             for (int k = 0; k < EPT; ++k) s = fmaf(w[k], w[k], s);
             return s;
           }, red32);
-          cluster_sum(1, true);
-          if (tid == 0) givens_step(j, hb[0]);
-          __syncthreads();
+          cluster_sum(1, true, [&] {
+            if (lane == 0) givens_step(j, hb[0]);
+          });
         }
       }
       brk = fl[1];
@@ -578,7 +585,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
       for (int k = 0; k < EPT; ++k) s = fmaf(r[k], r[k], s);
       return s;
     }, red32);
-    cluster_sum(1, true);
+    cluster_sum(1, true, no_tail);
     beta = sqrt(hb[0]);
     ++outer;
   }
