@@ -49,19 +49,22 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
 
 
-def test_tap_orientation_exact(kp):
-    ctx = kp.Context(max_n=4096)
-    H, W = 7, 5
-    net = kp.CNN(ctx, H, W, channels=(1, 1), max_batch=1)
+@pytest.mark.parametrize("H,W,tap", [(7, 5, (2, 0)), (100, 37, (2, 0)), (100, 37, (0, 2)), (128, 20, (1, 1))])
+def test_tap_orientation_exact(kp, H, W, tap):
+    # one tap of weight one, integer inputs: every kernel must return the
+    # shifted input exactly (H = 7: the row-tiled tensor-core kernel; H > 64:
+    # the column-aligned one, ragged last super tile at W = 37 and W = 20)
+    ctx = kp.Context(max_n=16384)
+    net = kp.CNN(ctx, H, W, channels=(1, 1), max_batch=2)
     w = np.zeros((1, 1, 3, 3))
-    w[0, 0, 2, 0] = 1.0                       # di = +1, dj = -1: x[i+1, j-1]
-    net.set_params(np.concatenate([w.ravel(), [0.0]]))
-    x = np.arange(W * H, dtype=np.float64).reshape(1, 1, W, H) % 17
-    xin = torch.as_tensor(x.reshape(1, 1, -1), dtype=torch.float32, device="cuda")
-    out = torch.zeros((1, 1, W * H), dtype=torch.float32, device="cuda")
+    w[0, 0, tap[0], tap[1]] = 1.0             # (2, 0): di = +1, dj = -1, x[i+1, j-1]
+    net.set_params(np.concatenate([w.ravel(), [0.5]]))
+    x = np.arange(2 * W * H, dtype=np.float64).reshape(2, 1, W, H) % 17
+    xin = torch.as_tensor(x.reshape(2, 1, -1), dtype=torch.float32, device="cuda")
+    out = torch.zeros((2, 1, W * H), dtype=torch.float32, device="cuda")
     net.forward(xin, out)
     torch.cuda.synchronize()
-    ref = R.conv(x, w, np.zeros(1))
+    ref = R.conv(x, w, np.full(1, 0.5))
     assert np.array_equal(out.cpu().numpy().reshape(ref.shape), ref)
 
 
