@@ -125,6 +125,16 @@ __device__ __forceinline__ void tmem_ld_x16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// zeros to 16 TMEM columns of the warp's 32 lanes (the caller waits with
+// tcgen05.wait::st before the columns are handed to the MMAs)
+__device__ __forceinline__ void tmem_zero_x16(uint32_t taddr) {
+  const uint32_t z = 0u;
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
+      "r"(z)
+      : "memory");
+}
+
 struct ConvArgs {
   const __nv_bfloat16* in;     // [B][CIC][Rp][8]
   const __nv_bfloat16* wf;     // [9][CIC][NOUT][8]
@@ -413,6 +423,17 @@ __global__ void __launch_bounds__(kColThreads, 1) conv3x3_col_kernel(const ConvA
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
+  // the accumulators start at zero and every epilogue returns the columns it
+  // read to zero, so every MMA accumulates (no first-touch MMA of its own)
+  if (warp < kColEpiWarps) {
+    const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+    for (uint32_t col = (uint32_t)(warp >> 2) * 16; col < 2u * kCT * NOUT; col += (kColEpiWarps / 4) * 16)
+      tmem_zero_x16(tmem + lanes + col);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
   if (warp == kColEpiWarps) {
     if (lane == 0) {
@@ -463,36 +484,25 @@ __global__ void __launch_bounds__(kColThreads, 1) conv3x3_col_kernel(const ConvA
         const uint64_t abase = desc_plain(su32(stage0 + s * SB), L * 16, 128);
         const uint64_t bbase = desc_plain(su32(wsm), 3 * NOUT * 16, 128);
         const uint32_t dbase = tmem + (uint32_t)(tb * kCT * NOUT);
-        int last = i0 - 1;                          // largest output column written so far
         const int cb = max(i0 - 1, 0), ce = min(i0 + kv, a.W - 1);   // input columns inside the image
 #pragma unroll 1
         for (int c = cb; c <= ce; ++c) {
           // groups g = di + 1 in [g0, g1] reach output columns c + 1 - g
-          // inside the tile; [g0, gn) are written for the first time
+          // inside the tile
           const int g0 = max(0, c + 2 - i0 - kv), g1 = min(2, c + 1 - i0);
-          const int gn = min(g1 + 1, max(g0, c + 1 - last));
-          last = c + 1 - g0;
+          const uint32_t idesc = idesc_f16(128, (g1 - g0 + 1) * NOUT);
           // A rows of input column c shifted by dj - 1: (c - i0 + 1) HP + dj
           const uint64_t acol = abase + (uint64_t)((c - i0 + 1) * HP);
-          // accumulators of output column c + 1 - ga at dcol + NOUT ga (mod 2^32)
-          const uint32_t dcol = dbase + (uint32_t)(NOUT * (kCT - 2 - c + i0));
+          // accumulators of output columns c + 1 - g0 .. c + 1 - g1 (descending
+          // order in TMEM), starting at output column c + 1 - g0
+          const uint32_t d = dbase + (uint32_t)(NOUT * (kCT - 2 - c + i0 + g0));
 #pragma unroll
           for (int dj = 0; dj < 3; ++dj) {
 #pragma unroll
             for (int kc = 0; kc < CIC / 2; ++kc) {
               const uint64_t ad = acol + (uint64_t)(2 * kc * L + dj);
-              const uint64_t bw = bbase + (uint64_t)((dj * CIC + 2 * kc) * 3 * NOUT);
-              // [ga, gb] with accumulate flag acc: one MMA of N = (gb-ga+1) NOUT
-              auto issue = [&](int ga, int gb, uint32_t acc) {
-                mma_f16(dcol + (uint32_t)(NOUT * ga), ad, bw + (uint64_t)(ga * NOUT),
-                        idesc_f16(128, (gb - ga + 1) * NOUT), acc);
-              };
-              if (dj == 0 && kc == 0) {
-                if (gn > g0) issue(g0, gn - 1, 0u);
-                if (gn <= g1) issue(gn, g1, 1u);
-              } else {
-                issue(g0, g1, 1u);
-              }
+              const uint64_t bd = bbase + (uint64_t)((dj * CIC + 2 * kc) * 3 * NOUT + g0 * NOUT);
+              mma_f16(d, ad, bd, idesc, 1u);
             }
           }
         }
@@ -558,6 +568,15 @@ __global__ void __launch_bounds__(kColThreads, 1) conv3x3_col_kernel(const ConvA
           }
         }
       }
+      // return the columns this warp read to zero for the MMAs of tile it + 2
+#pragma unroll 1
+      for (int q = warp >> 2; q < kv; q += kColEpiWarps / 4) {
+        const uint32_t taddr =
+            tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(tb * kCT * NOUT + NOUT * (kCT - 1 - q));
+#pragma unroll
+        for (int c0 = 0; c0 < NOUT; c0 += 16) tmem_zero_x16(taddr + (uint32_t)c0);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
       if (lane == 0) bar_arrive(&tempty[tb]);
