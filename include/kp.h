@@ -53,9 +53,12 @@ typedef enum {
 
 typedef enum {
   KP_PREC_FP64 = 0,  /* everything in FP64 */
-  KP_PREC_MIXED = 1  /* FP32 Krylov vectors and stencil inside FP64 iterative
-                        refinement; FP64 reductions, Hessenberg and Givens;
-                        BF16 tensor-core projection with FP32 accumulation */
+  KP_PREC_MIXED = 1  /* FP32 Krylov vectors and stencil inside iterative
+                        refinement whose solution, operator coefficients and
+                        true residual b - A x are double-float (a pair of FP32
+                        values, about 48 bits, on the FP32 pipe; FP64 in and
+                        out); FP64 Hessenberg and Givens; BF16 tensor-core
+                        projection with FP32 accumulation */
 } kp_precision;
 
 typedef struct kp_ctx kp_ctx;
@@ -96,7 +99,7 @@ typedef struct {
   int inner_digits;  /* mixed precision: each FP32 inner GMRES reduces its
                         residual estimate by 10^-inner_digits (or to a tenth of
                         the outer tolerance, whichever is reached first) before
-                        the FP64 iterative refinement recomputes the true
+                        the iterative refinement recomputes the true
                         residual; 1..7, 0 = 5                                     */
   int cluster_blocks_per_sm; /* cluster solver (grids above 4096 points): resident
                         CTAs per SM, 1 or 2 (16-CTA clusters: 2 or 4); 0 = 2

@@ -1,20 +1,24 @@
 // kp_gmres_mixed.cu -- mixed-precision solver for the five-point systems of
-// Sec. 2.3: FP64 iterative refinement around an FP32 restarted GMRES.
+// Sec. 2.3: iterative refinement around an FP32 restarted GMRES.
 //
 // On GB300 an SM retires about 2 FP64 FMAs per clock against 128 FP32 FMAs,
 // so the Krylov work (stencil, Gram-Schmidt updates, normalisation) runs in
-// FP32 on FP32 vectors held in shared memory, and FP64 is kept where the
-// answer's accuracy is decided:
-//   * the true residual r = b - A x and the solution x are FP64;
+// FP32 on FP32 vectors held in shared memory, and the refinement's
+// high-precision arithmetic -- the solution x, the operator coefficients and
+// the true residual r = b - A x -- runs in double-float (kp_dd.cuh: a pair of
+// floats, about 48 bits) on the FP32 pipe as well, with FP64 inputs split by
+// integer operations and the solution written back as FP64.  The residual's
+// error is a few units of 2^-44 times ||b||, far below every tolerance the
+// solver is asked for (>= 1e-12):
 //   * inner products of FP32 vectors are summed in FP32 within a warp (its
-//     few hundred products) and in FP64 across warps; the Gram-Schmidt
-//     coefficients of both CGS passes, all norms and the residual norms are
-//     FP64 numbers;
+//     few hundred products) and across warps, then held as FP64 numbers: the
+//     Gram-Schmidt coefficients of both CGS passes, all norms and the residual
+//     norms;
 //   * the Hessenberg matrix, Givens rotations and least-squares solve are FP64.
-// Outer loop: r = b - A x (FP64); inner GMRES(m) on A d = r in FP32 until the
-// residual estimate drops by eta = 1e-5 (FP32 cannot resolve much more) or to
-// a tenth of the outer target; x += d.  The outer loop stops on the FP64 true
-// residual, so every returned solve meets ||b - A x|| <= tol ||b|| in FP64.
+// Outer loop: r = b - A x (double-float); inner GMRES(m) on A d = r in FP32
+// until the residual estimate drops by eta = 1e-5 (FP32 cannot resolve much
+// more) or to a tenth of the outer target; x += d.  The outer loop stops on
+// the true residual, so every returned solve meets ||b - A x|| <= tol ||b||.
 //
 // The operator is applied from q_x = f_x/(2h) - e (m~_E - m~_W) and q_y per
 // point (two numbers instead of four coefficients, which keeps the 4096-point
@@ -24,6 +28,7 @@
 // listing after Eq. 11.  The Arnoldi process runs on A - cd I (same Krylov
 // space, H_A = H + cd I), which avoids the cancellation of the large
 // diagonal in Gram-Schmidt -- in FP32 it would cost a digit per step.
+#include "kp_dd.cuh"
 #include "kp_internal.cuh"
 
 namespace kp {
@@ -31,7 +36,8 @@ namespace {
 
 struct SmemM {
   float* V;      // [S][npad] FP32 Krylov vectors
-  double* xs;    // [npad] FP64 solution
+  float* xh;     // [npad] solution, double-float hi
+  float* xl;     // [npad] and lo parts
   double* red;   // [NWARPS][kMaxV]
   double* hb;    // [kMaxV]
   double* Hr;    // [(m+1) * m]
@@ -46,8 +52,9 @@ struct SmemM {
 
 __device__ __forceinline__ SmemM carve_m(double* base, int npad, int nwarps, int m, int S) {
   SmemM s;
-  s.xs = base;
-  s.red = s.xs + npad;
+  s.xh = reinterpret_cast<float*>(base);
+  s.xl = s.xh + npad;
+  s.red = base + npad;
   s.hb = s.red + nwarps * kMaxV;
   s.Hr = s.hb + kMaxV;
   s.g = s.Hr + (m + 1) * m;
@@ -104,56 +111,71 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
     float* capV = capture ? p.capV32 + (size_t)cidx * (p.cap_a + 1) * p.cap_ld : nullptr;
     double* capH = capture ? p.capH + (size_t)cidx * (p.cap_a + 1) * p.cap_a : nullptr;
 
-    // q_x, q_y per point (FP32 copies for the Krylov operator), the FP64 E and N
-    // coefficients cE = q_x - c, cN = q_y - c for the residual (W and S follow:
-    // cW = -2c - cE, cS = -2c - cN), and neighbour masks
-    double cEx[EPT], cNy[EPT];
+    // q_x, q_y per point (FP32 copies for the Krylov operator), the
+    // double-float E and N coefficients cE = q_x - c, cN = q_y - c for the
+    // residual (W and S follow: cW = -2c - cE, cS = -2c - cN), and neighbour
+    // masks; in the judge mode (a given guess) the warm start's residual norm
+    // comes out of the same loads: sw = sum of r_warm^2 over this thread's points
+    const bool judge = p.x0_mode == X0_GUESS_PROJECT;
+    const dd ccd = dd_from_double(cc), eed = dd_from_double(ee), cdd = dd_from_double(cd);
+    const dd i2hd = dd_from_double(i2h), c2d = dd_from_double(2.0 * cc);
+    dd cE[EPT], cN[EPT];
     float qxf[EPT], qyf[EPT];
     unsigned msk[EPT];                          // bit0 E, bit1 W, bit2 N, bit3 S present
+    float sw = 0.f;
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
       const int pp = tid + k * NT;
-      double qx = 0.0, qy = 0.0;
+      dd qx = {0.f, 0.f}, qy = {0.f, 0.f};
       msk[k] = 0;
       if (pp < N) {
         const int i = pp / H, j = pp - i * H;
-        const double mE = (i + 1 < W) ? d.mt[pp + H] : 0.0;
-        const double mW = (i > 0) ? d.mt[pp - H] : 0.0;
-        const double mN = (j + 1 < H) ? d.mt[pp + 1] : 0.0;
-        const double mS = (j > 0) ? d.mt[pp - 1] : 0.0;
-        if (drift) {
-          const double fxp = d.fx ? d.fx[pp] : 0.0;
-          const double fyp = d.fy ? d.fy[pp] : 0.0;
-          qx = fxp * i2h - ee * (mE - mW);
-          qy = fyp * i2h - ee * (mN - mS);
-        } else {                                // f = 0: the method's systems
-          qx = -ee * (mE - mW);
-          qy = -ee * (mN - mS);
-        }
         msk[k] = (i + 1 < W ? 1u : 0u) | (i > 0 ? 2u : 0u) | (j + 1 < H ? 4u : 0u) | (j > 0 ? 8u : 0u);
+        const dd mE = dd_from_double((msk[k] & 1u) ? d.mt[pp + H] : 0.0);
+        const dd mW = dd_from_double((msk[k] & 2u) ? d.mt[pp - H] : 0.0);
+        const dd mN = dd_from_double((msk[k] & 4u) ? d.mt[pp + 1] : 0.0);
+        const dd mS = dd_from_double((msk[k] & 8u) ? d.mt[pp - 1] : 0.0);
+        qx = dd_mul(eed, dd_sub(mW, mE));
+        qy = dd_mul(eed, dd_sub(mS, mN));
+        if (drift) {
+          if (d.fx) qx = dd_add(qx, dd_mul(dd_from_double(d.fx[pp]), i2hd));
+          if (d.fy) qy = dd_add(qy, dd_mul(dd_from_double(d.fy[pp]), i2hd));
+        }
+        cE[k] = dd_sub(qx, ccd);
+        cN[k] = dd_sub(qy, ccd);
+        if (judge) {
+          const dd mC = dd_from_double(d.mt[pp]);
+          dd t = dd_sub(dd_from_double(d.b[pp]), dd_mul(cdd, mC));
+          t = dd_sub(t, dd_mul(cE[k], dd_sub(mE, mW)));
+          t = dd_sub(t, dd_mul(cN[k], dd_sub(mN, mS)));
+          t = dd_add(t, dd_mul(c2d, dd_add(mW, mS)));
+          sw = fmaf(t.hi, t.hi, sw);
+        }
+      } else {
+        cE[k] = cN[k] = dd{0.f, 0.f};
       }
-      cEx[k] = qx - cc;
-      cNy[k] = qy - cc;
-      qxf[k] = (float)qx;
-      qyf[k] = (float)qy;
+      qxf[k] = qx.hi;
+      qyf[k] = qy.hi;
     }
-    // r = b - A v in FP64 with the masked neighbours:
-    // A v = cd v + cE (vE - vW) - 2c vW + cN (vN - vS) - 2c vS
-    const double c2 = 2.0 * cc;
-    auto residual_of = [&](const double* v, double (&out)[EPT]) {
+    // r = b - A x in double-float with the masked neighbours (A x = cd x +
+    // cE (xE - xW) - 2c xW + cN (xN - xS) - 2c xS); out = its hi part, which
+    // is all the FP32 Krylov and the norms need
+    auto residual_of = [&](float (&out)[EPT]) {
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
         const int pp = tid + k * NT;
-        out[k] = 0.0;
+        out[k] = 0.f;
         if (pp < N) {
-          const double xE = (msk[k] & 1u) ? v[pp + H] : 0.0;
-          const double xW = (msk[k] & 2u) ? v[pp - H] : 0.0;
-          const double xN = (msk[k] & 4u) ? v[pp + 1] : 0.0;
-          const double xS = (msk[k] & 8u) ? v[pp - 1] : 0.0;
-          double t = fma(-cd, v[pp], d.b[pp]);
-          t = fma(-cEx[k], xE - xW, t);
-          t = fma(-cNy[k], xN - xS, t);
-          out[k] = fma(c2, xW + xS, t);
+          const dd z = {0.f, 0.f};
+          const dd xE = (msk[k] & 1u) ? dd{sm.xh[pp + H], sm.xl[pp + H]} : z;
+          const dd xW = (msk[k] & 2u) ? dd{sm.xh[pp - H], sm.xl[pp - H]} : z;
+          const dd xN = (msk[k] & 4u) ? dd{sm.xh[pp + 1], sm.xl[pp + 1]} : z;
+          const dd xS = (msk[k] & 8u) ? dd{sm.xh[pp - 1], sm.xl[pp - 1]} : z;
+          dd t = dd_sub(dd_from_double(d.b[pp]), dd_mul(cdd, dd{sm.xh[pp], sm.xl[pp]}));
+          t = dd_sub(t, dd_mul(cE[k], dd_sub(xE, xW)));
+          t = dd_sub(t, dd_mul(cN[k], dd_sub(xN, xS)));
+          t = dd_add(t, dd_mul(c2d, dd_add(xW, xS)));
+          out[k] = t.hi;
         }
       }
     };
@@ -171,70 +193,80 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
         }
       }
     };
-    auto bval = [&](int pp) { return (pp < N) ? d.b[pp] : 0.0; };
-
-    // initial guess (FP64)
+    auto bhi = [&](int pp) { return (pp < N) ? dd_from_double(d.b[pp]).hi : 0.f; };
+    // x from an FP64 field (or zero), split into double-float
+    auto load_x = [&](const double* src) {
 #pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-      const int pp = tid + k * NT;
-      double x0 = 0.0;
-      if (pp < N) {
-        if (p.gdelta && (p.x0_mode == X0_READ || p.x0_mode == X0_GUESS_PROJECT))   // learned guess
-          x0 = fma(p.grho[sysi] / p.gdiv, (double)p.gdelta[(size_t)sysi * p.gdelta_ld + pp], d.mt[pp]);
-        else if (p.x0_mode == X0_READ || p.x0_mode == X0_GUESS_PROJECT) x0 = d.x[pp];
-        else if (p.x0_mode == X0_WARM) x0 = d.mt[pp];
+      for (int k = 0; k < EPT; ++k) {
+        const int pp = tid + k * NT;
+        const dd v = (src && pp < N) ? dd_from_double(src[pp]) : dd{0.f, 0.f};
+        sm.xh[pp] = v.hi;
+        sm.xl[pp] = v.lo;
       }
-      sm.xs[pp] = x0;
+    };
+
+    // initial guess
+    if (p.gdelta && (p.x0_mode == X0_READ || judge)) {
+      // the learned guess x_init = m~ + dt rho net, from the network's FP32
+      // output, in double-float
+      const float sg = (float)(p.grho[sysi] / p.gdiv);
+      const float* dl = p.gdelta + (size_t)sysi * p.gdelta_ld;
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const int pp = tid + k * NT;
+        const dd v = pp < N ? dd_add_f(dd_from_double(d.mt[pp]), sg * dl[pp]) : dd{0.f, 0.f};
+        sm.xh[pp] = v.hi;
+        sm.xl[pp] = v.lo;
+      }
+    } else {
+      load_x(p.x0_mode == X0_READ || judge ? d.x : p.x0_mode == X0_WARM ? d.mt : nullptr);
     }
     unsigned long long proj_flops = 0;
-    double r[EPT];
-    auto residual = [&]() { residual_of(sm.xs, r); };
-    bool r_current = false;                         // r already holds b - A x0 (FP64)
-    if (p.x0_mode == X0_GUESS_PROJECT) {
-      // the judge of a given guess (the learned one): its FP64 residual
-      // against the warm start's; a kept guess is projected below, the
-      // warm start (the fallback) starts unprojected, as in the warm mode
+    float r[EPT];
+    auto residual = [&]() { residual_of(r); };
+    bool r_current = false;                         // r already holds b - A x0
+    if (judge) {
+      // the judge of a given guess (the learned one): its true residual
+      // against the warm start's (sw, from the set-up); a kept guess is
+      // projected below, the warm start (the fallback) starts unprojected, as
+      // in the warm mode
       __syncthreads();                              // x_init complete for the stencil
       residual();
-      double rw[EPT];
-      residual_of(d.mt, rw);
-      block_partials<NT>(2, [&](int i) {
-        double s = 0.0;
+      block_partials_f32x<NT>(2, [&](int i) {
+        float s = 0.f;
+        if (i == 0) {
 #pragma unroll
-        for (int k = 0; k < EPT; ++k) s += (i == 0) ? r[k] * r[k] : rw[k] * rw[k];
-        return s;
-      }, sm.red);
-      if (tid == 0) sm.fl[5] = cross_warp<NT>(sm.red, 1) < cross_warp<NT>(sm.red, 0);
-      __syncthreads();
-      if (sm.fl[5]) {                               // the warm start wins
-#pragma unroll
-        for (int k = 0; k < EPT; ++k) {
-          const int pp = tid + k * NT;
-          r[k] = rw[k];
-          if (pp < N) sm.xs[pp] = d.mt[pp];
+          for (int k = 0; k < EPT; ++k) s = fmaf(r[k], r[k], s);
+        } else {
+          s = sw;
         }
+        return s;
+      }, red32);
+      if (warp == 0) {
+        cross_warp_f32<NT>(red32, 2, sm.hb, lane);
+        __syncwarp();
+        if (lane == 0) sm.fl[5] = sm.hb[1] < sm.hb[0];
       }
-      r_current = true;
+      __syncthreads();
+      if (sm.fl[5]) load_x(d.mt);                   // the warm start wins
+      r_current = !sm.fl[5];
       proj_flops = 26ull * (unsigned long long)N;
       // Sec. 3, Phase 2 on the residual of the guess: r = b - A x_init
-      // (FP64), c = V^T r (FP32 products, FP64 sums), alpha = H_a^{-1} c,
-      // x0 = x_init + V alpha
+      // (double-float), c = V^T r (FP32 products and sums), alpha = H_a^{-1} c
+      // (FP64), x0 = x_init + V alpha
       const int sl = d.slot + parity_base;
       const SlotMeta mt = p.slotMeta[sl];
       if (!sm.fl[5] && mt.timestep == tstep && mt.N == N && mt.a > 0) {   // uniform per block
         const int a = mt.a;
         const int nv = mt.lsq ? a + 1 : a;
         const float* V = p.slotV32 + (size_t)sl * (p.max_a + 1) * p.slot_ld;
-        float rv[EPT];
-#pragma unroll
-        for (int k = 0; k < EPT; ++k) rv[k] = (float)r[k];
         block_partials_f32x<NT>(nv, [&](int i) {
           const float* vi = V + (size_t)i * p.slot_ld;
           float s = 0.f;
 #pragma unroll
           for (int k = 0; k < EPT; ++k) {
             const int pp = tid + k * NT;
-            if (pp < N) s = fmaf(vi[pp], rv[k], s);
+            if (pp < N) s = fmaf(vi[pp], r[k], s);
           }
           return s;
         }, red32);
@@ -254,7 +286,9 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
           if (pp < N) {
             float xv = 0.f;
             for (int i = 0; i < a; ++i) xv = fmaf(red32[i], V[(size_t)i * p.slot_ld + pp], xv);
-            sm.xs[pp] += (double)xv;
+            const dd xn = dd_add_f(dd{sm.xh[pp], sm.xl[pp]}, xv);
+            sm.xh[pp] = xn.hi;
+            sm.xl[pp] = xn.lo;
           }
         }
         r_current = false;
@@ -277,7 +311,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
         } else {
           float bv[EPT];
 #pragma unroll
-          for (int k = 0; k < EPT; ++k) bv[k] = (float)bval(tid + k * NT);
+          for (int k = 0; k < EPT; ++k) bv[k] = bhi(tid + k * NT);
           block_partials_f32x<NT>(nv, [&](int i) {
             const float* vi = V + (size_t)i * p.slot_ld;
             float s = 0.f;
@@ -305,7 +339,8 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
           if (pp < N) {
             float xv = 0.f;
             for (int i = 0; i < a; ++i) xv = fmaf(red32[i], V[(size_t)i * p.slot_ld + pp], xv);
-            sm.xs[pp] = (double)xv;
+            sm.xh[pp] = xv;
+            sm.xl[pp] = 0.f;
           }
         }
         proj_flops = (unsigned long long)(2 * nv + 2 * a) * (unsigned long long)N;
@@ -343,7 +378,8 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
             if (pp < N) {
               float xv = 0.f;
               for (int i = 0; i < a; ++i) xv = fmaf(red32[i], V[(size_t)i * p.slot_ld + pp], xv);
-              sm.xs[pp] = (double)xv;
+              sm.xh[pp] = xv;
+              sm.xl[pp] = 0.f;
             }
           }
         }
@@ -353,22 +389,26 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
     __syncthreads();
     if (p.x0_mode == X0_ZERO) {
 #pragma unroll
-      for (int k = 0; k < EPT; ++k) r[k] = bval(tid + k * NT);
+      for (int k = 0; k < EPT; ++k) r[k] = bhi(tid + k * NT);
     } else if (!r_current) {
       residual();
     }
-    block_partials<NT>(2, [&](int i) {
-      double s = 0.0;
+    block_partials_f32x<NT>(2, [&](int i) {
+      float s = 0.f;
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
-        const double bv = bval(tid + k * NT);
-        s += (i == 0) ? bv * bv : r[k] * r[k];
+        const float v = (i == 0) ? bhi(tid + k * NT) : r[k];
+        s = fmaf(v, v, s);
       }
       return s;
-    }, sm.red);
-    if (tid == 0) {
-      sm.sc[0] = sqrt(cross_warp<NT>(sm.red, 0));
-      sm.sc[1] = sqrt(cross_warp<NT>(sm.red, 1));
+    }, red32);
+    if (warp == 0) {
+      cross_warp_f32<NT>(red32, 2, sm.hb, lane);
+      __syncwarp();
+      if (lane == 0) {
+        sm.sc[0] = sqrt(sm.hb[0]);
+        sm.sc[1] = sqrt(sm.hb[1]);
+      }
     }
     __syncthreads();
     const double bnorm = sm.sc[0];
@@ -376,7 +416,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
     int steps = 0, status = KP_NOT_CONVERGED, outer = 0, restarts = 0;
     if (bnorm == 0.0) {
 #pragma unroll
-      for (int k = 0; k < EPT; ++k) sm.xs[tid + k * NT] = 0.0;
+      for (int k = 0; k < EPT; ++k) sm.xh[tid + k * NT] = sm.xl[tid + k * NT] = 0.f;
       beta = 0.0;
       status = KP_OK;
     }
@@ -391,12 +431,12 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
       const double target = (capture && first) ? p.tol * bnorm : fmax(kEta * beta, 0.1 * p.tol * bnorm);
       // ---- inner FP32 GMRES(m) on A d = r, from d = 0
       {
-        const double ib = 1.0 / beta;
+        const float ib = 1.f / (float)beta;
         float* v0 = slot(0);
 #pragma unroll
         for (int k = 0; k < EPT; ++k) {
           const int pp = tid + k * NT;
-          const float v = (float)(r[k] * ib);
+          const float v = r[k] * ib;
           v0[pp] = v;
           if (capture && first && pp < N) {
             capV[pp] = v;
@@ -579,23 +619,29 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
         }
       }
       __syncthreads();
-      // d = V y in FP32, x += d in FP64
+      // d = V y in FP32, x += d in double-float
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
         const int pp = tid + k * NT;
         float dv = 0.f;
         for (int i = 0; i < kdone; ++i) dv = fmaf(red32[i], slot(i)[pp], dv);
-        sm.xs[pp] += (double)dv;
+        const dd xn = dd_add_f(dd{sm.xh[pp], sm.xl[pp]}, dv);
+        sm.xh[pp] = xn.hi;
+        sm.xl[pp] = xn.lo;
       }
       __syncthreads();
-      residual();                                 // FP64 true residual
-      block_partials<NT>(1, [&](int) {
-        double s = 0.0;
+      residual();                                 // the true residual (double-float)
+      block_partials_f32x<NT>(1, [&](int) {
+        float s = 0.f;
 #pragma unroll
-        for (int k = 0; k < EPT; ++k) s += r[k] * r[k];
+        for (int k = 0; k < EPT; ++k) s = fmaf(r[k], r[k], s);
         return s;
-      }, sm.red);
-      if (tid == 0) sm.sc[1] = sqrt(cross_warp<NT>(sm.red, 0));
+      }, red32);
+      if (warp == 0) {
+        cross_warp_f32<NT>(red32, 1, sm.hb, lane);
+        __syncwarp();
+        if (lane == 0) sm.sc[1] = sqrt(sm.hb[0]);
+      }
       __syncthreads();
       beta = sm.sc[1];
       ++outer;
@@ -618,8 +664,8 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
     for (int k = 0; k < EPT; ++k) {
       const int pp = tid + k * NT;
       if (pp < N) {
-        d.x[pp] = sm.xs[pp];
-        if (p.bnext) p.bnext[(size_t)sysi * p.bnext_ld + pp] = __float2bfloat16_rn((float)sm.xs[pp]);
+        d.x[pp] = dd_to_double(dd{sm.xh[pp], sm.xl[pp]});
+        if (p.bnext) p.bnext[(size_t)sysi * p.bnext_ld + pp] = __float2bfloat16_rn(sm.xh[pp]);
       }
     }
     if (tid == 0) {
@@ -633,8 +679,8 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
       }
       if (p.acc) {
         StepAcc* a = p.acc + tstep;
-        // FP64 flops of the refinement (residuals, x update); FP32 Krylov work
-        // is counted separately
+        // high-precision flops of the refinement (residuals, x update: in
+        // double-float); FP32 Krylov work is counted separately
         const unsigned long long fl = (unsigned long long)(14 + restarts * 13) * (unsigned long long)N;
         const unsigned long long fl32 = (gmres_flops(steps, m) - 14ull) * (unsigned long long)N;
         if (p.acc_kind == 0) {
