@@ -2,16 +2,19 @@
 """Benchmark: target systems solved per second to relative residual 1e-8,
 projected + refine vs plain GMRES, on one GB300 (or N replicas under torchrun).
 
-Workload (default): 32x32x3 blob images, 10 templates with one seed image
-each and 256 target images, T = 1000 implicit timesteps, GMRES restart 40,
-FP64 throughout -- 768 target systems and 30 seed systems per timestep.
-Synthetic images of the paper's CIFAR-10 shape stand in for the dataset.
-
-One step = one whole march n = 1..T over the batch (every row of the hot
-path: right-hand sides, seed GMRES with basis capture, basis store,
-projection, refine), from the initial images already resident in HBM.  The
-per-timestep working set fits in L2, so L2 is flushed (a 512 MiB write)
-between timed steps, outside the timed events.
+Workload (default): the learned + projected batched march at 128x128x3 --
+16 seed and 4096 target blob images (48 seed and 12288 target channels),
+T = 1000, mixed precision, the four-layer 32-channel network trained first on
+pairs the method generates.  One step = one 4-timestep slice of the full
+batch, the slices starting from the march's own states at timesteps 0, 250,
+500 and 750 (taken by one warm-start march beforehand); every mode (learned +
+projected, the guess alone, plain GMRES from zero and warm-started, the
+paper's projection) runs the same slices.  Each step's states (1.6 GB)
+exceed L2.  The 32x32x3 FP64 march, the 64x64x3 mixed-precision march and the
+batched uneven sizes follow as secondary keys of the same line (each a whole
+march of T = 1000 per step, L2 flushed between timed steps); --config 2/3/4
+runs one of them alone.  Synthetic images of the paper's CIFAR-10 / CelebA
+shapes stand in for the datasets.
 
 --impl reference times the FP64 CPU oracle on the host cores instead (a
 bounded sample of the same workload per step).
@@ -39,9 +42,10 @@ from paper_2511_17634_gb300 import synth  # noqa: E402
 FP64_PEAK_TFLOPS = 152 * 2070e6 * 4 / 1e12
 FP32_PEAK_TFLOPS = 152 * 2070e6 * 256 / 1e12
 ALU_PEAK_SOURCE = "derived: 152 SM x 2 FP64 / 128 FP32 FMA/clk x 2.07 GHz"
-# FP32 flop slots (an FMA issue = 2) one high-precision flop of the 128x128
-# solver's refinement costs in double-float: the residual's 13 flops per point
-# take about 105 FP32 instructions (TwoSum / TwoProduct forms), 8 per flop
+# FP32 flop slots (an FMA issue = 2) one high-precision flop of the
+# mixed-precision solvers' refinement costs in double-float: the residual's 13
+# flops per point take about 105 FP32 instructions (TwoSum / TwoProduct
+# forms), 8 per flop
 DD_SLOTS_PER_FLOP = 16
 
 
