@@ -344,10 +344,11 @@ __global__ void __launch_bounds__(kConvThreads, 1) conv3x3_tc_kernel(const ConvA
 //
 // A super tile is kCT output columns [i0, i0 + Kv) of one sample; its input
 // window is columns i0-1 .. i0+Kv (whole padded columns, zero rows included).
-// The first MMA of an input column overwrites the groups whose output column
-// it touches first (accumulate flag 0) and accumulates the others, so TMEM
-// needs no clearing.  Rows j >= H of a tile (H < 128) read the next column or
-// the slack rows at the end of the stage and land in discarded D rows.
+// Every MMA accumulates: the accumulators are zeroed once after allocation and
+// each epilogue stores zeros over the columns it has read, so no input column
+// needs a separate MMA for the output columns it reaches first.  Rows j >= H
+// of a tile (H < 128) read the next column or the slack rows at the end of
+// the stage and land in discarded D rows.
 constexpr int kCT = 8;                  // output columns per super tile
 constexpr int kColEpiWarps = 8;         // two epilogue warps per TMEM lane quadrant
 constexpr int kColThreads = 32 * (kColEpiWarps + 2);   // + producer warp + MMA warp
