@@ -6,11 +6,11 @@ Workload (default): the learned + projected batched march at 128x128x3 --
 16 seed and 4096 target blob images (48 seed and 12288 target channels),
 T = 1000, mixed precision, the four-layer 32-channel network trained first on
 pairs the method generates.  One step = one 4-timestep slice of the full
-batch, the slices starting from the march's own states at timesteps 0, 250,
-500 and 750 (taken by one warm-start march beforehand); every mode (learned +
-projected, the guess alone, plain GMRES from zero and warm-started, the
-paper's projection) runs the same slices.  Each step's states (1.6 GB)
-exceed L2.  The 32x32x3 FP64 march, the 64x64x3 mixed-precision march and the
+batch from each of the march's own states at timesteps 0, 250, 500 and 750
+(taken by one warm-start march beforehand), 16 timesteps in all; every mode
+(learned + projected, the guess alone, plain GMRES from zero and
+warm-started, the paper's projection) runs the same slices.  Each slice's
+states (1.6 GB) exceed L2.  The 32x32x3 FP64 march, the 64x64x3 mixed-precision march and the
 batched uneven sizes follow as secondary keys of the same line (each a whole
 march of T = 1000 per step, L2 flushed between timed steps); --config 2/3/4
 runs one of them alone.  Synthetic images of the paper's CIFAR-10 / CelebA
@@ -538,15 +538,16 @@ def run_north_star(args):
     stream = torch.cuda.current_stream()
 
     def timed(plan, k_steps, warmup, profile=False):
-        """k_steps slices of SLICE timesteps, slice j from anchor j mod len;
-        returns the seconds (max over ranks).  With profile, the timed loop is
-        the profiler's capture range (cudaProfilerStart/Stop: what ncu
-        --profile-from-start off records)."""
+        """k_steps steps, each one slice of SLICE timesteps from every anchor
+        (so every step weighs early, middle and late timesteps alike), the
+        slices' CUDA-event times summed; returns the seconds (max over ranks).
+        With profile, the timed loop is the profiler's capture range
+        (cudaProfilerStart/Stop: what ncu --profile-from-start off records)."""
         for j in range(warmup):
-            a = anchors[j % len(anchors)]
-            s_buf.copy_(snaps[j % len(anchors)][0])
-            t_buf.copy_(snaps[j % len(anchors)][1])
-            plan.run(a, SLICE)
+            for q, a in enumerate(anchors):
+                s_buf.copy_(snaps[q][0])
+                t_buf.copy_(snaps[q][1])
+                plan.run(a, SLICE)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -555,16 +556,16 @@ def run_north_star(args):
         if profile:
             torch.cuda.cudart().cudaProfilerStart()
         for j in range(k_steps):
-            q = j % len(anchors)
-            s_buf.copy_(snaps[q][0])
-            t_buf.copy_(snaps[q][1])
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            plan.run(anchors[q], SLICE)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            total += e0.elapsed_time(e1) / 1000.0
+            for q, a in enumerate(anchors):
+                s_buf.copy_(snaps[q][0])
+                t_buf.copy_(snaps[q][1])
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                plan.run(a, SLICE)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                total += e0.elapsed_time(e1) / 1000.0
         if profile:
             torch.cuda.cudart().cudaProfilerStop()
         return max_over_ranks(total, dist, dev)
@@ -592,7 +593,8 @@ def run_north_star(args):
                 "launches_per_slice": nl / len(anchors),
                 "max_rel_res": maxres, "not_converged": nc}
 
-    nsys_step = world * nt * SLICE
+    nsys_slice = world * nt * SLICE
+    nsys_step = nsys_slice * len(anchors)          # a step: one slice from every anchor
     modes = [("learned_projected", kp.MARCH_LEARNED), ("plain_x0_zero", kp.MARCH_PLAIN),
              ("plain_warm_start", kp.MARCH_WARM), ("projected_paper", kp.MARCH_PROJECTED),
              ("learned_only", kp.MARCH_LEARNED_ONLY)]
@@ -603,7 +605,7 @@ def run_north_star(args):
         for name, mode in modes:
             plan = kp.March(ctx, groups, T, wl.g2, mode=mode,
                             cnn=net if mode in (kp.MARCH_LEARNED, kp.MARCH_LEARNED_ONLY) else None, **common)
-            k = args.steps if name == "learned_projected" else len(anchors)
+            k = args.steps if name == "learned_projected" else 1
             w = args.warmup if name == "learned_projected" else 1
             t = timed(plan, k, w, profile=name == "learned_projected")
             res[name] = {"value": nsys_step * k / t, "unit": "systems/s", "seconds": t, "steps": k,
@@ -615,61 +617,64 @@ def run_north_star(args):
     head = res["learned_projected"]
     value = head["value"]
     # end to end through the public API, pipelined as a serving loop runs it:
-    # each step's states come from pinned host memory on a copy stream while
-    # the previous step computes, and its final states go back to pinned host
+    # each slice's states come from pinned host memory on a copy stream while
+    # the previous slice computes, and its final states go back to pinned host
     # memory while the next one computes.  Two plans on two sets of device
-    # states, so a copy never touches the states of a running step; every
-    # step's copies are inside the timed region (fill and drain included).
+    # states, so a copy never touches the states of a running slice; every
+    # slice's copies are inside the timed region (fill and drain included);
+    # two steps of slices.
     hs = [(a.cpu().pin_memory(), b.cpu().pin_memory()) for a, b in snaps]
     outs = [torch.empty_like(hs[0][1]).pin_memory() for _ in range(2)]
-    h2d = hs[0][0].numel() * 8 + hs[0][1].numel() * 8
-    d2h = outs[0].numel() * 8
+    h2d = (hs[0][0].numel() * 8 + hs[0][1].numel() * 8) * len(anchors)
+    d2h = outs[0].numel() * 8 * len(anchors)
     bufs = [(s_buf, t_buf), (s_buf.clone(), t_buf.clone())]
     plans = [keep, kp.March(ctx, [(bufs[1][0], bufs[1][1], g.target_seed, H, W)], T, wl.g2,
                             mode=kp.MARCH_LEARNED, cnn=net, **common)]
     plans[1].run(anchors[0], SLICE)                 # graph instantiation outside the timing
-    cs = torch.cuda.Stream()
+    # one copy stream per direction, so a slice's results going out and the
+    # next slice's states coming in overlap each other as well as the compute
+    cs_in, cs_out = torch.cuda.Stream(), torch.cuda.Stream()
     ready = [torch.cuda.Event() for _ in range(2)]
     done_ev = [torch.cuda.Event() for _ in range(2)]
     free = [torch.cuda.Event() for _ in range(2)]
-    nsteps = 2 * len(anchors)
+    nslices = 2 * len(anchors)                      # two steps
 
     def copy_in(j):
         sb, tb = bufs[j % 2]
         q = j % len(anchors)
-        with torch.cuda.stream(cs):
+        with torch.cuda.stream(cs_in):
             if j >= 2:
-                cs.wait_event(free[j % 2])           # results of step j - 2 are out
+                cs_in.wait_event(free[j % 2])       # results of slice j - 2 are out
             sb.copy_(hs[q][0], non_blocking=True)
             tb.copy_(hs[q][1], non_blocking=True)
-            ready[j % 2].record(cs)
+            ready[j % 2].record(cs_in)
 
     def copy_out(j):
-        with torch.cuda.stream(cs):
-            cs.wait_event(done_ev[j % 2])
+        with torch.cuda.stream(cs_out):
+            cs_out.wait_event(done_ev[j % 2])
             outs[j % 2].copy_(bufs[j % 2][1], non_blocking=True)
-            free[j % 2].record(cs)
+            free[j % 2].record(cs_out)
 
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    cs.wait_event(e0)
+    cs_in.wait_event(e0)
     copy_in(0)
-    for j in range(nsteps):
-        if j + 1 < nsteps:
+    for j in range(nslices):
+        if j + 1 < nslices:
             copy_in(j + 1)
         stream.wait_event(ready[j % 2])
         plans[j % 2].run(anchors[j % len(anchors)], SLICE)
         done_ev[j % 2].record(stream)
         copy_out(j)
-    stream.wait_event(free[(nsteps - 1) % 2])
+    stream.wait_event(free[(nslices - 1) % 2])
     e1.record(stream)
     torch.cuda.synchronize()
     plans[1].close()
     e2e_total = e0.elapsed_time(e1) / 1000.0
     e2e_total = max_over_ranks(e2e_total, dist, dev)
-    e2e_value = nsys_step * nsteps / e2e_total
+    e2e_value = nsys_slice * nslices / e2e_total
     # per-solve error of the learned path against the oracle's FP64 GMRES on
     # the same systems (the same m^{n-1}), 32 sampled targets at every anchor
     err = None
@@ -745,14 +750,16 @@ def run_north_star(args):
         "data": "synthetic (seeded blob images shaped like the paper's 128x128 CelebA set)",
         "config": {"workload": wl.name, "path": "learned guess + residual-form projection + refine (batched march)",
                    "T": T, "targets": nt, "seeds": wl.n_seed_planes, "grid": [H, W],
-                   "timesteps_per_step": SLICE, "anchor_timesteps": anchors, "tol": wl.tol, "m": wl.m,
+                   "timesteps_per_step": SLICE * len(anchors),
+                   "step": f"one {SLICE}-timestep slice of the full batch from each anchor timestep",
+                   "anchor_timesteps": anchors, "tol": wl.tol, "m": wl.m,
                    "inference_batch": net.inference_batch, "inner_digits": args.inner_digits or 5,
                    "network_channels": list(args.channels or learned.CHANNELS),
                    "orthogonalisation": "CGS2" if reorth == 0 else "CGS+DGKS",
                    "parallelism": f"replicas x{world}",
-                   "l2": "not flushed: each step's states (1.6 GB) exceed L2"},
+                   "l2": "not flushed: each slice's states (1.6 GB) exceed L2"},
         "e2e": {"value": e2e_value, "unit": "systems/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": int(head["launches_per_slice"] * args.steps),
+        "gpu_launches": int(head["launches_per_slice"] * len(anchors) * args.steps),
         "roofline": solver_roof if dominant == "solver" else cnn_roof,
         "roofline_other": cnn_roof if dominant == "solver" else solver_roof,
         "cpu_baseline": cpu, "clocks": clk.summary(), "oracle_error": err,
