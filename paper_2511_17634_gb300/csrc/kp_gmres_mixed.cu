@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
       }
     }
     if (p.x0_mode == X0_PROJECT) {
-      // Sec. 3, Phase 2 with the seed's FP32 basis: c = V^T b (FP64 sums),
+      // Sec. 3, Phase 2 with the seed's FP32 basis: c = V^T b (FP32 products and sums),
       // alpha = H_a^{-1} c (FP64), x0 = V alpha
       const int sl = d.slot + parity_base;
       const SlotMeta mt = p.slotMeta[sl];
