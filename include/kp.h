@@ -97,7 +97,7 @@ typedef struct {
                         only at an exact breakdown or maxit), and its iterate is
                         the GMRES minimiser over that whole space            */
   int inner_digits;  /* mixed precision: each FP32 inner GMRES reduces its
-                        residual estimate by 10^-inner_digits (or to a tenth of
+                        residual estimate by 10^-inner_digits (or to half of
                         the outer tolerance, whichever is reached first) before
                         the iterative refinement recomputes the true
                         residual; 1..7, 0 = 5                                     */

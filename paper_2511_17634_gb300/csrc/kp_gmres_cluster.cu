@@ -396,7 +396,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_cluster_kernel(const GmresPara
     if (!isfinite(beta)) { status = KP_BREAKDOWN; break; }
     if (steps >= p.maxit || outer >= 64) break;
     const bool first = (outer == 0);
-    const double target = (capture && first) ? p.tol * bnorm : fmax(kEta * beta, 0.1 * p.tol * bnorm);
+    const double target = (capture && first) ? p.tol * bnorm : fmax(kEta * beta, kInnerFloor * p.tol * bnorm);
     {
       const float ib = 1.f / (float)beta;
       float* v0 = vloc(0);

@@ -17,8 +17,9 @@
 //   * the Hessenberg matrix, Givens rotations and least-squares solve are FP64.
 // Outer loop: r = b - A x (double-float); inner GMRES(m) on A d = r in FP32
 // until the residual estimate drops by eta = 1e-5 (FP32 cannot resolve much
-// more) or to a tenth of the outer target; x += d.  The outer loop stops on
-// the true residual, so every returned solve meets ||b - A x|| <= tol ||b||.
+// more) or to half the outer target (kInnerFloor); x += d.  The outer loop
+// stops on the true residual, so every returned solve meets
+// ||b - A x|| <= tol ||b||.
 //
 // The operator is applied from q_x = f_x/(2h) - e (m~_E - m~_W) and q_y per
 // point (two numbers instead of four coefficients, which keeps the 4096-point
@@ -428,7 +429,7 @@ __global__ void __launch_bounds__(NT, MINB) gmres_mixed_kernel(const GmresParams
       const bool first = (outer == 0);
       // the seed's captured cycle runs to the seed tolerance, so its basis has
       // the dimension the FP64 method would keep (Sec. 3, Phase 1)
-      const double target = (capture && first) ? p.tol * bnorm : fmax(kEta * beta, 0.1 * p.tol * bnorm);
+      const double target = (capture && first) ? p.tol * bnorm : fmax(kEta * beta, kInnerFloor * p.tol * bnorm);
       // ---- inner FP32 GMRES(m) on A d = r, from d = 0
       {
         const float ib = 1.f / (float)beta;

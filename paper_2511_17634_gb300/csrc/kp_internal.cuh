@@ -63,6 +63,12 @@ struct CapMeta {
 
 constexpr int kMaxM = 64;            // largest restart length / basis size
 constexpr int kMaxV = kMaxM + 8;     // values per block reduction
+// Mixed precision: an inner FP32 GMRES cycle stops once its residual estimate
+// is below max(eta beta, kInnerFloor tol ||b||).  The estimate tracks the true
+// residual to about 1e-7 of the cycle's starting residual (FP32 rounding of
+// the correction), so a floor at half the outer tolerance lets the true
+// residual that follows meet tol without solving the last cycle further down.
+constexpr double kInnerFloor = 0.5;
 
 struct GmresParams {
   const SysDesc* sys;
