@@ -482,7 +482,7 @@ def cpu_learned_sample(args, wl, g, params, snaps_host, threads):
     return nsys, wall
 
 
-def run_north_star(args):
+def run_learned_march(args):
     """The learned + projected batched path on the learned-guess workload
     (128x128x3, 16 seeds + 4096 targets, T = 1000, mixed precision)."""
     import torch
@@ -789,7 +789,7 @@ def main():
         return run_reference(args)
     rank = int(os.environ.get("RANK", "0"))
     if args.config == 5:
-        line, dist = run_north_star(args)
+        line, dist = run_learned_march(args)
         if not args.no_secondary:
             # the 32x32x3 FP64 workload (projected vs plain, the basis sweep,
             # the optional paths) as a secondary key of the same line
